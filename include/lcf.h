@@ -1,0 +1,170 @@
+/*
+ * lcf.h — C ABI of the B300 (sm_103a) localized Gaussian-windowed EVD
+ * clutter filter (Huang, Lok, Zhang, Liu, Chen: "Real-time Adaptive and
+ * Localized Spatiotemporal Clutter Filtering for Ultrasound Small Vessel
+ * Imaging").
+ *
+ * One call turns a packet of complex IQ data S (Nz x Nx pixels x Nt
+ * slow-time frames) into one power-Doppler image:
+ *
+ *   for every 2-D Gaussian window g_k (Eq. 11; centres and SD set by the
+ *   number of subsets):
+ *     R_k = C_w^H C_w = sum_p g_k(p)^2 s_p^H s_p        (Eq. 1, Eq. 12)
+ *     R_k = V_k Lambda_k V_k^H, lambda descending       (Eq. 2)
+ *     wt_k from an eigenvalue thresholding rule          (methods 1-3, 5, 6;
+ *                                                         Eq. 6, 7, 9, 10)
+ *     PD_k(p) = mean_t |(C_w V_k diag(wt_k) V_k^H)(p,t)|^2  (Eq. 4)
+ *   PD = sum_k alpha_k PD_k,  alpha_k = 1 / mean_p PD_k  (Eq. 13)
+ *
+ * Layout: the packet is iq[t][z][x], complex64 (float re, float im
+ * interleaved), x fastest, with no padding (pitch = Nx).  The PD image is
+ * out_pd[z][x], float32.
+ *
+ * Ownership: the caller owns every buffer it passes.  A plan owns all device
+ * workspace it needs; lcf_filter allocates nothing, never synchronises, and
+ * writes every pixel of out_pd (it never accumulates into caller memory).
+ * A plan may be used from one stream at a time.
+ *
+ * Errors: argument errors return synchronously (LCF_EINVAL, nothing is
+ * launched).  CUDA launch errors return LCF_ECUDA.  Conditions found on the
+ * device (a Jacobi sweep cap hit, a subset with zero flow power) are written
+ * to a per-window status word that lcf_plan_status reads.
+ */
+#ifndef LCF_H_
+#define LCF_H_
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lcf_plan lcf_plan;
+
+typedef enum {
+  LCF_OK = 0,
+  LCF_EINVAL = 1,        /* bad argument or configuration                     */
+  LCF_ENOMEM = 2,        /* device or host allocation failed at plan_create    */
+  LCF_ECUDA = 3,         /* a CUDA call failed (launch, copy, capture)          */
+  LCF_ENOCONV = 4,       /* some window's Jacobi EVD hit its sweep cap          */
+  LCF_ETIMEOUT = 5,      /* a bounded device-side wait gave up                  */
+  LCF_EDEGENERATE = 6,   /* some window had zero flow power (its alpha set 0)   */
+  LCF_EUNSUPPORTED = 7   /* valid request this build does not implement         */
+} lcf_status;
+
+/* Eigenvalue thresholding rules (the paper's methods; k = number of
+ * rejected components, i = 1..Nt in descending eigenvalue order). */
+enum {
+  LCF_T_FIXED = 0,          /* hard, fixed k = k_fixed                             */
+  LCF_T_CURVATURE = 1,      /* method 1, Eq. 6: max curvature of the normalised
+                               log10-eigenvalue curve (scaling factor beta)       */
+  LCF_T_SLOPE = 2,          /* method 2: leading components whose normalised
+                               log-curve descent is steeper than beta             */
+  LCF_T_MEDIAN = 3,         /* method 3, Eq. 7: reject lambda > beta * median      */
+  LCF_T_SIGMOID = 4,        /* method 5, Eq. 9: wt_i = 1/(1+exp(-beta (i-k))),
+                               k from rule k_src with factor beta_src             */
+  LCF_T_ADAPTIVE_SOFT = 5,  /* method 6, Eq. 10: wt_i ~ win(i) / lambda_i^beta    */
+  LCF_T_NONE = 6            /* wt = 1 (identity reconstruction, for checks)       */
+};
+
+/* Status bits per window (lcf_plan_status). */
+enum { LCF_WFLAG_NOCONV = 1, LCF_WFLAG_DEGENERATE = 2 };
+
+/* Compute paths.  LCF_PATH_SIMT is the plain FP32 GPU path (CUDA cores,
+ * FP32 products, FP32 partial sums promoted to double-float);
+ * LCF_PATH_TC runs the Gram and the projection on the tcgen05 tensor cores
+ * as split-FP16 (hi + lo, three products) contractions with FP32
+ * accumulation promoted to double-float. */
+enum { LCF_PATH_SIMT = 0, LCF_PATH_TC = 1 };
+
+typedef struct {
+  int nz, nx, nt;          /* packet size: Nz axial x Nx lateral x Nt frames      */
+  int wz, wx;              /* window grid; Nd = wz*wx subsets                     */
+  float sigma_scale;       /* window SD = sigma_scale * window spacing (1.0)      */
+  float support_sigmas;    /* support clipped to |delta| <= this many SD (3.0);
+                              <= 0: no clipping                                    */
+  int all_ones_window;     /* 1: g == 1 on the whole image (global filter)       */
+  int thresh_mode;         /* LCF_T_*                                             */
+  float beta;              /* the rule's scaling factor                           */
+  int k_fixed;             /* k of LCF_T_FIXED (and of a FIXED k_src)             */
+  int k_src;               /* rule that supplies k to LCF_T_SIGMOID               */
+  float beta_src;          /* scaling factor of that rule                         */
+  int pd_mode;             /* 0: PD = mean over slow time, 1: sum                 */
+  int alpha_mode;          /* 0: alpha_k = Nz*Nx / sum PD_k (Eq. 13, default);
+                              1: alpha_k = 1; 2: mean over the window support     */
+  int curv_norm;           /* method 1/2 curve: 0 shifted to [0, beta*Nt];
+                              1 literal beta*y(n)/y(1)*Nt                          */
+  int gram_path;           /* LCF_PATH_*                                          */
+  int project_path;        /* LCF_PATH_*                                          */
+  int max_sweeps;          /* Jacobi sweep cap per level (<= 0: 40)               */
+} lcf_config;
+
+/* Fill *cfg with defaults for an nz x nx x nt packet and a wz x wx grid:
+ * sigma_scale 1, support 3 SD, curvature rule beta 1, PD mean, alpha by
+ * Eq. 13, tensor-core paths. */
+lcf_status lcf_config_default(lcf_config* cfg, int nz, int nx, int nt, int wz, int wx);
+
+/* Validate cfg, build the window geometry (Eq. 11) and allocate all device
+ * workspace on `device`.  Synchronous.  On success *out owns the workspace
+ * until lcf_plan_destroy.  Returns LCF_EINVAL (cfg invalid), LCF_ENOMEM,
+ * LCF_ECUDA or LCF_EUNSUPPORTED (e.g. nt beyond the EVD kernel's limit). */
+lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_plan** out);
+
+/* Filter one packet.  d_iq: device pointer to iq[nt][nz][nx] complex64
+ * (8-byte aligned).  d_out_pd: device pointer to out_pd[nz][nx] float32.
+ * Asynchronous on `stream`; no allocation, no synchronisation. */
+lcf_status lcf_filter(lcf_plan* plan, const void* d_iq, float* d_out_pd, cudaStream_t stream);
+
+/* Same computation with HOST buffers: copies h_iq to the device, filters,
+ * copies the image back to h_out_pd and synchronises `stream`.  Pinned host
+ * memory makes the copies asynchronous DMA; pageable memory also works. */
+lcf_status lcf_filter_host(lcf_plan* plan, const void* h_iq, float* h_out_pd, cudaStream_t stream);
+
+/* Sliding-packet processing (packets of nt frames every `stride` frames, as
+ * the paper's real-time processing does).  d_frames: device frames
+ * [n_frames][nz][nx] complex64; d_out_pd: [n_packets][nz][nx] with
+ * n_packets = (n_frames - nt) / stride + 1.  Asynchronous. */
+lcf_status lcf_filter_stream(lcf_plan* plan, const void* d_frames, int n_frames, int stride,
+                             float* d_out_pd, cudaStream_t stream);
+
+/* Synchronise the plan's last stream and read the per-window status words of
+ * the last filter call into per_window_flags[Nd] (host, may be NULL).
+ * Returns LCF_ENOCONV / LCF_EDEGENERATE if any window raised that flag. */
+lcf_status lcf_plan_status(lcf_plan* plan, int* per_window_flags);
+
+/* Copy the last call's intermediates to host memory (synchronises).  Any
+ * pointer may be NULL.  eig: [Nd][Nt] eigenvalues, descending; wt: [Nd][Nt]
+ * weights; k: [Nd] cutoffs (-1 for soft rules); alpha: [Nd]. */
+lcf_status lcf_debug_dump(lcf_plan* plan, double* eig, float* wt, int* k, float* alpha);
+
+/* Copy the last call's windowed Gram matrices R_k (Eq. 12) to host:
+ * R: [Nd][Nt][Nt] complex double (re, im interleaved, row-major). */
+lcf_status lcf_debug_gram(lcf_plan* plan, double* R);
+
+/* Copy the last call's eigenvectors to host: V: [Nd][Nt][Nt] complex
+ * float, column j = eigenvector of eig[j] (row-major, V[i][j]). */
+lcf_status lcf_debug_eigvecs(lcf_plan* plan, float* V);
+
+/* Reconstruct the filtered IQ of one subset (Eq. 4, C-hat = C_w V Lambda-hat
+ * V^H) from the last call's eigen-decomposition, for validation.  d_iq is
+ * the same packet; d_filt: device [nt][nz][nx] complex64, zero outside the
+ * subset's support.  Asynchronous. */
+lcf_status lcf_debug_filtered_iq(lcf_plan* plan, const void* d_iq, int subset, void* d_filt,
+                                 cudaStream_t stream);
+
+/* Number of windows and the support box of window k: box = {z0, z1, x0, x1}
+ * (half-open). */
+lcf_status lcf_plan_windows(lcf_plan* plan, int* nd, int k, int* box);
+
+/* Bytes of device workspace the plan holds. */
+size_t lcf_plan_workspace_bytes(const lcf_plan* plan);
+
+lcf_status lcf_plan_destroy(lcf_plan* plan);
+
+const char* lcf_status_string(lcf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LCF_H_ */

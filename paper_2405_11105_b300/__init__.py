@@ -1,0 +1,225 @@
+"""Python binding of the B300 localized EVD clutter filter (C ABI in include/lcf.h).
+
+Argument marshalling only: every step of the filter runs in the CUDA library
+``_lib/liblcf.so`` (sm_103a).  The functions keep the C names; ``Plan`` wraps
+them for torch tensors (PyTorch provides device memory and streams).
+
+There is no CPU fallback: if the library is missing, importing the binding
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
+
+LCF_OK, LCF_EINVAL, LCF_ENOMEM, LCF_ECUDA, LCF_ENOCONV, LCF_ETIMEOUT, LCF_EDEGENERATE, LCF_EUNSUPPORTED = range(8)
+(LCF_T_FIXED, LCF_T_CURVATURE, LCF_T_SLOPE, LCF_T_MEDIAN, LCF_T_SIGMOID, LCF_T_ADAPTIVE_SOFT,
+ LCF_T_NONE) = range(7)
+LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE = 1, 2
+LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
+
+
+class lcf_config(C.Structure):
+    _fields_ = [("nz", C.c_int), ("nx", C.c_int), ("nt", C.c_int), ("wz", C.c_int), ("wx", C.c_int),
+                ("sigma_scale", C.c_float), ("support_sigmas", C.c_float),
+                ("all_ones_window", C.c_int), ("thresh_mode", C.c_int), ("beta", C.c_float),
+                ("k_fixed", C.c_int), ("k_src", C.c_int), ("beta_src", C.c_float),
+                ("pd_mode", C.c_int), ("alpha_mode", C.c_int), ("curv_norm", C.c_int),
+                ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int)]
+
+
+class LcfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {lcf_status_string(status)} (status {status})")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2405_11105_b300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    vp, ip, dp, fp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_float)
+    sigs = {
+        "lcf_config_default": ([C.POINTER(lcf_config), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
+        "lcf_plan_create": ([C.POINTER(lcf_config), C.c_int, C.POINTER(vp)], C.c_int),
+        "lcf_filter": ([vp, vp, vp, vp], C.c_int),
+        "lcf_filter_host": ([vp, vp, vp, vp], C.c_int),
+        "lcf_filter_stream": ([vp, vp, C.c_int, C.c_int, vp, vp], C.c_int),
+        "lcf_plan_status": ([vp, ip], C.c_int),
+        "lcf_debug_dump": ([vp, dp, fp, ip, fp], C.c_int),
+        "lcf_debug_gram": ([vp, dp], C.c_int),
+        "lcf_debug_eigvecs": ([vp, fp], C.c_int),
+        "lcf_debug_filtered_iq": ([vp, vp, C.c_int, vp, vp], C.c_int),
+        "lcf_plan_windows": ([vp, ip, C.c_int, ip], C.c_int),
+        "lcf_plan_workspace_bytes": ([vp], C.c_size_t),
+        "lcf_plan_destroy": ([vp], C.c_int),
+        "lcf_status_string": ([C.c_int], C.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+_lib = _load()
+
+# ---- C-named wrappers (raw pointers as ints) ----
+
+
+def lcf_status_string(s: int) -> str:
+    return _lib.lcf_status_string(int(s)).decode()
+
+
+def lcf_config_default(nz, nx, nt, wz, wx) -> lcf_config:
+    c = lcf_config()
+    _check(_lib.lcf_config_default(C.byref(c), nz, nx, nt, wz, wx), "lcf_config_default")
+    return c
+
+
+def lcf_plan_create(cfg: lcf_config, device: int = 0) -> int:
+    h = C.c_void_p()
+    _check(_lib.lcf_plan_create(C.byref(cfg), int(device), C.byref(h)), "lcf_plan_create")
+    return h.value
+
+
+def lcf_filter(plan: int, d_iq: int, d_out_pd: int, stream: int = 0) -> int:
+    return _lib.lcf_filter(plan, d_iq, d_out_pd, stream)
+
+
+def lcf_filter_host(plan: int, h_iq: int, h_out_pd: int, stream: int = 0) -> int:
+    return _lib.lcf_filter_host(plan, h_iq, h_out_pd, stream)
+
+
+def lcf_filter_stream(plan: int, d_frames: int, n_frames: int, stride: int, d_out: int, stream: int = 0) -> int:
+    return _lib.lcf_filter_stream(plan, d_frames, int(n_frames), int(stride), d_out, stream)
+
+
+def lcf_plan_destroy(plan: int) -> int:
+    return _lib.lcf_plan_destroy(plan)
+
+
+def _check(s: int, where: str):
+    if s != LCF_OK:
+        raise LcfError(s, where)
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class Plan:
+    """A filter plan on one device.  Tensors are torch tensors on that device."""
+
+    def __init__(self, cfg: lcf_config, device: int = 0):
+        self.cfg = cfg
+        self.device = device
+        self.handle = lcf_plan_create(cfg, device)
+        nd = C.c_int()
+        _check(_lib.lcf_plan_windows(self.handle, C.byref(nd), -1, None), "lcf_plan_windows")
+        self.nd = nd.value
+
+    @staticmethod
+    def make(nz, nx, nt, wz, wx, device=0, **kw) -> "Plan":
+        c = lcf_config_default(nz, nx, nt, wz, wx)
+        for k, v in kw.items():
+            if not hasattr(c, k):
+                raise AttributeError(k)
+            setattr(c, k, v)
+        return Plan(c, device)
+
+    def close(self):
+        if self.handle:
+            lcf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(_lib.lcf_plan_workspace_bytes(self.handle))
+
+    def window_box(self, k: int):
+        box = np.zeros(4, np.int32)
+        _check(_lib.lcf_plan_windows(self.handle, None, int(k), _p(box, C.c_int)), "lcf_plan_windows")
+        return tuple(int(v) for v in box)
+
+    def filter(self, iq, out=None, stream=None):
+        """iq: complex64 CUDA tensor [nt, nz, nx] -> float32 PD image [nz, nx]."""
+        import torch
+        c = self.cfg
+        if iq.dtype != torch.complex64 or not iq.is_cuda or not iq.is_contiguous():
+            raise ValueError("iq must be a contiguous complex64 CUDA tensor")
+        if tuple(iq.shape) != (c.nt, c.nz, c.nx):
+            raise ValueError(f"iq shape {tuple(iq.shape)} != {(c.nt, c.nz, c.nx)}")
+        if out is None:
+            out = torch.empty((c.nz, c.nx), dtype=torch.float32, device=iq.device)
+        st = (stream or torch.cuda.current_stream(iq.device)).cuda_stream
+        _check(lcf_filter(self.handle, iq.data_ptr(), out.data_ptr(), st), "lcf_filter")
+        return out
+
+    def filter_host(self, iq_host, out_host=None, stream=None):
+        """Host buffers (numpy or pinned torch CPU tensors); synchronises."""
+        import torch
+        c = self.cfg
+        if out_host is None:
+            out_host = np.empty((c.nz, c.nx), np.float32)
+        ip = iq_host.data_ptr() if isinstance(iq_host, torch.Tensor) else iq_host.ctypes.data
+        op = out_host.data_ptr() if isinstance(out_host, torch.Tensor) else out_host.ctypes.data
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        _check(lcf_filter_host(self.handle, ip, op, st), "lcf_filter_host")
+        return out_host
+
+    def filter_stream(self, frames, stride: int, out=None, stream=None):
+        import torch
+        c = self.cfg
+        nf = frames.shape[0]
+        npk = (nf - c.nt) // stride + 1
+        if out is None:
+            out = torch.empty((npk, c.nz, c.nx), dtype=torch.float32, device=frames.device)
+        st = (stream or torch.cuda.current_stream(frames.device)).cuda_stream
+        _check(lcf_filter_stream(self.handle, frames.data_ptr(), nf, stride, out.data_ptr(), st),
+               "lcf_filter_stream")
+        return out
+
+    def status(self):
+        flags = np.zeros(self.nd, np.int32)
+        s = _lib.lcf_plan_status(self.handle, _p(flags, C.c_int))
+        return s, flags
+
+    def debug(self):
+        nd, nt = self.nd, self.cfg.nt
+        lam = np.zeros((nd, nt)); wt = np.zeros((nd, nt), np.float32)
+        k = np.zeros(nd, np.int32); al = np.zeros(nd, np.float32)
+        _check(_lib.lcf_debug_dump(self.handle, _p(lam, C.c_double), _p(wt, C.c_float), _p(k, C.c_int),
+                                   _p(al, C.c_float)), "lcf_debug_dump")
+        return {"lam": lam, "wt": wt, "k": k, "alpha": al}
+
+    def debug_gram(self):
+        nd, nt = self.nd, self.cfg.nt
+        R = np.zeros((nd, nt, nt), np.complex128)
+        _check(_lib.lcf_debug_gram(self.handle, R.ctypes.data_as(C.POINTER(C.c_double))), "lcf_debug_gram")
+        return R
+
+    def debug_eigvecs(self):
+        nd, nt = self.nd, self.cfg.nt
+        V = np.zeros((nd, nt, nt), np.complex64)
+        _check(_lib.lcf_debug_eigvecs(self.handle, V.ctypes.data_as(C.POINTER(C.c_float))), "lcf_debug_eigvecs")
+        return V
+
+    def debug_filtered_iq(self, iq, subset: int, stream=None):
+        import torch
+        out = torch.empty_like(iq)
+        st = (stream or torch.cuda.current_stream(iq.device)).cuda_stream
+        _check(_lib.lcf_debug_filtered_iq(self.handle, iq.data_ptr(), int(subset), out.data_ptr(), st),
+               "lcf_debug_filtered_iq")
+        return out

@@ -1,0 +1,332 @@
+// lcf_api.cu — the C ABI (include/lcf.h): plan creation with the window
+// geometry, workspace management and the per-packet launch sequence.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lcf_internal.cuh"
+
+using namespace lcf;
+
+#define LCF_CUDA(x)                          \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return LCF_ECUDA; \
+  } while (0)
+
+extern "C" const char* lcf_status_string(lcf_status s) {
+  switch (s) {
+    case LCF_OK: return "ok";
+    case LCF_EINVAL: return "invalid argument or configuration";
+    case LCF_ENOMEM: return "out of memory";
+    case LCF_ECUDA: return "CUDA error";
+    case LCF_ENOCONV: return "Jacobi EVD hit its sweep cap in some window";
+    case LCF_ETIMEOUT: return "bounded device wait gave up";
+    case LCF_EDEGENERATE: return "some window had zero flow power";
+    case LCF_EUNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+extern "C" lcf_status lcf_config_default(lcf_config* c, int nz, int nx, int nt, int wz, int wx) {
+  if (!c) return LCF_EINVAL;
+  memset(c, 0, sizeof(*c));
+  c->nz = nz; c->nx = nx; c->nt = nt; c->wz = wz; c->wx = wx;
+  c->sigma_scale = 1.0f;
+  c->support_sigmas = 3.0f;
+  c->thresh_mode = LCF_T_CURVATURE;
+  c->beta = 1.0f;
+  c->k_fixed = 0;
+  c->k_src = LCF_T_FIXED;
+  c->beta_src = 1.0f;
+  c->gram_path = LCF_PATH_SIMT;
+  c->project_path = LCF_PATH_SIMT;
+  c->max_sweeps = 40;
+  return LCF_OK;
+}
+
+static lcf_status validate(const lcf_config* c) {
+  if (!c) return LCF_EINVAL;
+  if (c->nz <= 0 || c->nx <= 0 || c->nt < 2 || c->wz <= 0 || c->wx <= 0) return LCF_EINVAL;
+  if (c->wz > c->nz || c->wx > c->nx) return LCF_EINVAL;
+  if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
+  if (c->thresh_mode < LCF_T_FIXED || c->thresh_mode > LCF_T_NONE) return LCF_EINVAL;
+  if (c->thresh_mode == LCF_T_SIGMOID && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
+  if (!isfinite(c->beta) || !isfinite(c->beta_src)) return LCF_EINVAL;
+  if (c->pd_mode < 0 || c->pd_mode > 1 || c->alpha_mode < 0 || c->alpha_mode > 2) return LCF_EINVAL;
+  if (c->curv_norm < 0 || c->curv_norm > 1) return LCF_EINVAL;
+  if (c->gram_path < LCF_PATH_SIMT || c->gram_path > LCF_PATH_TC) return LCF_EINVAL;
+  if (c->project_path < LCF_PATH_SIMT || c->project_path > LCF_PATH_TC) return LCF_EINVAL;
+  if ((long long)c->nz * c->nx * (c->nt + 1) > (1LL << 31)) return LCF_EUNSUPPORTED;
+  if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
+  return LCF_OK;
+}
+
+// Window geometry (Eq. 11): centres at the midpoints of a wz x wx grid of
+// cells, SD = sigma_scale * cell size, support |delta| <= support_sigmas*SD.
+static void build_geometry(const lcf_config& c, std::vector<Box>& boxes, std::vector<float>& gz,
+                           std::vector<float>& gx) {
+  const int nd = c.wz * c.wx;
+  boxes.resize(nd);
+  gz.assign((size_t)nd * c.nz, 0.f);
+  gx.assign((size_t)nd * c.nx, 0.f);
+  const double dz = (double)c.nz / c.wz, dx = (double)c.nx / c.wx;
+  for (int k = 0; k < nd; ++k) {
+    const int iz = k / c.wx, ix = k % c.wx;
+    Box b{0, c.nz, 0, c.nx};
+    if (c.all_ones_window) {
+      for (int z = 0; z < c.nz; ++z) gz[(size_t)k * c.nz + z] = 1.f;
+      for (int x = 0; x < c.nx; ++x) gx[(size_t)k * c.nx + x] = 1.f;
+      boxes[k] = b;
+      continue;
+    }
+    const double cz = (iz + 0.5) * dz - 0.5, cx = (ix + 0.5) * dx - 0.5;
+    const double sz = c.sigma_scale * dz, sx = c.sigma_scale * dx;
+    if (c.support_sigmas > 0.f) {
+      const double hz = c.support_sigmas * sz, hx = c.support_sigmas * sx;
+      b.z0 = (int)fmax(0.0, ceil(cz - hz));
+      b.z1 = (int)fmin((double)c.nz, floor(cz + hz) + 1.0);
+      b.x0 = (int)fmax(0.0, ceil(cx - hx));
+      b.x1 = (int)fmin((double)c.nx, floor(cx + hx) + 1.0);
+      if (b.z1 <= b.z0 || b.x1 <= b.x0) b = Box{0, 0, 0, 0};
+    }
+    for (int z = b.z0; z < b.z1; ++z) {
+      double u = (z - cz) / sz;
+      gz[(size_t)k * c.nz + z] = (float)exp(-0.5 * u * u);
+    }
+    for (int x = b.x0; x < b.x1; ++x) {
+      double u = (x - cx) / sx;
+      gx[(size_t)k * c.nx + x] = (float)exp(-0.5 * u * u);
+    }
+    boxes[k] = b;
+  }
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count, size_t* total) {
+  *total += count * sizeof(T);
+  return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+}
+
+static void free_ws(Workspace& w) {
+  void* ptrs[] = {w.gz, w.gx, w.box, w.xa, w.gpart, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
+                  w.flags, w.W, w.ncol, w.iq_stage, w.pd_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  w = Workspace();
+}
+
+static bool g_configured[64] = {false};
+
+extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_plan** out) {
+  if (!out) return LCF_EINVAL;
+  *out = nullptr;
+  lcf_status v = validate(cfg);
+  if (v != LCF_OK) return v;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LCF_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return LCF_ECUDA;
+  lcf_plan* P = new (std::nothrow) lcf_plan();
+  if (!P) { cudaSetDevice(prev); return LCF_ENOMEM; }
+  P->cfg = *cfg;
+  P->device = device;
+  P->nd = cfg->wz * cfg->wx;
+  P->nt = cfg->nt;
+  P->n1 = cfg->nt + 1;
+  P->npix = cfg->nz * cfg->nx;
+  P->gram_tiles = (P->n1 + 63) / 64;
+  cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, device);
+  {
+    int pairs = P->gram_tiles * (P->gram_tiles + 1) / 2;
+    int want = (4 * P->sm_count + pairs * P->nd - 1) / (pairs * P->nd);
+    P->gram_nsplit = want < 1 ? 1 : (want > 64 ? 64 : want);
+  }
+  P->ncp = 4 * project_cpt(P->nt);
+  std::vector<float> gz, gx;
+  build_geometry(*cfg, P->boxes, gz, gx);
+
+  Workspace& w = P->ws;
+  size_t tot = 0;
+  const size_t nd = P->nd, nt = P->nt, n1 = P->n1, npix = P->npix;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dalloc(&w.gz, nd * cfg->nz, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.gx, nd * cfg->nx, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.box, nd, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.xa, n1 * npix, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.gpart, nd * P->gram_nsplit * n1 * n1, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.lam, nd * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.V, nd * nt * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.wt, nd * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.kcut, nd, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.alpha, nd, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.flags, nd, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.W, nd * nt * P->ncp, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.ncol, nd, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.iq_stage, nt * npix, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.pd_stage, npix, &tot);
+  if (e != cudaSuccess) {
+    free_ws(w);
+    delete P;
+    cudaSetDevice(prev);
+    return e == cudaErrorMemoryAllocation ? LCF_ENOMEM : LCF_ECUDA;
+  }
+  P->ws_bytes = tot;
+  e = cudaMemcpy(w.gz, gz.data(), gz.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w.gx, gx.data(), gx.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(w.box, P->boxes.data(), nd * sizeof(Box), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(w.flags, 0, nd * sizeof(int));
+  if (e == cudaSuccess && (device >= 64 || !g_configured[device])) {
+    e = evd_configure();
+    if (e == cudaSuccess) e = project_configure();
+    if (e == cudaSuccess && device < 64) g_configured[device] = true;
+  }
+  if (e != cudaSuccess) {
+    free_ws(w);
+    delete P;
+    cudaSetDevice(prev);
+    return LCF_ECUDA;
+  }
+  cudaSetDevice(prev);
+  *out = P;
+  return LCF_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  if (c.gram_path != LCF_PATH_SIMT || c.project_path != LCF_PATH_SIMT) return LCF_EUNSUPPORTED;
+  LCF_CUDA(launch_center(P, iq, st));
+  LCF_CUDA(launch_gram_simt(P, st));
+  LCF_CUDA(launch_gram_assemble(P, st));
+  LCF_CUDA(launch_evd(P, st));
+  LCF_CUDA(launch_project_simt(P, iq, out, st));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd, cudaStream_t stream) {
+  if (!P || !d_iq || !d_out_pd) return LCF_EINVAL;
+  if (((uintptr_t)d_iq & 7) || ((uintptr_t)d_out_pd & 3)) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  lcf_status s = run_packet(P, (const float2*)d_iq, d_out_pd, stream);
+  P->last_stream = stream;
+  P->last_iq = (void*)d_iq;
+  return s;
+}
+
+extern "C" lcf_status lcf_filter_host(lcf_plan* P, const void* h_iq, float* h_out_pd, cudaStream_t stream) {
+  if (!P || !h_iq || !h_out_pd) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  const size_t in_bytes = (size_t)P->nt * P->npix * sizeof(float2);
+  LCF_CUDA(cudaMemcpyAsync(P->ws.iq_stage, h_iq, in_bytes, cudaMemcpyHostToDevice, stream));
+  lcf_status s = run_packet(P, P->ws.iq_stage, P->ws.pd_stage, stream);
+  if (s != LCF_OK) return s;
+  LCF_CUDA(cudaMemcpyAsync(h_out_pd, P->ws.pd_stage, (size_t)P->npix * sizeof(float), cudaMemcpyDeviceToHost,
+                           stream));
+  P->last_stream = stream;
+  P->last_iq = P->ws.iq_stage;
+  LCF_CUDA(cudaStreamSynchronize(stream));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_filter_stream(lcf_plan* P, const void* d_frames, int n_frames, int stride,
+                                        float* d_out_pd, cudaStream_t stream) {
+  if (!P || !d_frames || !d_out_pd || stride <= 0 || n_frames < P->nt) return LCF_EINVAL;
+  if (((uintptr_t)d_frames & 7) || ((uintptr_t)d_out_pd & 3)) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  const int npk = (n_frames - P->nt) / stride + 1;
+  const float2* fr = (const float2*)d_frames;
+  for (int i = 0; i < npk; ++i) {
+    lcf_status s = run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, stream);
+    if (s != LCF_OK) return s;
+  }
+  P->last_stream = stream;
+  P->last_iq = (void*)(fr + (size_t)(npk - 1) * stride * P->npix);
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_status(lcf_plan* P, int* per_window_flags) {
+  if (!P) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  LCF_CUDA(cudaStreamSynchronize(P->last_stream));
+  std::vector<int> f(P->nd);
+  LCF_CUDA(cudaMemcpy(f.data(), P->ws.flags, P->nd * sizeof(int), cudaMemcpyDeviceToHost));
+  if (per_window_flags) memcpy(per_window_flags, f.data(), P->nd * sizeof(int));
+  int any = 0;
+  for (int v : f) any |= v;
+  if (any & LCF_WFLAG_NOCONV) return LCF_ENOCONV;
+  if (any & LCF_WFLAG_DEGENERATE) return LCF_EDEGENERATE;
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_debug_dump(lcf_plan* P, double* eig, float* wt, int* k, float* alpha) {
+  if (!P) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  LCF_CUDA(cudaStreamSynchronize(P->last_stream));
+  const size_t nd = P->nd, nt = P->nt;
+  if (eig) LCF_CUDA(cudaMemcpy(eig, P->ws.lam, nd * nt * sizeof(double), cudaMemcpyDeviceToHost));
+  if (wt) LCF_CUDA(cudaMemcpy(wt, P->ws.wt, nd * nt * sizeof(float), cudaMemcpyDeviceToHost));
+  if (k) LCF_CUDA(cudaMemcpy(k, P->ws.kcut, nd * sizeof(int), cudaMemcpyDeviceToHost));
+  if (alpha) LCF_CUDA(cudaMemcpy(alpha, P->ws.alpha, nd * sizeof(float), cudaMemcpyDeviceToHost));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_debug_gram(lcf_plan* P, double* R) {
+  if (!P || !R) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  LCF_CUDA(cudaStreamSynchronize(P->last_stream));
+  LCF_CUDA(cudaMemcpy(R, P->ws.R, (size_t)P->nd * P->nt * P->nt * sizeof(double2), cudaMemcpyDeviceToHost));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_debug_eigvecs(lcf_plan* P, float* V) {
+  if (!P || !V) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  LCF_CUDA(cudaStreamSynchronize(P->last_stream));
+  LCF_CUDA(cudaMemcpy(V, P->ws.V, (size_t)P->nd * P->nt * P->nt * sizeof(float2), cudaMemcpyDeviceToHost));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_debug_filtered_iq(lcf_plan* P, const void* d_iq, int subset, void* d_filt,
+                                            cudaStream_t stream) {
+  if (!P || !d_iq || !d_filt || subset < 0 || subset >= P->nd) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  LCF_CUDA(launch_filtered_iq(P, (const float2*)d_iq, subset, (float2*)d_filt, stream));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_windows(lcf_plan* P, int* nd, int k, int* box) {
+  if (!P) return LCF_EINVAL;
+  if (nd) *nd = P->nd;
+  if (box) {
+    if (k < 0 || k >= P->nd) return LCF_EINVAL;
+    const Box& b = P->boxes[k];
+    box[0] = b.z0; box[1] = b.z1; box[2] = b.x0; box[3] = b.x1;
+  }
+  return LCF_OK;
+}
+
+extern "C" size_t lcf_plan_workspace_bytes(const lcf_plan* P) { return P ? P->ws_bytes : 0; }
+
+extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
+  if (!P) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  free_ws(P->ws);
+  delete P;
+  return LCF_OK;
+}

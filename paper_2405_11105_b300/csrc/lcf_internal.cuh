@@ -1,0 +1,137 @@
+// lcf_internal.cuh — plan layout, double-float helpers and kernel entry
+// points shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/lcf.h"
+
+namespace lcf {
+
+// Largest packet length the one-CTA-per-window EVD keeps in shared memory.
+constexpr int kEvdNmax = 112;
+// Subspace-iteration block of the EVD (head directions isolated exactly).
+constexpr int kEvdHead = 8;
+
+struct Box { int z0, z1, x0, x1; };
+
+struct Workspace {
+  // geometry
+  float* gz = nullptr;        // [nd][nz] Gaussian factor along z (0 outside support)
+  float* gx = nullptr;        // [nd][nx]
+  Box* box = nullptr;         // [nd]
+  // centred, augmented packet: xa[t][p] = s_p(t) - m_p (t < nt), xa[nt][p] = m_p
+  float2* xa = nullptr;       // [nt+1][nz*nx]
+  // Gram
+  double2* gpart = nullptr;   // [nd][nsplit][n1][n1] partial augmented Grams
+  double2* R = nullptr;       // [nd][nt][nt] windowed Gram (Eq. 12)
+  // EVD + weights
+  double* lam = nullptr;      // [nd][nt] descending eigenvalues
+  float2* V = nullptr;        // [nd][nt][nt] eigenvectors (columns)
+  float* wt = nullptr;        // [nd][nt]
+  int* kcut = nullptr;        // [nd]
+  float* alpha = nullptr;     // [nd]
+  int* flags = nullptr;       // [nd]
+  float2* W = nullptr;        // [nd][nt][ncp] projection weights V diag(wt sqrt(alpha/Nt))
+  int* ncol = nullptr;        // [nd]
+  // host-call staging
+  float2* iq_stage = nullptr; // [nt][nz][nx] device copy for lcf_filter_host
+  float* pd_stage = nullptr;  // [nz][nx]
+};
+
+}  // namespace lcf
+
+struct lcf_plan {
+  lcf_config cfg;
+  int device = 0;
+  int nd = 0, nt = 0, n1 = 0, npix = 0;
+  int gram_tiles = 0;   // 64-wide tiles per Gram dimension
+  int gram_nsplit = 1;  // pixel splits per window
+  int ncp = 0;          // padded projection columns
+  int sm_count = 0;
+  std::vector<lcf::Box> boxes;
+  lcf::Workspace ws;
+  size_t ws_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  void* last_iq = nullptr;
+};
+
+namespace lcf {
+
+// ----- double-float (two FP32 words) arithmetic on the FP32 pipes -----
+// B300's FP64 rate is ~1/62 of FP32, so extended precision is built from
+// error-free FP32 transformations (Knuth two-sum, FMA two-product).
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = two_sum(a.hi, b);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+// a * b with a double-float and b float
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_from_double(double d) {
+  float h = (float)d;
+  return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// complex double-float
+struct zdf { df re, im; };
+__device__ __forceinline__ zdf zdf_add(zdf a, zdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+// (a) * (b) with a complex double-float and b complex float
+__device__ __forceinline__ zdf zdf_mul_c(zdf a, float2 b) {
+  df rr = df_mul_f(a.re, b.x), ii = df_mul_f(a.im, b.y);
+  df ri = df_mul_f(a.re, b.y), ir = df_mul_f(a.im, b.x);
+  return {df_add(rr, df_neg(ii)), df_add(ri, ir)};
+}
+
+// ----- complex float helpers -----
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// ----- launchers (each returns cudaGetLastError() after the launch) -----
+cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
+cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
+cudaError_t launch_filtered_iq(const lcf_plan* P, const float2* iq, int subset, float2* out,
+                               cudaStream_t st);
+size_t evd_smem_bytes(int nt);
+cudaError_t evd_configure();
+cudaError_t project_configure();
+int project_cpt(int nt);
+
+}  // namespace lcf
