@@ -1,0 +1,288 @@
+#!/usr/bin/env python
+"""Power-Doppler frames/s of the localized EVD clutter filter on B300.
+
+Workload: 256 x 128 px, Nt = 100 complex64 packets, 8 x 8 Gaussian windows
+(64 subsets, 3-sigma supports), adaptive curvature threshold (method 1),
+alpha by Eq. 13.  One step = one packet -> one PD image.  Inputs are a ring of
+8 distinct seeded synthetic packets (210 MB, larger than the 126 MB L2),
+resident in HBM before the timed region.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NZ, NX, NT, WZ, WX = 256, 128, 100, 8, 8
+RING = 8
+METRIC = "power-Doppler frames/s (256x128 px, Nt=100, 8x8 subsets) vs plain FP32 path"
+WORKLOAD = "256x128 px x Nt=100 complex64 packets, 8x8 Gaussian windows (3-sigma support), adaptive curvature threshold"
+SUM_P = 778752          # pixels summed over the 64 window supports
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def algorithmic_work(nt=NT, nd=WZ * WX, sum_p=SUM_P):
+    """Per-launch algorithmic FLOPs of each stage (8 real flops per complex MAC)."""
+    return {
+        "gram": 0.5 * 8.0 * sum_p * nt * nt,          # Hermitian upper triangle of each R_k
+        "project": 8.0 * sum_p * nt * nt,             # C_w V for every window (one GEMM)
+        "evd": nd * 13.0 * nt ** 3,                   # Hermitian EVD with vectors (~13 n^3 real flops)
+        "prep": None, "assemble": None,
+    }
+
+
+def stage_bytes(nt=NT, npix=NZ * NX, nd=WZ * WX):
+    return {"prep": npix * nt * 8 * 2 + npix * (nt + 1) * 8, "assemble": None}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.remove(self.path)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_ring(seed0=0):
+    import numpy as np
+    from synth import REALTIME_256x128x100, generate_packet
+    return np.stack([generate_packet(REALTIME_256x128x100, seed=seed0 + i) for i in range(RING)])
+
+
+def cpu_oracle_rate(ring, n_packets, nthreads):
+    """Oracle packets/s on the host (FP64, OpenMP over windows)."""
+    import oracle as O
+    cfg = O.OracleConfig(NZ, NX, NT, WZ, WX, thresh_mode=O.T_CURVATURE, beta=1.0)
+    t0 = time.perf_counter()
+    for i in range(n_packets):
+        O.filter(ring[i % len(ring)], cfg, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return n_packets / dt, dt
+
+
+def reference_arm(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    nthreads = os.cpu_count() or 1
+    ring = make_ring(0)
+    cpu_oracle_rate(ring, max(0, args.warmup and 1), nthreads)   # page in, one warm-up packet
+    rate, dt = cpu_oracle_rate(ring, args.steps, nthreads)
+    line = {"metric": METRIC, "value": rate, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "nz": NZ, "nx": NX, "nt": NT, "windows": [WZ, WX]},
+            "cpu_baseline": {"value": rate, "unit": "frames/s", "cores": nthreads, "kind": "oracle",
+                             "sample": f"{args.steps} full packets of the workload"},
+            "e2e": {"value": rate, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="simt", choices=["simt", "tc"])
+    ap.add_argument("--cpu-packets", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import paper_2405_11105_b300 as L
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    ring = make_ring(seed0=1000 * rank)
+    d_ring = torch.from_numpy(ring).to(f"cuda:{local}")
+    out = torch.empty((NZ, NX), dtype=torch.float32, device=f"cuda:{local}")
+    st = torch.cuda.current_stream()
+
+    def plan_for(path):
+        return L.Plan.make(NZ, NX, NT, WZ, WX, device=local, thresh_mode=L.LCF_T_CURVATURE, beta=1.0,
+                           gram_path=path, project_path=path)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(plan, steps, warmup):
+        for i in range(warmup):
+            plan.filter(d_ring[i % RING], out)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(steps):
+            plan.filter(d_ring[i % RING], out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    path = L.LCF_PATH_TC if args.path == "tc" else L.LCF_PATH_SIMT
+    plan = plan_for(path)
+    with ClockSampler(local) as clk:
+        ms = timed(plan, args.steps, args.warmup)
+    clocks = clk.summary()
+    value = world * args.steps / (ms / 1e3)
+
+    # plain FP32 path (the metric's denominator) on the same ring
+    plain = plan if path == L.LCF_PATH_SIMT else plan_for(L.LCF_PATH_SIMT)
+    ms_plain = ms if plain is plan else timed(plain, args.steps, args.warmup)
+    plain_value = world * args.steps / (ms_plain / 1e3)
+
+    # per-stage device times (CUDA events between the stages on the launch stream)
+    plan.profile(True)
+    ms_prof = timed(plan, args.steps, 0)
+    stages, ncalls = plan.profile_read()
+    plan.profile(False)
+    per_launch = {k: v / max(ncalls, 1) for k, v in stages.items()}
+    work = algorithmic_work()
+    dom = max(per_launch, key=per_launch.get)
+    if dom in ("gram", "project") and path == L.LCF_PATH_TC:
+        bound, peak, peak_src = "tensor", None, "measured bf16 (dense fp16 rate is equal)"
+    else:
+        bound, peak, peak_src = "alu", FP32_PEAK_TFLOPS, "FP32 SIMT: 148 SMs x 128 lanes x 2 x 2.032 GHz"
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    if bound == "tensor":
+        peak = peaks.get("bf16_tflops", 1800.0)
+    achieved = (work.get(dom) or 0.0) / (per_launch[dom] * 1e-3) / 1e12 if work.get(dom) else None
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved and peak else None, "traffic": None,
+                "peak_source": peak_src,
+                "stage_ms_per_launch": per_launch}
+
+    # end to end through the public API with host buffers (pinned)
+    host_ring = torch.from_numpy(ring).pin_memory()
+    host_out = torch.empty((NZ, NX), dtype=torch.float32).pin_memory()
+    for i in range(args.warmup):
+        plan.filter_host(host_ring[i % RING], host_out)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        plan.filter_host(host_ring[i % RING], host_out)
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": int(NT * NZ * NX * 8), "d2h_bytes_per_step": int(NZ * NX * 4)}
+
+    st_code, flags = plan.status()
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if path == L.LCF_PATH_SIMT else "f16x3-split/f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nz": NZ, "nx": NX, "nt": NT, "windows": [WZ, WX],
+                       "path": args.path, "l2": f"ring of {RING} packets ({RING * NT * NZ * NX * 8 / 1e6:.0f} MB) > L2",
+                       "parallelism": f"replicas x{world} (independent packets)"},
+            "plain_fp32": {"value": plain_value, "unit": "frames/s", "ms_per_step": ms_plain / args.steps},
+            "vs_plain": value / plain_value,
+            "clocks": clocks, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": 5 * args.steps, "status": L.lcf_status_string(st_code)}
+    if rank == 0:
+        nthreads = os.cpu_count() or 1
+        rate, dt = cpu_oracle_rate(ring, args.cpu_packets, nthreads)
+        line["cpu_baseline"] = {"value": rate, "unit": "frames/s", "cores": nthreads, "kind": "oracle",
+                                "sample": f"{args.cpu_packets} full packets of the workload ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,6 +157,27 @@ lcf_status lcf_debug_filtered_iq(lcf_plan* plan, const void* d_iq, int subset, v
  * (half-open). */
 lcf_status lcf_plan_windows(lcf_plan* plan, int* nd, int k, int* box);
 
+/* Pipeline stages, in launch order, for lcf_plan_profile_read. */
+enum {
+  LCF_STAGE_PREP = 0,      /* packet centring (and split-precision staging)     */
+  LCF_STAGE_GRAM = 1,      /* windowed Gram contraction (Eq. 12)                */
+  LCF_STAGE_ASSEMBLE = 2,  /* cross-split reduction, Hermitian assembly         */
+  LCF_STAGE_EVD = 3,       /* EVD (Eq. 2), thresholding, alpha (Eq. 13)        */
+  LCF_STAGE_PROJECT = 4,   /* projection, |.|^2 reduction and blend (Eq. 4, 13) */
+  LCF_NSTAGES = 5
+};
+
+/* Turn per-stage device timing on (enable != 0) or off.  While on, every
+ * filter call records CUDA events between its stages on the call's stream
+ * (no synchronisation).  Enabling resets the accumulated times.  Up to 4096
+ * calls are kept between reads; older ones are dropped. */
+lcf_status lcf_plan_profile(lcf_plan* plan, int enable);
+
+/* Synchronise and return the device time of each stage summed over the
+ * calls recorded since profiling was enabled: ms[LCF_NSTAGES] (host),
+ * *n_calls = number of calls summed.  Either pointer may be NULL. */
+lcf_status lcf_plan_profile_read(lcf_plan* plan, double* ms, int* n_calls);
+
 /* Bytes of device workspace the plan holds. */
 size_t lcf_plan_workspace_bytes(const lcf_plan* plan);
 

@@ -22,6 +22,7 @@ LCF_OK, LCF_EINVAL, LCF_ENOMEM, LCF_ECUDA, LCF_ENOCONV, LCF_ETIMEOUT, LCF_EDEGEN
  LCF_T_NONE) = range(7)
 LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE = 1, 2
 LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
+STAGES = ("prep", "gram", "assemble", "evd", "project")
 
 
 class lcf_config(C.Structure):
@@ -57,6 +58,8 @@ def _load():
         "lcf_debug_filtered_iq": ([vp, vp, C.c_int, vp, vp], C.c_int),
         "lcf_plan_windows": ([vp, ip, C.c_int, ip], C.c_int),
         "lcf_plan_workspace_bytes": ([vp], C.c_size_t),
+        "lcf_plan_profile": ([vp, C.c_int], C.c_int),
+        "lcf_plan_profile_read": ([vp, dp, ip], C.c_int),
         "lcf_plan_destroy": ([vp], C.c_int),
         "lcf_status_string": ([C.c_int], C.c_char_p),
     }
@@ -190,6 +193,17 @@ class Plan:
         _check(lcf_filter_stream(self.handle, frames.data_ptr(), nf, stride, out.data_ptr(), st),
                "lcf_filter_stream")
         return out
+
+    def profile(self, enable: bool = True):
+        """Per-stage CUDA-event timing of subsequent filter calls (see lcf_plan_profile)."""
+        _check(_lib.lcf_plan_profile(self.handle, int(bool(enable))), "lcf_plan_profile")
+
+    def profile_read(self):
+        """(dict stage -> summed ms, number of calls) since profiling was enabled."""
+        ms = np.zeros(len(STAGES))
+        n = C.c_int()
+        _check(_lib.lcf_plan_profile_read(self.handle, _p(ms, C.c_double), C.byref(n)), "lcf_plan_profile_read")
+        return dict(zip(STAGES, ms.tolist())), n.value
 
     def status(self):
         flags = np.zeros(self.nd, np.int32)

@@ -208,14 +208,65 @@ struct DeviceGuard {
   }
 };
 
+// Event for stage boundary b (0..LCF_NSTAGES) of the current call, or null.
+static cudaEvent_t prof_event(lcf_plan* P, int b) {
+  if (!P->profiling) return nullptr;
+  size_t slot = (size_t)(P->prof_calls % kProfCalls) * (LCF_NSTAGES + 1) + b;
+  return P->prof_ev[slot];
+}
+
+#define LCF_MARK(b)                                              \
+  do {                                                           \
+    cudaEvent_t ev_ = prof_event(P, (b));                        \
+    if (ev_) LCF_CUDA(cudaEventRecord(ev_, st));                 \
+  } while (0)
+
 static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   if (c.gram_path != LCF_PATH_SIMT || c.project_path != LCF_PATH_SIMT) return LCF_EUNSUPPORTED;
+  LCF_MARK(LCF_STAGE_PREP);
   LCF_CUDA(launch_center(P, iq, st));
+  LCF_MARK(LCF_STAGE_GRAM);
   LCF_CUDA(launch_gram_simt(P, st));
+  LCF_MARK(LCF_STAGE_ASSEMBLE);
   LCF_CUDA(launch_gram_assemble(P, st));
+  LCF_MARK(LCF_STAGE_EVD);
   LCF_CUDA(launch_evd(P, st));
+  LCF_MARK(LCF_STAGE_PROJECT);
   LCF_CUDA(launch_project_simt(P, iq, out, st));
+  LCF_MARK(LCF_NSTAGES);
+  if (P->profiling) ++P->prof_calls;
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_profile(lcf_plan* P, int enable) {
+  if (!P) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  if (enable && P->prof_ev.empty()) {
+    P->prof_ev.resize((size_t)kProfCalls * (LCF_NSTAGES + 1));
+    for (auto& e : P->prof_ev) LCF_CUDA(cudaEventCreate(&e));
+  }
+  P->profiling = enable != 0;
+  P->prof_calls = 0;
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_profile_read(lcf_plan* P, double* ms, int* n_calls) {
+  if (!P) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  double acc[LCF_NSTAGES] = {0};
+  long n = P->prof_calls < kProfCalls ? P->prof_calls : kProfCalls;
+  if (n > 0) LCF_CUDA(cudaStreamSynchronize(P->last_stream));
+  for (long i = P->prof_calls - n; i < P->prof_calls; ++i) {
+    size_t base = (size_t)(i % kProfCalls) * (LCF_NSTAGES + 1);
+    for (int s = 0; s < LCF_NSTAGES; ++s) {
+      float t = 0.f;
+      LCF_CUDA(cudaEventElapsedTime(&t, P->prof_ev[base + s], P->prof_ev[base + s + 1]));
+      acc[s] += t;
+    }
+  }
+  if (ms) memcpy(ms, acc, sizeof(acc));
+  if (n_calls) *n_calls = (int)n;
   return LCF_OK;
 }
 
@@ -327,6 +378,7 @@ extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
   if (!P) return LCF_EINVAL;
   DeviceGuard g(P->device);
   free_ws(P->ws);
+  for (auto& e : P->prof_ev) cudaEventDestroy(e);
   delete P;
   return LCF_OK;
 }

@@ -14,6 +14,8 @@ namespace lcf {
 constexpr int kEvdNmax = 112;
 // Subspace-iteration block of the EVD (head directions isolated exactly).
 constexpr int kEvdHead = 8;
+// Calls whose stage events are kept between profile reads.
+constexpr int kProfCalls = 4096;
 
 struct Box { int z0, z1, x0, x1; };
 
@@ -56,6 +58,10 @@ struct lcf_plan {
   size_t ws_bytes = 0;
   cudaStream_t last_stream = nullptr;
   void* last_iq = nullptr;
+  // stage profiling: events[call % kProfCalls][stage boundary]
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;
+  long prof_calls = 0;
 };
 
 namespace lcf {
