@@ -50,7 +50,9 @@ typedef enum {
   LCF_ENOCONV = 4,       /* some window's Jacobi EVD hit its sweep cap          */
   LCF_ETIMEOUT = 5,      /* a bounded device-side wait gave up                  */
   LCF_EDEGENERATE = 6,   /* some window had zero flow power (its alpha set 0)   */
-  LCF_EUNSUPPORTED = 7   /* valid request this build does not implement         */
+  LCF_EUNSUPPORTED = 7,  /* valid request this build does not implement         */
+  LCF_ESCRATCH = 8       /* problem too large for lcf_gram_noalloc's static
+                            scratch (see lcf_gram_noalloc_scratch_bytes)        */
 } lcf_status;
 
 /* Eigenvalue thresholding rules (the paper's methods; k = number of
@@ -177,6 +179,31 @@ lcf_status lcf_plan_profile(lcf_plan* plan, int enable);
  * calls recorded since profiling was enabled: ms[LCF_NSTAGES] (host),
  * *n_calls = number of calls summed.  Either pointer may be NULL. */
 lcf_status lcf_plan_profile_read(lcf_plan* plan, double* ms, int* n_calls);
+
+/* Windowed Gram matrices of one packet without any allocation.  The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (real-time threads that must not wait on the allocator, hosts
+ * that own all device memory, fixed-budget embedded pipelines).
+ *
+ * Computes R_k = C_w^H C_w for every window of cfg on the CURRENT device,
+ * with the same arithmetic as the plain path's Gram stage.  d_iq: device
+ * iq[nt][nz][nx] complex64 (8-byte aligned); d_R: device output [Nd][Nt][Nt]
+ * complex double (16-byte aligned), fully written.  Asynchronous on
+ * `stream`; calls no allocator of any kind.
+ *
+ * Scratch: one file-scope static device array of
+ * lcf_gram_noalloc_scratch_bytes() bytes (64 MiB) that every GPU loading
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) and caches
+ * it; make that first call before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race.  Returns LCF_ESCRATCH when the
+ * window tables, the centred packet and one partial Gram per window do not
+ * fit (e.g. 256 x 128 x 100 with 8 x 8 windows fits; 512 x 256 x 100 does
+ * not), LCF_EINVAL for bad arguments, LCF_EUNSUPPORTED for nt > 112. */
+lcf_status lcf_gram_noalloc(const lcf_config* cfg, const void* d_iq, void* d_R, cudaStream_t stream);
+
+/* Size in bytes of lcf_gram_noalloc's static per-device scratch. */
+size_t lcf_gram_noalloc_scratch_bytes(void);
 
 /* Bytes of device workspace the plan holds. */
 size_t lcf_plan_workspace_bytes(const lcf_plan* plan);

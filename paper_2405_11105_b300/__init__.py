@@ -17,7 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
 
-LCF_OK, LCF_EINVAL, LCF_ENOMEM, LCF_ECUDA, LCF_ENOCONV, LCF_ETIMEOUT, LCF_EDEGENERATE, LCF_EUNSUPPORTED = range(8)
+(LCF_OK, LCF_EINVAL, LCF_ENOMEM, LCF_ECUDA, LCF_ENOCONV, LCF_ETIMEOUT, LCF_EDEGENERATE, LCF_EUNSUPPORTED,
+ LCF_ESCRATCH) = range(9)
 (LCF_T_FIXED, LCF_T_CURVATURE, LCF_T_SLOPE, LCF_T_MEDIAN, LCF_T_SIGMOID, LCF_T_ADAPTIVE_SOFT,
  LCF_T_NONE) = range(7)
 LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE = 1, 2
@@ -62,6 +63,8 @@ def _load():
         "lcf_plan_profile_read": ([vp, dp, ip], C.c_int),
         "lcf_plan_destroy": ([vp], C.c_int),
         "lcf_status_string": ([C.c_int], C.c_char_p),
+        "lcf_gram_noalloc": ([C.POINTER(lcf_config), vp, vp, vp], C.c_int),
+        "lcf_gram_noalloc_scratch_bytes": ([], C.c_size_t),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -105,6 +108,15 @@ def lcf_filter_stream(plan: int, d_frames: int, n_frames: int, stride: int, d_ou
 
 def lcf_plan_destroy(plan: int) -> int:
     return _lib.lcf_plan_destroy(plan)
+
+
+def lcf_gram_noalloc(cfg: lcf_config, d_iq: int, d_R: int, stream: int = 0) -> int:
+    """Windowed Gram matrices with no allocation (static per-device scratch)."""
+    return _lib.lcf_gram_noalloc(C.byref(cfg), d_iq, d_R, stream)
+
+
+def lcf_gram_noalloc_scratch_bytes() -> int:
+    return int(_lib.lcf_gram_noalloc_scratch_bytes())
 
 
 def _check(s: int, where: str):

@@ -1,0 +1,140 @@
+// k_noalloc.cu — lcf_gram_noalloc: the windowed Gram stage for callers that
+// cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc at all: real-time acquisition threads
+// that must not block on the allocator, code running under a driver or
+// framework that owns all device memory, or embedded pipelines with a fixed
+// memory budget.  This entry point computes every R_k of a packet with the
+// scratch it needs (window tables, the centred packet, per-split partial
+// Grams) in one file-scope static device array of kScratchBytes.  Every GPU
+// that loads the library holds that array until the process exits.
+//
+// The array's host-side name is only a stand-in for the device symbol, so the
+// first call on each device looks its device address up with
+// cudaGetSymbolAddress (with that device current) and caches it; that first
+// call should come before any stream capture.  All calls share the array and
+// it keeps the previous call's contents: nothing in it needs to start at
+// zero (every entry that is read is written earlier in the same call), but
+// calls whose work overlaps on the GPU (different streams, no ordering) race
+// on it.
+#include <math.h>
+
+#include "lcf_internal.cuh"
+
+namespace lcf {
+
+constexpr size_t kScratchBytes = 64ull << 20;   // 64 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+static void* g_scratch_addr[64];
+static bool g_scratch_ready[64];
+
+__global__ void center_kernel(const float2* __restrict__ iq, float2* __restrict__ xa, int nt, int npix);
+__global__ void gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1,
+                                 const Box* __restrict__ boxes, const float* __restrict__ gz,
+                                 const float* __restrict__ gx, int ntile, int nsplit,
+                                 double2* __restrict__ part);
+__global__ void gram_assemble_kernel(const double2* __restrict__ part, int nsplit, int nt,
+                                     double2* __restrict__ R);
+
+// Window geometry on the device (same definition as plan_create's):
+// centres at the cell midpoints, SD = sigma_scale * cell, support clip.
+__global__ void noalloc_geometry_kernel(int nz, int nx, int wz, int wx, float sigma_scale,
+                                        float support_sigmas, int all_ones, float* gz, float* gx,
+                                        Box* boxes) {
+  const int k = blockIdx.x;
+  const int iz = k / wx, ix = k % wx;
+  const double dz = (double)nz / wz, dx = (double)nx / wx;
+  const double cz = (iz + 0.5) * dz - 0.5, cx = (ix + 0.5) * dx - 0.5;
+  const double sz = sigma_scale * dz, sx = sigma_scale * dx;
+  Box b{0, nz, 0, nx};
+  if (!all_ones && support_sigmas > 0.f) {
+    const double hz = support_sigmas * sz, hx = support_sigmas * sx;
+    b.z0 = (int)fmax(0.0, ceil(cz - hz));
+    b.z1 = (int)fmin((double)nz, floor(cz + hz) + 1.0);
+    b.x0 = (int)fmax(0.0, ceil(cx - hx));
+    b.x1 = (int)fmin((double)nx, floor(cx + hx) + 1.0);
+    if (b.z1 <= b.z0 || b.x1 <= b.x0) b = Box{0, 0, 0, 0};
+  }
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    float v = 0.f;
+    if (z >= b.z0 && z < b.z1) {
+      double u = (z - cz) / sz;
+      v = all_ones ? 1.f : (float)exp(-0.5 * u * u);
+    }
+    gz[(size_t)k * nz + z] = v;
+  }
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    float v = 0.f;
+    if (x >= b.x0 && x < b.x1) {
+      double u = (x - cx) / sx;
+      v = all_ones ? 1.f : (float)exp(-0.5 * u * u);
+    }
+    gx[(size_t)k * nx + x] = v;
+  }
+  if (threadIdx.x == 0) boxes[k] = b;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace lcf
+
+using namespace lcf;
+
+extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, void* d_R, cudaStream_t stream) {
+  if (!c || !d_iq || !d_R) return LCF_EINVAL;
+  if (((uintptr_t)d_iq & 7) || ((uintptr_t)d_R & 15)) return LCF_EINVAL;
+  if (c->nz <= 0 || c->nx <= 0 || c->nt < 2 || c->wz <= 0 || c->wx <= 0 || c->wz > c->nz || c->wx > c->nx)
+    return LCF_EINVAL;
+  if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
+  if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
+  const size_t nd = (size_t)c->wz * c->wx, nt = c->nt, n1 = nt + 1, npix = (size_t)c->nz * c->nx;
+  const int tiles = (int)((n1 + 63) / 64), pairs = tiles * (tiles + 1) / 2;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LCF_ECUDA;
+  int sms = 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LCF_ECUDA;
+
+  // scratch layout: gz | gx | boxes | centred packet | partial Grams
+  const size_t off_gx = align256(nd * c->nz * sizeof(float));
+  const size_t off_box = off_gx + align256(nd * c->nx * sizeof(float));
+  const size_t off_xa = off_box + align256(nd * sizeof(Box));
+  const size_t off_part = off_xa + align256(n1 * npix * sizeof(float2));
+  const size_t per_split = nd * n1 * n1 * sizeof(double2);
+  if (off_part + per_split > kScratchBytes) return LCF_ESCRATCH;
+  int want = (int)((4 * sms + pairs * nd - 1) / (pairs * nd));
+  want = want < 1 ? 1 : (want > 64 ? 64 : want);
+  int nsplit = (int)((kScratchBytes - off_part) / per_split);
+  if (nsplit > want) nsplit = want;
+
+  if (!g_scratch_ready[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LCF_ECUDA;
+    g_scratch_addr[dev] = p;
+    g_scratch_ready[dev] = true;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  float* gz = reinterpret_cast<float*>(base);
+  float* gx = reinterpret_cast<float*>(base + off_gx);
+  Box* box = reinterpret_cast<Box*>(base + off_box);
+  float2* xa = reinterpret_cast<float2*>(base + off_xa);
+  double2* part = reinterpret_cast<double2*>(base + off_part);
+
+  noalloc_geometry_kernel<<<(unsigned)nd, 128, 0, stream>>>(c->nz, c->nx, c->wz, c->wx, c->sigma_scale,
+                                                            c->support_sigmas, c->all_ones_window, gz, gx, box);
+  if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
+  center_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>((const float2*)d_iq, xa, (int)nt, (int)npix);
+  if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
+  dim3 grid(pairs, nsplit, (unsigned)nd);
+  gram_simt_kernel<<<grid, 256, 0, stream>>>(xa, c->nz, c->nx, (int)n1, box, gz, gx, tiles, nsplit, part);
+  if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
+  int bx = (int)((nt * nt + 255) / 256);
+  dim3 ga(bx < 8 ? bx : 8, (unsigned)nd);
+  gram_assemble_kernel<<<ga, 256, 0, stream>>>(part, nsplit, (int)nt, (double2*)d_R);
+  if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
+  return LCF_OK;
+}
+
+extern "C" size_t lcf_gram_noalloc_scratch_bytes(void) { return kScratchBytes; }

@@ -26,6 +26,7 @@ extern "C" const char* lcf_status_string(lcf_status s) {
     case LCF_ETIMEOUT: return "bounded device wait gave up";
     case LCF_EDEGENERATE: return "some window had zero flow power";
     case LCF_EUNSUPPORTED: return "not supported by this build";
+    case LCF_ESCRATCH: return "problem too large for the no-allocation entry point's static scratch";
   }
   return "unknown status";
 }
