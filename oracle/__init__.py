@@ -79,6 +79,11 @@ def lib():
         L.ora_filter.argtypes = [fp, P(_Cfg), dp, dp, dp, ip, dp, ip, ip, dp, dp, dp, C.c_int,
                                  dp, C.c_int]
         L.ora_filter.restype = C.c_int
+        L.ora_filter_k.argtypes = [fp, P(_Cfg), dp, dp, dp, ip, dp, ip, ip, dp, dp, dp, C.c_int,
+                                   dp, C.c_int, ip]
+        L.ora_filter_k.restype = C.c_int
+        L.ora_rule_scores.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_int, dp]
+        L.ora_rule_scores.restype = C.c_int
         L.ora_eigh.argtypes = [C.c_int, dp, dp, dp, C.c_int]
         L.ora_eigh.restype = C.c_int
         L.ora_weights.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double,
@@ -121,8 +126,12 @@ class OracleResult:
 
 
 def filter(iq: np.ndarray, cfg: OracleConfig, want_R=False, want_V=False, want_pdk=False,
-           dbg_subset: int = -1, nthreads: int = 0) -> OracleResult:
-    """Run the whole localized filter on one packet iq[nt][nz][nx] (complex64)."""
+           dbg_subset: int = -1, nthreads: int = 0, k_override=None) -> OracleResult:
+    """Run the whole localized filter on one packet iq[nt][nz][nx] (complex64).
+
+    k_override: optional int array [nd]; entries >= 0 replace the rule's
+    cutoff of that window (to evaluate an equally valid cutoff at a near-tie).
+    """
     assert iq.shape == (cfg.nt, cfg.nz, cfg.nx), (iq.shape, cfg)
     nd, nt, npx = cfg.nd, cfg.nt, cfg.nz * cfg.nx
     buf = _iq_f32(iq)
@@ -135,17 +144,27 @@ def filter(iq: np.ndarray, cfg: OracleConfig, want_R=False, want_V=False, want_p
     pdk = np.zeros((nd, cfg.nz, cfg.nx)) if want_pdk else None
     filt = np.zeros((nt, cfg.nz, cfg.nx), np.complex128) if dbg_subset >= 0 else None
     cc = cfg.c()
-    rc = lib().ora_filter(_ptr(buf, C.c_float), C.byref(cc), _ptr(pd, C.c_double),
-                          _ptr(lam, C.c_double), _ptr(wt, C.c_double), _ptr(kk, C.c_int),
-                          _ptr(al, C.c_double), _ptr(fl, C.c_int), _ptr(sw, C.c_int),
-                          None if R is None else R.ctypes.data_as(C.POINTER(C.c_double)),
-                          None if V is None else V.ctypes.data_as(C.POINTER(C.c_double)),
-                          _ptr(pdk, C.c_double), int(dbg_subset),
-                          None if filt is None else filt.ctypes.data_as(C.POINTER(C.c_double)),
-                          int(nthreads))
+    ko = None if k_override is None else np.ascontiguousarray(k_override, dtype=np.int32)
+    rc = lib().ora_filter_k(_ptr(buf, C.c_float), C.byref(cc), _ptr(pd, C.c_double),
+                            _ptr(lam, C.c_double), _ptr(wt, C.c_double), _ptr(kk, C.c_int),
+                            _ptr(al, C.c_double), _ptr(fl, C.c_int), _ptr(sw, C.c_int),
+                            None if R is None else R.ctypes.data_as(C.POINTER(C.c_double)),
+                            None if V is None else V.ctypes.data_as(C.POINTER(C.c_double)),
+                            _ptr(pdk, C.c_double), int(dbg_subset),
+                            None if filt is None else filt.ctypes.data_as(C.POINTER(C.c_double)),
+                            int(nthreads), _ptr(ko, C.c_int))
     if rc != 0:
         raise RuntimeError(f"ora_filter failed: {rc}")
     return OracleResult(pd.reshape(cfg.nz, cfg.nx), lam, wt, kk, al, fl, sw, R, V, pdk, filt)
+
+
+def rule_scores(mode: int, lam: np.ndarray, beta: float = 1.0, curv_norm: int = 0) -> np.ndarray:
+    """Per-index quantity a hard rule decides on (curvature, descent, lambda/T)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    sc = np.zeros_like(lam)
+    lib().ora_rule_scores(int(mode), lam.size, _ptr(lam, C.c_double), float(beta), int(curv_norm),
+                          _ptr(sc, C.c_double))
+    return sc
 
 
 def eigh(A: np.ndarray, max_sweeps: int = 60):

@@ -358,10 +358,24 @@ int ora_weights(int mode, int n, const double* lam, double beta, int k_fixed, in
  *   Rout, Vout [nd*nt*nt] complex (row-major per window)
  *   pdk      [nd*nz*nx] per-window PD_k (full grid, 0 outside the support)
  *   dbg_subset >= 0 with filt [nt*nz*nx] complex: C-hat of that subset
+ *   k_override [nd] (nullable): where >= 0, the cutoff k of window k is this
+ *            value instead of the rule's (hard rules and the sigmoid centre);
+ *            used to evaluate a second, equally valid cutoff at a near-tie.
  * ---------------------------------------------------------------------- */
+int ora_filter_k(const float* iq, const ora_config* c, double* pd, double* lam, double* wt,
+                 int* kk, double* alpha, int* flags, int* sweeps, zc* Rout, zc* Vout,
+                 double* pdk, int dbg_subset, zc* filt, int nthreads, const int* k_override);
+
 int ora_filter(const float* iq, const ora_config* c, double* pd, double* lam, double* wt,
                int* kk, double* alpha, int* flags, int* sweeps, zc* Rout, zc* Vout,
                double* pdk, int dbg_subset, zc* filt, int nthreads) {
+  return ora_filter_k(iq, c, pd, lam, wt, kk, alpha, flags, sweeps, Rout, Vout, pdk, dbg_subset, filt,
+                      nthreads, NULL);
+}
+
+int ora_filter_k(const float* iq, const ora_config* c, double* pd, double* lam, double* wt,
+                 int* kk, double* alpha, int* flags, int* sweeps, zc* Rout, zc* Vout,
+                 double* pdk, int dbg_subset, zc* filt, int nthreads, const int* k_override) {
   int nd = c->wz * c->wx, nt = c->nt, npix = c->nz * c->nx;
   int max_sweeps = c->max_sweeps > 0 ? c->max_sweeps : 60;
   double* pdall = (double*)calloc((size_t)nd * npix, sizeof(double));
@@ -385,8 +399,15 @@ int ora_filter(const float* iq, const ora_config* c, double* pd, double* lam, do
     if (Rout) memcpy(Rout + (size_t)k * nt * nt, R, sizeof(zc) * nt * nt);
     int sw = ora_jacobi(nt, R, V, lk, max_sweeps);                  /* Eq. 2 */
     if (sw < 0) fl |= ORA_FLAG_NOCONV;
-    int kc = ora_weights(c->thresh_mode, nt, lk, c->beta, c->k_fixed, c->k_src, c->beta_src,
-                         c->curv_norm, wk);
+    int kc;
+    if (k_override && k_override[k] >= 0 && c->thresh_mode <= ORA_T_SIGMOID) {
+      /* the same weights with the cutoff given: a fixed-k rule, or the sigmoid at k */
+      int mode = (c->thresh_mode == ORA_T_SIGMOID) ? ORA_T_SIGMOID : ORA_T_FIXED;
+      kc = ora_weights(mode, nt, lk, c->beta, k_override[k], ORA_T_FIXED, 0.0, c->curv_norm, wk);
+    } else {
+      kc = ora_weights(c->thresh_mode, nt, lk, c->beta, c->k_fixed, c->k_src, c->beta_src,
+                       c->curv_norm, wk);
+    }
     /* M = V diag(wt) V^H : the parenthesised factor of Eq. 4 */
     for (int i = 0; i < nt; ++i)
       for (int j = 0; j < nt; ++j) {
@@ -452,4 +473,29 @@ int ora_eigh(int n, const zc* A, zc* V, double* lam, int max_sweeps) {
   return sw;
 }
 
-int ora_abi_version(void) { return 1; }
+/* The quantity each hard rule maximises or compares, per index n (0-based):
+ * method 1: the curvature K(n) (0 at the excluded ends); method 2: the descent
+ * -y'(n) of the normalised curve; method 3: lambda_n / (beta * median).
+ * Lets a test tell a near-tie (two cutoffs equally justified) from an error. */
+int ora_rule_scores(int mode, int n, const double* lam, double beta, int curv_norm, double* sc) {
+  double* y = (double*)malloc(sizeof(double) * n * 3);
+  double *d1 = y + n, *d2 = y + 2 * n;
+  for (int i = 0; i < n; ++i) sc[i] = 0.0;
+  if (mode == ORA_T_CURVATURE && n >= 3) {
+    norm_log_curve(lam, n, beta, curv_norm, y);
+    gradient(y, d1, n);
+    gradient(d1, d2, n);
+    for (int i = 1; i < n - 1; ++i) sc[i] = fabs(d2[i]) / pow(1.0 + d1[i] * d1[i], 1.5);
+  } else if (mode == ORA_T_SLOPE && n >= 2) {
+    norm_log_curve(lam, n, 1.0, curv_norm, y);
+    gradient(y, d1, n);
+    for (int i = 0; i < n; ++i) sc[i] = -d1[i];
+  } else if (mode == ORA_T_MEDIAN) {
+    double med = (n % 2) ? lam[n / 2] : 0.5 * (lam[n / 2 - 1] + lam[n / 2]);
+    for (int i = 0; i < n; ++i) sc[i] = lam[i] / (beta * med);
+  }
+  free(y);
+  return 0;
+}
+
+int ora_abi_version(void) { return 2; }

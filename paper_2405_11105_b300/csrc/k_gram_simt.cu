@@ -1,41 +1,80 @@
-// k_gram_simt.cu — packet centring and the plain FP32 (CUDA-core) windowed
+// k_gram_simt.cu — packet deflation and the plain FP32 (CUDA-core) windowed
 // Gram R_k = C_w^H C_w = sum_p g_k(p)^2 s_p^H s_p  (Eq. 1, Eq. 12).
 //
-// Numerics.  Each pixel row is split as s_p = c_p + m_p 1 with m_p its
-// slow-time mean.  The Gram of the augmented row [c_p, m_p] (Nt+1 entries)
-// gives R_c, u = sum g^2 conj(c) m and q = sum g^2 |m|^2, and
-//   R = R_c + u 1^T + 1 u^H + q 1 1^T
-// exactly (assembled in FP64).  Removing the static tissue echo first makes
-// the FP32 partial sums ~|moving tissue|^2 instead of ~|tissue|^2, which is
-// what keeps eigenvalues 1e-6 below the largest accurate to 1e-4.
-// Products and 32-pixel partial sums are FP32; partial sums are promoted
-// into double-float accumulators.
+// Numerics.  Each pixel row is split as s_p = c_p + sum_j a_pj phi_j, where
+// phi_j (j < d, d <= 4) are the first orthonormal DCT-II slow-time vectors
+// and a_pj = <phi_j, s_p>.  With the augmented row x_p = [c_p, a_p]
+// (Nt + d entries) and R' = sum_p g^2 x_p^H x_p,
+//   R = E^H R' E,  E = [I_Nt ; Phi^T]
+//     = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T,
+// U = R'[0:Nt, Nt:], Q = R'[Nt:, Nt:], assembled in FP64.  Slow tissue
+// motion lives in the low DCT coefficients, so the large same-sign sums
+// end up in U and Q (Nt*d + d^2 entries), which are accumulated with a
+// double-float promotion every 4 pixels; the Nt x Nt block only sums the
+// small residual c_p and uses 32-pixel FP32 partial sums.  Products are
+// FP32 throughout.
+#include <math.h>
+
 #include "lcf_internal.cuh"
 
 namespace lcf {
 
-// xa[t][p] = s_p(t) - m_p for t < nt, xa[nt][p] = m_p
-__global__ void center_kernel(const float2* __restrict__ iq, float2* __restrict__ xa, int nt,
-                              int npix) {
+// Orthonormal DCT-II slow-time vectors phi[j][t], j < nd_defl, evaluated in
+// double and stored as the float values every kernel and the assembly use.
+void dct_basis(int nt, int nd_defl, float* phi) {
+  for (int j = 0; j < nd_defl; ++j)
+    for (int t = 0; t < nt; ++t) {
+      double v = (j == 0) ? 1.0 / sqrt((double)nt)
+                          : sqrt(2.0 / nt) * cos(3.14159265358979323846 * j * (t + 0.5) / nt);
+      phi[j * nt + t] = (float)v;
+    }
+}
+
+// xa[t][p] = c_p(t) = s_p(t) - sum_j a_pj phi_j(t) (t < nt), xa[nt+j][p] = a_pj
+__global__ void center_kernel(const float2* __restrict__ iq, const float* __restrict__ phi,
+                              float2* __restrict__ xa, int nt, int nd_defl, int npix) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npix) return;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int t = 0; t < nt; ++t) acc = cadd(acc, iq[(size_t)t * npix + p]);
-  float2 m = cscale(acc, 1.0f / nt);
-  for (int t = 0; t < nt; ++t) xa[(size_t)t * npix + p] = csub(iq[(size_t)t * npix + p], m);
-  xa[(size_t)nt * npix + p] = m;
+  float2 a[kDeflateMax];
+#pragma unroll
+  for (int j = 0; j < kDeflateMax; ++j) a[j] = make_float2(0.f, 0.f);
+  for (int t = 0; t < nt; ++t) {
+    float2 v = iq[(size_t)t * npix + p];
+#pragma unroll
+    for (int j = 0; j < kDeflateMax; ++j)
+      if (j < nd_defl) {
+        float f = phi[j * nt + t];
+        a[j].x = fmaf(f, v.x, a[j].x);
+        a[j].y = fmaf(f, v.y, a[j].y);
+      }
+  }
+  for (int t = 0; t < nt; ++t) {
+    float2 v = iq[(size_t)t * npix + p];
+#pragma unroll
+    for (int j = 0; j < kDeflateMax; ++j)
+      if (j < nd_defl) {
+        float f = phi[j * nt + t];
+        v.x = fmaf(-f, a[j].x, v.x);
+        v.y = fmaf(-f, a[j].y, v.y);
+      }
+    xa[(size_t)t * npix + p] = v;
+  }
+#pragma unroll
+  for (int j = 0; j < kDeflateMax; ++j)
+    if (j < nd_defl) xa[(size_t)(nt + j) * npix + p] = a[j];
 }
 
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st) {
   int n = P->npix;
-  center_kernel<<<(n + 255) / 256, 256, 0, st>>>(iq, P->ws.xa, P->nt, n);
+  center_kernel<<<(n + 255) / 256, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n);
   return cudaGetLastError();
 }
 
 constexpr int GT = 64;   // Gram tile (complex entries per side)
 constexpr int GCH = 32;  // pixels per FP32 partial sum
 
-// grid: x = upper-triangle tile pair, y = pixel split, z = window
+// Residual block R'_cc.  grid: x = upper-triangle tile pair, y = pixel split,
+// z = window.  Writes part[k][s][i][j] for the tile's entries (i, j < n1).
 __global__ void __launch_bounds__(256, 1)
 gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1, const Box* __restrict__ boxes,
                  const float* __restrict__ gz, const float* __restrict__ gx, int ntile, int nsplit,
@@ -43,7 +82,6 @@ gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1, const Bo
   __shared__ float2 As[GCH][GT];   // g^2 conj(x_p(i))
   __shared__ float2 Bs[GCH][GT];   // x_p(j)
   const int k = blockIdx.z, s = blockIdx.y;
-  // decode the upper-triangle pair (ti <= tj)
   int ti = 0, rem = blockIdx.x;
   while (rem >= ntile - ti) { rem -= ntile - ti; ++ti; }
   const int tj = ti + rem;
@@ -68,7 +106,6 @@ gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1, const Bo
     }
 
   for (long l = l0; l < l1; l += GCH) {
-    // stage GCH pixels x GT slow-time entries of both tiles
     for (int e = threadIdx.x; e < GCH * GT; e += 256) {
       int pp = e % GCH, tt = e / GCH;
       long ll = l + pp;
@@ -102,7 +139,6 @@ gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1, const Bo
         }
     }
     __syncthreads();
-    // promote the FP32 partial sums
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -125,42 +161,167 @@ gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1, const Bo
 cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st) {
   int nt2 = P->gram_tiles * (P->gram_tiles + 1) / 2;
   dim3 grid(nt2, P->gram_nsplit, P->nd);
-  gram_simt_kernel<<<grid, 256, 0, st>>>(P->ws.xa, P->cfg.nz, P->cfg.nx, P->n1, P->ws.box, P->ws.gz,
+  gram_simt_kernel<<<grid, 256, 0, st>>>(P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ws.box, P->ws.gz,
                                           P->ws.gx, P->gram_tiles, P->gram_nsplit, P->ws.gpart);
   return cudaGetLastError();
 }
 
-// R[k][i][j] = f(i,j) + f(i,nt) + f(nt,j) + f(nt,nt), where f(a,b) is the
-// augmented Gram summed over splits (entries with a > b from conj of b,a).
-__device__ __forceinline__ double2 aug_entry(const double2* __restrict__ pk, int nsplit, int n1, int a,
-                                             int b) {
+constexpr int ACH = 32;  // pixels staged per step of the augmented-column kernel
+constexpr int APR = 4;   // pixels per FP32 partial sum there
+
+// Augmented columns Y[i][a] = sum_p g^2 conj(x_p(i)) a_p(a), i < nt + d, a < d
+// (rows i < nt give U, rows nt.. give Q).  grid: x = pixel split, y = window.
+__global__ void __launch_bounds__(256)
+gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl,
+                const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
+                int nsplit, double2* __restrict__ aug) {
+  extern __shared__ float2 Xs[];   // [ACH][nt + d]: x_p, pixel-major
+  __shared__ float g2s[ACH];
+  const int k = blockIdx.y, s = blockIdx.x;
+  const int na = nt + nd_defl, nout = na * nd_defl;
+  const Box b = boxes[k];
+  const int W = b.x1 - b.x0;
+  const long Pk = (long)(b.z1 - b.z0) * W;
+  const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
+  const int npix = nz * nx;
+  const float* gzk = gz + (size_t)k * nz;
+  const float* gxk = gx + (size_t)k * nx;
+  constexpr int OPT = 2;   // outputs per thread (nout <= (112 + 4) * 4 = 464 <= 512)
+  float2 acc[OPT];
+  df hr[OPT], hi[OPT];
+#pragma unroll
+  for (int u = 0; u < OPT; ++u) { acc[u] = make_float2(0.f, 0.f); hr[u] = {0.f, 0.f}; hi[u] = {0.f, 0.f}; }
+
+  for (long l = l0; l < l1; l += ACH) {
+    for (int e = threadIdx.x; e < ACH * na; e += blockDim.x) {
+      int pp = e % ACH, i = e / ACH;
+      long ll = l + pp;
+      float2 v = make_float2(0.f, 0.f);
+      if (ll < l1) {
+        int z = b.z0 + (int)(ll / W), x = b.x0 + (int)(ll % W);
+        v = xa[(size_t)i * npix + z * nx + x];
+        if (i == 0) { float g = gzk[z] * gxk[x]; g2s[pp] = g * g; }
+      } else if (i == 0) {
+        g2s[pp] = 0.f;
+      }
+      Xs[pp * na + i] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < OPT; ++u) {
+      int o = threadIdx.x + u * blockDim.x;
+      if (o >= nout) break;
+      int i = o / nd_defl, a = o % nd_defl;
+      if (i >= nt) {
+        // Q block: the largest entries of R', summed with exact products
+        // (g^2 * conj(x_i) * x_b in double-float) so that its rounding, which
+        // reaches every eigenvalue through Phi, stays at the double-float level
+        for (int pp = 0; pp < ACH; ++pp) {
+          float g2 = g2s[pp];
+          float2 xi = Xs[pp * na + i], xb = Xs[pp * na + nt + a];
+          df wr = two_prod_df(g2, xi.x), wi = two_prod_df(-g2, xi.y);      // g^2 conj(x_i)
+          df rr = df_mul_f(wr, xb.x), ii = df_mul_f(wi, xb.y);
+          df ri = df_mul_f(wr, xb.y), ir = df_mul_f(wi, xb.x);
+          hr[u] = df_add(hr[u], df_add(rr, df_neg(ii)));
+          hi[u] = df_add(hi[u], df_add(ri, ir));
+        }
+        continue;
+      }
+      for (int p0 = 0; p0 < ACH; p0 += APR) {
+#pragma unroll
+        for (int pp = p0; pp < p0 + APR; ++pp) {
+          float g2 = g2s[pp];
+          float2 xi = Xs[pp * na + i], xb = Xs[pp * na + nt + a];
+          float ar = g2 * xi.x, ai = -g2 * xi.y;          // g^2 conj(x_i)
+          acc[u].x = fmaf(ar, xb.x, fmaf(-ai, xb.y, acc[u].x));
+          acc[u].y = fmaf(ar, xb.y, fmaf(ai, xb.x, acc[u].y));
+        }
+        hr[u] = df_add_f(hr[u], acc[u].x);
+        hi[u] = df_add_f(hi[u], acc[u].y);
+        acc[u] = make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+  }
+  double2* out = aug + ((size_t)k * nsplit + s) * nout;
+#pragma unroll
+  for (int u = 0; u < OPT; ++u) {
+    int o = threadIdx.x + u * blockDim.x;
+    if (o < nout) out[o] = make_double2(df_to_double(hr[u]), df_to_double(hi[u]));
+  }
+}
+
+size_t gram_aug_smem_bytes(int nt, int nd_defl) { return (size_t)ACH * (nt + nd_defl) * sizeof(float2); }
+
+cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st) {
+  dim3 grid(P->aug_nsplit, P->nd);
+  gram_aug_kernel<<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
+      P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit, P->ws.gaug);
+  return cudaGetLastError();
+}
+
+// Residual-block entry summed over splits (entries with a > b from conj of b,a).
+__device__ __forceinline__ double2 cc_entry(const double2* __restrict__ pk, int nsplit, int n, int a, int b) {
   bool up = a <= b;
   int r = up ? a : b, c = up ? b : a;
   double sx = 0.0, sy = 0.0;
   for (int s = 0; s < nsplit; ++s) {
-    double2 v = pk[(size_t)s * n1 * n1 + (size_t)r * n1 + c];
+    double2 v = pk[(size_t)s * n * n + (size_t)r * n + c];
     sx += v.x;
     sy += v.y;
   }
   return up ? make_double2(sx, sy) : make_double2(sx, -sy);
 }
 
-__global__ void gram_assemble_kernel(const double2* __restrict__ part, int nsplit, int nt,
-                                     double2* __restrict__ R) {
+// R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T  (FP64)
+__global__ void gram_assemble_kernel(const double2* __restrict__ part, const double2* __restrict__ aug,
+                                     const float* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
+                                     int nd_defl, double2* __restrict__ R) {
   const int k = blockIdx.y;
-  const int n1 = nt + 1;
-  const double2* pk = part + (size_t)k * nsplit * n1 * n1;
-  __shared__ double2 u[kEvdNmax + 1];
-  __shared__ double2 q;
-  for (int i = threadIdx.x; i < nt; i += blockDim.x) u[i] = aug_entry(pk, nsplit, n1, i, nt);
-  if (threadIdx.x == 0) q = aug_entry(pk, nsplit, n1, nt, nt);
+  const int na = nt + nd_defl, nout = na * nd_defl;
+  const double2* pk = part + (size_t)k * nsplit * nt * nt;
+  const double2* ak = aug + (size_t)k * aug_nsplit * nout;
+  __shared__ double2 U[kEvdNmax][kDeflateMax];
+  __shared__ double2 Q[kDeflateMax][kDeflateMax];
+  __shared__ double ph[kDeflateMax][kEvdNmax];
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < aug_nsplit; ++s) {
+      double2 v = ak[(size_t)s * nout + o];
+      sx += v.x;
+      sy += v.y;
+    }
+    int i = o / nd_defl, a = o % nd_defl;
+    if (i < nt) U[i][a] = make_double2(sx, sy);
+    else Q[i - nt][a] = make_double2(sx, sy);
+  }
+  for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) ph[e / nt][e % nt] = (double)phi[e];
+  __syncthreads();
+  // Q is Hermitian: keep its Hermitian part so that R is exactly Hermitian
+  if (threadIdx.x == 0)
+    for (int a = 0; a < nd_defl; ++a)
+      for (int c = a; c < nd_defl; ++c) {
+        double2 x = Q[a][c], y = Q[c][a];
+        double2 h = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+        Q[a][c] = h;
+        Q[c][a] = make_double2(h.x, -h.y);
+      }
   __syncthreads();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt * nt; e += gridDim.x * blockDim.x) {
     int i = e / nt, j = e % nt;
-    double2 r = aug_entry(pk, nsplit, n1, i, j);
-    double2 ui = u[i], uj = u[j];
-    r.x += ui.x + uj.x + q.x;          // u_i + conj(u_j) + q
-    r.y += ui.y - uj.y;
+    double2 r = cc_entry(pk, nsplit, nt, i, j);
+    for (int a = 0; a < nd_defl; ++a) {
+      // U_ia phi_a(j) + phi_a(i) conj(U_ja)
+      r.x += U[i][a].x * ph[a][j] + ph[a][i] * U[j][a].x;
+      r.y += U[i][a].y * ph[a][j] - ph[a][i] * U[j][a].y;
+      double qx = 0.0, qy = 0.0;
+      for (int c = 0; c < nd_defl; ++c) {
+        qx += Q[a][c].x * ph[c][j];
+        qy += Q[a][c].y * ph[c][j];
+      }
+      r.x += ph[a][i] * qx;
+      r.y += ph[a][i] * qy;
+    }
     if (i == j) r.y = 0.0;
     R[(size_t)k * nt * nt + e] = r;
   }
@@ -168,7 +329,8 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, int nspli
 
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st) {
   dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
-  gram_assemble_kernel<<<grid, 256, 0, st>>>(P->ws.gpart, P->gram_nsplit, P->nt, P->ws.R);
+  gram_assemble_kernel<<<grid, 256, 0, st>>>(P->ws.gpart, P->ws.gaug, P->ws.phi, P->gram_nsplit, P->aug_nsplit,
+                                              P->nt, P->ndefl, P->ws.R);
   return cudaGetLastError();
 }
 

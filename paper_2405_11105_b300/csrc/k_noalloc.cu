@@ -30,13 +30,28 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 static void* g_scratch_addr[64];
 static bool g_scratch_ready[64];
 
-__global__ void center_kernel(const float2* __restrict__ iq, float2* __restrict__ xa, int nt, int npix);
+__global__ void center_kernel(const float2* __restrict__ iq, const float* __restrict__ phi,
+                              float2* __restrict__ xa, int nt, int nd_defl, int npix);
 __global__ void gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1,
                                  const Box* __restrict__ boxes, const float* __restrict__ gz,
                                  const float* __restrict__ gx, int ntile, int nsplit,
                                  double2* __restrict__ part);
-__global__ void gram_assemble_kernel(const double2* __restrict__ part, int nsplit, int nt,
-                                     double2* __restrict__ R);
+__global__ void gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl,
+                                const Box* __restrict__ boxes, const float* __restrict__ gz,
+                                const float* __restrict__ gx, int nsplit, double2* __restrict__ aug);
+__global__ void gram_assemble_kernel(const double2* __restrict__ part, const double2* __restrict__ aug,
+                                     const float* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
+                                     int nd_defl, double2* __restrict__ R);
+
+// Orthonormal DCT-II slow-time vectors (the Gram stage's deflation basis)
+__global__ void noalloc_basis_kernel(int nt, int nd_defl, float* phi) {
+  for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
+    int j = e / nt, t = e % nt;
+    double v = (j == 0) ? 1.0 / sqrt((double)nt)
+                        : sqrt(2.0 / nt) * cos(3.14159265358979323846 * j * (t + 0.5) / nt);
+    phi[e] = (float)v;
+  }
+}
 
 // Window geometry on the device (same definition as plan_create's):
 // centres at the cell midpoints, SD = sigma_scale * cell, support clip.
@@ -89,20 +104,24 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
     return LCF_EINVAL;
   if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
-  const size_t nd = (size_t)c->wz * c->wx, nt = c->nt, n1 = nt + 1, npix = (size_t)c->nz * c->nx;
-  const int tiles = (int)((n1 + 63) / 64), pairs = tiles * (tiles + 1) / 2;
+  const int ndefl = deflate_count(c->nt);
+  const size_t nd = (size_t)c->wz * c->wx, nt = c->nt, n1 = nt + ndefl, npix = (size_t)c->nz * c->nx;
+  const int tiles = (int)((nt + 63) / 64), pairs = tiles * (tiles + 1) / 2;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LCF_ECUDA;
   int sms = 148;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LCF_ECUDA;
 
-  // scratch layout: gz | gx | boxes | centred packet | partial Grams
+  // scratch layout: gz | gx | boxes | deflation basis | deflated packet |
+  //                 augmented-column partials (one per window) | residual-Gram partials
   const size_t off_gx = align256(nd * c->nz * sizeof(float));
   const size_t off_box = off_gx + align256(nd * c->nx * sizeof(float));
-  const size_t off_xa = off_box + align256(nd * sizeof(Box));
-  const size_t off_part = off_xa + align256(n1 * npix * sizeof(float2));
-  const size_t per_split = nd * n1 * n1 * sizeof(double2);
+  const size_t off_phi = off_box + align256(nd * sizeof(Box));
+  const size_t off_xa = off_phi + align256((size_t)ndefl * nt * sizeof(float));
+  const size_t off_aug = off_xa + align256(n1 * npix * sizeof(float2));
+  const size_t off_part = off_aug + align256(nd * n1 * ndefl * sizeof(double2));
+  const size_t per_split = nd * nt * nt * sizeof(double2);
   if (off_part + per_split > kScratchBytes) return LCF_ESCRATCH;
   int want = (int)((4 * sms + pairs * nd - 1) / (pairs * nd));
   want = want < 1 ? 1 : (want > 64 ? 64 : want);
@@ -119,20 +138,28 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   float* gz = reinterpret_cast<float*>(base);
   float* gx = reinterpret_cast<float*>(base + off_gx);
   Box* box = reinterpret_cast<Box*>(base + off_box);
+  float* phi = reinterpret_cast<float*>(base + off_phi);
   float2* xa = reinterpret_cast<float2*>(base + off_xa);
+  double2* aug = reinterpret_cast<double2*>(base + off_aug);
   double2* part = reinterpret_cast<double2*>(base + off_part);
 
   noalloc_geometry_kernel<<<(unsigned)nd, 128, 0, stream>>>(c->nz, c->nx, c->wz, c->wx, c->sigma_scale,
                                                             c->support_sigmas, c->all_ones_window, gz, gx, box);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
-  center_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>((const float2*)d_iq, xa, (int)nt, (int)npix);
+  noalloc_basis_kernel<<<1, 256, 0, stream>>>((int)nt, ndefl, phi);
+  if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
+  center_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>((const float2*)d_iq, phi, xa, (int)nt, ndefl,
+                                                                    (int)npix);
+  if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
+  gram_aug_kernel<<<dim3(1, (unsigned)nd), 256, gram_aug_smem_bytes((int)nt, ndefl), stream>>>(
+      xa, c->nz, c->nx, (int)nt, ndefl, box, gz, gx, 1, aug);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   dim3 grid(pairs, nsplit, (unsigned)nd);
-  gram_simt_kernel<<<grid, 256, 0, stream>>>(xa, c->nz, c->nx, (int)n1, box, gz, gx, tiles, nsplit, part);
+  gram_simt_kernel<<<grid, 256, 0, stream>>>(xa, c->nz, c->nx, (int)nt, box, gz, gx, tiles, nsplit, part);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   int bx = (int)((nt * nt + 255) / 256);
   dim3 ga(bx < 8 ? bx : 8, (unsigned)nd);
-  gram_assemble_kernel<<<ga, 256, 0, stream>>>(part, nsplit, (int)nt, (double2*)d_R);
+  gram_assemble_kernel<<<ga, 256, 0, stream>>>(part, aug, phi, nsplit, 1, (int)nt, ndefl, (double2*)d_R);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   return LCF_OK;
 }

@@ -60,7 +60,7 @@ static lcf_status validate(const lcf_config* c) {
   if (c->curv_norm < 0 || c->curv_norm > 1) return LCF_EINVAL;
   if (c->gram_path < LCF_PATH_SIMT || c->gram_path > LCF_PATH_TC) return LCF_EINVAL;
   if (c->project_path < LCF_PATH_SIMT || c->project_path > LCF_PATH_TC) return LCF_EINVAL;
-  if ((long long)c->nz * c->nx * (c->nt + 1) > (1LL << 31)) return LCF_EUNSUPPORTED;
+  if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
   return LCF_OK;
 }
@@ -112,7 +112,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 }
 
 static void free_ws(Workspace& w) {
-  void* ptrs[] = {w.gz, w.gx, w.box, w.xa, w.gpart, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
+  void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.xa, w.gpart, w.gaug, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
                   w.flags, w.W, w.ncol, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -137,14 +137,17 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   P->device = device;
   P->nd = cfg->wz * cfg->wx;
   P->nt = cfg->nt;
-  P->n1 = cfg->nt + 1;
+  P->ndefl = deflate_count(cfg->nt);
+  P->n1 = cfg->nt + P->ndefl;
   P->npix = cfg->nz * cfg->nx;
-  P->gram_tiles = (P->n1 + 63) / 64;
+  P->gram_tiles = (P->nt + 63) / 64;
   cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, device);
   {
     int pairs = P->gram_tiles * (P->gram_tiles + 1) / 2;
     int want = (4 * P->sm_count + pairs * P->nd - 1) / (pairs * P->nd);
     P->gram_nsplit = want < 1 ? 1 : (want > 64 ? 64 : want);
+    int wa = (2 * P->sm_count + P->nd - 1) / P->nd;
+    P->aug_nsplit = wa < 1 ? 1 : (wa > 64 ? 64 : wa);
   }
   P->ncp = 4 * project_cpt(P->nt);
   std::vector<float> gz, gx;
@@ -157,8 +160,10 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.gz, nd * cfg->nz, &tot);
   if (e == cudaSuccess) e = dalloc(&w.gx, nd * cfg->nx, &tot);
   if (e == cudaSuccess) e = dalloc(&w.box, nd, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.phi, (size_t)P->ndefl * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.xa, n1 * npix, &tot);
-  if (e == cudaSuccess) e = dalloc(&w.gpart, nd * P->gram_nsplit * n1 * n1, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.gpart, nd * P->gram_nsplit * nt * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.gaug, nd * P->aug_nsplit * n1 * P->ndefl, &tot);
   if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.lam, nd * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.V, nd * nt * nt, &tot);
@@ -181,6 +186,11 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = cudaMemcpy(w.gx, gx.data(), gx.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(w.box, P->boxes.data(), nd * sizeof(Box), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(w.flags, 0, nd * sizeof(int));
+  if (e == cudaSuccess) {
+    std::vector<float> phi((size_t)P->ndefl * nt);
+    dct_basis((int)nt, P->ndefl, phi.data());
+    e = cudaMemcpy(w.phi, phi.data(), phi.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && (device >= 64 || !g_configured[device])) {
     e = evd_configure();
     if (e == cudaSuccess) e = project_configure();
@@ -228,6 +238,7 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   LCF_MARK(LCF_STAGE_PREP);
   LCF_CUDA(launch_center(P, iq, st));
   LCF_MARK(LCF_STAGE_GRAM);
+  LCF_CUDA(launch_gram_aug(P, st));
   LCF_CUDA(launch_gram_simt(P, st));
   LCF_MARK(LCF_STAGE_ASSEMBLE);
   LCF_CUDA(launch_gram_assemble(P, st));

@@ -14,6 +14,12 @@ namespace lcf {
 constexpr int kEvdNmax = 112;
 // Subspace-iteration block of the EVD (head directions isolated exactly).
 constexpr int kEvdHead = 8;
+// Slow-time DCT-II vectors deflated from every pixel before the Gram.
+constexpr int kDeflateMax = 4;
+__host__ __device__ inline int deflate_count(int nt) {
+  int d = nt / 4;
+  return d < 1 ? 1 : (d > kDeflateMax ? kDeflateMax : d);
+}
 // Calls whose stage events are kept between profile reads.
 constexpr int kProfCalls = 4096;
 
@@ -24,10 +30,12 @@ struct Workspace {
   float* gz = nullptr;        // [nd][nz] Gaussian factor along z (0 outside support)
   float* gx = nullptr;        // [nd][nx]
   Box* box = nullptr;         // [nd]
-  // centred, augmented packet: xa[t][p] = s_p(t) - m_p (t < nt), xa[nt][p] = m_p
-  float2* xa = nullptr;       // [nt+1][nz*nx]
+  // deflated packet: s_p = c_p + sum_j a_pj phi_j
+  float* phi = nullptr;       // [ndefl][nt] orthonormal DCT-II slow-time vectors
+  float2* xa = nullptr;       // [nt+ndefl][nz*nx]: residual c_p(t), then coefficients a_pj
   // Gram
-  double2* gpart = nullptr;   // [nd][nsplit][n1][n1] partial augmented Grams
+  double2* gpart = nullptr;   // [nd][nsplit][nt][nt] partial residual Grams
+  double2* gaug = nullptr;    // [nd][aug_nsplit][(nt+ndefl)*ndefl] partial augmented columns
   double2* R = nullptr;       // [nd][nt][nt] windowed Gram (Eq. 12)
   // EVD + weights
   double* lam = nullptr;      // [nd][nt] descending eigenvalues
@@ -49,6 +57,8 @@ struct lcf_plan {
   lcf_config cfg;
   int device = 0;
   int nd = 0, nt = 0, n1 = 0, npix = 0;
+  int ndefl = 1;        // deflated slow-time vectors; the augmented row has nt + ndefl entries
+  int aug_nsplit = 1;   // pixel splits of the augmented-column kernel
   int gram_tiles = 0;   // 64-wide tiles per Gram dimension
   int gram_nsplit = 1;  // pixel splits per window
   int ncp = 0;          // padded projection columns
@@ -97,6 +107,11 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
   e = __fmaf_rn(a.lo, b, e);
   return quick_two_sum(p, e);
 }
+// exact product of two floats as a double-float
+__device__ __forceinline__ df two_prod_df(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
 __device__ __forceinline__ df df_from_double(double d) {
   float h = (float)d;
   return {h, (float)(d - (double)h)};
@@ -129,6 +144,9 @@ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y;
 
 // ----- launchers (each returns cudaGetLastError() after the launch) -----
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
+cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st);
+size_t gram_aug_smem_bytes(int nt, int nd_defl);
+void dct_basis(int nt, int nd_defl, float* phi);
 cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);

@@ -299,3 +299,24 @@ def test_fixed_rule_bounds():
     for kf, kexp in [(-1, 0), (0, 0), (3, 3), (9, 7)]:
         wt, k = O.weights(O.T_FIXED, lam, k_fixed=kf)
         assert k == kexp and wt.sum() == 7 - kexp
+
+
+def test_rule_scores_agree_with_rules_and_override_equals_fixed():
+    # the exported deciding quantities reproduce each rule's own choice
+    lam = 10.0 ** (-(np.minimum(np.arange(1, 41), 7) - 1.0)) * (1 + 0.01 * np.arange(40))[::-1]
+    lam = np.sort(lam)[::-1]
+    sc = O.rule_scores(O.T_CURVATURE, lam, beta=1.0)
+    _, k = O.weights(O.T_CURVATURE, lam, beta=1.0)
+    assert int(np.argmax(sc)) + 1 == k
+    sc = O.rule_scores(O.T_SLOPE, lam, beta=1.1)
+    _, k = O.weights(O.T_SLOPE, lam, beta=1.1)
+    assert np.all(sc[:k] > 1.1) and sc[k] <= 1.1
+    sc = O.rule_scores(O.T_MEDIAN, lam, beta=1.43)
+    _, k = O.weights(O.T_MEDIAN, lam, beta=1.43)
+    assert np.sum(sc > 1.0) == k
+    # a cutoff override gives exactly the fixed-k filter
+    iq = generate_packet(SMALL_96x64x32, seed=3)
+    a = O.filter(iq, O.OracleConfig(96, 64, 32, 3, 3, thresh_mode=O.T_CURVATURE),
+                 k_override=np.full(9, 5, np.int32))
+    b = O.filter(iq, O.OracleConfig(96, 64, 32, 3, 3, thresh_mode=O.T_FIXED, k_fixed=5))
+    assert np.array_equal(a.pd, b.pd) and np.all(a.k == 5)
