@@ -71,7 +71,9 @@ enum {
 };
 
 /* Status bits per window (lcf_plan_status). */
-enum { LCF_WFLAG_NOCONV = 1, LCF_WFLAG_DEGENERATE = 2 };
+/* Bits 8-15 of a window's status word hold the number of Jacobi sweeps its
+ * EVD used (for tuning and convergence monitoring). */
+enum { LCF_WFLAG_NOCONV = 1, LCF_WFLAG_DEGENERATE = 2, LCF_WFLAG_SWEEP_SHIFT = 8 };
 
 /* Compute paths.  LCF_PATH_SIMT is the plain FP32 GPU path (CUDA cores,
  * FP32 products, FP32 partial sums promoted to double-float);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
  LCF_ESCRATCH) = range(9)
 (LCF_T_FIXED, LCF_T_CURVATURE, LCF_T_SLOPE, LCF_T_MEDIAN, LCF_T_SIGMOID, LCF_T_ADAPTIVE_SOFT,
  LCF_T_NONE) = range(7)
-LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE = 1, 2
+LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE, LCF_WFLAG_SWEEP_SHIFT = 1, 2, 8
 LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
 STAGES = ("prep", "gram", "assemble", "evd", "project")
 

@@ -43,7 +43,7 @@ struct EvdArgs {
 size_t evd_smem_bytes(int nt) {
   int np = nt + (nt & 1);
   int m = nt < kEvdHead ? nt : kEvdHead;
-  size_t region0 = (size_t)np * np * 16;                       // df64 B, later A + V (fp32)
+  size_t region0 = (size_t)np * (np + 1) * 16;                 // df64 B, later A + V^T (fp32, odd stride)
   size_t ys = (size_t)np * m * 8 * 2;                          // Y and Z / reflectors
   size_t small = (size_t)(np / 2) * 32 + (size_t)np * 16 + 1024;
   return region0 + ys + small;
@@ -107,7 +107,6 @@ __device__ int rule_k(int mode, const double* lam, int n, double beta, int k_fix
 }
 
 // --------------------------------------------------------------------------
-__device__ __forceinline__ float2 ldA(const float2* A, int np, int a, int b) { return A[a * np + b]; }
 
 __global__ void __launch_bounds__(EVD_THREADS, 1)
 evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArgs g,
@@ -121,9 +120,12 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
 
   zdf* Rdf = reinterpret_cast<zdf*>(smem);                             // np*np (phase C)
   float2* Rh = reinterpret_cast<float2*>(smem);                        // np*np (phase A)
-  float2* A = reinterpret_cast<float2*>(smem);                         // np*np (phase D)
-  float2* Vs = reinterpret_cast<float2*>(smem + (size_t)np * np * 8);  // np*np (phase D)
-  float2* Ys = reinterpret_cast<float2*>(smem + (size_t)np * np * 16);
+  // phase D: A row-major and V^T (Vt[col][row]) with an odd row stride so that row and
+  // column walks of the 2x2 block updates fall on distinct shared-memory banks
+  const int ld = np + 1;
+  float2* A = reinterpret_cast<float2*>(smem);                             // np*ld
+  float2* Vt = reinterpret_cast<float2*>(smem + (size_t)np * ld * 8);      // np*ld
+  float2* Ys = reinterpret_cast<float2*>(smem + (size_t)np * ld * 16);
   float2* Zs = Ys + (size_t)np * m;                                    // later: reflectors
   unsigned char* sp = reinterpret_cast<unsigned char*>(Zs + (size_t)np * m);
   int* pr_p = reinterpret_cast<int*>(sp);                sp += h * 4;
@@ -329,7 +331,9 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     __syncthreads();
   }
 
-  // ---------------- convert B to fp32 A in place (chunks keep reads ahead of writes)
+  // ---------------- convert B to fp32 A in place: entry e = a*np + b moves to a*ld + b,
+  // which only overwrites df64 entries with index <= e, already read in this or an
+  // earlier chunk
   for (int base = 0; base < np * np; base += EVD_THREADS) {
     int e = base + tid;
     float2 v = make_float2(0.f, 0.f);
@@ -338,29 +342,50 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
       v = make_float2(r.re.hi + r.re.lo, r.im.hi + r.im.lo);
     }
     __syncthreads();
-    if (e < np * np) A[e] = v;
+    if (e < np * np) A[(e / np) * ld + (e % np)] = v;
     __syncthreads();
   }
   for (int e = tid; e < np * np; e += EVD_THREADS) {  // Hermitian mirror, real diagonal
     int a = e / np, b = e % np;
-    if (a > b) A[e] = cconj(A[b * np + a]);
-    else if (a == b) A[e].y = 0.f;
+    if (a > b) A[a * ld + b] = cconj(A[b * ld + a]);
+    else if (a == b) A[a * ld + b].y = 0.f;
   }
-  // V = Q = H_0 H_1 ... H_{m-1}  (applied to I, last reflector first)
-  for (int e = tid; e < np * np; e += EVD_THREADS) Vs[e] = make_float2((e / np) == (e % np) ? 1.f : 0.f, 0.f);
+  // V = Q = H_0 H_1 ... H_{m-1} (applied to I, last reflector first); V^T row c = column c
+  for (int e = tid; e < np * ld; e += EVD_THREADS) Vt[e] = make_float2((e / ld) == (e % ld) ? 1.f : 0.f, 0.f);
   __syncthreads();
   for (int j = m - 1; j >= 0; --j) {
     const float bj = betas[j];
     for (int c = tid; c < n; c += EVD_THREADS) {
       float2 t = make_float2(0.f, 0.f);
-      for (int a = j; a < n; ++a) t = cadd(t, cmulc(Zs[a * m + j], Vs[a * np + c]));
+      for (int a = j; a < n; ++a) t = cadd(t, cmulc(Zs[a * m + j], Vt[c * ld + a]));
       t = cscale(t, bj);
-      for (int a = j; a < n; ++a) Vs[a * np + c] = csub(Vs[a * np + c], cmul(Zs[a * m + j], t));
+      for (int a = j; a < n; ++a) Vt[c * ld + a] = csub(Vt[c * ld + a], cmul(Zs[a * m + j], t));
     }
     __syncthreads();
   }
 
   // ---------------- phase D: cyclic Jacobi (round-robin), relative test
+  // Work assignment is fixed for the whole solve: this thread's 2x2 blocks (ia <= ib of the
+  // round's pair list) and its (pair, V row) items are decoded once.
+  constexpr int MAXB = 4, MAXV = 13;        // ceil(56*57/2/512), ceil(112*56/512)
+  int blk[MAXB], vit[MAXV];
+  {
+    const int nblk = h * (h + 1) / 2;
+    for (int j = 0; j < MAXB; ++j) {
+      int e = tid + j * EVD_THREADS;
+      int code = -1;
+      if (e < nblk) {
+        int ia = 0, rem = e;
+        while (rem >= h - ia) { rem -= h - ia; ++ia; }
+        code = (ia << 8) | (ia + rem);
+      }
+      blk[j] = code;
+    }
+    for (int j = 0; j < MAXV; ++j) {
+      int e = tid + j * EVD_THREADS;
+      vit[j] = (e < n * h) ? (((e / n) << 8) | (e % n)) : -1;
+    }
+  }
   int sweeps = 0, converged = 0;
   const int maxsw = g.max_sweeps > 0 ? g.max_sweeps : 40;
   for (; sweeps < maxsw; ++sweeps) {
@@ -372,8 +397,8 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
         if (i == 0) { pa = r; pb = np - 1; }
         else { pa = (r + i) % (np - 1); pb = (r - i + np - 1) % (np - 1); }
         int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
-        float app = A[p * np + p].x, aqq = A[q * np + q].x;
-        float2 b = A[p * np + q];
+        float app = A[p * ld + p].x, aqq = A[q * ld + q].x;
+        float2 b = A[p * ld + q];
         float ab = sqrtf(cabs2(b));
         float c = 1.f, dp = app, dq = aqq;
         float2 st = make_float2(0.f, 0.f);
@@ -393,22 +418,23 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
       int anyr = __syncthreads_or(rot);
       if (!anyr) continue;
       any = 1;
-      for (int e = tid; e < h * h; e += EVD_THREADS) {
-        int ia = e / h, ib = e % h;
-        if (ia > ib) continue;
-        int ra = pr_rot[ia], rb = pr_rot[ib];
+#pragma unroll
+      for (int j = 0; j < MAXB; ++j) {
+        if (blk[j] < 0) continue;
+        const int ia = blk[j] >> 8, ib = blk[j] & 255;
+        const int ra = pr_rot[ia], rb = pr_rot[ib];
         if (!ra && !rb) continue;
-        int pa = pr_p[ia], qa = pr_q[ia], pb = pr_p[ib], qb = pr_q[ib];
+        const int pa = pr_p[ia], qa = pr_q[ia], pb = pr_p[ib], qb = pr_q[ib];
         if (ia == ib) {
-          A[pa * np + pa] = make_float2(pr_dp[ia], 0.f);
-          A[qa * np + qa] = make_float2(pr_dq[ia], 0.f);
-          A[pa * np + qa] = make_float2(0.f, 0.f);
-          A[qa * np + pa] = make_float2(0.f, 0.f);
+          A[pa * ld + pa] = make_float2(pr_dp[ia], 0.f);
+          A[qa * ld + qa] = make_float2(pr_dq[ia], 0.f);
+          A[pa * ld + qa] = make_float2(0.f, 0.f);
+          A[qa * ld + pa] = make_float2(0.f, 0.f);
           continue;
         }
-        float ca = pr_c[ia], cb = pr_c[ib];
-        float2 sa = pr_s[ia], sb = pr_s[ib];
-        float2 x00 = A[pa * np + pb], x01 = A[pa * np + qb], x10 = A[qa * np + pb], x11 = A[qa * np + qb];
+        const float ca = pr_c[ia], cb = pr_c[ib];
+        const float2 sa = pr_s[ia], sb = pr_s[ib];
+        float2 x00 = A[pa * ld + pb], x01 = A[pa * ld + qb], x10 = A[qa * ld + pb], x11 = A[qa * ld + qb];
         // Y = X J_b
         float2 sbc = cconj(sb);
         float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
@@ -417,19 +443,21 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
         float2 sac = cconj(sa);
         float2 z00 = csub(cscale(y00, ca), cmul(sa, y10)), z01 = csub(cscale(y01, ca), cmul(sa, y11));
         float2 z10 = cadd(cmul(sac, y00), cscale(y10, ca)), z11 = cadd(cmul(sac, y01), cscale(y11, ca));
-        A[pa * np + pb] = z00; A[pa * np + qb] = z01; A[qa * np + pb] = z10; A[qa * np + qb] = z11;
-        A[pb * np + pa] = cconj(z00); A[qb * np + pa] = cconj(z01);
-        A[pb * np + qa] = cconj(z10); A[qb * np + qa] = cconj(z11);
+        A[pa * ld + pb] = z00; A[pa * ld + qb] = z01; A[qa * ld + pb] = z10; A[qa * ld + qb] = z11;
+        A[pb * ld + pa] = cconj(z00); A[qb * ld + pa] = cconj(z01);
+        A[pb * ld + qa] = cconj(z10); A[qb * ld + qa] = cconj(z11);
       }
-      for (int e = tid; e < n * h; e += EVD_THREADS) {
-        int rr = e / h, ia = e % h;
+#pragma unroll
+      for (int j = 0; j < MAXV; ++j) {
+        if (vit[j] < 0) continue;
+        const int ia = vit[j] >> 8, rr = vit[j] & 255;
         if (!pr_rot[ia]) continue;
-        int p = pr_p[ia], q = pr_q[ia];
-        float c = pr_c[ia];
-        float2 s = pr_s[ia];
-        float2 vp = Vs[rr * np + p], vq = Vs[rr * np + q];
-        Vs[rr * np + p] = csub(cscale(vp, c), cmul(cconj(s), vq));
-        Vs[rr * np + q] = cadd(cmul(s, vp), cscale(vq, c));
+        const int p = pr_p[ia], q = pr_q[ia];
+        const float c = pr_c[ia];
+        const float2 s = pr_s[ia];
+        float2 vp = Vt[p * ld + rr], vq = Vt[q * ld + rr];
+        Vt[p * ld + rr] = csub(cscale(vp, c), cmul(cconj(s), vq));
+        Vt[q * ld + rr] = cadd(cmul(s, vp), cscale(vq, c));
       }
       __syncthreads();
     }
@@ -438,22 +466,22 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
 
   // ---------------- phase E: sort, phase-fix, weights, projection weights
   for (int i = tid; i < n; i += EVD_THREADS) {
-    float di = A[i * np + i].x;
+    float di = A[i * ld + i].x;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      float dj = A[j * np + j].x;
+      float dj = A[j * ld + j].x;
       rank += (dj > di) || (dj == di && j < i);
     }
     perm[rank] = i;
   }
   __syncthreads();
-  for (int i = tid; i < n; i += EVD_THREADS) lam_s[i] = (double)A[perm[i] * np + perm[i]].x * scale;
+  for (int i = tid; i < n; i += EVD_THREADS) lam_s[i] = (double)A[perm[i] * ld + perm[i]].x * scale;
   // phase of each (sorted) eigenvector: largest-magnitude entry made real positive
   for (int jj = warp; jj < n; jj += EVD_THREADS / 32) {
     int col = perm[jj];
     float best = -1.f; int bi = 0;
     for (int a = lane; a < n; a += 32) {
-      float mg = cabs2(Vs[a * np + col]);
+      float mg = cabs2(Vt[col * ld + a]);
       if (mg > best) { best = mg; bi = a; }
     }
     for (int o = 16; o; o >>= 1) {
@@ -462,7 +490,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     if (lane == 0) {
-      float2 v = Vs[bi * np + col];
+      float2 v = Vt[col * ld + bi];
       float mg = sqrtf(cabs2(v));
       sh_phase[jj] = mg > 0.f ? make_float2(v.x / mg, -v.y / mg) : make_float2(1.f, 0.f);
     }
@@ -470,7 +498,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
   __syncthreads();
   for (int e = tid; e < n * n; e += EVD_THREADS) {
     int a = e / n, jj = e % n;
-    V_out[(size_t)k * n * n + e] = cmul(Vs[a * np + perm[jj]], sh_phase[jj]);
+    V_out[(size_t)k * n * n + e] = cmul(Vt[perm[jj] * ld + a], sh_phase[jj]);
   }
   // thresholding rule (double precision, one thread)
   double* wts = reinterpret_cast<double*>(Rdf);  // scratch: A's storage is dead after the sort copy
@@ -504,7 +532,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     for (int i = 0; i < n; ++i) S += wts[i] * wts[i] * lam_s[i];
     double pdsum = g.pd_mode == 0 ? S / n : S;
     double al;
-    int fl = converged ? 0 : LCF_WFLAG_NOCONV;
+    int fl = (converged ? 0 : LCF_WFLAG_NOCONV) | ((sweeps < 255 ? sweeps : 255) << LCF_WFLAG_SWEEP_SHIFT);
     if (g.alpha_mode == 1) al = 1.0;
     else {
       Box bx = boxes[k];
