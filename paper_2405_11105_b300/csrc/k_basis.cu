@@ -1,0 +1,182 @@
+// k_basis.cu — per-packet slow-time deflation basis for the Gram stage.
+//
+// The Gram identity R = E^H R' E (see k_gram_simt.cu) is exact for any basis
+// Phi; the basis only decides how much of each pixel's signal is removed
+// before the FP32 / tensor-core partial sums.  The tissue's slow-time
+// behaviour is shared by the whole field of view (global motion), so the top
+// d eigenvectors of a global Gram G = sum_p s_p^H s_p (taken over every
+// fourth image row) capture it: after deflation the residual is blood and
+// noise, and the rounding of the partial sums (including the tensor core's
+// round-toward-zero accumulation) is relative to that small residual.
+//
+//  global_gram_kernel : FP32 partial Grams of the subsampled packet (64x64
+//                       complex tiles, upper triangle), one per pixel split;
+//  basis_kernel       : one CTA sums the partials, scales, and runs subspace
+//                       iteration from the DCT-II start (CGS2 by one warp),
+//                       writing phi[j][t] (complex, orthonormal columns).
+#include <math.h>
+
+#include "lcf_internal.cuh"
+
+namespace lcf {
+
+constexpr int BG_T = 64;        // tile side
+constexpr int BG_CH = 32;       // pixels staged per step
+constexpr int BASIS_ITERS = 8;
+
+__host__ __device__ inline int basis_zstep(int nz) { return nz >= 16 ? 4 : 1; }
+
+// grid: x = upper-triangle tile pair, y = pixel split.  Pixels: rows z = 0, zs, 2zs, ...
+__global__ void __launch_bounds__(256)
+global_gram_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int zs, int ntile, int nsplit,
+                   float2* __restrict__ part) {
+  __shared__ float2 As[BG_CH][BG_T];
+  __shared__ float2 Bs[BG_CH][BG_T];
+  const int s = blockIdx.y;
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= ntile - ti) { rem -= ntile - ti; ++ti; }
+  const int tj = ti + rem;
+  const int nzs = (nz + zs - 1) / zs;
+  const long Pk = (long)nzs * nx;
+  const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
+  const size_t npix = (size_t)nz * nx;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+  for (long l = l0; l < l1; l += BG_CH) {
+    for (int e = threadIdx.x; e < BG_CH * BG_T; e += 256) {
+      int pp = e % BG_CH, tt = e / BG_CH;
+      long ll = l + pp;
+      float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+      if (ll < l1) {
+        size_t p = (size_t)(ll / nx) * zs * nx + (size_t)(ll % nx);
+        int i = ti * BG_T + tt, j = tj * BG_T + tt;
+        if (i < nt) { float2 v = iq[(size_t)i * npix + p]; va = make_float2(v.x, -v.y); }
+        if (j < nt) vb = iq[(size_t)j * npix + p];
+      }
+      As[pp][tt] = va;
+      Bs[pp][tt] = vb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int pp = 0; pp < BG_CH; ++pp) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[pp][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[pp][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[a][c].x = fmaf(av[a].x, bv[c].x, fmaf(-av[a].y, bv[c].y, acc[a][c].x));
+          acc[a][c].y = fmaf(av[a].x, bv[c].y, fmaf(av[a].y, bv[c].x, acc[a][c].y));
+        }
+    }
+    __syncthreads();
+  }
+  float2* out = part + (size_t)s * nt * nt;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int i = ti * BG_T + ty + 16 * a, j = tj * BG_T + tx + 16 * c;
+      if (i < nt && j < nt) out[(size_t)i * nt + j] = acc[a][c];
+    }
+}
+
+// One CTA of 256 threads.  smem: G (nt*nt float2) + Y, Z (nt*d float2 each).
+__global__ void __launch_bounds__(256)
+basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, float2* __restrict__ phi) {
+  extern __shared__ float2 bsm[];
+  float2* G = bsm;                       // nt*nt
+  float2* Y = G + (size_t)nt * nt;       // nt*d, column j at Y[t*d + j]
+  float2* Z = Y + (size_t)nt * nd_defl;
+  __shared__ float gmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, d = nd_defl;
+  for (int e = tid; e < nt * nt; e += blockDim.x) {
+    int i = e / nt, j = e % nt;
+    bool up = i <= j;
+    int r = up ? i : j, c = up ? j : i;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < nsplit; ++s) acc = cadd(acc, part[(size_t)s * nt * nt + (size_t)r * nt + c]);
+    G[e] = up ? acc : cconj(acc);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int i = 0; i < nt; ++i) m = fmaxf(m, G[i * nt + i].x);
+    gmax = m > 0.f ? m : 1.f;
+  }
+  __syncthreads();
+  const float inv = 1.f / gmax;
+  for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = cscale(G[e], inv);
+  // DCT-II start
+  for (int e = tid; e < nt * d; e += blockDim.x) {
+    int t = e / d, j = e % d;
+    float v = (j == 0) ? rsqrtf((float)nt) : sqrtf(2.f / nt) * cosf(3.14159265f * j * (t + 0.5f) / nt);
+    Y[e] = make_float2(v, 0.f);
+  }
+  __syncthreads();
+  for (int it = 0; it < BASIS_ITERS; ++it) {
+    for (int e = tid; e < nt * d; e += blockDim.x) {
+      int t = e / d, j = e % d;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int u = 0; u < nt; ++u) acc = cadd(acc, cmul(G[t * nt + u], Y[u * d + j]));
+      Z[e] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {  // CGS2 orthonormalisation of Z -> Y
+      for (int j = 0; j < d; ++j) {
+        for (int pass = 0; pass < 2; ++pass)
+          for (int i = 0; i < j; ++i) {
+            float2 c = make_float2(0.f, 0.f);
+            for (int t = lane; t < nt; t += 32) c = cadd(c, cmulc(Y[t * d + i], Z[t * d + j]));
+            for (int o = 16; o; o >>= 1) { c.x += __shfl_xor_sync(~0u, c.x, o); c.y += __shfl_xor_sync(~0u, c.y, o); }
+            for (int t = lane; t < nt; t += 32) Z[t * d + j] = csub(Z[t * d + j], cmul(c, Y[t * d + i]));
+            __syncwarp();
+          }
+        float nr = 0.f;
+        for (int t = lane; t < nt; t += 32) nr += cabs2(Z[t * d + j]);
+        for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
+        if (nr > 0.f) {
+          float sc = rsqrtf(nr);
+          for (int t = lane; t < nt; t += 32) Y[t * d + j] = cscale(Z[t * d + j], sc);
+        }  // a vanishing direction keeps its previous (orthonormal) vector
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  // A row signal s_p = a phi^T puts conj(phi) in the column space of G, so the
+  // deflation basis is the conjugate of G's top eigenvectors.
+  for (int e = tid; e < nt * d; e += blockDim.x) {
+    int t = e / d, j = e % d;
+    phi[j * nt + t] = cconj(Y[e]);
+  }
+}
+
+size_t basis_smem_bytes(int nt, int nd_defl) { return ((size_t)nt * nt + 2 * (size_t)nt * nd_defl) * sizeof(float2); }
+
+cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  int ntile = (P->nt + BG_T - 1) / BG_T;
+  dim3 grid(ntile * (ntile + 1) / 2, P->basis_nsplit);
+  global_gram_kernel<<<grid, 256, 0, st>>>(iq, c.nz, c.nx, P->nt, basis_zstep(c.nz), ntile, P->basis_nsplit,
+                                           P->ws.gglob);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  basis_kernel<<<1, 256, basis_smem_bytes(P->nt, P->ndefl), st>>>(P->ws.gglob, P->basis_nsplit, P->nt, P->ndefl,
+                                                                  P->ws.phi);
+  return cudaGetLastError();
+}
+
+cudaError_t basis_configure() {
+  return cudaFuncSetAttribute(basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)basis_smem_bytes(kEvdNmax, kDeflateMax));
+}
+
+}  // namespace lcf

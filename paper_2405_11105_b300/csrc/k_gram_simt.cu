@@ -1,40 +1,32 @@
 // k_gram_simt.cu — packet deflation and the plain FP32 (CUDA-core) windowed
 // Gram R_k = C_w^H C_w = sum_p g_k(p)^2 s_p^H s_p  (Eq. 1, Eq. 12).
 //
-// Numerics.  Each pixel row is split as s_p = c_p + sum_j a_pj phi_j, where
-// phi_j (j < d, d <= 4) are the first orthonormal DCT-II slow-time vectors
-// and a_pj = <phi_j, s_p>.  With the augmented row x_p = [c_p, a_p]
-// (Nt + d entries) and R' = sum_p g^2 x_p^H x_p,
+// Numerics.  Each pixel row is split as s_p = c_p + sum_j a_pj phi_j^T, where
+// phi_j (j < d, d <= 4) is the per-packet slow-time basis of k_basis.cu (the
+// dominant global tissue modes) and a_pj = sum_t conj(phi_j(t)) s_p(t).  With
+// the augmented row x_p = [c_p, a_p] (Nt + d entries) and R' = sum_p g^2 x_p^H x_p,
 //   R = E^H R' E,  E = [I_Nt ; Phi^T]
-//     = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T,
-// U = R'[0:Nt, Nt:], Q = R'[Nt:, Nt:], assembled in FP64.  Slow tissue
-// motion lives in the low DCT coefficients, so the large same-sign sums
-// end up in U and Q (Nt*d + d^2 entries), which are accumulated with a
-// double-float promotion every 4 pixels; the Nt x Nt block only sums the
-// small residual c_p and uses 32-pixel FP32 partial sums.  Products are
-// FP32 throughout.
+//     = R'_cc + U Phi^T + conj(Phi) U^H + conj(Phi) Q Phi^T,
+// U = R'[0:Nt, Nt:], Q = R'[Nt:, Nt:], assembled in FP64; the identity holds
+// for any basis.  The large same-sign sums end up in Q (d^2 entries, exact
+// double-float products) and U (double-float promotion every 4 pixels); the
+// Nt x Nt block only sums the small residual c_p (blood and noise) with
+// 32-pixel FP32 partial sums.
 #include <math.h>
 
 #include "lcf_internal.cuh"
 
 namespace lcf {
 
-// Orthonormal DCT-II slow-time vectors phi[j][t], j < nd_defl, evaluated in
-// double and stored as the float values every kernel and the assembly use.
-void dct_basis(int nt, int nd_defl, float* phi) {
-  for (int j = 0; j < nd_defl; ++j)
-    for (int t = 0; t < nt; ++t) {
-      double v = (j == 0) ? 1.0 / sqrt((double)nt)
-                          : sqrt(2.0 / nt) * cos(3.14159265358979323846 * j * (t + 0.5) / nt);
-      phi[j * nt + t] = (float)v;
-    }
-}
-
-// xa[t][p] = c_p(t) = s_p(t) - sum_j a_pj phi_j(t) (t < nt), xa[nt+j][p] = a_pj
-__global__ void center_kernel(const float2* __restrict__ iq, const float* __restrict__ phi,
-                              float2* __restrict__ xa, int nt, int nd_defl, int npix) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npix) return;
+// xa[t][p] = c_p(t) = s_p(t) - sum_j a_pj phi_j(t) (t < nt), xa[nt+j][p] = a_pj.
+// If xmax_bits is given, the largest |component| written is max-reduced into it
+// (non-negative floats order like their bit patterns).
+__global__ void center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi,
+                              float2* __restrict__ xa, int nt, int nd_defl, int npix, unsigned* xmax_bits) {
+  const int p0 = blockIdx.x * blockDim.x + threadIdx.x;
+  float mx = 0.f;
+  if (p0 < npix) {
+  const int p = p0;
   float2 a[kDeflateMax];
 #pragma unroll
   for (int j = 0; j < kDeflateMax; ++j) a[j] = make_float2(0.f, 0.f);
@@ -43,9 +35,9 @@ __global__ void center_kernel(const float2* __restrict__ iq, const float* __rest
 #pragma unroll
     for (int j = 0; j < kDeflateMax; ++j)
       if (j < nd_defl) {
-        float f = phi[j * nt + t];
-        a[j].x = fmaf(f, v.x, a[j].x);
-        a[j].y = fmaf(f, v.y, a[j].y);
+        float2 f = phi[j * nt + t];          // a_j += conj(phi_j(t)) s(t)
+        a[j].x = fmaf(f.x, v.x, fmaf(f.y, v.y, a[j].x));
+        a[j].y = fmaf(f.x, v.y, fmaf(-f.y, v.x, a[j].y));
       }
   }
   for (int t = 0; t < nt; ++t) {
@@ -53,20 +45,35 @@ __global__ void center_kernel(const float2* __restrict__ iq, const float* __rest
 #pragma unroll
     for (int j = 0; j < kDeflateMax; ++j)
       if (j < nd_defl) {
-        float f = phi[j * nt + t];
-        v.x = fmaf(-f, a[j].x, v.x);
-        v.y = fmaf(-f, a[j].y, v.y);
+        float2 f = phi[j * nt + t];          // c(t) = s(t) - a_j phi_j(t)
+        v.x = fmaf(-a[j].x, f.x, fmaf(a[j].y, f.y, v.x));
+        v.y = fmaf(-a[j].x, f.y, fmaf(-a[j].y, f.x, v.y));
       }
     xa[(size_t)t * npix + p] = v;
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
 #pragma unroll
   for (int j = 0; j < kDeflateMax; ++j)
-    if (j < nd_defl) xa[(size_t)(nt + j) * npix + p] = a[j];
+    if (j < nd_defl) {
+      xa[(size_t)(nt + j) * npix + p] = a[j];
+      mx = fmaxf(mx, fmaxf(fabsf(a[j].x), fabsf(a[j].y)));
+    }
+  }
+  if (xmax_bits) {
+    unsigned m = __reduce_max_sync(~0u, __float_as_uint(mx));
+    if ((threadIdx.x & 31) == 0) atomicMax(xmax_bits, m);
+  }
 }
 
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st) {
   int n = P->npix;
-  center_kernel<<<(n + 255) / 256, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n);
+  unsigned* xm = nullptr;
+  if (P->cfg.gram_path == LCF_PATH_TC) {
+    xm = P->ws.xmax;
+    cudaError_t e = cudaMemsetAsync(xm, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  center_kernel<<<(n + 255) / 256, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
   return cudaGetLastError();
 }
 
@@ -275,7 +282,7 @@ __device__ __forceinline__ double2 cc_entry(const double2* __restrict__ pk, int 
 
 // R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T  (FP64)
 __global__ void gram_assemble_kernel(const double2* __restrict__ part, const double2* __restrict__ aug,
-                                     const float* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
+                                     const float2* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
                                      int nd_defl, double2* __restrict__ R) {
   const int k = blockIdx.y;
   const int na = nt + nd_defl, nout = na * nd_defl;
@@ -283,7 +290,7 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
   const double2* ak = aug + (size_t)k * aug_nsplit * nout;
   __shared__ double2 U[kEvdNmax][kDeflateMax];
   __shared__ double2 Q[kDeflateMax][kDeflateMax];
-  __shared__ double ph[kDeflateMax][kEvdNmax];
+  __shared__ double2 ph[kDeflateMax][kEvdNmax];
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     double sx = 0.0, sy = 0.0;
     for (int s = 0; s < aug_nsplit; ++s) {
@@ -295,7 +302,10 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
     if (i < nt) U[i][a] = make_double2(sx, sy);
     else Q[i - nt][a] = make_double2(sx, sy);
   }
-  for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) ph[e / nt][e % nt] = (double)phi[e];
+  for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
+    float2 f = phi[e];
+    ph[e / nt][e % nt] = make_double2((double)f.x, (double)f.y);
+  }
   __syncthreads();
   // Q is Hermitian: keep its Hermitian part so that R is exactly Hermitian
   if (threadIdx.x == 0)
@@ -310,18 +320,7 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt * nt; e += gridDim.x * blockDim.x) {
     int i = e / nt, j = e % nt;
     double2 r = cc_entry(pk, nsplit, nt, i, j);
-    for (int a = 0; a < nd_defl; ++a) {
-      // U_ia phi_a(j) + phi_a(i) conj(U_ja)
-      r.x += U[i][a].x * ph[a][j] + ph[a][i] * U[j][a].x;
-      r.y += U[i][a].y * ph[a][j] - ph[a][i] * U[j][a].y;
-      double qx = 0.0, qy = 0.0;
-      for (int c = 0; c < nd_defl; ++c) {
-        qx += Q[a][c].x * ph[c][j];
-        qy += Q[a][c].y * ph[c][j];
-      }
-      r.x += ph[a][i] * qx;
-      r.y += ph[a][i] * qy;
-    }
+    add_deflated_terms(r, i, j, nd_defl, U, Q, ph);
     if (i == j) r.y = 0.0;
     R[(size_t)k * nt * nt + e] = r;
   }

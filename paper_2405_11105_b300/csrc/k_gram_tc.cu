@@ -1,0 +1,329 @@
+// k_gram_tc.cu — windowed Gram on the tcgen05 tensor cores (Eq. 12).
+//
+// The deflated augmented row x_p = [c_p, a_p] (na = Nt + d entries, see
+// k_gram_simt.cu) is weighted, w_p = s g_k(p) x_p, and split per component
+// into fp16 halves, w = w_hi + w_lo (22 significant bits; s = 2^e keeps the
+// packet below 2^14).  With the complex product written as a real one over
+// K = (pixel, re/im),
+//   A[i][(p,re)] = Re w_hi(i),  A[i][(p,im)] = Im w_hi(i)
+//   B[j][(p,.)]  = (Re w(j), Im w(j))            j <  nbh   -> Re(conj(w_i) w_j)
+//   B[nbh+j][.]  = (Im w(j), -Re w(j))           (-i w)      -> Im(conj(w_i) w_j)
+// two passes, A B_hi^T + A (2 B_lo)^T, accumulate D' = P_hh + 2 P_hl in TMEM;
+// its Hermitian part P_hh + P_hl + P_hl^H equals sum_p g^2 x^H x up to the
+// dropped lo*lo term (relative 2^-22 squared).  A aliases the first 128 rows
+// of the B_hi buffer (rows past nbh only feed output rows that are unused).
+//
+// One CTA per (window, pixel range): 3-stage shared-memory ring of 32-pixel
+// K-slabs written by all 256 threads, one thread issuing tcgen05.mma, two TMEM
+// accumulators in ping-pong (128 pixels each), promoted into FP32 register
+// sums per (row, column half); the range's sum is written as a double partial.
+// The d x d coefficient block (largest entries) comes from gram_q_kernel with
+// exact double-float products instead.
+#include <math.h>
+
+#include "lcf_internal.cuh"
+#include "tc_util.cuh"
+
+namespace lcf {
+
+constexpr int TG_THREADS = 256;
+constexpr int TG_PX = 32;                  // pixels per stage
+constexpr int TG_K = 2 * TG_PX;            // K elements per stage
+constexpr int TG_STAGES = 3;
+// Stages per TMEM accumulation chain.  The tensor core's FP32 accumulation
+// rounds toward zero, so a chain of n additions biases same-sign sums by
+// ~n * 2^-25 (relative); short chains promoted into round-to-nearest FP32
+// register sums keep that bias at the 1e-7 level.
+constexpr int TG_CPA = 1;
+constexpr int TG_SBO = (TG_K / 8) * 128;   // bytes between 8-row groups
+constexpr int TG_NBH_MAX = 128;
+
+__host__ __device__ inline int tc_nbh(int na) { return (na + 7) / 8 * 8; }
+__host__ __device__ inline int tc_rows_hi(int nbh) { return 2 * nbh > 128 ? 2 * nbh : 128; }
+
+size_t gram_tc_smem_bytes(int na) {
+  int nbh = tc_nbh(na), rh = tc_rows_hi(nbh);
+  size_t hi = (size_t)rh * TG_K * 2, lo = (size_t)2 * nbh * TG_K * 2;
+  return TG_STAGES * (hi + lo) + 1024 + 2 * TG_PX * 8;
+}
+
+// 2^e with max|x| * 2^e < 2^14 (fp16 headroom for the products' inputs)
+__device__ __forceinline__ float tc_scale(const unsigned* xmax_bits) {
+  float xm = __uint_as_float(*xmax_bits);
+  if (!(xm > 0.f) || !isfinite(xm)) return 1.f;
+  int e;
+  frexpf(xm, &e);                // xm < 2^e
+  return ldexpf(1.f, 14 - e);
+}
+
+__global__ void __launch_bounds__(TG_THREADS, 1)
+gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box* __restrict__ boxes,
+               const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
+               int nsplit, double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t mma_bar[TG_STAGES];
+  __shared__ __align__(8) uint64_t acc_bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int pix_s[TG_PX];
+  __shared__ float gg_s[TG_PX];
+
+  const int k = blockIdx.y, s = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nbh = tc_nbh(na), N = 2 * nbh, rh = tc_rows_hi(nbh);
+  const size_t hi_bytes = (size_t)rh * 128, lo_bytes = (size_t)N * 128, st_bytes = hi_bytes + lo_bytes;
+  const Box b = boxes[k];
+  const int W = b.x1 - b.x0;
+  const long Pk = (long)(b.z1 - b.z0) * W;
+  const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
+  const int nst = (int)((l1 - l0 + TG_PX - 1) / TG_PX);
+  const size_t npix = (size_t)nz * nx;
+  const float sc = tc_scale(xmax_bits);
+  const float* gzk = gz + (size_t)k * nz;
+  const float* gxk = gx + (size_t)k * nx;
+  const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
+
+  // zero all stage buffers (padding rows stay zero)
+  for (size_t e = tid; e < TG_STAGES * st_bytes / 16; e += TG_THREADS)
+    reinterpret_cast<uint4*>(smem)[e] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    for (int i = 0; i < TG_STAGES; ++i) tc::mbar_init(&mma_bar[i], 1);
+    tc::mbar_init(&acc_bar[0], 1);
+    tc::mbar_init(&acc_bar[1], 1);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = tc::idesc_f16(128, N);
+
+  float sums[TG_NBH_MAX];
+#pragma unroll
+  for (int j = 0; j < TG_NBH_MAX; ++j) sums[j] = 0.f;
+  bool ok = true;
+
+  auto epilogue = [&](int c) {
+    ok &= tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);
+    tc::fence_after();
+    const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
+#pragma unroll
+    for (int cc = 0; cc < TG_NBH_MAX / 16; ++cc) {
+      if (cc * 16 < nbh) {
+        float v[16];
+        tc::tmem_ld16(base + cc * 16, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += v[j];
+      }
+    }
+    tc::fence_before();
+  };
+
+  for (int i = 0; i < nst; ++i) {
+    const int si = i % TG_STAGES;
+    unsigned char* Bhi = smem + si * st_bytes;
+    unsigned char* Blo = Bhi + hi_bytes;
+    if (i >= TG_STAGES) ok &= tc::mbar_wait(&mma_bar[si], ((i / TG_STAGES) - 1) & 1);
+    if (tid < TG_PX) {
+      long l = l0 + (long)i * TG_PX + tid;
+      int p = 0;
+      float g = 0.f;
+      if (l < l1) {
+        int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
+        p = z * nx + x;
+        g = gzk[z] * gxk[x] * sc;
+      }
+      pix_s[tid] = p;
+      gg_s[tid] = g;
+    }
+    __syncthreads();
+    const int r8 = (na + 7) >> 3;
+    for (int e = tid; e < 256 * r8; e += TG_THREADS) {
+      const int ln = e & 31, w = e >> 5;
+      const int pp = (w & 7) * 4 + (ln & 3), r = (w >> 3) * 8 + (ln >> 2);
+      if (r >= na) continue;
+      const float g = gg_s[pp];
+      const float2 v = xa[(size_t)r * npix + pix_s[pp]];
+      __half hr, lr, hm, lm;
+      tc::split_f16(v.x * g, hr, lr);
+      tc::split_f16(v.y * g, hm, lm);
+      const int kk = 2 * pp;
+      *reinterpret_cast<__half2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = __halves2half2(hr, hm);
+      *reinterpret_cast<__half2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(hm, __hneg(hr));
+      const __half lr2 = __hmul(lr, __float2half(2.f)), lm2 = __hmul(lm, __float2half(2.f));
+      *reinterpret_cast<__half2*>(Blo + tc::op_off(r, kk, TG_SBO)) = __halves2half2(lr2, lm2);
+      *reinterpret_cast<__half2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(lm2, __hneg(lr2));
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    const int c = i / TG_CPA;
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t d = tbase + (uint32_t)((c & 1) * 256);
+      const uint32_t bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll
+      for (int ks = 0; ks < TG_K / 16; ++ks) {
+        const uint64_t ad = tc::smem_desc(bh + ks * 256, 128, TG_SBO);
+        const uint64_t ld = tc::smem_desc(bl + ks * 256, 128, TG_SBO);
+        tc::mma_f16(d, ad, ad, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
+        tc::mma_f16(d, ad, ld, idesc, 1u);
+      }
+      tc::mma_commit(&mma_bar[si]);
+      if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
+    }
+    if (i % TG_CPA == 0 && c > 0) epilogue(c - 1);
+  }
+  if (nst > 0) epilogue((nst - 1) / TG_CPA);
+  if (!ok && lane == 0) atomicOr(err, 1);
+
+  // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na)
+  double* out = part + (((size_t)k * nsplit + s) * 2 + half) * na * na;
+  if (row < na) {
+#pragma unroll
+    for (int j = 0; j < TG_NBH_MAX; ++j)
+      if (j < na) out[(size_t)row * na + j] = (double)sums[j];
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// Coefficient block Q[a][b] = sum_p g^2 conj(a_pa) a_pb with exact products
+// (double-float), one partial per (window, split).
+__global__ void __launch_bounds__(256)
+gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, const Box* __restrict__ boxes,
+              const float* __restrict__ gz, const float* __restrict__ gx, int nsplit, double2* __restrict__ q) {
+  const int k = blockIdx.y, s = blockIdx.x, tid = threadIdx.x;
+  const Box b = boxes[k];
+  const int W = b.x1 - b.x0;
+  const long Pk = (long)(b.z1 - b.z0) * W;
+  const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
+  const size_t npix = (size_t)nz * nx;
+  df qr[kDeflateMax * kDeflateMax], qi[kDeflateMax * kDeflateMax];
+#pragma unroll
+  for (int e = 0; e < kDeflateMax * kDeflateMax; ++e) { qr[e] = {0.f, 0.f}; qi[e] = {0.f, 0.f}; }
+  for (long l = l0 + tid; l < l1; l += blockDim.x) {
+    const int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
+    const size_t p = (size_t)z * nx + x;
+    float g = gz[(size_t)k * nz + z] * gx[(size_t)k * nx + x];
+    float g2 = g * g;
+    float2 a[kDeflateMax];
+#pragma unroll
+    for (int j = 0; j < kDeflateMax; ++j) a[j] = j < nd_defl ? xa[(size_t)(nt + j) * npix + p] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < kDeflateMax; ++i)
+#pragma unroll
+      for (int j = 0; j < kDeflateMax; ++j) {
+        if (i >= nd_defl || j >= nd_defl) continue;
+        df wr = two_prod_df(g2, a[i].x), wi = two_prod_df(-g2, a[i].y);   // g^2 conj(a_i)
+        df rr = df_mul_f(wr, a[j].x), ii = df_mul_f(wi, a[j].y);
+        df ri = df_mul_f(wr, a[j].y), ir = df_mul_f(wi, a[j].x);
+        qr[i * kDeflateMax + j] = df_add(qr[i * kDeflateMax + j], df_add(rr, df_neg(ii)));
+        qi[i * kDeflateMax + j] = df_add(qi[i * kDeflateMax + j], df_add(ri, ir));
+      }
+  }
+  // block reduction in double-float
+  __shared__ df red_r[8][kDeflateMax * kDeflateMax], red_i[8][kDeflateMax * kDeflateMax];
+#pragma unroll
+  for (int e = 0; e < kDeflateMax * kDeflateMax; ++e) {
+    df vr = qr[e], vi = qi[e];
+    for (int o = 16; o; o >>= 1) {
+      df tr = {__shfl_xor_sync(~0u, vr.hi, o), __shfl_xor_sync(~0u, vr.lo, o)};
+      df ti = {__shfl_xor_sync(~0u, vi.hi, o), __shfl_xor_sync(~0u, vi.lo, o)};
+      vr = df_add(vr, tr);
+      vi = df_add(vi, ti);
+    }
+    if ((tid & 31) == 0) { red_r[tid >> 5][e] = vr; red_i[tid >> 5][e] = vi; }
+  }
+  __syncthreads();
+  if (tid < kDeflateMax * kDeflateMax) {
+    df vr = {0.f, 0.f}, vi = {0.f, 0.f};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { vr = df_add(vr, red_r[w][tid]); vi = df_add(vi, red_i[w][tid]); }
+    q[((size_t)k * nsplit + s) * kDeflateMax * kDeflateMax + tid] = make_double2(df_to_double(vr), df_to_double(vi));
+  }
+}
+
+// R from the tensor-core partials: R' = Herm(sum D') / s^2 for the residual block and U,
+// Q from the exact kernel; R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T (FP64)
+__global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const double2* __restrict__ qpart,
+                                        const float2* __restrict__ phi, const unsigned* __restrict__ xmax_bits,
+                                        int nsplit, int qsplit, int nt, int nd_defl, double2* __restrict__ R) {
+  const int k = blockIdx.y;
+  const int na = nt + nd_defl;
+  const double* pk = part + (size_t)k * nsplit * 2 * na * na;
+  __shared__ double2 U[kEvdNmax][kDeflateMax];
+  __shared__ double2 Q[kDeflateMax][kDeflateMax];
+  __shared__ double2 ph[kDeflateMax][kEvdNmax];
+  __shared__ double inv_s2;
+  if (threadIdx.x == 0) {
+    float sc = tc_scale(xmax_bits);
+    inv_s2 = 1.0 / ((double)sc * (double)sc);
+  }
+  __syncthreads();
+  const double is2 = inv_s2;
+  // Hermitian part of the summed D' at (a, b)
+  auto herm = [&](int a, int bb) {
+    double xr = 0.0, xi = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const double* re = pk + (size_t)s * 2 * na * na;
+      const double* im = re + (size_t)na * na;
+      xr += re[(size_t)a * na + bb] + re[(size_t)bb * na + a];
+      xi += im[(size_t)a * na + bb] - im[(size_t)bb * na + a];
+    }
+    return make_double2(0.5 * xr * is2, 0.5 * xi * is2);
+  };
+  for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
+    int i = e / nd_defl, a = e % nd_defl;
+    U[i][a] = herm(i, nt + a);
+    float2 f = phi[a * nt + i];
+    ph[a][i] = make_double2((double)f.x, (double)f.y);
+  }
+  if (threadIdx.x < nd_defl * nd_defl) {
+    int a = threadIdx.x / nd_defl, c = threadIdx.x % nd_defl;
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < qsplit; ++s) {
+      double2 v1 = qpart[((size_t)k * qsplit + s) * kDeflateMax * kDeflateMax + a * kDeflateMax + c];
+      double2 v2 = qpart[((size_t)k * qsplit + s) * kDeflateMax * kDeflateMax + c * kDeflateMax + a];
+      sx += 0.5 * (v1.x + v2.x);
+      sy += 0.5 * (v1.y - v2.y);
+    }
+    Q[a][c] = make_double2(sx, sy);
+  }
+  __syncthreads();
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt * nt; e += gridDim.x * blockDim.x) {
+    int i = e / nt, j = e % nt;
+    double2 r = herm(i, j);
+    add_deflated_terms(r, i, j, nd_defl, U, Q, ph);
+    if (i == j) r.y = 0.0;
+    R[(size_t)k * nt * nt + e] = r;
+  }
+}
+
+cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  const int na = P->nt + P->ndefl;
+  dim3 grid(P->tc_nsplit, P->nd);
+  gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
+                                                                    P->ws.gx, P->ws.xmax, P->tc_nsplit,
+                                                                    P->ws.gtc, P->ws.err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_q_kernel<<<dim3(P->q_nsplit, P->nd), 256, 0, st>>>(P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->ws.box,
+                                                          P->ws.gz, P->ws.gx, P->q_nsplit, P->ws.gq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
+  dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
+  gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.phi, P->ws.xmax, P->tc_nsplit,
+                                                 P->q_nsplit, P->nt, P->ndefl, P->ws.R);
+  return cudaGetLastError();
+}
+
+cudaError_t gram_tc_configure() {
+  return cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gram_tc_smem_bytes(kEvdNmax + kDeflateMax));
+}
+
+}  // namespace lcf

@@ -30,8 +30,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 static void* g_scratch_addr[64];
 static bool g_scratch_ready[64];
 
-__global__ void center_kernel(const float2* __restrict__ iq, const float* __restrict__ phi,
-                              float2* __restrict__ xa, int nt, int nd_defl, int npix);
+__global__ void center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi,
+                              float2* __restrict__ xa, int nt, int nd_defl, int npix, unsigned* xmax_bits);
 __global__ void gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1,
                                  const Box* __restrict__ boxes, const float* __restrict__ gz,
                                  const float* __restrict__ gx, int ntile, int nsplit,
@@ -40,16 +40,16 @@ __global__ void gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, i
                                 const Box* __restrict__ boxes, const float* __restrict__ gz,
                                 const float* __restrict__ gx, int nsplit, double2* __restrict__ aug);
 __global__ void gram_assemble_kernel(const double2* __restrict__ part, const double2* __restrict__ aug,
-                                     const float* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
+                                     const float2* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
                                      int nd_defl, double2* __restrict__ R);
 
 // Orthonormal DCT-II slow-time vectors (the Gram stage's deflation basis)
-__global__ void noalloc_basis_kernel(int nt, int nd_defl, float* phi) {
+__global__ void noalloc_basis_kernel(int nt, int nd_defl, float2* phi) {
   for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
     int j = e / nt, t = e % nt;
     double v = (j == 0) ? 1.0 / sqrt((double)nt)
                         : sqrt(2.0 / nt) * cos(3.14159265358979323846 * j * (t + 0.5) / nt);
-    phi[e] = (float)v;
+    phi[e] = make_float2((float)v, 0.f);
   }
 }
 
@@ -118,7 +118,7 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   const size_t off_gx = align256(nd * c->nz * sizeof(float));
   const size_t off_box = off_gx + align256(nd * c->nx * sizeof(float));
   const size_t off_phi = off_box + align256(nd * sizeof(Box));
-  const size_t off_xa = off_phi + align256((size_t)ndefl * nt * sizeof(float));
+  const size_t off_xa = off_phi + align256((size_t)ndefl * nt * sizeof(float2));
   const size_t off_aug = off_xa + align256(n1 * npix * sizeof(float2));
   const size_t off_part = off_aug + align256(nd * n1 * ndefl * sizeof(double2));
   const size_t per_split = nd * nt * nt * sizeof(double2);
@@ -138,7 +138,7 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   float* gz = reinterpret_cast<float*>(base);
   float* gx = reinterpret_cast<float*>(base + off_gx);
   Box* box = reinterpret_cast<Box*>(base + off_box);
-  float* phi = reinterpret_cast<float*>(base + off_phi);
+  float2* phi = reinterpret_cast<float2*>(base + off_phi);
   float2* xa = reinterpret_cast<float2*>(base + off_xa);
   double2* aug = reinterpret_cast<double2*>(base + off_aug);
   double2* part = reinterpret_cast<double2*>(base + off_part);
@@ -149,7 +149,7 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   noalloc_basis_kernel<<<1, 256, 0, stream>>>((int)nt, ndefl, phi);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   center_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>((const float2*)d_iq, phi, xa, (int)nt, ndefl,
-                                                                    (int)npix);
+                                                                    (int)npix, nullptr);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   gram_aug_kernel<<<dim3(1, (unsigned)nd), 256, gram_aug_smem_bytes((int)nt, ndefl), stream>>>(
       xa, c->nz, c->nx, (int)nt, ndefl, box, gz, gx, 1, aug);

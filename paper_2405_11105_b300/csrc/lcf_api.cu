@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "lcf_internal.cuh"
@@ -112,7 +113,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 }
 
 static void free_ws(Workspace& w) {
-  void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.xa, w.gpart, w.gaug, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
+  void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
                   w.flags, w.W, w.ncol, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -148,6 +149,19 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     P->gram_nsplit = want < 1 ? 1 : (want > 64 ? 64 : want);
     int wa = (2 * P->sm_count + P->nd - 1) / P->nd;
     P->aug_nsplit = wa < 1 ? 1 : (wa > 64 ? 64 : wa);
+    P->q_nsplit = P->aug_nsplit;
+    int gt = (P->nt + 63) / 64;
+    int gb = (P->sm_count + gt * (gt + 1) / 2 - 1) / (gt * (gt + 1) / 2);
+    P->basis_nsplit = gb < 1 ? 1 : (gb > 64 ? 64 : gb);
+  }
+  {
+    long pmax = 0;
+    std::vector<Box> bx;
+    std::vector<float> tz, tx;
+    build_geometry(*cfg, bx, tz, tx);
+    for (const Box& b : bx) pmax = std::max(pmax, (long)(b.z1 - b.z0) * (b.x1 - b.x0));
+    long ts = (pmax + 2047) / 2048;   // ~2048 pixels per tensor-core CTA
+    P->tc_nsplit = (int)(ts < 1 ? 1 : (ts > 64 ? 64 : ts));
   }
   P->ncp = 4 * project_cpt(P->nt);
   std::vector<float> gz, gx;
@@ -161,9 +175,16 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.gx, nd * cfg->nx, &tot);
   if (e == cudaSuccess) e = dalloc(&w.box, nd, &tot);
   if (e == cudaSuccess) e = dalloc(&w.phi, (size_t)P->ndefl * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.gglob, (size_t)P->basis_nsplit * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.xa, n1 * npix, &tot);
   if (e == cudaSuccess) e = dalloc(&w.gpart, nd * P->gram_nsplit * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.gaug, nd * P->aug_nsplit * n1 * P->ndefl, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.xmax, 1, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.err, 1, &tot);
+  if (cfg->gram_path == LCF_PATH_TC) {
+    if (e == cudaSuccess) e = dalloc(&w.gtc, nd * P->tc_nsplit * 2 * n1 * n1, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kDeflateMax * kDeflateMax, &tot);
+  }
   if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.lam, nd * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.V, nd * nt * nt, &tot);
@@ -186,14 +207,13 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = cudaMemcpy(w.gx, gx.data(), gx.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(w.box, P->boxes.data(), nd * sizeof(Box), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(w.flags, 0, nd * sizeof(int));
-  if (e == cudaSuccess) {
-    std::vector<float> phi((size_t)P->ndefl * nt);
-    dct_basis((int)nt, P->ndefl, phi.data());
-    e = cudaMemcpy(w.phi, phi.data(), phi.size() * sizeof(float), cudaMemcpyHostToDevice);
-  }
+  if (e == cudaSuccess) e = cudaMemset(w.err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(w.xmax, 0, sizeof(unsigned));
   if (e == cudaSuccess && (device >= 64 || !g_configured[device])) {
     e = evd_configure();
     if (e == cudaSuccess) e = project_configure();
+    if (e == cudaSuccess) e = gram_tc_configure();
+    if (e == cudaSuccess) e = basis_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
   }
   if (e != cudaSuccess) {
@@ -234,14 +254,21 @@ static cudaEvent_t prof_event(lcf_plan* P, int b) {
 
 static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
-  if (c.gram_path != LCF_PATH_SIMT || c.project_path != LCF_PATH_SIMT) return LCF_EUNSUPPORTED;
+  if (c.project_path != LCF_PATH_SIMT) return LCF_EUNSUPPORTED;
+  const bool tc = c.gram_path == LCF_PATH_TC;
   LCF_MARK(LCF_STAGE_PREP);
+  LCF_CUDA(launch_basis(P, iq, st));
   LCF_CUDA(launch_center(P, iq, st));
   LCF_MARK(LCF_STAGE_GRAM);
-  LCF_CUDA(launch_gram_aug(P, st));
-  LCF_CUDA(launch_gram_simt(P, st));
+  if (tc) {
+    LCF_CUDA(launch_gram_tc(P, st));
+  } else {
+    LCF_CUDA(launch_gram_aug(P, st));
+    LCF_CUDA(launch_gram_simt(P, st));
+  }
   LCF_MARK(LCF_STAGE_ASSEMBLE);
-  LCF_CUDA(launch_gram_assemble(P, st));
+  if (tc) LCF_CUDA(launch_gram_assemble_tc(P, st));
+  else LCF_CUDA(launch_gram_assemble(P, st));
   LCF_MARK(LCF_STAGE_EVD);
   LCF_CUDA(launch_evd(P, st));
   LCF_MARK(LCF_STAGE_PROJECT);
@@ -332,6 +359,9 @@ extern "C" lcf_status lcf_plan_status(lcf_plan* P, int* per_window_flags) {
   if (per_window_flags) memcpy(per_window_flags, f.data(), P->nd * sizeof(int));
   int any = 0;
   for (int v : f) any |= v;
+  int derr = 0;
+  LCF_CUDA(cudaMemcpy(&derr, P->ws.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) return LCF_ETIMEOUT;
   if (any & LCF_WFLAG_NOCONV) return LCF_ENOCONV;
   if (any & LCF_WFLAG_DEGENERATE) return LCF_EDEGENERATE;
   return LCF_OK;

@@ -31,11 +31,16 @@ struct Workspace {
   float* gx = nullptr;        // [nd][nx]
   Box* box = nullptr;         // [nd]
   // deflated packet: s_p = c_p + sum_j a_pj phi_j
-  float* phi = nullptr;       // [ndefl][nt] orthonormal DCT-II slow-time vectors
+  float2* phi = nullptr;      // [ndefl][nt] per-packet slow-time deflation basis (complex)
+  float2* gglob = nullptr;    // [basis_nsplit][nt][nt] partial global Grams (basis estimate)
   float2* xa = nullptr;       // [nt+ndefl][nz*nx]: residual c_p(t), then coefficients a_pj
   // Gram
   double2* gpart = nullptr;   // [nd][nsplit][nt][nt] partial residual Grams
   double2* gaug = nullptr;    // [nd][aug_nsplit][(nt+ndefl)*ndefl] partial augmented columns
+  unsigned* xmax = nullptr;   // [1] max |component| of the deflated packet (float bits)
+  double* gtc = nullptr;      // [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes)
+  double2* gq = nullptr;      // [nd][q_nsplit][kDeflateMax^2] exact coefficient-block partials
+  int* err = nullptr;         // [1] device error word (bit 0: a bounded wait gave up)
   double2* R = nullptr;       // [nd][nt][nt] windowed Gram (Eq. 12)
   // EVD + weights
   double* lam = nullptr;      // [nd][nt] descending eigenvalues
@@ -59,6 +64,9 @@ struct lcf_plan {
   int nd = 0, nt = 0, n1 = 0, npix = 0;
   int ndefl = 1;        // deflated slow-time vectors; the augmented row has nt + ndefl entries
   int aug_nsplit = 1;   // pixel splits of the augmented-column kernel
+  int tc_nsplit = 1;    // pixel ranges per window of the tensor-core Gram
+  int q_nsplit = 1;     // pixel splits of the exact coefficient-block kernel
+  int basis_nsplit = 1; // pixel splits of the global Gram behind the deflation basis
   int gram_tiles = 0;   // 64-wide tiles per Gram dimension
   int gram_nsplit = 1;  // pixel splits per window
   int ncp = 0;          // padded projection columns
@@ -142,12 +150,42 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
+// r += U_i. Phi^T e_j + conj(Phi^T e_i) . conj(U_j.) + conj(Phi^T e_i) Q Phi^T e_j, i.e. the
+// E^H R' E terms beyond the residual block (FP64; phi_a(t) = ph[a][t]).
+__device__ __forceinline__ void add_deflated_terms(double2& r, int i, int j, int nd_defl, const double2 (*U)[kDeflateMax],
+                                   const double2 (*Q)[kDeflateMax], const double2 (*ph)[kEvdNmax]) {
+  for (int a = 0; a < nd_defl; ++a) {
+    const double2 fi = ph[a][i], fj = ph[a][j];
+    const double2 ui = U[i][a], uj = U[j][a];
+    // U_ia phi_a(j)
+    r.x += ui.x * fj.x - ui.y * fj.y;
+    r.y += ui.x * fj.y + ui.y * fj.x;
+    // conj(phi_a(i) U_ja)
+    r.x += fi.x * uj.x - fi.y * uj.y;
+    r.y -= fi.x * uj.y + fi.y * uj.x;
+    // conj(phi_a(i)) sum_c Q_ac phi_c(j)
+    double qx = 0.0, qy = 0.0;
+    for (int c = 0; c < nd_defl; ++c) {
+      const double2 q = Q[a][c], fc = ph[c][j];
+      qx += q.x * fc.x - q.y * fc.y;
+      qy += q.x * fc.y + q.y * fc.x;
+    }
+    r.x += fi.x * qx + fi.y * qy;
+    r.y += fi.x * qy - fi.y * qx;
+  }
+}
+
 // ----- launchers (each returns cudaGetLastError() after the launch) -----
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st);
 size_t gram_aug_smem_bytes(int nt, int nd_defl);
-void dct_basis(int nt, int nd_defl, float* phi);
+cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st);
+cudaError_t basis_configure();
 cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st);
+cudaError_t gram_tc_configure();
+size_t gram_tc_smem_bytes(int na);
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);

@@ -1,0 +1,84 @@
+"""Tensor-core (tcgen05) paths vs the FP64 oracle, through the C ABI.
+
+Same tolerances as the plain FP32 path (see test_parity_gpu.py): PD rel L2
+<= 1e-3, eigenvalues in the 1e-6*lambda_1 band <= 1e-4 relative, Gram rel
+Frobenius <= 1e-6, hard cutoffs equal up to near-ties of the oracle's rule.
+"""
+import numpy as np
+import pytest
+
+from conftest import gpu_available
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+from synth import REALTIME_256x128x100, SMALL_96x64x32, generate_packet  # noqa: E402
+from test_parity_gpu import (ALPHA_TOL, EIG_TOL, GRAM_TOL, PD_TOL, L, compare, configs,  # noqa: E402
+                             rand_iq)
+
+
+def tc_cfg(*a, **kw):
+    lib = L()
+    cfg, oc = configs(*a, **kw)
+    cfg.gram_path = lib.LCF_PATH_TC
+    return cfg, oc
+
+
+def check(r, gram=True):
+    lib = L()
+    print({k: r[k] for k in ("pd_err", "eig_err", "alpha_err") + (("gram_err",) if gram else ())},
+          "flips", r["flips"], "ties", r["ties"])
+    assert r["status"] in (lib.LCF_OK,), r["flags"]
+    if gram:
+        assert r["gram_err"] <= GRAM_TOL
+    assert r["eig_err"] <= EIG_TOL
+    assert np.array_equal(r["k_gpu"], r["k_ora"])
+    assert r["alpha_err"] <= ALPHA_TOL
+    assert r["pd_err"] <= PD_TOL
+
+
+def test_tc_small_fixed_k3():
+    lib = L()
+    iq = generate_packet(SMALL_96x64x32, seed=0)
+    cfg, oc = tc_cfg(96, 64, 32, 3, 3, thresh_mode=lib.LCF_T_FIXED, k_fixed=3)
+    check(compare(iq, cfg, oc))
+
+
+def test_tc_realtime_curvature():
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=0)
+    cfg, oc = tc_cfg(256, 128, 100, 8, 8, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    check(compare(iq, cfg, oc))
+
+
+def test_tc_realtime_soft_rule():
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=3)
+    cfg, oc = tc_cfg(256, 128, 100, 8, 8, thresh_mode=lib.LCF_T_ADAPTIVE_SOFT, beta=0.5)
+    check(compare(iq, cfg, oc, want_gram=False), gram=False)
+
+
+@pytest.mark.parametrize("shape,grid,mode", [
+    ((33, 40, 70), (2, 3), "LCF_T_FIXED"),
+    ((16, 17, 23), (1, 1), "LCF_T_MEDIAN"),
+    ((112, 24, 20), (2, 2), "LCF_T_CURVATURE"),
+    ((2, 8, 8), (1, 1), "LCF_T_FIXED"),
+])
+def test_tc_edge_shapes(shape, grid, mode):
+    lib = L()
+    nt, nz, nx = shape
+    cfg, oc = tc_cfg(nz, nx, nt, grid[0], grid[1], thresh_mode=getattr(lib, mode), k_fixed=1, beta=1.0)
+    check(compare(rand_iq(3, nt, nz, nx), cfg, oc))
+
+
+def test_tc_matches_plain_path():
+    """The two Gram paths give the same image to well within the oracle tolerance."""
+    import torch
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=4)
+    d = torch.from_numpy(iq).cuda()
+    out = {}
+    for path in (lib.LCF_PATH_SIMT, lib.LCF_PATH_TC):
+        plan = lib.Plan.make(256, 128, 100, 8, 8, thresh_mode=lib.LCF_T_FIXED, k_fixed=4, gram_path=path)
+        out[path] = plan.filter(d).cpu().numpy().astype(np.float64)
+    a, b = out[lib.LCF_PATH_SIMT], out[lib.LCF_PATH_TC]
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) <= 2e-4
