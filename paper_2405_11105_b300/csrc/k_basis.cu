@@ -22,7 +22,7 @@ namespace lcf {
 
 constexpr int BG_T = 64;        // tile side
 constexpr int BG_CH = 32;       // pixels staged per step
-constexpr int BASIS_ITERS = 8;
+constexpr int BASIS_ITERS = 5;
 
 __host__ __device__ inline int basis_zstep(int nz) { return nz >= 16 ? 4 : 1; }
 
@@ -159,6 +159,16 @@ basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, f
   }
 }
 
+// part[0] += sum_{s>0} part[s] over the upper-triangle entries (fixed order)
+__global__ void basis_reduce_kernel(float2* __restrict__ part, int nsplit, int nt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt * nt || (e / nt) > (e % nt)) return;
+  float2 acc = part[e];
+#pragma unroll 8
+  for (int s = 1; s < nsplit; ++s) acc = cadd(acc, part[(size_t)s * nt * nt + e]);
+  part[e] = acc;
+}
+
 size_t basis_smem_bytes(int nt, int nd_defl) { return ((size_t)nt * nt + 2 * (size_t)nt * nd_defl) * sizeof(float2); }
 
 cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st) {
@@ -169,8 +179,12 @@ cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st) {
                                            P->ws.gglob);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  basis_kernel<<<1, 256, basis_smem_bytes(P->nt, P->ndefl), st>>>(P->ws.gglob, P->basis_nsplit, P->nt, P->ndefl,
-                                                                  P->ws.phi);
+  if (P->basis_nsplit > 1) {
+    basis_reduce_kernel<<<(P->nt * P->nt + 255) / 256, 256, 0, st>>>(P->ws.gglob, P->basis_nsplit, P->nt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  basis_kernel<<<1, 256, basis_smem_bytes(P->nt, P->ndefl), st>>>(P->ws.gglob, 1, P->nt, P->ndefl, P->ws.phi);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ __global__ void center_kernel(const float2* __restrict__ iq, const float2* __res
   float2 a[kDeflateMax];
 #pragma unroll
   for (int j = 0; j < kDeflateMax; ++j) a[j] = make_float2(0.f, 0.f);
+#pragma unroll 4
   for (int t = 0; t < nt; ++t) {
     float2 v = iq[(size_t)t * npix + p];
 #pragma unroll
@@ -40,6 +41,7 @@ __global__ void center_kernel(const float2* __restrict__ iq, const float2* __res
         a[j].y = fmaf(f.x, v.y, fmaf(-f.y, v.x, a[j].y));
       }
   }
+#pragma unroll 4
   for (int t = 0; t < nt; ++t) {
     float2 v = iq[(size_t)t * npix + p];
 #pragma unroll
@@ -73,7 +75,7 @@ cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st) 
     cudaError_t e = cudaMemsetAsync(xm, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
   }
-  center_kernel<<<(n + 255) / 256, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
+  center_kernel<<<(n + 127) / 128, 128, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
   return cudaGetLastError();
 }
 
@@ -317,10 +319,21 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
         Q[c][a] = make_double2(h.x, -h.y);
       }
   __syncthreads();
+  double2 wv[2];
+  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 448 < 512)
+    int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
+  }
+  __syncthreads();
+  for (int u = 0; u < 2; ++u) {
+    int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
+  }
+  __syncthreads();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt * nt; e += gridDim.x * blockDim.x) {
     int i = e / nt, j = e % nt;
     double2 r = cc_entry(pk, nsplit, nt, i, j);
-    add_deflated_terms(r, i, j, nd_defl, U, Q, ph);
+    add_w_terms(r, i, j, nd_defl, U, ph);
     if (i == j) r.y = 0.0;
     R[(size_t)k * nt * nt + e] = r;
   }

@@ -32,9 +32,11 @@ constexpr int TG_K = 2 * TG_PX;            // K elements per stage
 constexpr int TG_STAGES = 3;
 // Stages per TMEM accumulation chain.  The tensor core's FP32 accumulation
 // rounds toward zero, so a chain of n additions biases same-sign sums by
-// ~n * 2^-25 (relative); short chains promoted into round-to-nearest FP32
-// register sums keep that bias at the 1e-7 level.
-constexpr int TG_CPA = 1;
+// ~n * 2^-25 (relative) of the chain's magnitude.  After deflation the
+// chain sums residual (blood + noise) products only, so chains of 4 stages
+// (256 pixel products) promoted into round-to-nearest FP32 register sums keep
+// the bias below the 1e-7 level of the Gram tolerance.
+constexpr int TG_CPA = 4;
 constexpr int TG_SBO = (TG_K / 8) * 128;   // bytes between 8-row groups
 constexpr int TG_NBH_MAX = 128;
 
@@ -138,22 +140,35 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
       gg_s[tid] = g;
     }
     __syncthreads();
-    const int r8 = (na + 7) >> 3;
-    for (int e = tid; e < 256 * r8; e += TG_THREADS) {
-      const int ln = e & 31, w = e >> 5;
-      const int pp = (w & 7) * 4 + (ln & 3), r = (w >> 3) * 8 + (ln >> 2);
-      if (r >= na) continue;
+    {
+      // Each thread owns one pixel pp of the slab and rows r = 8j + lane/4: all of
+      // its loads are issued first (independent), then split and stored.  Lanes
+      // cover (row%8, pixel%4), so the 4-byte stores of a warp fill distinct banks.
+      const int pp = ((tid >> 5) & 7) * 4 + (lane & 3), rl = lane >> 2;
       const float g = gg_s[pp];
-      const float2 v = xa[(size_t)r * npix + pix_s[pp]];
-      __half hr, lr, hm, lm;
-      tc::split_f16(v.x * g, hr, lr);
-      tc::split_f16(v.y * g, hm, lm);
+      const float2* src = xa + pix_s[pp];
+      constexpr int RMAX = (TG_NBH_MAX + 7) / 8;
+      float2 v[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        const int r = 8 * j + rl;
+        v[j] = (r < na) ? src[(size_t)r * npix] : make_float2(0.f, 0.f);
+      }
       const int kk = 2 * pp;
-      *reinterpret_cast<__half2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = __halves2half2(hr, hm);
-      *reinterpret_cast<__half2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(hm, __hneg(hr));
-      const __half lr2 = __hmul(lr, __float2half(2.f)), lm2 = __hmul(lm, __float2half(2.f));
-      *reinterpret_cast<__half2*>(Blo + tc::op_off(r, kk, TG_SBO)) = __halves2half2(lr2, lm2);
-      *reinterpret_cast<__half2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(lm2, __hneg(lr2));
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        const int r = 8 * j + rl;
+        if (r < na) {
+          __half hr, lr, hm, lm;
+          tc::split_f16(v[j].x * g, hr, lr);
+          tc::split_f16(v[j].y * g, hm, lm);
+          *reinterpret_cast<__half2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = __halves2half2(hr, hm);
+          *reinterpret_cast<__half2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(hm, __hneg(hr));
+          const __half lr2 = __hmul(lr, __float2half(2.f)), lm2 = __hmul(lm, __float2half(2.f));
+          *reinterpret_cast<__half2*>(Blo + tc::op_off(r, kk, TG_SBO)) = __halves2half2(lr2, lm2);
+          *reinterpret_cast<__half2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(lm2, __hneg(lr2));
+        }
+      }
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -263,14 +278,12 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   __syncthreads();
   const double is2 = inv_s2;
   // Hermitian part of the summed D' at (a, b)
+  // (split 0 of each window holds the sum over splits, see gram_tc_reduce_kernel)
   auto herm = [&](int a, int bb) {
-    double xr = 0.0, xi = 0.0;
-    for (int s = 0; s < nsplit; ++s) {
-      const double* re = pk + (size_t)s * 2 * na * na;
-      const double* im = re + (size_t)na * na;
-      xr += re[(size_t)a * na + bb] + re[(size_t)bb * na + a];
-      xi += im[(size_t)a * na + bb] - im[(size_t)bb * na + a];
-    }
+    const double* re = pk;
+    const double* im = re + (size_t)na * na;
+    const double xr = re[(size_t)a * na + bb] + re[(size_t)bb * na + a];
+    const double xi = im[(size_t)a * na + bb] - im[(size_t)bb * na + a];
     return make_double2(0.5 * xr * is2, 0.5 * xi * is2);
   };
   for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
@@ -291,10 +304,21 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     Q[a][c] = make_double2(sx, sy);
   }
   __syncthreads();
+  double2 wv[2];
+  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 448 < 512)
+    int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
+  }
+  __syncthreads();
+  for (int u = 0; u < 2; ++u) {
+    int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
+  }
+  __syncthreads();
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt * nt; e += gridDim.x * blockDim.x) {
     int i = e / nt, j = e % nt;
     double2 r = herm(i, j);
-    add_deflated_terms(r, i, j, nd_defl, U, Q, ph);
+    add_w_terms(r, i, j, nd_defl, U, ph);
     if (i == j) r.y = 0.0;
     R[(size_t)k * nt * nt + e] = r;
   }
@@ -314,7 +338,28 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// part[k][0] += sum_{s>0} part[k][s] (coalesced; fixed split order)
+__global__ void gram_tc_reduce_kernel(double* __restrict__ part, int nsplit, size_t per_split) {
+  const int k = blockIdx.y;
+  double* pk = part + (size_t)k * nsplit * per_split;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_split; e += (size_t)gridDim.x * blockDim.x) {
+    double acc = pk[e];
+    for (int s = 1; s < nsplit; ++s) acc += pk[(size_t)s * per_split + e];
+    pk[e] = acc;
+  }
+}
+
 cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
+  const int na = P->nt + P->ndefl;
+  const size_t per_split = (size_t)2 * na * na;
+  if (P->tc_nsplit > 1) {
+    dim3 gr((unsigned)((per_split + 255) / 256), P->nd);
+    gram_tc_reduce_kernel<<<gr, 256, 0, st>>>(P->ws.gtc, P->tc_nsplit, per_split);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // the reduced sum sits in split 0 of each window: read it as a single split
+  // with the window stride of the full buffer
   dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
   gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.phi, P->ws.xmax, P->tc_nsplit,
                                                  P->q_nsplit, P->nt, P->ndefl, P->ws.R);

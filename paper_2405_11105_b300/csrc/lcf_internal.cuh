@@ -150,28 +150,25 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
-// r += U_i. Phi^T e_j + conj(Phi^T e_i) . conj(U_j.) + conj(Phi^T e_i) Q Phi^T e_j, i.e. the
-// E^H R' E terms beyond the residual block (FP64; phi_a(t) = ph[a][t]).
-__device__ __forceinline__ void add_deflated_terms(double2& r, int i, int j, int nd_defl, const double2 (*U)[kDeflateMax],
-                                   const double2 (*Q)[kDeflateMax], const double2 (*ph)[kEvdNmax]) {
+// W = U + 1/2 conj(Phi) Q for rows i (one thread per (i, a)); with it the E^H R' E
+// terms beyond the residual block are W Phi^T + (W Phi^T)^H (Q Hermitian).
+__device__ __forceinline__ double2 deflated_w(int i, int a, int nd_defl, const double2 (*U)[kDeflateMax],
+                                              const double2 (*Q)[kDeflateMax], const double2 (*ph)[kEvdNmax]) {
+  double2 w = U[i][a];
+  for (int c = 0; c < nd_defl; ++c) {          // 1/2 sum_c conj(phi_c(i)) Q[c][a]
+    const double2 f = ph[c][i], q = Q[c][a];
+    w.x += 0.5 * (f.x * q.x + f.y * q.y);
+    w.y += 0.5 * (f.x * q.y - f.y * q.x);
+  }
+  return w;
+}
+// r += sum_a W_ia phi_a(j) + conj(sum_a W_ja phi_a(i))
+__device__ __forceinline__ void add_w_terms(double2& r, int i, int j, int nd_defl, const double2 (*Wm)[kDeflateMax],
+                                            const double2 (*ph)[kEvdNmax]) {
   for (int a = 0; a < nd_defl; ++a) {
-    const double2 fi = ph[a][i], fj = ph[a][j];
-    const double2 ui = U[i][a], uj = U[j][a];
-    // U_ia phi_a(j)
-    r.x += ui.x * fj.x - ui.y * fj.y;
-    r.y += ui.x * fj.y + ui.y * fj.x;
-    // conj(phi_a(i) U_ja)
-    r.x += fi.x * uj.x - fi.y * uj.y;
-    r.y -= fi.x * uj.y + fi.y * uj.x;
-    // conj(phi_a(i)) sum_c Q_ac phi_c(j)
-    double qx = 0.0, qy = 0.0;
-    for (int c = 0; c < nd_defl; ++c) {
-      const double2 q = Q[a][c], fc = ph[c][j];
-      qx += q.x * fc.x - q.y * fc.y;
-      qy += q.x * fc.y + q.y * fc.x;
-    }
-    r.x += fi.x * qx + fi.y * qy;
-    r.y += fi.x * qy - fi.y * qx;
+    const double2 wi = Wm[i][a], fj = ph[a][j], wj = Wm[j][a], fi = ph[a][i];
+    r.x += (wi.x * fj.x - wi.y * fj.y) + (wj.x * fi.x - wj.y * fi.y);
+    r.y += (wi.x * fj.y + wi.y * fj.x) - (wj.x * fi.y + wj.y * fi.x);
   }
 }
 
