@@ -207,6 +207,11 @@ lcf_status lcf_gram_noalloc(const lcf_config* cfg, const void* d_iq, void* d_R, 
 /* Size in bytes of lcf_gram_noalloc's static per-device scratch. */
 size_t lcf_gram_noalloc_scratch_bytes(void);
 
+/* Number of kernels the plan has launched since it was created (every
+ * filter call adds the launches of its stages; debug dumps add theirs).
+ * *n (host) receives the count.  No synchronisation. */
+lcf_status lcf_plan_launch_count(const lcf_plan* plan, long long* n);
+
 /* Bytes of device workspace the plan holds. */
 size_t lcf_plan_workspace_bytes(const lcf_plan* plan);
 

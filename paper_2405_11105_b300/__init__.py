@@ -59,6 +59,7 @@ def _load():
         "lcf_debug_filtered_iq": ([vp, vp, C.c_int, vp, vp], C.c_int),
         "lcf_plan_windows": ([vp, ip, C.c_int, ip], C.c_int),
         "lcf_plan_workspace_bytes": ([vp], C.c_size_t),
+        "lcf_plan_launch_count": ([vp, C.POINTER(C.c_longlong)], C.c_int),
         "lcf_plan_profile": ([vp, C.c_int], C.c_int),
         "lcf_plan_profile_read": ([vp, dp, ip], C.c_int),
         "lcf_plan_destroy": ([vp], C.c_int),
@@ -158,6 +159,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def launch_count(self) -> int:
+        """Kernels this plan has launched since it was created."""
+        n = C.c_longlong()
+        _check(_lib.lcf_plan_launch_count(self.handle, C.byref(n)), "lcf_plan_launch_count")
+        return n.value
 
     @property
     def workspace_bytes(self) -> int:

@@ -13,7 +13,9 @@
 //                       complex tiles, upper triangle), one per pixel split;
 //  basis_kernel       : one CTA sums the partials, scales, and runs subspace
 //                       iteration from the DCT-II start (CGS2 by one warp),
-//                       writing phi[j][t] (complex, orthonormal columns).
+//                       writing phi[j][t] (complex, orthonormal columns),
+//                       and zeroes the packet maximum the centring kernel
+//                       accumulates.
 #include <math.h>
 
 #include "lcf_internal.cuh"
@@ -90,13 +92,15 @@ global_gram_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int zs
 
 // One CTA of 256 threads.  smem: G (nt*nt float2) + Y, Z (nt*d float2 each).
 __global__ void __launch_bounds__(256)
-basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, float2* __restrict__ phi) {
+basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, float2* __restrict__ phi,
+             unsigned* __restrict__ xmax) {
   extern __shared__ float2 bsm[];
   float2* G = bsm;                       // nt*nt
   float2* Y = G + (size_t)nt * nt;       // nt*d, column j at Y[t*d + j]
   float2* Z = Y + (size_t)nt * nd_defl;
   __shared__ float gmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, d = nd_defl;
+  if (tid == 0) *xmax = 0u;   // the centring kernel's atomicMax target for this packet
   for (int e = tid; e < nt * nt; e += blockDim.x) {
     int i = e / nt, j = e % nt;
     bool up = i <= j;
@@ -177,15 +181,16 @@ cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st) {
   dim3 grid(ntile * (ntile + 1) / 2, P->basis_nsplit);
   global_gram_kernel<<<grid, 256, 0, st>>>(iq, c.nz, c.nx, P->nt, basis_zstep(c.nz), ntile, P->basis_nsplit,
                                            P->ws.gglob);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
   if (P->basis_nsplit > 1) {
     basis_reduce_kernel<<<(P->nt * P->nt + 255) / 256, 256, 0, st>>>(P->ws.gglob, P->basis_nsplit, P->nt);
-    e = cudaGetLastError();
+    e = counted(P);
     if (e != cudaSuccess) return e;
   }
-  basis_kernel<<<1, 256, basis_smem_bytes(P->nt, P->ndefl), st>>>(P->ws.gglob, 1, P->nt, P->ndefl, P->ws.phi);
-  return cudaGetLastError();
+  basis_kernel<<<1, 256, basis_smem_bytes(P->nt, P->ndefl), st>>>(P->ws.gglob, 1, P->nt, P->ndefl, P->ws.phi,
+                                                                 P->ws.xmax);
+  return counted(P);
 }
 
 cudaError_t basis_configure() {

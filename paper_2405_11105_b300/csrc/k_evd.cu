@@ -581,7 +581,7 @@ cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st) {
   size_t sm = evd_smem_bytes(P->nt);
   evd_kernel<<<P->nd, EVD_THREADS, sm, st>>>(P->ws.R, P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt,
                                              P->ws.kcut, P->ws.alpha, P->ws.flags, P->ws.W, P->ws.ncol);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 cudaError_t evd_configure() {

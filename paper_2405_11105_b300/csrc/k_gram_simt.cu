@@ -69,14 +69,11 @@ __global__ void center_kernel(const float2* __restrict__ iq, const float2* __res
 
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st) {
   int n = P->npix;
-  unsigned* xm = nullptr;
-  if (P->cfg.gram_path == LCF_PATH_TC) {
-    xm = P->ws.xmax;
-    cudaError_t e = cudaMemsetAsync(xm, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-  }
+  // the basis kernel, launched before this one, has zeroed the packet maximum
+  const bool tc = P->cfg.gram_path == LCF_PATH_TC || P->cfg.project_path == LCF_PATH_TC;
+  unsigned* xm = tc ? P->ws.xmax : nullptr;
   center_kernel<<<(n + 127) / 128, 128, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 constexpr int GT = 64;   // Gram tile (complex entries per side)
@@ -172,7 +169,7 @@ cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st) {
   dim3 grid(nt2, P->gram_nsplit, P->nd);
   gram_simt_kernel<<<grid, 256, 0, st>>>(P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ws.box, P->ws.gz,
                                           P->ws.gx, P->gram_tiles, P->gram_nsplit, P->ws.gpart);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 constexpr int ACH = 32;  // pixels staged per step of the augmented-column kernel
@@ -266,7 +263,7 @@ cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st) {
   dim3 grid(P->aug_nsplit, P->nd);
   gram_aug_kernel<<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
       P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit, P->ws.gaug);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 // Residual-block entry summed over splits (entries with a > b from conj of b,a).
@@ -343,7 +340,7 @@ cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st) {
   dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
   gram_assemble_kernel<<<grid, 256, 0, st>>>(P->ws.gpart, P->ws.gaug, P->ws.phi, P->gram_nsplit, P->aug_nsplit,
                                               P->nt, P->ndefl, P->ws.R);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 }  // namespace lcf

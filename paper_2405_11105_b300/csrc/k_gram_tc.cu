@@ -49,15 +49,6 @@ size_t gram_tc_smem_bytes(int na) {
   return TG_STAGES * (hi + lo) + 1024 + 2 * TG_PX * 8;
 }
 
-// 2^e with max|x| * 2^e < 2^14 (fp16 headroom for the products' inputs)
-__device__ __forceinline__ float tc_scale(const unsigned* xmax_bits) {
-  float xm = __uint_as_float(*xmax_bits);
-  if (!(xm > 0.f) || !isfinite(xm)) return 1.f;
-  int e;
-  frexpf(xm, &e);                // xm < 2^e
-  return ldexpf(1.f, 14 - e);
-}
-
 __global__ void __launch_bounds__(TG_THREADS, 1)
 gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box* __restrict__ boxes,
                const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
@@ -80,7 +71,7 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
   const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
   const int nst = (int)((l1 - l0 + TG_PX - 1) / TG_PX);
   const size_t npix = (size_t)nz * nx;
-  const float sc = tc_scale(xmax_bits);
+  const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
   const float* gzk = gz + (size_t)k * nz;
   const float* gxk = gx + (size_t)k * nx;
   const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
@@ -272,7 +263,7 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   __shared__ double2 ph[kDeflateMax][kEvdNmax];
   __shared__ double inv_s2;
   if (threadIdx.x == 0) {
-    float sc = tc_scale(xmax_bits);
+    float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
     inv_s2 = 1.0 / ((double)sc * (double)sc);
   }
   __syncthreads();
@@ -331,11 +322,11 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
                                                                     P->ws.gx, P->ws.xmax, P->tc_nsplit,
                                                                     P->ws.gtc, P->ws.err);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
   gram_q_kernel<<<dim3(P->q_nsplit, P->nd), 256, 0, st>>>(P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->ws.box,
                                                           P->ws.gz, P->ws.gx, P->q_nsplit, P->ws.gq);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 // part[k][0] += sum_{s>0} part[k][s] (coalesced; fixed split order)
@@ -355,7 +346,7 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   if (P->tc_nsplit > 1) {
     dim3 gr((unsigned)((per_split + 255) / 256), P->nd);
     gram_tc_reduce_kernel<<<gr, 256, 0, st>>>(P->ws.gtc, P->tc_nsplit, per_split);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = counted(P);
     if (e != cudaSuccess) return e;
   }
   // the reduced sum sits in split 0 of each window: read it as a single split
@@ -363,7 +354,7 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
   gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.phi, P->ws.xmax, P->tc_nsplit,
                                                  P->q_nsplit, P->nt, P->ndefl, P->ws.R);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 cudaError_t gram_tc_configure() {

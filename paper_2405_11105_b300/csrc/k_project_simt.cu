@@ -86,7 +86,7 @@ cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out,
   else
     project_simt_kernel<28><<<grid, 256, sm, st>>>(iq, c.nz, c.nx, P->nt, P->nd, P->ws.box, P->ws.gz,
                                                    P->ws.gx, P->ws.W, P->ws.ncol, P->ncp, out);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 cudaError_t project_configure() {
@@ -132,7 +132,7 @@ cudaError_t launch_filtered_iq(const lcf_plan* P, const float2* iq, int k, float
   filtered_iq_kernel<<<(npix + 127) / 128, 128, 0, st>>>(
       iq, c.nz, c.nx, P->nt, P->boxes[k], P->ws.gz + (size_t)k * c.nz, P->ws.gx + (size_t)k * c.nx,
       P->ws.V + (size_t)k * P->nt * P->nt, P->ws.wt + (size_t)k * P->nt, out);
-  return cudaGetLastError();
+  return counted(P);
 }
 
 }  // namespace lcf

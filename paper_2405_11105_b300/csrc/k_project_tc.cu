@@ -1,0 +1,351 @@
+// k_project_tc.cu — projection, |.|^2 slow-time reduction and blend on the
+// 5th-generation tensor cores (tcgen05), Eq. 4 and Eq. 13.
+//
+// As on the CUDA-core path, V unitary turns the per-window filter into
+//   PD(p) = sum_k g_k(p)^2 sum_c |s_p W_k(:,c)|^2,  W_k = V diag(wt sqrt(alpha/Nt)),
+// one GEMM per window.  Here the rows come from the deflated packet of the
+// Gram stage, s_p = c_p + sum_j a_pj phi_j^T, so
+//   s_p W = [c_p, a_p] [W ; Phi^T W]
+// and the clutter that the global basis removes never enters the fp16 operands:
+// the residual c_p and the coefficients a_p are each split hi + lo (22 bits),
+// as are the augmented weights, and three passes (hi.hi, hi.lo, lo.hi) with
+// FP32 accumulation in TMEM give the product to ~2^-22.  The complex product
+// needs no real embedding: with S = Sr + i Si and W = Wr + i Wi,
+//   Yr = Sr Wr - Si Wi,   Yi = Si Wr + Sr Wi,
+// four real GEMMs sharing the operands (the minus sign is the MMA's negate-A
+// bit), into two TMEM accumulators per window.
+//
+// Work split: one CTA per 8 x 16-pixel tile (M = 128 rows, one per TMEM lane).
+// The tile's [c_p, a_p] rows are staged once in shared memory (fp16 hi/lo,
+// K-major); the windows whose support meets the tile are taken in a fixed order,
+// each window's pre-split weight image streamed by the TMA engine through a
+// 3-stage ring.  Warp 0 issues the copies, warp 1 the MMAs, warps 4-7 read the
+// accumulators (double-buffered, so the next window's MMAs overlap the read) and
+// keep the blended pixel in a register: every pixel is written once, no atomics.
+#include <math.h>
+
+#include "lcf_internal.cuh"
+#include "tc_util.cuh"
+
+namespace lcf {
+
+constexpr int PT_THREADS = 256;
+constexpr int PT_TZ = 8, PT_TX = 16;     // tile: 8 rows x 16 columns = 128 pixels
+constexpr int PT_KS = 2;                 // k-steps (16 K each) per weight stage
+constexpr int PT_STAGES = 3;
+constexpr int PT_ACC = 256;              // TMEM columns per accumulator buffer (Yr at +0, Yi at +128)
+
+int pt_k16(int nt, int nd_defl) { return (nt + nd_defl + 15) / 16 * 16; }
+__host__ __device__ inline int pt_n16(int ncol) { return (ncol + 15) / 16 * 16; }
+// One k-step of a window's weight image: Wr hi, Wr lo, Wi hi, Wi lo, each n16 rows x 16 K (fp16).
+__host__ __device__ inline int pt_kstep_bytes(int n16) { return 4 * n16 * 32; }
+// offset of (column c, k index kk < 16) inside one n16 x 16 sub-image (K-major, SBO = 256 B)
+__device__ __forceinline__ int pt_b_off(int c, int kk) { return (c >> 3) * 256 + (kk >> 3) * 128 + (c & 7) * 16 + (kk & 7) * 2; }
+
+size_t project_tc_image_bytes(int nt, int nd_defl) {
+  return (size_t)(pt_k16(nt, nd_defl) / 16) * pt_kstep_bytes(pt_n16(nt));
+}
+
+size_t project_tc_smem_bytes(int nt, int nd_defl) {
+  const int k16 = pt_k16(nt, nd_defl);
+  return 1024 + 4 * (size_t)128 * k16 * 2 + (size_t)PT_STAGES * PT_KS * pt_kstep_bytes(pt_n16(nt));
+}
+
+// ---------------------------------------------------------------------------
+// Weight images.  One CTA per window: the augmented block [W ; Phi^T W]
+// (rows t < Nt: W, rows Nt + j: phi_j^T W, in FP64), scaled by a power of two
+// into fp16 range and split hi/lo, laid out k-step by k-step in the exact
+// shared-memory image the MMA reads.
+__global__ void __launch_bounds__(256)
+project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, const float2* __restrict__ phi,
+                    int nt, int nd_defl, int ncp, int k16, int n16max, unsigned char* __restrict__ bimg,
+                    float* __restrict__ bscale) {
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const int nc = ncol[k], n16 = pt_n16(nc);
+  const float2* Wk = W + (size_t)k * nt * ncp;
+  __shared__ float2 PW[kDeflateMax][kEvdNmax];   // phi_j^T W(:, c)
+  __shared__ float red[8];
+  for (int e = tid; e < nd_defl * nc; e += blockDim.x) {
+    const int j = e / nc, c = e % nc;
+    double sr = 0.0, si = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const float2 f = phi[j * nt + t], w = Wk[(size_t)t * ncp + c];
+      sr += (double)f.x * w.x - (double)f.y * w.y;
+      si += (double)f.x * w.y + (double)f.y * w.x;
+    }
+    PW[j][c] = make_float2((float)sr, (float)si);
+  }
+  __syncthreads();
+  float m = 0.f;
+  for (int e = tid; e < nt * nc; e += blockDim.x) {
+    const float2 w = Wk[(size_t)(e / nc) * ncp + e % nc];
+    m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
+  }
+  for (int e = tid; e < nd_defl * nc; e += blockDim.x) {
+    const float2 w = PW[e / nc][e % nc];
+    m = fmaxf(m, fmaxf(fabsf(w.x), fabsf(w.y)));
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(~0u, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  if (tid < 32) {
+    float v = tid < (int)(blockDim.x >> 5) ? red[tid] : 0.f;
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(~0u, v, o));
+    if (tid == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float s = tc::pow2_scale(red[0]);
+  if (tid == 0) bscale[k] = s;
+  unsigned char* img = bimg + (size_t)k * (k16 / 16) * pt_kstep_bytes(n16max);
+  const int kb = pt_kstep_bytes(n16), sub = n16 * 32;
+  for (int e = tid; e < k16 * n16; e += blockDim.x) {
+    const int t = e / n16, c = e % n16;
+    float2 v = make_float2(0.f, 0.f);
+    if (c < nc) {
+      if (t < nt) v = Wk[(size_t)t * ncp + c];
+      else if (t < nt + nd_defl) v = PW[t - nt][c];
+    }
+    __half hr, lr, hi, li;
+    tc::split_f16(v.x * s, hr, lr);
+    tc::split_f16(v.y * s, hi, li);
+    unsigned char* base = img + (size_t)(t >> 4) * kb + pt_b_off(c, t & 15);
+    *reinterpret_cast<__half*>(base) = hr;
+    *reinterpret_cast<__half*>(base + sub) = lr;
+    *reinterpret_cast<__half*>(base + 2 * sub) = hi;
+    *reinterpret_cast<__half*>(base + 3 * sub) = li;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PT_THREADS, 1)
+project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, int k16, int n16max,
+                  int tiles_x, const int* __restrict__ tile_off, const int* __restrict__ tile_win,
+                  const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
+                  const int* __restrict__ ncol, const unsigned char* __restrict__ bimg,
+                  const float* __restrict__ bscale, float* __restrict__ out, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[PT_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[PT_STAGES];
+  __shared__ __align__(8) uint64_t accf[2];
+  __shared__ __align__(8) uint64_t acce[2];
+  __shared__ uint32_t tmem_base;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x, z0 = (tile / tiles_x) * PT_TZ, x0 = (tile % tiles_x) * PT_TX;
+  const int w0 = tile_off[tile], w1 = tile_off[tile + 1];
+  const int na = nt + nd_defl, nks = k16 / 16, nstw = (nks + PT_KS - 1) / PT_KS;
+  const size_t npix = (size_t)nz * nx;
+  const int a_sbo = (k16 / 8) * 128;
+  const size_t a_bytes = (size_t)128 * k16 * 2;            // one of Sr hi, Sr lo, Si hi, Si lo
+  unsigned char* A = smem;
+  unsigned char* Bring = smem + 4 * a_bytes;
+  const size_t st_bytes = (size_t)PT_KS * pt_kstep_bytes(n16max);
+  const size_t img_stride = (size_t)nks * pt_kstep_bytes(n16max);
+  const float sA = tc::pow2_scale(__uint_as_float(*xmax_bits));
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    for (int i = 0; i < PT_STAGES; ++i) {
+      tc::mbar_init(&full_bar[i], 1);
+      tc::mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&accf[i], 1);
+      tc::mbar_init(&acce[i], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+
+  // ---- stage the tile's rows [c_p, a_p] (scaled, split hi/lo), zero K padding ----
+  // item i: lane -> (row%8, k-pair), so a warp's 4-byte stores hit 32 distinct banks
+  for (int i = tid; i < 128 * (k16 / 2); i += PT_THREADS) {
+    const int ln = i & 31, rest = i >> 5;
+    const int m = (rest & 15) * 8 + (ln & 7), t = (rest >> 4) * 8 + (ln >> 3) * 2;
+    const int z = z0 + (m >> 4), x = x0 + (m & 15);
+    float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+    if (z < nz && x < nx) {
+      const size_t p = (size_t)z * nx + x;
+      if (t < na) v0 = xa[(size_t)t * npix + p];
+      if (t + 1 < na) v1 = xa[(size_t)(t + 1) * npix + p];
+    }
+    __half h0r, l0r, h1r, l1r, h0i, l0i, h1i, l1i;
+    tc::split_f16(v0.x * sA, h0r, l0r);
+    tc::split_f16(v1.x * sA, h1r, l1r);
+    tc::split_f16(v0.y * sA, h0i, l0i);
+    tc::split_f16(v1.y * sA, h1i, l1i);
+    const int off = tc::op_off(m, t, a_sbo);
+    *reinterpret_cast<__half2*>(A + off) = __halves2half2(h0r, h1r);
+    *reinterpret_cast<__half2*>(A + a_bytes + off) = __halves2half2(l0r, l1r);
+    *reinterpret_cast<__half2*>(A + 2 * a_bytes + off) = __halves2half2(h0i, h1i);
+    *reinterpret_cast<__half2*>(A + 3 * a_bytes + off) = __halves2half2(l0i, l1i);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tmem_base;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---------------- producer: weight stages through the ring ----------------
+    if (lane == 0) {
+      int q = 0;
+      for (int wi = w0; wi < w1 && ok; ++wi) {
+        const int k = tile_win[wi], nc = ncol[k];
+        if (nc == 0) continue;
+        const int kb = pt_kstep_bytes(pt_n16(nc));
+        const unsigned char* img = bimg + (size_t)k * img_stride;
+        for (int s = 0; s < nstw; ++s, ++q) {
+          const int slot = q % PT_STAGES;
+          if (q >= PT_STAGES && !(ok = tc::mbar_wait(&empty_bar[slot], ((q / PT_STAGES) - 1) & 1))) break;
+          const int nk = min(PT_KS, nks - s * PT_KS);
+          const uint32_t bytes = (uint32_t)(nk * kb);
+          tc::mbar_arrive_expect_tx(&full_bar[slot], bytes);
+          tc::bulk_g2s(Bring + slot * st_bytes, img + (size_t)s * PT_KS * kb, bytes, &full_bar[slot]);
+        }
+      }
+      // the copies still in flight land before the CTA exits
+      for (int r = 1; r <= PT_STAGES && r <= q; ++r) {
+        const int qq = q - r;
+        tc::mbar_wait(&full_bar[qq % PT_STAGES], (qq / PT_STAGES) & 1, 20000000L);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int q = 0, j = 0;
+      uint32_t a_h[2], a_l[2];
+      a_h[0] = tc::smem_u32(A);
+      a_l[0] = tc::smem_u32(A + a_bytes);
+      a_h[1] = tc::smem_u32(A + 2 * a_bytes);
+      a_l[1] = tc::smem_u32(A + 3 * a_bytes);
+      for (int wi = w0; wi < w1 && ok; ++wi) {
+        const int k = tile_win[wi], nc = ncol[k];
+        if (nc == 0) continue;
+        const int n16 = pt_n16(nc), kb = pt_kstep_bytes(n16), sub = n16 * 32;
+        const int buf = j & 1;
+        if (j >= 2 && !(ok = tc::mbar_wait(&acce[buf], ((j >> 1) - 1) & 1))) break;
+        tc::fence_after();
+        const uint32_t idesc = tc::idesc_f16(128, n16), idesc_neg = idesc | (1u << 13);   // bit 13: negate A
+        const uint32_t dr = tbase + (uint32_t)(buf * PT_ACC), di = dr + 128;
+        for (int s = 0; s < nstw; ++s, ++q) {
+          const int slot = q % PT_STAGES;
+          if (!(ok = tc::mbar_wait(&full_bar[slot], (q / PT_STAGES) & 1))) break;
+          tc::fence_after();
+          const int nk = min(PT_KS, nks - s * PT_KS);
+          const uint32_t bslot = tc::smem_u32(Bring + slot * st_bytes);
+          for (int kl = 0; kl < nk; ++kl) {
+            const int ks = s * PT_KS + kl;
+            const uint64_t srh = tc::smem_desc(a_h[0] + ks * 256, 128, a_sbo);
+            const uint64_t srl = tc::smem_desc(a_l[0] + ks * 256, 128, a_sbo);
+            const uint64_t sih = tc::smem_desc(a_h[1] + ks * 256, 128, a_sbo);
+            const uint64_t sil = tc::smem_desc(a_l[1] + ks * 256, 128, a_sbo);
+            const uint32_t bb = bslot + kl * kb;
+            const uint64_t wrh = tc::smem_desc(bb, 128, 256), wrl = tc::smem_desc(bb + sub, 128, 256);
+            const uint64_t wih = tc::smem_desc(bb + 2 * sub, 128, 256), wil = tc::smem_desc(bb + 3 * sub, 128, 256);
+            const uint32_t acc = ks == 0 ? 0u : 1u;
+            // Yr = Sr Wr - Si Wi
+            tc::mma_f16(dr, srh, wrh, idesc, acc);
+            tc::mma_f16(dr, srh, wrl, idesc, 1u);
+            tc::mma_f16(dr, srl, wrh, idesc, 1u);
+            tc::mma_f16(dr, sih, wih, idesc_neg, 1u);
+            tc::mma_f16(dr, sih, wil, idesc_neg, 1u);
+            tc::mma_f16(dr, sil, wih, idesc_neg, 1u);
+            // Yi = Si Wr + Sr Wi
+            tc::mma_f16(di, sih, wrh, idesc, acc);
+            tc::mma_f16(di, sih, wrl, idesc, 1u);
+            tc::mma_f16(di, sil, wrh, idesc, 1u);
+            tc::mma_f16(di, srh, wih, idesc, 1u);
+            tc::mma_f16(di, srh, wil, idesc, 1u);
+            tc::mma_f16(di, srl, wih, idesc, 1u);
+          }
+          tc::mma_commit(&empty_bar[slot]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&accf[buf]);
+        ++j;
+      }
+      // every MMA this thread issued has completed before TMEM is released
+      if (j > 0) tc::mbar_wait(&accf[(j - 1) & 1], ((j - 1) >> 1) & 1, 20000000L);
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue: |Y|^2 row sums, window weights, blend ----------------
+    const int m = (warp - 4) * 32 + lane;
+    const int z = z0 + (m >> 4), x = x0 + (m & 15);
+    const bool inside = z < nz && x < nx;
+    float pd = 0.f;
+    int j = 0;
+    for (int wi = w0; wi < w1; ++wi) {
+      const int k = tile_win[wi], nc = ncol[k];
+      if (nc == 0) continue;
+      const int n16 = pt_n16(nc), buf = j & 1;
+      // warp-uniform outcome: the TMEM loads below are .sync.aligned
+      if (!(ok = __all_sync(~0u, tc::mbar_wait(&accf[buf], (j >> 1) & 1)))) break;
+      tc::fence_after();
+      const uint32_t base = tbase + (uint32_t)(buf * PT_ACC) + ((uint32_t)((warp & 3) * 32) << 16);
+      float acc = 0.f;
+      for (int c = 0; c < n16; c += 16) {
+        float v[16];
+        tc::tmem_ld16(base + c, v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc = fmaf(v[u], v[u], acc);
+        tc::tmem_ld16(base + 128 + c, v);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc = fmaf(v[u], v[u], acc);
+      }
+      tc::fence_before();
+      tc::mbar_arrive(&acce[buf]);
+      if (inside) {
+        const float g = gz[(size_t)k * nz + z] * gx[(size_t)k * nx + x];
+        const float inv = 1.f / (sA * bscale[k]);
+        pd = fmaf(g * g * inv * inv, acc, pd);
+      }
+      ++j;
+    }
+    if (inside) out[(size_t)z * nx + x] = pd;
+  }
+  if (!ok) atomicOr(err, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  const int k16 = pt_k16(P->nt, P->ndefl), n16max = pt_n16(P->nt);
+  project_prep_kernel<<<P->nd, 256, 0, st>>>(P->ws.W, P->ws.ncol, P->ws.phi, P->nt, P->ndefl, P->ncp, k16, n16max,
+                                             P->ws.bimg, P->ws.bscale);
+  cudaError_t e = counted(P);
+  if (e != cudaSuccess) return e;
+  project_tc_kernel<<<P->ptiles_z * P->ptiles_x, PT_THREADS, project_tc_smem_bytes(P->nt, P->ndefl), st>>>(
+      P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, k16, n16max, P->ptiles_x, P->ws.tile_off, P->ws.tile_win, P->ws.gz,
+      P->ws.gx, P->ws.xmax, P->ws.ncol, P->ws.bimg, P->ws.bscale, out, P->ws.err);
+  return counted(P);
+}
+
+cudaError_t project_tc_configure() {
+  return cudaFuncSetAttribute(project_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)project_tc_smem_bytes(kEvdNmax, kDeflateMax));
+}
+
+void project_tc_tiles(const lcf_plan* P, int* tiles_z, int* tiles_x, std::vector<int>& off, std::vector<int>& win) {
+  const lcf_config& c = P->cfg;
+  *tiles_z = (c.nz + PT_TZ - 1) / PT_TZ;
+  *tiles_x = (c.nx + PT_TX - 1) / PT_TX;
+  off.assign(1, 0);
+  win.clear();
+  for (int tz = 0; tz < *tiles_z; ++tz)
+    for (int tx = 0; tx < *tiles_x; ++tx) {
+      const int za = tz * PT_TZ, zb = za + PT_TZ, xa0 = tx * PT_TX, xb = xa0 + PT_TX;
+      for (int k = 0; k < P->nd; ++k) {
+        const Box& b = P->boxes[k];
+        if (b.z1 <= b.z0 || b.x1 <= b.x0) continue;
+        if (b.z0 < zb && za < b.z1 && b.x0 < xb && xa0 < b.x1) win.push_back(k);
+      }
+      off.push_back((int)win.size());
+    }
+}
+
+}  // namespace lcf

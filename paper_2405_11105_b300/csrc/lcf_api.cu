@@ -114,7 +114,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
-                  w.flags, w.W, w.ncol, w.iq_stage, w.pd_stage};
+                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -194,6 +194,14 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.flags, nd, &tot);
   if (e == cudaSuccess) e = dalloc(&w.W, nd * nt * P->ncp, &tot);
   if (e == cudaSuccess) e = dalloc(&w.ncol, nd, &tot);
+  std::vector<int> toff, twin;
+  if (cfg->project_path == LCF_PATH_TC) {
+    project_tc_tiles(P, &P->ptiles_z, &P->ptiles_x, toff, twin);
+    if (e == cudaSuccess) e = dalloc(&w.tile_off, toff.size(), &tot);
+    if (e == cudaSuccess) e = dalloc(&w.tile_win, twin.size(), &tot);
+    if (e == cudaSuccess) e = dalloc(&w.bimg, nd * project_tc_image_bytes(P->nt, P->ndefl), &tot);
+    if (e == cudaSuccess) e = dalloc(&w.bscale, nd, &tot);
+  }
   if (e == cudaSuccess) e = dalloc(&w.iq_stage, nt * npix, &tot);
   if (e == cudaSuccess) e = dalloc(&w.pd_stage, npix, &tot);
   if (e != cudaSuccess) {
@@ -209,11 +217,17 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = cudaMemset(w.flags, 0, nd * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(w.err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(w.xmax, 0, sizeof(unsigned));
+  if (e == cudaSuccess && cfg->project_path == LCF_PATH_TC) {
+    e = cudaMemcpy(w.tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !twin.empty())
+      e = cudaMemcpy(w.tile_win, twin.data(), twin.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && (device >= 64 || !g_configured[device])) {
     e = evd_configure();
     if (e == cudaSuccess) e = project_configure();
     if (e == cudaSuccess) e = gram_tc_configure();
     if (e == cudaSuccess) e = basis_configure();
+    if (e == cudaSuccess) e = project_tc_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
   }
   if (e != cudaSuccess) {
@@ -254,7 +268,6 @@ static cudaEvent_t prof_event(lcf_plan* P, int b) {
 
 static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
-  if (c.project_path != LCF_PATH_SIMT) return LCF_EUNSUPPORTED;
   const bool tc = c.gram_path == LCF_PATH_TC;
   LCF_MARK(LCF_STAGE_PREP);
   LCF_CUDA(launch_basis(P, iq, st));
@@ -272,7 +285,8 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   LCF_MARK(LCF_STAGE_EVD);
   LCF_CUDA(launch_evd(P, st));
   LCF_MARK(LCF_STAGE_PROJECT);
-  LCF_CUDA(launch_project_simt(P, iq, out, st));
+  if (c.project_path == LCF_PATH_TC) LCF_CUDA(launch_project_tc(P, out, st));
+  else LCF_CUDA(launch_project_simt(P, iq, out, st));
   LCF_MARK(LCF_NSTAGES);
   if (P->profiling) ++P->prof_calls;
   return LCF_OK;
@@ -411,6 +425,12 @@ extern "C" lcf_status lcf_plan_windows(lcf_plan* P, int* nd, int k, int* box) {
     const Box& b = P->boxes[k];
     box[0] = b.z0; box[1] = b.z1; box[2] = b.x0; box[3] = b.x1;
   }
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_launch_count(const lcf_plan* P, long long* n) {
+  if (!P || !n) return LCF_EINVAL;
+  *n = P->launches;
   return LCF_OK;
 }
 

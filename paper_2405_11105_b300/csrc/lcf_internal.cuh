@@ -51,6 +51,11 @@ struct Workspace {
   int* flags = nullptr;       // [nd]
   float2* W = nullptr;        // [nd][nt][ncp] projection weights V diag(wt sqrt(alpha/Nt))
   int* ncol = nullptr;        // [nd]
+  // tensor-core projection
+  int* tile_off = nullptr;    // [ntiles+1] CSR offsets of the windows meeting each 8x16 tile
+  int* tile_win = nullptr;    // window indices, ascending per tile
+  unsigned char* bimg = nullptr;  // [nd] pre-split weight images (fp16 hi/lo, MMA layout)
+  float* bscale = nullptr;    // [nd] power-of-two scale of each weight image
   // host-call staging
   float2* iq_stage = nullptr; // [nt][nz][nx] device copy for lcf_filter_host
   float* pd_stage = nullptr;  // [nz][nx]
@@ -70,6 +75,7 @@ struct lcf_plan {
   int gram_tiles = 0;   // 64-wide tiles per Gram dimension
   int gram_nsplit = 1;  // pixel splits per window
   int ncp = 0;          // padded projection columns
+  int ptiles_z = 0, ptiles_x = 0;   // tensor-core projection tiles (8 x 16 pixels)
   int sm_count = 0;
   std::vector<lcf::Box> boxes;
   lcf::Workspace ws;
@@ -77,6 +83,8 @@ struct lcf_plan {
   cudaStream_t last_stream = nullptr;
   void* last_iq = nullptr;
   // stage profiling: events[call % kProfCalls][stage boundary]
+  // kernels this plan has launched (every launcher adds its own)
+  mutable long long launches = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;
   long prof_calls = 0;
@@ -173,6 +181,11 @@ __device__ __forceinline__ void add_w_terms(double2& r, int i, int j, int nd_def
 }
 
 // ----- launchers (each returns cudaGetLastError() after the launch) -----
+// Call after each kernel launch of a plan: counts it in P->launches.
+inline cudaError_t counted(const lcf_plan* P, int n = 1) {
+  P->launches += n;
+  return cudaGetLastError();
+}
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st);
 size_t gram_aug_smem_bytes(int nt, int nd_defl);
@@ -186,6 +199,10 @@ size_t gram_tc_smem_bytes(int na);
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
+cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st);
+cudaError_t project_tc_configure();
+size_t project_tc_image_bytes(int nt, int nd_defl);
+void project_tc_tiles(const lcf_plan* P, int* tiles_z, int* tiles_x, std::vector<int>& off, std::vector<int>& win);
 cudaError_t launch_filtered_iq(const lcf_plan* P, const float2* iq, int subset, float2* out,
                                cudaStream_t st);
 size_t evd_smem_bytes(int nt);

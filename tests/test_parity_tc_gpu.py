@@ -1,4 +1,4 @@
-"""Tensor-core (tcgen05) paths vs the FP64 oracle, through the C ABI.
+"""Tensor-core (tcgen05) paths (Gram, projection) vs the FP64 oracle, through the C ABI.
 
 Same tolerances as the plain FP32 path (see test_parity_gpu.py): PD rel L2
 <= 1e-3, eigenvalues in the 1e-6*lambda_1 band <= 1e-4 relative, Gram rel
@@ -16,10 +16,11 @@ from test_parity_gpu import (ALPHA_TOL, EIG_TOL, GRAM_TOL, PD_TOL, L, compare, c
                              rand_iq)
 
 
-def tc_cfg(*a, **kw):
+def tc_cfg(*a, project=False, gram=True, **kw):
     lib = L()
     cfg, oc = configs(*a, **kw)
-    cfg.gram_path = lib.LCF_PATH_TC
+    cfg.gram_path = lib.LCF_PATH_TC if gram else lib.LCF_PATH_SIMT
+    cfg.project_path = lib.LCF_PATH_TC if project else lib.LCF_PATH_SIMT
     return cfg, oc
 
 
@@ -82,3 +83,69 @@ def test_tc_matches_plain_path():
         out[path] = plan.filter(d).cpu().numpy().astype(np.float64)
     a, b = out[lib.LCF_PATH_SIMT], out[lib.LCF_PATH_TC]
     assert np.linalg.norm(a - b) / np.linalg.norm(a) <= 2e-4
+
+
+# ---- tensor-core projection (and both tensor-core stages together) ----
+
+def test_tcproj_small_fixed_k3():
+    lib = L()
+    iq = generate_packet(SMALL_96x64x32, seed=0)
+    cfg, oc = tc_cfg(96, 64, 32, 3, 3, project=True, thresh_mode=lib.LCF_T_FIXED, k_fixed=3)
+    check(compare(iq, cfg, oc))
+
+
+def test_tcproj_realtime_curvature():
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=0)
+    cfg, oc = tc_cfg(256, 128, 100, 8, 8, project=True, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    check(compare(iq, cfg, oc))
+
+
+def test_tcproj_with_plain_gram():
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=5)
+    cfg, oc = tc_cfg(256, 128, 100, 8, 8, project=True, gram=False, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    check(compare(iq, cfg, oc))
+
+
+@pytest.mark.parametrize("mode,beta", [("LCF_T_ADAPTIVE_SOFT", 0.5), ("LCF_T_NONE", 1.0), ("LCF_T_SIGMOID", 1.0)])
+def test_tcproj_soft_and_all_columns(mode, beta):
+    """Rules that keep (almost) every column: widest weight images (n16 = 112 for Nt = 100)."""
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=3)
+    cfg, oc = tc_cfg(256, 128, 100, 8, 8, project=True, thresh_mode=getattr(lib, mode), beta=beta, k_fixed=2)
+    check(compare(iq, cfg, oc, want_gram=False), gram=False)
+
+
+@pytest.mark.parametrize("shape,grid,mode", [
+    ((33, 40, 70), (2, 3), "LCF_T_FIXED"),      # ragged tiles in both directions
+    ((16, 17, 23), (1, 1), "LCF_T_MEDIAN"),
+    ((112, 24, 20), (2, 2), "LCF_T_CURVATURE"),  # largest packet: K = 128, n16 = 112
+    ((2, 8, 8), (1, 1), "LCF_T_FIXED"),         # one tile, one k-step
+    ((48, 9, 130), (3, 5), "LCF_T_CURVATURE"),  # more tiles along x than along z
+])
+def test_tcproj_edge_shapes(shape, grid, mode):
+    lib = L()
+    nt, nz, nx = shape
+    cfg, oc = tc_cfg(nz, nx, nt, grid[0], grid[1], project=True, thresh_mode=getattr(lib, mode), k_fixed=1,
+                     beta=1.0)
+    check(compare(rand_iq(3, nt, nz, nx), cfg, oc))
+
+
+def test_tcproj_matches_plain_path():
+    """Tensor-core projection vs the CUDA-core projection on the same Gram/EVD output."""
+    import torch
+    lib = L()
+    iq = generate_packet(REALTIME_256x128x100, seed=4)
+    d = torch.from_numpy(iq).cuda()
+    out = {}
+    for path in (lib.LCF_PATH_SIMT, lib.LCF_PATH_TC):
+        plan = lib.Plan.make(256, 128, 100, 8, 8, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0,
+                             gram_path=lib.LCF_PATH_TC, project_path=path)
+        out[path] = plan.filter(d).cpu().numpy().astype(np.float64)
+        st, _ = plan.status()
+        assert st == lib.LCF_OK
+    a, b = out[lib.LCF_PATH_SIMT], out[lib.LCF_PATH_TC]
+    rel = np.linalg.norm(a - b) / np.linalg.norm(a)
+    print("tc projection vs simt projection rel l2", rel, "max rel", np.max(np.abs(a - b) / np.maximum(a, 1e-30)))
+    assert rel <= 1e-4
