@@ -82,6 +82,12 @@ enum { LCF_WFLAG_NOCONV = 1, LCF_WFLAG_DEGENERATE = 2, LCF_WFLAG_SWEEP_SHIFT = 8
  * accumulation promoted to double-float. */
 enum { LCF_PATH_SIMT = 0, LCF_PATH_TC = 1 };
 
+/* EVD kernels.  LCF_EVD_CTA: one CTA per window holds A and V (plain path).
+ * LCF_EVD_PAIR: a two-CTA cluster per window; one CTA runs the Jacobi
+ * rotations on A and streams them through distributed shared memory to the
+ * other, which accumulates V.  Same arithmetic and tolerances. */
+enum { LCF_EVD_CTA = 0, LCF_EVD_PAIR = 1 };
+
 typedef struct {
   int nz, nx, nt;          /* packet size: Nz axial x Nx lateral x Nt frames      */
   int wz, wx;              /* window grid; Nd = wz*wx subsets                     */
@@ -102,6 +108,7 @@ typedef struct {
   int gram_path;           /* LCF_PATH_*                                          */
   int project_path;        /* LCF_PATH_*                                          */
   int max_sweeps;          /* Jacobi sweep cap per level (<= 0: 40)               */
+  int evd_path;            /* LCF_EVD_*                                           */
 } lcf_config;
 
 /* Fill *cfg with defaults for an nz x nx x nt packet and a wz x wx grid:
@@ -181,6 +188,14 @@ lcf_status lcf_plan_profile(lcf_plan* plan, int enable);
  * calls recorded since profiling was enabled: ms[LCF_NSTAGES] (host),
  * *n_calls = number of calls summed.  Either pointer may be NULL. */
 lcf_status lcf_plan_profile_read(lcf_plan* plan, double* ms, int* n_calls);
+
+/* EVD phase timing of the most recent filter call made while profiling was
+ * on: cycles[8] (host) receives the SM clock cycles of each phase averaged
+ * over the windows, in order: subspace iteration, QR of the block,
+ * double-float congruence, fp32 conversion and Q, Jacobi sweeps, sort and
+ * phase fix, thresholding rule, projection weights.  Synchronises the
+ * plan's last stream.  LCF_EINVAL if profiling was never enabled. */
+lcf_status lcf_plan_evd_phases(lcf_plan* plan, double* cycles);
 
 /* Windowed Gram matrices of one packet without any allocation.  The paper
  * has no counterpart: this entry point exists for callers that cannot call

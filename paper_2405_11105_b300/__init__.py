@@ -23,7 +23,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
  LCF_T_NONE) = range(7)
 LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE, LCF_WFLAG_SWEEP_SHIFT = 1, 2, 8
 LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
+LCF_EVD_CTA, LCF_EVD_PAIR = 0, 1
 STAGES = ("prep", "gram", "assemble", "evd", "project")
+EVD_PHASES = ("subspace", "qr", "congruence", "convert_q", "jacobi", "sort_phase", "rule", "weights")
 
 
 class lcf_config(C.Structure):
@@ -32,7 +34,8 @@ class lcf_config(C.Structure):
                 ("all_ones_window", C.c_int), ("thresh_mode", C.c_int), ("beta", C.c_float),
                 ("k_fixed", C.c_int), ("k_src", C.c_int), ("beta_src", C.c_float),
                 ("pd_mode", C.c_int), ("alpha_mode", C.c_int), ("curv_norm", C.c_int),
-                ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int)]
+                ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int),
+                ("evd_path", C.c_int)]
 
 
 class LcfError(RuntimeError):
@@ -60,6 +63,7 @@ def _load():
         "lcf_plan_windows": ([vp, ip, C.c_int, ip], C.c_int),
         "lcf_plan_workspace_bytes": ([vp], C.c_size_t),
         "lcf_plan_launch_count": ([vp, C.POINTER(C.c_longlong)], C.c_int),
+        "lcf_plan_evd_phases": ([vp, dp], C.c_int),
         "lcf_plan_profile": ([vp, C.c_int], C.c_int),
         "lcf_plan_profile_read": ([vp, dp, ip], C.c_int),
         "lcf_plan_destroy": ([vp], C.c_int),
@@ -159,6 +163,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def evd_phases(self):
+        """Mean SM cycles per EVD phase of the last call made while profiling was on."""
+        cyc = np.zeros(len(EVD_PHASES))
+        _check(_lib.lcf_plan_evd_phases(self.handle, _p(cyc, C.c_double)), "lcf_plan_evd_phases")
+        return dict(zip(EVD_PHASES, cyc.tolist()))
 
     def launch_count(self) -> int:
         """Kernels this plan has launched since it was created."""

@@ -27,7 +27,7 @@
 
 namespace lcf {
 
-constexpr int EVD_THREADS = 512;
+constexpr int EVD_THREADS = 1024;
 constexpr float JACOBI_TOL = 2.0e-6f;
 constexpr int SUBSPACE_ITERS = 6;
 
@@ -38,7 +38,14 @@ struct EvdArgs {
   int k_fixed, k_src;
   int pd_mode, alpha_mode, curv_norm, max_sweeps;
   int ncp;
+  long long* clk;   // [nd][kEvdPhases + 1] phase-boundary SM clocks (stage profiling), or null
 };
+
+// thread 0 stamps the SM clock at phase boundary b (right after a block-wide barrier)
+#define EVD_STAMP(b)                                                  \
+  do {                                                                \
+    if (g.clk && tid == 0) g.clk[(size_t)k * (kEvdPhases + 1) + (b)] = clock64(); \
+  } while (0)
 
 size_t evd_smem_bytes(int nt) {
   int np = nt + (nt & 1);
@@ -168,6 +175,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     return;
   }
   const double inv = 1.0 / scale;
+  EVD_STAMP(0);
 
   // ---------------- phase A: subspace iteration on Rh = fp32(R/scale)
   for (int e = tid; e < np * np; e += EVD_THREADS) {
@@ -220,6 +228,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     __syncthreads();
   }
 
+  EVD_STAMP(1);
   // ---------------- phase B: Householder QR of Y (one warp); reflectors -> Zs
   if (warp == 0) {
     for (int j = 0; j < m; ++j) {
@@ -250,6 +259,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
   }
   __syncthreads();
 
+  EVD_STAMP(2);
   // ---------------- phase C: B = Q^H R Q in double-float (upper triangle)
   for (int e = tid; e < np * np; e += EVD_THREADS) {
     int a = e / np, b = e % np;
@@ -331,6 +341,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     __syncthreads();
   }
 
+  EVD_STAMP(3);
   // ---------------- convert B to fp32 A in place: entry e = a*np + b moves to a*ld + b,
   // which only overwrites df64 entries with index <= e, already read in this or an
   // earlier chunk
@@ -364,10 +375,12 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     __syncthreads();
   }
 
+  EVD_STAMP(4);
   // ---------------- phase D: cyclic Jacobi (round-robin), relative test
   // Work assignment is fixed for the whole solve: this thread's 2x2 blocks (ia <= ib of the
   // round's pair list) and its (pair, V row) items are decoded once.
-  constexpr int MAXB = 4, MAXV = 13;        // ceil(56*57/2/512), ceil(112*56/512)
+  constexpr int MAXB = (56 * 57 / 2 + EVD_THREADS - 1) / EVD_THREADS;   // upper-triangle 2x2 blocks
+  constexpr int MAXV = (112 * 56 + EVD_THREADS - 1) / EVD_THREADS;      // (pair, V row) items
   int blk[MAXB], vit[MAXV];
   {
     const int nblk = h * (h + 1) / 2;
@@ -464,6 +477,8 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     if (!any) { converged = 1; break; }
   }
 
+  __syncthreads();
+  EVD_STAMP(5);
   // ---------------- phase E: sort, phase-fix, weights, projection weights
   for (int i = tid; i < n; i += EVD_THREADS) {
     float di = A[i * ld + i].x;
@@ -503,6 +518,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
   // thresholding rule (double precision, one thread)
   double* wts = reinterpret_cast<double*>(Rdf);  // scratch: A's storage is dead after the sort copy
   __syncthreads();
+  EVD_STAMP(6);
   if (tid == 0) {
     double* s0 = wts + np;          // scratch curves (A region no longer read)
     double* s1 = s0 + np;
@@ -555,6 +571,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
   }
   __syncthreads();
   const int nc = sh_flag;
+  EVD_STAMP(7);
   for (int i = tid; i < n; i += EVD_THREADS) {
     lam_out[(size_t)k * n + i] = lam_s[i];
     wt_out[(size_t)k * n + i] = (float)wts[i];
@@ -569,6 +586,8 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
     }
     W_out[(size_t)k * n * g.ncp + e] = v;
   }
+  __syncthreads();
+  EVD_STAMP(8);
 }
 
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st) {
@@ -578,6 +597,7 @@ cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st) {
   a.thresh_mode = c.thresh_mode; a.beta = c.beta; a.beta_src = c.beta_src;
   a.k_fixed = c.k_fixed; a.k_src = c.k_src; a.pd_mode = c.pd_mode; a.alpha_mode = c.alpha_mode;
   a.curv_norm = c.curv_norm; a.max_sweeps = c.max_sweeps; a.ncp = P->ncp;
+  a.clk = P->profiling ? P->ws.evd_clk : nullptr;
   size_t sm = evd_smem_bytes(P->nt);
   evd_kernel<<<P->nd, EVD_THREADS, sm, st>>>(P->ws.R, P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt,
                                              P->ws.kcut, P->ws.alpha, P->ws.flags, P->ws.W, P->ws.ncol);

@@ -1,0 +1,894 @@
+// k_evd_pair.cu — batched Hermitian EVD (Eq. 2), eigen-weights and projection
+// weights on a CTA pair per window (a thread-block cluster of two).
+//
+// Same numerical plan as the one-CTA kernel (k_evd.cu): FP32 subspace iteration
+// for the dominant (tissue) directions, Householder QR of that block, the
+// congruence B = Q^H R Q in double-float, cyclic Jacobi in FP32 with the
+// relative test, sort / phase fix / rule in double.  What changes is the
+// division of work and the data layout:
+//
+//  * CTA 0 owns A.  CTA 1 owns V.  A Jacobi step's rotations (c, s, p, q) go
+//    from CTA 0 into a 16-deep ring in CTA 1's shared memory (distributed
+//    shared memory stores + a remote mbarrier arrive per record); CTA 1
+//    applies them to V while CTA 0 already runs the next steps.  The V update
+//    (n x n/2 element pairs per step) was the larger half of a step.
+//  * The congruence uses the compact WY form Q = I - Vh T Vh^H:
+//      B = R - (Vh Z^H + Z Vh^H),   Z = (R Vh) T - 1/2 Vh (T^H (Vh^H R Vh) T),
+//    an identity for any T, so B is exactly Q^H R Q for the Q that seeds the
+//    eigenvectors; R is read from global memory twice, no n x n double-float
+//    copy is kept in shared memory.
+//  * The subspace block is stored column-major with an odd stride (the
+//    orthogonalisation's column walks are conflict-free) and its CGS2 runs on
+//    all warps; the thresholding rule runs on one warp (log10, gradients and
+//    curvature per lane, argmax by shuffles) in double precision.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "lcf_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lcf {
+
+constexpr int EP_THREADS = 512;
+constexpr int EP_RING = 16;                   // rotation records in flight between the CTAs
+constexpr float EP_TOL = 2.0e-6f;             // relative off-diagonal test
+constexpr int EP_SUBSPACE_ITERS = 6;
+constexpr unsigned long long EP_WAIT_NS = 2000000000ull;   // bound on every mbarrier wait (2 s)
+constexpr unsigned EP_REC_ROT = 1u << 16, EP_REC_END = 1u << 17;
+
+struct EpArgs {
+  int nt, nz, nx;
+  int thresh_mode;
+  double beta, beta_src;
+  int k_fixed, k_src;
+  int pd_mode, alpha_mode, curv_norm, max_sweeps;
+  int ncp;
+  int* err;
+  long long* clk;   // [nd][kEvdPhases + 1] phase-boundary SM clocks of CTA 0 (profiling), or null
+};
+
+#define EP_STAMP(b)                                                                  \
+  do {                                                                               \
+    if (g.clk && tid == 0) g.clk[(size_t)k * (kEvdPhases + 1) + (b)] = clock64();     \
+  } while (0)
+
+// ---- shared-memory layout (both CTAs get the larger of the two) ----
+struct EpLayout {
+  int np, ld, ldy, m, h;
+  size_t a, ys, zs, yd, zd, tm, w2, pr, prd, lam, perm, wts, s0, s1, s2, ebar, end_a;   // CTA 0
+  size_t vt, ring, vh, tv, vtm, fbar, rperm, rcoef, rkeep, phase, end_v;                 // CTA 1
+  size_t total;
+};
+
+__host__ __device__ inline size_t ep_align(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline EpLayout ep_layout(int n) {
+  EpLayout L;
+  L.np = n + (n & 1);
+  L.ld = L.np + 1;
+  L.ldy = L.np + 1;
+  L.m = n < kEvdHead ? n : kEvdHead;
+  L.h = L.np / 2;
+  size_t o = 0;
+  L.a = o;    o = ep_align(o + (size_t)L.np * L.ld * 8);      // A (phase A: R/scale in fp32)
+  L.ys = o;   o = ep_align(o + (size_t)L.m * L.ldy * 8);      // subspace block, column-major
+  L.zs = o;   o = ep_align(o + (size_t)L.m * L.ldy * 8);      // product block, then reflectors Vh
+  L.yd = o;   o = ep_align(o + (size_t)n * L.m * 16);         // R Vh (double-float, [a][j])
+  L.zd = o;   o = ep_align(o + (size_t)n * L.m * 16);         // Z
+  L.tm = o;   o = ep_align(o + (size_t)L.m * L.m * 8);        // T (fp32 complex)
+  L.w2 = o;   o = ep_align(o + (size_t)2 * L.m * L.m * 16);   // M T and T^H M T (double-float)
+  L.pr = o;   o = ep_align(o + (size_t)L.h * 16);             // rotation records
+  L.prd = o;  o = ep_align(o + (size_t)L.h * 8);              // new diagonal pair
+  L.lam = o;  o = ep_align(o + (size_t)L.np * 8);
+  L.perm = o; o = ep_align(o + (size_t)L.np * 4);
+  L.wts = o;  o = ep_align(o + (size_t)L.np * 8);
+  L.s0 = o;   o = ep_align(o + (size_t)L.np * 8);
+  L.s1 = o;   o = ep_align(o + (size_t)L.np * 8);
+  L.s2 = o;   o = ep_align(o + (size_t)L.np * 8);
+  L.ebar = o; o = ep_align(o + (size_t)EP_RING * 8);
+  L.end_a = o;
+  o = 0;
+  L.vt = o;    o = ep_align(o + (size_t)L.np * L.ld * 8);     // V^T (row c = column c of V)
+  L.ring = o;  o = ep_align(o + (size_t)EP_RING * L.h * 16);
+  L.vh = o;    o = ep_align(o + (size_t)L.m * L.ldy * 8);     // reflectors (received)
+  L.tv = o;    o = ep_align(o + (size_t)L.m * L.m * 8);       // T (received)
+  L.vtm = o;   o = ep_align(o + (size_t)n * L.m * 8);         // Vh T
+  L.fbar = o;  o = ep_align(o + (size_t)EP_RING * 8);
+  L.rperm = o; o = ep_align(o + (size_t)L.np * 4);            // sorted -> original index
+  L.rcoef = o; o = ep_align(o + (size_t)L.np * 4);            // wt * sqrt(alpha/Nt) per sorted index
+  L.rkeep = o; o = ep_align(o + (size_t)(L.np + 1) * 4);      // [0] = ncol, then kept sorted indices
+  L.phase = o; o = ep_align(o + (size_t)L.np * 8);
+  L.end_v = o;
+  L.total = (L.end_a > L.end_v ? L.end_a : L.end_v);
+  return L;
+}
+
+size_t evd_pair_smem_bytes(int nt) { return ep_layout(nt).total; }
+
+// ---- cluster primitives ----
+__device__ __forceinline__ uint32_t ep_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t ep_mapa(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void ep_st_remote_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void ep_arrive_remote(uint32_t bar_cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster_addr) : "memory");
+}
+// asynchronous 16-byte store into the partner's shared memory; completes 16 bytes of
+// the transaction count of the partner's mbarrier (no fence on the issuing thread)
+__device__ __forceinline__ void ep_st_async(uint32_t addr, float4 v, uint32_t bar_cluster_addr) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar_cluster_addr)
+               : "memory");
+}
+__device__ __forceinline__ void ep_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ep_smem(b)), "r"(bytes) : "memory");
+}
+// 1/sqrt(x) and 1/x: hardware approximation plus one Newton-Raphson step
+__device__ __forceinline__ float ep_rsqrt(float x) {
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+__device__ __forceinline__ float ep_rcp(float x) {
+  const float r = __fdividef(1.f, x);
+  return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+__device__ __forceinline__ void ep_bar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ep_smem(b)), "r"(count));
+}
+// Wait with acquire at cluster scope (the arrivals come from the partner CTA),
+// for at most EP_WAIT_NS of wall time; false if the limit ran out.
+__device__ __forceinline__ bool ep_try(uint64_t* b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred q;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 q, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(done)
+      : "r"(ep_smem(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ uint64_t ep_now() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool ep_wait(uint64_t* b, uint32_t parity) {
+  if (ep_try(b, parity)) return true;
+  const uint64_t t0 = ep_now();
+  for (;;) {
+    if (ep_try(b, parity)) return true;
+    if (ep_now() - t0 > EP_WAIT_NS) return false;
+  }
+}
+
+// ---- warp-parallel thresholding rules (double precision, warp 0) ----
+// Same arithmetic per element as the one-thread rule; reductions by shuffles.
+__device__ __forceinline__ double ep_floor(const double* lam, int n, int i) {
+  const double fl = lam[0] * n * 2.220446049250313e-16;
+  return lam[i] > fl ? lam[i] : fl;
+}
+__device__ void ep_norm_log(const double* lam, int n, double beta, int literal, double* y, int lane) {
+  for (int i = lane; i < n; i += 32) y[i] = log10(ep_floor(lam, n, i));
+  __syncwarp();
+  const double y1 = y[0], yn = y[n - 1], span = y1 - yn;
+  double v[4];
+  int c = 0;
+  for (int i = lane; i < n; i += 32, ++c) {
+    if (literal) v[c] = (y1 != 0.0) ? beta * y[i] / y1 * n : 0.0;
+    else v[c] = (span > 0) ? beta * n * (y[i] - yn) / span : 0.0;
+  }
+  __syncwarp();
+  c = 0;
+  for (int i = lane; i < n; i += 32, ++c) y[i] = v[c];
+  __syncwarp();
+}
+__device__ void ep_grad(const double* y, double* d, int n, int lane) {
+  for (int i = lane; i < n; i += 32) {
+    if (n == 1) d[i] = 0.0;
+    else if (i == 0) d[i] = y[1] - y[0];
+    else if (i == n - 1) d[i] = y[n - 1] - y[n - 2];
+    else d[i] = 0.5 * (y[i + 1] - y[i - 1]);
+  }
+  __syncwarp();
+}
+// k of a hard rule (FIXED, CURVATURE, SLOPE, MEDIAN); all lanes return it
+__device__ int ep_rule_k(int mode, const double* lam, int n, double beta, int k_fixed, int literal, double* s0,
+                         double* s1, double* s2, int lane) {
+  switch (mode) {
+    case LCF_T_FIXED: return k_fixed < 0 ? 0 : (k_fixed > n ? n : k_fixed);
+    case LCF_T_CURVATURE: {
+      if (n < 3) return 0;
+      ep_norm_log(lam, n, beta, literal, s0, lane);
+      ep_grad(s0, s1, n, lane);
+      ep_grad(s1, s2, n, lane);
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = 1 + lane; i < n - 1; i += 32) {
+        const double q = 1.0 + s1[i] * s1[i];
+        const double kap = fabs(s2[i]) / (q * sqrt(q));
+        if (kap > best) { best = kap; bi = i; }
+      }
+      for (int o = 16; o; o >>= 1) {   // max, ties to the smallest index (first maximum)
+        const double ob = __shfl_xor_sync(~0u, best, o);
+        const int oi = __shfl_xor_sync(~0u, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      return bi == 0x7fffffff ? 2 : bi + 1;
+    }
+    case LCF_T_SLOPE: {
+      if (n < 2) return 0;
+      ep_norm_log(lam, n, 1.0, literal, s0, lane);
+      ep_grad(s0, s1, n, lane);
+      int first = n - 1;
+      for (int i = lane; i < n; i += 32)
+        if (-s1[i] <= beta && i < first) first = i;
+      for (int o = 16; o; o >>= 1) first = min(first, __shfl_xor_sync(~0u, first, o));
+      return first;
+    }
+    case LCF_T_MEDIAN: {
+      const double med = (n & 1) ? lam[n / 2] : 0.5 * (lam[n / 2 - 1] + lam[n / 2]);
+      const double T = beta * med;
+      int cnt = 0;
+      for (int i = lane; i < n; i += 32) cnt += lam[i] > T;
+      for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(~0u, cnt, o);
+      return cnt;
+    }
+    default: return 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EP_THREADS, 1)
+evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EpArgs g,
+                double* __restrict__ lam_out, float2* __restrict__ V_out, float* __restrict__ wt_out,
+                int* __restrict__ kcut_out, float* __restrict__ alpha_out, int* __restrict__ flags_out,
+                float2* __restrict__ W_out, int* __restrict__ ncol_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int k = blockIdx.x >> 1, n = g.nt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const EpLayout L = ep_layout(n);
+  const int np = L.np, ld = L.ld, ldy = L.ldy, m = L.m, h = L.h;
+  const double2* R = Rg + (size_t)k * n * n;
+  __shared__ double sh_scale;
+  __shared__ int sh_ok[2];
+
+  // ---------------- power-of-two scale (max diagonal) and degenerate check, both CTAs
+  if (warp == 0) {
+    double mx = 0.0;
+    for (int i = lane; i < n; i += 32) mx = fmax(mx, R[(size_t)i * n + i].x);
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(~0u, mx, o));
+    if (lane == 0) sh_scale = mx;
+  }
+  __syncthreads();
+  const double dmax = sh_scale;
+  if (!(dmax > 0.0) || !isfinite(dmax)) {
+    if (rank == 0) {
+      for (int i = tid; i < n; i += EP_THREADS) {
+        lam_out[(size_t)k * n + i] = 0.0;
+        wt_out[(size_t)k * n + i] = 0.f;
+      }
+      if (tid == 0) {
+        kcut_out[k] = 0; alpha_out[k] = 0.f; ncol_out[k] = 0;
+        flags_out[k] = LCF_WFLAG_DEGENERATE;
+      }
+    } else {
+      for (int e = tid; e < n * n; e += EP_THREADS) V_out[(size_t)k * n * n + e] = make_float2(e / n == e % n, 0.f);
+      for (int e = tid; e < n * g.ncp; e += EP_THREADS) W_out[(size_t)k * n * g.ncp + e] = make_float2(0.f, 0.f);
+    }
+    return;   // both CTAs leave before any cluster-level exchange
+  }
+  int ex;
+  frexp(dmax, &ex);
+  const double scale = ldexp(1.0, ex);            // R / scale is exact; its max diagonal is in [1/2, 1)
+  const float s_lo = ldexpf(1.f, -ex);            // the same factor for the double-float words
+
+  uint64_t* ebar = reinterpret_cast<uint64_t*>(smem + L.ebar);   // CTA 0: ring slots free
+  uint64_t* fbar = reinterpret_cast<uint64_t*>(smem + L.fbar);   // CTA 1: ring slots full
+  if (tid == 0) {
+    if (rank == 0)
+      for (int i = 0; i < EP_RING; ++i) ep_bar_init(&ebar[i], 1);
+    else
+      for (int i = 0; i < EP_RING; ++i) ep_bar_init(&fbar[i], 1);   // CTA 1's own expect_tx arrive
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster.sync();   // #0: barriers of both CTAs initialised
+  const uint32_t peer = (uint32_t)(rank ^ 1);
+  bool ok = true;
+
+  if (rank == 0) {
+    // =====================================================================
+    // CTA 0: subspace, QR, congruence, Jacobi on A, sort and rule
+    // =====================================================================
+    float2* Rh = reinterpret_cast<float2*>(smem + L.a);    // phase A (np x np)
+    float2* A = reinterpret_cast<float2*>(smem + L.a);     // phase D (np x ld)
+    float2* Ys = reinterpret_cast<float2*>(smem + L.ys);   // [j][a], stride ldy
+    float2* Zs = reinterpret_cast<float2*>(smem + L.zs);
+    zdf* Yd = reinterpret_cast<zdf*>(smem + L.yd);          // [a][j]
+    zdf* Zd = reinterpret_cast<zdf*>(smem + L.zd);
+    float2* Tm = reinterpret_cast<float2*>(smem + L.tm);   // [i][j]
+    zdf* MT = reinterpret_cast<zdf*>(smem + L.w2);          // M T
+    zdf* W2 = MT + m * m;                                   // T^H M T
+    float4* pr = reinterpret_cast<float4*>(smem + L.pr);
+    float2* prd = reinterpret_cast<float2*>(smem + L.prd);
+    double* lam_s = reinterpret_cast<double*>(smem + L.lam);
+    int* perm = reinterpret_cast<int*>(smem + L.perm);
+    double* wts = reinterpret_cast<double*>(smem + L.wts);
+    double* s0 = reinterpret_cast<double*>(smem + L.s0);
+    double* s1 = reinterpret_cast<double*>(smem + L.s1);
+    double* s2 = reinterpret_cast<double*>(smem + L.s2);
+    __shared__ float betas[kEvdHead];
+    __shared__ float2 us[kEvdHead];
+
+    EP_STAMP(0);
+    // ---------------- phase A: subspace iteration on fp32(R / scale)
+    const float inv_s = (float)(1.0 / scale);
+    for (int e = tid; e < np * np; e += EP_THREADS) {
+      const int a = e / np, b = e % np;
+      float2 v = make_float2(0.f, 0.f);
+      if (a < n && b < n) {
+        const double2 r = R[(size_t)a * n + b];
+        v = make_float2((float)r.x * inv_s, (float)r.y * inv_s);
+      }
+      Rh[e] = v;
+    }
+    for (int e = tid; e < m * ldy; e += EP_THREADS) {
+      const int j = e / ldy, a = e % ldy;
+      unsigned hsh = (unsigned)(a * 2654435761u) ^ (unsigned)(j * 40503u + 7u);
+      hsh ^= hsh >> 13; hsh *= 0x5bd1e995u; hsh ^= hsh >> 15;
+      const float re = (float)(hsh & 0xffff) / 65536.f - 0.5f, im = (float)(hsh >> 16) / 65536.f - 0.5f;
+      Ys[e] = (a < n) ? make_float2(re, im) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    __shared__ float2 cs[kEvdHead];
+    __shared__ float sh_nrm;
+    for (int it = 0; it < EP_SUBSPACE_ITERS; ++it) {
+      for (int e = tid; e < n * m; e += EP_THREADS) {   // Z = Rh Y (8 lanes share a row of Rh)
+        const int a = e / m, j = e % m;
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* rr = Rh + (size_t)a * np;
+        const float2* yy = Ys + (size_t)j * ldy;
+        for (int b = 0; b < n; ++b) {
+          const float2 r = rr[b], y = yy[b];
+          acc.x = fmaf(r.x, y.x, fmaf(-r.y, y.y, acc.x));
+          acc.y = fmaf(r.x, y.y, fmaf(r.y, y.x, acc.y));
+        }
+        Zs[(size_t)j * ldy + a] = acc;
+      }
+      __syncthreads();
+      // CGS2 of Z's columns into Y: dots on warps 0..j-1, updates on all threads
+      for (int j = 0; j < m; ++j) {
+        float2* zj = Zs + (size_t)j * ldy;
+        for (int pass = 0; pass < 2 && j > 0; ++pass) {
+          if (warp < j) {
+            const float2* yw = Ys + (size_t)warp * ldy;
+            float2 c = make_float2(0.f, 0.f);
+            for (int a = lane; a < n; a += 32) c = cadd(c, cmulc(yw[a], zj[a]));
+            for (int o = 16; o; o >>= 1) { c.x += __shfl_xor_sync(~0u, c.x, o); c.y += __shfl_xor_sync(~0u, c.y, o); }
+            if (lane == 0) cs[warp] = c;
+          }
+          __syncthreads();
+          for (int a = tid; a < n; a += EP_THREADS) {
+            float2 z = zj[a];
+            for (int i = 0; i < j; ++i) z = csub(z, cmul(cs[i], Ys[(size_t)i * ldy + a]));
+            zj[a] = z;
+          }
+          __syncthreads();
+        }
+        if (warp == 0) {
+          float nr = 0.f;
+          for (int a = lane; a < n; a += 32) nr += cabs2(zj[a]);
+          for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
+          if (lane == 0) sh_nrm = nr;
+        }
+        __syncthreads();
+        const float nr = sh_nrm;
+        if (nr > 0.f) {   // a vanishing direction keeps its previous (orthonormal) vector
+          const float sc = rsqrtf(nr);
+          for (int a = tid; a < n; a += EP_THREADS) Ys[(size_t)j * ldy + a] = cscale(zj[a], sc);
+        }
+        __syncthreads();
+      }
+    }
+
+    EP_STAMP(1);
+    // ---------------- phase B: Householder QR of Y by warp 0 (reflectors -> Zs), then T
+    if (warp == 0) {
+      for (int j = 0; j < m; ++j) {
+        float2* yj = Ys + (size_t)j * ldy;
+        float nr = 0.f;
+        for (int a = j + lane; a < n; a += 32) nr += cabs2(yj[a]);
+        for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
+        const float alpha = sqrtf(nr);
+        const float2 x0 = yj[j];
+        const float ax0 = sqrtf(cabs2(x0));
+        const float2 e = ax0 > 0.f ? cscale(x0, 1.f / ax0) : make_float2(1.f, 0.f);
+        const float beta = alpha > 0.f ? 1.f / (alpha * (alpha + ax0)) : 0.f;
+        float2* vj = Zs + (size_t)j * ldy;
+        for (int a = lane; a < ldy; a += 32) {
+          float2 v = (a < j || a >= n) ? make_float2(0.f, 0.f) : yj[a];
+          if (a == j) v = cadd(x0, cscale(e, alpha));
+          vj[a] = v;
+        }
+        if (lane == 0) betas[j] = beta;
+        __syncwarp();
+        for (int c = j + 1; c < m; ++c) {
+          float2* yc = Ys + (size_t)c * ldy;
+          float2 t = make_float2(0.f, 0.f);
+          for (int a = j + lane; a < n; a += 32) t = cadd(t, cmulc(vj[a], yc[a]));
+          for (int o = 16; o; o >>= 1) { t.x += __shfl_xor_sync(~0u, t.x, o); t.y += __shfl_xor_sync(~0u, t.y, o); }
+          t = cscale(t, beta);
+          for (int a = j + lane; a < n; a += 32) yc[a] = csub(yc[a], cmul(vj[a], t));
+          __syncwarp();
+        }
+      }
+      // compact WY: H_0 ... H_{m-1} = I - Vh T Vh^H with T upper triangular,
+      // T[j][j] = beta_j, T[0:j, j] = -beta_j T[0:j, 0:j] (Vh[:, 0:j]^H v_j)
+      for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < j; ++i) {
+          float2 c = make_float2(0.f, 0.f);
+          for (int a = lane; a < n; a += 32) c = cadd(c, cmulc(Zs[(size_t)i * ldy + a], Zs[(size_t)j * ldy + a]));
+          for (int o = 16; o; o >>= 1) { c.x += __shfl_xor_sync(~0u, c.x, o); c.y += __shfl_xor_sync(~0u, c.y, o); }
+          if (lane == 0) us[i] = c;
+        }
+        __syncwarp();
+        if (lane < j) {
+          float2 acc = make_float2(0.f, 0.f);
+          for (int l = lane; l < j; ++l) acc = cadd(acc, cmul(Tm[lane * m + l], us[l]));
+          Tm[lane * m + j] = cscale(acc, -betas[j]);
+        }
+        if (lane == 0) {
+          Tm[j * m + j] = make_float2(betas[j], 0.f);
+          for (int i = j + 1; i < m; ++i) Tm[i * m + j] = make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // send Vh (m x ldy, column-major) and T to CTA 1
+    {
+      const uint32_t vh_r = ep_mapa(ep_smem(smem + L.vh), peer), tv_r = ep_mapa(ep_smem(smem + L.tv), peer);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(Zs);
+      for (int e = tid; e < 2 * m * ldy; e += EP_THREADS) ep_st_remote_u32(vh_r + 4u * e, src[e]);
+      const uint32_t* ts = reinterpret_cast<const uint32_t*>(Tm);
+      for (int e = tid; e < 2 * m * m; e += EP_THREADS) ep_st_remote_u32(tv_r + 4u * e, ts[e]);
+    }
+    cluster.sync();   // #1: CTA 1 may build Q
+    EP_STAMP(2);
+
+    // ---------------- phase C: B = Q^H R Q = R - (Vh Z^H + Z Vh^H) in double-float
+    // Yd = (R / scale) Vh : 4 threads per row, each a quarter of the columns b, 8 outputs
+    {
+      const int a = tid >> 2, sub = tid & 3;
+      zdf acc[kEvdHead];
+#pragma unroll
+      for (int j = 0; j < kEvdHead; ++j) acc[j] = {{0.f, 0.f}, {0.f, 0.f}};
+      if (a < n) {
+        for (int b = sub; b < n; b += 4) {
+          const double2 r = R[(size_t)a * n + b];
+          zdf rz;
+          rz.re = df_from_double(r.x); rz.im = df_from_double(r.y);
+          rz.re.hi *= s_lo; rz.re.lo *= s_lo; rz.im.hi *= s_lo; rz.im.lo *= s_lo;
+#pragma unroll
+          for (int j = 0; j < kEvdHead; ++j)
+            if (j < m) acc[j] = zdf_add(acc[j], zdf_mul_c(rz, Zs[(size_t)j * ldy + b]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kEvdHead; ++j) {
+        zdf v = acc[j];
+        for (int o = 1; o < 4; o <<= 1) {
+          zdf t;
+          t.re.hi = __shfl_xor_sync(~0u, v.re.hi, o); t.re.lo = __shfl_xor_sync(~0u, v.re.lo, o);
+          t.im.hi = __shfl_xor_sync(~0u, v.im.hi, o); t.im.lo = __shfl_xor_sync(~0u, v.im.lo, o);
+          v = zdf_add(v, t);
+        }
+        if (sub == 0 && a < n && j < m) Yd[a * m + j] = v;
+      }
+    }
+    __syncthreads();
+    // M = Vh^H Yd (m x m): warp w -> entries w, w + 16, ...
+    zdf* Mm = Zd;   // Zd is free until Z is formed; M needs m*m <= n*m entries
+    for (int q = warp; q < m * m; q += EP_THREADS / 32) {
+      const int i = q / m, j = q % m;
+      zdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int a = lane; a < n; a += 32) acc = zdf_add(acc, zdf_mul_c(Yd[a * m + j], cconj(Zs[(size_t)i * ldy + a])));
+      for (int o = 16; o; o >>= 1) {
+        zdf t;
+        t.re.hi = __shfl_xor_sync(~0u, acc.re.hi, o); t.re.lo = __shfl_xor_sync(~0u, acc.re.lo, o);
+        t.im.hi = __shfl_xor_sync(~0u, acc.im.hi, o); t.im.lo = __shfl_xor_sync(~0u, acc.im.lo, o);
+        acc = zdf_add(acc, t);
+      }
+      if (lane == 0) Mm[q] = acc;
+    }
+    __syncthreads();
+    if (tid < m * m) {   // MT = M T
+      const int i = tid / m, j = tid % m;
+      zdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int l = 0; l <= j; ++l) acc = zdf_add(acc, zdf_mul_c(Mm[i * m + l], Tm[l * m + j]));
+      MT[tid] = acc;
+    }
+    __syncthreads();
+    if (tid < m * m) {   // W2 = T^H (M T)
+      const int i = tid / m, j = tid % m;
+      zdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int l = 0; l <= i; ++l) acc = zdf_add(acc, zdf_mul_c(MT[l * m + j], cconj(Tm[l * m + i])));
+      W2[tid] = acc;
+    }
+    __syncthreads();
+    // Z = Yd T - 1/2 Vh W2   (n x m)
+    for (int e = tid; e < n * m; e += EP_THREADS) {
+      const int a = e / m, j = e % m;
+      zdf acc = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int l = 0; l <= j; ++l) acc = zdf_add(acc, zdf_mul_c(Yd[a * m + l], Tm[l * m + j]));
+      zdf c2 = {{0.f, 0.f}, {0.f, 0.f}};
+      for (int l = 0; l < m; ++l) c2 = zdf_add(c2, zdf_mul_c(W2[l * m + j], Zs[(size_t)l * ldy + a]));
+      c2.re.hi *= 0.5f; c2.re.lo *= 0.5f; c2.im.hi *= 0.5f; c2.im.lo *= 0.5f;
+      acc.re = df_add(acc.re, df_neg(c2.re));
+      acc.im = df_add(acc.im, df_neg(c2.im));
+      Zd[e] = acc;
+    }
+    __syncthreads();
+    // B upper triangle -> fp32 A (mirrored, real diagonal)
+    for (int e = tid; e < np * np; e += EP_THREADS) {
+      const int a = e / np, b = e % np;
+      if (a > b) continue;
+      float2 v = make_float2(0.f, 0.f);
+      if (b < n) {
+        const double2 r = R[(size_t)a * n + b];
+        zdf x;
+        x.re = df_from_double(r.x); x.im = df_from_double(r.y);
+        x.re.hi *= s_lo; x.re.lo *= s_lo; x.im.hi *= s_lo; x.im.lo *= s_lo;
+        zdf c = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int j = 0; j < m; ++j) {
+          // Vh_aj conj(Z_bj) + Z_aj conj(Vh_bj)
+          zdf zb = Zd[b * m + j];
+          zb.im = df_neg(zb.im);
+          c = zdf_add(c, zdf_mul_c(zb, Zs[(size_t)j * ldy + a]));
+          c = zdf_add(c, zdf_mul_c(Zd[a * m + j], cconj(Zs[(size_t)j * ldy + b])));
+        }
+        x.re = df_add(x.re, df_neg(c.re));
+        x.im = df_add(x.im, df_neg(c.im));
+        v = make_float2(x.re.hi + x.re.lo, a == b ? 0.f : x.im.hi + x.im.lo);
+      }
+      A[a * ld + b] = v;
+      if (a != b) A[b * ld + a] = cconj(v);
+    }
+    __syncthreads();
+
+    EP_STAMP(3);
+    EP_STAMP(4);
+    // ---------------- phase D: cyclic Jacobi on A; rotations streamed to CTA 1
+    constexpr int MAXB = (56 * 57 / 2 + EP_THREADS - 1) / EP_THREADS;
+    int blk[MAXB];
+    {
+      const int nblk = h * (h + 1) / 2;
+      for (int j = 0; j < MAXB; ++j) {
+        const int e = tid + j * EP_THREADS;
+        int code = -1;
+        if (e < nblk) {
+          int ia = 0, rem = e;
+          while (rem >= h - ia) { rem -= h - ia; ++ia; }
+          code = (ia << 8) | (ia + rem);
+        }
+        blk[j] = code;
+      }
+    }
+    const uint32_t ring_r = ep_mapa(ep_smem(reinterpret_cast<unsigned char*>(smem) + L.ring), peer);
+    const uint32_t fbar_r = ep_mapa(ep_smem(reinterpret_cast<unsigned char*>(smem) + L.fbar), peer);
+    int sweeps = 0, converged = 0, hand = 0;
+    const int maxsw = g.max_sweeps > 0 ? g.max_sweeps : 40;
+    for (; sweeps < maxsw && ok; ++sweeps) {
+      int any = 0;
+      for (int r = 0; r < np - 1; ++r) {
+        const int slot = hand % EP_RING;
+        if (tid == 0) sh_ok[r & 1] = hand < EP_RING || ep_wait(&ebar[slot], ((hand / EP_RING) - 1) & 1);
+        int rot = 0;
+        float4 rec;
+        if (tid < h) {
+          const int i = tid;
+          int pa, pb;
+          if (i == 0) { pa = r; pb = np - 1; }
+          else { pa = (r + i) % (np - 1); pb = (r - i + np - 1) % (np - 1); }
+          const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
+          const float app = A[p * ld + p].x, aqq = A[q * ld + q].x;
+          const float2 b = A[p * ld + q];
+          const float b2 = cabs2(b);
+          float c = 1.f, dp = app, dq = aqq;
+          float2 st = make_float2(0.f, 0.f);
+          // rotate unless |b_pq| <= tol sqrt(|b_pp b_qq|)  (squared form)
+          if (b2 > 0.f && b2 > (EP_TOL * EP_TOL) * fabsf(app * aqq)) {
+            const float ib = ep_rsqrt(b2), ab = b2 * ib;         // 1/|b|, |b|
+            const float zeta = 0.5f * (aqq - app) * ib;
+            float t;
+            if (fabsf(zeta) > 1e18f) {
+              t = 0.5f * ep_rcp(zeta);
+            } else {
+              const float z2 = fmaf(zeta, zeta, 1.f);
+              t = copysignf(ep_rcp(fabsf(zeta) + z2 * ep_rsqrt(z2)), zeta);   // 1 / (|zeta| + sqrt(1 + zeta^2))
+            }
+            c = ep_rsqrt(fmaf(t, t, 1.f));
+            const float sib = t * c * ib;
+            st = make_float2(sib * b.x, sib * b.y);
+            dp = fmaf(-t, ab, app);
+            dq = fmaf(t, ab, aqq);
+            rot = 1;
+          }
+          rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)p | ((unsigned)q << 8) | (rot ? EP_REC_ROT : 0u)));
+          pr[i] = rec;
+          prd[i] = make_float2(dp, dq);
+        }
+        const int anyr = __syncthreads_or(rot);
+        if (!sh_ok[r & 1]) { ok = false; break; }   // the partner stopped consuming: give up
+        if (!anyr) continue;
+        any = 1;
+        if (tid < h) {   // hand the step's records to CTA 1
+          ep_st_async(ring_r + (uint32_t)((slot * h + tid) * 16), rec, fbar_r + (uint32_t)(slot * 8));
+        }
+        ++hand;
+#pragma unroll
+        for (int j = 0; j < MAXB; ++j) {
+          if (blk[j] < 0) continue;
+          const int ia = blk[j] >> 8, ib = blk[j] & 255;
+          const float4 ra = pr[ia], rb = pr[ib];
+          const unsigned ma = __float_as_uint(ra.w), mb = __float_as_uint(rb.w);
+          if (!((ma | mb) & EP_REC_ROT)) continue;
+          const int pa = ma & 255, qa = (ma >> 8) & 255, pb = mb & 255, qb = (mb >> 8) & 255;
+          if (ia == ib) {
+            const float2 d = prd[ia];
+            A[pa * ld + pa] = make_float2(d.x, 0.f);
+            A[qa * ld + qa] = make_float2(d.y, 0.f);
+            A[pa * ld + qa] = make_float2(0.f, 0.f);
+            A[qa * ld + pa] = make_float2(0.f, 0.f);
+            continue;
+          }
+          const float ca = ra.x, cb = rb.x;
+          const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
+          const float2 x00 = A[pa * ld + pb], x01 = A[pa * ld + qb], x10 = A[qa * ld + pb], x11 = A[qa * ld + qb];
+          const float2 sbc = cconj(sb);
+          const float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
+          const float2 y10 = csub(cscale(x10, cb), cmul(sbc, x11)), y11 = cadd(cmul(sb, x10), cscale(x11, cb));
+          const float2 sac = cconj(sa);
+          const float2 z00 = csub(cscale(y00, ca), cmul(sa, y10)), z01 = csub(cscale(y01, ca), cmul(sa, y11));
+          const float2 z10 = cadd(cmul(sac, y00), cscale(y10, ca)), z11 = cadd(cmul(sac, y01), cscale(y11, ca));
+          A[pa * ld + pb] = z00; A[pa * ld + qb] = z01; A[qa * ld + pb] = z10; A[qa * ld + qb] = z11;
+          A[pb * ld + pa] = cconj(z00); A[qb * ld + pa] = cconj(z01);
+          A[pb * ld + qa] = cconj(z10); A[qb * ld + qa] = cconj(z11);
+        }
+        __syncthreads();
+      }
+      ok = __syncthreads_and(ok);
+      if (!any) { converged = 1; break; }
+    }
+    // end-of-stream record
+    {
+      const int slot = hand % EP_RING;
+      if (tid == 0 && ok && hand >= EP_RING) ok = ep_wait(&ebar[slot], ((hand / EP_RING) - 1) & 1);
+      ok = __syncthreads_and(ok);
+      if (ok && tid < h) {
+        ep_st_async(ring_r + (uint32_t)((slot * h + tid) * 16), make_float4(0.f, 0.f, 0.f, __uint_as_float(EP_REC_END)),
+                    fbar_r + (uint32_t)(slot * 8));
+      }
+    }
+
+    EP_STAMP(5);
+    // ---------------- phase E (CTA 0): sort, rule, alpha; results to CTA 1
+    for (int i = tid; i < n; i += EP_THREADS) {
+      const float di = A[i * ld + i].x;
+      int rk = 0;
+      for (int j = 0; j < n; ++j) {
+        const float dj = A[j * ld + j].x;
+        rk += (dj > di) || (dj == di && j < i);
+      }
+      perm[rk] = i;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += EP_THREADS) lam_s[i] = (double)A[perm[i] * ld + perm[i]].x * scale;
+    __syncthreads();
+    EP_STAMP(6);
+    if (warp == 0) {
+      int kk = -1;
+      const int md = g.thresh_mode;
+      if (md == LCF_T_NONE) {
+        for (int i = lane; i < n; i += 32) wts[i] = 1.0;
+        kk = 0;
+      } else if (md <= LCF_T_MEDIAN) {
+        kk = ep_rule_k(md, lam_s, n, g.beta, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+        for (int i = lane; i < n; i += 32) wts[i] = (i + 1 > kk) ? 1.0 : 0.0;
+      } else if (md == LCF_T_SIGMOID) {
+        kk = ep_rule_k(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+        for (int i = lane; i < n; i += 32) wts[i] = 1.0 / (1.0 + exp(-g.beta * ((i + 1) - kk)));
+      } else {   // LCF_T_ADAPTIVE_SOFT
+        double mx = -INFINITY;
+        for (int i = lane; i < n; i += 32) {
+          const double u = n > 1 ? 2.5 * i / (n - 1) : 0.0;
+          wts[i] = -0.5 * u * u - g.beta * log(ep_floor(lam_s, n, i));
+          mx = fmax(mx, wts[i]);
+        }
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(~0u, mx, o));
+        for (int i = lane; i < n; i += 32) wts[i] = exp(wts[i] - mx);
+        kk = -1;
+      }
+      __syncwarp();
+      double S = 0.0;
+      for (int i = lane; i < n; i += 32) S += wts[i] * wts[i] * lam_s[i];
+      for (int o = 16; o; o >>= 1) S += __shfl_xor_sync(~0u, S, o);
+      if (lane == 0) {
+        const double pdsum = g.pd_mode == 0 ? S / n : S;
+        double al;
+        int fl = (converged ? 0 : LCF_WFLAG_NOCONV) | ((sweeps < 255 ? sweeps : 255) << LCF_WFLAG_SWEEP_SHIFT);
+        if (g.alpha_mode == 1) al = 1.0;
+        else {
+          const Box bx = boxes[k];
+          const double cnt = g.alpha_mode == 2 ? (double)(bx.z1 - bx.z0) * (bx.x1 - bx.x0) : (double)g.nz * g.nx;
+          if (pdsum <= 1e-300) { al = 0.0; fl |= LCF_WFLAG_DEGENERATE; }
+          else al = cnt / pdsum;
+        }
+        kcut_out[k] = kk;
+        alpha_out[k] = (float)al;
+        flags_out[k] = fl;
+        s0[0] = sqrt(al * (g.pd_mode == 0 ? 1.0 / n : 1.0));
+      }
+      __syncwarp();
+      // kept columns in sorted order (ballot prefix)
+      const double cf = s0[0];
+      int base = 0;
+      const uint32_t rk_r = ep_mapa(ep_smem(smem + L.rkeep), peer);
+      const uint32_t rc_r = ep_mapa(ep_smem(smem + L.rcoef), peer);
+      for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool keep = i < n && wts[i] > 0.0;
+        const unsigned bal = __ballot_sync(~0u, keep);
+        if (keep) ep_st_remote_u32(rk_r + 4u * (1 + base + __popc(bal & ((1u << lane) - 1u))), (uint32_t)i);
+        if (i < n) ep_st_remote_u32(rc_r + 4u * i, __float_as_uint((float)(wts[i] * cf)));
+        base += __popc(bal);
+      }
+      if (lane == 0) {
+        ep_st_remote_u32(rk_r, (uint32_t)base);
+        ncol_out[k] = base;
+      }
+    }
+    {
+      const uint32_t rp_r = ep_mapa(ep_smem(smem + L.rperm), peer);
+      for (int i = tid; i < n; i += EP_THREADS) ep_st_remote_u32(rp_r + 4u * i, (uint32_t)perm[i]);
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += EP_THREADS) {
+      lam_out[(size_t)k * n + i] = lam_s[i];
+      wt_out[(size_t)k * n + i] = (float)wts[i];
+    }
+    if (!ok && tid == 0) atomicOr(g.err, 1);
+    __syncthreads();
+    EP_STAMP(7);
+    cluster.sync();   // #2: sorted order, coefficients and kept list are in CTA 1
+    EP_STAMP(8);
+  } else {
+    // =====================================================================
+    // CTA 1: V = Q, the streamed rotations, phase fix, V and W out
+    // =====================================================================
+    float2* Vt = reinterpret_cast<float2*>(smem + L.vt);
+    const float4* ring = reinterpret_cast<const float4*>(smem + L.ring);
+    const float2* Vh = reinterpret_cast<const float2*>(smem + L.vh);
+    const float2* Tv = reinterpret_cast<const float2*>(smem + L.tv);
+    float2* VT = reinterpret_cast<float2*>(smem + L.vtm);
+    cluster.sync();   // #1: reflectors and T have arrived
+    for (int e = tid; e < n * m; e += EP_THREADS) {   // VT = Vh T   ([a][j])
+      const int a = e / m, j = e % m;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int l = 0; l <= j; ++l) acc = cadd(acc, cmul(Vh[(size_t)l * ldy + a], Tv[l * m + j]));
+      VT[e] = acc;
+    }
+    __syncthreads();
+    // Vt[c][a] = Q[a][c] = delta_ac - sum_j VT[a][j] conj(Vh[c][j])
+    for (int e = tid; e < np * ld; e += EP_THREADS) {
+      const int c = e / ld, a = e % ld;
+      float2 v = make_float2(c == a ? 1.f : 0.f, 0.f);
+      if (a < n && c < n)
+        for (int j = 0; j < m; ++j) v = csub(v, cmul(VT[a * m + j], cconj(Vh[(size_t)j * ldy + c])));
+      Vt[e] = v;
+    }
+    __syncthreads();
+    // work items: (pair, V row), rows consecutive across lanes
+    constexpr int MAXV = (kEvdNmax * (kEvdNmax / 2) + EP_THREADS - 1) / EP_THREADS;
+    int vit[MAXV];
+    for (int j = 0; j < MAXV; ++j) {
+      const int e = tid + j * EP_THREADS;
+      vit[j] = (e < n * h) ? (((e / n) << 8) | (e % n)) : -1;
+    }
+    const uint32_t ebar_r = ep_mapa(ep_smem(smem + L.ebar), peer);
+    for (int hs = 0;; ++hs) {
+      const int slot = hs % EP_RING;
+      if (tid == 0) ep_arrive_expect_tx(&fbar[slot], (uint32_t)(h * 16));   // the step's h records
+      ok = __syncthreads_and(ep_wait(&fbar[slot], (hs / EP_RING) & 1));
+      if (!ok) break;
+      const float4* rs = ring + (size_t)slot * h;
+      if (__float_as_uint(rs[0].w) & EP_REC_END) break;
+#pragma unroll
+      for (int j = 0; j < MAXV; ++j) {
+        if (vit[j] < 0) continue;
+        const int ia = vit[j] >> 8, rr = vit[j] & 255;
+        const float4 rc = rs[ia];
+        const unsigned mt = __float_as_uint(rc.w);
+        if (!(mt & EP_REC_ROT)) continue;
+        const int p = mt & 255, q = (mt >> 8) & 255;
+        const float c = rc.x;
+        const float2 s = make_float2(rc.y, rc.z);
+        const float2 vp = Vt[p * ld + rr], vq = Vt[q * ld + rr];
+        Vt[p * ld + rr] = csub(cscale(vp, c), cmul(cconj(s), vq));
+        Vt[q * ld + rr] = cadd(cmul(s, vp), cscale(vq, c));
+      }
+      __syncthreads();
+      if (tid == 0) ep_arrive_remote(ebar_r + (uint32_t)(slot * 8));
+    }
+    if (!ok && tid == 0) atomicOr(g.err, 1);
+    cluster.sync();   // #2: sorted order and coefficients from CTA 0
+    const int* rperm = reinterpret_cast<const int*>(smem + L.rperm);
+    const float* rcoef = reinterpret_cast<const float*>(smem + L.rcoef);
+    const int* rkeep = reinterpret_cast<const int*>(smem + L.rkeep);
+    float2* phs = reinterpret_cast<float2*>(smem + L.phase);
+    // phase of each sorted eigenvector: largest-magnitude entry made real positive
+    for (int jj = warp; jj < n; jj += EP_THREADS / 32) {
+      const int col = rperm[jj];
+      float best = -1.f;
+      int bi = 0;
+      for (int a = lane; a < n; a += 32) {
+        const float mg = cabs2(Vt[col * ld + a]);
+        if (mg > best) { best = mg; bi = a; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const float ob = __shfl_xor_sync(~0u, best, o);
+        const int oi = __shfl_xor_sync(~0u, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        const float2 v = Vt[col * ld + bi];
+        const float mg = sqrtf(cabs2(v));
+        phs[jj] = mg > 0.f ? make_float2(v.x / mg, -v.y / mg) : make_float2(1.f, 0.f);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += EP_THREADS) {
+      const int a = e / n, jj = e % n;
+      V_out[(size_t)k * n * n + e] = cmul(Vt[rperm[jj] * ld + a], phs[jj]);
+    }
+    const int nc = rkeep[0];
+    for (int e = tid; e < n * g.ncp; e += EP_THREADS) {
+      const int t = e / g.ncp, c = e % g.ncp;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < nc) {
+        const int jj = rkeep[1 + c];
+        v = cscale(cmul(Vt[rperm[jj] * ld + t], phs[jj]), rcoef[jj]);
+      }
+      W_out[(size_t)k * n * g.ncp + e] = v;
+    }
+  }
+}
+
+cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st) {
+  EpArgs a;
+  const lcf_config& c = P->cfg;
+  a.nt = P->nt; a.nz = c.nz; a.nx = c.nx;
+  a.thresh_mode = c.thresh_mode; a.beta = c.beta; a.beta_src = c.beta_src;
+  a.k_fixed = c.k_fixed; a.k_src = c.k_src; a.pd_mode = c.pd_mode; a.alpha_mode = c.alpha_mode;
+  a.curv_norm = c.curv_norm; a.max_sweeps = c.max_sweeps; a.ncp = P->ncp;
+  a.err = P->ws.err;
+  a.clk = P->profiling ? P->ws.evd_clk : nullptr;
+  evd_pair_kernel<<<2 * P->nd, EP_THREADS, evd_pair_smem_bytes(P->nt), st>>>(
+      P->ws.R, P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt, P->ws.kcut, P->ws.alpha, P->ws.flags, P->ws.W,
+      P->ws.ncol);
+  return counted(P);
+}
+
+cudaError_t evd_pair_configure() {
+  return cudaFuncSetAttribute(evd_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)evd_pair_smem_bytes(kEvdNmax));
+}
+
+}  // namespace lcf

@@ -98,7 +98,7 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
   bool ok = true;
 
   auto epilogue = [&](int c) {
-    ok &= tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);
+    if (ok) ok = tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);   // after a timeout, no further waits
     tc::fence_after();
     const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
 #pragma unroll
@@ -117,7 +117,7 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
     const int si = i % TG_STAGES;
     unsigned char* Bhi = smem + si * st_bytes;
     unsigned char* Blo = Bhi + hi_bytes;
-    if (i >= TG_STAGES) ok &= tc::mbar_wait(&mma_bar[si], ((i / TG_STAGES) - 1) & 1);
+    if (i >= TG_STAGES && ok) ok = tc::mbar_wait(&mma_bar[si], ((i / TG_STAGES) - 1) & 1);
     if (tid < TG_PX) {
       long l = l0 + (long)i * TG_PX + tid;
       int p = 0;

@@ -208,7 +208,7 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
       // the copies still in flight land before the CTA exits
       for (int r = 1; r <= PT_STAGES && r <= q; ++r) {
         const int qq = q - r;
-        tc::mbar_wait(&full_bar[qq % PT_STAGES], (qq / PT_STAGES) & 1, 20000000L);
+        tc::mbar_wait(&full_bar[qq % PT_STAGES], (qq / PT_STAGES) & 1, 200000000ull);
       }
     }
   } else if (warp == 1) {
@@ -267,7 +267,7 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
         ++j;
       }
       // every MMA this thread issued has completed before TMEM is released
-      if (j > 0) tc::mbar_wait(&accf[(j - 1) & 1], ((j - 1) >> 1) & 1, 20000000L);
+      if (j > 0) tc::mbar_wait(&accf[(j - 1) & 1], ((j - 1) >> 1) & 1, 200000000ull);
     }
   } else if (warp >= 4) {
     // ---------------- epilogue: |Y|^2 row sums, window weights, blend ----------------

@@ -46,6 +46,7 @@ extern "C" lcf_status lcf_config_default(lcf_config* c, int nz, int nx, int nt, 
   c->gram_path = LCF_PATH_SIMT;
   c->project_path = LCF_PATH_SIMT;
   c->max_sweeps = 40;
+  c->evd_path = LCF_EVD_CTA;
   return LCF_OK;
 }
 
@@ -61,6 +62,7 @@ static lcf_status validate(const lcf_config* c) {
   if (c->curv_norm < 0 || c->curv_norm > 1) return LCF_EINVAL;
   if (c->gram_path < LCF_PATH_SIMT || c->gram_path > LCF_PATH_TC) return LCF_EINVAL;
   if (c->project_path < LCF_PATH_SIMT || c->project_path > LCF_PATH_TC) return LCF_EINVAL;
+  if (c->evd_path < LCF_EVD_CTA || c->evd_path > LCF_EVD_PAIR) return LCF_EINVAL;
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
   return LCF_OK;
@@ -114,7 +116,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
-                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.iq_stage, w.pd_stage};
+                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -228,6 +230,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = gram_tc_configure();
     if (e == cudaSuccess) e = basis_configure();
     if (e == cudaSuccess) e = project_tc_configure();
+    if (e == cudaSuccess) e = evd_pair_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
   }
   if (e != cudaSuccess) {
@@ -283,7 +286,8 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   if (tc) LCF_CUDA(launch_gram_assemble_tc(P, st));
   else LCF_CUDA(launch_gram_assemble(P, st));
   LCF_MARK(LCF_STAGE_EVD);
-  LCF_CUDA(launch_evd(P, st));
+  if (c.evd_path == LCF_EVD_PAIR) LCF_CUDA(launch_evd_pair(P, st));
+  else LCF_CUDA(launch_evd(P, st));
   LCF_MARK(LCF_STAGE_PROJECT);
   if (c.project_path == LCF_PATH_TC) LCF_CUDA(launch_project_tc(P, out, st));
   else LCF_CUDA(launch_project_simt(P, iq, out, st));
@@ -298,6 +302,10 @@ extern "C" lcf_status lcf_plan_profile(lcf_plan* P, int enable) {
   if (enable && P->prof_ev.empty()) {
     P->prof_ev.resize((size_t)kProfCalls * (LCF_NSTAGES + 1));
     for (auto& e : P->prof_ev) LCF_CUDA(cudaEventCreate(&e));
+  }
+  if (enable && !P->ws.evd_clk) {
+    LCF_CUDA(cudaMalloc((void**)&P->ws.evd_clk, (size_t)P->nd * (kEvdPhases + 1) * sizeof(long long)));
+    LCF_CUDA(cudaMemset(P->ws.evd_clk, 0, (size_t)P->nd * (kEvdPhases + 1) * sizeof(long long)));
   }
   P->profiling = enable != 0;
   P->prof_calls = 0;
@@ -320,6 +328,25 @@ extern "C" lcf_status lcf_plan_profile_read(lcf_plan* P, double* ms, int* n_call
   }
   if (ms) memcpy(ms, acc, sizeof(acc));
   if (n_calls) *n_calls = (int)n;
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_evd_phases(lcf_plan* P, double* cycles) {
+  if (!P || !cycles) return LCF_EINVAL;
+  if (!P->ws.evd_clk) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  LCF_CUDA(cudaStreamSynchronize(P->last_stream));
+  std::vector<long long> c((size_t)P->nd * (kEvdPhases + 1));
+  LCF_CUDA(cudaMemcpy(c.data(), P->ws.evd_clk, c.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+  for (int j = 0; j < kEvdPhases; ++j) {
+    double acc = 0.0;
+    int cnt = 0;
+    for (int k = 0; k < P->nd; ++k) {
+      const long long a = c[(size_t)k * (kEvdPhases + 1) + j], b = c[(size_t)k * (kEvdPhases + 1) + j + 1];
+      if (a != 0 && b >= a) { acc += (double)(b - a); ++cnt; }
+    }
+    cycles[j] = cnt ? acc / cnt : 0.0;
+  }
   return LCF_OK;
 }
 

@@ -20,6 +20,10 @@ __host__ __device__ inline int deflate_count(int nt) {
   int d = nt / 4;
   return d < 1 ? 1 : (d > kDeflateMax ? kDeflateMax : d);
 }
+// EVD phases timed by the stage profiler: subspace iteration, QR of the block,
+// double-float congruence, fp32 conversion + Q, Jacobi, sort + phase fix,
+// thresholding rule, projection weights.
+constexpr int kEvdPhases = 8;
 // Calls whose stage events are kept between profile reads.
 constexpr int kProfCalls = 4096;
 
@@ -56,6 +60,7 @@ struct Workspace {
   int* tile_win = nullptr;    // window indices, ascending per tile
   unsigned char* bimg = nullptr;  // [nd] pre-split weight images (fp16 hi/lo, MMA layout)
   float* bscale = nullptr;    // [nd] power-of-two scale of each weight image
+  long long* evd_clk = nullptr;  // [nd][kEvdPhases+1] EVD phase clocks (profiling only)
   // host-call staging
   float2* iq_stage = nullptr; // [nt][nz][nx] device copy for lcf_filter_host
   float* pd_stage = nullptr;  // [nz][nx]
@@ -198,6 +203,8 @@ cudaError_t gram_tc_configure();
 size_t gram_tc_smem_bytes(int na);
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st);
+cudaError_t evd_pair_configure();
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
 cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st);
 cudaError_t project_tc_configure();

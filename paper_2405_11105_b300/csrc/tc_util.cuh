@@ -65,19 +65,30 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
 }
-// Bounded wait for the completion of the phase with the given parity.
-// Returns false if the limit ran out (the caller reports a timeout).
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long limit = 200000000L) {
-  uint32_t done = 0;
-  for (long it = 0; it < limit; ++it) {
-    asm volatile(
-        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the completion of the phase with the given parity, for at most
+// limit_ns of wall time.  Returns false if the limit ran out (the caller
+// reports a timeout).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint64_t limit_ns = 2000000000ull) {
+  if (mbar_try(mbar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try(mbar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
-  return false;
 }
 
 // 32 lanes x 16 consecutive fp32 columns of TMEM (lane base in taddr bits 31..16)
