@@ -44,7 +44,7 @@ def algorithmic_work(nt=NT, nd=WZ * WX, sum_p=SUM_P):
     return {
         "gram": 0.5 * 8.0 * sum_p * nt * nt,          # Hermitian upper triangle of each R_k
         "project": 8.0 * sum_p * nt * nt,             # C_w V for every window (one GEMM)
-        "evd": nd * 13.0 * nt ** 3,                   # Hermitian EVD with vectors (~13 n^3 real flops)
+        "evd": nd * 240.0 * nt ** 3,                  # cyclic Jacobi with vectors, ~240 Nt^3 real flops per window
         "prep": None, "assemble": None,
     }
 
@@ -179,8 +179,10 @@ def main():
     st = torch.cuda.current_stream()
 
     def plan_for(path):
+        # optimized path: tensor-core Gram and projection, CTA-pair EVD; plain path: CUDA cores only
+        evd = L.LCF_EVD_PAIR if path == L.LCF_PATH_TC else L.LCF_EVD_CTA
         return L.Plan.make(NZ, NX, NT, WZ, WX, device=local, thresh_mode=L.LCF_T_CURVATURE, beta=1.0,
-                           gram_path=path, project_path=path)
+                           gram_path=path, project_path=path, evd_path=evd)
 
     def barrier():
         if dist is not None:
