@@ -1,7 +1,7 @@
 // k_evd.cu — batched Hermitian EVD R_k = V Lambda V^H (Eq. 2), eigen-weights
 // (thresholding methods 1-3, 5, 6) and the per-window projection weights.
 //
-// One CTA per window, the whole matrix in shared memory (Nt <= kEvdNmax).
+// One CTA per window, the whole matrix in shared memory (Nt <= kEvdCtaNmax).
 //
 // Precision plan (B300 FP64 is ~1/62 of FP32, so FP64 stays out of every
 // O(Nt^3) loop):
@@ -148,7 +148,7 @@ evd_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EvdArg
   __shared__ double sh_scale;
   __shared__ df sh_kappa;
   __shared__ int sh_flag;
-  __shared__ float2 sh_phase[kEvdNmax];
+  __shared__ float2 sh_phase[kEvdCtaNmax];
 
   const double2* R = Rg + (size_t)k * n * n;
 
@@ -606,7 +606,7 @@ cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st) {
 
 cudaError_t evd_configure() {
   return cudaFuncSetAttribute(evd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)evd_smem_bytes(kEvdNmax));
+                              (int)evd_smem_bytes(kEvdCtaNmax));
 }
 
 }  // namespace lcf

@@ -566,7 +566,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     EP_STAMP(3);
     EP_STAMP(4);
     // ---------------- phase D: cyclic Jacobi on A; rotations streamed to CTA 1
-    constexpr int MAXB = (56 * 57 / 2 + EP_THREADS - 1) / EP_THREADS;
+    constexpr int MAXB = ((kEvdNmax / 2) * (kEvdNmax / 2 + 1) / 2 + EP_THREADS - 1) / EP_THREADS;
     int blk[MAXB];
     {
       const int nblk = h * (h + 1) / 2;

@@ -192,7 +192,9 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
   const int npix = nz * nx;
   const float* gzk = gz + (size_t)k * nz;
   const float* gxk = gx + (size_t)k * nx;
-  constexpr int OPT = 2;   // outputs per thread (nout <= (112 + 4) * 4 = 464 <= 512)
+  // outputs per thread: nout = (nt + d) * d <= (kEvdNmax + kDeflateMax) * kDeflateMax over 256 threads
+  constexpr int OPT = ((kEvdNmax + kDeflateMax) * kDeflateMax + 255) / 256;
+  static_assert(OPT * 256 >= (kEvdNmax + kDeflateMax) * kDeflateMax, "augmented outputs per thread");
   float2 acc[OPT];
   df hr[OPT], hi[OPT];
 #pragma unroll
@@ -317,7 +319,8 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
       }
   __syncthreads();
   double2 wv[2];
-  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 448 < 512)
+  static_assert(kEvdNmax * kDeflateMax <= 512, "W rows per thread");
+  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 512)
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
   }

@@ -296,7 +296,7 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   }
   __syncthreads();
   double2 wv[2];
-  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 448 < 512)
+  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 496 < 512)
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
   }
@@ -359,7 +359,7 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
 
 cudaError_t gram_tc_configure() {
   return cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)gram_tc_smem_bytes(kEvdNmax + kDeflateMax));
+                              (int)gram_tc_smem_bytes(kTcGramNaMax));
 }
 
 }  // namespace lcf

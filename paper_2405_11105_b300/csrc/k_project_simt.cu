@@ -68,7 +68,7 @@ project_simt_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int n
   if (cg == 0 && x < nx) out[(size_t)z * nx + x] = pd;
 }
 
-int project_cpt(int nt) { return nt <= 32 ? 8 : (nt <= 64 ? 16 : 28); }
+int project_cpt(int nt) { return nt <= 32 ? 8 : (nt <= 64 ? 16 : (nt <= 112 ? 28 : 32)); }
 
 size_t project_smem_bytes(int nt, int ncp) { return (size_t)nt * 64 * 8 + (size_t)nt * ncp * 8; }
 
@@ -83,8 +83,11 @@ cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out,
   else if (cpt == 16)
     project_simt_kernel<16><<<grid, 256, sm, st>>>(iq, c.nz, c.nx, P->nt, P->nd, P->ws.box, P->ws.gz,
                                                    P->ws.gx, P->ws.W, P->ws.ncol, P->ncp, out);
-  else
+  else if (cpt == 28)
     project_simt_kernel<28><<<grid, 256, sm, st>>>(iq, c.nz, c.nx, P->nt, P->nd, P->ws.box, P->ws.gz,
+                                                   P->ws.gx, P->ws.W, P->ws.ncol, P->ncp, out);
+  else
+    project_simt_kernel<32><<<grid, 256, sm, st>>>(iq, c.nz, c.nx, P->nt, P->nd, P->ws.box, P->ws.gz,
                                                    P->ws.gx, P->ws.W, P->ws.ncol, P->ncp, out);
   return counted(P);
 }
@@ -96,6 +99,8 @@ cudaError_t project_configure() {
     e = cudaFuncSetAttribute(project_simt_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(project_simt_kernel<28>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(project_simt_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
   return e;
 }
 

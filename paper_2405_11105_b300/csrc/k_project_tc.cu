@@ -31,7 +31,7 @@ namespace lcf {
 
 constexpr int PT_THREADS = 256;
 constexpr int PT_TZ = 8, PT_TX = 16;     // tile: 8 rows x 16 columns = 128 pixels
-constexpr int PT_KS = 2;                 // k-steps (16 K each) per weight stage
+constexpr int PT_KS_MAX = 2;             // k-steps (16 K each) per weight stage, at most
 constexpr int PT_STAGES = 3;
 constexpr int PT_ACC = 256;              // TMEM columns per accumulator buffer (Yr at +0, Yi at +128)
 
@@ -46,9 +46,13 @@ size_t project_tc_image_bytes(int nt, int nd_defl) {
   return (size_t)(pt_k16(nt, nd_defl) / 16) * pt_kstep_bytes(pt_n16(nt));
 }
 
-size_t project_tc_smem_bytes(int nt, int nd_defl) {
+size_t project_tc_smem_bytes(int nt, int nd_defl, int ksps) {
   const int k16 = pt_k16(nt, nd_defl);
-  return 1024 + 4 * (size_t)128 * k16 * 2 + (size_t)PT_STAGES * PT_KS * pt_kstep_bytes(pt_n16(nt));
+  return 1024 + 4 * (size_t)128 * k16 * 2 + (size_t)PT_STAGES * ksps * pt_kstep_bytes(pt_n16(nt));
+}
+// k-steps per ring stage: two unless the stages would not fit beside the resident rows
+static int project_tc_ksps(int nt, int nd_defl) {
+  return project_tc_smem_bytes(nt, nd_defl, PT_KS_MAX) <= 232448 ? PT_KS_MAX : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -119,7 +123,7 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PT_THREADS, 1)
 project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, int k16, int n16max,
-                  int tiles_x, const int* __restrict__ tile_off, const int* __restrict__ tile_win,
+                  int ksps, int tiles_x, const int* __restrict__ tile_off, const int* __restrict__ tile_win,
                   const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
                   const int* __restrict__ ncol, const unsigned char* __restrict__ bimg,
                   const float* __restrict__ bscale, float* __restrict__ out, int* __restrict__ err) {
@@ -134,13 +138,13 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x, z0 = (tile / tiles_x) * PT_TZ, x0 = (tile % tiles_x) * PT_TX;
   const int w0 = tile_off[tile], w1 = tile_off[tile + 1];
-  const int na = nt + nd_defl, nks = k16 / 16, nstw = (nks + PT_KS - 1) / PT_KS;
+  const int na = nt + nd_defl, nks = k16 / 16, nstw = (nks + ksps - 1) / ksps;
   const size_t npix = (size_t)nz * nx;
   const int a_sbo = (k16 / 8) * 128;
   const size_t a_bytes = (size_t)128 * k16 * 2;            // one of Sr hi, Sr lo, Si hi, Si lo
   unsigned char* A = smem;
   unsigned char* Bring = smem + 4 * a_bytes;
-  const size_t st_bytes = (size_t)PT_KS * pt_kstep_bytes(n16max);
+  const size_t st_bytes = (size_t)ksps * pt_kstep_bytes(n16max);
   const size_t img_stride = (size_t)nks * pt_kstep_bytes(n16max);
   const float sA = tc::pow2_scale(__uint_as_float(*xmax_bits));
 
@@ -199,10 +203,10 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
         for (int s = 0; s < nstw; ++s, ++q) {
           const int slot = q % PT_STAGES;
           if (q >= PT_STAGES && !(ok = tc::mbar_wait(&empty_bar[slot], ((q / PT_STAGES) - 1) & 1))) break;
-          const int nk = min(PT_KS, nks - s * PT_KS);
+          const int nk = min(ksps, nks - s * ksps);
           const uint32_t bytes = (uint32_t)(nk * kb);
           tc::mbar_arrive_expect_tx(&full_bar[slot], bytes);
-          tc::bulk_g2s(Bring + slot * st_bytes, img + (size_t)s * PT_KS * kb, bytes, &full_bar[slot]);
+          tc::bulk_g2s(Bring + slot * st_bytes, img + (size_t)s * ksps * kb, bytes, &full_bar[slot]);
         }
       }
       // the copies still in flight land before the CTA exits
@@ -233,10 +237,10 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
           const int slot = q % PT_STAGES;
           if (!(ok = tc::mbar_wait(&full_bar[slot], (q / PT_STAGES) & 1))) break;
           tc::fence_after();
-          const int nk = min(PT_KS, nks - s * PT_KS);
+          const int nk = min(ksps, nks - s * ksps);
           const uint32_t bslot = tc::smem_u32(Bring + slot * st_bytes);
           for (int kl = 0; kl < nk; ++kl) {
-            const int ks = s * PT_KS + kl;
+            const int ks = s * ksps + kl;
             const uint64_t srh = tc::smem_desc(a_h[0] + ks * 256, 128, a_sbo);
             const uint64_t srl = tc::smem_desc(a_l[0] + ks * 256, 128, a_sbo);
             const uint64_t sih = tc::smem_desc(a_h[1] + ks * 256, 128, a_sbo);
@@ -319,15 +323,21 @@ cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st) {
                                              P->ws.bimg, P->ws.bscale);
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
-  project_tc_kernel<<<P->ptiles_z * P->ptiles_x, PT_THREADS, project_tc_smem_bytes(P->nt, P->ndefl), st>>>(
-      P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, k16, n16max, P->ptiles_x, P->ws.tile_off, P->ws.tile_win, P->ws.gz,
+  const int ksps = project_tc_ksps(P->nt, P->ndefl);
+  project_tc_kernel<<<P->ptiles_z * P->ptiles_x, PT_THREADS, project_tc_smem_bytes(P->nt, P->ndefl, ksps), st>>>(
+      P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, k16, n16max, ksps, P->ptiles_x, P->ws.tile_off, P->ws.tile_win, P->ws.gz,
       P->ws.gx, P->ws.xmax, P->ws.ncol, P->ws.bimg, P->ws.bscale, out, P->ws.err);
   return counted(P);
 }
 
 cudaError_t project_tc_configure() {
-  return cudaFuncSetAttribute(project_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)project_tc_smem_bytes(kEvdNmax, kDeflateMax));
+  size_t mx = 0;   // the largest launch over every packet length (two or one k-steps per stage)
+  for (int nt = 2; nt <= kEvdNmax; ++nt) {
+    const int d = deflate_count(nt);
+    const size_t b = project_tc_smem_bytes(nt, d, project_tc_ksps(nt, d));
+    mx = b > mx ? b : mx;
+  }
+  return cudaFuncSetAttribute(project_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 
 void project_tc_tiles(const lcf_plan* P, int* tiles_z, int* tiles_x, std::vector<int>& off, std::vector<int>& win) {

@@ -65,6 +65,8 @@ static lcf_status validate(const lcf_config* c) {
   if (c->evd_path < LCF_EVD_CTA || c->evd_path > LCF_EVD_PAIR) return LCF_EINVAL;
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
+  if (c->evd_path == LCF_EVD_CTA && c->nt > kEvdCtaNmax) return LCF_EUNSUPPORTED;
+  if (c->gram_path == LCF_PATH_TC && c->nt + deflate_count(c->nt) > kTcGramNaMax) return LCF_EUNSUPPORTED;
   return LCF_OK;
 }
 

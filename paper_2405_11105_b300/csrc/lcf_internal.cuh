@@ -10,8 +10,13 @@
 
 namespace lcf {
 
-// Largest packet length the one-CTA-per-window EVD keeps in shared memory.
-constexpr int kEvdNmax = 112;
+// Largest packet length of the library (the CTA-pair EVD keeps A in one SM's
+// shared memory and V in its partner's).
+constexpr int kEvdNmax = 128;
+// Largest packet length of the one-CTA EVD (A and V in one SM's shared memory).
+constexpr int kEvdCtaNmax = 112;
+// Largest augmented row (Nt + deflation vectors) of the tensor-core Gram (one M = 128 tile).
+constexpr int kTcGramNaMax = 128;
 // Subspace-iteration block of the EVD (head directions isolated exactly).
 constexpr int kEvdHead = 8;
 // Slow-time DCT-II vectors deflated from every pixel before the Gram.

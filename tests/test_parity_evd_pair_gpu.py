@@ -75,12 +75,43 @@ def test_pair_small_all_rules(mode, beta, extra):
     ((112, 24, 20), (2, 2), "LCF_T_CURVATURE"),   # largest Nt: 56 pairs, 13 V items per thread
     ((2, 8, 8), (1, 1), "LCF_T_FIXED"),          # one pair
     ((5, 12, 9), (2, 2), "LCF_T_CURVATURE"),     # head block = whole matrix (m = Nt)
+    ((128, 40, 36), (2, 2), "LCF_T_CURVATURE"),   # largest Nt of the library: 64 pairs, 16 V items per thread
+    ((127, 33, 29), (2, 3), "LCF_T_MEDIAN"),
 ])
 def test_pair_edge_shapes(shape, grid, mode):
     lib = L()
     nt, nz, nx = shape
     cfg, oc = pair_cfg(nz, nx, nt, grid[0], grid[1], thresh_mode=getattr(lib, mode), k_fixed=1, beta=1.0)
     check(compare(rand_iq(3, nt, nz, nx), cfg, oc, want_gram=False))
+
+
+@pytest.mark.parametrize("mode", ["LCF_T_CURVATURE", "LCF_T_ADAPTIVE_SOFT"])
+def test_pair_nt128_with_tensor_core_projection(mode):
+    """Nt = 128: plain Gram (Nt + d > 128 rows for the tensor-core Gram), CTA-pair EVD,
+    tensor-core projection with one k-step per weight stage."""
+    lib = L()
+    nt, nz, nx = 128, 48, 40
+    cfg, oc = pair_cfg(nz, nx, nt, 3, 2, thresh_mode=getattr(lib, mode), beta=1.0 if mode == "LCF_T_CURVATURE" else 0.5)
+    cfg.project_path = lib.LCF_PATH_TC
+    check(compare(rand_iq(5, nt, nz, nx), cfg, oc, want_gram=False), soft=mode != "LCF_T_CURVATURE")
+
+
+def test_packet_length_limits():
+    lib = L()
+    for kw, want in (({"nt": 128, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_EUNSUPPORTED),
+                     ({"nt": 128, "evd_path": lib.LCF_EVD_CTA}, lib.LCF_EUNSUPPORTED),
+                     ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_EUNSUPPORTED),
+                     ({"nt": 124, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK)):
+        c = lib.lcf_config_default(32, 32, kw["nt"], 2, 2)
+        for k, v in kw.items():
+            setattr(c, k, v)
+        try:
+            plan = lib.Plan(c)
+            got = lib.LCF_OK
+            plan.close()
+        except lib.LcfError as e:
+            got = e.status
+        assert got == want, (kw, got)
 
 
 def test_pair_zero_packet_is_degenerate():
