@@ -41,6 +41,7 @@ extern "C" {
 #endif
 
 typedef struct lcf_plan lcf_plan;
+typedef struct lcf_mlp lcf_mlp;
 
 typedef enum {
   LCF_OK = 0,
@@ -67,13 +68,18 @@ enum {
   LCF_T_SIGMOID = 4,        /* method 5, Eq. 9: wt_i = 1/(1+exp(-beta (i-k))),
                                k from rule k_src with factor beta_src             */
   LCF_T_ADAPTIVE_SOFT = 5,  /* method 6, Eq. 10: wt_i ~ win(i) / lambda_i^beta    */
-  LCF_T_NONE = 6            /* wt = 1 (identity reconstruction, for checks)       */
+  LCF_T_NONE = 6,           /* wt = 1 (identity reconstruction, for checks)       */
+  LCF_T_LEARNED = 7         /* hard cutoff k from the plan's learned rule (an MLP
+                               set by lcf_plan_set_mlp; no counterpart in the
+                               paper); below its confidence threshold the window
+                               falls back to rule k_src with factor beta_src     */
 };
 
 /* Status bits per window (lcf_plan_status). */
 /* Bits 8-15 of a window's status word hold the number of Jacobi sweeps its
  * EVD used (for tuning and convergence monitoring). */
-enum { LCF_WFLAG_NOCONV = 1, LCF_WFLAG_DEGENERATE = 2, LCF_WFLAG_SWEEP_SHIFT = 8 };
+/* LCF_WFLAG_FALLBACK: the learned rule was not confident and k_src decided. */
+enum { LCF_WFLAG_NOCONV = 1, LCF_WFLAG_DEGENERATE = 2, LCF_WFLAG_FALLBACK = 4, LCF_WFLAG_SWEEP_SHIFT = 8 };
 
 /* Compute paths.  LCF_PATH_SIMT is the plain FP32 GPU path (CUDA cores,
  * FP32 products, FP32 partial sums promoted to double-float);
@@ -221,6 +227,54 @@ lcf_status lcf_gram_noalloc(const lcf_config* cfg, const void* d_iq, void* d_R, 
 
 /* Size in bytes of lcf_gram_noalloc's static per-device scratch. */
 size_t lcf_gram_noalloc_scratch_bytes(void);
+
+/* ---- learned cutoff rule (no counterpart in the paper) ----
+ * A multilayer perceptron maps a window's normalised log-eigenvalue spectrum
+ * y_i = (log10 l_i - log10 l_Nt) / (log10 l_1 - log10 l_Nt)  (l_i = max(lambda_i,
+ * lambda_1 Nt 2^-52), the curve of method 1, Eq. 6) and the window centre
+ * ((iz + 1/2)/Wz, (ix + 1/2)/Wx) -- Nt + 2 inputs -- through 3 hidden ReLU
+ * layers of H units to Nt logits over the cutoff k = 0 .. Nt-1.  Parameters
+ * are one flat FP32 vector: W1 (H x (Nt+2)), b1 (H), W2 (H x H), b2, W3 (H x H),
+ * b3, W4 (Nt x H), b4 (Nt), matrices row-major.  Training (FP32) runs on the
+ * device with AdamW; inference runs inside the EVD kernel with bf16 weights
+ * and FP32 accumulation. */
+
+/* Create a network for packets of nt frames with hidden width H (<= 256) and
+ * training batches of up to max_batch samples, on `device`.  Parameters and
+ * optimiser moments start at zero.  Synchronous. */
+lcf_status lcf_mlp_create(int nt, int hidden, int max_batch, int device, lcf_mlp** out);
+/* Number of FP32 parameters (length of the flat vector). */
+size_t lcf_mlp_param_count(const lcf_mlp* mlp);
+/* Copy the flat parameter vector in from / out to host memory (synchronous).
+ * Setting parameters resets the AdamW moments and step count. */
+lcf_status lcf_mlp_set_params(lcf_mlp* mlp, const float* h_params);
+lcf_status lcf_mlp_get_params(const lcf_mlp* mlp, float* h_params);
+/* Gradients of the last lcf_mlp_loss_grad call, flat layout, to host (synchronous). */
+lcf_status lcf_mlp_get_grads(const lcf_mlp* mlp, float* h_grads);
+/* Logits for a batch: d_x [batch][Nt+2] f32 (device), d_logits [batch][Nt]
+ * f32 (device, written).  Asynchronous on `stream`. */
+lcf_status lcf_mlp_forward(lcf_mlp* mlp, const float* d_x, int batch, float* d_logits, cudaStream_t stream);
+/* Mean softmax cross-entropy of the batch against cutoffs d_k [batch] (int,
+ * device, in [0, Nt); a label outside gives a NaN loss and no gradient), and
+ * its gradient with respect to every parameter (kept on the device).  If
+ * h_loss is not NULL the call synchronises `stream` and writes the loss. */
+lcf_status lcf_mlp_loss_grad(lcf_mlp* mlp, const float* d_x, const int* d_k, int batch, float* h_loss,
+                             cudaStream_t stream);
+/* One AdamW step with the current gradients: bias-corrected moments, decoupled
+ * weight decay wd on the weight matrices only.  Asynchronous. */
+lcf_status lcf_mlp_adamw(lcf_mlp* mlp, float lr, float beta1, float beta2, float eps, float wd,
+                         cudaStream_t stream);
+lcf_status lcf_mlp_destroy(lcf_mlp* mlp);
+
+/* Give a plan the learned rule: the network's current parameters are copied
+ * (bf16 weights, FP32 biases) into plan-owned device memory; later changes to
+ * `mlp` do not affect the plan until this is called again.  p_min: windows whose
+ * largest class probability is below it use rule k_src instead (flagged
+ * LCF_WFLAG_FALLBACK); 0 <= p_min <= 2, above 1 every window falls back.  A
+ * learned plan normally runs with a small max_sweeps, so its status may read
+ * LCF_ENOCONV by design.  Requires mlp's Nt = the plan's Nt and the CTA-pair EVD.
+ * Synchronous. */
+lcf_status lcf_plan_set_mlp(lcf_plan* plan, const lcf_mlp* mlp, float p_min);
 
 /* Number of kernels the plan has launched since it was created (every
  * filter call adds the launches of its stages; debug dumps add theirs).

@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
 (LCF_OK, LCF_EINVAL, LCF_ENOMEM, LCF_ECUDA, LCF_ENOCONV, LCF_ETIMEOUT, LCF_EDEGENERATE, LCF_EUNSUPPORTED,
  LCF_ESCRATCH) = range(9)
 (LCF_T_FIXED, LCF_T_CURVATURE, LCF_T_SLOPE, LCF_T_MEDIAN, LCF_T_SIGMOID, LCF_T_ADAPTIVE_SOFT,
- LCF_T_NONE) = range(7)
-LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE, LCF_WFLAG_SWEEP_SHIFT = 1, 2, 8
+ LCF_T_NONE, LCF_T_LEARNED) = range(8)
+LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE, LCF_WFLAG_FALLBACK, LCF_WFLAG_SWEEP_SHIFT = 1, 2, 4, 8
 LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
 LCF_EVD_CTA, LCF_EVD_PAIR = 0, 1
 STAGES = ("prep", "gram", "assemble", "evd", "project")
@@ -70,6 +70,16 @@ def _load():
         "lcf_status_string": ([C.c_int], C.c_char_p),
         "lcf_gram_noalloc": ([C.POINTER(lcf_config), vp, vp, vp], C.c_int),
         "lcf_gram_noalloc_scratch_bytes": ([], C.c_size_t),
+        "lcf_mlp_create": ([C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
+        "lcf_mlp_param_count": ([vp], C.c_size_t),
+        "lcf_mlp_set_params": ([vp, fp], C.c_int),
+        "lcf_mlp_get_params": ([vp, fp], C.c_int),
+        "lcf_mlp_get_grads": ([vp, fp], C.c_int),
+        "lcf_mlp_forward": ([vp, vp, C.c_int, vp, vp], C.c_int),
+        "lcf_mlp_loss_grad": ([vp, vp, vp, C.c_int, fp, vp], C.c_int),
+        "lcf_mlp_adamw": ([vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, vp], C.c_int),
+        "lcf_mlp_destroy": ([vp], C.c_int),
+        "lcf_plan_set_mlp": ([vp, vp, C.c_float], C.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -170,6 +180,10 @@ class Plan:
         _check(_lib.lcf_plan_evd_phases(self.handle, _p(cyc, C.c_double)), "lcf_plan_evd_phases")
         return dict(zip(EVD_PHASES, cyc.tolist()))
 
+    def set_mlp(self, mlp: "Mlp", p_min: float = 0.5):
+        """Give the plan the learned cutoff rule (used when thresh_mode == LCF_T_LEARNED)."""
+        _check(_lib.lcf_plan_set_mlp(self.handle, mlp.handle, float(p_min)), "lcf_plan_set_mlp")
+
     def launch_count(self) -> int:
         """Kernels this plan has launched since it was created."""
         n = C.c_longlong()
@@ -266,3 +280,65 @@ class Plan:
         _check(_lib.lcf_debug_filtered_iq(self.handle, iq.data_ptr(), int(subset), out.data_ptr(), st),
                "lcf_debug_filtered_iq")
         return out
+
+
+def _stream_handle(stream):
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return st.cuda_stream
+
+
+class Mlp:
+    """The learned cutoff rule's network (see lcf_mlp_* in include/lcf.h).  Inputs
+    and labels are torch tensors on the network's device."""
+
+    def __init__(self, nt: int, hidden: int = 256, max_batch: int = 4096, device: int = 0):
+        h = C.c_void_p()
+        _check(_lib.lcf_mlp_create(int(nt), int(hidden), int(max_batch), int(device), C.byref(h)), "lcf_mlp_create")
+        self.handle, self.nt, self.hidden, self.max_batch, self.device = h.value, nt, hidden, max_batch, device
+        self.nparams = int(_lib.lcf_mlp_param_count(self.handle))
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(_lib.lcf_mlp_set_params(self.handle, _p(a, C.c_float)), "lcf_mlp_set_params")
+
+    def params(self):
+        a = np.empty(self.nparams, np.float32)
+        _check(_lib.lcf_mlp_get_params(self.handle, _p(a, C.c_float)), "lcf_mlp_get_params")
+        return a
+
+    def grads(self):
+        a = np.empty(self.nparams, np.float32)
+        _check(_lib.lcf_mlp_get_grads(self.handle, _p(a, C.c_float)), "lcf_mlp_get_grads")
+        return a
+
+    def forward(self, x, stream=None):
+        import torch
+        x = x.contiguous()
+        out = torch.empty((x.shape[0], self.nt), dtype=torch.float32, device=x.device)
+        _check(_lib.lcf_mlp_forward(self.handle, x.data_ptr(), int(x.shape[0]), out.data_ptr(), _stream_handle(stream)),
+               "lcf_mlp_forward")
+        return out
+
+    def loss_grad(self, x, k, stream=None) -> float:
+        x, k = x.contiguous(), k.contiguous()
+        loss = C.c_float()
+        _check(_lib.lcf_mlp_loss_grad(self.handle, x.data_ptr(), k.data_ptr(), int(x.shape[0]), C.byref(loss),
+                                      _stream_handle(stream)), "lcf_mlp_loss_grad")
+        return float(loss.value)
+
+    def adamw(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0, stream=None):
+        _check(_lib.lcf_mlp_adamw(self.handle, float(lr), float(beta1), float(beta2), float(eps), float(wd),
+                                  _stream_handle(stream)), "lcf_mlp_adamw")
+
+    def close(self):
+        if self.handle:
+            _lib.lcf_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -46,6 +46,11 @@ struct EpArgs {
   int ncp;
   int* err;
   long long* clk;   // [nd][kEvdPhases + 1] phase-boundary SM clocks of CTA 0 (profiling), or null
+  int wz, wx;                       // window grid (the learned rule's position input)
+  const __nv_bfloat16* mlp_w;       // learned rule: W1 | W2 | W3 | W4 (bf16)
+  const float* mlp_b;               //               b1 | b2 | b3 | b4
+  int mlp_h;                        // hidden width
+  float mlp_pmin;                   // confidence threshold
 };
 
 #define EP_STAMP(b)                                                                  \
@@ -56,7 +61,7 @@ struct EpArgs {
 // ---- shared-memory layout (both CTAs get the larger of the two) ----
 struct EpLayout {
   int np, ld, ldy, m, h;
-  size_t a, ys, zs, yd, zd, tm, w2, pr, prd, lam, perm, wts, s0, s1, s2, ebar, end_a;   // CTA 0
+  size_t a, ys, zs, yd, zd, tm, w2, pr, prd, lam, perm, wts, s0, s1, s2, ebar, mlp, end_a;   // CTA 0
   size_t vt, ring, vh, tv, vtm, fbar, rperm, rcoef, rkeep, phase, end_v;                 // CTA 1
   size_t total;
 };
@@ -87,6 +92,7 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
   L.s1 = o;   o = ep_align(o + (size_t)L.np * 8);
   L.s2 = o;   o = ep_align(o + (size_t)L.np * 8);
   L.ebar = o; o = ep_align(o + (size_t)EP_RING * 8);
+  L.mlp = o;  o = ep_align(o + (size_t)(L.np + 2 + 2 * kMlpHiddenMax) * 4);   // learned rule: input, 2 activations
   L.end_a = o;
   o = 0;
   L.vt = o;    o = ep_align(o + (size_t)L.np * L.ld * 8);     // V^T (row c = column c of V)
@@ -164,6 +170,22 @@ __device__ __forceinline__ bool ep_wait(uint64_t* b, uint32_t parity) {
   for (;;) {
     if (ep_try(b, parity)) return true;
     if (ep_now() - t0 > EP_WAIT_NS) return false;
+  }
+}
+
+// ---- learned cutoff rule: one dense layer on all warps of the CTA ----
+// out[o] = act(b[o] + sum_k W[o][k] x[k]), W bf16 row-major (K per row), FP32 accumulation
+__device__ void ep_dense(const float* x, int K, const __nv_bfloat16* __restrict__ W, const float* __restrict__ b,
+                         float* out, int N, bool relu, int warp, int lane) {
+  for (int o = warp; o < N; o += EP_THREADS / 32) {
+    const __nv_bfloat16* w = W + (size_t)o * K;
+    float s = 0.f;
+    for (int k = lane; k < K; k += 32) s = fmaf(__bfloat162float(w[k]), x[k], s);
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(~0u, s, off);
+    if (lane == 0) {
+      s += b[o];
+      out[o] = relu ? fmaxf(s, 0.f) : s;
+    }
   }
 }
 
@@ -693,8 +715,59 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     for (int i = tid; i < n; i += EP_THREADS) lam_s[i] = (double)A[perm[i] * ld + perm[i]].x * scale;
     __syncthreads();
     EP_STAMP(6);
+    __shared__ int sh_lk;
+    __shared__ float sh_lp;
+    if (g.thresh_mode == LCF_T_LEARNED) {
+      // learned rule: features (method 1's curve on [0, 1], window centre) -> MLP -> argmax k
+      float* xin = reinterpret_cast<float*>(smem + L.mlp);
+      float* h1 = xin + np + 2;
+      float* h2 = h1 + kMlpHiddenMax;
+      const int H = g.mlp_h, nin = n + 2;
+      if (warp == 0) {
+        const double fl = lam_s[0] * n * 2.220446049250313e-16;
+        const double y1 = log10(lam_s[0] > fl ? lam_s[0] : fl), yn = log10(lam_s[n - 1] > fl ? lam_s[n - 1] : fl);
+        const double span = y1 - yn;
+        for (int i = lane; i < n; i += 32) {
+          const double y = log10(lam_s[i] > fl ? lam_s[i] : fl);
+          xin[i] = span > 0 ? (float)((y - yn) / span) : 0.f;
+        }
+        if (lane == 0) {
+          xin[n] = (float)(((k / g.wx) + 0.5) / g.wz);
+          xin[n + 1] = (float)(((k % g.wx) + 0.5) / g.wx);
+        }
+      }
+      __syncthreads();
+      const __nv_bfloat16* W1 = g.mlp_w;
+      const __nv_bfloat16* W2 = W1 + (size_t)H * nin;
+      const __nv_bfloat16* W3 = W2 + (size_t)H * H;
+      const __nv_bfloat16* W4 = W3 + (size_t)H * H;
+      ep_dense(xin, nin, W1, g.mlp_b, h1, H, true, warp, lane);
+      __syncthreads();
+      ep_dense(h1, H, W2, g.mlp_b + H, h2, H, true, warp, lane);
+      __syncthreads();
+      ep_dense(h2, H, W3, g.mlp_b + 2 * H, h1, H, true, warp, lane);
+      __syncthreads();
+      ep_dense(h1, H, W4, g.mlp_b + 3 * H, h2, n, false, warp, lane);
+      __syncthreads();
+      if (warp == 0) {   // argmax (first index on ties) and its softmax probability
+        float mx = -INFINITY;
+        int bi = 0x7fffffff;
+        for (int i = lane; i < n; i += 32)
+          if (h2[i] > mx) { mx = h2[i]; bi = i; }
+        for (int o = 16; o; o >>= 1) {
+          const float om = __shfl_xor_sync(~0u, mx, o);
+          const int oi = __shfl_xor_sync(~0u, bi, o);
+          if (om > mx || (om == mx && oi < bi)) { mx = om; bi = oi; }
+        }
+        float se = 0.f;
+        for (int i = lane; i < n; i += 32) se += expf(h2[i] - mx);
+        for (int o = 16; o; o >>= 1) se += __shfl_xor_sync(~0u, se, o);
+        if (lane == 0) { sh_lk = bi; sh_lp = 1.f / se; }
+      }
+      __syncthreads();
+    }
     if (warp == 0) {
-      int kk = -1;
+      int kk = -1, fallback = 0;
       const int md = g.thresh_mode;
       if (md == LCF_T_NONE) {
         for (int i = lane; i < n; i += 32) wts[i] = 1.0;
@@ -705,6 +778,14 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       } else if (md == LCF_T_SIGMOID) {
         kk = ep_rule_k(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
         for (int i = lane; i < n; i += 32) wts[i] = 1.0 / (1.0 + exp(-g.beta * ((i + 1) - kk)));
+      } else if (md == LCF_T_LEARNED) {
+        if (sh_lp >= g.mlp_pmin) {
+          kk = sh_lk;
+        } else {
+          kk = ep_rule_k(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+          fallback = 1;
+        }
+        for (int i = lane; i < n; i += 32) wts[i] = (i + 1 > kk) ? 1.0 : 0.0;
       } else {   // LCF_T_ADAPTIVE_SOFT
         double mx = -INFINITY;
         for (int i = lane; i < n; i += 32) {
@@ -723,7 +804,8 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       if (lane == 0) {
         const double pdsum = g.pd_mode == 0 ? S / n : S;
         double al;
-        int fl = (converged ? 0 : LCF_WFLAG_NOCONV) | ((sweeps < 255 ? sweeps : 255) << LCF_WFLAG_SWEEP_SHIFT);
+        int fl = (converged ? 0 : LCF_WFLAG_NOCONV) | (fallback ? LCF_WFLAG_FALLBACK : 0) |
+                 ((sweeps < 255 ? sweeps : 255) << LCF_WFLAG_SWEEP_SHIFT);
         if (g.alpha_mode == 1) al = 1.0;
         else {
           const Box bx = boxes[k];
@@ -880,6 +962,8 @@ cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st) {
   a.curv_norm = c.curv_norm; a.max_sweeps = c.max_sweeps; a.ncp = P->ncp;
   a.err = P->ws.err;
   a.clk = P->profiling ? P->ws.evd_clk : nullptr;
+  a.wz = c.wz; a.wx = c.wx;
+  a.mlp_w = P->ws.mlp_w; a.mlp_b = P->ws.mlp_b; a.mlp_h = P->mlp_hidden; a.mlp_pmin = P->mlp_pmin;
   evd_pair_kernel<<<2 * P->nd, EP_THREADS, evd_pair_smem_bytes(P->nt), st>>>(
       P->ws.R, P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt, P->ws.kcut, P->ws.alpha, P->ws.flags, P->ws.W,
       P->ws.ncol);

@@ -55,7 +55,9 @@ static lcf_status validate(const lcf_config* c) {
   if (c->nz <= 0 || c->nx <= 0 || c->nt < 2 || c->wz <= 0 || c->wx <= 0) return LCF_EINVAL;
   if (c->wz > c->nz || c->wx > c->nx) return LCF_EINVAL;
   if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
-  if (c->thresh_mode < LCF_T_FIXED || c->thresh_mode > LCF_T_NONE) return LCF_EINVAL;
+  if (c->thresh_mode < LCF_T_FIXED || c->thresh_mode > LCF_T_LEARNED) return LCF_EINVAL;
+  if (c->thresh_mode == LCF_T_LEARNED && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
+  if (c->thresh_mode == LCF_T_LEARNED && c->evd_path != LCF_EVD_PAIR) return LCF_EUNSUPPORTED;
   if (c->thresh_mode == LCF_T_SIGMOID && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
   if (!isfinite(c->beta) || !isfinite(c->beta_src)) return LCF_EINVAL;
   if (c->pd_mode < 0 || c->pd_mode > 1 || c->alpha_mode < 0 || c->alpha_mode > 2) return LCF_EINVAL;
@@ -118,7 +120,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
-                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.iq_stage, w.pd_stage};
+                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -274,6 +276,7 @@ static cudaEvent_t prof_event(lcf_plan* P, int b) {
 static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   const bool tc = c.gram_path == LCF_PATH_TC;
+  if (c.thresh_mode == LCF_T_LEARNED && P->mlp_hidden == 0) return LCF_EINVAL;   // no network set
   LCF_MARK(LCF_STAGE_PREP);
   LCF_CUDA(launch_basis(P, iq, st));
   LCF_CUDA(launch_center(P, iq, st));

@@ -1,6 +1,7 @@
 // lcf_internal.cuh — plan layout, double-float helpers and kernel entry
 // points shared by the library's translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,8 @@ __host__ __device__ inline int deflate_count(int nt) {
 // double-float congruence, fp32 conversion + Q, Jacobi, sort + phase fix,
 // thresholding rule, projection weights.
 constexpr int kEvdPhases = 8;
+// Widest hidden layer of the learned cutoff rule (its activations live in shared memory).
+constexpr int kMlpHiddenMax = 256;
 // Calls whose stage events are kept between profile reads.
 constexpr int kProfCalls = 4096;
 
@@ -66,6 +69,9 @@ struct Workspace {
   unsigned char* bimg = nullptr;  // [nd] pre-split weight images (fp16 hi/lo, MMA layout)
   float* bscale = nullptr;    // [nd] power-of-two scale of each weight image
   long long* evd_clk = nullptr;  // [nd][kEvdPhases+1] EVD phase clocks (profiling only)
+  // learned cutoff rule (set by lcf_plan_set_mlp)
+  __nv_bfloat16* mlp_w = nullptr;   // W1 | W2 | W3 | W4, bf16
+  float* mlp_b = nullptr;           // b1 | b2 | b3 | b4
   // host-call staging
   float2* iq_stage = nullptr; // [nt][nz][nx] device copy for lcf_filter_host
   float* pd_stage = nullptr;  // [nz][nx]
@@ -86,6 +92,8 @@ struct lcf_plan {
   int gram_nsplit = 1;  // pixel splits per window
   int ncp = 0;          // padded projection columns
   int ptiles_z = 0, ptiles_x = 0;   // tensor-core projection tiles (8 x 16 pixels)
+  int mlp_hidden = 0;   // hidden width of the plan's learned rule (0: none set)
+  float mlp_pmin = 0.f; // confidence below which the learned rule falls back to k_src
   int sm_count = 0;
   std::vector<lcf::Box> boxes;
   lcf::Workspace ws;
@@ -208,6 +216,9 @@ cudaError_t gram_tc_configure();
 size_t gram_tc_smem_bytes(int na);
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);
+cudaError_t mlp_plan_weights(const lcf_mlp* N, __nv_bfloat16* w, float* b, cudaStream_t st);
+size_t mlp_plan_weight_count(int nt, int hidden);
+size_t mlp_plan_bias_count(int nt, int hidden);
 cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st);
 cudaError_t evd_pair_configure();
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
