@@ -149,6 +149,78 @@ def reference_arm(args):
     return 0
 
 
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_2405_11105_b300", "weights", "learned_384x256x128_16x16.npy")
+
+
+def learned_workload(args):
+    """384x256 px, Nt=128, 16x16 windows: the learned cutoff on a 2-sweep EVD against method 1 on
+    the converged EVD (its fallback and judge), same kernels otherwise."""
+    import numpy as np
+    import torch
+    import paper_2405_11105_b300 as L
+    from synth import LEARNED_384x256x128, generate_packet
+    nz, nx, nt, wz, wx = 384, 256, 128, 16, 16
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    ring = np.stack([generate_packet(LEARNED_384x256x128, seed=50000 + i) for i in range(4)])   # 403 MB > L2
+    d_ring = torch.from_numpy(ring).to(f"cuda:{local}")
+    out = torch.empty((nz, nx), dtype=torch.float32, device=f"cuda:{local}")
+    common = dict(device=local, gram_path=L.LCF_PATH_SIMT, project_path=L.LCF_PATH_TC, evd_path=L.LCF_EVD_PAIR)
+    judge = L.Plan.make(nz, nx, nt, wz, wx, thresh_mode=L.LCF_T_CURVATURE, beta=1.0, **common)
+    meta = json.load(open(os.path.splitext(LEARNED_WEIGHTS)[0] + ".json"))
+    fast = L.Plan.make(nz, nx, nt, wz, wx, thresh_mode=L.LCF_T_LEARNED, k_src=L.LCF_T_CURVATURE, beta_src=1.0,
+                       max_sweeps=meta["fast_sweeps"], **common)
+    net = L.Mlp(nt, hidden=meta["hidden"], max_batch=1, device=local)
+    net.set_params(np.load(LEARNED_WEIGHTS))
+    fast.set_mlp(net, p_min=0.5)
+    st = torch.cuda.current_stream()
+
+    def timed(plan):
+        for i in range(args.warmup):
+            plan.filter(d_ring[i % 4], out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(args.steps):
+            plan.filter(d_ring[i % 4], out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    with ClockSampler(local) as clk:
+        ms_fast = timed(fast)
+    ms_judge = timed(judge)
+    db, agree, fb = [], [], 0
+    for i in range(4):
+        a = judge.filter(d_ring[i]).cpu().numpy().astype(np.float64)
+        b = fast.filter(d_ring[i]).cpu().numpy().astype(np.float64)
+        m = a >= a.max() * 1e-3
+        db.append(float(np.mean(np.abs(10 * np.log10(b[m] / a[m])))))
+        agree.append(float(np.mean(judge.debug()["k"] == fast.debug()["k"])))
+        fb += int(np.sum(np.asarray(fast.status()[1]) & L.LCF_WFLAG_FALLBACK != 0))
+    fast.profile(True)
+    timed(fast)
+    stages, n = fast.profile_read()
+    fast.profile(False)
+    line = {"metric": "power-Doppler frames/s (384x256 px, Nt=128, 16x16 subsets), learned cutoff vs method 1",
+            "value": args.steps / (ms_fast / 1e3), "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_fast / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (MLP: bf16 weights, f32 accumulate)",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": "384x256 px x Nt=128, 16x16 windows, learned cutoff on a "
+                                   f"{meta['fast_sweeps']}-sweep EVD", "l2": "ring of 4 packets (403 MB) > L2"},
+            "method1_converged": {"value": args.steps / (ms_judge / 1e3), "unit": "frames/s",
+                                  "ms_per_step": ms_judge / args.steps},
+            "speedup_vs_method1": ms_judge / ms_fast,
+            "pd_db_error": {"mean_abs_db": float(np.mean(db)), "max_packet_mean_abs_db": float(np.max(db)),
+                            "pixels": "PD >= 1e-3 x max of the method-1 image"},
+            "cutoff_agreement": float(np.mean(agree)), "fallback_windows": fb, "windows": 4 * wz * wx,
+            "stage_ms_per_launch": {k: v / max(n, 1) for k, v in stages.items()},
+            "training": meta, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -157,10 +229,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="tc", choices=["simt", "tc"])
     ap.add_argument("--cpu-packets", type=int, default=10)
+    ap.add_argument("--workload", default="realtime", choices=["realtime", "learned"],
+                    help="realtime: 256x128x100 8x8 (the headline); learned: 384x256x128 16x16 with the learned cutoff")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "learned":
+        return learned_workload(args)
 
     import numpy as np
     import torch
