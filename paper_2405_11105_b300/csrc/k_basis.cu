@@ -90,34 +90,41 @@ global_gram_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int zs
     }
 }
 
-// One CTA of 256 threads.  smem: G (nt*nt float2) + Y, Z (nt*d float2 each).
+// Packets up to this length keep G in shared memory; longer ones read it from
+// the (L2-resident) reduced partial sums.
+constexpr int kBasisSmemNt = 128;
+
+// One CTA of 256 threads.  smem: G (nt*nt float2, nt <= kBasisSmemNt) + Y, Z (nt*d float2 each).
+// part: split 0 holds the full sum (upper triangle) when nsplit == 1.
 __global__ void __launch_bounds__(256)
 basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, float2* __restrict__ phi,
              unsigned* __restrict__ xmax) {
   extern __shared__ float2 bsm[];
-  float2* G = bsm;                       // nt*nt
-  float2* Y = G + (size_t)nt * nt;       // nt*d, column j at Y[t*d + j]
+  const bool gsm = nt <= kBasisSmemNt;
+  float2* G = bsm;                                   // nt*nt (shared-memory mode)
+  float2* Y = gsm ? G + (size_t)nt * nt : bsm;       // nt*d, column j at Y[t*d + j]
   float2* Z = Y + (size_t)nt * nd_defl;
   __shared__ float gmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, d = nd_defl;
   if (tid == 0) *xmax = 0u;   // the centring kernel's atomicMax target for this packet
-  for (int e = tid; e < nt * nt; e += blockDim.x) {
-    int i = e / nt, j = e % nt;
-    bool up = i <= j;
-    int r = up ? i : j, c = up ? j : i;
+  // entry (t, u) of the summed global Gram (Hermitian, from its upper triangle)
+  auto gsum = [&](int t, int u) {
+    const bool up = t <= u;
+    const int r = up ? t : u, c = up ? u : t;
     float2 acc = make_float2(0.f, 0.f);
     for (int s = 0; s < nsplit; ++s) acc = cadd(acc, part[(size_t)s * nt * nt + (size_t)r * nt + c]);
-    G[e] = up ? acc : cconj(acc);
-  }
-  __syncthreads();
+    return up ? acc : cconj(acc);
+  };
   if (tid == 0) {
     float m = 0.f;
-    for (int i = 0; i < nt; ++i) m = fmaxf(m, G[i * nt + i].x);
+    for (int i = 0; i < nt; ++i) m = fmaxf(m, gsum(i, i).x);
     gmax = m > 0.f ? m : 1.f;
   }
   __syncthreads();
   const float inv = 1.f / gmax;
-  for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = cscale(G[e], inv);
+  if (gsm) {
+    for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = cscale(gsum(e / nt, e % nt), inv);
+  }
   // DCT-II start
   for (int e = tid; e < nt * d; e += blockDim.x) {
     int t = e / d, j = e % d;
@@ -129,7 +136,10 @@ basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, f
     for (int e = tid; e < nt * d; e += blockDim.x) {
       int t = e / d, j = e % d;
       float2 acc = make_float2(0.f, 0.f);
-      for (int u = 0; u < nt; ++u) acc = cadd(acc, cmul(G[t * nt + u], Y[u * d + j]));
+      if (gsm)
+        for (int u = 0; u < nt; ++u) acc = cadd(acc, cmul(G[t * nt + u], Y[u * d + j]));
+      else
+        for (int u = 0; u < nt; ++u) acc = cadd(acc, cmul(cscale(gsum(t, u), inv), Y[u * d + j]));
       Z[e] = acc;
     }
     __syncthreads();
@@ -173,7 +183,9 @@ __global__ void basis_reduce_kernel(float2* __restrict__ part, int nsplit, int n
   part[e] = acc;
 }
 
-size_t basis_smem_bytes(int nt, int nd_defl) { return ((size_t)nt * nt + 2 * (size_t)nt * nd_defl) * sizeof(float2); }
+size_t basis_smem_bytes(int nt, int nd_defl) {
+  return ((nt <= kBasisSmemNt ? (size_t)nt * nt : 0) + 2 * (size_t)nt * nd_defl) * sizeof(float2);
+}
 
 cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st) {
   const lcf_config& c = P->cfg;
@@ -195,7 +207,7 @@ cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st) {
 
 cudaError_t basis_configure() {
   return cudaFuncSetAttribute(basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)basis_smem_bytes(kEvdNmax, kDeflateMax));
+                              (int)basis_smem_bytes(kBasisSmemNt, kDeflateMax));
 }
 
 }  // namespace lcf

@@ -261,6 +261,12 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
 
 size_t gram_aug_smem_bytes(int nt, int nd_defl) { return (size_t)ACH * (nt + nd_defl) * sizeof(float2); }
 
+// the augmented-column kernel's staging passes 48 KB beyond Nt = 188
+cudaError_t gram_simt_configure() {
+  return cudaFuncSetAttribute(gram_aug_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
+}
+
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st) {
   dim3 grid(P->aug_nsplit, P->nd);
   gram_aug_kernel<<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
@@ -318,14 +324,14 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
         Q[c][a] = make_double2(h.x, -h.y);
       }
   __syncthreads();
-  double2 wv[2];
-  static_assert(kEvdNmax * kDeflateMax <= 512, "W rows per thread");
-  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 512)
+  constexpr int WPT = (kEvdNmax * kDeflateMax + 255) / 256;   // W entries per thread (blockDim 256)
+  double2 wv[WPT];
+  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 512)
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
   }
   __syncthreads();
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < WPT; ++u) {
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
   }

@@ -295,13 +295,14 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     Q[a][c] = make_double2(sx, sy);
   }
   __syncthreads();
-  double2 wv[2];
-  for (int u = 0; u < 2; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 496 < 512)
+  constexpr int WPT = (kEvdNmax * kDeflateMax + 255) / 256;   // W entries per thread (blockDim 256)
+  double2 wv[WPT];
+  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 496 < 512)
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
   }
   __syncthreads();
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < WPT; ++u) {
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
   }

@@ -131,6 +131,7 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   if (!g_scratch_ready[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LCF_ECUDA;
+    if (gram_simt_configure() != cudaSuccess) return LCF_ECUDA;   // long packets stage > 48 KB
     g_scratch_addr[dev] = p;
     g_scratch_ready[dev] = true;
   }

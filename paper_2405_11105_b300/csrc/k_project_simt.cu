@@ -68,12 +68,88 @@ project_simt_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int n
   if (cg == 0 && x < nx) out[(size_t)z * nx + x] = pd;
 }
 
+// Packets longer than 128 frames: 32-pixel row segments, the window's weights
+// streamed through shared memory in blocks of 64 rows x 128 columns (eight
+// groups of 16 columns per pixel), |.|^2 summed over the column blocks.
+__global__ void __launch_bounds__(256)
+project_simt_long_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int nd,
+                         const Box* __restrict__ boxes, const float* __restrict__ gz,
+                         const float* __restrict__ gx, const float2* __restrict__ W,
+                         const int* __restrict__ ncol, int ncp, float* __restrict__ out) {
+  extern __shared__ float2 sm[];
+  float2* Ss = sm;              // [nt][32]
+  float2* Wc = sm + nt * 32;    // [64][128]
+  __shared__ float red[8][32];
+  const int z = blockIdx.y, xb = blockIdx.x * 32;
+  const int tid = threadIdx.x, pix = tid & 31, cg = tid >> 5;
+  const int x = xb + pix;
+  const size_t npix = (size_t)nz * nx;
+  for (int e = tid; e < nt * 32; e += 256) {
+    const int t = e >> 5, pp = e & 31, xx = xb + pp;
+    Ss[e] = xx < nx ? iq[t * npix + (size_t)z * nx + xx] : make_float2(0.f, 0.f);
+  }
+  float pd = 0.f;
+  for (int k = 0; k < nd; ++k) {
+    const Box b = boxes[k];
+    if (z < b.z0 || z >= b.z1 || xb + 31 < b.x0 || xb >= b.x1) continue;
+    const int nc = ncol[k];
+    if (nc == 0) continue;
+    const float2* Wk = W + (size_t)k * nt * ncp;
+    float part = 0.f;
+    for (int c0 = 0; c0 < nc; c0 += 128) {
+      float2 y[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) y[c] = make_float2(0.f, 0.f);
+      for (int t0 = 0; t0 < nt; t0 += 64) {
+        __syncthreads();
+        for (int e = tid; e < 64 * 128; e += 256) {
+          const int tt = e >> 7, cc = e & 127;
+          Wc[e] = (t0 + tt < nt && c0 + cc < nc) ? Wk[(size_t)(t0 + tt) * ncp + c0 + cc] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const int tn = nt - t0 < 64 ? nt - t0 : 64;
+        const float2* wrow = Wc + cg * 16;
+        for (int tt = 0; tt < tn; ++tt) {
+          const float2 sv = Ss[(t0 + tt) * 32 + pix];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const float2 w = wrow[tt * 128 + c];
+            y[c].x = fmaf(sv.x, w.x, fmaf(-sv.y, w.y, y[c].x));
+            y[c].y = fmaf(sv.x, w.y, fmaf(sv.y, w.x, y[c].y));
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) part += y[c].x * y[c].x + y[c].y * y[c].y;
+    }
+    __syncthreads();
+    red[cg][pix] = part;
+    __syncthreads();
+    if (cg == 0) {
+      const float g = (x < nx) ? gz[(size_t)k * nz + z] * gx[(size_t)k * nx + x] : 0.f;
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += red[q][pix];
+      pd += g * g * acc;
+    }
+  }
+  if (cg == 0 && x < nx) out[(size_t)z * nx + x] = pd;
+}
+
+size_t project_long_smem_bytes(int nt) { return (size_t)nt * 32 * 8 + 64 * 128 * 8; }
+
 int project_cpt(int nt) { return nt <= 32 ? 8 : (nt <= 64 ? 16 : (nt <= 112 ? 28 : 32)); }
 
 size_t project_smem_bytes(int nt, int ncp) { return (size_t)nt * 64 * 8 + (size_t)nt * ncp * 8; }
 
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
+  if (P->nt > kProjectShortNmax) {
+    dim3 g2((c.nx + 31) / 32, c.nz);
+    project_simt_long_kernel<<<g2, 256, project_long_smem_bytes(P->nt), st>>>(
+        iq, c.nz, c.nx, P->nt, P->nd, P->ws.box, P->ws.gz, P->ws.gx, P->ws.W, P->ws.ncol, P->ncp, out);
+    return counted(P);
+  }
   dim3 grid((c.nx + 63) / 64, c.nz);
   size_t sm = project_smem_bytes(P->nt, P->ncp);
   int cpt = project_cpt(P->nt);
@@ -93,7 +169,7 @@ cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out,
 }
 
 cudaError_t project_configure() {
-  size_t mx = project_smem_bytes(kEvdNmax, kEvdNmax);
+  size_t mx = project_smem_bytes(kProjectShortNmax, 4 * project_cpt(kProjectShortNmax));
   cudaError_t e = cudaFuncSetAttribute(project_simt_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(project_simt_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
@@ -101,6 +177,9 @@ cudaError_t project_configure() {
     e = cudaFuncSetAttribute(project_simt_kernel<28>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(project_simt_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(project_simt_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)project_long_smem_bytes(kEvdNmax));
   return e;
 }
 

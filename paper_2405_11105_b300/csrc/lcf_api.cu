@@ -57,7 +57,9 @@ static lcf_status validate(const lcf_config* c) {
   if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
   if (c->thresh_mode < LCF_T_FIXED || c->thresh_mode > LCF_T_LEARNED) return LCF_EINVAL;
   if (c->thresh_mode == LCF_T_LEARNED && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
-  if (c->thresh_mode == LCF_T_LEARNED && c->evd_path != LCF_EVD_PAIR) return LCF_EUNSUPPORTED;
+  if (c->thresh_mode == LCF_T_LEARNED && (c->evd_path != LCF_EVD_PAIR || c->nt > kEvdPairNmax))
+    return LCF_EUNSUPPORTED;
+  if (c->project_path == LCF_PATH_TC && c->nt > kProjectShortNmax) return LCF_EUNSUPPORTED;
   if (c->thresh_mode == LCF_T_SIGMOID && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
   if (!isfinite(c->beta) || !isfinite(c->beta_src)) return LCF_EINVAL;
   if (c->pd_mode < 0 || c->pd_mode > 1 || c->alpha_mode < 0 || c->alpha_mode > 2) return LCF_EINVAL;
@@ -120,7 +122,8 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
-                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.iq_stage, w.pd_stage};
+                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.evd_B, w.evd_vh, w.evd_t,
+                  w.evd_scale, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -169,7 +172,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     long ts = (pmax + 2047) / 2048;   // ~2048 pixels per tensor-core CTA
     P->tc_nsplit = (int)(ts < 1 ? 1 : (ts > 64 ? 64 : ts));
   }
-  P->ncp = 4 * project_cpt(P->nt);
+  P->ncp = P->nt <= kProjectShortNmax ? 4 * project_cpt(P->nt) : (P->nt + 15) / 16 * 16;
   std::vector<float> gz, gx;
   build_geometry(*cfg, P->boxes, gz, gx);
 
@@ -200,6 +203,13 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.flags, nd, &tot);
   if (e == cudaSuccess) e = dalloc(&w.W, nd * nt * P->ncp, &tot);
   if (e == cudaSuccess) e = dalloc(&w.ncol, nd, &tot);
+  if (cfg->evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) {
+    const size_t m = P->nt < kEvdHead ? P->nt : kEvdHead;
+    if (e == cudaSuccess) e = dalloc(&w.evd_B, nd * nt * nt, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.evd_vh, nd * m * nt, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.evd_t, nd * m * m, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.evd_scale, nd, &tot);
+  }
   std::vector<int> toff, twin;
   if (cfg->project_path == LCF_PATH_TC) {
     project_tc_tiles(P, &P->ptiles_z, &P->ptiles_x, toff, twin);
@@ -235,6 +245,8 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = basis_configure();
     if (e == cudaSuccess) e = project_tc_configure();
     if (e == cudaSuccess) e = evd_pair_configure();
+    if (e == cudaSuccess) e = evd_dist_configure();
+    if (e == cudaSuccess) e = gram_simt_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
   }
   if (e != cudaSuccess) {
@@ -291,7 +303,8 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   if (tc) LCF_CUDA(launch_gram_assemble_tc(P, st));
   else LCF_CUDA(launch_gram_assemble(P, st));
   LCF_MARK(LCF_STAGE_EVD);
-  if (c.evd_path == LCF_EVD_PAIR) LCF_CUDA(launch_evd_pair(P, st));
+  if (c.evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) LCF_CUDA(launch_evd_dist(P, st));
+  else if (c.evd_path == LCF_EVD_PAIR) LCF_CUDA(launch_evd_pair(P, st));
   else LCF_CUDA(launch_evd(P, st));
   LCF_MARK(LCF_STAGE_PROJECT);
   if (c.project_path == LCF_PATH_TC) LCF_CUDA(launch_project_tc(P, out, st));

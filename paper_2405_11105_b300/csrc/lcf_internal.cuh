@@ -11,11 +11,17 @@
 
 namespace lcf {
 
-// Largest packet length of the library (the CTA-pair EVD keeps A in one SM's
-// shared memory and V in its partner's).
-constexpr int kEvdNmax = 128;
+// Largest packet length of the library (the distributed EVD spreads A and V
+// over a cluster of up to 8 CTAs).
+constexpr int kEvdNmax = 320;
+// Largest packet length of the CTA-pair EVD (A in one SM's shared memory, V
+// in its partner's); longer packets use the distributed EVD.
+constexpr int kEvdPairNmax = 128;
 // Largest packet length of the one-CTA EVD (A and V in one SM's shared memory).
 constexpr int kEvdCtaNmax = 112;
+// Longest packet of the shared-memory-resident projections (CUDA-core with the
+// whole W_k in shared memory; tensor-core with the tile's rows resident).
+constexpr int kProjectShortNmax = 128;
 // Largest augmented row (Nt + deflation vectors) of the tensor-core Gram (one M = 128 tile).
 constexpr int kTcGramNaMax = 128;
 // Subspace-iteration block of the EVD (head directions isolated exactly).
@@ -69,6 +75,11 @@ struct Workspace {
   unsigned char* bimg = nullptr;  // [nd] pre-split weight images (fp16 hi/lo, MMA layout)
   float* bscale = nullptr;    // [nd] power-of-two scale of each weight image
   long long* evd_clk = nullptr;  // [nd][kEvdPhases+1] EVD phase clocks (profiling only)
+  // distributed EVD (Nt > kEvdPairNmax)
+  float2* evd_B = nullptr;    // [nd][nt][nt] B = Q^H (R/scale) Q, fp32
+  float2* evd_vh = nullptr;   // [nd][m][nt] Householder vectors of Q
+  float2* evd_t = nullptr;    // [nd][m][m] compact WY factor T
+  double* evd_scale = nullptr;// [nd] power-of-two scale (0: degenerate window)
   // learned cutoff rule (set by lcf_plan_set_mlp)
   __nv_bfloat16* mlp_w = nullptr;   // W1 | W2 | W3 | W4, bf16
   float* mlp_b = nullptr;           // b1 | b2 | b3 | b4
@@ -207,6 +218,7 @@ inline cudaError_t counted(const lcf_plan* P, int n = 1) {
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st);
 size_t gram_aug_smem_bytes(int nt, int nd_defl);
+cudaError_t gram_simt_configure();
 cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st);
 cudaError_t basis_configure();
 cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st);
@@ -220,6 +232,8 @@ cudaError_t mlp_plan_weights(const lcf_mlp* N, __nv_bfloat16* w, float* b, cudaS
 size_t mlp_plan_weight_count(int nt, int hidden);
 size_t mlp_plan_bias_count(int nt, int hidden);
 cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_evd_dist(const lcf_plan* P, cudaStream_t st);
+cudaError_t evd_dist_configure();
 cudaError_t evd_pair_configure();
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
 cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st);
