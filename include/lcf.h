@@ -141,7 +141,11 @@ lcf_status lcf_filter_host(lcf_plan* plan, const void* h_iq, float* h_out_pd, cu
 /* Sliding-packet processing (packets of nt frames every `stride` frames, as
  * the paper's real-time processing does).  d_frames: device frames
  * [n_frames][nz][nx] complex64; d_out_pd: [n_packets][nz][nx] with
- * n_packets = (n_frames - nt) / stride + 1.  Asynchronous. */
+ * n_packets = (n_frames - nt) / stride + 1.  Asynchronous.  All packets run
+ * as one CUDA graph: the first call with a given (d_frames, n_frames, stride,
+ * d_out_pd) captures it on a plan-owned stream (this first call allocates the
+ * graph; later calls with the same buffers only launch it on `stream`).  While
+ * stage profiling is on, the packets are launched one by one instead. */
 lcf_status lcf_filter_stream(lcf_plan* plan, const void* d_frames, int n_frames, int stride,
                              float* d_out_pd, cudaStream_t stream);
 

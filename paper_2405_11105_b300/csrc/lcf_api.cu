@@ -400,9 +400,48 @@ extern "C" lcf_status lcf_filter_stream(lcf_plan* P, const void* d_frames, int n
   DeviceGuard g(P->device);
   const int npk = (n_frames - P->nt) / stride + 1;
   const float2* fr = (const float2*)d_frames;
-  for (int i = 0; i < npk; ++i) {
-    lcf_status s = run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, stream);
-    if (s != LCF_OK) return s;
+  if (P->profiling) {   // stage events need the packets launched one by one
+    for (int i = 0; i < npk; ++i) {
+      lcf_status s = run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, stream);
+      if (s != LCF_OK) return s;
+    }
+  } else {
+    // every packet of the stream in one CUDA graph, captured on the plan's own stream the first
+    // time these buffers are seen and replayed on `stream` afterwards
+    const bool hit = P->sg_exec && P->sg_frames == d_frames && P->sg_out == d_out_pd && P->sg_n == n_frames &&
+                     P->sg_stride == stride;
+    if (!hit) {
+      if (P->sg_exec) {
+        cudaGraphExecDestroy(P->sg_exec);
+        P->sg_exec = nullptr;
+      }
+      if (!P->cap_stream) LCF_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+      const long long l0 = P->launches;
+      LCF_CUDA(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+      lcf_status s = LCF_OK;
+      for (int i = 0; i < npk && s == LCF_OK; ++i)
+        s = run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, P->cap_stream);
+      cudaGraph_t gr = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &gr);
+      P->sg_launches = P->launches - l0;
+      P->launches = l0;
+      if (s != LCF_OK || ce != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return s != LCF_OK ? s : LCF_ECUDA;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&P->sg_exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) {
+        P->sg_exec = nullptr;
+        return LCF_ECUDA;
+      }
+      P->sg_frames = d_frames;
+      P->sg_out = d_out_pd;
+      P->sg_n = n_frames;
+      P->sg_stride = stride;
+    }
+    LCF_CUDA(cudaGraphLaunch(P->sg_exec, stream));
+    P->launches += P->sg_launches;
   }
   P->last_stream = stream;
   P->last_iq = (void*)(fr + (size_t)(npk - 1) * stride * P->npix);
@@ -486,6 +525,8 @@ extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
   DeviceGuard g(P->device);
   free_ws(P->ws);
   for (auto& e : P->prof_ev) cudaEventDestroy(e);
+  if (P->sg_exec) cudaGraphExecDestroy(P->sg_exec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   delete P;
   return LCF_OK;
 }

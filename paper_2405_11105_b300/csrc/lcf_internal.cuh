@@ -114,6 +114,13 @@ struct lcf_plan {
   // stage profiling: events[call % kProfCalls][stage boundary]
   // kernels this plan has launched (every launcher adds its own)
   mutable long long launches = 0;
+  // the last stream of packets, captured as one CUDA graph (lcf_filter_stream)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t sg_exec = nullptr;
+  const void* sg_frames = nullptr;
+  float* sg_out = nullptr;
+  int sg_n = 0, sg_stride = 0;
+  long long sg_launches = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;
   long prof_calls = 0;
