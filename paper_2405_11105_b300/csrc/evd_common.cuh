@@ -168,4 +168,51 @@ __device__ inline int ep_rule_k(int mode, const double* lam, int n, double beta,
 }
 
 
+// ---- cyclic round-robin ordering over np (even) indices in h = np/2 pair slots ----
+// At step r (0 <= r < np-1) slot i holds ((r + i) mod (np-1), (r - i) mod (np-1)), slot 0 (r, np-1).
+// Returns the slot of index x and sets its partner.
+__device__ __forceinline__ int ep_slot(int x, int r, int np, int h, int& partner) {
+  const int M = np - 1;
+  if (x == M) { partner = r; return 0; }
+  int i = x - r;
+  if (i < 0) i += M;                        // x = (r + i) mod M
+  if (i < h) {
+    partner = i == 0 ? M : (r - i < 0 ? r - i + M : r - i);
+    return i;
+  }
+  const int i2 = M - i;                     // x = (r - i2) mod M, 1 <= i2 < h
+  partner = r + i2 >= M ? r + i2 - M : r + i2;
+  return i2;
+}
+
+// Complex Jacobi rotation for the Hermitian 2x2 block [[app, b], [conj(b), aqq]] (p < q):
+// rotate unless |b| <= tol sqrt(|app aqq|); c real, st = s b/|b|; new diagonal dp, dq.
+// 1/sqrt and 1/x by the hardware approximation plus one Newton-Raphson step.
+__device__ __forceinline__ void ep_rotation(float app, float aqq, float2 b, float tol, float& c, float2& st,
+                                            float& dp, float& dq, int& rot) {
+  const float b2 = b.x * b.x + b.y * b.y;
+  c = 1.f;
+  st = make_float2(0.f, 0.f);
+  dp = app;
+  dq = aqq;
+  rot = 0;
+  if (b2 > 0.f && b2 > (tol * tol) * fabsf(app * aqq)) {
+    const float ib = ep_rsqrt(b2), ab = b2 * ib;   // 1/|b|, |b|
+    const float zeta = 0.5f * (aqq - app) * ib;
+    float t;
+    if (fabsf(zeta) > 1e18f) {
+      t = 0.5f * ep_rcp(zeta);
+    } else {
+      const float z2 = fmaf(zeta, zeta, 1.f);
+      t = copysignf(ep_rcp(fabsf(zeta) + z2 * ep_rsqrt(z2)), zeta);   // 1 / (|zeta| + sqrt(1 + zeta^2))
+    }
+    c = ep_rsqrt(fmaf(t, t, 1.f));
+    const float sib = t * c * ib;
+    st = make_float2(sib * b.x, sib * b.y);
+    dp = fmaf(-t, ab, app);
+    dq = fmaf(t, ab, aqq);
+    rot = 1;
+  }
+}
+
 }  // namespace lcf

@@ -467,29 +467,9 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
           if (i == 0) { pa = r; pb = np - 1; }
           else { pa = (r + i) % (np - 1); pb = (r - i + np - 1) % (np - 1); }
           const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
-          const float app = A[p * ld + p].x, aqq = A[q * ld + q].x;
-          const float2 b = A[p * ld + q];
-          const float b2 = cabs2(b);
-          float c = 1.f, dp = app, dq = aqq;
-          float2 st = make_float2(0.f, 0.f);
-          // rotate unless |b_pq| <= tol sqrt(|b_pp b_qq|)  (squared form)
-          if (b2 > 0.f && b2 > (EP_TOL * EP_TOL) * fabsf(app * aqq)) {
-            const float ib = ep_rsqrt(b2), ab = b2 * ib;         // 1/|b|, |b|
-            const float zeta = 0.5f * (aqq - app) * ib;
-            float t;
-            if (fabsf(zeta) > 1e18f) {
-              t = 0.5f * ep_rcp(zeta);
-            } else {
-              const float z2 = fmaf(zeta, zeta, 1.f);
-              t = copysignf(ep_rcp(fabsf(zeta) + z2 * ep_rsqrt(z2)), zeta);   // 1 / (|zeta| + sqrt(1 + zeta^2))
-            }
-            c = ep_rsqrt(fmaf(t, t, 1.f));
-            const float sib = t * c * ib;
-            st = make_float2(sib * b.x, sib * b.y);
-            dp = fmaf(-t, ab, app);
-            dq = fmaf(t, ab, aqq);
-            rot = 1;
-          }
+          float c, dp, dq;
+          float2 st;
+          ep_rotation(A[p * ld + p].x, A[q * ld + q].x, A[p * ld + q], EP_TOL, c, st, dp, dq, rot);
           rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)p | ((unsigned)q << 8) | (rot ? EP_REC_ROT : 0u)));
           pr[i] = rec;
           prd[i] = make_float2(dp, dq);
@@ -514,22 +494,29 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
             const float2 d = prd[ia];
             A[pa * ld + pa] = make_float2(d.x, 0.f);
             A[qa * ld + qa] = make_float2(d.y, 0.f);
-            A[pa * ld + qa] = make_float2(0.f, 0.f);
-            A[qa * ld + pa] = make_float2(0.f, 0.f);
+            A[pa * ld + qa] = make_float2(0.f, 0.f);   // pa < qa: the kept entry
             continue;
           }
+          // only the upper triangle is kept: an entry below the diagonal is the conjugate of its mirror
           const float ca = ra.x, cb = rb.x;
           const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
-          const float2 x00 = A[pa * ld + pb], x01 = A[pa * ld + qb], x10 = A[qa * ld + pb], x11 = A[qa * ld + qb];
+          const int o00 = pa < pb ? pa * ld + pb : pb * ld + pa, o01 = pa < qb ? pa * ld + qb : qb * ld + pa;
+          const int o10 = qa < pb ? qa * ld + pb : pb * ld + qa, o11 = qa < qb ? qa * ld + qb : qb * ld + qa;
+          float2 x00 = A[o00], x01 = A[o01], x10 = A[o10], x11 = A[o11];
+          if (pa > pb) x00 = cconj(x00);
+          if (pa > qb) x01 = cconj(x01);
+          if (qa > pb) x10 = cconj(x10);
+          if (qa > qb) x11 = cconj(x11);
           const float2 sbc = cconj(sb);
           const float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
           const float2 y10 = csub(cscale(x10, cb), cmul(sbc, x11)), y11 = cadd(cmul(sb, x10), cscale(x11, cb));
           const float2 sac = cconj(sa);
           const float2 z00 = csub(cscale(y00, ca), cmul(sa, y10)), z01 = csub(cscale(y01, ca), cmul(sa, y11));
           const float2 z10 = cadd(cmul(sac, y00), cscale(y10, ca)), z11 = cadd(cmul(sac, y01), cscale(y11, ca));
-          A[pa * ld + pb] = z00; A[pa * ld + qb] = z01; A[qa * ld + pb] = z10; A[qa * ld + qb] = z11;
-          A[pb * ld + pa] = cconj(z00); A[qb * ld + pa] = cconj(z01);
-          A[pb * ld + qa] = cconj(z10); A[qb * ld + qa] = cconj(z11);
+          A[o00] = pa < pb ? z00 : cconj(z00);
+          A[o01] = pa < qb ? z01 : cconj(z01);
+          A[o10] = qa < pb ? z10 : cconj(z10);
+          A[o11] = qa < qb ? z11 : cconj(z11);
         }
         __syncthreads();
       }
@@ -703,6 +690,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     // CTA 1: V = Q, the streamed rotations, phase fix, V and W out
     // =====================================================================
     float2* Vt = reinterpret_cast<float2*>(smem + L.vt);
+    const int ldv = np;   // even: entries (rr, rr + 1) of a row of V^T form one 16-byte word
     const float4* ring = reinterpret_cast<const float4*>(smem + L.ring);
     const float2* Vh = reinterpret_cast<const float2*>(smem + L.vh);
     const float2* Tv = reinterpret_cast<const float2*>(smem + L.tv);
@@ -716,27 +704,33 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     }
     __syncthreads();
     // Vt[c][a] = Q[a][c] = delta_ac - sum_j VT[a][j] conj(Vh[c][j])
-    for (int e = tid; e < np * ld; e += EP_THREADS) {
-      const int c = e / ld, a = e % ld;
+    for (int e = tid; e < np * ldv; e += EP_THREADS) {
+      const int c = e / ldv, a = e % ldv;
       float2 v = make_float2(c == a ? 1.f : 0.f, 0.f);
       if (a < n && c < n)
         for (int j = 0; j < m; ++j) v = csub(v, cmul(VT[a * m + j], cconj(Vh[(size_t)j * ldy + c])));
       Vt[e] = v;
     }
     __syncthreads();
-    // work items: (pair, V row), rows consecutive across lanes
-    constexpr int MAXV = (kEvdPairNmax * (kEvdPairNmax / 2) + EP_THREADS - 1) / EP_THREADS;
+    // work items: (pair, two consecutive V rows), row pairs consecutive across lanes
+    constexpr int MAXV = ((kEvdPairNmax / 2) * (kEvdPairNmax / 2) + EP_THREADS - 1) / EP_THREADS;
     int vit[MAXV];
     for (int j = 0; j < MAXV; ++j) {
       const int e = tid + j * EP_THREADS;
-      vit[j] = (e < n * h) ? (((e / n) << 8) | (e % n)) : -1;
+      vit[j] = (e < h * h) ? (((e / h) << 8) | (2 * (e % h))) : -1;
     }
+    __shared__ int sh_vok;
     const uint32_t ebar_r = ep_mapa(ep_smem(smem + L.ebar), peer);
     for (int hs = 0;; ++hs) {
       const int slot = hs % EP_RING;
-      if (tid == 0) ep_arrive_expect_tx(&fbar[slot], (uint32_t)(h * 16));   // the step's h records
-      ok = __syncthreads_and(ep_wait(&fbar[slot], (hs / EP_RING) & 1));
+      if (tid == 0) {   // one thread polls; the others acquire the completed phase after the barrier
+        ep_arrive_expect_tx(&fbar[slot], (uint32_t)(h * 16));   // the step's h records
+        sh_vok = ep_wait(&fbar[slot], (hs / EP_RING) & 1);
+      }
+      __syncthreads();
+      ok = sh_vok != 0;
       if (!ok) break;
+      ep_try(&fbar[slot], (hs / EP_RING) & 1);
       const float4* rs = ring + (size_t)slot * h;
       if (__float_as_uint(rs[0].w) & EP_REC_END) break;
 #pragma unroll
@@ -749,9 +743,16 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
         const int p = mt & 255, q = (mt >> 8) & 255;
         const float c = rc.x;
         const float2 s = make_float2(rc.y, rc.z);
-        const float2 vp = Vt[p * ld + rr], vq = Vt[q * ld + rr];
-        Vt[p * ld + rr] = csub(cscale(vp, c), cmul(cconj(s), vq));
-        Vt[q * ld + rr] = cadd(cmul(s, vp), cscale(vq, c));
+        float4* pp = reinterpret_cast<float4*>(Vt + p * ldv + rr);
+        float4* qq = reinterpret_cast<float4*>(Vt + q * ldv + rr);
+        const float4 P4 = *pp, Q4 = *qq;
+        const float2 vp0 = make_float2(P4.x, P4.y), vp1 = make_float2(P4.z, P4.w);
+        const float2 vq0 = make_float2(Q4.x, Q4.y), vq1 = make_float2(Q4.z, Q4.w);
+        const float2 sc = cconj(s);
+        const float2 np0 = csub(cscale(vp0, c), cmul(sc, vq0)), np1 = csub(cscale(vp1, c), cmul(sc, vq1));
+        const float2 nq0 = cadd(cmul(s, vp0), cscale(vq0, c)), nq1 = cadd(cmul(s, vp1), cscale(vq1, c));
+        *pp = make_float4(np0.x, np0.y, np1.x, np1.y);
+        *qq = make_float4(nq0.x, nq0.y, nq1.x, nq1.y);
       }
       __syncthreads();
       if (tid == 0) ep_arrive_remote(ebar_r + (uint32_t)(slot * 8));
@@ -768,7 +769,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       float best = -1.f;
       int bi = 0;
       for (int a = lane; a < n; a += 32) {
-        const float mg = cabs2(Vt[col * ld + a]);
+        const float mg = cabs2(Vt[col * ldv + a]);
         if (mg > best) { best = mg; bi = a; }
       }
       for (int o = 16; o; o >>= 1) {
@@ -777,7 +778,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (lane == 0) {
-        const float2 v = Vt[col * ld + bi];
+        const float2 v = Vt[col * ldv + bi];
         const float mg = sqrtf(cabs2(v));
         phs[jj] = mg > 0.f ? make_float2(v.x / mg, -v.y / mg) : make_float2(1.f, 0.f);
       }
@@ -785,7 +786,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     __syncthreads();
     for (int e = tid; e < n * n; e += EP_THREADS) {
       const int a = e / n, jj = e % n;
-      V_out[(size_t)k * n * n + e] = cmul(Vt[rperm[jj] * ld + a], phs[jj]);
+      V_out[(size_t)k * n * n + e] = cmul(Vt[rperm[jj] * ldv + a], phs[jj]);
     }
     const int nc = rkeep[0];
     for (int e = tid; e < n * g.ncp; e += EP_THREADS) {
@@ -793,7 +794,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       float2 v = make_float2(0.f, 0.f);
       if (c < nc) {
         const int jj = rkeep[1 + c];
-        v = cscale(cmul(Vt[rperm[jj] * ld + t], phs[jj]), rcoef[jj]);
+        v = cscale(cmul(Vt[rperm[jj] * ldv + t], phs[jj]), rcoef[jj]);
       }
       W_out[(size_t)k * n * g.ncp + e] = v;
     }
