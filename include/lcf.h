@@ -280,6 +280,14 @@ lcf_status lcf_mlp_destroy(lcf_mlp* mlp);
  * Synchronous. */
 lcf_status lcf_plan_set_mlp(lcf_plan* plan, const lcf_mlp* mlp, float p_min);
 
+/* Self-test of the device-side failure path (no counterpart in the paper):
+ * one CTA waits on an mbarrier phase that nothing completes, with the bounded
+ * wait every kernel of the library uses, for at most limit_ns (<= 2 s); the
+ * kernel records the timeout and returns, the context stays usable.  Returns
+ * LCF_ETIMEOUT when the wait ran out (the expected outcome), writes the time
+ * waited (seconds, host) to *waited_s if not NULL.  Synchronous. */
+lcf_status lcf_selftest_wait_timeout(int device, unsigned long long limit_ns, double* waited_s);
+
 /* Number of kernels the plan has launched since it was created (every
  * filter call adds the launches of its stages; debug dumps add theirs).
  * *n (host) receives the count.  No synchronisation. */

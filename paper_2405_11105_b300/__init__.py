@@ -80,6 +80,7 @@ def _load():
         "lcf_mlp_adamw": ([vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, vp], C.c_int),
         "lcf_mlp_destroy": ([vp], C.c_int),
         "lcf_plan_set_mlp": ([vp, vp, C.c_float], C.c_int),
+        "lcf_selftest_wait_timeout": ([C.c_int, C.c_ulonglong, dp], C.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -342,3 +343,10 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def selftest_wait_timeout(limit_s: float = 0.05, device: int = 0):
+    """Run the bounded-wait self-test kernel; returns (status, seconds waited)."""
+    w = C.c_double()
+    st = _lib.lcf_selftest_wait_timeout(int(device), int(limit_s * 1e9), C.byref(w))
+    return st, w.value
