@@ -5,7 +5,7 @@
 // before the FP32 / tensor-core partial sums.  The tissue's slow-time
 // behaviour is shared by the whole field of view (global motion), so the top
 // d eigenvectors of a global Gram G = sum_p s_p^H s_p (taken over every
-// fourth image row) capture it: after deflation the residual is blood and
+// eighth image row) capture it: after deflation the residual is blood and
 // noise, and the rounding of the partial sums (including the tensor core's
 // round-toward-zero accumulation) is relative to that small residual.
 //
@@ -24,9 +24,9 @@ namespace lcf {
 
 constexpr int BG_T = 64;        // tile side
 constexpr int BG_CH = 32;       // pixels staged per step
-constexpr int BASIS_ITERS = 5;
+constexpr int BASIS_ITERS = 4;
 
-__host__ __device__ inline int basis_zstep(int nz) { return nz >= 16 ? 4 : 1; }
+__host__ __device__ inline int basis_zstep(int nz) { return nz >= 64 ? 8 : (nz >= 16 ? 4 : 1); }
 
 // grid: x = upper-triangle tile pair, y = pixel split.  Pixels: rows z = 0, zs, 2zs, ...
 __global__ void __launch_bounds__(256)
@@ -115,15 +115,20 @@ basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, f
     for (int s = 0; s < nsplit; ++s) acc = cadd(acc, part[(size_t)s * nt * nt + (size_t)r * nt + c]);
     return up ? acc : cconj(acc);
   };
-  if (tid == 0) {
+  if (gsm) {
+    for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = gsum(e / nt, e % nt);
+    __syncthreads();
+  }
+  if (warp == 0) {   // largest diagonal entry
     float m = 0.f;
-    for (int i = 0; i < nt; ++i) m = fmaxf(m, gsum(i, i).x);
-    gmax = m > 0.f ? m : 1.f;
+    for (int i = lane; i < nt; i += 32) m = fmaxf(m, gsm ? G[i * nt + i].x : gsum(i, i).x);
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(~0u, m, o));
+    if (lane == 0) gmax = m > 0.f ? m : 1.f;
   }
   __syncthreads();
   const float inv = 1.f / gmax;
   if (gsm) {
-    for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = cscale(gsum(e / nt, e % nt), inv);
+    for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = cscale(G[e], inv);
   }
   // DCT-II start
   for (int e = tid; e < nt * d; e += blockDim.x) {

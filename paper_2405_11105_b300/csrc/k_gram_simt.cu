@@ -21,48 +21,61 @@ namespace lcf {
 // xa[t][p] = c_p(t) = s_p(t) - sum_j a_pj phi_j(t) (t < nt), xa[nt+j][p] = a_pj.
 // If xmax_bits is given, the largest |component| written is max-reduced into it
 // (non-negative floats order like their bit patterns).
-__global__ void center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi,
-                              float2* __restrict__ xa, int nt, int nd_defl, int npix, unsigned* xmax_bits) {
-  const int p0 = blockIdx.x * blockDim.x + threadIdx.x;
-  float mx = 0.f;
-  if (p0 < npix) {
-  const int p = p0;
+// A CTA is 64 pixels x 4 slow-time phases (t = sub mod 4, one phase per pair of
+// warps): a warp reads 32 consecutive pixels of one frame, and four times as many
+// loads are in flight as with one thread per pixel.
+__global__ void __launch_bounds__(256)
+center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, float2* __restrict__ xa, int nt,
+              int nd_defl, int npix, unsigned* xmax_bits) {
+  __shared__ float2 red[4][kDeflateMax][64];
+  const int pix = threadIdx.x & 63, sub = threadIdx.x >> 6;
+  const int p = blockIdx.x * 64 + pix;
+  const bool valid = p < npix;
   float2 a[kDeflateMax];
 #pragma unroll
   for (int j = 0; j < kDeflateMax; ++j) a[j] = make_float2(0.f, 0.f);
+  if (valid) {
 #pragma unroll 4
-  for (int t = 0; t < nt; ++t) {
-    float2 v = iq[(size_t)t * npix + p];
+    for (int t = sub; t < nt; t += 4) {
+      const float2 v = iq[(size_t)t * npix + p];
 #pragma unroll
-    for (int j = 0; j < kDeflateMax; ++j)
-      if (j < nd_defl) {
-        float2 f = phi[j * nt + t];          // a_j += conj(phi_j(t)) s(t)
-        a[j].x = fmaf(f.x, v.x, fmaf(f.y, v.y, a[j].x));
-        a[j].y = fmaf(f.x, v.y, fmaf(-f.y, v.x, a[j].y));
-      }
+      for (int j = 0; j < kDeflateMax; ++j)
+        if (j < nd_defl) {
+          const float2 f = phi[j * nt + t];   // a_j += conj(phi_j(t)) s(t)
+          a[j].x = fmaf(f.x, v.x, fmaf(f.y, v.y, a[j].x));
+          a[j].y = fmaf(f.x, v.y, fmaf(-f.y, v.x, a[j].y));
+        }
+    }
   }
-#pragma unroll 4
-  for (int t = 0; t < nt; ++t) {
-    float2 v = iq[(size_t)t * npix + p];
 #pragma unroll
-    for (int j = 0; j < kDeflateMax; ++j)
-      if (j < nd_defl) {
-        float2 f = phi[j * nt + t];          // c(t) = s(t) - a_j phi_j(t)
-        v.x = fmaf(-a[j].x, f.x, fmaf(a[j].y, f.y, v.x));
-        v.y = fmaf(-a[j].x, f.y, fmaf(-a[j].y, f.x, v.y));
-      }
-    xa[(size_t)t * npix + p] = v;
-    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-  }
+  for (int j = 0; j < kDeflateMax; ++j) red[sub][j][pix] = a[j];
+  __syncthreads();
 #pragma unroll
   for (int j = 0; j < kDeflateMax; ++j)
-    if (j < nd_defl) {
-      xa[(size_t)(nt + j) * npix + p] = a[j];
-      mx = fmaxf(mx, fmaxf(fabsf(a[j].x), fabsf(a[j].y)));
+    a[j] = cadd(cadd(red[0][j][pix], red[1][j][pix]), cadd(red[2][j][pix], red[3][j][pix]));
+  float mx = 0.f;
+  if (valid) {
+#pragma unroll 4
+    for (int t = sub; t < nt; t += 4) {
+      float2 v = iq[(size_t)t * npix + p];
+#pragma unroll
+      for (int j = 0; j < kDeflateMax; ++j)
+        if (j < nd_defl) {
+          const float2 f = phi[j * nt + t];   // c(t) = s(t) - a_j phi_j(t)
+          v.x = fmaf(-a[j].x, f.x, fmaf(a[j].y, f.y, v.x));
+          v.y = fmaf(-a[j].x, f.y, fmaf(-a[j].y, f.x, v.y));
+        }
+      xa[(size_t)t * npix + p] = v;
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    if (sub < nd_defl) {
+      const float2 c = a[sub];
+      xa[(size_t)(nt + sub) * npix + p] = c;
+      mx = fmaxf(mx, fmaxf(fabsf(c.x), fabsf(c.y)));
     }
   }
   if (xmax_bits) {
-    unsigned m = __reduce_max_sync(~0u, __float_as_uint(mx));
+    const unsigned m = __reduce_max_sync(~0u, __float_as_uint(mx));
     if ((threadIdx.x & 31) == 0) atomicMax(xmax_bits, m);
   }
 }
@@ -72,7 +85,7 @@ cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st) 
   // the basis kernel, launched before this one, has zeroed the packet maximum
   const bool tc = P->cfg.gram_path == LCF_PATH_TC || P->cfg.project_path == LCF_PATH_TC;
   unsigned* xm = tc ? P->ws.xmax : nullptr;
-  center_kernel<<<(n + 127) / 128, 128, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
+  center_kernel<<<(n + 63) / 64, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
   return counted(P);
 }
 

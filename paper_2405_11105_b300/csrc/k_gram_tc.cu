@@ -43,23 +43,39 @@ constexpr int TG_NBH_MAX = 128;
 __host__ __device__ inline int tc_nbh(int na) { return (na + 7) / 8 * 8; }
 __host__ __device__ inline int tc_rows_hi(int nbh) { return 2 * nbh > 128 ? 2 * nbh : 128; }
 
-size_t gram_tc_smem_bytes(int na) {
+// fp32 slab staging (cp.async, one stage ahead of the split): 2 buffers of TG_PX pixels x (na + 1) rows
+__host__ __device__ inline size_t tc_raw_bytes(int na) { return (size_t)2 * TG_PX * (na + 1) * 8; }
+size_t gram_tc_smem_bytes_n(int na, int nstg) {
   int nbh = tc_nbh(na), rh = tc_rows_hi(nbh);
   size_t hi = (size_t)rh * TG_K * 2, lo = (size_t)2 * nbh * TG_K * 2;
-  return TG_STAGES * (hi + lo) + 1024 + 2 * TG_PX * 8;
+  return nstg * (hi + lo) + 1024 + tc_raw_bytes(na);
 }
+// MMA operand stages: three when they fit beside the fp32 staging, else two
+int gram_tc_stages(int na) { return gram_tc_smem_bytes_n(na, TG_STAGES) <= 232448 ? TG_STAGES : 2; }
+size_t gram_tc_smem_bytes(int na) { return gram_tc_smem_bytes_n(na, gram_tc_stages(na)); }
+
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src, bool valid) {
+  // 8-byte asynchronous copy; an invalid source copies nothing and zero-fills
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_u32(dst_smem)), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(TG_THREADS, 1)
 gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box* __restrict__ boxes,
                const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
-               int nsplit, double* __restrict__ part, int* __restrict__ err) {
+               int nsplit, int nstg, double* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t mma_bar[TG_STAGES];
   __shared__ __align__(8) uint64_t acc_bar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int pix_s[TG_PX];
-  __shared__ float gg_s[TG_PX];
+  __shared__ int pix_s[3][TG_PX];     // stage s uses buffer s % 3
+  __shared__ float gg_s[3][TG_PX];
+  __shared__ unsigned char ok_s[3][TG_PX];
 
   const int k = blockIdx.y, s = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -76,12 +92,14 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
   const float* gxk = gx + (size_t)k * nx;
   const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
 
+  const int rld = na + 1;   // fp32 slab row stride (odd: fewer bank conflicts in the split)
+  float2* raw = reinterpret_cast<float2*>(smem + nstg * st_bytes);   // [2][TG_PX][rld]
   // zero all stage buffers (padding rows stay zero)
-  for (size_t e = tid; e < TG_STAGES * st_bytes / 16; e += TG_THREADS)
+  for (size_t e = tid; e < nstg * st_bytes / 16; e += TG_THREADS)
     reinterpret_cast<uint4*>(smem)[e] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
-    for (int i = 0; i < TG_STAGES; ++i) tc::mbar_init(&mma_bar[i], 1);
+    for (int i = 0; i < nstg; ++i) tc::mbar_init(&mma_bar[i], 1);
     tc::mbar_init(&acc_bar[0], 1);
     tc::mbar_init(&acc_bar[1], 1);
   }
@@ -101,64 +119,97 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
     if (ok) ok = tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);   // after a timeout, no further waits
     tc::fence_after();
     const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
+    // two 16-column loads in flight per wait
 #pragma unroll
-    for (int cc = 0; cc < TG_NBH_MAX / 16; ++cc) {
+    for (int cc = 0; cc < TG_NBH_MAX / 16; cc += 2) {
       if (cc * 16 < nbh) {
-        float v[16];
-        tc::tmem_ld16(base + cc * 16, v);
+        uint32_t v0[16], v1[16];
+        tc::tmem_ld16_async(base + cc * 16, v0);
+        if ((cc + 1) * 16 < nbh) tc::tmem_ld16_async(base + (cc + 1) * 16, v1);
+        tc::tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += v[j];
+        for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += __uint_as_float(v0[j]);
+        if ((cc + 1) * 16 < nbh) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sums[(cc + 1) * 16 + j] += __uint_as_float(v1[j]);
+        }
       }
     }
     tc::fence_before();
   };
 
+  // pixel index and window weight of the slab of stage i (threads < TG_PX)
+  auto slab_pix = [&](int i) {
+    const long l = l0 + (long)i * TG_PX + tid;
+    int p = 0;
+    float g = 0.f;
+    const bool v = i < nst && l < l1;
+    if (v) {
+      const int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
+      p = z * nx + x;
+      g = gzk[z] * gxk[x] * sc;
+    }
+    pix_s[i % 3][tid] = p;
+    gg_s[i % 3][tid] = g;
+    ok_s[i % 3][tid] = v;
+  };
+  // asynchronous copy of stage i's fp32 slab into raw buffer i & 1 (rows r of pixel pp at [pp][r])
+  auto slab_copy = [&](int i) {
+    const int* px = pix_s[i % 3];
+    const unsigned char* vk = ok_s[i % 3];
+    float2* dst = raw + (size_t)(i & 1) * TG_PX * rld;
+    for (int e = tid; e < TG_PX * na; e += TG_THREADS) {
+      const int r = e / TG_PX, pp = e % TG_PX;
+      cp_async8(dst + pp * rld + r, xa + (size_t)r * npix + px[pp], vk[pp] != 0);
+    }
+    cp_async_commit();
+  };
+  if (tid < TG_PX) { slab_pix(0); slab_pix(1); }
+  __syncthreads();
+  if (nst > 0) slab_copy(0);
+
+  int next_epi = 0;   // first chunk whose accumulator is still to be read
   for (int i = 0; i < nst; ++i) {
-    const int si = i % TG_STAGES;
+    const int si = i % nstg;
     unsigned char* Bhi = smem + si * st_bytes;
     unsigned char* Blo = Bhi + hi_bytes;
-    if (i >= TG_STAGES && ok) ok = tc::mbar_wait(&mma_bar[si], ((i / TG_STAGES) - 1) & 1);
-    if (tid < TG_PX) {
-      long l = l0 + (long)i * TG_PX + tid;
-      int p = 0;
-      float g = 0.f;
-      if (l < l1) {
-        int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
-        p = z * nx + x;
-        g = gzk[z] * gxk[x] * sc;
-      }
-      pix_s[tid] = p;
-      gg_s[tid] = g;
+    if (i + 1 < nst) {   // the next slab's copy overlaps this one's split and MMAs
+      slab_copy(i + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
-    __syncthreads();
+    __syncthreads();   // slab i complete for every thread
+    if (tid < TG_PX) slab_pix(i + 2);
+    if (i >= nstg && ok) ok = tc::mbar_wait(&mma_bar[si], ((i / nstg) - 1) & 1);
     {
-      // Each thread owns one pixel pp of the slab and rows r = 8j + lane/4: all of
-      // its loads are issued first (independent), then split and stored.  Lanes
-      // cover (row%8, pixel%4), so the 4-byte stores of a warp fill distinct banks.
-      const int pp = ((tid >> 5) & 7) * 4 + (lane & 3), rl = lane >> 2;
-      const float g = gg_s[pp];
-      const float2* src = xa + pix_s[pp];
-      constexpr int RMAX = (TG_NBH_MAX + 7) / 8;
-      float2 v[RMAX];
-#pragma unroll
-      for (int j = 0; j < RMAX; ++j) {
-        const int r = 8 * j + rl;
-        v[j] = (r < na) ? src[(size_t)r * npix] : make_float2(0.f, 0.f);
-      }
+      // Each thread owns two adjacent pixels (pp, pp + 1) of the slab and rows r = 16j + lane/2:
+      // their four K entries (re, im, re, im) are 8 contiguous bytes of a core-matrix row.
+      // A warp's 8-byte stores cover 16 rows x 2 pixel pairs: two wavefronts, no further conflicts.
+      const int pp = 2 * (((tid >> 5) & 7) * 2 + (lane & 1)), rl = lane >> 1;
+      const float g0 = gg_s[i % 3][pp], g1 = gg_s[i % 3][pp + 1];
+      const float2* src0 = raw + (size_t)(i & 1) * TG_PX * rld + pp * rld;
+      const float2* src1 = src0 + rld;
       const int kk = 2 * pp;
-#pragma unroll
-      for (int j = 0; j < RMAX; ++j) {
-        const int r = 8 * j + rl;
-        if (r < na) {
-          __half hr, lr, hm, lm;
-          tc::split_f16(v[j].x * g, hr, lr);
-          tc::split_f16(v[j].y * g, hm, lm);
-          *reinterpret_cast<__half2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = __halves2half2(hr, hm);
-          *reinterpret_cast<__half2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(hm, __hneg(hr));
-          const __half lr2 = __hmul(lr, __float2half(2.f)), lm2 = __hmul(lm, __float2half(2.f));
-          *reinterpret_cast<__half2*>(Blo + tc::op_off(r, kk, TG_SBO)) = __halves2half2(lr2, lm2);
-          *reinterpret_cast<__half2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = __halves2half2(lm2, __hneg(lr2));
-        }
+#pragma unroll 4
+      for (int r = rl; r < na; r += 16) {   // independent rows interleaved: two warps per scheduler need ILP
+        const float2 v0 = src0[r], v1 = src1[r];
+        __half hr0, lr0, hm0, lm0, hr1, lr1, hm1, lm1;
+        tc::split_f16(v0.x * g0, hr0, lr0);
+        tc::split_f16(v0.y * g0, hm0, lm0);
+        tc::split_f16(v1.x * g1, hr1, lr1);
+        tc::split_f16(v1.y * g1, hm1, lm1);
+        const __half two = __float2half(2.f);
+        const __half lr0b = __hmul(lr0, two), lm0b = __hmul(lm0, two), lr1b = __hmul(lr1, two), lm1b = __hmul(lm1, two);
+        __half2 w[2];
+        w[0] = __halves2half2(hr0, hm0); w[1] = __halves2half2(hr1, hm1);
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        w[0] = __halves2half2(hm0, __hneg(hr0)); w[1] = __halves2half2(hm1, __hneg(hr1));
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        w[0] = __halves2half2(lr0b, lm0b); w[1] = __halves2half2(lr1b, lm1b);
+        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        w[0] = __halves2half2(lm0b, __hneg(lr0b)); w[1] = __halves2half2(lm1b, __hneg(lr1b));
+        *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
       }
     }
     tc::fence_proxy_async();
@@ -178,9 +229,12 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
       tc::mma_commit(&mma_bar[si]);
       if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
     }
-    if (i % TG_CPA == 0 && c > 0) epilogue(c - 1);
+    // Chunk c-1's accumulator is read half-way through chunk c, when its MMAs have long
+    // completed (reading it right after its last MMA would stall every thread on them);
+    // chunk c+1, which reuses that accumulator, starts later.
+    if (i % TG_CPA == TG_CPA / 2 && c > 0) { epilogue(c - 1); next_epi = c; }
   }
-  if (nst > 0) epilogue((nst - 1) / TG_CPA);
+  for (int e = next_epi; nst > 0 && e <= (nst - 1) / TG_CPA; ++e) epilogue(e);
   if (!ok && lane == 0) atomicOr(err, 1);
 
   // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na)
@@ -322,7 +376,7 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   dim3 grid(P->tc_nsplit, P->nd);
   gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
                                                                     P->ws.gx, P->ws.xmax, P->tc_nsplit,
-                                                                    P->ws.gtc, P->ws.err);
+                                                                    gram_tc_stages(na), P->ws.gtc, P->ws.err);
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
   gram_q_kernel<<<dim3(P->q_nsplit, P->nd), 256, 0, st>>>(P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->ws.box,
@@ -359,8 +413,9 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
 }
 
 cudaError_t gram_tc_configure() {
-  return cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)gram_tc_smem_bytes(kTcGramNaMax));
+  size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
+  for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
+  return cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 
 }  // namespace lcf

@@ -149,7 +149,7 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   noalloc_basis_kernel<<<1, 256, 0, stream>>>((int)nt, ndefl, phi);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
-  center_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, stream>>>((const float2*)d_iq, phi, xa, (int)nt, ndefl,
+  center_kernel<<<(unsigned)((npix + 63) / 64), 256, 0, stream>>>((const float2*)d_iq, phi, xa, (int)nt, ndefl,
                                                                     (int)npix, nullptr);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   gram_aug_kernel<<<dim3(1, (unsigned)nd), 256, gram_aug_smem_bytes((int)nt, ndefl), stream>>>(

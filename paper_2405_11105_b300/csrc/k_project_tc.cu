@@ -57,10 +57,10 @@ static int project_tc_ksps(int nt, int nd_defl) {
 
 // ---------------------------------------------------------------------------
 // Weight images.  One CTA per window: the augmented block [W ; Phi^T W]
-// (rows t < Nt: W, rows Nt + j: phi_j^T W, in FP64), scaled by a power of two
+// (rows t < Nt: W, rows Nt + j: phi_j^T W, double-float sums), scaled by a power of two
 // into fp16 range and split hi/lo, laid out k-step by k-step in the exact
 // shared-memory image the MMA reads.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, const float2* __restrict__ phi,
                     int nt, int nd_defl, int ncp, int k16, int n16max, unsigned char* __restrict__ bimg,
                     float* __restrict__ bscale) {
@@ -68,16 +68,16 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
   const int nc = ncol[k], n16 = pt_n16(nc);
   const float2* Wk = W + (size_t)k * nt * ncp;
   __shared__ float2 PW[kDeflateMax][kEvdNmax];   // phi_j^T W(:, c)
-  __shared__ float red[8];
-  for (int e = tid; e < nd_defl * nc; e += blockDim.x) {
+  __shared__ float red[16];
+  for (int e = tid; e < nd_defl * nc; e += blockDim.x) {   // phi_j^T W(:, c), double-float sums
     const int j = e / nc, c = e % nc;
-    double sr = 0.0, si = 0.0;
+    df sr = {0.f, 0.f}, si = {0.f, 0.f};
     for (int t = 0; t < nt; ++t) {
       const float2 f = phi[j * nt + t], w = Wk[(size_t)t * ncp + c];
-      sr += (double)f.x * w.x - (double)f.y * w.y;
-      si += (double)f.x * w.y + (double)f.y * w.x;
+      sr = df_add(sr, df_add(two_prod_df(f.x, w.x), df_neg(two_prod_df(f.y, w.y))));
+      si = df_add(si, df_add(two_prod_df(f.x, w.y), two_prod_df(f.y, w.x)));
     }
-    PW[j][c] = make_float2((float)sr, (float)si);
+    PW[j][c] = make_float2(sr.hi + sr.lo, si.hi + si.lo);
   }
   __syncthreads();
   float m = 0.f;
@@ -102,21 +102,29 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
   if (tid == 0) bscale[k] = s;
   unsigned char* img = bimg + (size_t)k * (k16 / 16) * pt_kstep_bytes(n16max);
   const int kb = pt_kstep_bytes(n16), sub = n16 * 32;
-  for (int e = tid; e < k16 * n16; e += blockDim.x) {
-    const int t = e / n16, c = e % n16;
-    float2 v = make_float2(0.f, 0.f);
-    if (c < nc) {
-      if (t < nt) v = Wk[(size_t)t * ncp + c];
-      else if (t < nt + nd_defl) v = PW[t - nt][c];
+  // one item = 8 consecutive rows t of column c: one 16-byte core-matrix row of each sub-image
+  for (int e = tid; e < (k16 / 8) * n16; e += blockDim.x) {
+    const int o = e / n16, c = e % n16, t0 = 8 * o;
+    __align__(16) __half hr[8];
+    __align__(16) __half lr[8];
+    __align__(16) __half hi[8];
+    __align__(16) __half li[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < nc) {
+        if (t < nt) v = Wk[(size_t)t * ncp + c];
+        else if (t < nt + nd_defl) v = PW[t - nt][c];
+      }
+      tc::split_f16(v.x * s, hr[u], lr[u]);
+      tc::split_f16(v.y * s, hi[u], li[u]);
     }
-    __half hr, lr, hi, li;
-    tc::split_f16(v.x * s, hr, lr);
-    tc::split_f16(v.y * s, hi, li);
-    unsigned char* base = img + (size_t)(t >> 4) * kb + pt_b_off(c, t & 15);
-    *reinterpret_cast<__half*>(base) = hr;
-    *reinterpret_cast<__half*>(base + sub) = lr;
-    *reinterpret_cast<__half*>(base + 2 * sub) = hi;
-    *reinterpret_cast<__half*>(base + 3 * sub) = li;
+    unsigned char* base = img + (size_t)(t0 >> 4) * kb + pt_b_off(c, t0 & 15);
+    *reinterpret_cast<uint4*>(base) = *reinterpret_cast<const uint4*>(hr);
+    *reinterpret_cast<uint4*>(base + sub) = *reinterpret_cast<const uint4*>(lr);
+    *reinterpret_cast<uint4*>(base + 2 * sub) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(base + 3 * sub) = *reinterpret_cast<const uint4*>(li);
   }
 }
 
@@ -289,14 +297,16 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
       tc::fence_after();
       const uint32_t base = tbase + (uint32_t)(buf * PT_ACC) + ((uint32_t)((warp & 3) * 32) << 16);
       float acc = 0.f;
-      for (int c = 0; c < n16; c += 16) {
-        float v[16];
-        tc::tmem_ld16(base + c, v);
+      for (int c = 0; c < n16; c += 16) {   // Yr and Yi columns c..c+15, one wait for both
+        uint32_t vr[16], vi[16];
+        tc::tmem_ld16_async(base + c, vr);
+        tc::tmem_ld16_async(base + 128 + c, vi);
+        tc::tmem_wait_ld();
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc = fmaf(v[u], v[u], acc);
-        tc::tmem_ld16(base + 128 + c, v);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) acc = fmaf(v[u], v[u], acc);
+        for (int u = 0; u < 16; ++u) {
+          const float a = __uint_as_float(vr[u]), b2 = __uint_as_float(vi[u]);
+          acc = fmaf(a, a, fmaf(b2, b2, acc));
+        }
       }
       tc::fence_before();
       tc::mbar_arrive(&acce[buf]);
@@ -319,7 +329,7 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
 cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   const int k16 = pt_k16(P->nt, P->ndefl), n16max = pt_n16(P->nt);
-  project_prep_kernel<<<P->nd, 256, 0, st>>>(P->ws.W, P->ws.ncol, P->ws.phi, P->nt, P->ndefl, P->ncp, k16, n16max,
+  project_prep_kernel<<<P->nd, 512, 0, st>>>(P->ws.W, P->ws.ncol, P->ws.phi, P->nt, P->ndefl, P->ncp, k16, n16max,
                                              P->ws.bimg, P->ws.bscale);
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
