@@ -154,7 +154,7 @@ LEARNED_WEIGHTS = os.path.join(ROOT, "paper_2405_11105_b300", "weights", "learne
 
 def learned_workload(args):
     """384x256 px, Nt=128, 16x16 windows: the learned cutoff on a 2-sweep EVD against method 1 on
-    the converged EVD (its fallback and judge), same kernels otherwise."""
+    the converged EVD (its fallback and its reference), same kernels otherwise."""
     import numpy as np
     import torch
     import paper_2405_11105_b300 as L
@@ -165,8 +165,8 @@ def learned_workload(args):
     ring = np.stack([generate_packet(LEARNED_384x256x128, seed=50000 + i) for i in range(4)])   # 403 MB > L2
     d_ring = torch.from_numpy(ring).to(f"cuda:{local}")
     out = torch.empty((nz, nx), dtype=torch.float32, device=f"cuda:{local}")
-    common = dict(device=local, gram_path=L.LCF_PATH_SIMT, project_path=L.LCF_PATH_TC, evd_path=L.LCF_EVD_PAIR)
-    judge = L.Plan.make(nz, nx, nt, wz, wx, thresh_mode=L.LCF_T_CURVATURE, beta=1.0, **common)
+    common = dict(device=local, gram_path=L.LCF_PATH_TC, project_path=L.LCF_PATH_TC, evd_path=L.LCF_EVD_PAIR)
+    conv = L.Plan.make(nz, nx, nt, wz, wx, thresh_mode=L.LCF_T_CURVATURE, beta=1.0, **common)
     meta = json.load(open(os.path.splitext(LEARNED_WEIGHTS)[0] + ".json"))
     fast = L.Plan.make(nz, nx, nt, wz, wx, thresh_mode=L.LCF_T_LEARNED, k_src=L.LCF_T_CURVATURE, beta_src=1.0,
                        max_sweeps=meta["fast_sweeps"], **common)
@@ -189,14 +189,14 @@ def learned_workload(args):
 
     with ClockSampler(local) as clk:
         ms_fast = timed(fast)
-    ms_judge = timed(judge)
+    ms_conv = timed(conv)
     db, agree, fb = [], [], 0
     for i in range(4):
-        a = judge.filter(d_ring[i]).cpu().numpy().astype(np.float64)
+        a = conv.filter(d_ring[i]).cpu().numpy().astype(np.float64)
         b = fast.filter(d_ring[i]).cpu().numpy().astype(np.float64)
         m = a >= a.max() * 1e-3
         db.append(float(np.mean(np.abs(10 * np.log10(b[m] / a[m])))))
-        agree.append(float(np.mean(judge.debug()["k"] == fast.debug()["k"])))
+        agree.append(float(np.mean(conv.debug()["k"] == fast.debug()["k"])))
         fb += int(np.sum(np.asarray(fast.status()[1]) & L.LCF_WFLAG_FALLBACK != 0))
     fast.profile(True)
     timed(fast)
@@ -209,9 +209,9 @@ def learned_workload(args):
             "data": "synthetic", "impl": "ours",
             "config": {"workload": "384x256 px x Nt=128, 16x16 windows, learned cutoff on a "
                                    f"{meta['fast_sweeps']}-sweep EVD", "l2": "ring of 4 packets (403 MB) > L2"},
-            "method1_converged": {"value": args.steps / (ms_judge / 1e3), "unit": "frames/s",
-                                  "ms_per_step": ms_judge / args.steps},
-            "speedup_vs_method1": ms_judge / ms_fast,
+            "method1_converged": {"value": args.steps / (ms_conv / 1e3), "unit": "frames/s",
+                                  "ms_per_step": ms_conv / args.steps},
+            "speedup_vs_method1": ms_conv / ms_fast,
             "pd_db_error": {"mean_abs_db": float(np.mean(db)), "max_packet_mean_abs_db": float(np.max(db)),
                             "pixels": "PD >= 1e-3 x max of the method-1 image"},
             "cutoff_agreement": float(np.mean(agree)), "fallback_windows": fb, "windows": 4 * wz * wx,

@@ -215,4 +215,38 @@ __device__ __forceinline__ void ep_rotation(float app, float aqq, float2 b, floa
   }
 }
 
+// The same rotation from two reciprocal square roots: with d = aqq - app and
+// x = d^2 + 4|b|^2, cos 2theta = |d| / sqrt(x), c^2 = y = (1 + cos 2theta) / 2,
+//   st = sgn(d) b / (sqrt(x) c),   t|b| = sgn(d) |b|^2 / (sqrt(x) y),
+// which equals the tangent form's t = sgn(d) / (|zeta| + sqrt(1 + zeta^2)) (zeta = d / 2|b|),
+// c = 1 / sqrt(1 + t^2), st = t c b / |b|.  x below 2^-100 takes the tangent form.
+__device__ __forceinline__ void ep_rotation2(float app, float aqq, float2 b, float tol, float& c, float2& st,
+                                             float& dp, float& dq, int& rot) {
+  const float b2 = b.x * b.x + b.y * b.y;
+  c = 1.f;
+  st = make_float2(0.f, 0.f);
+  dp = app;
+  dq = aqq;
+  rot = 0;
+  if (b2 > 0.f && b2 > (tol * tol) * fabsf(app * aqq)) {
+    const float d = aqq - app;
+    const float x = fmaf(d, d, 4.f * b2);
+    if (!(x >= 7.888609052e-31f)) {   // 2^-100
+      ep_rotation(app, aqq, b, tol, c, st, dp, dq, rot);
+      return;
+    }
+    const float ir = ep_rsqrt(x);
+    const float y = fmaf(0.5f * fabsf(d), ir, 0.5f);
+    const float ic = ep_rsqrt(y);
+    c = y * ic;
+    const float sg = d < 0.f ? -1.f : 1.f;
+    const float f = sg * ir * ic;
+    st = make_float2(f * b.x, f * b.y);
+    const float tb = sg * b2 * ir * (ic * ic);
+    dp = app - tb;
+    dq = aqq + tb;
+    rot = 1;
+  }
+}
+
 }  // namespace lcf

@@ -76,7 +76,10 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
   L.m = n < kEvdHead ? n : kEvdHead;
   L.h = L.np / 2;
   size_t o = 0;
-  L.a = o;    o = ep_align(o + (size_t)L.np * L.ld * 8);      // A (phase A: R/scale in fp32)
+  {
+    const size_t dense = (size_t)L.np * L.ld * 8, slots = (size_t)2 * 4 * (L.h * (L.h + 1) / 2) * 8;
+    L.a = o;  o = ep_align(o + (dense > slots ? dense : slots));   // R/scale in fp32, then two slot buffers
+  }
   L.ys = o;   o = ep_align(o + (size_t)L.m * L.ldy * 8);      // subspace block, column-major
   L.zs = o;   o = ep_align(o + (size_t)L.m * L.ldy * 8);      // product block, then reflectors Vh
   L.yd = o;   o = ep_align(o + (size_t)n * L.m * 16);         // R Vh (double-float, [a][j])
@@ -112,6 +115,41 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
 
 size_t evd_pair_smem_bytes(int nt) { return ep_layout(nt).total; }
 
+// ---- pair-slot storage of the Hermitian matrix during the Jacobi sweeps ----
+// At step r slot i holds (first, second) = ((r + i) mod M, (r - i) mod M), slot 0 (r, M),
+// M = np - 1.  Entry A[x][y] with x in slot a (role ra: 0 first, 1 second) and y in slot b
+// (role rb) lives in block (a, b) when a < b, or a == b and ra <= rb, in plane 2 ra + rb at
+// block index bid(a, b) (upper triangle of slots, row-wise); otherwise its conjugate lives
+// in block (b, a), plane 2 rb + ra.  Plane 2 of a diagonal block is unused.  From one step to
+// the next every first member moves down one slot and every second member up one (slot 0's
+// first becomes slot 1's second, slot h-1's second becomes its first, M stays): the same
+// permutation at every step, so each block's destinations are fixed.
+__device__ __forceinline__ int sl_bid(int a, int b, int h) { return a * h - (a * (a - 1)) / 2 + (b - a); }
+__device__ __forceinline__ void sl_move(int& sl, int& role, int h) {
+  if (h == 1) return;
+  if (role == 0) {
+    if (sl == 0) { sl = 1; role = 1; }
+    else --sl;
+  } else if (sl == h - 1) {
+    role = 0;
+  } else if (sl > 0) {
+    ++sl;
+  }
+}
+// offset (float2 units within a buffer of 4 planes of nblk entries) of entry (x at (a, ra), y at (b, rb))
+__device__ __forceinline__ int sl_off(int a, int ra, int b, int rb, int h, int nblk, bool& cj) {
+  if (a < b || (a == b && ra <= rb)) { cj = false; return (2 * ra + rb) * nblk + sl_bid(a, b, h); }
+  cj = true;
+  return (2 * rb + ra) * nblk + sl_bid(b, a, h);
+}
+// slot and role of index x at step 0
+__device__ __forceinline__ void sl_home(int x, int h, int& sl, int& role) {
+  const int M = 2 * h - 1;
+  if (x == M) { sl = 0; role = 1; }
+  else if (x < h) { sl = x; role = 0; }
+  else { sl = M - x; role = 1; }
+}
+
 // ---------------------------------------------------------------------------
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EP_THREADS, 1)
 evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, EpArgs g,
@@ -124,7 +162,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
   const int k = blockIdx.x >> 1, n = g.nt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const EpLayout L = ep_layout(n);
-  const int np = L.np, ld = L.ld, ldy = L.ldy, m = L.m, h = L.h;
+  const int np = L.np, ldy = L.ldy, m = L.m, h = L.h;
   const double2* R = Rg + (size_t)k * n * n;
   __shared__ double sh_scale;
   __shared__ int sh_ok[2];
@@ -177,7 +215,6 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     // CTA 0: subspace, QR, congruence, Jacobi on A, sort and rule
     // =====================================================================
     float2* Rh = reinterpret_cast<float2*>(smem + L.a);    // phase A (np x np)
-    float2* A = reinterpret_cast<float2*>(smem + L.a);     // phase D (np x ld)
     float2* Ys = reinterpret_cast<float2*>(smem + L.ys);   // [j][a], stride ldy
     float2* Zs = reinterpret_cast<float2*>(smem + L.zs);
     zdf* Yd = reinterpret_cast<zdf*>(smem + L.yd);          // [a][j]
@@ -405,7 +442,9 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       Zd[e] = acc;
     }
     __syncthreads();
-    // B upper triangle -> fp32 A (mirrored, real diagonal)
+    // B upper triangle -> fp32 pair-slot buffer 0 (real diagonal)
+    const int nblk = h * (h + 1) / 2;
+    float2* S0 = reinterpret_cast<float2*>(smem + L.a);
     for (int e = tid; e < np * np; e += EP_THREADS) {
       const int a = e / np, b = e % np;
       if (a > b) continue;
@@ -427,102 +466,155 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
         x.im = df_add(x.im, df_neg(c.im));
         v = make_float2(x.re.hi + x.re.lo, a == b ? 0.f : x.im.hi + x.im.lo);
       }
-      A[a * ld + b] = v;
-      if (a != b) A[b * ld + a] = cconj(v);
+      int sa, ra, sb, rb;
+      sl_home(a, h, sa, ra);
+      sl_home(b, h, sb, rb);
+      bool cj;
+      const int o = sl_off(sa, ra, sb, rb, h, nblk, cj);
+      S0[o] = cj ? cconj(v) : v;
     }
     __syncthreads();
 
     EP_STAMP(3);
     EP_STAMP(4);
-    // ---------------- phase D: cyclic Jacobi on A; rotations streamed to CTA 1
-    constexpr int MAXB = ((kEvdPairNmax / 2) * (kEvdPairNmax / 2 + 1) / 2 + EP_THREADS - 1) / EP_THREADS;
-    int blk[MAXB];
+    // ---------------- phase D: cyclic Jacobi in pair-slot storage; rotations streamed to CTA 1
+    // Step r reads buffer par and writes every entry, rotated and moved to its step-(r+1)
+    // place, into buffer par ^ 1.  Thread i < h rotates slot i (its diagonal block); the
+    // off-diagonal blocks (a < b) are spread over all threads, with fixed source and
+    // destination offsets.
+    constexpr int MAXB = ((kEvdPairNmax / 2) * (kEvdPairNmax / 2 - 1) / 2 + EP_THREADS - 1) / EP_THREADS;
+    int bab[MAXB], bsrc[MAXB], bdst[MAXB][4];
+    unsigned bcj[MAXB];
     {
-      const int nblk = h * (h + 1) / 2;
+      const int noff = h * (h - 1) / 2;
+#pragma unroll
       for (int j = 0; j < MAXB; ++j) {
         const int e = tid + j * EP_THREADS;
-        int code = -1;
-        if (e < nblk) {
-          int ia = 0, rem = e;
-          while (rem >= h - ia) { rem -= h - ia; ++ia; }
-          code = (ia << 8) | (ia + rem);
+        bab[j] = -1;
+        bsrc[j] = 0;
+        bcj[j] = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bdst[j][q] = 0;
+        if (e < noff) {
+          int a = 0, rem = e;
+          while (rem >= h - 1 - a) { rem -= h - 1 - a; ++a; }
+          const int b = a + 1 + rem;
+          bab[j] = a | (b << 8);
+          bsrc[j] = sl_bid(a, b, h);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int a2 = a, r2 = q >> 1, b2 = b, s2 = q & 1;
+            sl_move(a2, r2, h);
+            sl_move(b2, s2, h);
+            bool cj;
+            bdst[j][q] = sl_off(a2, r2, b2, s2, h, nblk, cj);
+            bcj[j] |= (cj ? 1u : 0u) << q;
+          }
         }
-        blk[j] = code;
       }
     }
+    int dsrc = 0, dd0 = 0, dd1 = 0, dd3 = 0;
+    bool dcj = false;
+    if (tid < h) {   // the diagonal block of slot i and where its three entries go
+      int a0 = tid, r0 = 0, a1 = tid, r1 = 1;
+      sl_move(a0, r0, h);
+      sl_move(a1, r1, h);
+      bool cj;
+      dsrc = sl_bid(tid, tid, h);
+      dd0 = sl_off(a0, r0, a0, r0, h, nblk, cj);
+      dd3 = sl_off(a1, r1, a1, r1, h, nblk, cj);
+      dd1 = sl_off(a0, r0, a1, r1, h, nblk, dcj);
+    }
+    const int M = np - 1;
     const uint32_t ring_r = ep_mapa(ep_smem(reinterpret_cast<unsigned char*>(smem) + L.ring), peer);
     const uint32_t fbar_r = ep_mapa(ep_smem(reinterpret_cast<unsigned char*>(smem) + L.fbar), peer);
-    int sweeps = 0, converged = 0, hand = 0;
+    int sweeps = 0, converged = 0, hand = 0, par = 0;
     const int maxsw = g.max_sweeps > 0 ? g.max_sweeps : 40;
     for (; sweeps < maxsw && ok; ++sweeps) {
       int any = 0;
-      for (int r = 0; r < np - 1; ++r) {
+      for (int r = 0; r < M; ++r) {
+        const float2* cur = S0 + (size_t)par * 4 * nblk;
+        float2* nxt = S0 + (size_t)(par ^ 1) * 4 * nblk;
         const int slot = hand % EP_RING;
         if (tid == 0) sh_ok[r & 1] = hand < EP_RING || ep_wait(&ebar[slot], ((hand / EP_RING) - 1) & 1);
         int rot = 0;
         float4 rec;
         if (tid < h) {
           const int i = tid;
-          int pa, pb;
-          if (i == 0) { pa = r; pb = np - 1; }
-          else { pa = (r + i) % (np - 1); pb = (r - i + np - 1) % (np - 1); }
-          const int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
+          const float app = cur[dsrc].x, aqq = cur[3 * nblk + dsrc].x;
+          const float2 bq = cur[nblk + dsrc];
           float c, dp, dq;
           float2 st;
-          ep_rotation(A[p * ld + p].x, A[q * ld + q].x, A[p * ld + q], EP_TOL, c, st, dp, dq, rot);
-          rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)p | ((unsigned)q << 8) | (rot ? EP_REC_ROT : 0u)));
+          ep_rotation2(app, aqq, bq, EP_TOL, c, st, dp, dq, rot);
+          int f = r, sc = M;   // original indices of the slot's members at this step
+          if (i > 0) {
+            f = r + i;
+            if (f >= M) f -= M;
+            sc = r - i;
+            if (sc < 0) sc += M;
+          }
+          rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)f | ((unsigned)sc << 8) | (rot ? EP_REC_ROT : 0u)));
           pr[i] = rec;
-          prd[i] = make_float2(dp, dq);
+          nxt[dd0] = make_float2(dp, 0.f);
+          nxt[dd3] = make_float2(dq, 0.f);
+          nxt[dd1] = rot ? make_float2(0.f, 0.f) : (dcj ? cconj(bq) : bq);
         }
         const int anyr = __syncthreads_or(rot);
         if (!sh_ok[r & 1]) { ok = false; break; }   // the partner stopped consuming: give up
-        if (!anyr) continue;
-        any = 1;
-        if (tid < h) {   // hand the step's records to CTA 1
-          ep_st_async(ring_r + (uint32_t)((slot * h + tid) * 16), rec, fbar_r + (uint32_t)(slot * 8));
+        if (anyr) {
+          any = 1;
+          if (tid < h) {   // hand the step's records to CTA 1
+            ep_st_async(ring_r + (uint32_t)((slot * h + tid) * 16), rec, fbar_r + (uint32_t)(slot * 8));
+          }
+          ++hand;
         }
-        ++hand;
 #pragma unroll
         for (int j = 0; j < MAXB; ++j) {
-          if (blk[j] < 0) continue;
-          const int ia = blk[j] >> 8, ib = blk[j] & 255;
-          const float4 ra = pr[ia], rb = pr[ib];
-          const unsigned ma = __float_as_uint(ra.w), mb = __float_as_uint(rb.w);
-          if (!((ma | mb) & EP_REC_ROT)) continue;
-          const int pa = ma & 255, qa = (ma >> 8) & 255, pb = mb & 255, qb = (mb >> 8) & 255;
-          if (ia == ib) {
-            const float2 d = prd[ia];
-            A[pa * ld + pa] = make_float2(d.x, 0.f);
-            A[qa * ld + qa] = make_float2(d.y, 0.f);
-            A[pa * ld + qa] = make_float2(0.f, 0.f);   // pa < qa: the kept entry
-            continue;
+          if (bab[j] < 0) continue;
+          const int so = bsrc[j];
+          float2 x00 = cur[so], x01 = cur[nblk + so], x10 = cur[2 * nblk + so], x11 = cur[3 * nblk + so];
+          if (anyr) {
+            const float4 ra = pr[bab[j] & 255], rb = pr[bab[j] >> 8];
+            if ((__float_as_uint(ra.w) | __float_as_uint(rb.w)) & EP_REC_ROT) {
+              // columns by slot b's rotation, then rows by slot a's
+              const float ca = ra.x, cb = rb.x;
+              const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
+              const float2 sbc = cconj(sb), sac = cconj(sa);
+              const float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
+              const float2 y10 = csub(cscale(x10, cb), cmul(sbc, x11)), y11 = cadd(cmul(sb, x10), cscale(x11, cb));
+              x00 = csub(cscale(y00, ca), cmul(sa, y10));
+              x01 = csub(cscale(y01, ca), cmul(sa, y11));
+              x10 = cadd(cmul(sac, y00), cscale(y10, ca));
+              x11 = cadd(cmul(sac, y01), cscale(y11, ca));
+            }
           }
-          // only the upper triangle is kept: an entry below the diagonal is the conjugate of its mirror
-          const float ca = ra.x, cb = rb.x;
-          const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
-          const int o00 = pa < pb ? pa * ld + pb : pb * ld + pa, o01 = pa < qb ? pa * ld + qb : qb * ld + pa;
-          const int o10 = qa < pb ? qa * ld + pb : pb * ld + qa, o11 = qa < qb ? qa * ld + qb : qb * ld + qa;
-          float2 x00 = A[o00], x01 = A[o01], x10 = A[o10], x11 = A[o11];
-          if (pa > pb) x00 = cconj(x00);
-          if (pa > qb) x01 = cconj(x01);
-          if (qa > pb) x10 = cconj(x10);
-          if (qa > qb) x11 = cconj(x11);
-          const float2 sbc = cconj(sb);
-          const float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
-          const float2 y10 = csub(cscale(x10, cb), cmul(sbc, x11)), y11 = cadd(cmul(sb, x10), cscale(x11, cb));
-          const float2 sac = cconj(sa);
-          const float2 z00 = csub(cscale(y00, ca), cmul(sa, y10)), z01 = csub(cscale(y01, ca), cmul(sa, y11));
-          const float2 z10 = cadd(cmul(sac, y00), cscale(y10, ca)), z11 = cadd(cmul(sac, y01), cscale(y11, ca));
-          A[o00] = pa < pb ? z00 : cconj(z00);
-          A[o01] = pa < qb ? z01 : cconj(z01);
-          A[o10] = qa < pb ? z10 : cconj(z10);
-          A[o11] = qa < qb ? z11 : cconj(z11);
+          const unsigned cj = bcj[j];
+          if (cj & 1u) x00.y = -x00.y;
+          if (cj & 2u) x01.y = -x01.y;
+          if (cj & 4u) x10.y = -x10.y;
+          if (cj & 8u) x11.y = -x11.y;
+          nxt[bdst[j][0]] = x00;
+          nxt[bdst[j][1]] = x01;
+          nxt[bdst[j][2]] = x10;
+          nxt[bdst[j][3]] = x11;
         }
         __syncthreads();
+        par ^= 1;
       }
       ok = __syncthreads_and(ok);
       if (!any) { converged = 1; break; }
     }
+    // the diagonal by original index: after whole sweeps every index is back at its step-0 place
+    float* dg = reinterpret_cast<float*>(prd);   // np floats
+    {
+      const float2* fin = S0 + (size_t)par * 4 * nblk;
+      for (int x = tid; x < np; x += EP_THREADS) {
+        int sl, ro;
+        sl_home(x, h, sl, ro);
+        dg[x] = fin[3 * ro * nblk + sl_bid(sl, sl, h)].x;
+      }
+    }
+    __syncthreads();
     // end-of-stream record
     {
       const int slot = hand % EP_RING;
@@ -537,16 +629,16 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     EP_STAMP(5);
     // ---------------- phase E (CTA 0): sort, rule, alpha; results to CTA 1
     for (int i = tid; i < n; i += EP_THREADS) {
-      const float di = A[i * ld + i].x;
+      const float di = dg[i];
       int rk = 0;
       for (int j = 0; j < n; ++j) {
-        const float dj = A[j * ld + j].x;
+        const float dj = dg[j];
         rk += (dj > di) || (dj == di && j < i);
       }
       perm[rk] = i;
     }
     __syncthreads();
-    for (int i = tid; i < n; i += EP_THREADS) lam_s[i] = (double)A[perm[i] * ld + perm[i]].x * scale;
+    for (int i = tid; i < n; i += EP_THREADS) lam_s[i] = (double)dg[perm[i]] * scale;
     __syncthreads();
     EP_STAMP(6);
     __shared__ int sh_lk;

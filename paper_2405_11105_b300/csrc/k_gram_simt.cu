@@ -188,16 +188,17 @@ cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st) {
 constexpr int ACH = 32;  // pixels staged per step of the augmented-column kernel
 constexpr int APR = 4;   // pixels per FP32 partial sum there
 
-// Augmented columns Y[i][a] = sum_p g^2 conj(x_p(i)) a_p(a), i < nt + d, a < d
-// (rows i < nt give U, rows nt.. give Q).  grid: x = pixel split, y = window.
+// Augmented columns Y[i][a] = sum_p g^2 conj(x_p(i)) a_p(a), i < nt + qrows, a < d
+// (rows i < nt give U, rows nt.. give Q; qrows = d, or 0 when Q comes from the
+// exact coefficient kernel).  grid: x = pixel split, y = window.
 __global__ void __launch_bounds__(256)
 gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl,
                 const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
-                int nsplit, double2* __restrict__ aug) {
+                int nsplit, int qrows, double2* __restrict__ aug) {
   extern __shared__ float2 Xs[];   // [ACH][nt + d]: x_p, pixel-major
   __shared__ float g2s[ACH];
   const int k = blockIdx.y, s = blockIdx.x;
-  const int na = nt + nd_defl, nout = na * nd_defl;
+  const int na = nt + nd_defl, nout = (nt + qrows) * nd_defl;
   const Box b = boxes[k];
   const int W = b.x1 - b.x0;
   const long Pk = (long)(b.z1 - b.z0) * W;
@@ -280,10 +281,11 @@ cudaError_t gram_simt_configure() {
                               (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
 }
 
-cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st) {
+cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st, bool with_q) {
   dim3 grid(P->aug_nsplit, P->nd);
   gram_aug_kernel<<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
-      P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit, P->ws.gaug);
+      P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit,
+      with_q ? P->ndefl : 0, P->ws.gaug);
   return counted(P);
 }
 

@@ -304,13 +304,17 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
   }
 }
 
-// R from the tensor-core partials: R' = Herm(sum D') / s^2 for the residual block and U,
-// Q from the exact kernel; R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T (FP64)
+// R from the tensor-core partials: R' = Herm(sum D') / s^2 for the residual block and U
+// (U from the CUDA-core augmented-column partials instead when the tensor-core rows
+// nb are the residual rows alone, nb = nt), Q from the exact kernel;
+// R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T (FP64)
 __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const double2* __restrict__ qpart,
+                                        const double2* __restrict__ aug, int aug_nsplit,
                                         const float2* __restrict__ phi, const unsigned* __restrict__ xmax_bits,
-                                        int nsplit, int qsplit, int nt, int nd_defl, double2* __restrict__ R) {
+                                        int nsplit, int qsplit, int nt, int nd_defl, int nb,
+                                        double2* __restrict__ R) {
   const int k = blockIdx.y;
-  const int na = nt + nd_defl;
+  const int na = nb;   // row length of the tensor-core partials
   const double* pk = part + (size_t)k * nsplit * 2 * na * na;
   __shared__ double2 U[kEvdNmax][kDeflateMax];
   __shared__ double2 Q[kDeflateMax][kDeflateMax];
@@ -331,9 +335,20 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     const double xi = im[(size_t)a * na + bb] - im[(size_t)bb * na + a];
     return make_double2(0.5 * xr * is2, 0.5 * xi * is2);
   };
+  const double2* ak = aug + (size_t)k * aug_nsplit * nt * nd_defl;
   for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
     int i = e / nd_defl, a = e % nd_defl;
-    U[i][a] = herm(i, nt + a);
+    if (nb > nt) {
+      U[i][a] = herm(i, nt + a);
+    } else {
+      double sx = 0.0, sy = 0.0;
+      for (int s = 0; s < aug_nsplit; ++s) {
+        const double2 v = ak[(size_t)s * nt * nd_defl + e];
+        sx += v.x;
+        sy += v.y;
+      }
+      U[i][a] = make_double2(sx, sy);
+    }
     float2 f = phi[a * nt + i];
     ph[a][i] = make_double2((double)f.x, (double)f.y);
   }
@@ -372,7 +387,7 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
 
 cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   const lcf_config& c = P->cfg;
-  const int na = P->nt + P->ndefl;
+  const int na = P->tc_na;
   dim3 grid(P->tc_nsplit, P->nd);
   gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
                                                                     P->ws.gx, P->ws.xmax, P->tc_nsplit,
@@ -381,7 +396,9 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   gram_q_kernel<<<dim3(P->q_nsplit, P->nd), 256, 0, st>>>(P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->ws.box,
                                                           P->ws.gz, P->ws.gx, P->q_nsplit, P->ws.gq);
-  return counted(P);
+  e = counted(P);
+  if (e != cudaSuccess || na > P->nt) return e;
+  return launch_gram_aug(P, st, false);   // U for the residual-only tensor-core rows
 }
 
 // part[k][0] += sum_{s>0} part[k][s] (coalesced; fixed split order)
@@ -396,7 +413,7 @@ __global__ void gram_tc_reduce_kernel(double* __restrict__ part, int nsplit, siz
 }
 
 cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
-  const int na = P->nt + P->ndefl;
+  const int na = P->tc_na;
   const size_t per_split = (size_t)2 * na * na;
   if (P->tc_nsplit > 1) {
     dim3 gr((unsigned)((per_split + 255) / 256), P->nd);
@@ -407,8 +424,9 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   // the reduced sum sits in split 0 of each window: read it as a single split
   // with the window stride of the full buffer
   dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
-  gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.phi, P->ws.xmax, P->tc_nsplit,
-                                                 P->q_nsplit, P->nt, P->ndefl, P->ws.R);
+  gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ws.phi,
+                                                 P->ws.xmax, P->tc_nsplit, P->q_nsplit, P->nt, P->ndefl, na,
+                                                 P->ws.R);
   return counted(P);
 }
 

@@ -38,7 +38,7 @@ __global__ void gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, 
                                  double2* __restrict__ part);
 __global__ void gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl,
                                 const Box* __restrict__ boxes, const float* __restrict__ gz,
-                                const float* __restrict__ gx, int nsplit, double2* __restrict__ aug);
+                                const float* __restrict__ gx, int nsplit, int qrows, double2* __restrict__ aug);
 __global__ void gram_assemble_kernel(const double2* __restrict__ part, const double2* __restrict__ aug,
                                      const float2* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
                                      int nd_defl, double2* __restrict__ R);
@@ -153,7 +153,7 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
                                                                     (int)npix, nullptr);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   gram_aug_kernel<<<dim3(1, (unsigned)nd), 256, gram_aug_smem_bytes((int)nt, ndefl), stream>>>(
-      xa, c->nz, c->nx, (int)nt, ndefl, box, gz, gx, 1, aug);
+      xa, c->nz, c->nx, (int)nt, ndefl, box, gz, gx, 1, ndefl, aug);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   dim3 grid(pairs, nsplit, (unsigned)nd);
   gram_simt_kernel<<<grid, 256, 0, stream>>>(xa, c->nz, c->nx, (int)nt, box, gz, gx, tiles, nsplit, part);

@@ -70,7 +70,7 @@ static lcf_status validate(const lcf_config* c) {
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
   if (c->evd_path == LCF_EVD_CTA && c->nt > kEvdCtaNmax) return LCF_EUNSUPPORTED;
-  if (c->gram_path == LCF_PATH_TC && c->nt + deflate_count(c->nt) > kTcGramNaMax) return LCF_EUNSUPPORTED;
+  if (c->gram_path == LCF_PATH_TC && c->nt > kTcGramNaMax) return LCF_EUNSUPPORTED;
   return LCF_OK;
 }
 
@@ -172,6 +172,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     long ts = (pmax + 2047) / 2048;   // ~2048 pixels per tensor-core CTA
     P->tc_nsplit = (int)(ts < 1 ? 1 : (ts > 64 ? 64 : ts));
   }
+  P->tc_na = P->n1 <= kTcGramNaMax ? P->n1 : P->nt;
   P->ncp = P->nt <= kProjectShortNmax ? 4 * project_cpt(P->nt) : (P->nt + 15) / 16 * 16;
   std::vector<float> gz, gx;
   build_geometry(*cfg, P->boxes, gz, gx);
@@ -191,7 +192,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.xmax, 1, &tot);
   if (e == cudaSuccess) e = dalloc(&w.err, 1, &tot);
   if (cfg->gram_path == LCF_PATH_TC) {
-    if (e == cudaSuccess) e = dalloc(&w.gtc, nd * P->tc_nsplit * 2 * n1 * n1, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.gtc, nd * P->tc_nsplit * 2 * P->tc_na * P->tc_na, &tot);
     if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kDeflateMax * kDeflateMax, &tot);
   }
   if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);

@@ -97,6 +97,8 @@ struct lcf_plan {
   int ndefl = 1;        // deflated slow-time vectors; the augmented row has nt + ndefl entries
   int aug_nsplit = 1;   // pixel splits of the augmented-column kernel
   int tc_nsplit = 1;    // pixel ranges per window of the tensor-core Gram
+  int tc_na = 0;        // rows of the tensor-core Gram: nt + ndefl when that fits one MMA tile, else nt
+                        // (the coefficient columns U then come from the CUDA-core kernel)
   int q_nsplit = 1;     // pixel splits of the exact coefficient-block kernel
   int basis_nsplit = 1; // pixel splits of the global Gram behind the deflation basis
   int gram_tiles = 0;   // 64-wide tiles per Gram dimension
@@ -223,7 +225,7 @@ inline cudaError_t counted(const lcf_plan* P, int n = 1) {
   return cudaGetLastError();
 }
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
-cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st);
+cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st, bool with_q = true);
 size_t gram_aug_smem_bytes(int nt, int nd_defl);
 cudaError_t gram_simt_configure();
 cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st);

@@ -39,7 +39,7 @@ def window_centres(wz, wx):
 
 def make_plans(nz, nx, nt, wz, wx, fast_sweeps, beta=1.0, device=0):
     """(converged plan with method 1, capped-sweep plan with method 1) for one geometry."""
-    tc = LCF_PATH_TC if nt + min(4, max(1, nt // 4)) <= 128 else LCF_PATH_SIMT
+    tc = LCF_PATH_TC if nt <= 128 else LCF_PATH_SIMT
     full = Plan.make(nz, nx, nt, wz, wx, device=device, thresh_mode=LCF_T_CURVATURE, beta=beta,
                      gram_path=tc, project_path=LCF_PATH_TC, evd_path=LCF_EVD_PAIR)
     fast = Plan.make(nz, nx, nt, wz, wx, device=device, thresh_mode=LCF_T_CURVATURE, beta=beta,

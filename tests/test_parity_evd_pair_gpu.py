@@ -87,7 +87,7 @@ def test_pair_edge_shapes(shape, grid, mode):
 
 @pytest.mark.parametrize("mode", ["LCF_T_CURVATURE", "LCF_T_ADAPTIVE_SOFT"])
 def test_pair_nt128_with_tensor_core_projection(mode):
-    """Nt = 128: plain Gram (Nt + d > 128 rows for the tensor-core Gram), CTA-pair EVD,
+    """Nt = 128: plain Gram, CTA-pair EVD,
     tensor-core projection with one k-step per weight stage."""
     lib = L()
     nt, nz, nx = 128, 48, 40
@@ -98,7 +98,8 @@ def test_pair_nt128_with_tensor_core_projection(mode):
 
 def test_packet_length_limits():
     lib = L()
-    for kw, want in (({"nt": 128, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_EUNSUPPORTED),
+    for kw, want in (({"nt": 129, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_EUNSUPPORTED),
+                     ({"nt": 128, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),
                      ({"nt": 128, "evd_path": lib.LCF_EVD_CTA}, lib.LCF_EUNSUPPORTED),
                      ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),          # distributed EVD
                      ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR, "project_path": lib.LCF_PATH_TC},

@@ -105,7 +105,7 @@ def compare(iq, cfg, ocfg, want_gram=True):
     flips = [int(k) for k in np.nonzero(dbg["k"] != ora.k)[0]]
     ties = [k for k in flips if near_tie(ocfg, ora.lam[k], dbg["lam"][k], int(dbg["k"][k]), int(ora.k[k]))]
     if flips and len(ties) == len(flips):
-        # every flip is an ambiguous-but-correct cutoff: judge the image against the oracle
+        # every flip is an ambiguous-but-correct cutoff: check the image against the oracle
         # evaluated at the GPU's cutoffs for those windows
         ko = np.full(ocfg.nd, -1, np.int32)
         ko[ties] = dbg["k"][ties]

@@ -71,6 +71,31 @@ def test_tc_edge_shapes(shape, grid, mode):
     check(compare(rand_iq(3, nt, nz, nx), cfg, oc))
 
 
+@pytest.mark.parametrize("nt,nz,nx,grid,seed", [
+    (125, 40, 36, (2, 2), 11),    # Nt + d = 129: one row past a single MMA tile
+    (128, 48, 40, (3, 2), 12),    # Nt + d = 132: the 128 residual rows fill the tile
+])
+def test_tc_residual_rows_only(nt, nz, nx, grid, seed):
+    """Nt + d > 128: the tensor cores take the Nt x Nt residual block, the CUDA-core
+    kernel the coefficient columns U (and the exact kernel Q)."""
+    lib = L()
+    cfg, oc = tc_cfg(nz, nx, nt, grid[0], grid[1], thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    cfg.evd_path = lib.LCF_EVD_PAIR
+    check(compare(rand_iq(seed, nt, nz, nx), cfg, oc))
+
+
+def test_tc_residual_rows_only_realistic():
+    """Nt = 128 on a tissue/vessel packet (the learned workload's recipe, cut down)."""
+    from synth.iq import Recipe
+    lib = L()
+    rec = Recipe(64, 48, 128, n_vessels=3, width_px=(2.0, 6.0), phi_rad=(0.05, 1.0), tbr_db=50.0,
+                 noise_db=-65.0, motion_amp_px=0.5)
+    iq = generate_packet(rec, seed=21)
+    cfg, oc = tc_cfg(64, 48, 128, 4, 3, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0, project=True)
+    cfg.evd_path = lib.LCF_EVD_PAIR
+    check(compare(iq, cfg, oc))
+
+
 def test_tc_matches_plain_path():
     """The two Gram paths give the same image to well within the oracle tolerance."""
     import torch
