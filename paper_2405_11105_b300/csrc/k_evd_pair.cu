@@ -36,6 +36,7 @@ constexpr int EP_RING = 16;                   // rotation records in flight betw
 constexpr float EP_TOL = 2.0e-6f;             // relative off-diagonal test
 constexpr int EP_SUBSPACE_ITERS = 6;
 constexpr unsigned EP_REC_ROT = 1u << 16, EP_REC_END = 1u << 17;
+constexpr int EP_PLANE = (kEvdPairNmax / 2) * (kEvdPairNmax / 2 + 1) / 2;   // blocks per plane of the slot storage
 
 struct EpArgs {
   int nt, nz, nx;
@@ -61,7 +62,7 @@ struct EpArgs {
 // ---- shared-memory layout (both CTAs get the larger of the two) ----
 struct EpLayout {
   int np, ld, ldy, m, h;
-  size_t a, ys, zs, yd, zd, tm, w2, pr, prd, lam, perm, wts, s0, s1, s2, ebar, mlp, end_a;   // CTA 0
+  size_t a, ys, zs, yd, zd, tm, w2, pr, prd, lam, perm, wts, s0, s1, s2, ebar, mlp, sinfo, end_a;   // CTA 0
   size_t vt, ring, vh, tv, vtm, fbar, rperm, rcoef, rkeep, phase, end_v;                 // CTA 1
   size_t total;
 };
@@ -77,7 +78,7 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
   L.h = L.np / 2;
   size_t o = 0;
   {
-    const size_t dense = (size_t)L.np * L.ld * 8, slots = (size_t)2 * 4 * (L.h * (L.h + 1) / 2) * 8;
+    const size_t dense = (size_t)L.np * L.ld * 8, slots = (size_t)2 * 4 * EP_PLANE * 8;
     L.a = o;  o = ep_align(o + (dense > slots ? dense : slots));   // R/scale in fp32, then two slot buffers
   }
   L.ys = o;   o = ep_align(o + (size_t)L.m * L.ldy * 8);      // subspace block, column-major
@@ -86,8 +87,8 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
   L.zd = o;   o = ep_align(o + (size_t)n * L.m * 16);         // Z
   L.tm = o;   o = ep_align(o + (size_t)L.m * L.m * 8);        // T (fp32 complex)
   L.w2 = o;   o = ep_align(o + (size_t)2 * L.m * L.m * 16);   // M T and T^H M T (double-float)
-  L.pr = o;   o = ep_align(o + (size_t)L.h * 16);             // rotation records
-  L.prd = o;  o = ep_align(o + (size_t)L.h * 8);              // new diagonal pair
+  L.pr = o;   o = ep_align(o + (size_t)2 * L.h * 16);         // rotation records (two steps)
+  L.prd = o;  o = ep_align(o + (size_t)2 * L.h * 8);          // new diagonal pairs (two steps)
   L.lam = o;  o = ep_align(o + (size_t)L.np * 8);
   L.perm = o; o = ep_align(o + (size_t)L.np * 4);
   L.wts = o;  o = ep_align(o + (size_t)L.np * 8);
@@ -96,6 +97,7 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
   L.s2 = o;   o = ep_align(o + (size_t)L.np * 8);
   L.ebar = o; o = ep_align(o + (size_t)EP_RING * 8);
   L.mlp = o;  o = ep_align(o + (size_t)(L.np + 2 + 2 * kMlpHiddenMax) * 4);   // learned rule: input, 2 activations
+  L.sinfo = o; o = ep_align(o + (size_t)L.h * 3 * 16);       // per slot: fixed offsets of the Jacobi steps
   L.end_a = o;
   o = 0;
   L.vt = o;    o = ep_align(o + (size_t)L.np * L.ld * 8);     // V^T (row c = column c of V)
@@ -443,7 +445,6 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     }
     __syncthreads();
     // B upper triangle -> fp32 pair-slot buffer 0 (real diagonal)
-    const int nblk = h * (h + 1) / 2;
     float2* S0 = reinterpret_cast<float2*>(smem + L.a);
     for (int e = tid; e < np * np; e += EP_THREADS) {
       const int a = e / np, b = e % np;
@@ -470,7 +471,7 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       sl_home(a, h, sa, ra);
       sl_home(b, h, sb, rb);
       bool cj;
-      const int o = sl_off(sa, ra, sb, rb, h, nblk, cj);
+      const int o = sl_off(sa, ra, sb, rb, h, EP_PLANE, cj);
       S0[o] = cj ? cconj(v) : v;
     }
     __syncthreads();
@@ -479,139 +480,240 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     EP_STAMP(4);
     // ---------------- phase D: cyclic Jacobi in pair-slot storage; rotations streamed to CTA 1
     // Step r reads buffer par and writes every entry, rotated and moved to its step-(r+1)
-    // place, into buffer par ^ 1.  Thread i < h rotates slot i (its diagonal block); the
-    // off-diagonal blocks (a < b) are spread over all threads, with fixed source and
-    // destination offsets.
-    constexpr int MAXB = ((kEvdPairNmax / 2) * (kEvdPairNmax / 2 - 1) / 2 + EP_THREADS - 1) / EP_THREADS;
-    int bab[MAXB], bsrc[MAXB], bdst[MAXB][4];
-    unsigned bcj[MAXB];
+    // place, into buffer par ^ 1.  Thread i < h owns slot i: it writes its diagonal block and,
+    // during step r, already forms step r+1's rotation of slot i from the entries that step r
+    // moves onto it (its off-diagonal comes from one element of one rotated block).  One
+    // barrier per step.  Slot i runs on thread i of the first EP_SLOTW warps, which take no
+    // off-diagonal blocks; the blocks (a < b) are spread over the other warps with fixed
+    // source and destination offsets.
+    constexpr int EP_SLOTW = (kEvdPairNmax / 2 + 31) / 32;     // warps holding the slots
+    constexpr int BT = EP_THREADS - 32 * EP_SLOTW;              // threads holding blocks
+    constexpr int MAXB = ((kEvdPairNmax / 2) * (kEvdPairNmax / 2 - 1) / 2 + BT - 1) / BT;
+    // per block: source block id (bits 0-11, 0xfff: none), slots a (12-17) and b (18-23), conjugation
+    // of entry q at bit 31 - q; destinations of entries 0, 1 and 2, 3 (16 bits each)
+    unsigned binf[MAXB], bd01[MAXB], bd23[MAXB];
     {
       const int noff = h * (h - 1) / 2;
 #pragma unroll
       for (int j = 0; j < MAXB; ++j) {
-        const int e = tid + j * EP_THREADS;
-        bab[j] = -1;
-        bsrc[j] = 0;
-        bcj[j] = 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bdst[j][q] = 0;
+        const int e = (tid < 32 * EP_SLOTW) ? noff : tid - 32 * EP_SLOTW + j * BT;
+        binf[j] = 0xfffu;
+        bd01[j] = 0u;
+        bd23[j] = 0u;
         if (e < noff) {
           int a = 0, rem = e;
           while (rem >= h - 1 - a) { rem -= h - 1 - a; ++a; }
           const int b = a + 1 + rem;
-          bab[j] = a | (b << 8);
-          bsrc[j] = sl_bid(a, b, h);
+          binf[j] = (unsigned)sl_bid(a, b, h) | ((unsigned)a << 12) | ((unsigned)b << 18);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             int a2 = a, r2 = q >> 1, b2 = b, s2 = q & 1;
             sl_move(a2, r2, h);
             sl_move(b2, s2, h);
             bool cj;
-            bdst[j][q] = sl_off(a2, r2, b2, s2, h, nblk, cj);
-            bcj[j] |= (cj ? 1u : 0u) << q;
+            const unsigned d = (unsigned)sl_off(a2, r2, b2, s2, h, EP_PLANE, cj);
+            if (q < 2) bd01[j] |= d << (16 * q);
+            else bd23[j] |= d << (16 * (q - 2));
+            binf[j] |= (cj ? 0x80000000u : 0u) >> q;   // sign bit of entry q's imaginary part, shifted by q
           }
         }
       }
     }
-    int dsrc = 0, dd0 = 0, dd1 = 0, dd3 = 0;
-    bool dcj = false;
-    if (tid < h) {   // the diagonal block of slot i and where its three entries go
-      int a0 = tid, r0 = 0, a1 = tid, r1 = 1;
+    // slot thread i: its diagonal block, where the block's entries go, and where slot i's
+    // members of the next step come from (slot, role) with the block holding their entry
+    const int my_slot = tid;
+    const bool is_slot = tid < h;
+    int4* sinfo = reinterpret_cast<int4*>(smem + L.sinfo);   // [h][3]
+    if (is_slot) {
+      const int i = my_slot;
+      int a0 = i, r0 = 0, a1 = i, r1 = 1;
       sl_move(a0, r0, h);
       sl_move(a1, r1, h);
-      bool cj;
-      dsrc = sl_bid(tid, tid, h);
-      dd0 = sl_off(a0, r0, a0, r0, h, nblk, cj);
-      dd3 = sl_off(a1, r1, a1, r1, h, nblk, cj);
-      dd1 = sl_off(a0, r0, a1, r1, h, nblk, dcj);
+      bool cj, dcj;
+      const int dsrc = sl_bid(i, i, h);
+      const int dd0 = sl_off(a0, r0, a0, r0, h, EP_PLANE, cj);
+      const int dd3 = sl_off(a1, r1, a1, r1, h, EP_PLANE, cj);
+      const int dd1 = sl_off(a0, r0, a1, r1, h, EP_PLANE, dcj);
+      // inverse moves of (i, first) and (i, second)
+      int sa = 0, ra = 0, sb = 0, rb = 1;
+      if (h > 1) {
+        if (i <= h - 2) { sa = i + 1; ra = 0; } else { sa = h - 1; ra = 1; }
+        if (i >= 2) { sb = i - 1; rb = 1; } else if (i == 1) { sb = 0; rb = 0; } else { sb = 0; rb = 1; }
+      }
+      int la_a, la_b, la_el, la_cj;
+      if (sa < sb) { la_a = sa; la_b = sb; la_el = 2 * ra + rb; la_cj = 0; }
+      else { la_a = sb; la_b = sa; la_el = 2 * rb + ra; la_cj = 1; }
+      // (diagonal block, its three destinations), (block with the next off-diagonal, element | flags),
+      // (slot | role << 16 of the next first and second member's diagonal value)
+      sinfo[3 * i] = make_int4(dsrc, dd0, dd1, dd3);
+      sinfo[3 * i + 1] = make_int4(la_a, la_b, sl_bid(la_a, la_b, h), la_el | (dcj ? 4 : 0) | (la_cj << 3));
+      sinfo[3 * i + 2] = make_int4(sa | (ra << 16), sb | (rb << 16), 0, 0);
     }
+    __syncthreads();
+    float4* pr2 = pr;                                     // [2][h] rotation records by step parity
+    float2* pd2 = prd;                                    // [2][h] new diagonal pairs by step parity
     const int M = np - 1;
     const uint32_t ring_r = ep_mapa(ep_smem(reinterpret_cast<unsigned char*>(smem) + L.ring), peer);
     const uint32_t fbar_r = ep_mapa(ep_smem(reinterpret_cast<unsigned char*>(smem) + L.fbar), peer);
+    constexpr int WT = EP_THREADS - 1;   // the thread that waits for free ring slots (no slot, few blocks)
+    const float tol2 = EP_TOL * EP_TOL;
     int sweeps = 0, converged = 0, hand = 0, par = 0;
     const int maxsw = g.max_sweeps > 0 ? g.max_sweeps : 40;
+    // slot thread state for the step about to run: rotation, new diagonal, old off-diagonal
+    float4 rec = make_float4(1.f, 0.f, 0.f, 0.f);
+    float sdp = 0.f, sdq = 0.f;
+    float2 sbq = make_float2(0.f, 0.f);
+    int srot = 0;
     for (; sweeps < maxsw && ok; ++sweeps) {
-      int any = 0;
-      for (int r = 0; r < M; ++r) {
-        const float2* cur = S0 + (size_t)par * 4 * nblk;
-        float2* nxt = S0 + (size_t)(par ^ 1) * 4 * nblk;
-        const int slot = hand % EP_RING;
-        if (tid == 0) sh_ok[r & 1] = hand < EP_RING || ep_wait(&ebar[slot], ((hand / EP_RING) - 1) & 1);
-        int rot = 0;
-        float4 rec;
-        if (tid < h) {
-          const int i = tid;
-          const float app = cur[dsrc].x, aqq = cur[3 * nblk + dsrc].x;
-          const float2 bq = cur[nblk + dsrc];
-          float c, dp, dq;
-          float2 st;
-          ep_rotation2(app, aqq, bq, EP_TOL, c, st, dp, dq, rot);
-          int f = r, sc = M;   // original indices of the slot's members at this step
-          if (i > 0) {
-            f = r + i;
-            if (f >= M) f -= M;
-            sc = r - i;
-            if (sc < 0) sc += M;
-          }
-          rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)f | ((unsigned)sc << 8) | (rot ? EP_REC_ROT : 0u)));
-          pr[i] = rec;
-          nxt[dd0] = make_float2(dp, 0.f);
-          nxt[dd3] = make_float2(dq, 0.f);
-          nxt[dd1] = rot ? make_float2(0.f, 0.f) : (dcj ? cconj(bq) : bq);
+      int anyr;
+      {
+        // Sweep start (step-0 layout).  A sweep with no rotation leaves A unchanged, so it is
+        // the same as testing every pair at once: do that instead of the sweep.
+        const float2* cur = S0 + (size_t)par * 4 * EP_PLANE;
+        if (tid == WT) sh_ok[0] = hand < EP_RING || ep_wait(&ebar[hand % EP_RING], ((hand / EP_RING) - 1) & 1);
+        int big = 0;
+#pragma unroll
+        for (int j = 0; j < MAXB; ++j) {
+          if ((binf[j] & 0xfffu) == 0xfffu) continue;
+          const int a = (binf[j] >> 12) & 63, b = (binf[j] >> 18) & 63, so = binf[j] & 0xfffu;
+          const float da0 = cur[sl_bid(a, a, h)].x, da1 = cur[3 * EP_PLANE + sl_bid(a, a, h)].x;
+          const float db0 = cur[sl_bid(b, b, h)].x, db1 = cur[3 * EP_PLANE + sl_bid(b, b, h)].x;
+          const float n00 = cabs2(cur[so]), n01 = cabs2(cur[EP_PLANE + so]);
+          const float n10 = cabs2(cur[2 * EP_PLANE + so]), n11 = cabs2(cur[3 * EP_PLANE + so]);
+          big |= (n00 > 0.f && n00 > tol2 * fabsf(da0 * db0)) | (n01 > 0.f && n01 > tol2 * fabsf(da0 * db1)) |
+                 (n10 > 0.f && n10 > tol2 * fabsf(da1 * db0)) | (n11 > 0.f && n11 > tol2 * fabsf(da1 * db1));
         }
-        const int anyr = __syncthreads_or(rot);
-        if (!sh_ok[r & 1]) { ok = false; break; }   // the partner stopped consuming: give up
+        srot = 0;
+        if (is_slot) {   // step 0's rotation of slot i
+          const int i = my_slot;
+          const int dsrc = sinfo[3 * i].x;
+          const float app = cur[dsrc].x, aqq = cur[3 * EP_PLANE + dsrc].x;
+          sbq = cur[EP_PLANE + dsrc];
+          float c;
+          float2 st;
+          ep_rotation2(app, aqq, sbq, EP_TOL, c, st, sdp, sdq, srot);
+          const int f = i == 0 ? 0 : i, sc = i == 0 ? M : M - i;
+          rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)f | ((unsigned)sc << 8) | (srot ? EP_REC_ROT : 0u)));
+          pr2[i] = rec;
+          pd2[i] = make_float2(sdp, sdq);
+          big |= srot;
+        }
+        if (!__syncthreads_or(big)) { converged = 1; break; }
+        anyr = __syncthreads_or(srot);
+      }
+      for (int r = 0; r < M; ++r) {
+        const int pb = r & 1;
+        if (!sh_ok[pb]) { ok = false; break; }   // the partner stopped consuming: give up
+        const float2* cur = S0 + (size_t)par * 4 * EP_PLANE;
+        float2* nxt = S0 + (size_t)(par ^ 1) * 4 * EP_PLANE;
         if (anyr) {
-          any = 1;
-          if (tid < h) {   // hand the step's records to CTA 1
-            ep_st_async(ring_r + (uint32_t)((slot * h + tid) * 16), rec, fbar_r + (uint32_t)(slot * 8));
+          if (is_slot) {   // hand the step's records to CTA 1
+            const int slot = hand % EP_RING;
+            ep_st_async(ring_r + (uint32_t)((slot * h + my_slot) * 16), rec, fbar_r + (uint32_t)(slot * 8));
           }
           ++hand;
         }
-#pragma unroll
-        for (int j = 0; j < MAXB; ++j) {
-          if (bab[j] < 0) continue;
-          const int so = bsrc[j];
-          float2 x00 = cur[so], x01 = cur[nblk + so], x10 = cur[2 * nblk + so], x11 = cur[3 * nblk + so];
-          if (anyr) {
-            const float4 ra = pr[bab[j] & 255], rb = pr[bab[j] >> 8];
-            if ((__float_as_uint(ra.w) | __float_as_uint(rb.w)) & EP_REC_ROT) {
-              // columns by slot b's rotation, then rows by slot a's
-              const float ca = ra.x, cb = rb.x;
-              const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
-              const float2 sbc = cconj(sb), sac = cconj(sa);
-              const float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
-              const float2 y10 = csub(cscale(x10, cb), cmul(sbc, x11)), y11 = cadd(cmul(sb, x10), cscale(x11, cb));
-              x00 = csub(cscale(y00, ca), cmul(sa, y10));
-              x01 = csub(cscale(y01, ca), cmul(sa, y11));
-              x10 = cadd(cmul(sac, y00), cscale(y10, ca));
-              x11 = cadd(cmul(sac, y01), cscale(y11, ca));
+        // the ring slot of the next hand-off (checked by everyone after the step's barrier)
+        if (tid == WT) sh_ok[pb ^ 1] = hand < EP_RING || ep_wait(&ebar[hand % EP_RING], ((hand / EP_RING) - 1) & 1);
+        const float4* prc = pr2 + pb * h;
+        int nrot = 0;
+        if (is_slot) {
+          const int i = my_slot;
+          const int4 i0 = sinfo[3 * i], i1 = sinfo[3 * i + 1], i2 = sinfo[3 * i + 2];
+          const int la_a = i1.x, la_b = i1.y, la_src = i1.z, la_el = i1.w & 3, la_pa = i2.x, la_pb = i2.y;
+          const bool dcj = (i1.w & 4) != 0, la_cj = (i1.w & 8) != 0;
+          nxt[i0.y] = make_float2(sdp, 0.f);
+          nxt[i0.w] = make_float2(sdq, 0.f);
+          nxt[i0.z] = srot ? make_float2(0.f, 0.f) : (dcj ? cconj(sbq) : sbq);
+          if (r + 1 < M) {
+            // step r+1's off-diagonal of slot i: element la_el of block (la_a, la_b) after step r
+            float2 z;
+            if (h == 1) {
+              z = srot ? make_float2(0.f, 0.f) : sbq;
+            } else {
+              const float4 Ra = prc[la_a], Rb = prc[la_b];
+              const int ec = la_el & 1, er = la_el >> 1;
+              const float2 xa0 = cur[la_src], xa1 = cur[EP_PLANE + la_src];
+              const float2 xb0 = cur[2 * EP_PLANE + la_src], xb1 = cur[3 * EP_PLANE + la_src];
+              const float cb = Rb.x, ca = Ra.x;
+              const float2 sb = make_float2(Rb.y, Rb.z), sa = make_float2(Ra.y, Ra.z);
+              float2 y0, y1;   // column ec of the block after slot la_b's rotation (rows 0, 1)
+              if (ec == 0) {
+                y0 = csub(cscale(xa0, cb), cmul(cconj(sb), xa1));
+                y1 = csub(cscale(xb0, cb), cmul(cconj(sb), xb1));
+              } else {
+                y0 = cadd(cmul(sb, xa0), cscale(xa1, cb));
+                y1 = cadd(cmul(sb, xb0), cscale(xb1, cb));
+              }
+              z = er == 0 ? csub(cscale(y0, ca), cmul(sa, y1)) : cadd(cmul(cconj(sa), y0), cscale(y1, ca));
+              if (la_cj) z = cconj(z);
             }
+            const float2 da = pd2[pb * h + (la_pa & 0xffff)], db = pd2[pb * h + (la_pb & 0xffff)];
+            const float app = (la_pa >> 16) ? da.y : da.x, aqq = (la_pb >> 16) ? db.y : db.x;
+            float c, ndp, ndq;
+            float2 st;
+            ep_rotation2(app, aqq, z, EP_TOL, c, st, ndp, ndq, nrot);
+            int f = r + 1, sc = M;   // original indices of slot i's members at step r+1
+            if (i > 0) {
+              f = r + 1 + i;
+              if (f >= M) f -= M;
+              sc = r + 1 - i;
+              if (sc < 0) sc += M;
+            }
+            rec = make_float4(c, st.x, st.y, __uint_as_float((unsigned)f | ((unsigned)sc << 8) | (nrot ? EP_REC_ROT : 0u)));
+            pr2[(pb ^ 1) * h + i] = rec;
+            pd2[(pb ^ 1) * h + i] = make_float2(ndp, ndq);
+            sdp = ndp;
+            sdq = ndq;
+            sbq = z;
           }
-          const unsigned cj = bcj[j];
-          if (cj & 1u) x00.y = -x00.y;
-          if (cj & 2u) x01.y = -x01.y;
-          if (cj & 4u) x10.y = -x10.y;
-          if (cj & 8u) x11.y = -x11.y;
-          nxt[bdst[j][0]] = x00;
-          nxt[bdst[j][1]] = x01;
-          nxt[bdst[j][2]] = x10;
-          nxt[bdst[j][3]] = x11;
         }
-        __syncthreads();
+        if (warp >= EP_SLOTW) {
+#pragma unroll
+          for (int j = 0; j < MAXB; ++j) {
+            const unsigned bi = binf[j];
+            if ((bi & 0xfffu) == 0xfffu) continue;
+            const int so = bi & 0xfffu;
+            float2 x00 = cur[so], x01 = cur[EP_PLANE + so], x10 = cur[2 * EP_PLANE + so], x11 = cur[3 * EP_PLANE + so];
+            if (anyr) {
+              const float4 ra = prc[(bi >> 12) & 63], rb = prc[(bi >> 18) & 63];
+              if ((__float_as_uint(ra.w) | __float_as_uint(rb.w)) & EP_REC_ROT) {
+                // columns by slot b's rotation, then rows by slot a's
+                const float ca = ra.x, cb = rb.x;
+                const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
+                const float2 sbc = cconj(sb), sac = cconj(sa);
+                const float2 y00 = csub(cscale(x00, cb), cmul(sbc, x01)), y01 = cadd(cmul(sb, x00), cscale(x01, cb));
+                const float2 y10 = csub(cscale(x10, cb), cmul(sbc, x11)), y11 = cadd(cmul(sb, x10), cscale(x11, cb));
+                x00 = csub(cscale(y00, ca), cmul(sa, y10));
+                x01 = csub(cscale(y01, ca), cmul(sa, y11));
+                x10 = cadd(cmul(sac, y00), cscale(y10, ca));
+                x11 = cadd(cmul(sac, y01), cscale(y11, ca));
+              }
+            }
+            x00.y = __uint_as_float(__float_as_uint(x00.y) ^ (bi & 0x80000000u));
+            x01.y = __uint_as_float(__float_as_uint(x01.y) ^ ((bi << 1) & 0x80000000u));
+            x10.y = __uint_as_float(__float_as_uint(x10.y) ^ ((bi << 2) & 0x80000000u));
+            x11.y = __uint_as_float(__float_as_uint(x11.y) ^ ((bi << 3) & 0x80000000u));
+            nxt[bd01[j] & 0xffffu] = x00;
+            nxt[bd01[j] >> 16] = x01;
+            nxt[bd23[j] & 0xffffu] = x10;
+            nxt[bd23[j] >> 16] = x11;
+          }
+        }
+        srot = nrot;
+        anyr = __syncthreads_or(nrot);
         par ^= 1;
       }
       ok = __syncthreads_and(ok);
-      if (!any) { converged = 1; break; }
     }
     // the diagonal by original index: after whole sweeps every index is back at its step-0 place
     float* dg = reinterpret_cast<float*>(prd);   // np floats
     {
-      const float2* fin = S0 + (size_t)par * 4 * nblk;
+      const float2* fin = S0 + (size_t)par * 4 * EP_PLANE;
       for (int x = tid; x < np; x += EP_THREADS) {
         int sl, ro;
         sl_home(x, h, sl, ro);
-        dg[x] = fin[3 * ro * nblk + sl_bid(sl, sl, h)].x;
+        dg[x] = fin[3 * ro * EP_PLANE + sl_bid(sl, sl, h)].x;
       }
     }
     __syncthreads();
@@ -804,13 +906,11 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       Vt[e] = v;
     }
     __syncthreads();
-    // work items: (pair, two consecutive V rows), row pairs consecutive across lanes
-    constexpr int MAXV = ((kEvdPairNmax / 2) * (kEvdPairNmax / 2) + EP_THREADS - 1) / EP_THREADS;
-    int vit[MAXV];
-    for (int j = 0; j < MAXV; ++j) {
-      const int e = tid + j * EP_THREADS;
-      vit[j] = (e < h * h) ? (((e / h) << 8) | (2 * (e % h))) : -1;
-    }
+    // work: warp w takes the pairs w, w + 16, w + 32, w + 48 of every step (one record per
+    // pair, read by all lanes), lane l the entries (2l, 2l + 1) and (2l + 64, 2l + 65) of the
+    // pair's two rows of V^T
+    constexpr int VPW = (kEvdPairNmax / 2 + EP_THREADS / 32 - 1) / (EP_THREADS / 32);   // pairs per warp
+    static_assert(2 * 32 * 2 >= kEvdPairNmax, "two 16-byte words per lane cover a row of V^T");
     __shared__ int sh_vok;
     const uint32_t ebar_r = ep_mapa(ep_smem(smem + L.ebar), peer);
     for (int hs = 0;; ++hs) {
@@ -825,26 +925,45 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       ep_try(&fbar[slot], (hs / EP_RING) & 1);
       const float4* rs = ring + (size_t)slot * h;
       if (__float_as_uint(rs[0].w) & EP_REC_END) break;
+      // every record and V entry of the warp's pairs is loaded before any is written
+      float4 rc[VPW];
 #pragma unroll
-      for (int j = 0; j < MAXV; ++j) {
-        if (vit[j] < 0) continue;
-        const int ia = vit[j] >> 8, rr = vit[j] & 255;
-        const float4 rc = rs[ia];
-        const unsigned mt = __float_as_uint(rc.w);
-        if (!(mt & EP_REC_ROT)) continue;
-        const int p = mt & 255, q = (mt >> 8) & 255;
-        const float c = rc.x;
-        const float2 s = make_float2(rc.y, rc.z);
-        float4* pp = reinterpret_cast<float4*>(Vt + p * ldv + rr);
-        float4* qq = reinterpret_cast<float4*>(Vt + q * ldv + rr);
-        const float4 P4 = *pp, Q4 = *qq;
-        const float2 vp0 = make_float2(P4.x, P4.y), vp1 = make_float2(P4.z, P4.w);
-        const float2 vq0 = make_float2(Q4.x, Q4.y), vq1 = make_float2(Q4.z, Q4.w);
-        const float2 sc = cconj(s);
-        const float2 np0 = csub(cscale(vp0, c), cmul(sc, vq0)), np1 = csub(cscale(vp1, c), cmul(sc, vq1));
-        const float2 nq0 = cadd(cmul(s, vp0), cscale(vq0, c)), nq1 = cadd(cmul(s, vp1), cscale(vq1, c));
-        *pp = make_float4(np0.x, np0.y, np1.x, np1.y);
-        *qq = make_float4(nq0.x, nq0.y, nq1.x, nq1.y);
+      for (int u = 0; u < VPW; ++u) {
+        const int ia = warp + u * (EP_THREADS / 32);
+        rc[u] = ia < h ? rs[ia] : make_float4(1.f, 0.f, 0.f, 0.f);
+      }
+      float4 P4[VPW][2], Q4[VPW][2];
+      int po[VPW], qo[VPW];
+#pragma unroll
+      for (int u = 0; u < VPW; ++u) {
+        const unsigned mt = __float_as_uint(rc[u].w);
+        po[u] = (int)(mt & 255) * ldv + 2 * lane;
+        qo[u] = (int)((mt >> 8) & 255) * ldv + 2 * lane;
+        if (mt & EP_REC_ROT) {
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            if (lane + 32 * t < h) {
+              P4[u][t] = *reinterpret_cast<const float4*>(Vt + po[u] + 64 * t);
+              Q4[u][t] = *reinterpret_cast<const float4*>(Vt + qo[u] + 64 * t);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < VPW; ++u) {
+        if (!(__float_as_uint(rc[u].w) & EP_REC_ROT)) continue;
+        const float c = rc[u].x;
+        const float2 s = make_float2(rc[u].y, rc[u].z), sc = cconj(s);
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (lane + 32 * t >= h) continue;
+          const float2 vp0 = make_float2(P4[u][t].x, P4[u][t].y), vp1 = make_float2(P4[u][t].z, P4[u][t].w);
+          const float2 vq0 = make_float2(Q4[u][t].x, Q4[u][t].y), vq1 = make_float2(Q4[u][t].z, Q4[u][t].w);
+          const float2 np0 = csub(cscale(vp0, c), cmul(sc, vq0)), np1 = csub(cscale(vp1, c), cmul(sc, vq1));
+          const float2 nq0 = cadd(cmul(s, vp0), cscale(vq0, c)), nq1 = cadd(cmul(s, vp1), cscale(vq1, c));
+          *reinterpret_cast<float4*>(Vt + po[u] + 64 * t) = make_float4(np0.x, np0.y, np1.x, np1.y);
+          *reinterpret_cast<float4*>(Vt + qo[u] + 64 * t) = make_float4(nq0.x, nq0.y, nq1.x, nq1.y);
+        }
       }
       __syncthreads();
       if (tid == 0) ep_arrive_remote(ebar_r + (uint32_t)(slot * 8));
