@@ -34,7 +34,7 @@ namespace lcf {
 constexpr int EP_THREADS = 512;
 constexpr int EP_RING = 16;                   // rotation records in flight between the CTAs
 constexpr float EP_TOL = 2.0e-6f;             // relative off-diagonal test
-constexpr int EP_SUBSPACE_ITERS = 6;
+constexpr int EP_SUBSPACE_ITERS = 3;
 constexpr unsigned EP_REC_ROT = 1u << 16, EP_REC_END = 1u << 17;
 constexpr int EP_PLANE = (kEvdPairNmax / 2) * (kEvdPairNmax / 2 + 1) / 2;   // blocks per plane of the slot storage
 
@@ -63,7 +63,7 @@ struct EpArgs {
 struct EpLayout {
   int np, ld, ldy, m, h;
   size_t a, ys, zs, yd, zd, tm, w2, pr, prd, lam, perm, wts, s0, s1, s2, ebar, mlp, sinfo, end_a;   // CTA 0
-  size_t vt, ring, vh, tv, vtm, fbar, rperm, rcoef, rkeep, phase, end_v;                 // CTA 1
+  size_t vt, ring, vh, tv, vtm, fbar, rperm, rcoef, rkeep, phase, zcp, end_v;            // CTA 1
   size_t total;
 };
 
@@ -110,6 +110,7 @@ __host__ __device__ inline EpLayout ep_layout(int n) {
   L.rcoef = o; o = ep_align(o + (size_t)L.np * 4);            // wt * sqrt(alpha/Nt) per sorted index
   L.rkeep = o; o = ep_align(o + (size_t)(L.np + 1) * 4);      // [0] = ncol, then kept sorted indices
   L.phase = o; o = ep_align(o + (size_t)L.np * 8);
+  L.zcp = o;   o = ep_align(o + (size_t)n * L.m * 16);        // Z (received for the congruence)
   L.end_v = o;
   L.total = (L.end_a > L.end_v ? L.end_a : L.end_v);
   return L;
@@ -150,6 +151,103 @@ __device__ __forceinline__ void sl_home(int x, int h, int& sl, int& role) {
   if (x == M) { sl = 0; role = 1; }
   else if (x < h) { sl = x; role = 0; }
   else { sl = M - x; role = 1; }
+}
+
+// ---- the congruence B = Q^H R Q, shared by the two CTAs ----
+// (h, l) += (ah + al) b: FMA two-product, Knuth two-sum of the high words, the
+// rounding errors summed into the low word (renormalised once at the end).
+__device__ __forceinline__ void ep_acc(float& h, float& l, float ah, float al, float b) {
+  const float p = ah * b;
+  const float e = fmaf(al, b, fmaf(ah, b, -p));
+  const float s = h + p;
+  const float bb = s - h;
+  l += ((h - (s - bb)) + (p - bb)) + e;
+  h = s;
+}
+// complex accumulator (re hi, re lo, im hi, im lo) += a * b, a double-float, b float
+__device__ __forceinline__ void ep_cmac(float4& c, const zdf& a, float2 b) {
+  ep_acc(c.x, c.y, a.re.hi, a.re.lo, b.x);
+  ep_acc(c.x, c.y, -a.im.hi, -a.im.lo, b.y);
+  ep_acc(c.z, c.w, a.re.hi, a.re.lo, b.y);
+  ep_acc(c.z, c.w, a.im.hi, a.im.lo, b.x);
+}
+__device__ __forceinline__ zdf ep_cacc_zdf(float4 c) { return {quick_two_sum(c.x, c.y), quick_two_sum(c.z, c.w)}; }
+
+// Rows [a0, a1) of Yd = (R / scale) Vh (n x m, double-float, [a][j]); 8 threads per row,
+// each an eighth of the columns b, reduced by shuffles.  Vh column-major (stride ldy).
+__device__ void ep_yd_rows(const double2* __restrict__ R, int n, int m, int ldy, float s_lo, const float2* Vh,
+                           int a0, int a1, zdf* Yd, int tid) {
+  for (int base = a0; base < a1; base += EP_THREADS / 8) {
+    const int a = base + (tid >> 3), sub = tid & 7;
+    float4 acc[kEvdHead];
+#pragma unroll
+    for (int j = 0; j < kEvdHead; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a < a1) {
+      double2 rn = sub < n ? R[(size_t)a * n + sub] : make_double2(0.0, 0.0);
+      for (int b = sub; b < n; b += 8) {
+        const double2 r = rn;
+        if (b + 8 < n) rn = R[(size_t)a * n + b + 8];   // next column's entry in flight
+        zdf rz;
+        rz.re = df_from_double(r.x); rz.im = df_from_double(r.y);
+        rz.re.hi *= s_lo; rz.re.lo *= s_lo; rz.im.hi *= s_lo; rz.im.lo *= s_lo;
+#pragma unroll
+        for (int j = 0; j < kEvdHead; ++j)
+          if (j < m) ep_cmac(acc[j], rz, Vh[(size_t)j * ldy + b]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kEvdHead; ++j) {
+      zdf v = ep_cacc_zdf(acc[j]);
+      for (int o = 1; o < 8; o <<= 1) {
+        zdf t;
+        t.re.hi = __shfl_xor_sync(~0u, v.re.hi, o); t.re.lo = __shfl_xor_sync(~0u, v.re.lo, o);
+        t.im.hi = __shfl_xor_sync(~0u, v.im.hi, o); t.im.lo = __shfl_xor_sync(~0u, v.im.lo, o);
+        v = zdf_add(v, t);
+      }
+      if (sub == 0 && a < a1 && j < m) Yd[a * m + j] = v;
+    }
+  }
+}
+
+// Upper-triangle entries [e0, e1) (row-wise over np x np) of B = R - (Vh Z^H + Z Vh^H),
+// rounded to fp32 and stored in pair-slot buffer S (step-0 places).
+__device__ void ep_bfill(const double2* __restrict__ R, int n, int np, int h, int m, int ldy, float s_lo,
+                         const zdf* Zd, const float2* Vh, int e0, int e1, float2* S, int tid) {
+  const float two_np1 = (float)(2 * np + 1);
+  for (int e = e0 + tid; e < e1; e += EP_THREADS) {
+    // row a: the largest a with a np - a (a - 1) / 2 <= e
+    int a = (int)floorf(0.5f * (two_np1 - sqrtf(fmaxf(two_np1 * two_np1 - 8.f * (float)e, 0.f))));
+    a = a < 0 ? 0 : (a > np - 1 ? np - 1 : a);
+    while (a > 0 && a * np - (a * (a - 1)) / 2 > e) --a;
+    while (a + 1 < np && (a + 1) * np - ((a + 1) * a) / 2 <= e) ++a;
+    const int b = a + (e - (a * np - (a * (a - 1)) / 2));
+    float2 v = make_float2(0.f, 0.f);
+    if (b < n) {
+      const double2 r = R[(size_t)a * n + b];
+      float4 c1 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = c1;   // Vh Z^H and Z Vh^H terms
+#pragma unroll
+      for (int j = 0; j < kEvdHead; ++j) {
+        if (j >= m) break;
+        zdf zb = Zd[b * m + j];
+        zb.im = df_neg(zb.im);
+        ep_cmac(c1, zb, Vh[(size_t)j * ldy + a]);                 // Vh_aj conj(Z_bj)
+        ep_cmac(c2, Zd[a * m + j], cconj(Vh[(size_t)j * ldy + b]));   // Z_aj conj(Vh_bj)
+      }
+      zdf x;
+      x.re = df_from_double(r.x); x.im = df_from_double(r.y);
+      x.re.hi *= s_lo; x.re.lo *= s_lo; x.im.hi *= s_lo; x.im.lo *= s_lo;
+      const zdf t1 = ep_cacc_zdf(c1), t2 = ep_cacc_zdf(c2);
+      x.re = df_add(x.re, df_neg(df_add(t1.re, t2.re)));
+      x.im = df_add(x.im, df_neg(df_add(t1.im, t2.im)));
+      v = make_float2(x.re.hi + x.re.lo, a == b ? 0.f : x.im.hi + x.im.lo);
+    }
+    int sa, ra, sb, rb;
+    sl_home(a, h, sa, ra);
+    sl_home(b, h, sb, rb);
+    bool cj;
+    const int o = sl_off(sa, ra, sb, rb, h, EP_PLANE, cj);
+    S[o] = cj ? cconj(v) : v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -372,36 +470,10 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     EP_STAMP(2);
 
     // ---------------- phase C: B = Q^H R Q = R - (Vh Z^H + Z Vh^H) in double-float
-    // Yd = (R / scale) Vh : 4 threads per row, each a quarter of the columns b, 8 outputs
-    {
-      const int a = tid >> 2, sub = tid & 3;
-      zdf acc[kEvdHead];
-#pragma unroll
-      for (int j = 0; j < kEvdHead; ++j) acc[j] = {{0.f, 0.f}, {0.f, 0.f}};
-      if (a < n) {
-        for (int b = sub; b < n; b += 4) {
-          const double2 r = R[(size_t)a * n + b];
-          zdf rz;
-          rz.re = df_from_double(r.x); rz.im = df_from_double(r.y);
-          rz.re.hi *= s_lo; rz.re.lo *= s_lo; rz.im.hi *= s_lo; rz.im.lo *= s_lo;
-#pragma unroll
-          for (int j = 0; j < kEvdHead; ++j)
-            if (j < m) acc[j] = zdf_add(acc[j], zdf_mul_c(rz, Zs[(size_t)j * ldy + b]));
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kEvdHead; ++j) {
-        zdf v = acc[j];
-        for (int o = 1; o < 4; o <<= 1) {
-          zdf t;
-          t.re.hi = __shfl_xor_sync(~0u, v.re.hi, o); t.re.lo = __shfl_xor_sync(~0u, v.re.lo, o);
-          t.im.hi = __shfl_xor_sync(~0u, v.im.hi, o); t.im.lo = __shfl_xor_sync(~0u, v.im.lo, o);
-          v = zdf_add(v, t);
-        }
-        if (sub == 0 && a < n && j < m) Yd[a * m + j] = v;
-      }
-    }
-    __syncthreads();
+    // Yd = (R / scale) Vh: rows [0, n / 2) here, the rest by CTA 1 into this CTA's Yd
+    const int nA = (n + 1) / 2;
+    ep_yd_rows(R, n, m, ldy, s_lo, Zs, 0, nA, Yd, tid);
+    cluster.sync();   // #1b: every row of Yd is here
     // M = Vh^H Yd (m x m): warp w -> entries w, w + 16, ...
     zdf* Mm = Zd;   // Zd is free until Z is formed; M needs m*m <= n*m entries
     for (int q = warp; q < m * m; q += EP_THREADS / 32) {
@@ -444,38 +516,16 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       Zd[e] = acc;
     }
     __syncthreads();
-    // B upper triangle -> fp32 pair-slot buffer 0 (real diagonal)
-    float2* S0 = reinterpret_cast<float2*>(smem + L.a);
-    for (int e = tid; e < np * np; e += EP_THREADS) {
-      const int a = e / np, b = e % np;
-      if (a > b) continue;
-      float2 v = make_float2(0.f, 0.f);
-      if (b < n) {
-        const double2 r = R[(size_t)a * n + b];
-        zdf x;
-        x.re = df_from_double(r.x); x.im = df_from_double(r.y);
-        x.re.hi *= s_lo; x.re.lo *= s_lo; x.im.hi *= s_lo; x.im.lo *= s_lo;
-        zdf c = {{0.f, 0.f}, {0.f, 0.f}};
-        for (int j = 0; j < m; ++j) {
-          // Vh_aj conj(Z_bj) + Z_aj conj(Vh_bj)
-          zdf zb = Zd[b * m + j];
-          zb.im = df_neg(zb.im);
-          c = zdf_add(c, zdf_mul_c(zb, Zs[(size_t)j * ldy + a]));
-          c = zdf_add(c, zdf_mul_c(Zd[a * m + j], cconj(Zs[(size_t)j * ldy + b])));
-        }
-        x.re = df_add(x.re, df_neg(c.re));
-        x.im = df_add(x.im, df_neg(c.im));
-        v = make_float2(x.re.hi + x.re.lo, a == b ? 0.f : x.im.hi + x.im.lo);
-      }
-      int sa, ra, sb, rb;
-      sl_home(a, h, sa, ra);
-      sl_home(b, h, sb, rb);
-      bool cj;
-      const int o = sl_off(sa, ra, sb, rb, h, EP_PLANE, cj);
-      S0[o] = cj ? cconj(v) : v;
+    // Z to CTA 1; B's upper triangle split between the CTAs (fp32 pair-slot buffer 0, real diagonal)
+    {
+      zdf* zr = cluster.map_shared_rank(reinterpret_cast<zdf*>(smem + L.zcp), (unsigned)peer);
+      for (int e = tid; e < n * m; e += EP_THREADS) zr[e] = Zd[e];
     }
-    __syncthreads();
-
+    cluster.sync();   // #1c: Z is in CTA 1
+    float2* S0 = reinterpret_cast<float2*>(smem + L.a);
+    const int ne = np * (np + 1) / 2;
+    ep_bfill(R, n, np, h, m, ldy, s_lo, Zd, Zs, 0, ne / 2, S0, tid);
+    cluster.sync();   // #1d: CTA 1's half of B is here
     EP_STAMP(3);
     EP_STAMP(4);
     // ---------------- phase D: cyclic Jacobi in pair-slot storage; rotations streamed to CTA 1
@@ -890,6 +940,11 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     const float2* Tv = reinterpret_cast<const float2*>(smem + L.tv);
     float2* VT = reinterpret_cast<float2*>(smem + L.vtm);
     cluster.sync();   // #1: reflectors and T have arrived
+    {   // rows [n / 2, n) of Yd into CTA 0
+      zdf* ydr = cluster.map_shared_rank(reinterpret_cast<zdf*>(smem + L.yd), (unsigned)peer);
+      ep_yd_rows(R, n, m, ldy, s_lo, Vh, (n + 1) / 2, n, ydr, tid);
+    }
+    cluster.sync();   // #1b
     for (int e = tid; e < n * m; e += EP_THREADS) {   // VT = Vh T   ([a][j])
       const int a = e / m, j = e % m;
       float2 acc = make_float2(0.f, 0.f);
@@ -905,7 +960,13 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
         for (int j = 0; j < m; ++j) v = csub(v, cmul(VT[a * m + j], cconj(Vh[(size_t)j * ldy + c])));
       Vt[e] = v;
     }
-    __syncthreads();
+    cluster.sync();   // #1c: Z has arrived
+    {   // the second half of B's upper triangle into CTA 0's pair-slot buffer 0
+      float2* s0r = cluster.map_shared_rank(reinterpret_cast<float2*>(smem + L.a), (unsigned)peer);
+      const int ne = np * (np + 1) / 2;
+      ep_bfill(R, n, np, h, m, ldy, s_lo, reinterpret_cast<const zdf*>(smem + L.zcp), Vh, ne / 2, ne, s0r, tid);
+    }
+    cluster.sync();   // #1d
     // work: warp w takes the pairs w, w + 16, w + 32, w + 48 of every step (one record per
     // pair, read by all lanes), lane l the entries (2l, 2l + 1) and (2l + 64, 2l + 65) of the
     // pair's two rows of V^T
