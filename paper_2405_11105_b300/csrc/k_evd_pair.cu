@@ -331,7 +331,6 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     double* s1 = reinterpret_cast<double*>(smem + L.s1);
     double* s2 = reinterpret_cast<double*>(smem + L.s2);
     __shared__ float betas[kEvdHead];
-    __shared__ float2 us[kEvdHead];
 
     EP_STAMP(0);
     // ---------------- phase A: subspace iteration on fp32(R / scale)
@@ -405,10 +404,12 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
     }
 
     EP_STAMP(1);
-    // ---------------- phase B: Householder QR of Y by warp 0 (reflectors -> Zs), then T
-    if (warp == 0) {
-      for (int j = 0; j < m; ++j) {
-        float2* yj = Ys + (size_t)j * ldy;
+    // ---------------- phase B: Householder QR of Y (reflectors -> Zs), then T
+    // Reflector j on warp 0; the columns after it updated by one warp each.
+    for (int j = 0; j < m; ++j) {
+      float2* yj = Ys + (size_t)j * ldy;
+      float2* vj = Zs + (size_t)j * ldy;
+      if (warp == 0) {
         float nr = 0.f;
         for (int a = j + lane; a < n; a += 32) nr += cabs2(yj[a]);
         for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
@@ -417,37 +418,43 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
         const float ax0 = sqrtf(cabs2(x0));
         const float2 e = ax0 > 0.f ? cscale(x0, 1.f / ax0) : make_float2(1.f, 0.f);
         const float beta = alpha > 0.f ? 1.f / (alpha * (alpha + ax0)) : 0.f;
-        float2* vj = Zs + (size_t)j * ldy;
         for (int a = lane; a < ldy; a += 32) {
           float2 v = (a < j || a >= n) ? make_float2(0.f, 0.f) : yj[a];
           if (a == j) v = cadd(x0, cscale(e, alpha));
           vj[a] = v;
         }
         if (lane == 0) betas[j] = beta;
-        __syncwarp();
-        for (int c = j + 1; c < m; ++c) {
-          float2* yc = Ys + (size_t)c * ldy;
-          float2 t = make_float2(0.f, 0.f);
-          for (int a = j + lane; a < n; a += 32) t = cadd(t, cmulc(vj[a], yc[a]));
-          for (int o = 16; o; o >>= 1) { t.x += __shfl_xor_sync(~0u, t.x, o); t.y += __shfl_xor_sync(~0u, t.y, o); }
-          t = cscale(t, beta);
-          for (int a = j + lane; a < n; a += 32) yc[a] = csub(yc[a], cmul(vj[a], t));
-          __syncwarp();
-        }
       }
-      // compact WY: H_0 ... H_{m-1} = I - Vh T Vh^H with T upper triangular,
-      // T[j][j] = beta_j, T[0:j, j] = -beta_j T[0:j, 0:j] (Vh[:, 0:j]^H v_j)
+      __syncthreads();
+      const int c = j + warp;   // warps 1 .. m - 1 - j
+      if (warp >= 1 && c < m) {
+        float2* yc = Ys + (size_t)c * ldy;
+        float2 t = make_float2(0.f, 0.f);
+        for (int a = j + lane; a < n; a += 32) t = cadd(t, cmulc(vj[a], yc[a]));
+        for (int o = 16; o; o >>= 1) { t.x += __shfl_xor_sync(~0u, t.x, o); t.y += __shfl_xor_sync(~0u, t.y, o); }
+        t = cscale(t, betas[j]);
+        for (int a = j + lane; a < n; a += 32) yc[a] = csub(yc[a], cmul(vj[a], t));
+      }
+      __syncthreads();
+    }
+    // compact WY: H_0 ... H_{m-1} = I - Vh T Vh^H with T upper triangular,
+    // T[j][j] = beta_j, T[0:j, j] = -beta_j T[0:j, 0:j] (Vh[:, 0:j]^H v_j).
+    // The products Vh[:, i]^H v_j (i < j) on all warps, then the recurrence on warp 0.
+    __shared__ float2 vv[kEvdHead * kEvdHead];
+    for (int q = warp; q < m * m; q += EP_THREADS / 32) {
+      const int i = q / m, j = q % m;
+      if (i >= j) continue;
+      float2 cc = make_float2(0.f, 0.f);
+      for (int a = lane; a < n; a += 32) cc = cadd(cc, cmulc(Zs[(size_t)i * ldy + a], Zs[(size_t)j * ldy + a]));
+      for (int o = 16; o; o >>= 1) { cc.x += __shfl_xor_sync(~0u, cc.x, o); cc.y += __shfl_xor_sync(~0u, cc.y, o); }
+      if (lane == 0) vv[q] = cc;
+    }
+    __syncthreads();
+    if (warp == 0) {
       for (int j = 0; j < m; ++j) {
-        for (int i = 0; i < j; ++i) {
-          float2 c = make_float2(0.f, 0.f);
-          for (int a = lane; a < n; a += 32) c = cadd(c, cmulc(Zs[(size_t)i * ldy + a], Zs[(size_t)j * ldy + a]));
-          for (int o = 16; o; o >>= 1) { c.x += __shfl_xor_sync(~0u, c.x, o); c.y += __shfl_xor_sync(~0u, c.y, o); }
-          if (lane == 0) us[i] = c;
-        }
-        __syncwarp();
         if (lane < j) {
           float2 acc = make_float2(0.f, 0.f);
-          for (int l = lane; l < j; ++l) acc = cadd(acc, cmul(Tm[lane * m + l], us[l]));
+          for (int l = lane; l < j; ++l) acc = cadd(acc, cmul(Tm[lane * m + l], vv[l * m + j]));
           Tm[lane * m + j] = cscale(acc, -betas[j]);
         }
         if (lane == 0) {
