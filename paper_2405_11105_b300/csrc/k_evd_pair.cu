@@ -7,20 +7,22 @@
 // relative test, sort / phase fix / rule in double.  What changes is the
 // division of work and the data layout:
 //
-//  * CTA 0 owns A.  CTA 1 owns V.  A Jacobi step's rotations (c, s, p, q) go
-//    from CTA 0 into a 16-deep ring in CTA 1's shared memory (distributed
-//    shared memory stores + a remote mbarrier arrive per record); CTA 1
-//    applies them to V while CTA 0 already runs the next steps.  The V update
-//    (n x n/2 element pairs per step) was the larger half of a step.
+//  * CTA 0 owns A, CTA 1 owns V.  A Jacobi step's rotations (c, s, p, q) go
+//    from CTA 0 into a 16-deep ring in CTA 1's shared memory (st.async with a
+//    complete_tx on CTA 1's mbarrier); CTA 1 applies them to V while CTA 0
+//    already runs the next steps, and frees ring slots with a remote arrive.
 //  * The congruence uses the compact WY form Q = I - Vh T Vh^H:
-//      B = R - (Vh Z^H + Z Vh^H),   Z = (R Vh) T - 1/2 Vh (T^H (Vh^H R Vh) T),
+//      B = R - (Vh Z^H + Z Vh^H),   Z = (R Vh)T - 1/2 Vh(T^H (Vh^H R Vh) T),
 //    an identity for any T, so B is exactly Q^H R Q for the Q that seeds the
-//    eigenvectors; R is read from global memory twice, no n x n double-float
-//    copy is kept in shared memory.
-//  * The subspace block is stored column-major with an odd stride (the
-//    orthogonalisation's column walks are conflict-free) and its CGS2 runs on
-//    all warps; the thresholding rule runs on one warp (log10, gradients and
-//    curvature per lane, argmax by shuffles) in double precision.
+//    eigenvectors.  The two CTAs split the rows of R Vh and the entries of B.
+//  * The Jacobi sweeps keep A's upper triangle in pair-slot storage (by slot and
+//    role of the round-robin ordering, see sl_bid / sl_move below): the pairs
+//    of a step are the diagonal blocks, and every step rotates and moves the
+//    whole triangle into a second buffer with fixed per-thread offsets.  Slot
+//    threads form the next step's rotations while the block threads work, so a
+//    step has one barrier.
+//  * The thresholding rule runs on one warp (log10, gradients and curvature per
+//    lane, argmax by shuffles) in double precision.
 #include <cooperative_groups.h>
 #include <math.h>
 
