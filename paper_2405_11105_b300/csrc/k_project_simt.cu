@@ -71,22 +71,28 @@ project_simt_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int n
 // Packets longer than 128 frames: 32-pixel row segments, the window's weights
 // streamed through shared memory in blocks of 64 rows x 128 columns (eight
 // groups of 16 columns per pixel), |.|^2 summed over the column blocks.
+// The rows are the deflated packet of the Gram stage, s_p = c_p + sum_j a_pj phi_j,
+// so s_p W = [c_p, a_p] [W ; Phi^T W]: the large clutter coefficients a_p meet the
+// small Phi^T W (formed with double-float sums) and the residual c_p meets W, so
+// the FP32 sums never cancel the clutter against itself.
 __global__ void __launch_bounds__(256)
-project_simt_long_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, int nd,
+project_simt_long_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, int nd,
                          const Box* __restrict__ boxes, const float* __restrict__ gz,
                          const float* __restrict__ gx, const float2* __restrict__ W,
-                         const int* __restrict__ ncol, int ncp, float* __restrict__ out) {
+                         const float2* __restrict__ PW, const int* __restrict__ ncol, int ncp,
+                         float* __restrict__ out) {
   extern __shared__ float2 sm[];
-  float2* Ss = sm;              // [nt][32]
-  float2* Wc = sm + nt * 32;    // [64][128]
+  const int nk = nt + nd_defl;
+  float2* Ss = sm;              // [nk][32]
+  float2* Wc = sm + nk * 32;    // [64][128]
   __shared__ float red[8][32];
   const int z = blockIdx.y, xb = blockIdx.x * 32;
   const int tid = threadIdx.x, pix = tid & 31, cg = tid >> 5;
   const int x = xb + pix;
   const size_t npix = (size_t)nz * nx;
-  for (int e = tid; e < nt * 32; e += 256) {
+  for (int e = tid; e < nk * 32; e += 256) {
     const int t = e >> 5, pp = e & 31, xx = xb + pp;
-    Ss[e] = xx < nx ? iq[t * npix + (size_t)z * nx + xx] : make_float2(0.f, 0.f);
+    Ss[e] = xx < nx ? xa[t * npix + (size_t)z * nx + xx] : make_float2(0.f, 0.f);
   }
   float pd = 0.f;
   for (int k = 0; k < nd; ++k) {
@@ -95,19 +101,25 @@ project_simt_long_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, 
     const int nc = ncol[k];
     if (nc == 0) continue;
     const float2* Wk = W + (size_t)k * nt * ncp;
+    const float2* PWk = PW + (size_t)k * kDeflateMax * ncp;
     float part = 0.f;
     for (int c0 = 0; c0 < nc; c0 += 128) {
       float2 y[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) y[c] = make_float2(0.f, 0.f);
-      for (int t0 = 0; t0 < nt; t0 += 64) {
+      for (int t0 = 0; t0 < nk; t0 += 64) {
         __syncthreads();
         for (int e = tid; e < 64 * 128; e += 256) {
-          const int tt = e >> 7, cc = e & 127;
-          Wc[e] = (t0 + tt < nt && c0 + cc < nc) ? Wk[(size_t)(t0 + tt) * ncp + c0 + cc] : make_float2(0.f, 0.f);
+          const int tt = t0 + (e >> 7), cc = c0 + (e & 127);
+          float2 w = make_float2(0.f, 0.f);
+          if (cc < nc) {
+            if (tt < nt) w = Wk[(size_t)tt * ncp + cc];
+            else if (tt < nk) w = PWk[(size_t)(tt - nt) * ncp + cc];
+          }
+          Wc[e] = w;
         }
         __syncthreads();
-        const int tn = nt - t0 < 64 ? nt - t0 : 64;
+        const int tn = nk - t0 < 64 ? nk - t0 : 64;
         const float2* wrow = Wc + cg * 16;
         for (int tt = 0; tt < tn; ++tt) {
           const float2 sv = Ss[(t0 + tt) * 32 + pix];
@@ -136,7 +148,30 @@ project_simt_long_kernel(const float2* __restrict__ iq, int nz, int nx, int nt, 
   if (cg == 0 && x < nx) out[(size_t)z * nx + x] = pd;
 }
 
-size_t project_long_smem_bytes(int nt) { return (size_t)nt * 32 * 8 + 64 * 128 * 8; }
+size_t project_long_smem_bytes(int nt) { return (size_t)(nt + kDeflateMax) * 32 * 8 + 64 * 128 * 8; }
+
+// Phi^T W of every window for the long-packet projection: PW[k][j][c] = sum_t phi_j(t) W_k(t, c)
+// in double-float, one CTA per window.
+__global__ void __launch_bounds__(256)
+project_pw_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, const float2* __restrict__ phi,
+                  int nt, int nd_defl, int ncp, float2* __restrict__ PW) {
+  const int k = blockIdx.x, nc = ncol[k];
+  const float2* Wk = W + (size_t)k * nt * ncp;
+  for (int e = threadIdx.x; e < kDeflateMax * ncp; e += blockDim.x) {
+    const int j = e / ncp, c = e % ncp;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < nd_defl && c < nc) {
+      df sr = {0.f, 0.f}, si = {0.f, 0.f};
+      for (int t = 0; t < nt; ++t) {
+        const float2 f = phi[j * nt + t], w = Wk[(size_t)t * ncp + c];
+        sr = df_add(sr, df_add(two_prod_df(f.x, w.x), df_neg(two_prod_df(f.y, w.y))));
+        si = df_add(si, df_add(two_prod_df(f.x, w.y), two_prod_df(f.y, w.x)));
+      }
+      v = make_float2(sr.hi + sr.lo, si.hi + si.lo);
+    }
+    PW[(size_t)k * kDeflateMax * ncp + e] = v;
+  }
+}
 
 int project_cpt(int nt) { return nt <= 32 ? 8 : (nt <= 64 ? 16 : (nt <= 112 ? 28 : 32)); }
 
@@ -145,9 +180,13 @@ size_t project_smem_bytes(int nt, int ncp) { return (size_t)nt * 64 * 8 + (size_
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   if (P->nt > kProjectShortNmax) {
+    project_pw_kernel<<<P->nd, 256, 0, st>>>(P->ws.W, P->ws.ncol, P->ws.phi, P->nt, P->ndefl, P->ncp, P->ws.pw);
+    cudaError_t e = counted(P);
+    if (e != cudaSuccess) return e;
     dim3 g2((c.nx + 31) / 32, c.nz);
     project_simt_long_kernel<<<g2, 256, project_long_smem_bytes(P->nt), st>>>(
-        iq, c.nz, c.nx, P->nt, P->nd, P->ws.box, P->ws.gz, P->ws.gx, P->ws.W, P->ws.ncol, P->ncp, out);
+        P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->nd, P->ws.box, P->ws.gz, P->ws.gx, P->ws.W, P->ws.pw,
+        P->ws.ncol, P->ncp, out);
     return counted(P);
   }
   dim3 grid((c.nx + 63) / 64, c.nz);

@@ -122,7 +122,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
-                  w.flags, w.W, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.evd_B, w.evd_vh, w.evd_t,
+                  w.flags, w.W, w.pw, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.evd_B, w.evd_vh, w.evd_t,
                   w.evd_scale, w.iq_stage, w.pd_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -203,6 +203,8 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.alpha, nd, &tot);
   if (e == cudaSuccess) e = dalloc(&w.flags, nd, &tot);
   if (e == cudaSuccess) e = dalloc(&w.W, nd * nt * P->ncp, &tot);
+  if (e == cudaSuccess && nt > (size_t)kProjectShortNmax)
+    e = dalloc(&w.pw, nd * kDeflateMax * P->ncp, &tot);
   if (e == cudaSuccess) e = dalloc(&w.ncol, nd, &tot);
   if (cfg->evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) {
     const size_t m = P->nt < kEvdHead ? P->nt : kEvdHead;

@@ -68,6 +68,7 @@ struct Workspace {
   float* alpha = nullptr;     // [nd]
   int* flags = nullptr;       // [nd]
   float2* W = nullptr;        // [nd][nt][ncp] projection weights V diag(wt sqrt(alpha/Nt))
+  float2* pw = nullptr;       // [nd][kDeflateMax][ncp] Phi^T W (long-packet CUDA-core projection)
   int* ncol = nullptr;        // [nd]
   // tensor-core projection
   int* tile_off = nullptr;    // [ntiles+1] CSR offsets of the windows meeting each 8x16 tile
