@@ -116,7 +116,37 @@ basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, f
     return up ? acc : cconj(acc);
   };
   if (gsm) {
-    for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = gsum(e / nt, e % nt);
+    if (nsplit == 1) {   // the upper triangle once (four loads in flight per thread), mirrored
+      const int nup = nt * (nt + 1) / 2;
+      for (int e0 = tid; e0 < nup; e0 += 4 * blockDim.x) {
+        float2 v[4];
+        int tt[4], uu[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = e0 + q * blockDim.x;
+          int t = 0, u = 0;
+          if (e < nup) {
+            const float tw = (float)(2 * nt + 1);
+            t = (int)floorf(0.5f * (tw - sqrtf(fmaxf(tw * tw - 8.f * (float)e, 0.f))));
+            t = t < 0 ? 0 : (t > nt - 1 ? nt - 1 : t);
+            while (t > 0 && t * nt - (t * (t - 1)) / 2 > e) --t;
+            while (t + 1 < nt && (t + 1) * nt - ((t + 1) * t) / 2 <= e) ++t;
+            u = t + (e - (t * nt - (t * (t - 1)) / 2));
+            v[q] = part[(size_t)t * nt + u];
+          }
+          tt[q] = e < nup ? t : -1;
+          uu[q] = u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (tt[q] < 0) continue;
+          G[tt[q] * nt + uu[q]] = v[q];
+          G[uu[q] * nt + tt[q]] = cconj(v[q]);
+        }
+      }
+    } else {
+      for (int e = tid; e < nt * nt; e += blockDim.x) G[e] = gsum(e / nt, e % nt);
+    }
     __syncthreads();
   }
   if (warp == 0) {   // largest diagonal entry
@@ -141,9 +171,16 @@ basis_kernel(const float2* __restrict__ part, int nsplit, int nt, int nd_defl, f
     for (int e = tid; e < nt * d; e += blockDim.x) {
       int t = e / d, j = e % d;
       float2 acc = make_float2(0.f, 0.f);
-      if (gsm)
-        for (int u = 0; u < nt; ++u) acc = cadd(acc, cmul(G[t * nt + u], Y[u * d + j]));
-      else
+      if (gsm) {   // four interleaved partial sums
+        float2 a4[4] = {acc, acc, acc, acc};
+        int u = 0;
+        for (; u + 4 <= nt; u += 4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a4[q] = cadd(a4[q], cmul(G[t * nt + u + q], Y[(u + q) * d + j]));
+        }
+        for (; u < nt; ++u) a4[0] = cadd(a4[0], cmul(G[t * nt + u], Y[u * d + j]));
+        acc = cadd(cadd(a4[0], a4[1]), cadd(a4[2], a4[3]));
+      } else
         for (int u = 0; u < nt; ++u) acc = cadd(acc, cmul(cscale(gsum(t, u), inv), Y[u * d + j]));
       Z[e] = acc;
     }

@@ -376,12 +376,20 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
   }
   __syncthreads();
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nt * nt; e += gridDim.x * blockDim.x) {
-    int i = e / nt, j = e % nt;
+  // upper triangle (row-wise enumeration), each entry written with its mirror
+  const int nup = nt * (nt + 1) / 2;
+  const float two_n1 = (float)(2 * nt + 1);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nup; e += gridDim.x * blockDim.x) {
+    int i = (int)floorf(0.5f * (two_n1 - sqrtf(fmaxf(two_n1 * two_n1 - 8.f * (float)e, 0.f))));
+    i = i < 0 ? 0 : (i > nt - 1 ? nt - 1 : i);
+    while (i > 0 && i * nt - (i * (i - 1)) / 2 > e) --i;
+    while (i + 1 < nt && (i + 1) * nt - ((i + 1) * i) / 2 <= e) ++i;
+    const int j = i + (e - (i * nt - (i * (i - 1)) / 2));
     double2 r = herm(i, j);
     add_w_terms(r, i, j, nd_defl, U, ph);
     if (i == j) r.y = 0.0;
-    R[(size_t)k * nt * nt + e] = r;
+    R[(size_t)k * nt * nt + (size_t)i * nt + j] = r;
+    if (i != j) R[(size_t)k * nt * nt + (size_t)j * nt + i] = make_double2(r.x, -r.y);
   }
 }
 
@@ -423,7 +431,8 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   }
   // the reduced sum sits in split 0 of each window: read it as a single split
   // with the window stride of the full buffer
-  dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
+  const int nup = P->nt * (P->nt + 1) / 2;
+  dim3 grid((nup + 255) / 256 < 8 ? (nup + 255) / 256 : 8, P->nd);
   gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ws.phi,
                                                  P->ws.xmax, P->tc_nsplit, P->q_nsplit, P->nt, P->ndefl, na,
                                                  P->ws.R);
