@@ -30,7 +30,7 @@
 namespace lcf {
 
 constexpr int PT_THREADS = 256;
-constexpr int PT_TZ = 8, PT_TX = 16;     // tile: 8 rows x 16 columns = 128 pixels
+constexpr int PT_TX = 16;                // tile: 16 columns x (8 rows, fewer for long packets)
 constexpr int PT_KS_MAX = 2;             // k-steps (16 K each) per weight stage, at most
 constexpr int PT_STAGES = 3;
 constexpr int PT_ACC = 256;              // TMEM columns per accumulator buffer (Yr at +0, Yi at +128)
@@ -42,17 +42,40 @@ __host__ __device__ inline int pt_kstep_bytes(int n16) { return 4 * n16 * 32; }
 // offset of (column c, k index kk < 16) inside one n16 x 16 sub-image (K-major, SBO = 256 B)
 __device__ __forceinline__ int pt_b_off(int c, int kk) { return (c >> 3) * 256 + (kk >> 3) * 128 + (c & 7) * 16 + (kk & 7) * 2; }
 
+// Long packets (Nt > kProjectShortNmax): the weight columns are taken in chunks of at most
+// PT_NCH (one accumulator buffer each), the image is chunk-major with 128-row sub-images
+// (PT_LKB bytes per k-step and chunk), and the tile keeps fewer pixel rows resident
+// (tile_rows(): 16 x tz pixels, the MMA's remaining rows read past the plane and are ignored).
+constexpr int PT_NCH = 128;
+constexpr int PT_LKB = 4 * PT_NCH * 32;
+constexpr size_t PT_SMEM_MAX = 232448;
+__host__ __device__ inline bool pt_long(int nt) { return nt > kProjectShortNmax; }
+__host__ __device__ inline int pt_nchunks(int n16) { return (n16 + PT_NCH - 1) / PT_NCH; }
+
 size_t project_tc_image_bytes(int nt, int nd_defl) {
-  return (size_t)(pt_k16(nt, nd_defl) / 16) * pt_kstep_bytes(pt_n16(nt));
+  const int nks = pt_k16(nt, nd_defl) / 16, n16 = pt_n16(nt);
+  if (pt_long(nt)) return (size_t)pt_nchunks(n16) * nks * PT_LKB;
+  return (size_t)nks * pt_kstep_bytes(n16);
 }
 
-size_t project_tc_smem_bytes(int nt, int nd_defl, int ksps) {
-  const int k16 = pt_k16(nt, nd_defl);
-  return 1024 + 4 * (size_t)128 * k16 * 2 + (size_t)PT_STAGES * ksps * pt_kstep_bytes(pt_n16(nt));
+static size_t pt_stage_bytes(int nt) { return pt_long(nt) ? (size_t)PT_LKB : (size_t)pt_kstep_bytes(pt_n16(nt)); }
+static size_t pt_smem(int nt, int nd_defl, int ksps, int rows) {
+  return 1024 + 4 * (size_t)rows * pt_k16(nt, nd_defl) * 2 + (size_t)PT_STAGES * ksps * pt_stage_bytes(nt);
+}
+// resident pixel rows of a tile: 128 for short packets, else the most that fit beside the ring
+int project_tc_tile_rows(int nt, int nd_defl) {
+  if (!pt_long(nt)) return 128;
+  int tz = 8;
+  while (tz > 1 && pt_smem(nt, nd_defl, 1, 16 * tz) > PT_SMEM_MAX) --tz;
+  return 16 * tz;
 }
 // k-steps per ring stage: two unless the stages would not fit beside the resident rows
 static int project_tc_ksps(int nt, int nd_defl) {
-  return project_tc_smem_bytes(nt, nd_defl, PT_KS_MAX) <= 232448 ? PT_KS_MAX : 1;
+  if (pt_long(nt)) return 1;
+  return pt_smem(nt, nd_defl, PT_KS_MAX, 128) <= PT_SMEM_MAX ? PT_KS_MAX : 1;
+}
+size_t project_tc_smem_bytes(int nt, int nd_defl, int ksps) {
+  return pt_smem(nt, nd_defl, ksps, project_tc_tile_rows(nt, nd_defl));
 }
 
 // ---------------------------------------------------------------------------
@@ -100,8 +123,11 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
   __syncthreads();
   const float s = tc::pow2_scale(red[0]);
   if (tid == 0) bscale[k] = s;
-  unsigned char* img = bimg + (size_t)k * (k16 / 16) * pt_kstep_bytes(n16max);
-  const int kb = pt_kstep_bytes(n16), sub = n16 * 32;
+  const bool lng = pt_long(nt);
+  const int nks = k16 / 16;
+  unsigned char* img = bimg + (size_t)k * (lng ? (size_t)pt_nchunks(n16max) * nks * PT_LKB
+                                               : (size_t)nks * pt_kstep_bytes(n16max));
+  const int kb = lng ? PT_LKB : pt_kstep_bytes(n16), sub = lng ? PT_NCH * 32 : n16 * 32;
   // one item = 8 consecutive rows t of column c: one 16-byte core-matrix row of each sub-image
   for (int e = tid; e < (k16 / 8) * n16; e += blockDim.x) {
     const int o = e / n16, c = e % n16, t0 = 8 * o;
@@ -120,7 +146,8 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
       tc::split_f16(v.x * s, hr[u], lr[u]);
       tc::split_f16(v.y * s, hi[u], li[u]);
     }
-    unsigned char* base = img + (size_t)(t0 >> 4) * kb + pt_b_off(c, t0 & 15);
+    unsigned char* base = lng ? img + ((size_t)(c / PT_NCH) * nks + (t0 >> 4)) * PT_LKB + pt_b_off(c % PT_NCH, t0 & 15)
+                              : img + (size_t)(t0 >> 4) * kb + pt_b_off(c, t0 & 15);
     *reinterpret_cast<uint4*>(base) = *reinterpret_cast<const uint4*>(hr);
     *reinterpret_cast<uint4*>(base + sub) = *reinterpret_cast<const uint4*>(lr);
     *reinterpret_cast<uint4*>(base + 2 * sub) = *reinterpret_cast<const uint4*>(hi);
@@ -131,7 +158,7 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PT_THREADS, 1)
 project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, int k16, int n16max,
-                  int ksps, int tiles_x, const int* __restrict__ tile_off, const int* __restrict__ tile_win,
+                  int ksps, int rows, int tiles_x, const int* __restrict__ tile_off, const int* __restrict__ tile_win,
                   const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
                   const int* __restrict__ ncol, const unsigned char* __restrict__ bimg,
                   const float* __restrict__ bscale, float* __restrict__ out, int* __restrict__ err) {
@@ -144,16 +171,18 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
   __shared__ uint32_t tmem_base;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x, z0 = (tile / tiles_x) * PT_TZ, x0 = (tile % tiles_x) * PT_TX;
+  const int tz = rows / PT_TX;   // tile: tz x 16 pixels (rows pixels), 128 MMA rows
+  const int tile = blockIdx.x, z0 = (tile / tiles_x) * tz, x0 = (tile % tiles_x) * PT_TX;
   const int w0 = tile_off[tile], w1 = tile_off[tile + 1];
   const int na = nt + nd_defl, nks = k16 / 16, nstw = (nks + ksps - 1) / ksps;
   const size_t npix = (size_t)nz * nx;
   const int a_sbo = (k16 / 8) * 128;
-  const size_t a_bytes = (size_t)128 * k16 * 2;            // one of Sr hi, Sr lo, Si hi, Si lo
+  const size_t a_bytes = (size_t)rows * k16 * 2;           // one of Sr hi, Sr lo, Si hi, Si lo
   unsigned char* A = smem;
   unsigned char* Bring = smem + 4 * a_bytes;
-  const size_t st_bytes = (size_t)ksps * pt_kstep_bytes(n16max);
-  const size_t img_stride = (size_t)nks * pt_kstep_bytes(n16max);
+  const bool lng = pt_long(nt);
+  const size_t st_bytes = (size_t)ksps * (lng ? (size_t)PT_LKB : (size_t)pt_kstep_bytes(n16max));
+  const size_t img_stride = lng ? (size_t)pt_nchunks(n16max) * nks * PT_LKB : (size_t)nks * pt_kstep_bytes(n16max);
   const float sA = tc::pow2_scale(__uint_as_float(*xmax_bits));
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
@@ -171,9 +200,9 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
 
   // ---- stage the tile's rows [c_p, a_p] (scaled, split hi/lo), zero K padding ----
   // item i: lane -> (row%8, k-pair), so a warp's 4-byte stores hit 32 distinct banks
-  for (int i = tid; i < 128 * (k16 / 2); i += PT_THREADS) {
-    const int ln = i & 31, rest = i >> 5;
-    const int m = (rest & 15) * 8 + (ln & 7), t = (rest >> 4) * 8 + (ln >> 3) * 2;
+  for (int i = tid; i < rows * (k16 / 2); i += PT_THREADS) {
+    const int ln = i & 31, rest = i >> 5, rg = rows / 8;
+    const int m = (rest % rg) * 8 + (ln & 7), t = (rest / rg) * 8 + (ln >> 3) * 2;
     const int z = z0 + (m >> 4), x = x0 + (m & 15);
     float2 v0 = make_float2(0.f, 0.f), v1 = v0;
     if (z < nz && x < nx) {
@@ -206,15 +235,17 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
       for (int wi = w0; wi < w1 && ok; ++wi) {
         const int k = tile_win[wi], nc = ncol[k];
         if (nc == 0) continue;
-        const int kb = pt_kstep_bytes(pt_n16(nc));
-        const unsigned char* img = bimg + (size_t)k * img_stride;
-        for (int s = 0; s < nstw; ++s, ++q) {
-          const int slot = q % PT_STAGES;
-          if (q >= PT_STAGES && !(ok = tc::mbar_wait(&empty_bar[slot], ((q / PT_STAGES) - 1) & 1))) break;
-          const int nk = min(ksps, nks - s * ksps);
-          const uint32_t bytes = (uint32_t)(nk * kb);
-          tc::mbar_arrive_expect_tx(&full_bar[slot], bytes);
-          tc::bulk_g2s(Bring + slot * st_bytes, img + (size_t)s * ksps * kb, bytes, &full_bar[slot]);
+        const int kb = lng ? PT_LKB : pt_kstep_bytes(pt_n16(nc)), nch = lng ? pt_nchunks(pt_n16(nc)) : 1;
+        for (int ch = 0; ch < nch && ok; ++ch) {
+          const unsigned char* img = bimg + (size_t)k * img_stride + (size_t)ch * nks * kb;
+          for (int s = 0; s < nstw; ++s, ++q) {
+            const int slot = q % PT_STAGES;
+            if (q >= PT_STAGES && !(ok = tc::mbar_wait(&empty_bar[slot], ((q / PT_STAGES) - 1) & 1))) break;
+            const int nk = min(ksps, nks - s * ksps);
+            const uint32_t bytes = (uint32_t)(nk * kb);
+            tc::mbar_arrive_expect_tx(&full_bar[slot], bytes);
+            tc::bulk_g2s(Bring + slot * st_bytes, img + (size_t)s * ksps * kb, bytes, &full_bar[slot]);
+          }
         }
       }
       // the copies still in flight land before the CTA exits
@@ -233,9 +264,11 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
       a_h[1] = tc::smem_u32(A + 2 * a_bytes);
       a_l[1] = tc::smem_u32(A + 3 * a_bytes);
       for (int wi = w0; wi < w1 && ok; ++wi) {
-        const int k = tile_win[wi], nc = ncol[k];
-        if (nc == 0) continue;
-        const int n16 = pt_n16(nc), kb = pt_kstep_bytes(n16), sub = n16 * 32;
+       const int k = tile_win[wi], nc = ncol[k];
+       const int n16w = pt_n16(nc), nch = nc == 0 ? 0 : (lng ? pt_nchunks(n16w) : 1);
+       for (int ch = 0; ch < nch && ok; ++ch) {
+        const int n16 = lng ? min(PT_NCH, n16w - ch * PT_NCH) : n16w;
+        const int kb = lng ? PT_LKB : pt_kstep_bytes(n16), sub = lng ? PT_NCH * 32 : n16 * 32;
         const int buf = j & 1;
         if (j >= 2 && !(ok = tc::mbar_wait(&acce[buf], ((j >> 1) - 1) & 1))) break;
         tc::fence_after();
@@ -277,6 +310,7 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
         if (!ok) break;
         tc::mma_commit(&accf[buf]);
         ++j;
+       }
       }
       // every MMA this thread issued has completed before TMEM is released
       if (j > 0) tc::mbar_wait(&accf[(j - 1) & 1], ((j - 1) >> 1) & 1, 200000000ull);
@@ -285,13 +319,14 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
     // ---------------- epilogue: |Y|^2 row sums, window weights, blend ----------------
     const int m = (warp - 4) * 32 + lane;
     const int z = z0 + (m >> 4), x = x0 + (m & 15);
-    const bool inside = z < nz && x < nx;
+    const bool inside = m < rows && z < nz && x < nx;
     float pd = 0.f;
     int j = 0;
-    for (int wi = w0; wi < w1; ++wi) {
-      const int k = tile_win[wi], nc = ncol[k];
-      if (nc == 0) continue;
-      const int n16 = pt_n16(nc), buf = j & 1;
+    for (int wi = w0; wi < w1 && ok; ++wi) {
+     const int k = tile_win[wi], nc = ncol[k];
+     const int n16w = pt_n16(nc), nch = nc == 0 ? 0 : (lng ? pt_nchunks(n16w) : 1);
+     for (int ch = 0; ch < nch; ++ch) {
+      const int n16 = lng ? min(PT_NCH, n16w - ch * PT_NCH) : n16w, buf = j & 1;
       // warp-uniform outcome: the TMEM loads below are .sync.aligned
       if (!(ok = __all_sync(~0u, tc::mbar_wait(&accf[buf], (j >> 1) & 1)))) break;
       tc::fence_after();
@@ -316,6 +351,7 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
         pd = fmaf(g * g * inv * inv, acc, pd);
       }
       ++j;
+     }
     }
     if (inside) out[(size_t)z * nx + x] = pd;
   }
@@ -333,16 +369,16 @@ cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st) {
                                              P->ws.bimg, P->ws.bscale);
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
-  const int ksps = project_tc_ksps(P->nt, P->ndefl);
+  const int ksps = project_tc_ksps(P->nt, P->ndefl), rows = project_tc_tile_rows(P->nt, P->ndefl);
   project_tc_kernel<<<P->ptiles_z * P->ptiles_x, PT_THREADS, project_tc_smem_bytes(P->nt, P->ndefl, ksps), st>>>(
-      P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, k16, n16max, ksps, P->ptiles_x, P->ws.tile_off, P->ws.tile_win, P->ws.gz,
+      P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, k16, n16max, ksps, rows, P->ptiles_x, P->ws.tile_off, P->ws.tile_win, P->ws.gz,
       P->ws.gx, P->ws.xmax, P->ws.ncol, P->ws.bimg, P->ws.bscale, out, P->ws.err);
   return counted(P);
 }
 
 cudaError_t project_tc_configure() {
   size_t mx = 0;   // the largest launch over every packet length (two or one k-steps per stage)
-  for (int nt = 2; nt <= kProjectShortNmax; ++nt) {
+  for (int nt = 2; nt <= kEvdNmax; ++nt) {
     const int d = deflate_count(nt);
     const size_t b = project_tc_smem_bytes(nt, d, project_tc_ksps(nt, d));
     mx = b > mx ? b : mx;
@@ -352,13 +388,14 @@ cudaError_t project_tc_configure() {
 
 void project_tc_tiles(const lcf_plan* P, int* tiles_z, int* tiles_x, std::vector<int>& off, std::vector<int>& win) {
   const lcf_config& c = P->cfg;
-  *tiles_z = (c.nz + PT_TZ - 1) / PT_TZ;
+  const int trz = project_tc_tile_rows(P->nt, P->ndefl) / PT_TX;   // tile rows (z)
+  *tiles_z = (c.nz + trz - 1) / trz;
   *tiles_x = (c.nx + PT_TX - 1) / PT_TX;
   off.assign(1, 0);
   win.clear();
   for (int tz = 0; tz < *tiles_z; ++tz)
     for (int tx = 0; tx < *tiles_x; ++tx) {
-      const int za = tz * PT_TZ, zb = za + PT_TZ, xa0 = tx * PT_TX, xb = xa0 + PT_TX;
+      const int za = tz * trz, zb = za + trz, xa0 = tx * PT_TX, xb = xa0 + PT_TX;
       for (int k = 0; k < P->nd; ++k) {
         const Box& b = P->boxes[k];
         if (b.z1 <= b.z0 || b.x1 <= b.x0) continue;

@@ -59,7 +59,6 @@ static lcf_status validate(const lcf_config* c) {
   if (c->thresh_mode == LCF_T_LEARNED && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
   if (c->thresh_mode == LCF_T_LEARNED && (c->evd_path != LCF_EVD_PAIR || c->nt > kEvdPairNmax))
     return LCF_EUNSUPPORTED;
-  if (c->project_path == LCF_PATH_TC && c->nt > kProjectShortNmax) return LCF_EUNSUPPORTED;
   if (c->thresh_mode == LCF_T_SIGMOID && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
   if (!isfinite(c->beta) || !isfinite(c->beta_src)) return LCF_EINVAL;
   if (c->pd_mode < 0 || c->pd_mode > 1 || c->alpha_mode < 0 || c->alpha_mode > 2) return LCF_EINVAL;

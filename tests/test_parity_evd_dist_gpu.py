@@ -30,6 +30,23 @@ def test_dist_shapes(shape, grid, mode):
     check(compare(rand_iq(7, nt, nz, nx), cfg, oc, want_gram=False), soft=mode == "LCF_T_ADAPTIVE_SOFT")
 
 
+@pytest.mark.parametrize("shape,grid,mode", [
+    ((129, 33, 29), (2, 2), "LCF_T_MEDIAN"),       # shortest long packet: 128-row tiles, two column chunks
+    ((200, 40, 36), (2, 2), "LCF_T_CURVATURE"),    # 96-row tiles, two chunks
+    ((200, 40, 36), (2, 2), "LCF_T_ADAPTIVE_SOFT"),  # every column kept
+    ((300, 36, 30), (2, 2), "LCF_T_CURVATURE"),    # 64-row tiles, three chunks
+    ((320, 20, 20), (1, 1), "LCF_T_ADAPTIVE_SOFT"),  # longest packet, three chunks
+])
+def test_long_tensor_core_projection(shape, grid, mode):
+    """Tensor-core projection of long packets (fewer resident tile rows, weight columns in
+    chunks of 128) with the distributed EVD and the CUDA-core Gram."""
+    lib = L()
+    nt, nz, nx = shape
+    cfg, oc = pair_cfg(nz, nx, nt, grid[0], grid[1], thresh_mode=getattr(lib, mode), k_fixed=3, beta=1.0)
+    cfg.project_path = lib.LCF_PATH_TC
+    check(compare(rand_iq(8, nt, nz, nx), cfg, oc, want_gram=False), soft=mode == "LCF_T_ADAPTIVE_SOFT")
+
+
 def test_dist_zero_packet_is_degenerate():
     import torch
     lib = L()
@@ -44,8 +61,8 @@ def test_dist_zero_packet_is_degenerate():
 def test_long_packet_limits():
     lib = L()
     for kw, want in (({"nt": 321, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_EUNSUPPORTED),
-                     ({"nt": 200, "evd_path": lib.LCF_EVD_PAIR, "project_path": lib.LCF_PATH_TC},
-                      lib.LCF_EUNSUPPORTED),
+                     ({"nt": 200, "evd_path": lib.LCF_EVD_PAIR, "project_path": lib.LCF_PATH_TC}, lib.LCF_OK),
+                     ({"nt": 320, "evd_path": lib.LCF_EVD_PAIR, "project_path": lib.LCF_PATH_TC}, lib.LCF_OK),
                      ({"nt": 200, "evd_path": lib.LCF_EVD_PAIR, "thresh_mode": lib.LCF_T_LEARNED},
                       lib.LCF_EUNSUPPORTED),
                      ({"nt": 320, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK)):

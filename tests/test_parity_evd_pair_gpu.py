@@ -102,8 +102,7 @@ def test_packet_length_limits():
                      ({"nt": 128, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),
                      ({"nt": 128, "evd_path": lib.LCF_EVD_CTA}, lib.LCF_EUNSUPPORTED),
                      ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),          # distributed EVD
-                     ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR, "project_path": lib.LCF_PATH_TC},
-                      lib.LCF_EUNSUPPORTED),
+                     ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR, "project_path": lib.LCF_PATH_TC}, lib.LCF_OK),
                      ({"nt": 124, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK)):
         c = lib.lcf_config_default(32, 32, kw["nt"], 2, 2)
         for k, v in kw.items():
