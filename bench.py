@@ -239,7 +239,7 @@ def stream_workload(args):
     del frames
     out = torch.empty((npk, nz, nx), dtype=torch.float32, device=f"cuda:{local}")
     plan = L.Plan.make(nz, nx, nt, wz, wx, device=local, thresh_mode=L.LCF_T_ADAPTIVE_SOFT, beta=1.0,
-                       gram_path=L.LCF_PATH_SIMT, project_path=L.LCF_PATH_TC, evd_path=L.LCF_EVD_PAIR)
+                       gram_path=L.LCF_PATH_TC, project_path=L.LCF_PATH_TC, evd_path=L.LCF_EVD_PAIR)
     st = torch.cuda.current_stream()
     plan.filter_stream(d, stride, out)          # captures the stream graph
     torch.cuda.synchronize()

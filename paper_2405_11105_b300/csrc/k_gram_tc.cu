@@ -249,6 +249,191 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
+
+// ---------------------------------------------------------------------------
+// Long packets (Nt > 128 residual rows): the Nt x Nt residual block in row tiles of tb
+// rows (T tiles), one CTA per (window, tile pair (a, b)) over the whole window support.
+// The CTA forms D'(a, b) = A_hi(a) (B_hi(b) + 2 B_lo(b))^T with the operands of the short
+// kernel (B(b) = [w ; -i w] of tile b's rows), A from tile a's rows (aliasing B_hi when
+// a == b); both orders of every off-diagonal pair are formed, so the assembly takes the
+// Hermitian part 1/2 (D'(a, b) + D'(b, a)^H) as before.  The split reads the packet
+// directly (no fp32 staging: the two tiles' rows would not fit beside the stages).
+constexpr int TB_STAGES = 3;
+__host__ __device__ inline size_t tcb_stage_bytes(int tb, bool same) {
+  const int nbh = tc_nbh(tb), rh = same ? tc_rows_hi(nbh) : 2 * nbh;
+  return (same ? 0 : (size_t)128 * TG_K * 2) + (size_t)rh * TG_K * 2 + (size_t)2 * nbh * TG_K * 2;
+}
+size_t gram_tcb_smem_bytes(int tb) {
+  const size_t a = tcb_stage_bytes(tb, true), b = tcb_stage_bytes(tb, false);
+  return 1024 + TB_STAGES * (a > b ? a : b);
+}
+
+__global__ void __launch_bounds__(TG_THREADS, 1)
+gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, int T, const Box* __restrict__ boxes,
+                const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
+                double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t mma_bar[TB_STAGES];
+  __shared__ __align__(8) uint64_t acc_bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int pix_s[TG_PX];
+  __shared__ float gg_s[TG_PX];
+
+  const int k = blockIdx.y, ta = blockIdx.x / T, tbk = blockIdx.x % T;
+  const bool same = ta == tbk;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ra0 = ta * tb, rna = min(tb, nt - ra0), rb0 = tbk * tb, rnb = min(tb, nt - rb0);
+  const int nbh = tc_nbh(rnb), N = 2 * nbh, rh = same ? tc_rows_hi(nbh) : N;
+  const size_t a_bytes = same ? 0 : (size_t)128 * TG_K * 2, hi_bytes = (size_t)rh * TG_K * 2;
+  const size_t st_bytes = a_bytes + hi_bytes + (size_t)N * TG_K * 2;
+  const Box b = boxes[k];
+  const int W = b.x1 - b.x0;
+  const long Pk = (long)(b.z1 - b.z0) * W;
+  const int nst = (int)((Pk + TG_PX - 1) / TG_PX);
+  const size_t npix = (size_t)nz * nx;
+  const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
+  const float* gzk = gz + (size_t)k * nz;
+  const float* gxk = gx + (size_t)k * nx;
+  const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
+
+  for (size_t e = tid; e < TB_STAGES * st_bytes / 16; e += TG_THREADS)
+    reinterpret_cast<uint4*>(smem)[e] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    for (int i = 0; i < TB_STAGES; ++i) tc::mbar_init(&mma_bar[i], 1);
+    tc::mbar_init(&acc_bar[0], 1);
+    tc::mbar_init(&acc_bar[1], 1);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t idesc = tc::idesc_f16(128, N);
+
+  float sums[TG_NBH_MAX];
+#pragma unroll
+  for (int j = 0; j < TG_NBH_MAX; ++j) sums[j] = 0.f;
+  bool ok = true;
+  auto epilogue = [&](int c) {
+    if (ok) ok = tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);
+    tc::fence_after();
+    const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
+#pragma unroll
+    for (int cc = 0; cc < TG_NBH_MAX / 16; cc += 2) {
+      if (cc * 16 < nbh) {
+        uint32_t v0[16], v1[16];
+        tc::tmem_ld16_async(base + cc * 16, v0);
+        if ((cc + 1) * 16 < nbh) tc::tmem_ld16_async(base + (cc + 1) * 16, v1);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += __uint_as_float(v0[j]);
+        if ((cc + 1) * 16 < nbh) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sums[(cc + 1) * 16 + j] += __uint_as_float(v1[j]);
+        }
+      }
+    }
+    tc::fence_before();
+  };
+
+  int next_epi = 0;
+  for (int i = 0; i < nst; ++i) {
+    const int si = i % TB_STAGES;
+    unsigned char* Ahi = smem + si * st_bytes;
+    unsigned char* Bhi = Ahi + a_bytes;
+    unsigned char* Blo = Bhi + hi_bytes;
+    if (tid < TG_PX) {
+      const long l = (long)i * TG_PX + tid;
+      int pp = 0;
+      float g = 0.f;
+      if (l < Pk) {
+        const int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
+        pp = z * nx + x;
+        g = gzk[z] * gxk[x] * sc;
+      }
+      pix_s[tid] = pp;
+      gg_s[tid] = g;
+    }
+    if (i >= TB_STAGES && ok) ok = tc::mbar_wait(&mma_bar[si], ((i / TB_STAGES) - 1) & 1);
+    __syncthreads();
+    {
+      // two adjacent pixels of the slab and rows 16 j + lane / 2 per thread (as the short kernel)
+      const int pp = 2 * (((tid >> 5) & 7) * 2 + (lane & 1)), rl = lane >> 1;
+      const float g0 = gg_s[pp], g1 = gg_s[pp + 1];
+      const size_t p0 = pix_s[pp], p1 = pix_s[pp + 1];
+      const int kk = 2 * pp;
+      const __half two = __float2half(2.f);
+      for (int r = rl; r < rnb; r += 16) {
+        const float2* src = xa + (size_t)(rb0 + r) * npix;
+        const float2 v0 = src[p0], v1 = src[p1];
+        __half hr0, lr0, hm0, lm0, hr1, lr1, hm1, lm1;
+        tc::split_f16(v0.x * g0, hr0, lr0);
+        tc::split_f16(v0.y * g0, hm0, lm0);
+        tc::split_f16(v1.x * g1, hr1, lr1);
+        tc::split_f16(v1.y * g1, hm1, lm1);
+        const __half lr0b = __hmul(lr0, two), lm0b = __hmul(lm0, two), lr1b = __hmul(lr1, two), lm1b = __hmul(lm1, two);
+        __half2 w[2];
+        w[0] = __halves2half2(hr0, hm0); w[1] = __halves2half2(hr1, hm1);
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        w[0] = __halves2half2(hm0, __hneg(hr0)); w[1] = __halves2half2(hm1, __hneg(hr1));
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        w[0] = __halves2half2(lr0b, lm0b); w[1] = __halves2half2(lr1b, lm1b);
+        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        w[0] = __halves2half2(lm0b, __hneg(lr0b)); w[1] = __halves2half2(lm1b, __hneg(lr1b));
+        *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+      }
+      if (!same) {
+        for (int r = rl; r < rna; r += 16) {
+          const float2* src = xa + (size_t)(ra0 + r) * npix;
+          const float2 v0 = src[p0], v1 = src[p1];
+          __half hr0, lr0, hm0, lm0, hr1, lr1, hm1, lm1;
+          tc::split_f16(v0.x * g0, hr0, lr0);
+          tc::split_f16(v0.y * g0, hm0, lm0);
+          tc::split_f16(v1.x * g1, hr1, lr1);
+          tc::split_f16(v1.y * g1, hm1, lm1);
+          __half2 w[2];
+          w[0] = __halves2half2(hr0, hm0); w[1] = __halves2half2(hr1, hm1);
+          *reinterpret_cast<uint2*>(Ahi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        }
+      }
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    const int c = i / TG_CPA;
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t d = tbase + (uint32_t)((c & 1) * 256);
+      const uint32_t ah = tc::smem_u32(same ? Bhi : Ahi), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll
+      for (int ks = 0; ks < TG_K / 16; ++ks) {
+        const uint64_t ad = tc::smem_desc(ah + ks * 256, 128, TG_SBO);
+        const uint64_t hd = tc::smem_desc(bh + ks * 256, 128, TG_SBO);
+        const uint64_t ld = tc::smem_desc(bl + ks * 256, 128, TG_SBO);
+        tc::mma_f16(d, ad, hd, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
+        tc::mma_f16(d, ad, ld, idesc, 1u);
+      }
+      tc::mma_commit(&mma_bar[si]);
+      if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
+    }
+    if (i % TG_CPA == TG_CPA / 2 && c > 0) { epilogue(c - 1); next_epi = c; }
+  }
+  for (int e = next_epi; nst > 0 && e <= (nst - 1) / TG_CPA; ++e) epilogue(e);
+  if (!ok && lane == 0) atomicOr(err, 1);
+
+  // block partial: plane 0 = Re D', plane 1 = Im D' (rows i < rna, columns j < rnb), stride tb
+  double* out = part + ((((size_t)k * T + ta) * T + tbk) * 2 + half) * (size_t)tb * tb;
+  if (row < rna) {
+#pragma unroll
+    for (int j = 0; j < TG_NBH_MAX; ++j)
+      if (j < rnb) out[(size_t)row * tb + j] = (double)sums[j];
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
 // Coefficient block Q[a][b] = sum_p g^2 conj(a_pa) a_pb with exact products
 // (double-float), one partial per (window, split).
 __global__ void __launch_bounds__(256)
@@ -311,11 +496,12 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
 __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const double2* __restrict__ qpart,
                                         const double2* __restrict__ aug, int aug_nsplit,
                                         const float2* __restrict__ phi, const unsigned* __restrict__ xmax_bits,
-                                        int nsplit, int qsplit, int nt, int nd_defl, int nb,
+                                        size_t wstride, int T, int tb, int qsplit, int nt, int nd_defl, int nb,
                                         double2* __restrict__ R) {
+  // partials of window k: tile pairs (a, b) of tb rows, [a][b][Re, Im][tb][tb] (T = 1, tb = nb for
+  // packets whose augmented rows fit one tile)
   const int k = blockIdx.y;
-  const int na = nb;   // row length of the tensor-core partials
-  const double* pk = part + (size_t)k * nsplit * 2 * na * na;
+  const double* pk = part + (size_t)k * wstride;
   __shared__ double2 U[kEvdNmax][kDeflateMax];
   __shared__ double2 Q[kDeflateMax][kDeflateMax];
   __shared__ double2 ph[kDeflateMax][kEvdNmax];
@@ -328,11 +514,14 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   const double is2 = inv_s2;
   // Hermitian part of the summed D' at (a, b)
   // (split 0 of each window holds the sum over splits, see gram_tc_reduce_kernel)
+  const size_t t2 = (size_t)tb * tb;
+  auto dre = [&](int a, int bb, int plane) {   // plane of D' at (a, bb)
+    const int ta = a / tb, tbk = bb / tb;
+    return pk[((size_t)(ta * T + tbk) * 2 + plane) * t2 + (size_t)(a - ta * tb) * tb + (bb - tbk * tb)];
+  };
   auto herm = [&](int a, int bb) {
-    const double* re = pk;
-    const double* im = re + (size_t)na * na;
-    const double xr = re[(size_t)a * na + bb] + re[(size_t)bb * na + a];
-    const double xi = im[(size_t)a * na + bb] - im[(size_t)bb * na + a];
+    const double xr = dre(a, bb, 0) + dre(bb, a, 0);
+    const double xi = dre(a, bb, 1) - dre(bb, a, 1);
     return make_double2(0.5 * xr * is2, 0.5 * xi * is2);
   };
   const double2* ak = aug + (size_t)k * aug_nsplit * nt * nd_defl;
@@ -396,10 +585,16 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
 cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   const int na = P->tc_na;
-  dim3 grid(P->tc_nsplit, P->nd);
-  gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
-                                                                    P->ws.gx, P->ws.xmax, P->tc_nsplit,
-                                                                    gram_tc_stages(na), P->ws.gtc, P->ws.err);
+  if (P->tc_T > 1) {
+    dim3 gb(P->tc_T * P->tc_T, P->nd);
+    gram_tcb_kernel<<<gb, TG_THREADS, gram_tcb_smem_bytes(P->tc_tb), st>>>(
+        P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc, P->ws.err);
+  } else {
+    dim3 grid(P->tc_nsplit, P->nd);
+    gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
+                                                                      P->ws.gx, P->ws.xmax, P->tc_nsplit,
+                                                                      gram_tc_stages(na), P->ws.gtc, P->ws.err);
+  }
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
   gram_q_kernel<<<dim3(P->q_nsplit, P->nd), 256, 0, st>>>(P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->ws.box,
@@ -423,7 +618,7 @@ __global__ void gram_tc_reduce_kernel(double* __restrict__ part, int nsplit, siz
 cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   const int na = P->tc_na;
   const size_t per_split = (size_t)2 * na * na;
-  if (P->tc_nsplit > 1) {
+  if (P->tc_T == 1 && P->tc_nsplit > 1) {
     dim3 gr((unsigned)((per_split + 255) / 256), P->nd);
     gram_tc_reduce_kernel<<<gr, 256, 0, st>>>(P->ws.gtc, P->tc_nsplit, per_split);
     cudaError_t e = counted(P);
@@ -434,7 +629,10 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   const int nup = P->nt * (P->nt + 1) / 2;
   dim3 grid((nup + 255) / 256 < 8 ? (nup + 255) / 256 : 8, P->nd);
   gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ws.phi,
-                                                 P->ws.xmax, P->tc_nsplit, P->q_nsplit, P->nt, P->ndefl, na,
+                                                 P->ws.xmax,
+                                                 P->tc_T > 1 ? (size_t)P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
+                                                             : (size_t)P->tc_nsplit * per_split,
+                                                 P->tc_T, P->tc_tb, P->q_nsplit, P->nt, P->ndefl, na,
                                                  P->ws.R);
   return counted(P);
 }
@@ -442,7 +640,10 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
 cudaError_t gram_tc_configure() {
   size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
   for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
-  return cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(gram_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gram_tcb_smem_bytes(kTcTileMax));
 }
 
 }  // namespace lcf

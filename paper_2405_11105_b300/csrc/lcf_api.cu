@@ -69,7 +69,6 @@ static lcf_status validate(const lcf_config* c) {
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
   if (c->evd_path == LCF_EVD_CTA && c->nt > kEvdCtaNmax) return LCF_EUNSUPPORTED;
-  if (c->gram_path == LCF_PATH_TC && c->nt > kTcGramNaMax) return LCF_EUNSUPPORTED;
   return LCF_OK;
 }
 
@@ -172,6 +171,14 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     P->tc_nsplit = (int)(ts < 1 ? 1 : (ts > 64 ? 64 : ts));
   }
   P->tc_na = P->n1 <= kTcGramNaMax ? P->n1 : P->nt;
+  if (P->tc_na > kTcGramNaMax) {   // long packets: tile pairs of at most kTcTileMax rows, no pixel splits
+    P->tc_T = (P->nt + kTcTileMax - 1) / kTcTileMax;
+    P->tc_tb = ((P->nt + P->tc_T - 1) / P->tc_T + 7) / 8 * 8;
+    P->tc_nsplit = 1;
+  } else {
+    P->tc_T = 1;
+    P->tc_tb = P->tc_na;
+  }
   P->ncp = P->nt <= kProjectShortNmax ? 4 * project_cpt(P->nt) : (P->nt + 15) / 16 * 16;
   std::vector<float> gz, gx;
   build_geometry(*cfg, P->boxes, gz, gx);
@@ -191,7 +198,9 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.xmax, 1, &tot);
   if (e == cudaSuccess) e = dalloc(&w.err, 1, &tot);
   if (cfg->gram_path == LCF_PATH_TC) {
-    if (e == cudaSuccess) e = dalloc(&w.gtc, nd * P->tc_nsplit * 2 * P->tc_na * P->tc_na, &tot);
+    if (e == cudaSuccess)
+      e = dalloc(&w.gtc, P->tc_T > 1 ? nd * P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
+                                      : nd * P->tc_nsplit * 2 * P->tc_na * P->tc_na, &tot);
     if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kDeflateMax * kDeflateMax, &tot);
   }
   if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);

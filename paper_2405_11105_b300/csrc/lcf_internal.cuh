@@ -24,6 +24,7 @@ constexpr int kEvdCtaNmax = 112;
 constexpr int kProjectShortNmax = 128;
 // Largest augmented row (Nt + deflation vectors) of the tensor-core Gram (one M = 128 tile).
 constexpr int kTcGramNaMax = 128;
+constexpr int kTcTileMax = 112;   // row tile of the long-packet tensor-core Gram (three stages fit)
 // Subspace-iteration block of the EVD (head directions isolated exactly).
 constexpr int kEvdHead = 8;
 // Slow-time DCT-II vectors deflated from every pixel before the Gram.
@@ -56,7 +57,8 @@ struct Workspace {
   double2* gpart = nullptr;   // [nd][nsplit][nt][nt] partial residual Grams
   double2* gaug = nullptr;    // [nd][aug_nsplit][(nt+ndefl)*ndefl] partial augmented columns
   unsigned* xmax = nullptr;   // [1] max |component| of the deflated packet (float bits)
-  double* gtc = nullptr;      // [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes)
+  double* gtc = nullptr;      // [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes),
+                              // or [nd][T][T][2][tb][tb] tile-pair partials for long packets
   double2* gq = nullptr;      // [nd][q_nsplit][kDeflateMax^2] exact coefficient-block partials
   int* err = nullptr;         // [1] device error word (bit 0: a bounded wait gave up)
   double2* R = nullptr;       // [nd][nt][nt] windowed Gram (Eq. 12)
@@ -99,6 +101,7 @@ struct lcf_plan {
   int aug_nsplit = 1;   // pixel splits of the augmented-column kernel
   int tc_nsplit = 1;    // pixel ranges per window of the tensor-core Gram
   int tc_na = 0;        // rows of the tensor-core Gram: nt + ndefl when that fits one MMA tile, else nt
+  int tc_T = 1, tc_tb = 0;  // row tiles of the residual block (T > 1 for Nt > 128) and their size
                         // (the coefficient columns U then come from the CUDA-core kernel)
   int q_nsplit = 1;     // pixel splits of the exact coefficient-block kernel
   int basis_nsplit = 1; // pixel splits of the global Gram behind the deflation basis

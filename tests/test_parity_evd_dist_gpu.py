@@ -47,6 +47,25 @@ def test_long_tensor_core_projection(shape, grid, mode):
     check(compare(rand_iq(8, nt, nz, nx), cfg, oc, want_gram=False), soft=mode == "LCF_T_ADAPTIVE_SOFT")
 
 
+@pytest.mark.parametrize("shape,grid,mode", [
+    ((129, 33, 29), (2, 2), "LCF_T_MEDIAN"),        # two row tiles of 72 / 57 rows
+    ((200, 40, 36), (2, 2), "LCF_T_CURVATURE"),     # two tiles of 104 / 96 rows (the streaming length)
+    ((256, 24, 20), (1, 2), "LCF_T_SLOPE"),         # three tiles of 88 rows
+    ((300, 36, 30), (2, 2), "LCF_T_ADAPTIVE_SOFT"), # three tiles of 104 / 104 / 92 rows
+    ((320, 20, 20), (1, 1), "LCF_T_CURVATURE"),     # three tiles of 112 / 112 / 96 rows
+])
+def test_long_tensor_core_gram(shape, grid, mode):
+    """Tensor-core Gram of long packets (tile pairs of at most 112 residual rows, both
+    orders of each off-diagonal pair), with the tensor-core projection and the distributed EVD."""
+    lib = L()
+    nt, nz, nx = shape
+    cfg, oc = pair_cfg(nz, nx, nt, grid[0], grid[1], thresh_mode=getattr(lib, mode), k_fixed=3, beta=1.0, tc=True)
+    r = compare(rand_iq(9, nt, nz, nx), cfg, oc, want_gram=True)
+    print("gram", r["gram_err"])
+    assert r["gram_err"] <= 1e-6
+    check(r, soft=mode == "LCF_T_ADAPTIVE_SOFT")
+
+
 def test_dist_zero_packet_is_degenerate():
     import torch
     lib = L()

@@ -98,7 +98,7 @@ def test_pair_nt128_with_tensor_core_projection(mode):
 
 def test_packet_length_limits():
     lib = L()
-    for kw, want in (({"nt": 129, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_EUNSUPPORTED),
+    for kw, want in (({"nt": 129, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),
                      ({"nt": 128, "gram_path": lib.LCF_PATH_TC, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),
                      ({"nt": 128, "evd_path": lib.LCF_EVD_CTA}, lib.LCF_EUNSUPPORTED),
                      ({"nt": 129, "evd_path": lib.LCF_EVD_PAIR}, lib.LCF_OK),          # distributed EVD
