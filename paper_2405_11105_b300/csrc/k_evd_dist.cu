@@ -302,7 +302,7 @@ __host__ __device__ inline size_t ed_align(size_t x) { return (x + 15) & ~(size_
 // evd_dist_kernel shared-memory layout (every CTA of the cluster the same)
 struct EdLayout {
   int np, h, C, nsmax, vmax;
-  size_t rows, v, rec, dq, tb, bb, end;
+  size_t rows, v, rec, dq, tb, bb, ta, end;
 };
 __host__ __device__ inline EdLayout ed_layout(int n, int C) {
   EdLayout L;
@@ -318,6 +318,7 @@ __host__ __device__ inline EdLayout ed_layout(int n, int C) {
   L.dq = o;   o = ed_align(o + (size_t)L.h * 8);                         // new diagonal of own pairs
   L.tb = o;   o = ed_align(o + (size_t)L.nsmax * 4);                     // buffer of each own pair's top row
   L.bb = o;   o = ed_align(o + (size_t)L.nsmax * 4);                     // ... and bottom row
+  L.ta = o;   o = ed_align(o + (size_t)L.nsmax * 4);                     // first index of each own pair
   L.end = o;
   return L;
 }
@@ -354,6 +355,7 @@ evd_dist_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, c
   float2* dq = reinterpret_cast<float2*>(smem + L.dq);
   int* tb = reinterpret_cast<int*>(smem + L.tb);
   int* bb = reinterpret_cast<int*>(smem + L.bb);
+  int* ta_s = reinterpret_cast<int*>(smem + L.ta);    // first index of each own pair at this step
   const double scale = scale_g[k];
 
   if (!(scale > 0.0)) {   // degenerate window (zero Gram): every CTA writes its share of the empty result
@@ -419,6 +421,7 @@ evd_dist_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, c
         int ta, ba;
         if (i == 0) { ta = r; ba = np - 1; }
         else { ta = (r + i) % (np - 1); ba = (r - i + np - 1) % (np - 1); }
+        ta_s[ls] = ta;
         const float2* Rt = rows + (size_t)tb[ls] * np;
         const float2* Rb = rows + (size_t)bb[ls] * np;
         const bool tlow = ta < ba;
@@ -467,9 +470,7 @@ evd_dist_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, c
           const unsigned ma = __float_as_uint(ra.w), mbits = __float_as_uint(rb.w);
           if (!((ma | mbits) & ED_REC_ROT)) continue;
           const int pa = ma & 1023, qa = (ma >> 10) & 1023, pb = mbits & 1023, qb = (mbits >> 10) & 1023;
-          int ta;
-          if (i == 0) ta = r;
-          else ta = (r + i) % (np - 1);
+          const int ta = ta_s[ls];
           float2* Rp = rows + (size_t)(ta == pa ? tb[ls] : bb[ls]) * np;
           float2* Rq = rows + (size_t)(ta == pa ? bb[ls] : tb[ls]) * np;
           if (t == i) {
@@ -522,26 +523,31 @@ evd_dist_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, c
       //     (slot 0 keeps Np-1; slot 1 takes slot 0's first index; the last slot's first index is
       //     the old second index of the last slot).  Buffers of rows that left take the arrivals.
       __shared__ int sh_in[2];
-      if (tid == 0) {
+      {
         const int T0 = tb[0], Bl = bb[ns - 1], B0 = bb[0];
-        for (int ls = 0; ls + 1 < ns; ++ls) tb[ls] = tb[ls + 1];
-        for (int ls = ns - 1; ls >= 1; --ls) bb[ls] = bb[ls - 1];
-        int in_top = -1, in_bot = -1;
-        if (rank == 0) {
-          bb[0] = B0;
-          bb[1] = T0;
-        } else {
-          in_bot = (rank + 1 < C) ? Bl : T0;
-          bb[0] = in_bot;
+        // shifted roles, read before any is written
+        const int ntb = tid + 1 < ns ? tb[tid + 1] : 0, nbb = (tid >= 1 && tid < ns) ? bb[tid - 1] : 0;
+        __syncthreads();
+        if (tid + 1 < ns) tb[tid] = ntb;
+        if (tid >= 1 && tid < ns && !(rank == 0 && tid == 1)) bb[tid] = nbb;   // rank 0's bb[1] is set below
+        if (tid == 0) {
+          int in_top = -1, in_bot = -1;
+          if (rank == 0) {
+            bb[0] = B0;
+            bb[1] = T0;
+          } else {
+            in_bot = (rank + 1 < C) ? Bl : T0;
+            bb[0] = in_bot;
+          }
+          if (rank + 1 < C) {
+            in_top = (rank > 0) ? T0 : Bl;
+            tb[ns - 1] = in_top;
+          } else {
+            tb[ns - 1] = Bl;
+          }
+          sh_in[0] = in_top;
+          sh_in[1] = in_bot;
         }
-        if (rank + 1 < C) {
-          in_top = (rank > 0) ? T0 : Bl;
-          tb[ns - 1] = in_top;
-        } else {
-          tb[ns - 1] = Bl;
-        }
-        sh_in[0] = in_top;
-        sh_in[1] = in_bot;
       }
       __syncthreads();
       if (sh_in[0] >= 0) {   // the top row that came from rank + 1
