@@ -302,7 +302,7 @@ __host__ __device__ inline size_t ed_align(size_t x) { return (x + 15) & ~(size_
 // evd_dist_kernel shared-memory layout (every CTA of the cluster the same)
 struct EdLayout {
   int np, h, C, nsmax, vmax;
-  size_t rows, v, rec, dq, tb, bb, ta, end;
+  size_t rows, v, rec, dq, tb, bb, ta, dg, fl, end;
 };
 __host__ __device__ inline EdLayout ed_layout(int n, int C) {
   EdLayout L;
@@ -319,6 +319,8 @@ __host__ __device__ inline EdLayout ed_layout(int n, int C) {
   L.tb = o;   o = ed_align(o + (size_t)L.nsmax * 4);                     // buffer of each own pair's top row
   L.bb = o;   o = ed_align(o + (size_t)L.nsmax * 4);                     // ... and bottom row
   L.ta = o;   o = ed_align(o + (size_t)L.nsmax * 4);                     // first index of each own pair
+  L.dg = o;   o = ed_align(o + (size_t)L.np * 4);                        // whole diagonal (sweep-start test)
+  L.fl = o;   o = ed_align(o + (size_t)16 * 4);                          // per-CTA test flags
   L.end = o;
   return L;
 }
@@ -412,7 +414,39 @@ evd_dist_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, c
   const uint32_t down_top = rank > 0 ? ep_mapa(ep_smem(mb_top), rank - 1) : 0u;
   int sweeps = 0, converged = 0;
   const int maxsw = g.max_sweeps > 0 ? g.max_sweeps : 40;
+  float* dgl = reinterpret_cast<float*>(smem + L.dg);
+  int* flg = reinterpret_cast<int*>(smem + L.fl);
   for (; sweeps < maxsw; ++sweeps) {
+    if (sweeps > 0) {
+      // A sweep with no rotation leaves A unchanged: test every pair at once instead (step-0
+      // layout here: own slot i holds rows i and Np-1-i).  The diagonal goes to every CTA, each
+      // tests its own rows, the flags are exchanged.
+      for (int ls = tid; ls < ns; ls += ED_THREADS) {
+        const int i = i0 + ls, x0 = i, x1 = np - 1 - i;
+        const float d0 = rows[(size_t)tb[ls] * np + x0].x, d1 = rows[(size_t)bb[ls] * np + x1].x;
+        for (int dst = 0; dst < C; ++dst) {
+          ep_st_remote_u32(ep_mapa(ep_smem(dgl + x0), dst), __float_as_uint(d0));
+          ep_st_remote_u32(ep_mapa(ep_smem(dgl + x1), dst), __float_as_uint(d1));
+        }
+      }
+      cluster.sync();
+      int big = 0;
+      const float tol2 = ED_TOL * ED_TOL;
+      for (int e = tid; e < 2 * ns * np; e += ED_THREADS) {
+        const int bq = e / np, c = e - bq * np, ls = bq >> 1, i = i0 + ls;
+        const int x = (bq & 1) ? np - 1 - i : i;
+        if (c == x) continue;
+        const float2 v = rows[(size_t)((bq & 1) ? bb[ls] : tb[ls]) * np + c];
+        const float v2 = cabs2(v);
+        big |= v2 > 0.f && v2 > tol2 * fabsf(dgl[x] * dgl[c]);
+      }
+      big = __syncthreads_or(big);
+      if (tid < C) ep_st_remote_u32(ep_mapa(ep_smem(flg + rank), tid), (unsigned)big);
+      cluster.sync();
+      int anybig = 0;
+      for (int q = 0; q < C; ++q) anybig |= flg[q];
+      if (!anybig) { converged = 1; break; }
+    }
     int any = 0;
     for (int r = 0; r < np - 1; ++r) {
       // (a) rotations of the own pairs; records to every CTA
