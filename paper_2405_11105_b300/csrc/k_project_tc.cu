@@ -199,27 +199,41 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
   }
 
   // ---- stage the tile's rows [c_p, a_p] (scaled, split hi/lo), zero K padding ----
-  // item i: lane -> (row%8, k-pair), so a warp's 4-byte stores hit 32 distinct banks
-  for (int i = tid; i < rows * (k16 / 2); i += PT_THREADS) {
-    const int ln = i & 31, rest = i >> 5, rg = rows / 8;
-    const int m = (rest % rg) * 8 + (ln & 7), t = (rest / rg) * 8 + (ln >> 3) * 2;
-    const int z = z0 + (m >> 4), x = x0 + (m & 15);
-    float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-    if (z < nz && x < nx) {
-      const size_t p = (size_t)z * nx + x;
-      if (t < na) v0 = xa[(size_t)t * npix + p];
-      if (t + 1 < na) v1 = xa[(size_t)(t + 1) * npix + p];
+  // item i: lane -> (row%8, k-pair), so a warp's 4-byte stores hit 32 distinct banks;
+  // four items per thread at a time, their eight loads issued before any is split
+  const int nitems = rows * (k16 / 2), rg = rows / 8;
+  for (int i0 = tid; i0 < nitems; i0 += 4 * PT_THREADS) {
+    float2 v0[4], v1[4];
+    int mm[4], tt[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * PT_THREADS;
+      const int ln = i & 31, rest = i >> 5;
+      mm[u] = (rest % rg) * 8 + (ln & 7);
+      tt[u] = (rest / rg) * 8 + (ln >> 3) * 2;
+      const int z = z0 + (mm[u] >> 4), x = x0 + (mm[u] & 15);
+      v0[u] = make_float2(0.f, 0.f);
+      v1[u] = v0[u];
+      if (i < nitems && z < nz && x < nx) {
+        const size_t p = (size_t)z * nx + x;
+        if (tt[u] < na) v0[u] = xa[(size_t)tt[u] * npix + p];
+        if (tt[u] + 1 < na) v1[u] = xa[(size_t)(tt[u] + 1) * npix + p];
+      }
     }
-    __half h0r, l0r, h1r, l1r, h0i, l0i, h1i, l1i;
-    tc::split_f16(v0.x * sA, h0r, l0r);
-    tc::split_f16(v1.x * sA, h1r, l1r);
-    tc::split_f16(v0.y * sA, h0i, l0i);
-    tc::split_f16(v1.y * sA, h1i, l1i);
-    const int off = tc::op_off(m, t, a_sbo);
-    *reinterpret_cast<__half2*>(A + off) = __halves2half2(h0r, h1r);
-    *reinterpret_cast<__half2*>(A + a_bytes + off) = __halves2half2(l0r, l1r);
-    *reinterpret_cast<__half2*>(A + 2 * a_bytes + off) = __halves2half2(h0i, h1i);
-    *reinterpret_cast<__half2*>(A + 3 * a_bytes + off) = __halves2half2(l0i, l1i);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (i0 + u * PT_THREADS >= nitems) break;
+      __half h0r, l0r, h1r, l1r, h0i, l0i, h1i, l1i;
+      tc::split_f16(v0[u].x * sA, h0r, l0r);
+      tc::split_f16(v1[u].x * sA, h1r, l1r);
+      tc::split_f16(v0[u].y * sA, h0i, l0i);
+      tc::split_f16(v1[u].y * sA, h1i, l1i);
+      const int off = tc::op_off(mm[u], tt[u], a_sbo);
+      *reinterpret_cast<__half2*>(A + off) = __halves2half2(h0r, h1r);
+      *reinterpret_cast<__half2*>(A + a_bytes + off) = __halves2half2(l0r, l1r);
+      *reinterpret_cast<__half2*>(A + 2 * a_bytes + off) = __halves2half2(h0i, h1i);
+      *reinterpret_cast<__half2*>(A + 3 * a_bytes + off) = __halves2half2(l0i, l1i);
+    }
   }
   tc::fence_proxy_async();
   tc::fence_before();
