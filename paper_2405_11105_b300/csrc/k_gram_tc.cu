@@ -191,24 +191,18 @@ gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box*
       const float2* src0 = raw + (size_t)(i & 1) * TG_PX * rld + pp * rld;
       const float2* src1 = src0 + rld;
       const int kk = 2 * pp;
+      const float2 gg0 = make_float2(g0, g0), gg1 = make_float2(g1, g1);
+      const float2 gd0 = make_float2(2.f * g0, 2.f * g0), gd1 = make_float2(2.f * g1, 2.f * g1);
 #pragma unroll 4
       for (int r = rl; r < na; r += 16) {   // independent rows interleaved: two warps per scheduler need ILP
-        const float2 v0 = src0[r], v1 = src1[r];
-        __half hr0, lr0, hm0, lm0, hr1, lr1, hm1, lm1;
-        tc::split_f16(v0.x * g0, hr0, lr0);
-        tc::split_f16(v0.y * g0, hm0, lm0);
-        tc::split_f16(v1.x * g1, hr1, lr1);
-        tc::split_f16(v1.y * g1, hm1, lm1);
-        const __half two = __float2half(2.f);
-        const __half lr0b = __hmul(lr0, two), lm0b = __hmul(lm0, two), lr1b = __hmul(lr1, two), lm1b = __hmul(lm1, two);
-        __half2 w[2];
-        w[0] = __halves2half2(hr0, hm0); w[1] = __halves2half2(hr1, hm1);
-        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        w[0] = __halves2half2(hm0, __hneg(hr0)); w[1] = __halves2half2(hm1, __hneg(hr1));
+        __half2 h[2], l[2], w[2];
+        tc::split2_f16(src0[r], gg0, gd0, h[0], l[0]);
+        tc::split2_f16(src1[r], gg1, gd1, h[1], l[1]);
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(h);
+        w[0] = tc::neg_i(h[0]); w[1] = tc::neg_i(h[1]);
         *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        w[0] = __halves2half2(lr0b, lm0b); w[1] = __halves2half2(lr1b, lm1b);
-        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        w[0] = __halves2half2(lm0b, __hneg(lr0b)); w[1] = __halves2half2(lm1b, __hneg(lr1b));
+        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(l);
+        w[0] = tc::neg_i(l[0]); w[1] = tc::neg_i(l[1]);
         *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
       }
     }
@@ -364,38 +358,27 @@ gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, i
       const float g0 = gg_s[pp], g1 = gg_s[pp + 1];
       const size_t p0 = pix_s[pp], p1 = pix_s[pp + 1];
       const int kk = 2 * pp;
-      const __half two = __float2half(2.f);
+      const float2 gg0 = make_float2(g0, g0), gg1 = make_float2(g1, g1);
+      const float2 gd0 = make_float2(2.f * g0, 2.f * g0), gd1 = make_float2(2.f * g1, 2.f * g1);
       for (int r = rl; r < rnb; r += 16) {
         const float2* src = xa + (size_t)(rb0 + r) * npix;
-        const float2 v0 = src[p0], v1 = src[p1];
-        __half hr0, lr0, hm0, lm0, hr1, lr1, hm1, lm1;
-        tc::split_f16(v0.x * g0, hr0, lr0);
-        tc::split_f16(v0.y * g0, hm0, lm0);
-        tc::split_f16(v1.x * g1, hr1, lr1);
-        tc::split_f16(v1.y * g1, hm1, lm1);
-        const __half lr0b = __hmul(lr0, two), lm0b = __hmul(lm0, two), lr1b = __hmul(lr1, two), lm1b = __hmul(lm1, two);
-        __half2 w[2];
-        w[0] = __halves2half2(hr0, hm0); w[1] = __halves2half2(hr1, hm1);
-        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        w[0] = __halves2half2(hm0, __hneg(hr0)); w[1] = __halves2half2(hm1, __hneg(hr1));
+        __half2 hh[2], ll[2], w[2];
+        tc::split2_f16(src[p0], gg0, gd0, hh[0], ll[0]);
+        tc::split2_f16(src[p1], gg1, gd1, hh[1], ll[1]);
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(hh);
+        w[0] = tc::neg_i(hh[0]); w[1] = tc::neg_i(hh[1]);
         *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        w[0] = __halves2half2(lr0b, lm0b); w[1] = __halves2half2(lr1b, lm1b);
-        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        w[0] = __halves2half2(lm0b, __hneg(lr0b)); w[1] = __halves2half2(lm1b, __hneg(lr1b));
+        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(ll);
+        w[0] = tc::neg_i(ll[0]); w[1] = tc::neg_i(ll[1]);
         *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
       }
       if (!same) {
         for (int r = rl; r < rna; r += 16) {
           const float2* src = xa + (size_t)(ra0 + r) * npix;
-          const float2 v0 = src[p0], v1 = src[p1];
-          __half hr0, lr0, hm0, lm0, hr1, lr1, hm1, lm1;
-          tc::split_f16(v0.x * g0, hr0, lr0);
-          tc::split_f16(v0.y * g0, hm0, lm0);
-          tc::split_f16(v1.x * g1, hr1, lr1);
-          tc::split_f16(v1.y * g1, hm1, lm1);
-          __half2 w[2];
-          w[0] = __halves2half2(hr0, hm0); w[1] = __halves2half2(hr1, hm1);
-          *reinterpret_cast<uint2*>(Ahi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+          __half2 hh[2];
+          hh[0] = __float22half2_rn(__fmul2_rn(src[p0], gg0));
+          hh[1] = __float22half2_rn(__fmul2_rn(src[p1], gg1));
+          *reinterpret_cast<uint2*>(Ahi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(hh);
         }
       }
     }

@@ -146,6 +146,21 @@ __device__ __forceinline__ void split_f16(float v, __half& hi, __half& lo) {
   hi = __float2half_rn(v);
   lo = __float2half_rn(v - __half2float(hi));
 }
+// Packed split of a complex value x scaled by g: hi = fp16(g x), lo2 = fp16(2 (g x - hi)),
+// both components at once (g x and 2 g x are exact scalings of each other, and g x - hi is
+// exact, so lo2 is the doubled low half rounded once).
+__device__ __forceinline__ void split2_f16(float2 x, float2 gg, float2 gg2, __half2& hi, __half2& lo2) {
+  const float2 v = __fmul2_rn(x, gg), v2 = __fmul2_rn(x, gg2);
+  hi = __float22half2_rn(v);
+  lo2 = __float22half2_rn(__ffma2_rn(__half22float2(hi), make_float2(-2.f, -2.f), v2));
+}
+// (a, b) -> (b, -a): the fp16 pair of -i (a + i b)
+__device__ __forceinline__ __half2 neg_i(__half2 h) {
+  const __half2 sw = __lowhigh2highlow(h);
+  uint32_t u = *reinterpret_cast<const uint32_t*>(&sw);
+  u ^= 0x80000000u;
+  return *reinterpret_cast<const __half2*>(&u);
+}
 
 }  // namespace tc
 }  // namespace lcf
