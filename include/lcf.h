@@ -138,6 +138,19 @@ lcf_status lcf_filter(lcf_plan* plan, const void* d_iq, float* d_out_pd, cudaStr
  * memory makes the copies asynchronous DMA; pageable memory also works. */
 lcf_status lcf_filter_host(lcf_plan* plan, const void* h_iq, float* h_out_pd, cudaStream_t stream);
 
+/* Pipelined form of lcf_filter_host for a sequence of packets: returns without
+ * synchronising.  The packet's host-to-device copy runs on a plan-owned copy
+ * stream into one of two device staging buffers (alternating between calls),
+ * so it overlaps the previous packet's kernels on `stream`; the image is copied
+ * back to h_out_pd on `stream`.  h_iq must stay unchanged and h_out_pd must not
+ * be read until lcf_plan_sync returns (pinned host memory required for the
+ * overlap).  Calls of one plan must use the same `stream`.  The first call
+ * creates the copy stream and its events. */
+lcf_status lcf_filter_host_async(lcf_plan* plan, const void* h_iq, float* h_out_pd, cudaStream_t stream);
+
+/* Wait for every copy and kernel of the plan's pipelined host calls. */
+lcf_status lcf_plan_sync(lcf_plan* plan);
+
 /* Sliding-packet processing (packets of nt frames every `stride` frames, as
  * the paper's real-time processing does).  d_frames: device frames
  * [n_frames][nz][nx] complex64; d_out_pd: [n_packets][nz][nx] with

@@ -54,6 +54,8 @@ def _load():
         "lcf_plan_create": ([C.POINTER(lcf_config), C.c_int, C.POINTER(vp)], C.c_int),
         "lcf_filter": ([vp, vp, vp, vp], C.c_int),
         "lcf_filter_host": ([vp, vp, vp, vp], C.c_int),
+        "lcf_filter_host_async": ([vp, vp, vp, vp], C.c_int),
+        "lcf_plan_sync": ([vp], C.c_int),
         "lcf_filter_stream": ([vp, vp, C.c_int, C.c_int, vp, vp], C.c_int),
         "lcf_plan_status": ([vp, ip], C.c_int),
         "lcf_debug_dump": ([vp, dp, fp, ip, fp], C.c_int),
@@ -116,6 +118,14 @@ def lcf_filter(plan: int, d_iq: int, d_out_pd: int, stream: int = 0) -> int:
 
 def lcf_filter_host(plan: int, h_iq: int, h_out_pd: int, stream: int = 0) -> int:
     return _lib.lcf_filter_host(plan, h_iq, h_out_pd, stream)
+
+
+def lcf_filter_host_async(plan: int, h_iq: int, h_out_pd: int, stream: int = 0) -> int:
+    return _lib.lcf_filter_host_async(plan, h_iq, h_out_pd, stream)
+
+
+def lcf_plan_sync(plan: int) -> int:
+    return _lib.lcf_plan_sync(plan)
 
 
 def lcf_filter_stream(plan: int, d_frames: int, n_frames: int, stride: int, d_out: int, stream: int = 0) -> int:
@@ -225,6 +235,19 @@ class Plan:
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         _check(lcf_filter_host(self.handle, ip, op, st), "lcf_filter_host")
         return out_host
+
+    def filter_host_async(self, iq_host, out_host, stream=None):
+        """Pipelined host call (pinned torch CPU tensors): returns at once; the next call's
+        input copy overlaps this packet's kernels.  Inputs stay untouched and outputs unread
+        until sync()."""
+        import torch
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        _check(lcf_filter_host_async(self.handle, iq_host.data_ptr(), out_host.data_ptr(), st),
+               "lcf_filter_host_async")
+        return out_host
+
+    def sync(self):
+        _check(lcf_plan_sync(self.handle), "lcf_plan_sync")
 
     def filter_stream(self, frames, stride: int, out=None, stream=None):
         import torch

@@ -394,7 +394,7 @@ extern "C" lcf_status lcf_plan_set_mlp(lcf_plan* P, const lcf_mlp* N, float p_mi
     P->ws_bytes += nw * sizeof(__nv_bfloat16) + nb * sizeof(float);
   }
   // the plan's stream may still be reading the previous weights
-  if (P->last_stream && cudaStreamSynchronize(P->last_stream) != cudaSuccess) return LCF_ECUDA;
+  if (P->launched && cudaStreamSynchronize(P->last_stream) != cudaSuccess) return LCF_ECUDA;
   if (mlp_plan_weights(N, P->ws.mlp_w, P->ws.mlp_b, 0) != cudaSuccess) return LCF_ECUDA;
   if (cudaStreamSynchronize(0) != cudaSuccess) return LCF_ECUDA;
   P->mlp_hidden = N->hidden;

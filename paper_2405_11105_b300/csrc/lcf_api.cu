@@ -229,8 +229,8 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = dalloc(&w.bimg, nd * project_tc_image_bytes(P->nt, P->ndefl), &tot);
     if (e == cudaSuccess) e = dalloc(&w.bscale, nd, &tot);
   }
-  if (e == cudaSuccess) e = dalloc(&w.iq_stage, nt * npix, &tot);
-  if (e == cudaSuccess) e = dalloc(&w.pd_stage, npix, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.iq_stage, 2 * nt * npix, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.pd_stage, 2 * npix, &tot);
   if (e != cudaSuccess) {
     free_ws(w);
     delete P;
@@ -385,6 +385,7 @@ extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd,
   DeviceGuard g(P->device);
   lcf_status s = run_packet(P, (const float2*)d_iq, d_out_pd, stream);
   P->last_stream = stream;
+  P->launched = true;
   P->last_iq = (void*)d_iq;
   return s;
 }
@@ -399,8 +400,51 @@ extern "C" lcf_status lcf_filter_host(lcf_plan* P, const void* h_iq, float* h_ou
   LCF_CUDA(cudaMemcpyAsync(h_out_pd, P->ws.pd_stage, (size_t)P->npix * sizeof(float), cudaMemcpyDeviceToHost,
                            stream));
   P->last_stream = stream;
+  P->launched = true;
   P->last_iq = P->ws.iq_stage;
   LCF_CUDA(cudaStreamSynchronize(stream));
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float* h_out_pd, cudaStream_t stream) {
+  if (!P || !h_iq || !h_out_pd) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  if (!P->h2d_stream) {
+    LCF_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      LCF_CUDA(cudaEventCreateWithFlags(&P->ev_in[b], cudaEventDisableTiming));
+      LCF_CUDA(cudaEventCreateWithFlags(&P->ev_done[b], cudaEventDisableTiming));
+    }
+  }
+  const int b = (int)(P->host_seq & 1);
+  const size_t in_elems = (size_t)P->nt * P->npix;
+  float2* iq = P->ws.iq_stage + (size_t)b * in_elems;
+  float* pd = P->ws.pd_stage + (size_t)b * P->npix;
+  // the buffer's previous packet has finished with it before the copy overwrites it
+  if (P->host_seq >= 2) LCF_CUDA(cudaStreamWaitEvent(P->h2d_stream, P->ev_done[b], 0));
+  LCF_CUDA(cudaMemcpyAsync(iq, h_iq, in_elems * sizeof(float2), cudaMemcpyHostToDevice, P->h2d_stream));
+  LCF_CUDA(cudaEventRecord(P->ev_in[b], P->h2d_stream));
+  LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_in[b], 0));
+  lcf_status s = run_packet(P, iq, pd, stream);
+  if (s != LCF_OK) return s;
+  LCF_CUDA(cudaMemcpyAsync(h_out_pd, pd, (size_t)P->npix * sizeof(float), cudaMemcpyDeviceToHost, stream));
+  LCF_CUDA(cudaEventRecord(P->ev_done[b], stream));
+  P->host_seq++;
+  P->last_stream = stream;
+  P->launched = true;
+  P->last_iq = iq;
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_plan_sync(lcf_plan* P) {
+  if (!P) return LCF_EINVAL;
+  DeviceGuard g(P->device);
+  if (P->h2d_stream) LCF_CUDA(cudaStreamSynchronize(P->h2d_stream));
+  // the last pipelined packet of each staging buffer, whichever stream it ran on; earlier
+  // packets of a buffer finished before its next input copy began
+  for (int b = 0; b < 2; ++b)
+    if (P->host_seq > b) LCF_CUDA(cudaEventSynchronize(P->ev_done[b]));
+  if (P->launched) LCF_CUDA(cudaStreamSynchronize(P->last_stream));
   return LCF_OK;
 }
 
@@ -455,6 +499,7 @@ extern "C" lcf_status lcf_filter_stream(lcf_plan* P, const void* d_frames, int n
     P->launches += P->sg_launches;
   }
   P->last_stream = stream;
+  P->launched = true;
   P->last_iq = (void*)(fr + (size_t)(npk - 1) * stride * P->npix);
   return LCF_OK;
 }
@@ -534,10 +579,17 @@ extern "C" size_t lcf_plan_workspace_bytes(const lcf_plan* P) { return P ? P->ws
 extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
   if (!P) return LCF_EINVAL;
   DeviceGuard g(P->device);
+  if (P->h2d_stream) cudaStreamSynchronize(P->h2d_stream);   // pipelined host calls still in flight
+  if (P->launched) cudaStreamSynchronize(P->last_stream);
   free_ws(P->ws);
   for (auto& e : P->prof_ev) cudaEventDestroy(e);
   if (P->sg_exec) cudaGraphExecDestroy(P->sg_exec);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  if (P->h2d_stream) cudaStreamDestroy(P->h2d_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (P->ev_in[b]) cudaEventDestroy(P->ev_in[b]);
+    if (P->ev_done[b]) cudaEventDestroy(P->ev_done[b]);
+  }
   delete P;
   return LCF_OK;
 }

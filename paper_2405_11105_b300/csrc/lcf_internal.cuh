@@ -87,8 +87,8 @@ struct Workspace {
   __nv_bfloat16* mlp_w = nullptr;   // W1 | W2 | W3 | W4, bf16
   float* mlp_b = nullptr;           // b1 | b2 | b3 | b4
   // host-call staging
-  float2* iq_stage = nullptr; // [nt][nz][nx] device copy for lcf_filter_host
-  float* pd_stage = nullptr;  // [nz][nx]
+  float2* iq_stage = nullptr; // [2][nt][nz][nx] device copies for lcf_filter_host(_async)
+  float* pd_stage = nullptr;  // [2][nz][nx]
 };
 
 }  // namespace lcf
@@ -115,7 +115,12 @@ struct lcf_plan {
   std::vector<lcf::Box> boxes;
   lcf::Workspace ws;
   size_t ws_bytes = 0;
-  cudaStream_t last_stream = nullptr;
+  cudaStream_t last_stream = nullptr;       // stream of the latest call (0 = the legacy default stream)
+  bool launched = false;                    // some call has put work on last_stream
+  cudaStream_t h2d_stream = nullptr;        // copy stream of lcf_filter_host_async
+  cudaEvent_t ev_in[2] = {nullptr, nullptr};  // staging buffer b filled
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};  // staging buffer b consumed
+  long long host_seq = 0;                   // pipelined host calls so far
   void* last_iq = nullptr;
   // stage profiling: events[call % kProfCalls][stage boundary]
   // kernels this plan has launched (every launcher adds its own)

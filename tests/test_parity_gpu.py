@@ -286,3 +286,31 @@ def test_host_and_stream_entry_points_match_device_path():
     host_out = torch.empty((96, 64), dtype=torch.float32).pin_memory()
     plan.filter_host(host_in, host_out)
     assert torch.equal(host_out, outs[1].cpu())
+
+
+def test_pipelined_host_calls_match_device_path():
+    """lcf_filter_host_async over a sequence of packets (alternating staging buffers, copies
+    overlapping the previous packet's kernels) gives every packet's image bit for bit."""
+    import torch
+    lib = L()
+    from synth import generate_frames
+    frames = generate_frames(SMALL_96x64x32, 32 + 5 * 8, seed=6)
+    cfg, _ = configs(96, 64, 32, 3, 3, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    plan = lib.Plan(cfg)
+    d = torch.from_numpy(frames).cuda()
+    ref = [plan.filter(d[i * 8:i * 8 + 32].contiguous()).cpu() for i in range(6)]
+    torch.cuda.synchronize()
+    hin = [torch.from_numpy(frames[i * 8:i * 8 + 32].copy()).pin_memory() for i in range(6)]
+    hout = [torch.full((96, 64), -1.0, dtype=torch.float32).pin_memory() for _ in range(6)]
+    for i in range(6):
+        plan.filter_host_async(hin[i], hout[i])
+    plan.sync()
+    for i in range(6):
+        assert torch.equal(hout[i], ref[i]), i
+    # sync after every call: the last packets are waited for too (the calls run on the legacy
+    # default stream, handle 0)
+    for i in range(6):
+        hout[i].fill_(-1.0)
+        plan.filter_host_async(hin[i], hout[i])
+        plan.sync()
+        assert torch.equal(hout[i], ref[i]), i
