@@ -31,6 +31,32 @@ WORKLOAD = "256x128 px x Nt=100 complex64 packets, 8x8 Gaussian windows (3-sigma
 SUM_P = 778752          # pixels summed over the 64 window supports
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the kernel on this workload, valid only while the kernel's sources hash as they did then
+CAPTURED_TRAFFIC = {
+    "evd": {"bytes": 10.55e6, "profile": "profiles/evd_pair_kernel_256x128x100_8x8.md",
+            "sources": {"paper_2405_11105_b300/csrc/k_evd_pair.cu":
+                        "1009f85991485b46621e713d25b5986447e5b8d30cb1cd7cbbef818ea32fe087",
+                        "paper_2405_11105_b300/csrc/evd_common.cuh":
+                        "5f49c4e22ff1c65643b5fa3ad4b49488b54f5289a099077851b31487f275d22d"}},
+}
+
+
+def captured_traffic(stage):
+    """Bytes per launch from the capture, or None once a source of the kernel has changed."""
+    import hashlib
+    rec = CAPTURED_TRAFFIC.get(stage)
+    if not rec:
+        return None
+    for rel, digest in rec["sources"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return rec["bytes"]
+
 
 def env_int(k, d):
     try:
@@ -390,7 +416,9 @@ def main():
         peak = peaks.get("bf16_tflops", 1800.0)
     achieved = (work.get(dom) or 0.0) / (per_launch[dom] * 1e-3) / 1e12 if work.get(dom) else None
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved and peak else None, "traffic": None,
+                "frac": (achieved / peak) if achieved and peak else None,
+                "traffic": captured_traffic(dom) if path == L.LCF_PATH_TC else None,
+                "traffic_unit": "bytes per launch (ncu capture)",
                 "peak_source": peak_src,
                 "stage_ms_per_launch": per_launch}
 
