@@ -13,13 +13,19 @@
 // dropped lo*lo term (relative 2^-22 squared).  A aliases the first 128 rows
 // of the B_hi buffer (rows past nbh only feed output rows that are unused).
 //
-// One CTA per (window, pixel range): 3-stage shared-memory ring of 32-pixel
-// K-slabs written by all 256 threads, one thread issuing tcgen05.mma, two TMEM
-// accumulators in ping-pong (128 pixels each), promoted into FP32 register
+// One CTA per (window, range of 32-pixel slabs), warp-specialised: a loader
+// warp brings each slab (32 pixels of a box row x all rows) into shared memory
+// with one tensor-map load; eight producer warps split it into a 3-stage ring of
+// MMA operands and signal the stage's `full` mbarrier; one warp issues the
+// tcgen05.mma chain and commits `empty` (stage reusable) and the accumulator's
+// barrier.  No CTA-wide barrier inside the loop.  Two TMEM accumulators in
+// ping-pong (128 pixels each) are promoted by the producers into FP32 register
 // sums per (row, column half); the range's sum is written as a double partial.
 // The d x d coefficient block (largest entries) comes from gram_q_kernel with
 // exact double-float products instead.
 #include <math.h>
+
+#include <cudaTypedefs.h>
 
 #include "lcf_internal.cuh"
 #include "tc_util.cuh"
@@ -43,15 +49,27 @@ constexpr int TG_NBH_MAX = 128;
 __host__ __device__ inline int tc_nbh(int na) { return (na + 7) / 8 * 8; }
 __host__ __device__ inline int tc_rows_hi(int nbh) { return 2 * nbh > 128 ? 2 * nbh : 128; }
 
-// fp32 slab staging (cp.async, one stage ahead of the split): 2 buffers of TG_PX pixels x (na + 1) rows
-__host__ __device__ inline size_t tc_raw_bytes(int na) { return (size_t)2 * TG_PX * (na + 1) * 8; }
+constexpr int TW_PROD = 8;                       // producer warps: split, promote
+constexpr int TW_THREADS = 32 * (TW_PROD + 2);   // + one warp issuing the MMAs, one loading the slabs
+
+// fp32 slab staging, two slots: row r of the slab at r * 272 bytes when the loader warp copies it
+// (one tensor-map load of kTcSlabBox pixels x na rows; the rows' 16-byte pitch offset keeps the
+// producers' 16-row reads free of bank conflicts), or thread t's two pixels of rows rl + 16 j at
+// j * 4096 + t * 16 when each producer thread copies its own (cp.async, odd Nz Nx)
+constexpr int TW_ROWB = kTcSlabBox * 8;
+__host__ __device__ inline size_t tc_slot_bytes(int na) {
+  const size_t a = (size_t)na * TW_ROWB, b = (size_t)((na + 15) / 16) * 4096;
+  return ((a > b ? a : b) + 1023) / 1024 * 1024;
+}
+__host__ __device__ inline size_t tc_raw_bytes(int na) { return 2 * tc_slot_bytes(na); }
 size_t gram_tc_smem_bytes_n(int na, int nstg) {
   int nbh = tc_nbh(na), rh = tc_rows_hi(nbh);
   size_t hi = (size_t)rh * TG_K * 2, lo = (size_t)2 * nbh * TG_K * 2;
   return nstg * (hi + lo) + 1024 + tc_raw_bytes(na);
 }
-// MMA operand stages: three when they fit beside the fp32 staging, else two
-int gram_tc_stages(int na) { return gram_tc_smem_bytes_n(na, TG_STAGES) <= 232448 ? TG_STAGES : 2; }
+// MMA operand stages: three when they fit beside the fp32 staging (and the kernel's static
+// barriers, within the 227 KB a block may hold), else two
+int gram_tc_stages(int na) { return gram_tc_smem_bytes_n(na, TG_STAGES) <= 232448 - 1024 ? TG_STAGES : 2; }
 size_t gram_tc_smem_bytes(int na) { return gram_tc_smem_bytes_n(na, gram_tc_stages(na)); }
 
 __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src, bool valid) {
@@ -64,185 +82,234 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__global__ void __launch_bounds__(TG_THREADS, 1)
-gram_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int na, const Box* __restrict__ boxes,
-               const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
-               int nsplit, int nstg, double* __restrict__ part, int* __restrict__ err) {
+// A slab is 32 consecutive pixels of one box row, starting at xs = x0 - ((z nx + x0) mod 2) + 32 c
+// (an even linear index: a tensor-map load must start on a 16-byte boundary); pixels outside
+// [x0, x1) take weight 0.  nch = ceil((x1 - x0 + 1) / 32) slabs per box row.
+struct TcSlab {
+  int z, xs;
+  long p0;
+};
+__device__ __forceinline__ TcSlab tc_slab(const Box& b, int nx, int nch, int t) {
+  TcSlab q;
+  const int zr = t / nch, cx = t - zr * nch;
+  q.z = b.z0 + zr;
+  q.xs = b.x0 - ((q.z * nx + b.x0) & 1) + 32 * cx;
+  q.p0 = (long)q.z * nx + q.xs;
+  return q;
+}
+
+// NS: FP32 register sums per thread (>= nbh, a multiple of 16)
+template <int NS>
+__global__ void __launch_bounds__(TW_THREADS, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float2* __restrict__ xa, int nz, int nx,
+               int na, const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
+               const unsigned* __restrict__ xmax_bits, int nsplit, int nstg, double* __restrict__ part,
+               int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t mma_bar[TG_STAGES];
-  __shared__ __align__(8) uint64_t acc_bar[2];
+  __shared__ __align__(8) uint64_t full_bar[TG_STAGES];    // stage's operands written (one arrive per producer warp)
+  __shared__ __align__(8) uint64_t empty_bar[TG_STAGES];   // stage's MMAs done
+  __shared__ __align__(8) uint64_t acc_bar[2];             // accumulator's chunk done
+  __shared__ __align__(8) uint64_t rfull_bar[2];           // slab slot loaded (tensor-map path)
+  __shared__ __align__(8) uint64_t rempty_bar[2];          // slab slot read by every producer warp (tensor-map path)
   __shared__ uint32_t tmem_base;
-  __shared__ int pix_s[3][TG_PX];     // stage s uses buffer s % 3
-  __shared__ float gg_s[3][TG_PX];
-  __shared__ unsigned char ok_s[3][TG_PX];
 
   const int k = blockIdx.y, s = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nbh = tc_nbh(na), N = 2 * nbh, rh = tc_rows_hi(nbh);
   const size_t hi_bytes = (size_t)rh * 128, lo_bytes = (size_t)N * 128, st_bytes = hi_bytes + lo_bytes;
   const Box b = boxes[k];
-  const int W = b.x1 - b.x0;
-  const long Pk = (long)(b.z1 - b.z0) * W;
-  const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
-  const int nst = (int)((l1 - l0 + TG_PX - 1) / TG_PX);
+  const int nch = (b.x1 - b.x0 + 1 + TG_PX - 1) / TG_PX;
+  const int S = (b.z1 - b.z0) * nch;
+  const int t0 = (int)((long)S * s / nsplit), nst = (int)((long)S * (s + 1) / nsplit) - t0;
   const size_t npix = (size_t)nz * nx;
-  const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
-  const float* gzk = gz + (size_t)k * nz;
-  const float* gxk = gx + (size_t)k * nx;
-  const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
+  const bool bulk = use_map != 0;
+  const int rb = (na + 15) / 16;
+  const size_t slot_bytes = tc_slot_bytes(na);
+  unsigned char* raw = smem + nstg * st_bytes;   // two slab slots
 
-  const int rld = na + 1;   // fp32 slab row stride (odd: fewer bank conflicts in the split)
-  float2* raw = reinterpret_cast<float2*>(smem + nstg * st_bytes);   // [2][TG_PX][rld]
-  // zero all stage buffers (padding rows stay zero)
-  for (size_t e = tid; e < nstg * st_bytes / 16; e += TG_THREADS)
+  // zero the stage buffers (padding rows stay zero) and the slab slots
+  for (size_t e = tid; e < (nstg * st_bytes + tc_raw_bytes(na)) / 16; e += TW_THREADS)
     reinterpret_cast<uint4*>(smem)[e] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
-    for (int i = 0; i < nstg; ++i) tc::mbar_init(&mma_bar[i], 1);
-    tc::mbar_init(&acc_bar[0], 1);
-    tc::mbar_init(&acc_bar[1], 1);
+    for (int i = 0; i < nstg; ++i) {
+      tc::mbar_init(&full_bar[i], TW_PROD);
+      tc::mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&acc_bar[i], 1);
+      tc::mbar_init(&rfull_bar[i], 1);
+      tc::mbar_init(&rempty_bar[i], TW_PROD);
+    }
   }
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t idesc = tc::idesc_f16(128, N);
 
-  float sums[TG_NBH_MAX];
+  if (warp == TW_PROD) {
+    // ---- MMA warp: D' = A B_hi^T + A (2 B_lo)^T per stage, chains of TG_CPA stages
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16(128, N);
+      const uint32_t sb = tc::smem_u32(smem);
+      const uint64_t dh0 = tc::smem_desc(sb, 128, TG_SBO), dl0 = tc::smem_desc(sb + (uint32_t)hi_bytes, 128, TG_SBO);
+      bool ok = true;
+      for (int i = 0; i < nst; ++i) {
+        const int si = i % nstg, c = i / TG_CPA;
+        if (ok) ok = tc::mbar_wait(&full_bar[si], (i / nstg) & 1);
+        tc::fence_after();
+        // descriptors advance in 16-byte units: a stage, then two core matrices (16 K) per step
+        const uint64_t so = (uint64_t)((si * st_bytes) >> 4);
+        const uint32_t d = tbase + (uint32_t)((c & 1) * 256);
 #pragma unroll
-  for (int j = 0; j < TG_NBH_MAX; ++j) sums[j] = 0.f;
-  bool ok = true;
+        for (int ks = 0; ks < TG_K / 16; ++ks) {
+          const uint64_t ad = dh0 + so + (uint64_t)(16 * ks), ld = dl0 + so + (uint64_t)(16 * ks);
+          tc::mma_f16(d, ad, ad, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
+          tc::mma_f16(d, ad, ld, idesc, 1u);
+        }
+        tc::mma_commit(&empty_bar[si]);
+        if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
+      }
+      if (!ok) atomicOr(err, 1);
+    }
+  } else if (warp == TW_PROD + 1) {
+    // ---- loader warp (tensor-map path): slab i into slot i & 1, one load of kTcSlabBox x na
+    // (pixels past the image read as zero)
+    if (bulk && lane == 0) {
+      bool ok = true;
+      for (int i = 0; i < nst; ++i) {
+        const TcSlab q = tc_slab(b, nx, nch, t0 + i);
+        if (i >= 2 && ok) ok = tc::mbar_wait(&rempty_bar[i & 1], ((i >> 1) - 1) & 1);
+        tc::mbar_arrive_expect_tx(&rfull_bar[i & 1], (uint32_t)(na * TW_ROWB));
+        tc::tma_load_2d(raw + (size_t)(i & 1) * slot_bytes, &tmx, (int)q.p0, 0, &rfull_bar[i & 1]);
+      }
+      if (!ok) atomicOr(err, 1);
+    }
+  } else {
+    // ---- producer warps: lane owns pixel slots (ps, ps + 1) of every slab and rows rl + 16 j
+    const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
+    const int ps = 4 * warp + 2 * (lane & 1), rl = lane >> 1;
+    const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
+    const float* gzk = gz + (size_t)k * nz;
+    const float* gxk = gx + (size_t)k * nx;
+    const int roff = bulk ? rl * TW_ROWB + ps * 8 : tid * 16;   // this thread's 16 bytes of row rl in a slot
+    const int jstr = bulk ? 16 * TW_ROWB : 4096;                   // ... and of row rl + 16 j
+    float sums[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) sums[j] = 0.f;
+    bool ok = true;
 
-  auto epilogue = [&](int c) {
-    if (ok) ok = tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);   // after a timeout, no further waits
-    tc::fence_after();
-    const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
-    // two 16-column loads in flight per wait
+    // cp.async path: this thread's two pixels of slab i (every row) into slot i & 1
+    auto issue = [&](int i) {
+      const TcSlab q = tc_slab(b, nx, nch, t0 + i);
+      const long pa = q.p0 + ps;
+      const bool v0 = pa >= 0 && pa < (long)npix, v1 = pa + 1 >= 0 && pa + 1 < (long)npix;
+      float2* dst = reinterpret_cast<float2*>(raw + (size_t)(i & 1) * slot_bytes + roff);
+      for (int j = 0; j < rb; ++j) {
+        const int r = rl + 16 * j;
+        const bool vr = r < na;
+        const float2* srow = xa + (size_t)(vr ? r : 0) * npix;
+        cp_async8(dst + (size_t)j * 512, srow + (v0 ? pa : 0), vr && v0);
+        cp_async8(dst + (size_t)j * 512 + 1, srow + (v1 ? pa + 1 : 0), vr && v1);
+      }
+      cp_async_commit();
+    };
+    auto epilogue = [&](int c) {
+      if (ok) ok = tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);   // after a timeout, no further waits
+      tc::fence_after();
+      const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
+      // two 16-column loads in flight per wait
 #pragma unroll
-    for (int cc = 0; cc < TG_NBH_MAX / 16; cc += 2) {
-      if (cc * 16 < nbh) {
-        uint32_t v0[16], v1[16];
-        tc::tmem_ld16_async(base + cc * 16, v0);
-        if ((cc + 1) * 16 < nbh) tc::tmem_ld16_async(base + (cc + 1) * 16, v1);
-        tc::tmem_wait_ld();
+      for (int cc = 0; cc < NS / 16; cc += 2) {
+        if (cc * 16 < nbh) {
+          uint32_t v0[16], v1[16];
+          tc::tmem_ld16_async(base + cc * 16, v0);
+          if ((cc + 1) * 16 < nbh) tc::tmem_ld16_async(base + (cc + 1) * 16, v1);
+          tc::tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += __uint_as_float(v0[j]);
-        if ((cc + 1) * 16 < nbh) {
+          for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += __uint_as_float(v0[j]);
+          if ((cc + 1) * 16 < nbh) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sums[(cc + 1) * 16 + j] += __uint_as_float(v1[j]);
+            for (int j = 0; j < 16; ++j) sums[(cc + 1) * 16 + j] += __uint_as_float(v1[j]);
+          }
         }
       }
-    }
-    tc::fence_before();
-  };
+      // the accumulator is reused by chunk c + 2, whose MMAs wait for this warp's later `full` arrival
+      tc::fence_before();
+    };
 
-  // pixel index and window weight of the slab of stage i (threads < TG_PX)
-  auto slab_pix = [&](int i) {
-    const long l = l0 + (long)i * TG_PX + tid;
-    int p = 0;
-    float g = 0.f;
-    const bool v = i < nst && l < l1;
-    if (v) {
-      const int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
-      p = z * nx + x;
-      g = gzk[z] * gxk[x] * sc;
-    }
-    pix_s[i % 3][tid] = p;
-    gg_s[i % 3][tid] = g;
-    ok_s[i % 3][tid] = v;
-  };
-  // asynchronous copy of stage i's fp32 slab into raw buffer i & 1 (rows r of pixel pp at [pp][r])
-  auto slab_copy = [&](int i) {
-    const int* px = pix_s[i % 3];
-    const unsigned char* vk = ok_s[i % 3];
-    float2* dst = raw + (size_t)(i & 1) * TG_PX * rld;
-    for (int e = tid; e < TG_PX * na; e += TG_THREADS) {
-      const int r = e / TG_PX, pp = e % TG_PX;
-      cp_async8(dst + pp * rld + r, xa + (size_t)r * npix + px[pp], vk[pp] != 0);
-    }
-    cp_async_commit();
-  };
-  if (tid < TG_PX) { slab_pix(0); slab_pix(1); }
-  __syncthreads();
-  if (nst > 0) slab_copy(0);
-
-  int next_epi = 0;   // first chunk whose accumulator is still to be read
-  for (int i = 0; i < nst; ++i) {
-    const int si = i % nstg;
-    unsigned char* Bhi = smem + si * st_bytes;
-    unsigned char* Blo = Bhi + hi_bytes;
-    if (i + 1 < nst) {   // the next slab's copy overlaps this one's split and MMAs
-      slab_copy(i + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();   // slab i complete for every thread
-    if (tid < TG_PX) slab_pix(i + 2);
-    if (i >= nstg && ok) ok = tc::mbar_wait(&mma_bar[si], ((i / nstg) - 1) & 1);
-    {
-      // Each thread owns two adjacent pixels (pp, pp + 1) of the slab and rows r = 16j + lane/2:
-      // their four K entries (re, im, re, im) are 8 contiguous bytes of a core-matrix row.
-      // A warp's 8-byte stores cover 16 rows x 2 pixel pairs: two wavefronts, no further conflicts.
-      const int pp = 2 * (((tid >> 5) & 7) * 2 + (lane & 1)), rl = lane >> 1;
-      const float g0 = gg_s[i % 3][pp], g1 = gg_s[i % 3][pp + 1];
-      const float2* src0 = raw + (size_t)(i & 1) * TG_PX * rld + pp * rld;
-      const float2* src1 = src0 + rld;
-      const int kk = 2 * pp;
-      const float2 gg0 = make_float2(g0, g0), gg1 = make_float2(g1, g1);
-      const float2 gd0 = make_float2(2.f * g0, 2.f * g0), gd1 = make_float2(2.f * g1, 2.f * g1);
+    if (!bulk && nst > 0) issue(0);
+    int next_epi = 0;   // first chunk whose accumulator is still to be read
+    for (int i = 0; i < nst; ++i) {
+      const int si = i % nstg;
+      // window weights of this thread's two pixels
+      const TcSlab q = tc_slab(b, nx, nch, t0 + i);
+      const int xa0 = q.xs + ps;
+      const float gzz = gzk[q.z];
+      const float g0 = (xa0 >= b.x0 && xa0 < b.x1) ? gzz * gxk[xa0] : 0.f;
+      const float g1 = (xa0 + 1 >= b.x0 && xa0 + 1 < b.x1) ? gzz * gxk[xa0 + 1] : 0.f;
+      if (bulk) {
+        if (ok) ok = tc::mbar_wait(&rfull_bar[i & 1], (i >> 1) & 1);
+      } else if (i + 1 < nst) {   // the next slab's copy overlaps this one's split
+        issue(i + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      if (i >= nstg && ok) ok = tc::mbar_wait(&empty_bar[si], ((i / nstg) - 1) & 1);
+      {
+        // The pixel pair's four K entries (re, im, re, im) of row r are 8 contiguous bytes of a
+        // core-matrix row; a warp's 8-byte stores cover 16 rows x 2 pixel pairs (two wavefronts).
+        unsigned char* Bhi = smem + si * st_bytes;
+        unsigned char* Blo = Bhi + hi_bytes;
+        const unsigned char* src = raw + (size_t)(i & 1) * slot_bytes + roff;
+        const int kk = 2 * ps;
+        const float2 gg0 = make_float2(g0 * sc, g0 * sc), gg1 = make_float2(g1 * sc, g1 * sc);
+        const float2 gd0 = make_float2(2.f * gg0.x, 2.f * gg0.x), gd1 = make_float2(2.f * gg1.x, 2.f * gg1.x);
 #pragma unroll 4
-      for (int r = rl; r < na; r += 16) {   // independent rows interleaved: two warps per scheduler need ILP
-        __half2 h[2], l[2], w[2];
-        tc::split2_f16(src0[r], gg0, gd0, h[0], l[0]);
-        tc::split2_f16(src1[r], gg1, gd1, h[1], l[1]);
-        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(h);
-        w[0] = tc::neg_i(h[0]); w[1] = tc::neg_i(h[1]);
-        *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(l);
-        w[0] = tc::neg_i(l[0]); w[1] = tc::neg_i(l[1]);
-        *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        for (int j = 0; j < rb; ++j) {
+          const int r = rl + 16 * j;
+          if (r >= na) break;
+          const float4 v = *reinterpret_cast<const float4*>(src + (size_t)j * jstr);
+          __half2 h[2], l[2], w[2];
+          tc::split2_f16(make_float2(v.x, v.y), gg0, gd0, h[0], l[0]);
+          tc::split2_f16(make_float2(v.z, v.w), gg1, gd1, h[1], l[1]);
+          *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(h);
+          w[0] = tc::neg_i(h[0]); w[1] = tc::neg_i(h[1]);
+          *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+          *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(l);
+          w[0] = tc::neg_i(l[0]); w[1] = tc::neg_i(l[1]);
+          *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        }
       }
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    const int c = i / TG_CPA;
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t d = tbase + (uint32_t)((c & 1) * 256);
-      const uint32_t bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
-#pragma unroll
-      for (int ks = 0; ks < TG_K / 16; ++ks) {
-        const uint64_t ad = tc::smem_desc(bh + ks * 256, 128, TG_SBO);
-        const uint64_t ld = tc::smem_desc(bl + ks * 256, 128, TG_SBO);
-        tc::mma_f16(d, ad, ad, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
-        tc::mma_f16(d, ad, ld, idesc, 1u);
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(&full_bar[si]);
+        if (bulk) tc::mbar_arrive(&rempty_bar[i & 1]);
       }
-      tc::mma_commit(&mma_bar[si]);
-      if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
+      // Chunk c-1's accumulator is read half-way through chunk c, when its MMAs have long
+      // completed; chunk c+1, which reuses it, needs this warp's arrival on a later stage.
+      const int c = i / TG_CPA;
+      if (i % TG_CPA == TG_CPA / 2 && c > 0) { epilogue(c - 1); next_epi = c; }
     }
-    // Chunk c-1's accumulator is read half-way through chunk c, when its MMAs have long
-    // completed (reading it right after its last MMA would stall every thread on them);
-    // chunk c+1, which reuses that accumulator, starts later.
-    if (i % TG_CPA == TG_CPA / 2 && c > 0) { epilogue(c - 1); next_epi = c; }
-  }
-  for (int e = next_epi; nst > 0 && e <= (nst - 1) / TG_CPA; ++e) epilogue(e);
-  if (!ok && lane == 0) atomicOr(err, 1);
+    for (int e = next_epi; nst > 0 && e <= (nst - 1) / TG_CPA; ++e) epilogue(e);
+    if (!ok && lane == 0) atomicOr(err, 1);
 
-  // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na)
-  double* out = part + (((size_t)k * nsplit + s) * 2 + half) * na * na;
-  if (row < na) {
+    // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na)
+    double* out = part + (((size_t)k * nsplit + s) * 2 + half) * na * na;
+    if (row < na) {
 #pragma unroll
-    for (int j = 0; j < TG_NBH_MAX; ++j)
-      if (j < na) out[(size_t)row * na + j] = (double)sums[j];
+      for (int j = 0; j < NS; ++j)
+        if (j < na) out[(size_t)row * na + j] = (double)sums[j];
+    }
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
-
 
 // ---------------------------------------------------------------------------
 // Long packets (Nt > 128 residual rows): the Nt x Nt residual block in row tiles of tb
@@ -574,9 +641,12 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
         P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc, P->ws.err);
   } else {
     dim3 grid(P->tc_nsplit, P->nd);
-    gram_tc_kernel<<<grid, TG_THREADS, gram_tc_smem_bytes(na), st>>>(P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz,
-                                                                      P->ws.gx, P->ws.xmax, P->tc_nsplit,
-                                                                      gram_tc_stages(na), P->ws.gtc, P->ws.err);
+    const int nbh = tc_nbh(na);
+    auto kern = nbh <= 32 ? gram_tc_kernel<32> : nbh <= 64 ? gram_tc_kernel<64> : nbh <= 96 ? gram_tc_kernel<96>
+              : nbh <= 112 ? gram_tc_kernel<112> : gram_tc_kernel<128>;
+    kern<<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(P->tm_xa, P->tm_xa_ok ? 1 : 0, P->ws.xa, c.nz, c.nx, na,
+                                                          P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->tc_nsplit,
+                                                          gram_tc_stages(na), P->ws.gtc, P->ws.err);
   }
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
@@ -620,11 +690,41 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   return counted(P);
 }
 
+// Tensor map of the augmented rows for the slab loads: 8-byte elements, [n1][npix], boxes of
+// kTcSlabBox x tc_na, zero fill outside.  Needs the row pitch (npix * 8 bytes) to be a multiple
+// of 16; odd pixel counts keep the per-thread copies.
+cudaError_t gram_tc_make_map(lcf_plan* P) {
+  P->tm_xa_ok = false;
+  if (P->tc_T != 1 || (P->npix & 1)) return cudaSuccess;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)P->npix, (cuuint64_t)P->n1};
+  const cuuint64_t strides[1] = {(cuuint64_t)P->npix * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)kTcSlabBox, (cuuint32_t)P->tc_na};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&P->tm_xa, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, P->ws.xa, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  P->tm_xa_ok = true;
+  return cudaSuccess;
+}
+
 cudaError_t gram_tc_configure() {
   size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
   for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-  if (e != cudaSuccess) return e;
+  for (auto kern : {gram_tc_kernel<32>, gram_tc_kernel<64>, gram_tc_kernel<96>, gram_tc_kernel<112>,
+                    gram_tc_kernel<128>}) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(gram_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gram_tcb_smem_bytes(kTcTileMax));
 }

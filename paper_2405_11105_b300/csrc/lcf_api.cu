@@ -202,6 +202,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
       e = dalloc(&w.gtc, P->tc_T > 1 ? nd * P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
                                       : nd * P->tc_nsplit * 2 * P->tc_na * P->tc_na, &tot);
     if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kDeflateMax * kDeflateMax, &tot);
+    if (e == cudaSuccess) e = gram_tc_make_map(P);
   }
   if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.lam, nd * nt, &tot);

@@ -1,6 +1,7 @@
 // lcf_internal.cuh — plan layout, double-float helpers and kernel entry
 // points shared by the library's translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,6 +26,7 @@ constexpr int kProjectShortNmax = 128;
 // Largest augmented row (Nt + deflation vectors) of the tensor-core Gram (one M = 128 tile).
 constexpr int kTcGramNaMax = 128;
 constexpr int kTcTileMax = 112;   // row tile of the long-packet tensor-core Gram (three stages fit)
+constexpr int kTcSlabBox = 34;    // pixels per tensor-core Gram slab load (32 used; 272-byte rows)
 // Subspace-iteration block of the EVD (head directions isolated exactly).
 constexpr int kEvdHead = 8;
 // Slow-time DCT-II vectors deflated from every pixel before the Gram.
@@ -115,6 +117,10 @@ struct lcf_plan {
   std::vector<lcf::Box> boxes;
   lcf::Workspace ws;
   size_t ws_bytes = 0;
+  // xa as a 2-D tensor of 8-byte elements ([n1 rows][npix]), boxes of kTcSlabBox pixels x tc_na
+  // rows: the tensor-core Gram's slab loads (valid when npix is even and tc_T == 1)
+  CUtensorMap tm_xa{};
+  bool tm_xa_ok = false;
   cudaStream_t last_stream = nullptr;       // stream of the latest call (0 = the legacy default stream)
   bool launched = false;                    // some call has put work on last_stream
   cudaStream_t h2d_stream = nullptr;        // copy stream of lcf_filter_host_async
@@ -243,6 +249,7 @@ cudaError_t launch_gram_simt(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st);
 cudaError_t gram_tc_configure();
+cudaError_t gram_tc_make_map(lcf_plan* P);
 size_t gram_tc_smem_bytes(int na);
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd(const lcf_plan* P, cudaStream_t st);
