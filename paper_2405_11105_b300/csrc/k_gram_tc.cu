@@ -52,15 +52,12 @@ __host__ __device__ inline int tc_rows_hi(int nbh) { return 2 * nbh > 128 ? 2 * 
 constexpr int TW_PROD = 8;                       // producer warps: split, promote
 constexpr int TW_THREADS = 32 * (TW_PROD + 2);   // + one warp issuing the MMAs, one loading the slabs
 
-// fp32 slab staging, two slots: row r of the slab at r * 272 bytes when the loader warp copies it
-// (one tensor-map load of kTcSlabBox pixels x na rows; the rows' 16-byte pitch offset keeps the
-// producers' 16-row reads free of bank conflicts), or thread t's two pixels of rows rl + 16 j at
-// j * 4096 + t * 16 when each producer thread copies its own (cp.async, odd Nz Nx)
+// fp32 slab staging, two slots: row r of the slab at r * 272 bytes, filled by one tensor-map load
+// of kTcSlabBox pixels x na rows (the 16 bytes past 32 pixels offset the rows' banks, so the
+// producers' 16-row reads are free of conflicts), or, for odd Nz Nx, by each producer thread's
+// cp.async copies of exactly the 16 bytes per row that it reads
 constexpr int TW_ROWB = kTcSlabBox * 8;
-__host__ __device__ inline size_t tc_slot_bytes(int na) {
-  const size_t a = (size_t)na * TW_ROWB, b = (size_t)((na + 15) / 16) * 4096;
-  return ((a > b ? a : b) + 1023) / 1024 * 1024;
-}
+__host__ __device__ inline size_t tc_slot_bytes(int na) { return ((size_t)na * TW_ROWB + 1023) / 1024 * 1024; }
 __host__ __device__ inline size_t tc_raw_bytes(int na) { return 2 * tc_slot_bytes(na); }
 size_t gram_tc_smem_bytes_n(int na, int nstg) {
   int nbh = tc_nbh(na), rh = tc_rows_hi(nbh);
@@ -84,18 +81,36 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // A slab is 32 consecutive pixels of one box row, starting at xs = x0 - ((z nx + x0) mod 2) + 32 c
 // (an even linear index: a tensor-map load must start on a 16-byte boundary); pixels outside
-// [x0, x1) take weight 0.  nch = ceil((x1 - x0 + 1) / 32) slabs per box row.
+// [x0, x1) take weight 0.  The shift is x0 mod 2 on every row when Nx is even, else 0 or 1, so
+// nch = ceil((x1 - x0 + sh) / 32) slabs per box row with sh = x0 mod 2 (Nx even) or 1 (Nx odd).
+// Slabs are visited in order: (row zr, chunk cx) advance without divisions.
 struct TcSlab {
-  int z, xs;
-  long p0;
+  int zr, cx;
+  __device__ __forceinline__ void start(int t, int nch) {
+    zr = t / nch;
+    cx = t - zr * nch;
+  }
+  __device__ __forceinline__ void next(int nch) {
+    if (++cx == nch) { cx = 0; ++zr; }
+  }
+  __device__ __forceinline__ int z(const Box& b) const { return b.z0 + zr; }
+  __device__ __forceinline__ int xs(const Box& b, int nx) const {
+    return b.x0 - (((b.z0 + zr) * nx + b.x0) & 1) + 32 * cx;
+  }
+  __device__ __forceinline__ long p0(const Box& b, int nx) const { return (long)(b.z0 + zr) * nx + xs(b, nx); }
 };
-__device__ __forceinline__ TcSlab tc_slab(const Box& b, int nx, int nch, int t) {
-  TcSlab q;
-  const int zr = t / nch, cx = t - zr * nch;
-  q.z = b.z0 + zr;
-  q.xs = b.x0 - ((q.z * nx + b.x0) & 1) + 32 * cx;
-  q.p0 = (long)q.z * nx + q.xs;
-  return q;
+
+// barrier among the producer warps (threads 0 .. 32 TW_PROD - 1) only
+__device__ __forceinline__ void tc_bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TW_PROD) : "memory"); }
+// float -> double on the integer pipes (exact for normal numbers, zero, infinities and NaN;
+// subnormal floats become signed zero): the double conversion runs on the FP64 units, which
+// are few on this part
+__device__ __forceinline__ double tc_f2d(float f) {
+  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const uint64_t e2 = e == 0xffu ? 0x7ffu : (uint64_t)e + 896u;
+  return __longlong_as_double((long long)(sign | (e2 << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
 }
 
 // NS: FP32 register sums per thread (>= nbh, a multiple of 16)
@@ -106,7 +121,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
                const unsigned* __restrict__ xmax_bits, int nsplit, int nstg, double* __restrict__ part,
                int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned, derived from the shared array itself (shared-space addressing)
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full_bar[TG_STAGES];    // stage's operands written (one arrive per producer warp)
   __shared__ __align__(8) uint64_t empty_bar[TG_STAGES];   // stage's MMAs done
   __shared__ __align__(8) uint64_t acc_bar[2];             // accumulator's chunk done
@@ -119,7 +135,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
   const int nbh = tc_nbh(na), N = 2 * nbh, rh = tc_rows_hi(nbh);
   const size_t hi_bytes = (size_t)rh * 128, lo_bytes = (size_t)N * 128, st_bytes = hi_bytes + lo_bytes;
   const Box b = boxes[k];
-  const int nch = (b.x1 - b.x0 + 1 + TG_PX - 1) / TG_PX;
+  const int nch = (b.x1 - b.x0 + ((nx & 1) ? 1 : (b.x0 & 1)) + TG_PX - 1) / TG_PX;
   const int S = (b.z1 - b.z0) * nch;
   const int t0 = (int)((long)S * s / nsplit), nst = (int)((long)S * (s + 1) / nsplit) - t0;
   const size_t npix = (size_t)nz * nx;
@@ -179,11 +195,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     // (pixels past the image read as zero)
     if (bulk && lane == 0) {
       bool ok = true;
-      for (int i = 0; i < nst; ++i) {
-        const TcSlab q = tc_slab(b, nx, nch, t0 + i);
+      TcSlab q;
+      q.start(t0, nch);
+      for (int i = 0; i < nst; ++i, q.next(nch)) {
         if (i >= 2 && ok) ok = tc::mbar_wait(&rempty_bar[i & 1], ((i >> 1) - 1) & 1);
         tc::mbar_arrive_expect_tx(&rfull_bar[i & 1], (uint32_t)(na * TW_ROWB));
-        tc::tma_load_2d(raw + (size_t)(i & 1) * slot_bytes, &tmx, (int)q.p0, 0, &rfull_bar[i & 1]);
+        tc::tma_load_2d(raw + (size_t)(i & 1) * slot_bytes, &tmx, (int)q.p0(b, nx), 0, &rfull_bar[i & 1]);
       }
       if (!ok) atomicOr(err, 1);
     }
@@ -194,25 +211,28 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
     const float* gzk = gz + (size_t)k * nz;
     const float* gxk = gx + (size_t)k * nx;
-    const int roff = bulk ? rl * TW_ROWB + ps * 8 : tid * 16;   // this thread's 16 bytes of row rl in a slot
-    const int jstr = bulk ? 16 * TW_ROWB : 4096;                   // ... and of row rl + 16 j
+    // this thread's 16 bytes of slab row rl + 16 j: roff + j * 16 * TW_ROWB within a slot
+    const int roff = rl * TW_ROWB + ps * 8;
+    // its operand entries of row rl + 16 j (K entries 2 ps .. 2 ps + 3): soff + 2048 j within the
+    // B_hi / B_lo buffers, rows nbh + r another (nbh / 8) core-row groups further
+    const uint32_t soff = (uint32_t)((rl >> 3) * TG_SBO + (2 * ps >> 3) * 128 + (rl & 7) * 16 + (2 * ps & 7) * 2);
+    const uint32_t sneg = (uint32_t)(nbh >> 3) * TG_SBO;
     float sums[NS];
 #pragma unroll
     for (int j = 0; j < NS; ++j) sums[j] = 0.f;
     bool ok = true;
 
     // cp.async path: this thread's two pixels of slab i (every row) into slot i & 1
-    auto issue = [&](int i) {
-      const TcSlab q = tc_slab(b, nx, nch, t0 + i);
-      const long pa = q.p0 + ps;
+    auto issue = [&](int i, const TcSlab& q) {
+      const long pa = q.p0(b, nx) + ps;
       const bool v0 = pa >= 0 && pa < (long)npix, v1 = pa + 1 >= 0 && pa + 1 < (long)npix;
-      float2* dst = reinterpret_cast<float2*>(raw + (size_t)(i & 1) * slot_bytes + roff);
+      unsigned char* dst = raw + (size_t)(i & 1) * slot_bytes + roff;
       for (int j = 0; j < rb; ++j) {
         const int r = rl + 16 * j;
-        const bool vr = r < na;
-        const float2* srow = xa + (size_t)(vr ? r : 0) * npix;
-        cp_async8(dst + (size_t)j * 512, srow + (v0 ? pa : 0), vr && v0);
-        cp_async8(dst + (size_t)j * 512 + 1, srow + (v1 ? pa + 1 : 0), vr && v1);
+        if (r >= na) break;
+        const float2* srow = xa + (size_t)r * npix;
+        cp_async8(dst + (size_t)j * 16 * TW_ROWB, srow + (v0 ? pa : 0), v0);
+        cp_async8(dst + (size_t)j * 16 * TW_ROWB + 8, srow + (v1 ? pa + 1 : 0), v1);
       }
       cp_async_commit();
     };
@@ -240,20 +260,23 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
       tc::fence_before();
     };
 
-    if (!bulk && nst > 0) issue(0);
+    TcSlab q, qn;
+    q.start(t0, nch);
+    qn = q;
+    qn.next(nch);
+    if (!bulk && nst > 0) issue(0, q);
     int next_epi = 0;   // first chunk whose accumulator is still to be read
-    for (int i = 0; i < nst; ++i) {
+    for (int i = 0; i < nst; ++i, q = qn, qn.next(nch)) {
       const int si = i % nstg;
       // window weights of this thread's two pixels
-      const TcSlab q = tc_slab(b, nx, nch, t0 + i);
-      const int xa0 = q.xs + ps;
-      const float gzz = gzk[q.z];
+      const int xa0 = q.xs(b, nx) + ps;
+      const float gzz = gzk[q.z(b)];
       const float g0 = (xa0 >= b.x0 && xa0 < b.x1) ? gzz * gxk[xa0] : 0.f;
       const float g1 = (xa0 + 1 >= b.x0 && xa0 + 1 < b.x1) ? gzz * gxk[xa0 + 1] : 0.f;
       if (bulk) {
         if (ok) ok = tc::mbar_wait(&rfull_bar[i & 1], (i >> 1) & 1);
       } else if (i + 1 < nst) {   // the next slab's copy overlaps this one's split
-        issue(i + 1);
+        issue(i + 1, qn);
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
@@ -262,26 +285,25 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
       {
         // The pixel pair's four K entries (re, im, re, im) of row r are 8 contiguous bytes of a
         // core-matrix row; a warp's 8-byte stores cover 16 rows x 2 pixel pairs (two wavefronts).
-        unsigned char* Bhi = smem + si * st_bytes;
+        unsigned char* Bhi = smem + si * st_bytes + soff;
         unsigned char* Blo = Bhi + hi_bytes;
         const unsigned char* src = raw + (size_t)(i & 1) * slot_bytes + roff;
-        const int kk = 2 * ps;
         const float2 gg0 = make_float2(g0 * sc, g0 * sc), gg1 = make_float2(g1 * sc, g1 * sc);
         const float2 gd0 = make_float2(2.f * gg0.x, 2.f * gg0.x), gd1 = make_float2(2.f * gg1.x, 2.f * gg1.x);
-#pragma unroll 4
-        for (int j = 0; j < rb; ++j) {
-          const int r = rl + 16 * j;
-          if (r >= na) break;
-          const float4 v = *reinterpret_cast<const float4*>(src + (size_t)j * jstr);
-          __half2 h[2], l[2], w[2];
-          tc::split2_f16(make_float2(v.x, v.y), gg0, gd0, h[0], l[0]);
-          tc::split2_f16(make_float2(v.z, v.w), gg1, gd1, h[1], l[1]);
-          *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(h);
-          w[0] = tc::neg_i(h[0]); w[1] = tc::neg_i(h[1]);
-          *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-          *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(l);
-          w[0] = tc::neg_i(l[0]); w[1] = tc::neg_i(l[1]);
-          *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+#pragma unroll
+        for (int j = 0; j < kTcGramNaMax / 16; ++j) {
+          if (rl + 16 * j < na) {
+            const float4 v = *reinterpret_cast<const float4*>(src + j * 16 * TW_ROWB);
+            __half2 h[2], l[2], w[2];
+            tc::split2_f16(make_float2(v.x, v.y), gg0, gd0, h[0], l[0]);
+            tc::split2_f16(make_float2(v.z, v.w), gg1, gd1, h[1], l[1]);
+            *reinterpret_cast<uint2*>(Bhi + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(h);
+            w[0] = tc::neg_i(h[0]); w[1] = tc::neg_i(h[1]);
+            *reinterpret_cast<uint2*>(Bhi + sneg + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(w);
+            *reinterpret_cast<uint2*>(Blo + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(l);
+            w[0] = tc::neg_i(l[0]); w[1] = tc::neg_i(l[1]);
+            *reinterpret_cast<uint2*>(Blo + sneg + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(w);
+          }
         }
       }
       tc::fence_proxy_async();
@@ -298,12 +320,22 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     for (int e = next_epi; nst > 0 && e <= (nst - 1) / TG_CPA; ++e) epilogue(e);
     if (!ok && lane == 0) atomicOr(err, 1);
 
-    // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na)
-    double* out = part + (((size_t)k * nsplit + s) * 2 + half) * na * na;
+    // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na), written coalesced
+    // through shared memory (every MMA has completed and every producer has split its last slab
+    // once this warp's last epilogue returned, so the operand and slab buffers are free)
+    float* tr = reinterpret_cast<float*>(smem);   // [2][na][ldt], ldt odd: conflict-free column writes
+    const int ldt = na + 1 - (na & 1);
+    tc_bar_producers();
     if (row < na) {
 #pragma unroll
       for (int j = 0; j < NS; ++j)
-        if (j < na) out[(size_t)row * na + j] = (double)sums[j];
+        if (j < na) tr[((size_t)half * na + row) * ldt + j] = sums[j];
+    }
+    tc_bar_producers();
+    double* out = part + ((size_t)k * nsplit + s) * 2 * na * na;
+    for (int e = tid; e < 2 * na * na; e += 32 * TW_PROD) {
+      const int pl = e / (na * na), rem = e - pl * na * na, r = rem / na, j = rem - r * na;
+      out[e] = tc_f2d(tr[((size_t)pl * na + r) * ldt + j]);
     }
   }
   tc::fence_before();
