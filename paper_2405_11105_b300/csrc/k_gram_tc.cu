@@ -15,12 +15,13 @@
 //
 // One CTA per (window, range of 32-pixel slabs), warp-specialised: a loader
 // warp brings each slab (32 pixels of a box row x all rows) into shared memory
-// with one tensor-map load; eight producer warps split it into a 3-stage ring of
-// MMA operands and signal the stage's `full` mbarrier; one warp issues the
+// with one tensor-map load; sixteen producer warps split it into a 3-stage ring
+// of MMA operands and signal the stage's `full` mbarrier; one warp issues the
 // tcgen05.mma chain and commits `empty` (stage reusable) and the accumulator's
-// barrier.  No CTA-wide barrier inside the loop.  Two TMEM accumulators in
-// ping-pong (128 pixels each) are promoted by the producers into FP32 register
-// sums per (row, column half); the range's sum is written as a double partial.
+// barrier.  No CTA-wide barrier inside the loop.  The TMEM accumulator holds a
+// chain of TG_CPA slabs; the producers promote it into round-to-nearest
+// FP32 sums kept in a second TMEM region (load, add, store back) before the next
+// chain starts; the range's sum is written as a double partial.
 // The d x d coefficient block (largest entries) comes from gram_q_kernel with
 // exact double-float products instead.
 #include <math.h>
@@ -36,20 +37,21 @@ constexpr int TG_THREADS = 256;
 constexpr int TG_PX = 32;                  // pixels per stage
 constexpr int TG_K = 2 * TG_PX;            // K elements per stage
 constexpr int TG_STAGES = 3;
-// Stages per TMEM accumulation chain.  The tensor core's FP32 accumulation
-// rounds toward zero, so a chain of n additions biases same-sign sums by
-// ~n * 2^-25 (relative) of the chain's magnitude.  After deflation the
-// chain sums residual (blood + noise) products only, so chains of 4 stages
-// (256 pixel products) promoted into round-to-nearest FP32 register sums keep
-// the bias below the 1e-7 level of the Gram tolerance.
-constexpr int TG_CPA = 4;
+// Stages per TMEM accumulation chain before the chain is promoted into the
+// round-to-nearest FP32 sums.  The tensor core's FP32 accumulation rounds
+// toward zero, which biases long same-sign chains; after deflation the chains
+// sum residual (blood + noise) products only, and chains of 16 stages (512
+// pixel products) leave the Gram's error against the FP64 oracle where chains
+// of 4 had it (1.6e-8 relative at 256x128 px, Nt = 100; 8.9e-9 at 96x64x32;
+// unchanged up to 64 stages), far inside the 1e-6 tolerance.
+constexpr int TG_CPA = 16;
 constexpr int TG_SBO = (TG_K / 8) * 128;   // bytes between 8-row groups
 constexpr int TG_NBH_MAX = 128;
 
 __host__ __device__ inline int tc_nbh(int na) { return (na + 7) / 8 * 8; }
 __host__ __device__ inline int tc_rows_hi(int nbh) { return 2 * nbh > 128 ? 2 * nbh : 128; }
 
-constexpr int TW_PROD = 8;                       // producer warps: split, promote
+constexpr int TW_PROD = 16;                      // producer warps: split, promote
 constexpr int TW_THREADS = 32 * (TW_PROD + 2);   // + one warp issuing the MMAs, one loading the slabs
 
 // fp32 slab staging, two slots: row r of the slab at r * 272 bytes, filled by one tensor-map load
@@ -113,8 +115,11 @@ __device__ __forceinline__ double tc_f2d(float f) {
   return __longlong_as_double((long long)(sign | (e2 << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
 }
 
-// NS: FP32 register sums per thread (>= nbh, a multiple of 16)
-template <int NS>
+// Promotion: the accumulator (columns [0, 2 nbh)) holds one chain of TG_CPA slabs; the FP32
+// sums of the chains live in TMEM columns [256, 256 + 2 nbh).  Producer warp w promotes the
+// 16-column blocks w / 4, w / 4 + 4, ... of TMEM lane quarter w mod 4.
+constexpr uint32_t TW_SUMS = 256;
+
 __global__ void __launch_bounds__(TW_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float2* __restrict__ xa, int nz, int nx,
                int na, const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
@@ -125,7 +130,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
   unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full_bar[TG_STAGES];    // stage's operands written (one arrive per producer warp)
   __shared__ __align__(8) uint64_t empty_bar[TG_STAGES];   // stage's MMAs done
-  __shared__ __align__(8) uint64_t acc_bar[2];             // accumulator's chunk done
+  __shared__ __align__(8) uint64_t acc_bar;                // the accumulator's chain done
+  __shared__ __align__(8) uint64_t accfree_bar;            // the chain promoted (one arrive per producer warp)
   __shared__ __align__(8) uint64_t rfull_bar[2];           // slab slot loaded (tensor-map path)
   __shared__ __align__(8) uint64_t rempty_bar[2];          // slab slot read by every producer warp (tensor-map path)
   __shared__ uint32_t tmem_base;
@@ -138,6 +144,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
   const int nch = (b.x1 - b.x0 + ((nx & 1) ? 1 : (b.x0 & 1)) + TG_PX - 1) / TG_PX;
   const int S = (b.z1 - b.z0) * nch;
   const int t0 = (int)((long)S * s / nsplit), nst = (int)((long)S * (s + 1) / nsplit) - t0;
+  const int nchain = (nst + TG_CPA - 1) / TG_CPA;
   const size_t npix = (size_t)nz * nx;
   const bool bulk = use_map != 0;
   const int rb = (na + 15) / 16;
@@ -153,8 +160,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
       tc::mbar_init(&full_bar[i], TW_PROD);
       tc::mbar_init(&empty_bar[i], 1);
     }
+    tc::mbar_init(&acc_bar, 1);
+    tc::mbar_init(&accfree_bar, TW_PROD);
     for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(&acc_bar[i], 1);
       tc::mbar_init(&rfull_bar[i], 1);
       tc::mbar_init(&rempty_bar[i], TW_PROD);
     }
@@ -166,8 +174,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
   const uint32_t tbase = tmem_base;
 
   if (warp == TW_PROD) {
-    // ---- MMA warp: D' = A B_hi^T + A (2 B_lo)^T per stage, chains of TG_CPA stages
-    if (lane == 0) {
+    // ---- MMA warp: D' = A B_hi^T + A (2 B_lo)^T per stage, chains of TG_CPA stages.  The whole
+    // warp runs the loop (warp-uniform counters and descriptors); one elected lane issues.
+    {
       const uint32_t idesc = tc::idesc_f16(128, N);
       const uint32_t sb = tc::smem_u32(smem);
       const uint64_t dh0 = tc::smem_desc(sb, 128, TG_SBO), dl0 = tc::smem_desc(sb + (uint32_t)hi_bytes, 128, TG_SBO);
@@ -175,20 +184,25 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
       for (int i = 0; i < nst; ++i) {
         const int si = i % nstg, c = i / TG_CPA;
         if (ok) ok = tc::mbar_wait(&full_bar[si], (i / nstg) & 1);
+        // a chain starts once the previous one has been promoted out of the accumulator
+        if (i % TG_CPA == 0 && c > 0 && ok) ok = tc::mbar_wait(&accfree_bar, (c - 1) & 1);
+        ok = __all_sync(~0u, ok);
         tc::fence_after();
         // descriptors advance in 16-byte units: a stage, then two core matrices (16 K) per step
         const uint64_t so = (uint64_t)((si * st_bytes) >> 4);
-        const uint32_t d = tbase + (uint32_t)((c & 1) * 256);
+        if (tc::elect_one()) {
 #pragma unroll
-        for (int ks = 0; ks < TG_K / 16; ++ks) {
-          const uint64_t ad = dh0 + so + (uint64_t)(16 * ks), ld = dl0 + so + (uint64_t)(16 * ks);
-          tc::mma_f16(d, ad, ad, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
-          tc::mma_f16(d, ad, ld, idesc, 1u);
+          for (int ks = 0; ks < TG_K / 16; ++ks) {
+            const uint64_t ad = dh0 + so + (uint64_t)(16 * ks), ld = dl0 + so + (uint64_t)(16 * ks);
+            tc::mma_f16(tbase, ad, ad, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
+            tc::mma_f16(tbase, ad, ld, idesc, 1u);
+          }
+          tc::mma_commit(&empty_bar[si]);
+          if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar);
         }
-        tc::mma_commit(&empty_bar[si]);
-        if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
+        __syncwarp();
       }
-      if (!ok) atomicOr(err, 1);
+      if (!ok && lane == 0) atomicOr(err, 1);
     }
   } else if (warp == TW_PROD + 1) {
     // ---- loader warp (tensor-map path): slab i into slot i & 1, one load of kTcSlabBox x na
@@ -205,9 +219,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
       if (!ok) atomicOr(err, 1);
     }
   } else {
-    // ---- producer warps: lane owns pixel slots (ps, ps + 1) of every slab and rows rl + 16 j
-    const int half = warp >> 2, lgrp = warp & 3, row = lgrp * 32 + lane;
-    const int ps = 4 * warp + 2 * (lane & 1), rl = lane >> 1;
+    // ---- producer warps: warp w splits pixel slots (ps, ps + 1), ps = 4 (w mod 8) + 2 (lane mod 2),
+    // of rows rl + 16 j for j = w / 8, w / 8 + 2, ...
+    const int pg = warp & 7, jh = warp >> 3, lgrp = warp & 3, cq = warp >> 2;
+    const int ps = 4 * pg + 2 * (lane & 1), rl = lane >> 1;
     const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
     const float* gzk = gz + (size_t)k * nz;
     const float* gxk = gx + (size_t)k * nx;
@@ -217,17 +232,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     // B_hi / B_lo buffers, rows nbh + r another (nbh / 8) core-row groups further
     const uint32_t soff = (uint32_t)((rl >> 3) * TG_SBO + (2 * ps >> 3) * 128 + (rl & 7) * 16 + (2 * ps & 7) * 2);
     const uint32_t sneg = (uint32_t)(nbh >> 3) * TG_SBO;
-    float sums[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) sums[j] = 0.f;
+    const uint32_t tl = tbase + ((uint32_t)(lgrp * 32) << 16);   // this warp's TMEM lane quarter
+    const int nb16 = (N + 15) / 16;
     bool ok = true;
 
-    // cp.async path: this thread's two pixels of slab i (every row) into slot i & 1
+    // cp.async path: this thread's two pixels of slab i (its rows) into slot i & 1
     auto issue = [&](int i, const TcSlab& q) {
       const long pa = q.p0(b, nx) + ps;
       const bool v0 = pa >= 0 && pa < (long)npix, v1 = pa + 1 >= 0 && pa + 1 < (long)npix;
       unsigned char* dst = raw + (size_t)(i & 1) * slot_bytes + roff;
-      for (int j = 0; j < rb; ++j) {
+      for (int j = jh; j < rb; j += 2) {
         const int r = rl + 16 * j;
         if (r >= na) break;
         const float2* srow = xa + (size_t)r * npix;
@@ -236,28 +250,29 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
       }
       cp_async_commit();
     };
-    auto epilogue = [&](int c) {
-      if (ok) ok = tc::mbar_wait(&acc_bar[c & 1], (c >> 1) & 1);   // after a timeout, no further waits
+    // chain c: sums += accumulator (c == 0: sums = accumulator), this warp's column blocks
+    auto promote = [&](int c) {
+      if (ok) ok = tc::mbar_wait(&acc_bar, c & 1);   // after a timeout, no further waits
       tc::fence_after();
-      const uint32_t base = tbase + (uint32_t)((c & 1) * 256) + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)(half * nbh);
-      // two 16-column loads in flight per wait
 #pragma unroll
-      for (int cc = 0; cc < NS / 16; cc += 2) {
-        if (cc * 16 < nbh) {
-          uint32_t v0[16], v1[16];
-          tc::tmem_ld16_async(base + cc * 16, v0);
-          if ((cc + 1) * 16 < nbh) tc::tmem_ld16_async(base + (cc + 1) * 16, v1);
+      for (int bq = 0; bq < 4; ++bq) {
+        const int blk = cq + 4 * bq;
+        if (blk < nb16) {
+          uint32_t a[16], t[16];
+          tc::tmem_ld16_async(tl + (uint32_t)(16 * blk), a);
+          if (c > 0) tc::tmem_ld16_async(tl + TW_SUMS + (uint32_t)(16 * blk), t);
           tc::tmem_wait_ld();
+          if (c > 0) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sums[cc * 16 + j] += __uint_as_float(v0[j]);
-          if ((cc + 1) * 16 < nbh) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) sums[(cc + 1) * 16 + j] += __uint_as_float(v1[j]);
+            for (int j = 0; j < 16; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(t[j]));
           }
+          tc::tmem_st16(tl + TW_SUMS + (uint32_t)(16 * blk), a);
         }
       }
-      // the accumulator is reused by chunk c + 2, whose MMAs wait for this warp's later `full` arrival
+      tc::tmem_wait_st();
       tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&accfree_bar);
     };
 
     TcSlab q, qn;
@@ -265,7 +280,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     qn = q;
     qn.next(nch);
     if (!bulk && nst > 0) issue(0, q);
-    int next_epi = 0;   // first chunk whose accumulator is still to be read
+    int next_c = 0;   // first chain still to be promoted
     for (int i = 0; i < nst; ++i, q = qn, qn.next(nch)) {
       const int si = i % nstg;
       // window weights of this thread's two pixels
@@ -291,7 +306,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
         const float2 gg0 = make_float2(g0 * sc, g0 * sc), gg1 = make_float2(g1 * sc, g1 * sc);
         const float2 gd0 = make_float2(2.f * gg0.x, 2.f * gg0.x), gd1 = make_float2(2.f * gg1.x, 2.f * gg1.x);
 #pragma unroll
-        for (int j = 0; j < kTcGramNaMax / 16; ++j) {
+        for (int jj = 0; jj < kTcGramNaMax / 32; ++jj) {
+          const int j = 2 * jj + jh;
           if (rl + 16 * j < na) {
             const float4 v = *reinterpret_cast<const float4*>(src + j * 16 * TW_ROWB);
             __half2 h[2], l[2], w[2];
@@ -312,25 +328,42 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
         tc::mbar_arrive(&full_bar[si]);
         if (bulk) tc::mbar_arrive(&rempty_bar[i & 1]);
       }
-      // Chunk c-1's accumulator is read half-way through chunk c, when its MMAs have long
-      // completed; chunk c+1, which reuses it, needs this warp's arrival on a later stage.
-      const int c = i / TG_CPA;
-      if (i % TG_CPA == TG_CPA / 2 && c > 0) { epilogue(c - 1); next_epi = c; }
+      // Chain c ends with slab C c + C - 1 (C = TG_CPA); its promotion comes after slab C (c + 1) + 1
+      // is split, where the next slab would wait for the same MMAs to free its operand stage.
+      if (i % TG_CPA == 1 && i / TG_CPA >= 1) promote(next_c++);
     }
-    for (int e = next_epi; nst > 0 && e <= (nst - 1) / TG_CPA; ++e) epilogue(e);
+    while (next_c < nchain) promote(next_c++);
     if (!ok && lane == 0) atomicOr(err, 1);
 
     // partial: plane 0 = Re D', plane 1 = Im D' (rows i < na, columns j < na), written coalesced
     // through shared memory (every MMA has completed and every producer has split its last slab
-    // once this warp's last epilogue returned, so the operand and slab buffers are free)
+    // once the last chain was promoted, so the operand and slab buffers are free)
     float* tr = reinterpret_cast<float*>(smem);   // [2][na][ldt], ldt odd: conflict-free column writes
     const int ldt = na + 1 - (na & 1);
     tc_bar_producers();
-    if (row < na) {
+    const int row = lgrp * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < NS; ++j)
-        if (j < na) tr[((size_t)half * na + row) * ldt + j] = sums[j];
+    for (int bq = 0; bq < 4; ++bq) {
+      const int blk = cq + 4 * bq;
+      if (blk < nb16) {
+        uint32_t a[16];
+        if (nchain > 0) {
+          tc::tmem_ld16_async(tl + TW_SUMS + (uint32_t)(16 * blk), a);
+          tc::tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) a[j] = 0u;
+        }
+        if (row < na) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = 16 * blk + j, pl = col >= nbh ? 1 : 0, cj = col - pl * nbh;
+            if (col < N && cj < na) tr[((size_t)pl * na + row) * ldt + cj] = __uint_as_float(a[j]);
+          }
+        }
+      }
     }
+    tc::fence_before();
     tc_bar_producers();
     double* out = part + ((size_t)k * nsplit + s) * 2 * na * na;
     for (int e = tid; e < 2 * na * na; e += 32 * TW_PROD) {
@@ -673,10 +706,7 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
         P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc, P->ws.err);
   } else {
     dim3 grid(P->tc_nsplit, P->nd);
-    const int nbh = tc_nbh(na);
-    auto kern = nbh <= 32 ? gram_tc_kernel<32> : nbh <= 64 ? gram_tc_kernel<64> : nbh <= 96 ? gram_tc_kernel<96>
-              : nbh <= 112 ? gram_tc_kernel<112> : gram_tc_kernel<128>;
-    kern<<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(P->tm_xa, P->tm_xa_ok ? 1 : 0, P->ws.xa, c.nz, c.nx, na,
+    gram_tc_kernel<<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(P->tm_xa, P->tm_xa_ok ? 1 : 0, P->ws.xa, c.nz, c.nx, na,
                                                           P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->tc_nsplit,
                                                           gram_tc_stages(na), P->ws.gtc, P->ws.err);
   }
@@ -752,11 +782,8 @@ cudaError_t gram_tc_make_map(lcf_plan* P) {
 cudaError_t gram_tc_configure() {
   size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
   for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
-  for (auto kern : {gram_tc_kernel<32>, gram_tc_kernel<64>, gram_tc_kernel<96>, gram_tc_kernel<112>,
-                    gram_tc_kernel<128>}) {
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    if (e != cudaSuccess) return e;
-  }
+  const cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(gram_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gram_tcb_smem_bytes(kTcTileMax));
 }
