@@ -269,14 +269,16 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    // ---------------- MMA issuer: the whole warp runs the loop (warp-uniform counters and
+    // descriptors), one elected lane issues ----------------
+    {
       int q = 0, j = 0;
-      uint32_t a_h[2], a_l[2];
-      a_h[0] = tc::smem_u32(A);
-      a_l[0] = tc::smem_u32(A + a_bytes);
-      a_h[1] = tc::smem_u32(A + 2 * a_bytes);
-      a_l[1] = tc::smem_u32(A + 3 * a_bytes);
+      // descriptors advance in 16-byte units: a k-step is two core matrices (256 bytes) of A
+      const uint64_t d_srh = tc::smem_desc(tc::smem_u32(A), 128, a_sbo);
+      const uint64_t d_srl = tc::smem_desc(tc::smem_u32(A + a_bytes), 128, a_sbo);
+      const uint64_t d_sih = tc::smem_desc(tc::smem_u32(A + 2 * a_bytes), 128, a_sbo);
+      const uint64_t d_sil = tc::smem_desc(tc::smem_u32(A + 3 * a_bytes), 128, a_sbo);
+      const uint64_t d_b = tc::smem_desc(tc::smem_u32(Bring), 128, 256);
       for (int wi = w0; wi < w1 && ok; ++wi) {
        const int k = tile_win[wi], nc = ncol[k];
        const int n16w = pt_n16(nc), nch = nc == 0 ? 0 : (lng ? pt_nchunks(n16w) : 1);
@@ -284,25 +286,22 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
         const int n16 = lng ? min(PT_NCH, n16w - ch * PT_NCH) : n16w;
         const int kb = lng ? PT_LKB : pt_kstep_bytes(n16), sub = lng ? PT_NCH * 32 : n16 * 32;
         const int buf = j & 1;
-        if (j >= 2 && !(ok = tc::mbar_wait(&acce[buf], ((j >> 1) - 1) & 1))) break;
+        if (j >= 2 && !(ok = __all_sync(~0u, tc::mbar_wait(&acce[buf], ((j >> 1) - 1) & 1)))) break;
         tc::fence_after();
         const uint32_t idesc = tc::idesc_f16(128, n16), idesc_neg = idesc | (1u << 13);   // bit 13: negate A
         const uint32_t dr = tbase + (uint32_t)(buf * PT_ACC), di = dr + 128;
         for (int s = 0; s < nstw; ++s, ++q) {
           const int slot = q % PT_STAGES;
-          if (!(ok = tc::mbar_wait(&full_bar[slot], (q / PT_STAGES) & 1))) break;
+          if (!(ok = __all_sync(~0u, tc::mbar_wait(&full_bar[slot], (q / PT_STAGES) & 1)))) break;
           tc::fence_after();
           const int nk = min(ksps, nks - s * ksps);
-          const uint32_t bslot = tc::smem_u32(Bring + slot * st_bytes);
+          if (tc::elect_one()) {
           for (int kl = 0; kl < nk; ++kl) {
             const int ks = s * ksps + kl;
-            const uint64_t srh = tc::smem_desc(a_h[0] + ks * 256, 128, a_sbo);
-            const uint64_t srl = tc::smem_desc(a_l[0] + ks * 256, 128, a_sbo);
-            const uint64_t sih = tc::smem_desc(a_h[1] + ks * 256, 128, a_sbo);
-            const uint64_t sil = tc::smem_desc(a_l[1] + ks * 256, 128, a_sbo);
-            const uint32_t bb = bslot + kl * kb;
-            const uint64_t wrh = tc::smem_desc(bb, 128, 256), wrl = tc::smem_desc(bb + sub, 128, 256);
-            const uint64_t wih = tc::smem_desc(bb + 2 * sub, 128, 256), wil = tc::smem_desc(bb + 3 * sub, 128, 256);
+            const uint64_t ao = (uint64_t)(16 * ks);
+            const uint64_t srh = d_srh + ao, srl = d_srl + ao, sih = d_sih + ao, sil = d_sil + ao;
+            const uint64_t bo = (uint64_t)((slot * st_bytes + (size_t)kl * kb) >> 4), so = (uint64_t)(sub >> 4);
+            const uint64_t wrh = d_b + bo, wrl = wrh + so, wih = wrl + so, wil = wih + so;
             const uint32_t acc = ks == 0 ? 0u : 1u;
             // Yr = Sr Wr - Si Wi
             tc::mma_f16(dr, srh, wrh, idesc, acc);
@@ -320,13 +319,16 @@ project_tc_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_
             tc::mma_f16(di, srl, wih, idesc, 1u);
           }
           tc::mma_commit(&empty_bar[slot]);
+          }
+          __syncwarp();
         }
         if (!ok) break;
-        tc::mma_commit(&accf[buf]);
+        if (tc::elect_one()) tc::mma_commit(&accf[buf]);
+        __syncwarp();
         ++j;
        }
       }
-      // every MMA this thread issued has completed before TMEM is released
+      // every MMA this warp issued has completed before TMEM is released
       if (j > 0) tc::mbar_wait(&accf[(j - 1) & 1], ((j - 1) >> 1) & 1, 200000000ull);
     }
   } else if (warp >= 4) {
