@@ -197,6 +197,7 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
                 int nsplit, int qrows, double2* __restrict__ aug) {
   extern __shared__ float2 Xs[];   // [ACH][nt + d]: x_p, pixel-major
   __shared__ float g2s[ACH];
+  __shared__ int pix[ACH];         // linear pixel index of the step's pixels (-1: past the range)
   const int k = blockIdx.y, s = blockIdx.x;
   const int na = nt + nd_defl, nout = (nt + qrows) * nd_defl;
   const Box b = boxes[k];
@@ -215,18 +216,24 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
   for (int u = 0; u < OPT; ++u) { acc[u] = make_float2(0.f, 0.f); hr[u] = {0.f, 0.f}; hi[u] = {0.f, 0.f}; }
 
   for (long l = l0; l < l1; l += ACH) {
-    for (int e = threadIdx.x; e < ACH * na; e += blockDim.x) {
-      int pp = e % ACH, i = e / ACH;
-      long ll = l + pp;
-      float2 v = make_float2(0.f, 0.f);
+    if (threadIdx.x < ACH) {   // the step's pixels and weights, once per pixel
+      const int ll = (int)l + threadIdx.x;   // box pixel counts are below 2^31 (plan validation)
+      int p = -1;
+      float g2 = 0.f;
       if (ll < l1) {
-        int z = b.z0 + (int)(ll / W), x = b.x0 + (int)(ll % W);
-        v = xa[(size_t)i * npix + z * nx + x];
-        if (i == 0) { float g = gzk[z] * gxk[x]; g2s[pp] = g * g; }
-      } else if (i == 0) {
-        g2s[pp] = 0.f;
+        const int zr = ll / W, xr = ll - zr * W;
+        const int z = b.z0 + zr, x = b.x0 + xr;
+        p = z * nx + x;
+        const float g = gzk[z] * gxk[x];
+        g2 = g * g;
       }
-      Xs[pp * na + i] = v;
+      pix[threadIdx.x] = p;
+      g2s[threadIdx.x] = g2;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ACH * na; e += blockDim.x) {
+      const int pp = e % ACH, i = e / ACH, p = pix[pp];
+      Xs[pp * na + i] = p >= 0 ? xa[(size_t)i * npix + p] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll

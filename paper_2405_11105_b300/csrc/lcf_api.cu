@@ -154,7 +154,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     int pairs = P->gram_tiles * (P->gram_tiles + 1) / 2;
     int want = (4 * P->sm_count + pairs * P->nd - 1) / (pairs * P->nd);
     P->gram_nsplit = want < 1 ? 1 : (want > 64 ? 64 : want);
-    int wa = (2 * P->sm_count + P->nd - 1) / P->nd;
+    int wa = (4 * P->sm_count + P->nd - 1) / P->nd;   // about four pixel ranges per SM
     P->aug_nsplit = wa < 1 ? 1 : (wa > 64 ? 64 : wa);
     P->q_nsplit = P->aug_nsplit;
     int gt = (P->nt + 63) / 64;
