@@ -124,16 +124,29 @@ gram_simt_kernel(const float2* __restrict__ xa, int nz, int nx, int n1, const Bo
       hi[a][c] = {0.f, 0.f};
     }
 
+  __shared__ int gpix[GCH];     // the step's linear pixel indices (-1: past the range)
+  __shared__ float gg2[GCH];    // and squared window weights
   for (long l = l0; l < l1; l += GCH) {
+    if (threadIdx.x < GCH) {   // (the previous step's tables were read before its closing barrier)
+      const int ll = (int)l + threadIdx.x;   // box pixel counts are below 2^31 (plan validation)
+      int p = -1;
+      float g2 = 0.f;
+      if (ll < l1) {
+        const int zr = ll / W, xr = ll - zr * W;
+        p = (b.z0 + zr) * nx + b.x0 + xr;
+        const float g = gzk[b.z0 + zr] * gxk[b.x0 + xr];
+        g2 = g * g;
+      }
+      gpix[threadIdx.x] = p;
+      gg2[threadIdx.x] = g2;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < GCH * GT; e += 256) {
       int pp = e % GCH, tt = e / GCH;
-      long ll = l + pp;
       float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
-      if (ll < l1) {
-        int z = b.z0 + (int)(ll / W), x = b.x0 + (int)(ll % W);
-        int p = z * nx + x;
-        float g = gzk[z] * gxk[x];
-        float g2 = g * g;
+      const int p = gpix[pp];
+      if (p >= 0) {
+        const float g2 = gg2[pp];
         int i = ti * GT + tt, j = tj * GT + tt;
         if (i < n1) { float2 v = xa[(size_t)i * npix + p]; va = make_float2(g2 * v.x, -g2 * v.y); }
         if (j < n1) vb = xa[(size_t)j * npix + p];

@@ -475,7 +475,7 @@ gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, i
       int pp = 0;
       float g = 0.f;
       if (l < Pk) {
-        const int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
+        const int zr = (int)l / W, z = b.z0 + zr, x = b.x0 + (int)l - zr * W;   // below 2^31
         pp = z * nx + x;
         g = gzk[z] * gxk[x] * sc;
       }
@@ -564,7 +564,7 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
 #pragma unroll
   for (int e = 0; e < kDeflateMax * kDeflateMax; ++e) { qr[e] = {0.f, 0.f}; qi[e] = {0.f, 0.f}; }
   for (long l = l0 + tid; l < l1; l += blockDim.x) {
-    const int z = b.z0 + (int)(l / W), x = b.x0 + (int)(l % W);
+    const int zr = (int)l / W, z = b.z0 + zr, x = b.x0 + (int)l - zr * W;   // box pixel counts are below 2^31
     const size_t p = (size_t)z * nx + x;
     float g = gz[(size_t)k * nz + z] * gx[(size_t)k * nx + x];
     float g2 = g * g;
