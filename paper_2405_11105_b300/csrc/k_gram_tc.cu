@@ -742,7 +742,9 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   // the reduced sum sits in split 0 of each window: read it as a single split
   // with the window stride of the full buffer
   const int nup = P->nt * (P->nt + 1) / 2;
-  dim3 grid((nup + 255) / 256 < 8 ? (nup + 255) / 256 : 8, P->nd);
+  // four blocks per window: each recomputes the window's W-form columns (FP64), so fewer blocks
+  // cost less FP64 work in total, and four still fill the GPU at Nd = 64
+  dim3 grid((nup + 255) / 256 < 4 ? (nup + 255) / 256 : 4, P->nd);
   gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ws.phi,
                                                  P->ws.xmax,
                                                  P->tc_T > 1 ? (size_t)P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
