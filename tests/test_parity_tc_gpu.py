@@ -63,6 +63,8 @@ def test_tc_realtime_soft_rule():
     ((16, 17, 23), (1, 1), "LCF_T_MEDIAN"),
     ((112, 24, 20), (2, 2), "LCF_T_CURVATURE"),
     ((2, 8, 8), (1, 1), "LCF_T_FIXED"),
+    ((48, 24, 17), (2, 2), "LCF_T_CURVATURE"),   # Nz Nx even, Nx odd: slab starts alternate parity by row
+    ((40, 34, 33), (3, 2), "LCF_T_FIXED"),       # boxes wider than one 32-pixel slab, odd Nx
 ])
 def test_tc_edge_shapes(shape, grid, mode):
     lib = L()
