@@ -135,6 +135,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
   __shared__ __align__(8) uint64_t rfull_bar[2];           // slab slot loaded (tensor-map path)
   __shared__ __align__(8) uint64_t rempty_bar[2];          // slab slot read by every producer warp (tensor-map path)
   __shared__ uint32_t tmem_base;
+  __shared__ float wts[2][TG_PX];   // window weights of the slab in slot 0 / 1 (tensor-map path)
 
   const int k = blockIdx.y, s = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -206,17 +207,25 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     }
   } else if (warp == TW_PROD + 1) {
     // ---- loader warp (tensor-map path): slab i into slot i & 1, one load of kTcSlabBox x na
-    // (pixels past the image read as zero)
-    if (bulk && lane == 0) {
+    // (pixels past the image read as zero), and the slab's window weights, one pixel per lane
+    if (bulk) {
       bool ok = true;
+      const float* gzk = gz + (size_t)k * nz;
+      const float* gxk = gx + (size_t)k * nx;
       TcSlab q;
       q.start(t0, nch);
       for (int i = 0; i < nst; ++i, q.next(nch)) {
         if (i >= 2 && ok) ok = tc::mbar_wait(&rempty_bar[i & 1], ((i >> 1) - 1) & 1);
-        tc::mbar_arrive_expect_tx(&rfull_bar[i & 1], (uint32_t)(na * TW_ROWB));
-        tc::tma_load_2d(raw + (size_t)(i & 1) * slot_bytes, &tmx, (int)q.p0(b, nx), 0, &rfull_bar[i & 1]);
+        ok = __all_sync(~0u, ok);
+        const int x = q.xs(b, nx) + lane;
+        wts[i & 1][lane] = (x >= b.x0 && x < b.x1) ? gzk[q.z(b)] * gxk[x] : 0.f;
+        __syncwarp();   // the weights are written before the slab's arrival publishes them
+        if (lane == 0) {
+          tc::mbar_arrive_expect_tx(&rfull_bar[i & 1], (uint32_t)(na * TW_ROWB));
+          tc::tma_load_2d(raw + (size_t)(i & 1) * slot_bytes, &tmx, (int)q.p0(b, nx), 0, &rfull_bar[i & 1]);
+        }
       }
-      if (!ok) atomicOr(err, 1);
+      if (!ok && lane == 0) atomicOr(err, 1);
     }
   } else {
     // ---- producer warps: warp w splits pixel slots (ps, ps + 1), ps = 4 (w mod 8) + 2 (lane mod 2),
@@ -283,18 +292,26 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     int next_c = 0;   // first chain still to be promoted
     for (int i = 0; i < nst; ++i, q = qn, qn.next(nch)) {
       const int si = i % nstg;
-      // window weights of this thread's two pixels
-      const int xa0 = q.xs(b, nx) + ps;
-      const float gzz = gzk[q.z(b)];
-      const float g0 = (xa0 >= b.x0 && xa0 < b.x1) ? gzz * gxk[xa0] : 0.f;
-      const float g1 = (xa0 + 1 >= b.x0 && xa0 + 1 < b.x1) ? gzz * gxk[xa0 + 1] : 0.f;
+      // window weights of this thread's two pixels: from the loader (published with the slab)
+      // or computed here
+      float g0, g1;
       if (bulk) {
         if (ok) ok = tc::mbar_wait(&rfull_bar[i & 1], (i >> 1) & 1);
-      } else if (i + 1 < nst) {   // the next slab's copy overlaps this one's split
-        issue(i + 1, qn);
-        cp_async_wait<1>();
+        g0 = wts[i & 1][ps];
+        g1 = wts[i & 1][ps + 1];
       } else {
-        cp_async_wait<0>();
+        const int xa0 = q.xs(b, nx) + ps;
+        const float gzz = gzk[q.z(b)];
+        g0 = (xa0 >= b.x0 && xa0 < b.x1) ? gzz * gxk[xa0] : 0.f;
+        g1 = (xa0 + 1 >= b.x0 && xa0 + 1 < b.x1) ? gzz * gxk[xa0 + 1] : 0.f;
+      }
+      if (!bulk) {
+        if (i + 1 < nst) {   // the next slab's copy overlaps this one's split
+          issue(i + 1, qn);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
       }
       if (i >= nstg && ok) ok = tc::mbar_wait(&empty_bar[si], ((i / nstg) - 1) & 1);
       {
