@@ -773,7 +773,8 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
 
 // Tensor map of the augmented rows for the slab loads: 8-byte elements, [n1][npix], boxes of
 // kTcSlabBox x tc_na, zero fill outside.  Needs the row pitch (npix * 8 bytes) to be a multiple
-// of 16; odd pixel counts keep the per-thread copies.
+// of 16; odd pixel counts keep the per-thread copies, and so does a plan whose map cannot be
+// made (no driver entry point), with the same results.
 cudaError_t gram_tc_make_map(lcf_plan* P) {
   P->tm_xa_ok = false;
   if (P->tc_T != 1 || (P->npix & 1)) return cudaSuccess;
@@ -782,8 +783,11 @@ cudaError_t gram_tc_make_map(lcf_plan* P) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();   // not sticky: clear it, keep the per-thread copies
+      return cudaSuccess;
+    }
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaSuccess;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t dims[2] = {(cuuint64_t)P->npix, (cuuint64_t)P->n1};
@@ -793,8 +797,7 @@ cudaError_t gram_tc_make_map(lcf_plan* P) {
   const CUresult r = encode(&P->tm_xa, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, P->ws.xa, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  P->tm_xa_ok = true;
+  P->tm_xa_ok = r == CUDA_SUCCESS;
   return cudaSuccess;
 }
 
