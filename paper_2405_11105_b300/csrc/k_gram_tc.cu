@@ -21,7 +21,8 @@
 // barrier.  No CTA-wide barrier inside the loop.  The TMEM accumulator holds a
 // chain of TG_CPA slabs; the producers promote it into round-to-nearest
 // FP32 sums kept in a second TMEM region (load, add, store back) before the next
-// chain starts; the range's sum is written as a double partial.
+// chain starts; the range's sum is written as an FP32 partial, added over the
+// ranges in double by gram_tc_reduce_kernel.
 // The d x d coefficient block (largest entries) comes from gram_q_kernel with
 // exact double-float products instead.
 #include <math.h>
@@ -104,17 +105,6 @@ struct TcSlab {
 
 // barrier among the producer warps (threads 0 .. 32 TW_PROD - 1) only
 __device__ __forceinline__ void tc_bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TW_PROD) : "memory"); }
-// float -> double on the integer pipes (exact for normal numbers, zero, infinities and NaN;
-// subnormal floats become signed zero): the double conversion runs on the FP64 units, which
-// are few on this part
-__device__ __forceinline__ double tc_f2d(float f) {
-  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
-  const uint64_t sign = (uint64_t)(u >> 31) << 63;
-  if (e == 0) return __longlong_as_double((long long)sign);
-  const uint64_t e2 = e == 0xffu ? 0x7ffu : (uint64_t)e + 896u;
-  return __longlong_as_double((long long)(sign | (e2 << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
-}
-
 // Promotion: the accumulator (columns [0, 2 nbh)) holds one chain of TG_CPA slabs; the FP32
 // sums of the chains live in TMEM columns [256, 256 + 2 nbh).  Producer warp w promotes the
 // 16-column blocks w / 4, w / 4 + 4, ... of TMEM lane quarter w mod 4.
@@ -382,10 +372,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     }
     tc::fence_before();
     tc_bar_producers();
-    double* out = part + ((size_t)k * nsplit + s) * 2 * na * na;
+    // FP32 partials (the sums are FP32): gram_tc_reduce_kernel adds the splits in double
+    float* out = reinterpret_cast<float*>(part) + ((size_t)k * nsplit + s) * 2 * na * na;
     for (int e = tid; e < 2 * na * na; e += 32 * TW_PROD) {
       const int pl = e / (na * na), rem = e - pl * na * na, r = rem / na, j = rem - r * na;
-      out[e] = tc_f2d(tr[((size_t)pl * na + r) * ldt + j]);
+      out[e] = tr[((size_t)pl * na + r) * ldt + j];
     }
   }
   tc::fence_before();
@@ -736,36 +727,57 @@ cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
   return launch_gram_aug(P, st, false);   // U for the residual-only tensor-core rows
 }
 
-// part[k][0] += sum_{s>0} part[k][s] (coalesced; fixed split order)
-__global__ void gram_tc_reduce_kernel(double* __restrict__ part, int nsplit, size_t per_split) {
+// float -> double on the integer pipes (exact for normal numbers, zero, infinities and NaN;
+// subnormal floats become signed zero): the conversion instruction runs on the FP64 units,
+// which are few on this part
+__device__ __forceinline__ double tc_f2d(float f) {
+  const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const uint64_t e2 = e == 0xffu ? 0x7ffu : (uint64_t)e + 896u;
+  return __longlong_as_double((long long)(sign | (e2 << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+
+// sums[k] = sum_s part[k][s], splits in order (coalesced); part holds FP32 partials, added in
+// double-float on the FP32 pipes (~2^-48 relative, far below the partials' own rounding) and
+// converted once
+__global__ void gram_tc_reduce_kernel(const float* __restrict__ part, double* __restrict__ sums, int nsplit,
+                                      size_t per_split) {
   const int k = blockIdx.y;
-  double* pk = part + (size_t)k * nsplit * per_split;
+  const float* pk = part + (size_t)k * nsplit * per_split;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_split; e += (size_t)gridDim.x * blockDim.x) {
-    double acc = pk[e];
-    for (int s = 1; s < nsplit; ++s) acc += pk[(size_t)s * per_split + e];
-    pk[e] = acc;
+    df acc = {pk[e], 0.f};
+    for (int s = 1; s < nsplit; ++s) acc = df_add_f(acc, pk[(size_t)s * per_split + e]);
+    sums[(size_t)k * per_split + e] = tc_f2d(acc.hi) + tc_f2d(acc.lo);
   }
+}
+
+// FP32 partials of the one-tile tensor-core Gram at the start of gtc, their double sums after
+// them (the buffer holds max(nsplit, 2) splits' worth of doubles)
+size_t gram_tc_sums_offset(const lcf_plan* P) {
+  const size_t per_split = (size_t)2 * P->tc_na * P->tc_na, nf = (size_t)P->nd * P->tc_nsplit * per_split;
+  return (nf + 1) / 2;   // in doubles
 }
 
 cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   const int na = P->tc_na;
   const size_t per_split = (size_t)2 * na * na;
-  if (P->tc_T == 1 && P->tc_nsplit > 1) {
+  double* sums = P->ws.gtc + gram_tc_sums_offset(P);
+  if (P->tc_T == 1) {
     dim3 gr((unsigned)((per_split + 255) / 256), P->nd);
-    gram_tc_reduce_kernel<<<gr, 256, 0, st>>>(P->ws.gtc, P->tc_nsplit, per_split);
+    gram_tc_reduce_kernel<<<gr, 256, 0, st>>>(reinterpret_cast<const float*>(P->ws.gtc), sums, P->tc_nsplit,
+                                              per_split);
     cudaError_t e = counted(P);
     if (e != cudaSuccess) return e;
   }
-  // the reduced sum sits in split 0 of each window: read it as a single split
-  // with the window stride of the full buffer
   const int nup = P->nt * (P->nt + 1) / 2;
   // four blocks per window: each recomputes the window's W-form columns (FP64), so fewer blocks
   // cost less FP64 work in total, and four still fill the GPU at Nd = 64
   dim3 grid((nup + 255) / 256 < 4 ? (nup + 255) / 256 : 4, P->nd);
-  gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->ws.gtc, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ws.phi,
-                                                 P->ws.xmax,
+  gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->tc_T > 1 ? P->ws.gtc : sums, P->ws.gq, P->ws.gaug,
+                                                 P->aug_nsplit, P->ws.phi, P->ws.xmax,
                                                  P->tc_T > 1 ? (size_t)P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
-                                                             : (size_t)P->tc_nsplit * per_split,
+                                                             : per_split,
                                                  P->tc_T, P->tc_tb, P->q_nsplit, P->nt, P->ndefl, na,
                                                  P->ws.R);
   return counted(P);

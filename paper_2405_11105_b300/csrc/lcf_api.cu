@@ -200,7 +200,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (cfg->gram_path == LCF_PATH_TC) {
     if (e == cudaSuccess)
       e = dalloc(&w.gtc, P->tc_T > 1 ? nd * P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
-                                      : nd * P->tc_nsplit * 2 * P->tc_na * P->tc_na, &tot);
+                                      : nd * std::max(P->tc_nsplit, 2) * 2 * P->tc_na * P->tc_na, &tot);
     if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kDeflateMax * kDeflateMax, &tot);
     if (e == cudaSuccess) e = gram_tc_make_map(P);
   }

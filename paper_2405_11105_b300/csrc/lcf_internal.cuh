@@ -59,8 +59,9 @@ struct Workspace {
   double2* gpart = nullptr;   // [nd][nsplit][nt][nt] partial residual Grams
   double2* gaug = nullptr;    // [nd][aug_nsplit][(nt+ndefl)*ndefl] partial augmented columns
   unsigned* xmax = nullptr;   // [1] max |component| of the deflated packet (float bits)
-  double* gtc = nullptr;      // [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes),
-                              // or [nd][T][T][2][tb][tb] tile-pair partials for long packets
+  double* gtc = nullptr;      // f32 [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes)
+                              // then their f64 sums [nd][2][na][na]; or f64 [nd][T][T][2][tb][tb]
+                              // tile-pair partials for long packets
   double2* gq = nullptr;      // [nd][q_nsplit][kDeflateMax^2] exact coefficient-block partials
   int* err = nullptr;         // [1] device error word (bit 0: a bounded wait gave up)
   double2* R = nullptr;       // [nd][nt][nt] windowed Gram (Eq. 12)
