@@ -95,6 +95,8 @@ project_prep_kernel(const float2* __restrict__ W, const int* __restrict__ ncol, 
   for (int e = tid; e < nd_defl * nc; e += blockDim.x) {   // phi_j^T W(:, c), double-float sums
     const int j = e / nc, c = e % nc;
     df sr = {0.f, 0.f}, si = {0.f, 0.f};
+    // unrolled so that the loads run ahead of the (serial) double-float sums
+#pragma unroll 10
     for (int t = 0; t < nt; ++t) {
       const float2 f = phi[j * nt + t], w = Wk[(size_t)t * ncp + c];
       sr = df_add(sr, df_add(two_prod_df(f.x, w.x), df_neg(two_prod_df(f.y, w.y))));
