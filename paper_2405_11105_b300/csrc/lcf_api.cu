@@ -121,7 +121,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
                   w.flags, w.W, w.pw, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.evd_B, w.evd_vh, w.evd_t,
-                  w.evd_scale, w.iq_stage, w.pd_stage};
+                  w.evd_scale, w.iq_stage, w.pd_stage, w.phi_alt, w.xmax_alt, w.gglob_async};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -191,11 +191,14 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = dalloc(&w.gx, nd * cfg->nx, &tot);
   if (e == cudaSuccess) e = dalloc(&w.box, nd, &tot);
   if (e == cudaSuccess) e = dalloc(&w.phi, (size_t)P->ndefl * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.phi_alt, (size_t)P->ndefl * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.gglob, (size_t)P->basis_nsplit * nt * nt, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.gglob_async, (size_t)P->basis_nsplit * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.xa, n1 * npix, &tot);
   if (e == cudaSuccess) e = dalloc(&w.gpart, nd * P->gram_nsplit * nt * nt, &tot);
   if (e == cudaSuccess) e = dalloc(&w.gaug, nd * P->aug_nsplit * n1 * P->ndefl, &tot);
   if (e == cudaSuccess) e = dalloc(&w.xmax, 1, &tot);
+  if (e == cudaSuccess) e = dalloc(&w.xmax_alt, 1, &tot);
   if (e == cudaSuccess) e = dalloc(&w.err, 1, &tot);
   if (cfg->gram_path == LCF_PATH_TC) {
     if (e == cudaSuccess)
@@ -245,6 +248,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess) e = cudaMemset(w.flags, 0, nd * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(w.err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(w.xmax, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(w.xmax_alt, 0, sizeof(unsigned));
   if (e == cudaSuccess && cfg->project_path == LCF_PATH_TC) {
     e = cudaMemcpy(w.tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !twin.empty())
@@ -297,12 +301,13 @@ static cudaEvent_t prof_event(lcf_plan* P, int b) {
     if (ev_) LCF_CUDA(cudaEventRecord(ev_, st));                 \
   } while (0)
 
-static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
+// with_basis false: the packet's basis (phi, xmax) was prepared on another stream already
+static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t st, bool with_basis = true) {
   const lcf_config& c = P->cfg;
   const bool tc = c.gram_path == LCF_PATH_TC;
   if (c.thresh_mode == LCF_T_LEARNED && P->mlp_hidden == 0) return LCF_EINVAL;   // no network set
   LCF_MARK(LCF_STAGE_PREP);
-  LCF_CUDA(launch_basis(P, iq, st));
+  if (with_basis) LCF_CUDA(launch_basis(P, iq, st));
   LCF_CUDA(launch_center(P, iq, st));
   LCF_MARK(LCF_STAGE_GRAM);
   if (tc) {
@@ -380,6 +385,15 @@ extern "C" lcf_status lcf_plan_evd_phases(lcf_plan* P, double* cycles) {
   return LCF_OK;
 }
 
+// A filter call other than the pipelined one: the next pipelined packet's basis prep (on its own
+// stream) must not overwrite the basis buffers this call reads, so it waits for this event once.
+static lcf_status note_seq(lcf_plan* P, cudaStream_t stream) {
+  if (!P->ev_seq) LCF_CUDA(cudaEventCreateWithFlags(&P->ev_seq, cudaEventDisableTiming));
+  LCF_CUDA(cudaEventRecord(P->ev_seq, stream));
+  P->seq_since_async = true;
+  return LCF_OK;
+}
+
 extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd, cudaStream_t stream) {
   if (!P || !d_iq || !d_out_pd) return LCF_EINVAL;
   if (((uintptr_t)d_iq & 7) || ((uintptr_t)d_out_pd & 3)) return LCF_EINVAL;
@@ -388,6 +402,7 @@ extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd,
   P->last_stream = stream;
   P->launched = true;
   P->last_iq = (void*)d_iq;
+  if (s == LCF_OK) s = note_seq(P, stream);
   return s;
 }
 
@@ -397,6 +412,8 @@ extern "C" lcf_status lcf_filter_host(lcf_plan* P, const void* h_iq, float* h_ou
   const size_t in_bytes = (size_t)P->nt * P->npix * sizeof(float2);
   LCF_CUDA(cudaMemcpyAsync(P->ws.iq_stage, h_iq, in_bytes, cudaMemcpyHostToDevice, stream));
   lcf_status s = run_packet(P, P->ws.iq_stage, P->ws.pd_stage, stream);
+  if (s != LCF_OK) return s;
+  s = note_seq(P, stream);
   if (s != LCF_OK) return s;
   LCF_CUDA(cudaMemcpyAsync(h_out_pd, P->ws.pd_stage, (size_t)P->npix * sizeof(float), cudaMemcpyDeviceToHost,
                            stream));
@@ -412,12 +429,21 @@ extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float
   DeviceGuard g(P->device);
   if (!P->h2d_stream) {
     LCF_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
+    LCF_CUDA(cudaStreamCreateWithFlags(&P->prep_stream, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
       LCF_CUDA(cudaEventCreateWithFlags(&P->ev_in[b], cudaEventDisableTiming));
       LCF_CUDA(cudaEventCreateWithFlags(&P->ev_done[b], cudaEventDisableTiming));
+      LCF_CUDA(cudaEventCreateWithFlags(&P->ev_prep[b], cudaEventDisableTiming));
     }
   }
   const int b = (int)(P->host_seq & 1);
+  // the packet's basis and maximum live in buffer pair b, so that the next packet's basis prep
+  // can run while this packet's later kernels still read them
+  if (P->basis_par != b) {
+    std::swap(P->ws.phi, P->ws.phi_alt);
+    std::swap(P->ws.xmax, P->ws.xmax_alt);
+    P->basis_par = b;
+  }
   const size_t in_elems = (size_t)P->nt * P->npix;
   float2* iq = P->ws.iq_stage + (size_t)b * in_elems;
   float* pd = P->ws.pd_stage + (size_t)b * P->npix;
@@ -425,8 +451,27 @@ extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float
   if (P->host_seq >= 2) LCF_CUDA(cudaStreamWaitEvent(P->h2d_stream, P->ev_done[b], 0));
   LCF_CUDA(cudaMemcpyAsync(iq, h_iq, in_elems * sizeof(float2), cudaMemcpyHostToDevice, P->h2d_stream));
   LCF_CUDA(cudaEventRecord(P->ev_in[b], P->h2d_stream));
-  LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_in[b], 0));
-  lcf_status s = run_packet(P, iq, pd, stream);
+  lcf_status s;
+  if (P->profiling) {   // stage events want every stage on `stream`
+    LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_in[b], 0));
+    s = run_packet(P, iq, pd, stream);
+  } else {
+    // basis prep on the plan's prep stream once the input is in (buffer pair b is free by then:
+    // the copy waited for the packet two back), overlapping the previous packet's kernels
+    LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, P->ev_in[b], 0));
+    if (P->seq_since_async) {   // another filter call since the last pipelined one may still read phi
+      LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, P->ev_seq, 0));
+      P->seq_since_async = false;
+    }
+    // its own global-Gram scratch: a synchronous call on `stream` may be running its basis
+    std::swap(P->ws.gglob, P->ws.gglob_async);
+    const cudaError_t eb = launch_basis(P, iq, P->prep_stream);
+    std::swap(P->ws.gglob, P->ws.gglob_async);
+    LCF_CUDA(eb);
+    LCF_CUDA(cudaEventRecord(P->ev_prep[b], P->prep_stream));
+    LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_prep[b], 0));
+    s = run_packet(P, iq, pd, stream, false);
+  }
   if (s != LCF_OK) return s;
   LCF_CUDA(cudaMemcpyAsync(h_out_pd, pd, (size_t)P->npix * sizeof(float), cudaMemcpyDeviceToHost, stream));
   LCF_CUDA(cudaEventRecord(P->ev_done[b], stream));
@@ -441,6 +486,7 @@ extern "C" lcf_status lcf_plan_sync(lcf_plan* P) {
   if (!P) return LCF_EINVAL;
   DeviceGuard g(P->device);
   if (P->h2d_stream) LCF_CUDA(cudaStreamSynchronize(P->h2d_stream));
+  if (P->prep_stream) LCF_CUDA(cudaStreamSynchronize(P->prep_stream));
   // the last pipelined packet of each staging buffer, whichever stream it ran on; earlier
   // packets of a buffer finished before its next input copy began
   for (int b = 0; b < 2; ++b)
@@ -502,7 +548,7 @@ extern "C" lcf_status lcf_filter_stream(lcf_plan* P, const void* d_frames, int n
   P->last_stream = stream;
   P->launched = true;
   P->last_iq = (void*)(fr + (size_t)(npk - 1) * stride * P->npix);
-  return LCF_OK;
+  return note_seq(P, stream);
 }
 
 extern "C" lcf_status lcf_plan_status(lcf_plan* P, int* per_window_flags) {
@@ -581,16 +627,20 @@ extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
   if (!P) return LCF_EINVAL;
   DeviceGuard g(P->device);
   if (P->h2d_stream) cudaStreamSynchronize(P->h2d_stream);   // pipelined host calls still in flight
+  if (P->prep_stream) cudaStreamSynchronize(P->prep_stream);
   if (P->launched) cudaStreamSynchronize(P->last_stream);
   free_ws(P->ws);
   for (auto& e : P->prof_ev) cudaEventDestroy(e);
   if (P->sg_exec) cudaGraphExecDestroy(P->sg_exec);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->h2d_stream) cudaStreamDestroy(P->h2d_stream);
+  if (P->prep_stream) cudaStreamDestroy(P->prep_stream);
   for (int b = 0; b < 2; ++b) {
     if (P->ev_in[b]) cudaEventDestroy(P->ev_in[b]);
     if (P->ev_done[b]) cudaEventDestroy(P->ev_done[b]);
+    if (P->ev_prep[b]) cudaEventDestroy(P->ev_prep[b]);
   }
+  if (P->ev_seq) cudaEventDestroy(P->ev_seq);
   delete P;
   return LCF_OK;
 }

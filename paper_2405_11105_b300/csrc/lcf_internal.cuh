@@ -54,11 +54,14 @@ struct Workspace {
   // deflated packet: s_p = c_p + sum_j a_pj phi_j
   float2* phi = nullptr;      // [ndefl][nt] per-packet slow-time deflation basis (complex)
   float2* gglob = nullptr;    // [basis_nsplit][nt][nt] partial global Grams (basis estimate)
+  float2* gglob_async = nullptr;  // the same for the pipelined host calls' prep stream
   float2* xa = nullptr;       // [nt+ndefl][nz*nx]: residual c_p(t), then coefficients a_pj
   // Gram
   double2* gpart = nullptr;   // [nd][nsplit][nt][nt] partial residual Grams
   double2* gaug = nullptr;    // [nd][aug_nsplit][(nt+ndefl)*ndefl] partial augmented columns
   unsigned* xmax = nullptr;   // [1] max |component| of the deflated packet (float bits)
+  float2* phi_alt = nullptr;  // the other staging parity's basis and packet maximum (pipelined
+  unsigned* xmax_alt = nullptr;  // host calls swap them with phi / xmax packet by packet)
   double* gtc = nullptr;      // f32 [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes)
                               // then their f64 sums [nd][2][na][na]; or f64 [nd][T][T][2][tb][tb]
                               // tile-pair partials for long packets
@@ -128,6 +131,11 @@ struct lcf_plan {
   cudaEvent_t ev_in[2] = {nullptr, nullptr};  // staging buffer b filled
   cudaEvent_t ev_done[2] = {nullptr, nullptr};  // staging buffer b consumed
   long long host_seq = 0;                   // pipelined host calls so far
+  cudaStream_t prep_stream = nullptr;       // their basis prep, overlapping the previous packet's kernels
+  cudaEvent_t ev_prep[2] = {nullptr, nullptr};  // staging buffer b's basis ready
+  int basis_par = 0;                        // parity whose basis / maximum are phi / xmax now
+  cudaEvent_t ev_seq = nullptr;             // end of the latest other filter call on its stream
+  bool seq_since_async = false;             // ... not yet waited for by the prep stream
   void* last_iq = nullptr;
   // stage profiling: events[call % kProfCalls][stage boundary]
   // kernels this plan has launched (every launcher adds its own)

@@ -314,3 +314,20 @@ def test_pipelined_host_calls_match_device_path():
         plan.filter_host_async(hin[i], hout[i])
         plan.sync()
         assert torch.equal(hout[i], ref[i]), i
+    # pipelined calls interleaved with the device and synchronous host calls of the same plan
+    # (their basis buffers are shared with the pipelined calls' prep stream)
+    for i in range(6):
+        hout[i].fill_(-1.0)
+    dev = [None] * 6
+    plan.filter_host_async(hin[0], hout[0])
+    plan.filter_host_async(hin[1], hout[1])
+    dev[2] = plan.filter(d[16:48].contiguous())
+    plan.filter_host_async(hin[3], hout[3])
+    host4 = plan.filter_host(hin[4].numpy())
+    plan.filter_host_async(hin[5], hout[5])
+    plan.filter_host_async(hin[2], hout[2])
+    plan.sync()
+    for i in (0, 1, 2, 3, 5):
+        assert torch.equal(hout[i], ref[i]), ("interleaved", i)
+    assert torch.equal(dev[2].cpu(), ref[2])
+    assert np.array_equal(host4, ref[4].numpy())
