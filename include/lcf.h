@@ -141,8 +141,11 @@ lcf_status lcf_filter_host(lcf_plan* plan, const void* h_iq, float* h_out_pd, cu
 /* Pipelined form of lcf_filter_host for a sequence of packets: returns without
  * synchronising.  The packet's host-to-device copy runs on a plan-owned copy
  * stream into one of two device staging buffers (alternating between calls),
- * so it overlaps the previous packet's kernels on `stream`; the image is copied
- * back to h_out_pd on `stream`.  h_iq must stay unchanged and h_out_pd must not
+ * so it overlaps the previous packet's kernels on `stream`; so does the
+ * packet's deflation-basis prep, on a second plan-owned stream once the copy
+ * is in (the basis and packet maximum are kept per staging buffer); the image
+ * is copied back to h_out_pd on `stream`.  Other filter calls on the same plan
+ * may be interleaved (the next pipelined prep waits for them).  h_iq must stay unchanged and h_out_pd must not
  * be read until lcf_plan_sync returns (pinned host memory required for the
  * overlap).  Calls of one plan must use the same `stream`.  The first call
  * creates the copy stream and its events. */
