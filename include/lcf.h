@@ -115,6 +115,11 @@ typedef struct {
   int project_path;        /* LCF_PATH_*                                          */
   int max_sweeps;          /* Jacobi sweep cap per level (<= 0: 40)               */
   int evd_path;            /* LCF_EVD_*                                           */
+  int inputs_ready;        /* 1: every lcf_filter input is complete when the call  */
+                           /* is made (e.g. a resident packet ring), so each       */
+                           /* packet's basis prep starts on a plan-owned stream    */
+                           /* while the previous packet's kernels run; 0 (default):*/
+                           /* the input is read in `stream` order                  */
 } lcf_config;
 
 /* Fill *cfg with defaults for an nz x nx x nt packet and a wz x wx grid:

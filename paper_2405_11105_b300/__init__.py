@@ -35,7 +35,7 @@ class lcf_config(C.Structure):
                 ("k_fixed", C.c_int), ("k_src", C.c_int), ("beta_src", C.c_float),
                 ("pd_mode", C.c_int), ("alpha_mode", C.c_int), ("curv_norm", C.c_int),
                 ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int),
-                ("evd_path", C.c_int)]
+                ("evd_path", C.c_int), ("inputs_ready", C.c_int)]
 
 
 class LcfError(RuntimeError):

@@ -394,15 +394,59 @@ static lcf_status note_seq(lcf_plan* P, cudaStream_t stream) {
   return LCF_OK;
 }
 
+// The pipelined basis prep (lcf_filter_host_async, and lcf_filter when cfg.inputs_ready):
+// packet q's basis and maximum live in buffer pair q mod 2, written on the plan's prep stream
+// once the packet two back (same pair) is done with them and any other filter call since the
+// last prep has finished; `after` orders the prep after the packet's own input.
+static lcf_status pipe_streams(lcf_plan* P) {
+  if (P->prep_stream) return LCF_OK;
+  LCF_CUDA(cudaStreamCreateWithFlags(&P->prep_stream, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b) {
+    LCF_CUDA(cudaEventCreateWithFlags(&P->ev_prep[b], cudaEventDisableTiming));
+    LCF_CUDA(cudaEventCreateWithFlags(&P->ev_pdone[b], cudaEventDisableTiming));
+  }
+  return LCF_OK;
+}
+static lcf_status pipe_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t stream, cudaEvent_t after) {
+  lcf_status s = pipe_streams(P);
+  if (s != LCF_OK) return s;
+  const int p = (int)(P->pipe_seq & 1);
+  if (P->basis_par != p) {
+    std::swap(P->ws.phi, P->ws.phi_alt);
+    std::swap(P->ws.xmax, P->ws.xmax_alt);
+    P->basis_par = p;
+  }
+  if (after) LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, after, 0));
+  if (P->pipe_seq >= 2) LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, P->ev_pdone[p], 0));
+  if (P->seq_since_async) {   // another filter call since the last prep may still read phi
+    LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, P->ev_seq, 0));
+    P->seq_since_async = false;
+  }
+  // its own global-Gram scratch: a synchronous call on `stream` may be running its basis
+  std::swap(P->ws.gglob, P->ws.gglob_async);
+  const cudaError_t eb = launch_basis(P, iq, P->prep_stream);
+  std::swap(P->ws.gglob, P->ws.gglob_async);
+  LCF_CUDA(eb);
+  LCF_CUDA(cudaEventRecord(P->ev_prep[p], P->prep_stream));
+  LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_prep[p], 0));
+  s = run_packet(P, iq, out, stream, false);
+  if (s != LCF_OK) return s;
+  LCF_CUDA(cudaEventRecord(P->ev_pdone[p], stream));
+  ++P->pipe_seq;
+  return LCF_OK;
+}
+
 extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd, cudaStream_t stream) {
   if (!P || !d_iq || !d_out_pd) return LCF_EINVAL;
   if (((uintptr_t)d_iq & 7) || ((uintptr_t)d_out_pd & 3)) return LCF_EINVAL;
   DeviceGuard g(P->device);
-  lcf_status s = run_packet(P, (const float2*)d_iq, d_out_pd, stream);
+  const bool pipe = P->cfg.inputs_ready && !P->profiling;
+  lcf_status s = pipe ? pipe_packet(P, (const float2*)d_iq, d_out_pd, stream, nullptr)
+                      : run_packet(P, (const float2*)d_iq, d_out_pd, stream);
   P->last_stream = stream;
   P->launched = true;
   P->last_iq = (void*)d_iq;
-  if (s == LCF_OK) s = note_seq(P, stream);
+  if (s == LCF_OK && !pipe) s = note_seq(P, stream);
   return s;
 }
 
@@ -429,21 +473,12 @@ extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float
   DeviceGuard g(P->device);
   if (!P->h2d_stream) {
     LCF_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
-    LCF_CUDA(cudaStreamCreateWithFlags(&P->prep_stream, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
       LCF_CUDA(cudaEventCreateWithFlags(&P->ev_in[b], cudaEventDisableTiming));
       LCF_CUDA(cudaEventCreateWithFlags(&P->ev_done[b], cudaEventDisableTiming));
-      LCF_CUDA(cudaEventCreateWithFlags(&P->ev_prep[b], cudaEventDisableTiming));
     }
   }
   const int b = (int)(P->host_seq & 1);
-  // the packet's basis and maximum live in buffer pair b, so that the next packet's basis prep
-  // can run while this packet's later kernels still read them
-  if (P->basis_par != b) {
-    std::swap(P->ws.phi, P->ws.phi_alt);
-    std::swap(P->ws.xmax, P->ws.xmax_alt);
-    P->basis_par = b;
-  }
   const size_t in_elems = (size_t)P->nt * P->npix;
   float2* iq = P->ws.iq_stage + (size_t)b * in_elems;
   float* pd = P->ws.pd_stage + (size_t)b * P->npix;
@@ -455,22 +490,9 @@ extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float
   if (P->profiling) {   // stage events want every stage on `stream`
     LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_in[b], 0));
     s = run_packet(P, iq, pd, stream);
-  } else {
-    // basis prep on the plan's prep stream once the input is in (buffer pair b is free by then:
-    // the copy waited for the packet two back), overlapping the previous packet's kernels
-    LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, P->ev_in[b], 0));
-    if (P->seq_since_async) {   // another filter call since the last pipelined one may still read phi
-      LCF_CUDA(cudaStreamWaitEvent(P->prep_stream, P->ev_seq, 0));
-      P->seq_since_async = false;
-    }
-    // its own global-Gram scratch: a synchronous call on `stream` may be running its basis
-    std::swap(P->ws.gglob, P->ws.gglob_async);
-    const cudaError_t eb = launch_basis(P, iq, P->prep_stream);
-    std::swap(P->ws.gglob, P->ws.gglob_async);
-    LCF_CUDA(eb);
-    LCF_CUDA(cudaEventRecord(P->ev_prep[b], P->prep_stream));
-    LCF_CUDA(cudaStreamWaitEvent(stream, P->ev_prep[b], 0));
-    s = run_packet(P, iq, pd, stream, false);
+    if (s == LCF_OK) s = note_seq(P, stream);
+  } else {   // basis prep on the prep stream once the input is in, overlapping the previous packet
+    s = pipe_packet(P, iq, pd, stream, P->ev_in[b]);
   }
   if (s != LCF_OK) return s;
   LCF_CUDA(cudaMemcpyAsync(h_out_pd, pd, (size_t)P->npix * sizeof(float), cudaMemcpyDeviceToHost, stream));
@@ -639,6 +661,7 @@ extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
     if (P->ev_in[b]) cudaEventDestroy(P->ev_in[b]);
     if (P->ev_done[b]) cudaEventDestroy(P->ev_done[b]);
     if (P->ev_prep[b]) cudaEventDestroy(P->ev_prep[b]);
+    if (P->ev_pdone[b]) cudaEventDestroy(P->ev_pdone[b]);
   }
   if (P->ev_seq) cudaEventDestroy(P->ev_seq);
   delete P;

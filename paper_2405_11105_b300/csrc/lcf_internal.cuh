@@ -134,6 +134,8 @@ struct lcf_plan {
   cudaStream_t prep_stream = nullptr;       // their basis prep, overlapping the previous packet's kernels
   cudaEvent_t ev_prep[2] = {nullptr, nullptr};  // staging buffer b's basis ready
   int basis_par = 0;                        // parity whose basis / maximum are phi / xmax now
+  long long pipe_seq = 0;                   // packets whose basis prep ran on the prep stream
+  cudaEvent_t ev_pdone[2] = {nullptr, nullptr};  // end of the last such packet of basis parity p
   cudaEvent_t ev_seq = nullptr;             // end of the latest other filter call on its stream
   bool seq_since_async = false;             // ... not yet waited for by the prep stream
   void* last_iq = nullptr;

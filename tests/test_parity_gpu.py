@@ -331,3 +331,37 @@ def test_pipelined_host_calls_match_device_path():
         assert torch.equal(hout[i], ref[i]), ("interleaved", i)
     assert torch.equal(dev[2].cpu(), ref[2])
     assert np.array_equal(host4, ref[4].numpy())
+
+
+def test_inputs_ready_device_calls_match():
+    """cfg.inputs_ready: lcf_filter starts each packet's basis prep on the plan's prep stream
+    (buffer pairs by packet parity); every image equals the in-order plan's, also with
+    synchronous and pipelined host calls interleaved."""
+    import torch
+    lib = L()
+    from synth import generate_frames
+    frames = generate_frames(SMALL_96x64x32, 32 + 5 * 8, seed=7)
+    cfg, _ = configs(96, 64, 32, 3, 3, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    ref_plan = lib.Plan(cfg)
+    d = torch.from_numpy(frames).cuda()
+    pk = [d[i * 8:i * 8 + 32].contiguous() for i in range(6)]
+    ref = [ref_plan.filter(pk[i]).cpu() for i in range(6)]
+    cfg.inputs_ready = 1
+    plan = lib.Plan(cfg)
+    torch.cuda.synchronize()
+    outs = [plan.filter(pk[i]) for i in range(6)]
+    torch.cuda.synchronize()
+    for i in range(6):
+        assert torch.equal(outs[i].cpu(), ref[i]), i
+    hin = torch.from_numpy(frames[8:40].copy()).pin_memory()
+    hout = torch.full((96, 64), -1.0, dtype=torch.float32).pin_memory()
+    o0 = plan.filter(pk[0])
+    plan.filter_host_async(hin, hout)
+    o2 = plan.filter(pk[2])
+    h3 = plan.filter_host(frames[24:56].copy())
+    o4 = plan.filter(pk[4])
+    plan.sync()
+    torch.cuda.synchronize()
+    assert torch.equal(o0.cpu(), ref[0]) and torch.equal(hout, ref[1])
+    assert torch.equal(o2.cpu(), ref[2]) and np.array_equal(h3, ref[3].numpy())
+    assert torch.equal(o4.cpu(), ref[4])
