@@ -135,7 +135,11 @@ lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_plan** out);
 
 /* Filter one packet.  d_iq: device pointer to iq[nt][nz][nx] complex64
  * (8-byte aligned).  d_out_pd: device pointer to out_pd[nz][nx] float32.
- * Asynchronous on `stream`; no allocation, no synchronisation. */
+ * Asynchronous on `stream`; no allocation, no synchronisation.  d_iq is read
+ * in `stream` order, except with cfg.inputs_ready set, where the packet's
+ * basis prep may read it on a plan-owned stream as soon as the call is made
+ * (so d_iq must be complete then); the image is written in `stream` order
+ * either way. */
 lcf_status lcf_filter(lcf_plan* plan, const void* d_iq, float* d_out_pd, cudaStream_t stream);
 
 /* Same computation with HOST buffers: copies h_iq to the device, filters,
