@@ -32,27 +32,25 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_config_struct_layout_matches_header():
+    """Every field of the ctypes mirror sits at the C struct's offset, and the sizes agree."""
     import paper_2405_11105_b300 as L
-    prog = r"""
-    #include <stdio.h>
-    #include <stddef.h>
-    #include "lcf.h"
-    int main(void) {
-      printf("%zu %zu %zu %zu\n", sizeof(lcf_config), offsetof(lcf_config, beta),
-             offsetof(lcf_config, gram_path), offsetof(lcf_config, max_sweeps));
-      return 0;
-    }"""
+    cfg = L.lcf_config
+    names = [f[0] for f in cfg._fields_]
+    prints = "".join('      printf("%%zu\\n", offsetof(lcf_config, %s));\n' % n for n in names)
+    prog = (
+        "#include <stdio.h>\n#include <stddef.h>\n#include \"lcf.h\"\n"
+        "int main(void) {\n"
+        '      printf("%zu\\n", sizeof(lcf_config));\n' + prints + "      return 0;\n}\n")
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         open(c, "w").write(prog)
         exe = os.path.join(d, "t")
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include", c,
                         "-o", exe], check=True)
-        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
-    size, beta, gp, ms = map(int, out)
-    cfg = L.lcf_config
-    assert C.sizeof(cfg) == size
-    assert cfg.beta.offset == beta and cfg.gram_path.offset == gp and cfg.max_sweeps.offset == ms
+        out = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
+    assert C.sizeof(cfg) == out[0]
+    for n, off in zip(names, out[1:]):
+        assert getattr(cfg, n).offset == off, n
 
 
 def test_config_default_and_status_strings():
