@@ -21,6 +21,7 @@ import numpy as np
 from . import build as _build
 
 T_FIXED, T_CURVATURE, T_SLOPE, T_MEDIAN, T_SIGMOID, T_ADAPTIVE_SOFT, T_NONE = range(7)
+T_NCC = 8   # method 4 (Eq. 8); method 5 takes its k with thresh_mode T_SIGMOID, k_src T_NCC
 FLAG_NOCONV, FLAG_DEGENERATE = 1, 2
 
 
@@ -95,6 +96,8 @@ def lib():
         L.ora_window_box.restype = C.c_int
         L.ora_window_weights.argtypes = [P(_Cfg), C.c_int, dp]
         L.ora_window_weights.restype = None
+        L.ora_ncc_curve.argtypes = [fp, P(_Cfg), C.c_int, dp]
+        L.ora_ncc_curve.restype = C.c_int
         _lib = L
     return _lib
 
@@ -196,6 +199,16 @@ def gram(iq: np.ndarray, cfg: OracleConfig, k: int) -> np.ndarray:
     cc = cfg.c()
     lib().ora_gram(_ptr(buf, C.c_float), C.byref(cc), int(k), R.ctypes.data_as(C.POINTER(C.c_double)))
     return R
+
+
+def ncc_curve(iq: np.ndarray, cfg: OracleConfig, k: int):
+    """Method 4 (Eq. 8) of window k from the oracle's own Gram and EVD: (k, curve), where
+    curve[j] = NCC at cutoff j + 1 (NaN where the fn-neighbourhoods do not exist)."""
+    buf = _iq_f32(iq)
+    curve = np.zeros(cfg.nt)
+    cc = cfg.c()
+    kk = lib().ora_ncc_curve(_ptr(buf, C.c_float), C.byref(cc), int(k), _ptr(curve, C.c_double))
+    return int(kk), curve
 
 
 def window_box(cfg: OracleConfig, k: int):

@@ -17,14 +17,14 @@
  *                                Eq. 3)
  *   R_k = V Lambda V^H           Eq. 2, eigenvalues sorted descending; the
  *                                solver is a hand-written cyclic Jacobi
- *   weights wt (Lambda-hat)      thresholding methods 1, 2, 3, 5, 6 (Eq. 6,
- *                                Eq. 7, Eq. 9, Eq. 10) and a fixed cutoff k
+ *   weights wt (Lambda-hat)      thresholding methods 1-6 (Eq. 6, Eq. 7,
+ *                                Eq. 8, Eq. 9, Eq. 10) and a fixed cutoff k
  *   C-hat = C_w (V Lambda-hat V^H)  Eq. 4, literally (the parenthesised
  *                                product is formed first)
  *   PD_k = mean_t |C-hat|^2      power Doppler, mean (or sum) over slow time
  *   PD = sum_k alpha_k PD_k      Eq. 13, alpha_k = 1 / mean flow power
  *
- * Readings of points the paper leaves open (listed in the design doc):
+ * Readings of points the paper leaves open, as this oracle takes them:
  *   - centres at cell midpoints, sigma = sigma_scale * spacing, box support
  *     |dz| <= s*sigma_z and |dx| <= s*sigma_x (s = support_sigmas; s <= 0 means
  *     no clipping);
@@ -76,7 +76,10 @@ typedef struct {
 } ora_config;
 
 enum { ORA_T_FIXED = 0, ORA_T_CURVATURE = 1, ORA_T_SLOPE = 2, ORA_T_MEDIAN = 3,
-       ORA_T_SIGMOID = 4, ORA_T_ADAPTIVE_SOFT = 5, ORA_T_NONE = 6 };
+       ORA_T_SIGMOID = 4, ORA_T_ADAPTIVE_SOFT = 5, ORA_T_NONE = 6, ORA_T_NCC = 8 };
+
+/* neighbours on each side of the cutoff in method 4 (the paper's fn = 5) */
+#define ORA_NCC_FN 5
 
 enum { ORA_FLAG_NOCONV = 1, ORA_FLAG_DEGENERATE = 2 };
 
@@ -351,6 +354,79 @@ int ora_weights(int mode, int n, const double* lam, double beta, int k_fixed, in
 }
 
 /* ------------------------------------------------------------------------
+ * Method 4 (Eq. 8): the cutoff k that minimises the normalised spatial
+ * cross-correlation of a tissue image and a blood image built from the left
+ * singular vectors next to the cutoff.  With C_w V = U D (lambda_i = sigma_i^2),
+ * |u_i(p)| = |(C_w v_i)(p)| / sigma_i per pixel p of the window's support;
+ * I_T(k) = sum_{i=k-fn+1..k} |u_i|, I_B(k) = sum_{i=k+1..k+fn} |u_i| (weights 1),
+ *   NCC(k) = sum_p I_T I_B / (sqrt(sum_p I_T^2) sqrt(sum_p I_B^2)),
+ * for the k whose neighbourhoods exist, fn <= k <= Nt - fn (1-based), with
+ * fn = min(5, Nt/2).  Readings: sigma_i = sqrt(lambda~_i) (the floored
+ * eigenvalue, so a zero eigenvalue gives a zero image, not a division by
+ * zero); a k whose I_T or I_B is zero everywhere gets NCC = 1; ties take the
+ * smallest k.  curve[k-1] = NCC(k), NaN outside the range (nullable).
+ * V: the window's eigenvectors (columns, descending eigenvalues).
+ * ---------------------------------------------------------------------- */
+static int ncc_fn(int n) { return n / 2 < ORA_NCC_FN ? n / 2 : ORA_NCC_FN; }
+
+static int k_ncc(const float* iq, const ora_config* c, const ora_window* w, const zc* V, const double* lam,
+                 double* curve) {
+  int n = c->nt, fn = ncc_fn(n);
+  if (fn < 1) { if (curve) for (int i = 0; i < n; ++i) curve[i] = NAN; return 0; }
+  int nk = n - 2 * fn + 1;                 /* k = fn .. n - fn */
+  double* num = (double*)calloc(3 * (size_t)nk, sizeof(double));
+  double *dt = num + nk, *db = num + 2 * nk;
+  double* sig = (double*)malloc(sizeof(double) * n);
+  double* m = (double*)malloc(sizeof(double) * n);
+  zc* s = (zc*)malloc(sizeof(zc) * n);
+  for (int i = 0; i < n; ++i) sig[i] = sqrt(floor_lambda(lam, n, i));
+  for (int z = w->z0; z < w->z1; ++z)
+    for (int x = w->x0; x < w->x1; ++x) {
+      double g = window_weight(w, z, x);
+      for (int t = 0; t < n; ++t) s[t] = g * iq_at(iq, c, t, z, x);      /* row of C_w */
+      for (int i = 0; i < n; ++i) {                                        /* |u_i(p)| */
+        zc acc = 0;
+        for (int t = 0; t < n; ++t) acc += s[t] * V[t * n + i];
+        m[i] = cabs(acc) / sig[i];
+      }
+      for (int j = 0; j < nk; ++j) {
+        int k = fn + j;                    /* 1-based cutoff */
+        double it = 0.0, ib = 0.0;
+        for (int i = k - fn; i < k; ++i) it += m[i];          /* paper i = k-fn+1 .. k */
+        for (int i = k; i < k + fn; ++i) ib += m[i];          /* paper i = k+1 .. k+fn */
+        num[j] += it * ib;
+        dt[j] += it * it;
+        db[j] += ib * ib;
+      }
+    }
+  if (curve) for (int i = 0; i < n; ++i) curve[i] = NAN;
+  int kbest = fn; double best = INFINITY;
+  for (int j = 0; j < nk; ++j) {
+    double den = sqrt(dt[j]) * sqrt(db[j]);
+    double v = den > 0.0 ? num[j] / den : 1.0;
+    if (curve) curve[fn + j - 1] = v;
+    if (v < best) { best = v; kbest = fn + j; }
+  }
+  free(num); free(sig); free(m); free(s);
+  return kbest;
+}
+
+/* NCC curve of window k (Eq. 8) from the oracle's own Gram and EVD; returns its argmin. */
+int ora_ncc_curve(const float* iq, const ora_config* c, int k, double* curve) {
+  int nt = c->nt;
+  ora_window w = make_window(c, k);
+  zc* R = (zc*)malloc(sizeof(zc) * nt * nt);
+  zc* V = (zc*)malloc(sizeof(zc) * nt * nt);
+  zc* s = (zc*)malloc(sizeof(zc) * nt);
+  double* lk = (double*)malloc(sizeof(double) * nt);
+  gram_window(iq, c, &w, R, s);
+  ora_jacobi(nt, R, V, lk, c->max_sweeps > 0 ? c->max_sweeps : 60);
+  int kk = k_ncc(iq, c, &w, V, lk, curve);
+  free(R); free(V); free(s); free(lk);
+  return kk;
+}
+
+/* ------------------------------------------------------------------------
  * Full pipeline.  Outputs (nullable unless stated):
  *   pd       [nz*nx]   PD_final (required)
  *   lam, wt  [nd*nt]   per-window eigenvalues / weights
@@ -400,10 +476,16 @@ int ora_filter_k(const float* iq, const ora_config* c, double* pd, double* lam, 
     int sw = ora_jacobi(nt, R, V, lk, max_sweeps);                  /* Eq. 2 */
     if (sw < 0) fl |= ORA_FLAG_NOCONV;
     int kc;
-    if (k_override && k_override[k] >= 0 && c->thresh_mode <= ORA_T_SIGMOID) {
+    int uses_ncc = c->thresh_mode == ORA_T_NCC || (c->thresh_mode == ORA_T_SIGMOID && c->k_src == ORA_T_NCC);
+    if (k_override && k_override[k] >= 0 && (c->thresh_mode <= ORA_T_SIGMOID || c->thresh_mode == ORA_T_NCC)) {
       /* the same weights with the cutoff given: a fixed-k rule, or the sigmoid at k */
       int mode = (c->thresh_mode == ORA_T_SIGMOID) ? ORA_T_SIGMOID : ORA_T_FIXED;
       kc = ora_weights(mode, nt, lk, c->beta, k_override[k], ORA_T_FIXED, 0.0, c->curv_norm, wk);
+    } else if (uses_ncc) {
+      /* method 4 (Eq. 8) decides k from the data; method 5 (Eq. 9) may take that k */
+      int kn = k_ncc(iq, c, &w, V, lk, NULL);
+      if (c->thresh_mode == ORA_T_NCC) kc = ora_weights(ORA_T_FIXED, nt, lk, c->beta, kn, ORA_T_FIXED, 0.0, c->curv_norm, wk);
+      else kc = ora_weights(ORA_T_SIGMOID, nt, lk, c->beta, kn, ORA_T_FIXED, 0.0, c->curv_norm, wk);
     } else {
       kc = ora_weights(c->thresh_mode, nt, lk, c->beta, c->k_fixed, c->k_src, c->beta_src,
                        c->curv_norm, wk);
@@ -498,4 +580,4 @@ int ora_rule_scores(int mode, int n, const double* lam, double beta, int curv_no
   return 0;
 }
 
-int ora_abi_version(void) { return 2; }
+int ora_abi_version(void) { return 3; }

@@ -264,6 +264,36 @@ def test_curvature_knee(golden):
         assert k == c["k"], c
 
 
+def test_curvature_knee_literal_normalisation(golden):
+    """curv_norm 1: the paper's literal beta*y(n)/y(1)*Nt curve (method 1, Eq. 6), on spectra
+    whose cutoff follows by hand from the slope s = beta*N/|y(1)| (including y(1) < 0 and
+    y(1) = 0)."""
+    for c in golden["knee_curvature_literal"]:
+        n = np.arange(1, c["N"] + 1)
+        lam = 10.0 ** (c["a"] - (np.minimum(n, c["m"]) - 1.0))
+        _, k = O.weights(O.T_CURVATURE, lam, beta=c["beta"], curv_norm=1)
+        assert k == c["k"], c
+        # the shifted curve of the same spectrum has slope s0 = beta*N/(m-1) whatever a is
+        _, k0 = O.weights(O.T_CURVATURE, lam, beta=c["beta"], curv_norm=0)
+        assert k0 == (c["m"] if c["beta"] * c["N"] / (c["m"] - 1) < 1.5328 else c["m"] + 1), c
+
+
+def test_pd_sum_over_slow_time(golden):
+    """pd_mode 1 (PD summed over slow time instead of averaged) on hand-derived packets:
+    one all-ones window, a fixed cutoff or identity weights; alpha = 1 exposes the factor Nt,
+    alpha by Eq. 13 cancels it."""
+    for c in golden["pd_sum_over_time"]:
+        rows = np.array(c["rows"], float)                     # [pixel][t][re, im]
+        iq = (rows[..., 0] + 1j * rows[..., 1]).T.reshape(c["nt"], c["nz"], c["nx"]).astype(np.complex64)
+        mode = O.T_FIXED if c["k"] >= 0 else O.T_NONE
+        for pd_mode, alpha_mode, key in ((1, 1, "pd_sum_alpha1"), (0, 1, "pd_mean_alpha1"),
+                                         (1, 0, "pd_alpha_eq13"), (0, 0, "pd_alpha_eq13")):
+            cfg = O.OracleConfig(c["nz"], c["nx"], c["nt"], 1, 1, all_ones_window=1, thresh_mode=mode,
+                                 k_fixed=max(c["k"], 0), pd_mode=pd_mode, alpha_mode=alpha_mode)
+            pd = O.filter(iq, cfg).pd.ravel()
+            np.testing.assert_allclose(pd, c[key], rtol=1e-14, atol=1e-14, err_msg=f"{key} pd_mode {pd_mode}")
+
+
 def test_slope_knee(golden):
     for c in golden["knee_slope"]:
         wt, k = O.weights(O.T_SLOPE, knee_spectrum(c["N"], c["m"]), beta=c["beta"])
@@ -320,3 +350,77 @@ def test_rule_scores_agree_with_rules_and_override_equals_fixed():
                  k_override=np.full(9, 5, np.int32))
     b = O.filter(iq, O.OracleConfig(96, 64, 32, 3, 3, thresh_mode=O.T_FIXED, k_fixed=5))
     assert np.array_equal(a.pd, b.pd) and np.all(a.k == 5)
+
+
+# ------------------------------------------------- method 4 (NCC, Eq. 8)
+def ncc_from_left_vectors(absU, fn):
+    """NCC(k) of Eq. 8 from the magnitudes of left singular vectors [pixels, Nt] (numpy)."""
+    n = absU.shape[1]
+    curve = np.full(n, np.nan)
+    for k in range(fn, n - fn + 1):
+        it = absU[:, k - fn:k].sum(axis=1)
+        ib = absU[:, k:k + fn].sum(axis=1)
+        curve[k - 1] = np.sum(it * ib) / (np.sqrt(np.sum(it * it)) * np.sqrt(np.sum(ib * ib)))
+    return curve
+
+
+@pytest.mark.parametrize("grid,win", [((1, 1), 0), ((2, 2), 3)])
+def test_ncc_curve_matches_svd_of_windowed_casorati(grid, win):
+    """The oracle's NCC curve (its Jacobi V, |C_w v_i| / sigma_i) against the same curve from
+    LAPACK's SVD of the windowed Casorati matrix (|u_i| directly), on random data."""
+    rng = np.random.default_rng(11)
+    nt, nz, nx = 16, 12, 10
+    iq = (rng.standard_normal((nt, nz, nx)) + 1j * rng.standard_normal((nt, nz, nx))).astype(np.complex64)
+    cfg = O.OracleConfig(nz, nx, nt, grid[0], grid[1], all_ones_window=int(grid == (1, 1)))
+    k, curve = O.ncc_curve(iq, cfg, win)
+    g = O.window_weights(cfg, win).ravel()
+    sup = g > 0
+    C = iq.reshape(nt, -1).T.astype(np.complex128)[sup] * g[sup, None]       # C_w on the support
+    U, sv, _ = np.linalg.svd(C, full_matrices=False)
+    ref = ncc_from_left_vectors(np.abs(U), 5)
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(curve))
+    np.testing.assert_allclose(curve[fin], ref[fin], rtol=1e-10)
+    assert k == int(np.nanargmin(ref)) + 1
+
+
+def test_ncc_disjoint_supports_pick_the_split():
+    """C = U D V^H whose first 9 left singular vectors live on one half of the image and the
+    other 15 on the other half: at k = 9 the tissue and blood images do not overlap, so NCC(9)
+    is 0 and every other cutoff mixes the halves (NCC > 0); methods 4 and 5 take k = 9."""
+    rng = np.random.default_rng(5)
+    nt, nz, nx, kst = 24, 12, 10, 9
+    npx = nz * nx
+
+    def orth(rows, cols):
+        a = rng.standard_normal((rows, cols)) + 1j * rng.standard_normal((rows, cols))
+        return np.linalg.qr(a)[0]
+    U = np.zeros((npx, nt), complex)
+    U[:npx // 2, :kst] = orth(npx // 2, kst)
+    U[npx // 2:, kst:] = orth(npx - npx // 2, nt - kst)
+    sv = 2.0 ** (np.arange(nt, 0, -1) / 4.0)     # distinct, within 2^6 (little complex64 rounding leak)
+    V = orth(nt, nt)
+    C = (U * sv) @ V.conj().T
+    iq = np.ascontiguousarray(C.T.reshape(nt, nz, nx)).astype(np.complex64)
+    cfg = O.OracleConfig(nz, nx, nt, 1, 1, all_ones_window=1)
+    k, curve = O.ncc_curve(iq, cfg, 0)
+    assert k == kst
+    assert curve[kst - 1] <= 1e-6   # zero up to the complex64 rounding of the packet
+    others = np.delete(curve, kst - 1)
+    assert np.nanmin(others) >= 0.05
+    r = O.filter(iq, O.OracleConfig(nz, nx, nt, 1, 1, all_ones_window=1, thresh_mode=O.T_NCC))
+    assert int(r.k[0]) == kst and np.all(r.wt[0][:kst] == 0) and np.all(r.wt[0][kst:] == 1)
+    r = O.filter(iq, O.OracleConfig(nz, nx, nt, 1, 1, all_ones_window=1, thresh_mode=O.T_SIGMOID,
+                                    k_src=O.T_NCC, beta=2.0))
+    assert int(r.k[0]) == kst
+    np.testing.assert_allclose(r.wt[0], 1.0 / (1.0 + np.exp(-2.0 * (np.arange(1, nt + 1) - kst))), rtol=1e-15)
+
+
+@pytest.mark.parametrize("nt,ks", [(10, [5]), (7, [3, 4]), (6, [3]), (2, [1])])
+def test_ncc_cutoff_range(nt, ks):
+    """fn = min(5, Nt/2) neighbours on each side: the curve exists exactly for fn <= k <= Nt - fn."""
+    rng = np.random.default_rng(nt)
+    iq = (rng.standard_normal((nt, 8, 6)) + 1j * rng.standard_normal((nt, 8, 6))).astype(np.complex64)
+    k, curve = O.ncc_curve(iq, O.OracleConfig(8, 6, nt, 1, 1, all_ones_window=1), 0)
+    assert [i + 1 for i in np.nonzero(np.isfinite(curve))[0]] == ks
+    assert k in ks
