@@ -69,10 +69,17 @@ enum {
                                k from rule k_src with factor beta_src             */
   LCF_T_ADAPTIVE_SOFT = 5,  /* method 6, Eq. 10: wt_i ~ win(i) / lambda_i^beta    */
   LCF_T_NONE = 6,           /* wt = 1 (identity reconstruction, for checks)       */
-  LCF_T_LEARNED = 7         /* hard cutoff k from the plan's learned rule (an MLP
+  LCF_T_LEARNED = 7,        /* hard cutoff k from the plan's learned rule (an MLP
                                set by lcf_plan_set_mlp; no counterpart in the
                                paper); below its confidence threshold the window
                                falls back to rule k_src with factor beta_src     */
+  LCF_T_NCC = 8             /* method 4, Eq. 8: the k (fn <= k <= Nt - fn, fn =
+                               min(5, Nt/2)) minimising the normalised spatial
+                               cross-correlation of the tissue image
+                               sum_{i=k-fn+1..k} |u_i| and the blood image
+                               sum_{i=k+1..k+fn} |u_i|, u_i = C_w v_i / sigma_i;
+                               also a k_src of LCF_T_SIGMOID (method 5 at
+                               method 4's k, as the paper evaluates it)          */
 };
 
 /* Status bits per window (lcf_plan_status). */
@@ -94,6 +101,35 @@ enum { LCF_PATH_SIMT = 0, LCF_PATH_TC = 1 };
  * other, which accumulates V.  Same arithmetic and tolerances. */
 enum { LCF_EVD_CTA = 0, LCF_EVD_PAIR = 1 };
 
+/* Product precision of the tensor-core Gram (gram_path = LCF_PATH_TC; the
+ * plain path's products are FP32).  Each weighted component of the deflated
+ * packet is scaled by a power of two and split into tensor-core words; the
+ * MMAs accumulate in FP32, promoted to double-float across chains.
+ *   LCF_GP_F16X3   fp16 hi + lo (22 significant bits); products hi*hi +
+ *                  hi*lo + lo*hi (default)
+ *   LCF_GP_BF16X3  bf16 hi + lo (16 bits); the same three products on bf16 MMAs
+ *   LCF_GP_F16     fp16 hi only (11 bits, TF32's significand; the scaled packet
+ *                  lies inside fp16's range, so every product equals the TF32
+ *                  product of the same operands), one MMA pass
+ *   LCF_GP_BF16    bf16 hi only (8 bits), one pass
+ *   LCF_GP_E4M3    FP8 E4M3 operands (4 bits, saturating at 448 after a
+ *                  power-of-two scale), one pass on the fp16 MMA, which holds
+ *                  E4M3 values and their products exactly: the precision study's
+ *                  FP8 case (not an FP8 MMA instruction). */
+enum { LCF_GP_F16X3 = 0, LCF_GP_BF16X3 = 1, LCF_GP_F16 = 2, LCF_GP_BF16 = 3, LCF_GP_E4M3 = 4 };
+
+/* Eigen-decomposition precision (Eq. 2 on every path).
+ *   LCF_EP_FP32        FP32 Jacobi rotations after a double-float congruence
+ *                      that isolates the dominant subspace (default)
+ *   LCF_EP_FP64_POLISH the same, then every eigenvalue is replaced by the
+ *                      Rayleigh quotient v^H R v / v^H v of its FP32 eigenvector
+ *                      against the FP64 Gram, formed in double-float; the
+ *                      eigenpairs are re-sorted and the rule, alpha (Eq. 13) and
+ *                      the projection weights use the polished values.  For
+ *                      packets whose kept eigenvalues lie near the FP32 unit
+ *                      roundoff of lambda_1 (60 dB tissue-to-blood, long packets). */
+enum { LCF_EP_FP32 = 0, LCF_EP_FP64_POLISH = 1 };
+
 typedef struct {
   int nz, nx, nt;          /* packet size: Nz axial x Nx lateral x Nt frames      */
   int wz, wx;              /* window grid; Nd = wz*wx subsets                     */
@@ -104,7 +140,8 @@ typedef struct {
   int thresh_mode;         /* LCF_T_*                                             */
   float beta;              /* the rule's scaling factor                           */
   int k_fixed;             /* k of LCF_T_FIXED (and of a FIXED k_src)             */
-  int k_src;               /* rule that supplies k to LCF_T_SIGMOID               */
+  int k_src;               /* rule that supplies k to LCF_T_SIGMOID (FIXED..MEDIAN
+                              or LCF_T_NCC)                                        */
   float beta_src;          /* scaling factor of that rule                         */
   int pd_mode;             /* 0: PD = mean over slow time, 1: sum                 */
   int alpha_mode;          /* 0: alpha_k = Nz*Nx / sum PD_k (Eq. 13, default);
@@ -120,11 +157,29 @@ typedef struct {
                            /* packet's basis prep starts on a plan-owned stream    */
                            /* while the previous packet's kernels run; 0 (default):*/
                            /* the input is read in `stream` order                  */
+  int gram_precision;      /* LCF_GP_* (tensor-core Gram only; 0 = LCF_GP_F16X3)  */
+  int evd_precision;       /* LCF_EP_* (0 = LCF_EP_FP32)                          */
+  int graph;               /* 1: lcf_filter runs each packet as one CUDA graph
+                              launch (captured on the first call with a given
+                              (d_iq, d_out_pd) pair, up to 16 pairs per plan;
+                              capturing allocates the graph); 0 (default): the
+                              stages are launched one by one.  Not combined
+                              with inputs_ready's early basis prep, nor used
+                              while stage profiling is on                        */
+  int deflate;             /* slow-time vectors deflated from every pixel before
+                              the Gram and projection products, 1..16 (< Nt);
+                              0: clamp(Nt/4, 1, 4).  The deflated part is summed
+                              with exact double-float products, so only the
+                              residual meets the FP32 / tensor-core products:
+                              strong tissue motion (a pixel or more) needs 8-16
+                              to bring the residual down to blood and noise     */
 } lcf_config;
 
 /* Fill *cfg with defaults for an nz x nx x nt packet and a wz x wx grid:
  * sigma_scale 1, support 3 SD, curvature rule beta 1, PD mean, alpha by
- * Eq. 13, tensor-core paths. */
+ * Eq. 13, the fast path: tensor-core Gram and projection (LCF_PATH_TC) and the
+ * cluster EVD (LCF_EVD_PAIR), 40-sweep cap.  The plain FP32 path is
+ * gram_path = project_path = LCF_PATH_SIMT with evd_path = LCF_EVD_CTA. */
 lcf_status lcf_config_default(lcf_config* cfg, int nz, int nx, int nt, int wz, int wx);
 
 /* Validate cfg, build the window geometry (Eq. 11) and allocate all device
@@ -232,26 +287,67 @@ lcf_status lcf_plan_profile_read(lcf_plan* plan, double* ms, int* n_calls);
  * plan's last stream.  LCF_EINVAL if profiling was never enabled. */
 lcf_status lcf_plan_evd_phases(lcf_plan* plan, double* cycles);
 
+/* ---- launch tuning (no counterpart in the paper) ----
+ * How a plan spreads its work over the GPU: pixel splits of the Gram stages
+ * (more splits = more CTAs and more partial sums to add) and the cluster size
+ * of the distributed EVD.  The values change the order of some FP32 partial
+ * sums, not the method; every value is within the library's tolerances. */
+typedef struct {
+  int gram_splits;       /* pixel ranges per window of the one-tile tensor-core Gram */
+  int simt_gram_splits;  /* pixel splits per window of the CUDA-core residual Gram  */
+  int aug_splits;        /* pixel splits of the CUDA-core coefficient columns (U, Q) */
+  int q_splits;          /* pixel splits of the exact coefficient block (depth <= 4) */
+  int basis_splits;      /* pixel splits of the global Gram behind the deflation basis */
+  int ncc_splits;        /* pixel splits of method 4's band sums                      */
+  int evd_cluster;       /* CTAs per window of the distributed EVD (Nt > 128): 4
+                            (Nt <= 224 only) or 8                                    */
+} lcf_tuning;
+
+/* The plan's current tuning (host struct).  No synchronisation. */
+lcf_status lcf_plan_get_tuning(const lcf_plan* plan, lcf_tuning* t);
+
+/* Apply a tuning: splits in 1..64, evd_cluster 4 or 8.  Synchronous (waits for
+ * the plan's work, reallocates the partial-sum buffers, drops captured graphs);
+ * LCF_EINVAL for values out of range, LCF_ENOMEM. */
+lcf_status lcf_plan_set_tuning(lcf_plan* plan, const lcf_tuning* t);
+
+/* Autotune the plan's launch shapes on one packet (d_iq on the plan's device,
+ * read only): each tunable in turn takes the candidate with the shortest packet
+ * time (CUDA events on `stream`, best of three after a warm-up), the others held.
+ * cache_path (may be NULL): a text file of earlier results, one line per
+ * (GPU name, packet and window sizes, paths, precisions, deflation depth, rule
+ * family); a line for this plan's key is applied without timing and
+ * *from_cache (may be NULL) set to 1, else the result is appended.  Synchronous;
+ * allocates (it is a setup call, like lcf_plan_create). */
+lcf_status lcf_plan_autotune(lcf_plan* plan, const void* d_iq, cudaStream_t stream, const char* cache_path,
+                             int* from_cache);
+
 /* Windowed Gram matrices of one packet without any allocation.  The paper
  * has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc (real-time threads that must not wait on the allocator, hosts
  * that own all device memory, fixed-budget embedded pipelines).
  *
- * Computes R_k = C_w^H C_w for every window of cfg on the CURRENT device,
- * with the same arithmetic as the plain path's Gram stage.  d_iq: device
+ * Computes R_k = C_w^H C_w for every window of cfg on the CURRENT device with
+ * the plain path's Gram kernels (FP32 products, double-float promotion),
+ * deflating the packet with a fixed orthonormal DCT-II slow-time basis
+ * instead of a plan's data-derived one; the deflation identity is exact for
+ * any basis, so R_k agrees with a plan's Gram (and the FP64 oracle) within the
+ * library's Gram tolerance (relative Frobenius error 1e-6), not bit for bit.
+ * cfg's path, rule and precision fields are ignored.  d_iq: device
  * iq[nt][nz][nx] complex64 (8-byte aligned); d_R: device output [Nd][Nt][Nt]
- * complex double (16-byte aligned), fully written.  Asynchronous on
- * `stream`; calls no allocator of any kind.
+ * complex double (16-byte aligned), fully written.  Asynchronous on `stream`;
+ * calls no allocator of any kind.
  *
  * Scratch: one file-scope static device array of
  * lcf_gram_noalloc_scratch_bytes() bytes (64 MiB) that every GPU loading
  * the library holds until the process exits.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress) and caches
- * it; make that first call before any stream capture.  Calls share the
- * array: calls that overlap on the GPU race.  Returns LCF_ESCRATCH when the
- * window tables, the centred packet and one partial Gram per window do not
- * fit (e.g. 256 x 128 x 100 with 8 x 8 windows fits; 512 x 256 x 100 does
- * not), LCF_EINVAL for bad arguments, LCF_EUNSUPPORTED for nt > 112. */
+ * looks up that array's device address (cudaGetSymbolAddress) and caches it
+ * (safe from several host threads); make that first call before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race.
+ * Returns LCF_ESCRATCH when the window tables, the centred packet and one
+ * partial Gram per window do not fit (e.g. 256 x 128 x 100 with 8 x 8
+ * windows fits; 512 x 256 x 100 does not), LCF_EINVAL for bad arguments,
+ * LCF_EUNSUPPORTED for nt > 320 or nz*nx*(nt+4) > 2^31. */
 lcf_status lcf_gram_noalloc(const lcf_config* cfg, const void* d_iq, void* d_R, cudaStream_t stream);
 
 /* Size in bytes of lcf_gram_noalloc's static per-device scratch. */
@@ -304,6 +400,13 @@ lcf_status lcf_mlp_destroy(lcf_mlp* mlp);
  * LCF_ENOCONV by design.  Requires mlp's Nt = the plan's Nt and the CTA-pair EVD.
  * Synchronous. */
 lcf_status lcf_plan_set_mlp(lcf_plan* plan, const lcf_mlp* mlp, float p_min);
+
+/* The learned rule's network input and output of every window of the last
+ * LCF_T_LEARNED filter call (for validation; synchronises): features [Nd][Nt+2]
+ * (the normalised log-spectrum computed in the EVD kernel, then the window
+ * centre) and logits [Nd][Nt], host, either may be NULL.  LCF_EINVAL if no
+ * network was set. */
+lcf_status lcf_debug_learned(lcf_plan* plan, float* features, float* logits);
 
 /* Self-test of the device-side failure path (no counterpart in the paper):
  * one CTA waits on an mbarrier phase that nothing completes, with the bounded

@@ -20,10 +20,12 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
 (LCF_OK, LCF_EINVAL, LCF_ENOMEM, LCF_ECUDA, LCF_ENOCONV, LCF_ETIMEOUT, LCF_EDEGENERATE, LCF_EUNSUPPORTED,
  LCF_ESCRATCH) = range(9)
 (LCF_T_FIXED, LCF_T_CURVATURE, LCF_T_SLOPE, LCF_T_MEDIAN, LCF_T_SIGMOID, LCF_T_ADAPTIVE_SOFT,
- LCF_T_NONE, LCF_T_LEARNED) = range(8)
+ LCF_T_NONE, LCF_T_LEARNED, LCF_T_NCC) = range(9)
 LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE, LCF_WFLAG_FALLBACK, LCF_WFLAG_SWEEP_SHIFT = 1, 2, 4, 8
 LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
 LCF_EVD_CTA, LCF_EVD_PAIR = 0, 1
+LCF_GP_F16X3, LCF_GP_BF16X3, LCF_GP_F16, LCF_GP_BF16, LCF_GP_E4M3 = range(5)
+LCF_EP_FP32, LCF_EP_FP64_POLISH = 0, 1
 STAGES = ("prep", "gram", "assemble", "evd", "project")
 EVD_PHASES = ("subspace", "qr", "congruence", "convert_q", "jacobi", "sort_phase", "rule", "weights")
 
@@ -35,7 +37,18 @@ class lcf_config(C.Structure):
                 ("k_fixed", C.c_int), ("k_src", C.c_int), ("beta_src", C.c_float),
                 ("pd_mode", C.c_int), ("alpha_mode", C.c_int), ("curv_norm", C.c_int),
                 ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int),
-                ("evd_path", C.c_int), ("inputs_ready", C.c_int)]
+                ("evd_path", C.c_int), ("inputs_ready", C.c_int),
+                ("gram_precision", C.c_int), ("evd_precision", C.c_int), ("graph", C.c_int),
+                ("deflate", C.c_int)]
+
+
+class lcf_tuning(C.Structure):
+    _fields_ = [("gram_splits", C.c_int), ("simt_gram_splits", C.c_int), ("aug_splits", C.c_int),
+                ("q_splits", C.c_int), ("basis_splits", C.c_int), ("ncc_splits", C.c_int),
+                ("evd_cluster", C.c_int)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
 class LcfError(RuntimeError):
@@ -82,6 +95,10 @@ def _load():
         "lcf_mlp_adamw": ([vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, vp], C.c_int),
         "lcf_mlp_destroy": ([vp], C.c_int),
         "lcf_plan_set_mlp": ([vp, vp, C.c_float], C.c_int),
+        "lcf_debug_learned": ([vp, fp, fp], C.c_int),
+        "lcf_plan_get_tuning": ([vp, C.POINTER(lcf_tuning)], C.c_int),
+        "lcf_plan_set_tuning": ([vp, C.POINTER(lcf_tuning)], C.c_int),
+        "lcf_plan_autotune": ([vp, vp, vp, C.c_char_p, ip], C.c_int),
         "lcf_selftest_wait_timeout": ([C.c_int, C.c_ulonglong, dp], C.c_int),
     }
     for name, (args, res) in sigs.items():
@@ -195,6 +212,32 @@ class Plan:
         """Give the plan the learned cutoff rule (used when thresh_mode == LCF_T_LEARNED)."""
         _check(_lib.lcf_plan_set_mlp(self.handle, mlp.handle, float(p_min)), "lcf_plan_set_mlp")
 
+    def tuning(self) -> lcf_tuning:
+        """The plan's launch tuning (lcf_plan_get_tuning)."""
+        t = lcf_tuning()
+        _check(_lib.lcf_plan_get_tuning(self.handle, C.byref(t)), "lcf_plan_get_tuning")
+        return t
+
+    def set_tuning(self, **kw):
+        """Change some tunables (lcf_plan_set_tuning); returns the new tuning."""
+        t = self.tuning()
+        for k, v in kw.items():
+            if not hasattr(t, k):
+                raise AttributeError(k)
+            setattr(t, k, int(v))
+        _check(_lib.lcf_plan_set_tuning(self.handle, C.byref(t)), "lcf_plan_set_tuning")
+        return t
+
+    def autotune(self, iq, cache_path=None, stream=None) -> bool:
+        """Autotune the launch shapes on one packet (lcf_plan_autotune); True if the result
+        came from the cache file."""
+        import torch
+        st = (stream or torch.cuda.current_stream(iq.device)).cuda_stream
+        hit = C.c_int()
+        path = None if cache_path is None else str(cache_path).encode()
+        _check(_lib.lcf_plan_autotune(self.handle, iq.data_ptr(), st, path, C.byref(hit)), "lcf_plan_autotune")
+        return bool(hit.value)
+
     def launch_count(self) -> int:
         """Kernels this plan has launched since it was created."""
         n = C.c_longlong()
@@ -284,6 +327,14 @@ class Plan:
         _check(_lib.lcf_debug_dump(self.handle, _p(lam, C.c_double), _p(wt, C.c_float), _p(k, C.c_int),
                                    _p(al, C.c_float)), "lcf_debug_dump")
         return {"lam": lam, "wt": wt, "k": k, "alpha": al}
+
+    def debug_learned(self):
+        """(features [nd, nt+2], logits [nd, nt]) of the learned rule in the last call."""
+        nd, nt = self.nd, self.cfg.nt
+        f = np.zeros((nd, nt + 2), np.float32)
+        z = np.zeros((nd, nt), np.float32)
+        _check(_lib.lcf_debug_learned(self.handle, _p(f, C.c_float), _p(z, C.c_float)), "lcf_debug_learned")
+        return f, z
 
     def debug_gram(self):
         nd, nt = self.nd, self.cfg.nt

@@ -324,7 +324,7 @@ __host__ __device__ inline EdLayout ed_layout(int n, int C) {
   L.end = o;
   return L;
 }
-size_t evd_dist_smem_bytes(int nt) { return ed_layout(nt, evd_dist_cluster(nt)).end; }
+size_t evd_dist_smem_bytes(int nt, int C) { return ed_layout(nt, C).end; }
 
 __device__ __forceinline__ void ed_st_remote4(uint32_t addr, float4 v) {
   asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
@@ -777,11 +777,11 @@ cudaError_t launch_evd_dist(const lcf_plan* P, cudaStream_t st) {
   a.k_fixed = c.k_fixed; a.k_src = c.k_src; a.pd_mode = c.pd_mode; a.alpha_mode = c.alpha_mode;
   a.curv_norm = c.curv_norm; a.max_sweeps = c.max_sweeps; a.ncp = P->ncp;
   a.err = P->ws.err;
-  const int C = evd_dist_cluster(P->nt);
+  const int C = P->evd_cluster > 0 ? P->evd_cluster : evd_dist_cluster(P->nt);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C * P->nd);
   cfg.blockDim = dim3(ED_THREADS);
-  cfg.dynamicSmemBytes = evd_dist_smem_bytes(P->nt);
+  cfg.dynamicSmemBytes = evd_dist_smem_bytes(P->nt, C);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -801,7 +801,8 @@ cudaError_t evd_dist_configure() {
   cudaError_t e = cudaFuncSetAttribute(evd_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)evd_prep_smem_bytes(kEvdNmax));
   size_t mx = 0;
-  for (int nt = kEvdPairNmax + 1; nt <= kEvdNmax; ++nt) mx = evd_dist_smem_bytes(nt) > mx ? evd_dist_smem_bytes(nt) : mx;
+  for (int nt = kEvdPairNmax + 1; nt <= kEvdNmax; ++nt)   // both cluster sizes where they fit
+    for (int C = evd_dist_cluster(nt); C <= 8; C += 4) mx = evd_dist_smem_bytes(nt, C) > mx ? evd_dist_smem_bytes(nt, C) : mx;
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(evd_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
   return e;

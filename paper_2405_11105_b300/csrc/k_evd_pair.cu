@@ -54,6 +54,7 @@ struct EpArgs {
   const float* mlp_b;               //               b1 | b2 | b3 | b4
   int mlp_h;                        // hidden width
   float mlp_pmin;                   // confidence threshold
+  float* mlp_dbg;                   // [nd][2 nt + 2]: features, then logits (or null)
 };
 
 #define EP_STAMP(b)                                                                  \
@@ -836,6 +837,11 @@ evd_pair_kernel(const double2* __restrict__ Rg, const Box* __restrict__ boxes, E
       __syncthreads();
       ep_dense(h1, H, W4, g.mlp_b + 3 * H, h2, n, false, warp, lane, EP_THREADS / 32);
       __syncthreads();
+      if (g.mlp_dbg) {   // the window's network input and logits, for validation
+        float* dbo = g.mlp_dbg + (size_t)k * (2 * n + 2);
+        for (int i = tid; i < n + 2; i += EP_THREADS) dbo[i] = xin[i];
+        for (int i = tid; i < n; i += EP_THREADS) dbo[n + 2 + i] = h2[i];
+      }
       if (warp == 0) {   // argmax (first index on ties) and its softmax probability
         float mx = -INFINITY;
         int bi = 0x7fffffff;
@@ -1093,6 +1099,7 @@ cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st) {
   a.clk = P->profiling ? P->ws.evd_clk : nullptr;
   a.wz = c.wz; a.wx = c.wx;
   a.mlp_w = P->ws.mlp_w; a.mlp_b = P->ws.mlp_b; a.mlp_h = P->mlp_hidden; a.mlp_pmin = P->mlp_pmin;
+  a.mlp_dbg = P->ws.mlp_dbg;
   evd_pair_kernel<<<2 * P->nd, EP_THREADS, evd_pair_smem_bytes(P->nt), st>>>(
       P->ws.R, P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt, P->ws.kcut, P->ws.alpha, P->ws.flags, P->ws.W,
       P->ws.ncol);

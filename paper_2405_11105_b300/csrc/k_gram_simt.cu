@@ -2,7 +2,7 @@
 // Gram R_k = C_w^H C_w = sum_p g_k(p)^2 s_p^H s_p  (Eq. 1, Eq. 12).
 //
 // Numerics.  Each pixel row is split as s_p = c_p + sum_j a_pj phi_j^T, where
-// phi_j (j < d, d <= 4) is the per-packet slow-time basis of k_basis.cu (the
+// phi_j (j < d, d <= 16) is the per-packet slow-time basis of k_basis.cu (the
 // dominant global tissue modes) and a_pj = sum_t conj(phi_j(t)) s_p(t).  With
 // the augmented row x_p = [c_p, a_p] (Nt + d entries) and R' = sum_p g^2 x_p^H x_p,
 //   R = E^H R' E,  E = [I_Nt ; Phi^T]
@@ -24,22 +24,23 @@ namespace lcf {
 // A CTA is 64 pixels x 4 slow-time phases (t = sub mod 4, one phase per pair of
 // warps): a warp reads 32 consecutive pixels of one frame, and four times as many
 // loads are in flight as with one thread per pixel.
-__global__ void __launch_bounds__(256)
-center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, float2* __restrict__ xa, int nt,
-              int nd_defl, int npix, unsigned* xmax_bits) {
-  __shared__ float2 red[4][kDeflateMax][64];
+// DM: the largest deflation depth the instance handles (4 or kDeflateMax); nd_defl <= DM.
+template <int DM>
+__device__ __forceinline__ void center_body(const float2* __restrict__ iq, const float2* __restrict__ phi, float2* __restrict__ xa, int nt,
+                int nd_defl, int npix, unsigned* xmax_bits) {
+  __shared__ float2 red[4][DM][64];
   const int pix = threadIdx.x & 63, sub = threadIdx.x >> 6;
   const int p = blockIdx.x * 64 + pix;
   const bool valid = p < npix;
-  float2 a[kDeflateMax];
+  float2 a[DM];
 #pragma unroll
-  for (int j = 0; j < kDeflateMax; ++j) a[j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < DM; ++j) a[j] = make_float2(0.f, 0.f);
   if (valid) {
 #pragma unroll 4
     for (int t = sub; t < nt; t += 4) {
       const float2 v = iq[(size_t)t * npix + p];
 #pragma unroll
-      for (int j = 0; j < kDeflateMax; ++j)
+      for (int j = 0; j < DM; ++j)
         if (j < nd_defl) {
           const float2 f = phi[j * nt + t];   // a_j += conj(phi_j(t)) s(t)
           a[j].x = fmaf(f.x, v.x, fmaf(f.y, v.y, a[j].x));
@@ -48,10 +49,10 @@ center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, flo
     }
   }
 #pragma unroll
-  for (int j = 0; j < kDeflateMax; ++j) red[sub][j][pix] = a[j];
+  for (int j = 0; j < DM; ++j) red[sub][j][pix] = a[j];
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < kDeflateMax; ++j)
+  for (int j = 0; j < DM; ++j)
     a[j] = cadd(cadd(red[0][j][pix], red[1][j][pix]), cadd(red[2][j][pix], red[3][j][pix]));
   float mx = 0.f;
   if (valid) {
@@ -59,7 +60,7 @@ center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, flo
     for (int t = sub; t < nt; t += 4) {
       float2 v = iq[(size_t)t * npix + p];
 #pragma unroll
-      for (int j = 0; j < kDeflateMax; ++j)
+      for (int j = 0; j < DM; ++j)
         if (j < nd_defl) {
           const float2 f = phi[j * nt + t];   // c(t) = s(t) - a_j phi_j(t)
           v.x = fmaf(-a[j].x, f.x, fmaf(a[j].y, f.y, v.x));
@@ -68,11 +69,13 @@ center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, flo
       xa[(size_t)t * npix + p] = v;
       mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
-    if (sub < nd_defl) {
-      const float2 c = a[sub];
-      xa[(size_t)(nt + sub) * npix + p] = c;
-      mx = fmaxf(mx, fmaxf(fabsf(c.x), fabsf(c.y)));
-    }
+#pragma unroll
+    for (int j = 0; j < DM; j += 4)   // coefficient rows sub, sub + 4, ...
+      if (j + sub < nd_defl) {
+        const float2 c = a[j + sub];
+        xa[(size_t)(nt + j + sub) * npix + p] = c;
+        mx = fmaxf(mx, fmaxf(fabsf(c.x), fabsf(c.y)));
+      }
   }
   if (xmax_bits) {
     const unsigned m = __reduce_max_sync(~0u, __float_as_uint(mx));
@@ -80,13 +83,30 @@ center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, flo
   }
 }
 
+template <int DM>
+__global__ void __launch_bounds__(256)
+center_kernel_t(const float2* __restrict__ iq, const float2* __restrict__ phi, float2* __restrict__ xa, int nt,
+                int nd_defl, int npix, unsigned* xmax_bits) {
+  center_body<DM>(iq, phi, xa, nt, nd_defl, npix, xmax_bits);
+}
+
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st) {
   int n = P->npix;
   // the basis kernel, launched before this one, has zeroed the packet maximum
   const bool tc = P->cfg.gram_path == LCF_PATH_TC || P->cfg.project_path == LCF_PATH_TC;
   unsigned* xm = tc ? P->ws.xmax : nullptr;
-  center_kernel<<<(n + 63) / 64, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
+  if (P->ndefl <= 4)
+    center_kernel_t<4><<<(n + 63) / 64, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
+  else
+    center_kernel_t<kDeflateMax><<<(n + 63) / 64, 256, 0, st>>>(iq, P->ws.phi, P->ws.xa, P->nt, P->ndefl, n, xm);
   return counted(P);
+}
+
+// the depth-4 instance under a plain name, for the allocation-free entry point (default depths)
+__global__ void __launch_bounds__(256)
+center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi, float2* __restrict__ xa, int nt,
+              int nd_defl, int npix, unsigned* xmax_bits) {
+  center_body<4>(iq, phi, xa, nt, nd_defl, npix, xmax_bits);
 }
 
 constexpr int GT = 64;   // Gram tile (complex entries per side)
@@ -296,9 +316,16 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
 size_t gram_aug_smem_bytes(int nt, int nd_defl) { return (size_t)ACH * (nt + nd_defl) * sizeof(float2); }
 
 // the augmented-column kernel's staging passes 48 KB beyond Nt = 188
+size_t gram_assemble_smem_bytes(int nt, int nd_defl);
+__global__ void gram_assemble_kernel(const double2* __restrict__ part, const double2* __restrict__ aug,
+                                     const float2* __restrict__ phi, int nsplit, int aug_nsplit, int nt,
+                                     int nd_defl, double2* __restrict__ R);
 cudaError_t gram_simt_configure() {
-  return cudaFuncSetAttribute(gram_aug_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
+  cudaError_t e = cudaFuncSetAttribute(gram_aug_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(gram_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gram_assemble_smem_bytes(kEvdNmax, kDeflateMax));
 }
 
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st, bool with_q) {
@@ -330,9 +357,11 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
   const int na = nt + nd_defl, nout = na * nd_defl;
   const double2* pk = part + (size_t)k * nsplit * nt * nt;
   const double2* ak = aug + (size_t)k * aug_nsplit * nout;
-  __shared__ double2 U[kEvdNmax][kDeflateMax];
-  __shared__ double2 Q[kDeflateMax][kDeflateMax];
-  __shared__ double2 ph[kDeflateMax][kEvdNmax];
+  extern __shared__ double2 asm_dyn[];   // U [nt][kDeflateMax], Q [kDeflateMax]^2, ph [d][kEvdNmax]
+  double2 (*U)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn);
+  double2 (*Q)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn + (size_t)nt * kDeflateMax);
+  double2 (*ph)[kEvdNmax] =
+      reinterpret_cast<double2 (*)[kEvdNmax]>(asm_dyn + (size_t)(nt + kDeflateMax) * kDeflateMax);
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     double sx = 0.0, sy = 0.0;
     for (int s = 0; s < aug_nsplit; ++s) {
@@ -361,7 +390,7 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
   __syncthreads();
   constexpr int WPT = (kEvdNmax * kDeflateMax + 255) / 256;   // W entries per thread (blockDim 256)
   double2 wv[WPT];
-  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 512)
+  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q
     int e = threadIdx.x + u * blockDim.x;
     if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
   }
@@ -380,9 +409,14 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
   }
 }
 
+// U (nt rows), Q and the basis (d rows) in double precision: the assembly kernels' shared memory
+size_t gram_assemble_smem_bytes(int nt, int nd_defl) {
+  return ((size_t)(nt + kDeflateMax) * kDeflateMax + (size_t)nd_defl * kEvdNmax) * sizeof(double2);
+}
+
 cudaError_t launch_gram_assemble(const lcf_plan* P, cudaStream_t st) {
   dim3 grid((P->nt * P->nt + 255) / 256 < 8 ? (P->nt * P->nt + 255) / 256 : 8, P->nd);
-  gram_assemble_kernel<<<grid, 256, 0, st>>>(P->ws.gpart, P->ws.gaug, P->ws.phi, P->gram_nsplit, P->aug_nsplit,
+  gram_assemble_kernel<<<grid, 256, gram_assemble_smem_bytes(P->nt, P->ndefl), st>>>(P->ws.gpart, P->ws.gaug, P->ws.phi, P->gram_nsplit, P->aug_nsplit,
                                               P->nt, P->ndefl, P->ws.R);
   return counted(P);
 }

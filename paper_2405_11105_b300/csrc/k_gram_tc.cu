@@ -25,6 +25,11 @@
 // ranges in double by gram_tc_reduce_kernel.
 // The d x d coefficient block (largest entries) comes from gram_q_kernel with
 // exact double-float products instead.
+//
+// Both Gram kernels are templates on the product precision (LCF_GP_*): the
+// split above is LCF_GP_F16X3; LCF_GP_BF16X3 splits into bf16 halves (bf16
+// MMAs); the one-pass modes keep the hi words only (fp16, bf16, or E4M3 values
+// held in fp16) and issue only the A B_hi^T MMAs.
 #include <math.h>
 
 #include <cudaTypedefs.h>
@@ -110,6 +115,7 @@ __device__ __forceinline__ void tc_bar_producers() { asm volatile("bar.sync 1, %
 // 16-column blocks w / 4, w / 4 + 4, ... of TMEM lane quarter w mod 4.
 constexpr uint32_t TW_SUMS = 256;
 
+template <int GP>
 __global__ void __launch_bounds__(TW_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float2* __restrict__ xa, int nz, int nx,
                int na, const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
@@ -168,7 +174,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
     // ---- MMA warp: D' = A B_hi^T + A (2 B_lo)^T per stage, chains of TG_CPA stages.  The whole
     // warp runs the loop (warp-uniform counters and descriptors); one elected lane issues.
     {
-      const uint32_t idesc = tc::idesc_f16(128, N);
+      const uint32_t idesc = tc::gp_bf16(GP) ? tc::idesc_bf16(128, N) : tc::idesc_f16(128, N);
       const uint32_t sb = tc::smem_u32(smem);
       const uint64_t dh0 = tc::smem_desc(sb, 128, TG_SBO), dl0 = tc::smem_desc(sb + (uint32_t)hi_bytes, 128, TG_SBO);
       bool ok = true;
@@ -186,7 +192,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
           for (int ks = 0; ks < TG_K / 16; ++ks) {
             const uint64_t ad = dh0 + so + (uint64_t)(16 * ks), ld = dl0 + so + (uint64_t)(16 * ks);
             tc::mma_f16(tbase, ad, ad, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
-            tc::mma_f16(tbase, ad, ld, idesc, 1u);
+            if constexpr (tc::gp_three_products(GP)) tc::mma_f16(tbase, ad, ld, idesc, 1u);
           }
           tc::mma_commit(&empty_bar[si]);
           if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar);
@@ -317,15 +323,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
           const int j = 2 * jj + jh;
           if (rl + 16 * j < na) {
             const float4 v = *reinterpret_cast<const float4*>(src + j * 16 * TW_ROWB);
-            __half2 h[2], l[2], w[2];
-            tc::split2_f16(make_float2(v.x, v.y), gg0, gd0, h[0], l[0]);
-            tc::split2_f16(make_float2(v.z, v.w), gg1, gd1, h[1], l[1]);
-            *reinterpret_cast<uint2*>(Bhi + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(h);
-            w[0] = tc::neg_i(h[0]); w[1] = tc::neg_i(h[1]);
-            *reinterpret_cast<uint2*>(Bhi + sneg + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(w);
-            *reinterpret_cast<uint2*>(Blo + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(l);
-            w[0] = tc::neg_i(l[0]); w[1] = tc::neg_i(l[1]);
-            *reinterpret_cast<uint2*>(Blo + sneg + j * 2 * TG_SBO) = *reinterpret_cast<const uint2*>(w);
+            uint32_t h0, h1, l0 = 0u, l1 = 0u;
+            tc::split2_gp<GP>(make_float2(v.x, v.y), gg0, gd0, h0, l0);
+            tc::split2_gp<GP>(make_float2(v.z, v.w), gg1, gd1, h1, l1);
+            *reinterpret_cast<uint2*>(Bhi + j * 2 * TG_SBO) = make_uint2(h0, h1);
+            *reinterpret_cast<uint2*>(Bhi + sneg + j * 2 * TG_SBO) = make_uint2(tc::neg_i_raw(h0), tc::neg_i_raw(h1));
+            if constexpr (tc::gp_three_products(GP)) {
+              *reinterpret_cast<uint2*>(Blo + j * 2 * TG_SBO) = make_uint2(l0, l1);
+              *reinterpret_cast<uint2*>(Blo + sneg + j * 2 * TG_SBO) = make_uint2(tc::neg_i_raw(l0), tc::neg_i_raw(l1));
+            }
           }
         }
       }
@@ -402,6 +408,7 @@ size_t gram_tcb_smem_bytes(int tb) {
   return 1024 + TB_STAGES * (a > b ? a : b);
 }
 
+template <int GP>
 __global__ void __launch_bounds__(TG_THREADS, 1)
 gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, int T, const Box* __restrict__ boxes,
                 const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
@@ -444,7 +451,7 @@ gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, i
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t idesc = tc::idesc_f16(128, N);
+  const uint32_t idesc = tc::gp_bf16(GP) ? tc::idesc_bf16(128, N) : tc::idesc_f16(128, N);
 
   float sums[TG_NBH_MAX];
 #pragma unroll
@@ -502,23 +509,23 @@ gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, i
       const float2 gd0 = make_float2(2.f * g0, 2.f * g0), gd1 = make_float2(2.f * g1, 2.f * g1);
       for (int r = rl; r < rnb; r += 16) {
         const float2* src = xa + (size_t)(rb0 + r) * npix;
-        __half2 hh[2], ll[2], w[2];
-        tc::split2_f16(src[p0], gg0, gd0, hh[0], ll[0]);
-        tc::split2_f16(src[p1], gg1, gd1, hh[1], ll[1]);
-        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(hh);
-        w[0] = tc::neg_i(hh[0]); w[1] = tc::neg_i(hh[1]);
-        *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
-        *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(ll);
-        w[0] = tc::neg_i(ll[0]); w[1] = tc::neg_i(ll[1]);
-        *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(w);
+        uint32_t h0, h1, l0 = 0u, l1 = 0u;
+        tc::split2_gp<GP>(src[p0], gg0, gd0, h0, l0);
+        tc::split2_gp<GP>(src[p1], gg1, gd1, h1, l1);
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(r, kk, TG_SBO)) = make_uint2(h0, h1);
+        *reinterpret_cast<uint2*>(Bhi + tc::op_off(nbh + r, kk, TG_SBO)) =
+            make_uint2(tc::neg_i_raw(h0), tc::neg_i_raw(h1));
+        if constexpr (tc::gp_three_products(GP)) {
+          *reinterpret_cast<uint2*>(Blo + tc::op_off(r, kk, TG_SBO)) = make_uint2(l0, l1);
+          *reinterpret_cast<uint2*>(Blo + tc::op_off(nbh + r, kk, TG_SBO)) =
+              make_uint2(tc::neg_i_raw(l0), tc::neg_i_raw(l1));
+        }
       }
       if (!same) {
         for (int r = rl; r < rna; r += 16) {
           const float2* src = xa + (size_t)(ra0 + r) * npix;
-          __half2 hh[2];
-          hh[0] = __float22half2_rn(__fmul2_rn(src[p0], gg0));
-          hh[1] = __float22half2_rn(__fmul2_rn(src[p1], gg1));
-          *reinterpret_cast<uint2*>(Ahi + tc::op_off(r, kk, TG_SBO)) = *reinterpret_cast<const uint2*>(hh);
+          *reinterpret_cast<uint2*>(Ahi + tc::op_off(r, kk, TG_SBO)) =
+              make_uint2(tc::hi2_gp<GP>(src[p0], gg0), tc::hi2_gp<GP>(src[p1], gg1));
         }
       }
     }
@@ -535,7 +542,7 @@ gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, i
         const uint64_t hd = tc::smem_desc(bh + ks * 256, 128, TG_SBO);
         const uint64_t ld = tc::smem_desc(bl + ks * 256, 128, TG_SBO);
         tc::mma_f16(d, ad, hd, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
-        tc::mma_f16(d, ad, ld, idesc, 1u);
+        if constexpr (tc::gp_three_products(GP)) tc::mma_f16(d, ad, ld, idesc, 1u);
       }
       tc::mma_commit(&mma_bar[si]);
       if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar[c & 1]);
@@ -568,33 +575,33 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
   const long Pk = (long)(b.z1 - b.z0) * W;
   const long l0 = Pk * s / nsplit, l1 = Pk * (s + 1) / nsplit;
   const size_t npix = (size_t)nz * nx;
-  df qr[kDeflateMax * kDeflateMax], qi[kDeflateMax * kDeflateMax];
+  df qr[kQExactMax * kQExactMax], qi[kQExactMax * kQExactMax];
 #pragma unroll
-  for (int e = 0; e < kDeflateMax * kDeflateMax; ++e) { qr[e] = {0.f, 0.f}; qi[e] = {0.f, 0.f}; }
+  for (int e = 0; e < kQExactMax * kQExactMax; ++e) { qr[e] = {0.f, 0.f}; qi[e] = {0.f, 0.f}; }
   for (long l = l0 + tid; l < l1; l += blockDim.x) {
     const int zr = (int)l / W, z = b.z0 + zr, x = b.x0 + (int)l - zr * W;   // box pixel counts are below 2^31
     const size_t p = (size_t)z * nx + x;
     float g = gz[(size_t)k * nz + z] * gx[(size_t)k * nx + x];
     float g2 = g * g;
-    float2 a[kDeflateMax];
+    float2 a[kQExactMax];
 #pragma unroll
-    for (int j = 0; j < kDeflateMax; ++j) a[j] = j < nd_defl ? xa[(size_t)(nt + j) * npix + p] : make_float2(0.f, 0.f);
+    for (int j = 0; j < kQExactMax; ++j) a[j] = j < nd_defl ? xa[(size_t)(nt + j) * npix + p] : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < kDeflateMax; ++i)
+    for (int i = 0; i < kQExactMax; ++i)
 #pragma unroll
-      for (int j = 0; j < kDeflateMax; ++j) {
+      for (int j = 0; j < kQExactMax; ++j) {
         if (i >= nd_defl || j >= nd_defl) continue;
         df wr = two_prod_df(g2, a[i].x), wi = two_prod_df(-g2, a[i].y);   // g^2 conj(a_i)
         df rr = df_mul_f(wr, a[j].x), ii = df_mul_f(wi, a[j].y);
         df ri = df_mul_f(wr, a[j].y), ir = df_mul_f(wi, a[j].x);
-        qr[i * kDeflateMax + j] = df_add(qr[i * kDeflateMax + j], df_add(rr, df_neg(ii)));
-        qi[i * kDeflateMax + j] = df_add(qi[i * kDeflateMax + j], df_add(ri, ir));
+        qr[i * kQExactMax + j] = df_add(qr[i * kQExactMax + j], df_add(rr, df_neg(ii)));
+        qi[i * kQExactMax + j] = df_add(qi[i * kQExactMax + j], df_add(ri, ir));
       }
   }
   // block reduction in double-float
-  __shared__ df red_r[8][kDeflateMax * kDeflateMax], red_i[8][kDeflateMax * kDeflateMax];
+  __shared__ df red_r[8][kQExactMax * kQExactMax], red_i[8][kQExactMax * kQExactMax];
 #pragma unroll
-  for (int e = 0; e < kDeflateMax * kDeflateMax; ++e) {
+  for (int e = 0; e < kQExactMax * kQExactMax; ++e) {
     df vr = qr[e], vi = qi[e];
     for (int o = 16; o; o >>= 1) {
       df tr = {__shfl_xor_sync(~0u, vr.hi, o), __shfl_xor_sync(~0u, vr.lo, o)};
@@ -605,10 +612,10 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
     if ((tid & 31) == 0) { red_r[tid >> 5][e] = vr; red_i[tid >> 5][e] = vi; }
   }
   __syncthreads();
-  if (tid < kDeflateMax * kDeflateMax) {
+  if (tid < kQExactMax * kQExactMax) {
     df vr = {0.f, 0.f}, vi = {0.f, 0.f};
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { vr = df_add(vr, red_r[w][tid]); vi = df_add(vi, red_i[w][tid]); }
-    q[((size_t)k * nsplit + s) * kDeflateMax * kDeflateMax + tid] = make_double2(df_to_double(vr), df_to_double(vi));
+    q[((size_t)k * nsplit + s) * kQExactMax * kQExactMax + tid] = make_double2(df_to_double(vr), df_to_double(vi));
   }
 }
 
@@ -617,7 +624,7 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
 // nb are the residual rows alone, nb = nt), Q from the exact kernel;
 // R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T (FP64)
 __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const double2* __restrict__ qpart,
-                                        const double2* __restrict__ aug, int aug_nsplit,
+                                        const double2* __restrict__ aug, int aug_nsplit, int aug_qrows,
                                         const float2* __restrict__ phi, const unsigned* __restrict__ xmax_bits,
                                         size_t wstride, int T, int tb, int qsplit, int nt, int nd_defl, int nb,
                                         double2* __restrict__ R) {
@@ -625,9 +632,11 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   // packets whose augmented rows fit one tile)
   const int k = blockIdx.y;
   const double* pk = part + (size_t)k * wstride;
-  __shared__ double2 U[kEvdNmax][kDeflateMax];
-  __shared__ double2 Q[kDeflateMax][kDeflateMax];
-  __shared__ double2 ph[kDeflateMax][kEvdNmax];
+  extern __shared__ double2 asm_dyn[];   // U [nt][kDeflateMax], Q [kDeflateMax]^2, ph [d][kEvdNmax]
+  double2 (*U)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn);
+  double2 (*Q)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn + (size_t)nt * kDeflateMax);
+  double2 (*ph)[kEvdNmax] =
+      reinterpret_cast<double2 (*)[kEvdNmax]>(asm_dyn + (size_t)(nt + kDeflateMax) * kDeflateMax);
   __shared__ double inv_s2;
   if (threadIdx.x == 0) {
     float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
@@ -647,7 +656,8 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     const double xi = dre(a, bb, 1) - dre(bb, a, 1);
     return make_double2(0.5 * xr * is2, 0.5 * xi * is2);
   };
-  const double2* ak = aug + (size_t)k * aug_nsplit * nt * nd_defl;
+  const size_t aout = (size_t)(nt + aug_qrows) * nd_defl;   // augmented-column outputs per split
+  const double2* ak = aug + (size_t)k * aug_nsplit * aout;
   for (int e = threadIdx.x; e < nt * nd_defl; e += blockDim.x) {
     int i = e / nd_defl, a = e % nd_defl;
     if (nb > nt) {
@@ -655,7 +665,7 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     } else {
       double sx = 0.0, sy = 0.0;
       for (int s = 0; s < aug_nsplit; ++s) {
-        const double2 v = ak[(size_t)s * nt * nd_defl + e];
+        const double2 v = ak[(size_t)s * aout + e];
         sx += v.x;
         sy += v.y;
       }
@@ -664,14 +674,23 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     float2 f = phi[a * nt + i];
     ph[a][i] = make_double2((double)f.x, (double)f.y);
   }
-  if (threadIdx.x < nd_defl * nd_defl) {
-    int a = threadIdx.x / nd_defl, c = threadIdx.x % nd_defl;
+  for (int e = threadIdx.x; e < nd_defl * nd_defl; e += blockDim.x) {
+    int a = e / nd_defl, c = e % nd_defl;
     double sx = 0.0, sy = 0.0;
-    for (int s = 0; s < qsplit; ++s) {
-      double2 v1 = qpart[((size_t)k * qsplit + s) * kDeflateMax * kDeflateMax + a * kDeflateMax + c];
-      double2 v2 = qpart[((size_t)k * qsplit + s) * kDeflateMax * kDeflateMax + c * kDeflateMax + a];
-      sx += 0.5 * (v1.x + v2.x);
-      sy += 0.5 * (v1.y - v2.y);
+    if (aug_qrows > 0) {   // exact-product rows of the augmented-column kernel: Q[a][c] at row nt + a
+      for (int s = 0; s < aug_nsplit; ++s) {
+        const double2 v1 = ak[(size_t)s * aout + (size_t)(nt + a) * nd_defl + c];
+        const double2 v2 = ak[(size_t)s * aout + (size_t)(nt + c) * nd_defl + a];
+        sx += 0.5 * (v1.x + v2.x);
+        sy += 0.5 * (v1.y - v2.y);
+      }
+    } else {
+      for (int s = 0; s < qsplit; ++s) {
+        double2 v1 = qpart[((size_t)k * qsplit + s) * kQExactMax * kQExactMax + a * kQExactMax + c];
+        double2 v2 = qpart[((size_t)k * qsplit + s) * kQExactMax * kQExactMax + c * kQExactMax + a];
+        sx += 0.5 * (v1.x + v2.x);
+        sy += 0.5 * (v1.y - v2.y);
+      }
     }
     Q[a][c] = make_double2(sx, sy);
   }
@@ -705,21 +724,35 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   }
 }
 
-cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
+template <int GP>
+static void launch_gram_tc_gp(const lcf_plan* P, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   const int na = P->tc_na;
   if (P->tc_T > 1) {
     dim3 gb(P->tc_T * P->tc_T, P->nd);
-    gram_tcb_kernel<<<gb, TG_THREADS, gram_tcb_smem_bytes(P->tc_tb), st>>>(
+    gram_tcb_kernel<GP><<<gb, TG_THREADS, gram_tcb_smem_bytes(P->tc_tb), st>>>(
         P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc, P->ws.err);
   } else {
     dim3 grid(P->tc_nsplit, P->nd);
-    gram_tc_kernel<<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(P->tm_xa, P->tm_xa_ok ? 1 : 0, P->ws.xa, c.nz, c.nx, na,
-                                                          P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->tc_nsplit,
-                                                          gram_tc_stages(na), P->ws.gtc, P->ws.err);
+    gram_tc_kernel<GP><<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(
+        P->tm_xa, P->tm_xa_ok ? 1 : 0, P->ws.xa, c.nz, c.nx, na, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax,
+        P->tc_nsplit, gram_tc_stages(na), P->ws.gtc, P->ws.err);
+  }
+}
+
+cudaError_t launch_gram_tc(const lcf_plan* P, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  const int na = P->tc_na;
+  switch (c.gram_precision) {
+    case LCF_GP_BF16X3: launch_gram_tc_gp<LCF_GP_BF16X3>(P, st); break;
+    case LCF_GP_F16: launch_gram_tc_gp<LCF_GP_F16>(P, st); break;
+    case LCF_GP_BF16: launch_gram_tc_gp<LCF_GP_BF16>(P, st); break;
+    case LCF_GP_E4M3: launch_gram_tc_gp<LCF_GP_E4M3>(P, st); break;
+    default: launch_gram_tc_gp<LCF_GP_F16X3>(P, st); break;
   }
   cudaError_t e = counted(P);
   if (e != cudaSuccess) return e;
+  if (P->ndefl > kQExactMax) return launch_gram_aug(P, st, true);   // U and Q (exact products) on CUDA cores
   gram_q_kernel<<<dim3(P->q_nsplit, P->nd), 256, 0, st>>>(P->ws.xa, c.nz, c.nx, P->nt, P->ndefl, P->ws.box,
                                                           P->ws.gz, P->ws.gx, P->q_nsplit, P->ws.gq);
   e = counted(P);
@@ -774,8 +807,9 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   // four blocks per window: each recomputes the window's W-form columns (FP64), so fewer blocks
   // cost less FP64 work in total, and four still fill the GPU at Nd = 64
   dim3 grid((nup + 255) / 256 < 4 ? (nup + 255) / 256 : 4, P->nd);
-  gram_assemble_tc_kernel<<<grid, 256, 0, st>>>(P->tc_T > 1 ? P->ws.gtc : sums, P->ws.gq, P->ws.gaug,
-                                                 P->aug_nsplit, P->ws.phi, P->ws.xmax,
+  gram_assemble_tc_kernel<<<grid, 256, gram_assemble_smem_bytes(P->nt, P->ndefl), st>>>(
+      P->tc_T > 1 ? P->ws.gtc : sums, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ndefl > kQExactMax ? P->ndefl : 0,
+      P->ws.phi, P->ws.xmax,
                                                  P->tc_T > 1 ? (size_t)P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
                                                              : per_split,
                                                  P->tc_T, P->tc_tb, P->q_nsplit, P->nt, P->ndefl, na,
@@ -813,13 +847,25 @@ cudaError_t gram_tc_make_map(lcf_plan* P) {
   return cudaSuccess;
 }
 
+template <int GP>
+static cudaError_t gram_tc_configure_gp(size_t mx) {
+  const cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(gram_tcb_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gram_tcb_smem_bytes(kTcTileMax));
+}
+
 cudaError_t gram_tc_configure() {
   size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
   for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
-  const cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(gram_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)gram_tcb_smem_bytes(kTcTileMax));
+  cudaError_t e = cudaFuncSetAttribute(gram_assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gram_assemble_smem_bytes(kEvdNmax, kDeflateMax));
+  if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_F16X3>(mx);
+  if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_BF16X3>(mx);
+  if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_F16>(mx);
+  if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_BF16>(mx);
+  if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_E4M3>(mx);
+  return e;
 }
 
 }  // namespace lcf

@@ -393,12 +393,36 @@ extern "C" lcf_status lcf_plan_set_mlp(lcf_plan* P, const lcf_mlp* N, float p_mi
     if (cudaMalloc((void**)&P->ws.mlp_b, nb * sizeof(float)) != cudaSuccess) return LCF_ENOMEM;
     P->ws_bytes += nw * sizeof(__nv_bfloat16) + nb * sizeof(float);
   }
+  if (!P->ws.mlp_dbg) {
+    const size_t nf = (size_t)P->nd * (2 * P->nt + 2);
+    if (cudaMalloc((void**)&P->ws.mlp_dbg, nf * sizeof(float)) != cudaSuccess) return LCF_ENOMEM;
+    if (cudaMemset(P->ws.mlp_dbg, 0, nf * sizeof(float)) != cudaSuccess) return LCF_ECUDA;
+    P->ws_bytes += nf * sizeof(float);
+  }
   // the plan's stream may still be reading the previous weights
   if (P->launched && cudaStreamSynchronize(P->last_stream) != cudaSuccess) return LCF_ECUDA;
+  plan_drop_graphs(P);   // captured packets may point at the weights just replaced
   if (mlp_plan_weights(N, P->ws.mlp_w, P->ws.mlp_b, 0) != cudaSuccess) return LCF_ECUDA;
   if (cudaStreamSynchronize(0) != cudaSuccess) return LCF_ECUDA;
   P->mlp_hidden = N->hidden;
   P->mlp_pmin = p_min;
+  return LCF_OK;
+}
+
+extern "C" lcf_status lcf_debug_learned(lcf_plan* P, float* features, float* logits) {
+  if (!P) return LCF_EINVAL;
+  if (!P->ws.mlp_dbg) return LCF_EINVAL;   // no network set
+  Dev guard(P->device);
+  if (P->launched && cudaStreamSynchronize(P->last_stream) != cudaSuccess) return LCF_ECUDA;
+  const int n = P->nt;
+  std::vector<float> h((size_t)P->nd * (2 * n + 2));
+  if (cudaMemcpy(h.data(), P->ws.mlp_dbg, h.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LCF_ECUDA;
+  for (int k = 0; k < P->nd; ++k) {
+    const float* r = h.data() + (size_t)k * (2 * n + 2);
+    if (features) memcpy(features + (size_t)k * (n + 2), r, (n + 2) * sizeof(float));
+    if (logits) memcpy(logits + (size_t)k * n, r + n + 2, n * sizeof(float));
+  }
   return LCF_OK;
 }
 

@@ -11,13 +11,25 @@
 //
 // The array's host-side name is only a stand-in for the device symbol, so the
 // first call on each device looks its device address up with
-// cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should come before any stream capture.  All calls share the array and
-// it keeps the previous call's contents: nothing in it needs to start at
+// cudaGetSymbolAddress (with that device current) and caches it, under a
+// mutex so that first calls from several host threads are safe; that first
+// call should come before any stream capture.
+//
+// The arithmetic is the plain path's Gram stage except for the deflation
+// basis: a fixed orthonormal DCT-II basis of the slow-time axis instead of the
+// plan's data-derived basis (the top eigenvectors of a subsampled global Gram,
+// which would need the plan's workspace).  The Gram identity R = E^H R' E is
+// exact for any basis; the basis only decides how much tissue energy is left
+// in the FP32 residual sums, so the result agrees with a plan's Gram to the
+// library's Gram tolerance rather than bit for bit.
+//
+// All calls share the array and it keeps the previous call's contents: nothing in it needs to start at
 // zero (every entry that is read is written earlier in the same call), but
 // calls whose work overlaps on the GPU (different streams, no ordering) race
 // on it.
 #include <math.h>
+
+#include <mutex>
 
 #include "lcf_internal.cuh"
 
@@ -29,6 +41,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 static void* g_scratch_addr[64];
 static bool g_scratch_ready[64];
+static std::mutex g_scratch_mutex;   // guards the two tables above
 
 __global__ void center_kernel(const float2* __restrict__ iq, const float2* __restrict__ phi,
                               float2* __restrict__ xa, int nt, int nd_defl, int npix, unsigned* xmax_bits);
@@ -104,6 +117,9 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
     return LCF_EINVAL;
   if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
+  // the kernels index the deflated packet in 32 bits (the bound lcf_plan_create applies), and
+  // with it every size_t product below stays far from overflow
+  if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   const int ndefl = deflate_count(c->nt);
   const size_t nd = (size_t)c->wz * c->wx, nt = c->nt, n1 = nt + ndefl, npix = (size_t)c->nz * c->nx;
   const int tiles = (int)((nt + 63) / 64), pairs = tiles * (tiles + 1) / 2;
@@ -128,14 +144,18 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   int nsplit = (int)((kScratchBytes - off_part) / per_split);
   if (nsplit > want) nsplit = want;
 
-  if (!g_scratch_ready[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LCF_ECUDA;
-    if (gram_simt_configure() != cudaSuccess) return LCF_ECUDA;   // long packets stage > 48 KB
-    g_scratch_addr[dev] = p;
-    g_scratch_ready[dev] = true;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ready[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LCF_ECUDA;
+      if (gram_simt_configure() != cudaSuccess) return LCF_ECUDA;   // long packets stage > 48 KB
+      g_scratch_addr[dev] = p;
+      g_scratch_ready[dev] = true;
+    }
+    base = static_cast<unsigned char*>(g_scratch_addr[dev]);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
   float* gz = reinterpret_cast<float*>(base);
   float* gx = reinterpret_cast<float*>(base + off_gx);
   Box* box = reinterpret_cast<Box*>(base + off_box);
@@ -160,7 +180,8 @@ extern "C" lcf_status lcf_gram_noalloc(const lcf_config* c, const void* d_iq, vo
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   int bx = (int)((nt * nt + 255) / 256);
   dim3 ga(bx < 8 ? bx : 8, (unsigned)nd);
-  gram_assemble_kernel<<<ga, 256, 0, stream>>>(part, aug, phi, nsplit, 1, (int)nt, ndefl, (double2*)d_R);
+  gram_assemble_kernel<<<ga, 256, gram_assemble_smem_bytes((int)nt, ndefl), stream>>>(part, aug, phi, nsplit, 1, (int)nt, ndefl,
+                                                                       (double2*)d_R);
   if (cudaGetLastError() != cudaSuccess) return LCF_ECUDA;
   return LCF_OK;
 }

@@ -395,12 +395,12 @@ cudaError_t launch_project_tc(const lcf_plan* P, float* out, cudaStream_t st) {
 }
 
 cudaError_t project_tc_configure() {
-  size_t mx = 0;   // the largest launch over every packet length (two or one k-steps per stage)
-  for (int nt = 2; nt <= kEvdNmax; ++nt) {
-    const int d = deflate_count(nt);
-    const size_t b = project_tc_smem_bytes(nt, d, project_tc_ksps(nt, d));
-    mx = b > mx ? b : mx;
-  }
+  size_t mx = 0;   // the largest launch over every packet length and deflation depth
+  for (int nt = 2; nt <= kEvdNmax; ++nt)
+    for (int d = 1; d <= kDeflateMax && d < nt + (nt == 2); ++d) {
+      const size_t b = project_tc_smem_bytes(nt, d, project_tc_ksps(nt, d));
+      mx = b > mx ? b : mx;
+    }
   return cudaFuncSetAttribute(project_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 

@@ -43,10 +43,10 @@ extern "C" lcf_status lcf_config_default(lcf_config* c, int nz, int nx, int nt, 
   c->k_fixed = 0;
   c->k_src = LCF_T_FIXED;
   c->beta_src = 1.0f;
-  c->gram_path = LCF_PATH_SIMT;
-  c->project_path = LCF_PATH_SIMT;
+  c->gram_path = LCF_PATH_TC;
+  c->project_path = LCF_PATH_TC;
   c->max_sweeps = 40;
-  c->evd_path = LCF_EVD_CTA;
+  c->evd_path = LCF_EVD_PAIR;
   return LCF_OK;
 }
 
@@ -55,17 +55,24 @@ static lcf_status validate(const lcf_config* c) {
   if (c->nz <= 0 || c->nx <= 0 || c->nt < 2 || c->wz <= 0 || c->wx <= 0) return LCF_EINVAL;
   if (c->wz > c->nz || c->wx > c->nx) return LCF_EINVAL;
   if (!(c->sigma_scale > 0.f) || !isfinite(c->sigma_scale) || !isfinite(c->support_sigmas)) return LCF_EINVAL;
-  if (c->thresh_mode < LCF_T_FIXED || c->thresh_mode > LCF_T_LEARNED) return LCF_EINVAL;
+  if (c->thresh_mode < LCF_T_FIXED || c->thresh_mode > LCF_T_NCC) return LCF_EINVAL;
   if (c->thresh_mode == LCF_T_LEARNED && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
   if (c->thresh_mode == LCF_T_LEARNED && (c->evd_path != LCF_EVD_PAIR || c->nt > kEvdPairNmax))
     return LCF_EUNSUPPORTED;
-  if (c->thresh_mode == LCF_T_SIGMOID && (c->k_src < LCF_T_FIXED || c->k_src > LCF_T_MEDIAN)) return LCF_EINVAL;
+  if (c->thresh_mode == LCF_T_SIGMOID && !((c->k_src >= LCF_T_FIXED && c->k_src <= LCF_T_MEDIAN) || c->k_src == LCF_T_NCC))
+    return LCF_EINVAL;
+  if (c->thresh_mode == LCF_T_LEARNED && c->evd_precision != LCF_EP_FP32) return LCF_EUNSUPPORTED;
   if (!isfinite(c->beta) || !isfinite(c->beta_src)) return LCF_EINVAL;
   if (c->pd_mode < 0 || c->pd_mode > 1 || c->alpha_mode < 0 || c->alpha_mode > 2) return LCF_EINVAL;
   if (c->curv_norm < 0 || c->curv_norm > 1) return LCF_EINVAL;
   if (c->gram_path < LCF_PATH_SIMT || c->gram_path > LCF_PATH_TC) return LCF_EINVAL;
   if (c->project_path < LCF_PATH_SIMT || c->project_path > LCF_PATH_TC) return LCF_EINVAL;
   if (c->evd_path < LCF_EVD_CTA || c->evd_path > LCF_EVD_PAIR) return LCF_EINVAL;
+  if (c->gram_precision < LCF_GP_F16X3 || c->gram_precision > LCF_GP_E4M3) return LCF_EINVAL;
+  if (c->gram_path != LCF_PATH_TC && c->gram_precision != LCF_GP_F16X3) return LCF_EINVAL;
+  if (c->evd_precision < LCF_EP_FP32 || c->evd_precision > LCF_EP_FP64_POLISH) return LCF_EINVAL;
+  if (c->graph < 0 || c->graph > 1) return LCF_EINVAL;
+  if (c->deflate < 0 || c->deflate > kDeflateMax || (c->deflate > 0 && c->deflate >= c->nt)) return LCF_EINVAL;
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
   if (c->evd_path == LCF_EVD_CTA && c->nt > kEvdCtaNmax) return LCF_EUNSUPPORTED;
@@ -120,8 +127,9 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
-                  w.flags, w.W, w.pw, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.evd_B, w.evd_vh, w.evd_t,
-                  w.evd_scale, w.iq_stage, w.pd_stage, w.phi_alt, w.xmax_alt, w.gglob_async};
+                  w.flags, w.W, w.pw, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.mlp_dbg, w.evd_B, w.evd_vh, w.evd_t,
+                  w.evd_scale, w.iq_stage, w.pd_stage, w.phi_alt, w.xmax_alt, w.gglob_async, w.post_rq,
+                  w.post_pv, w.post_isig, w.post_band};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -145,7 +153,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   P->device = device;
   P->nd = cfg->wz * cfg->wx;
   P->nt = cfg->nt;
-  P->ndefl = deflate_count(cfg->nt);
+  P->ndefl = deflate_depth(cfg->nt, cfg->deflate);
   P->n1 = cfg->nt + P->ndefl;
   P->npix = cfg->nz * cfg->nx;
   P->gram_tiles = (P->nt + 63) / 64;
@@ -170,7 +178,9 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     long ts = (pmax + 2047) / 2048;   // ~2048 pixels per tensor-core CTA
     P->tc_nsplit = (int)(ts < 1 ? 1 : (ts > 64 ? 64 : ts));
   }
-  P->tc_na = P->n1 <= kTcGramNaMax ? P->n1 : P->nt;
+  // one tensor-core tile holds the augmented rows when they fit and the exact-product kernel
+  // takes the coefficient block; otherwise the residual rows alone, U and Q from CUDA cores
+  P->tc_na = (P->n1 <= kTcGramNaMax && P->ndefl <= kQExactMax) ? P->n1 : P->nt;
   if (P->tc_na > kTcGramNaMax) {   // long packets: tile pairs of at most kTcTileMax rows, no pixel splits
     P->tc_T = (P->nt + kTcTileMax - 1) / kTcTileMax;
     P->tc_tb = ((P->nt + P->tc_T - 1) / P->tc_T + 7) / 8 * 8;
@@ -180,6 +190,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     P->tc_tb = P->tc_na;
   }
   P->ncp = P->nt <= kProjectShortNmax ? 4 * project_cpt(P->nt) : (P->nt + 15) / 16 * 16;
+  P->evd_cluster = evd_dist_cluster(P->nt);
   std::vector<float> gz, gx;
   build_geometry(*cfg, P->boxes, gz, gx);
 
@@ -204,7 +215,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess)
       e = dalloc(&w.gtc, P->tc_T > 1 ? nd * P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
                                       : nd * std::max(P->tc_nsplit, 2) * 2 * P->tc_na * P->tc_na, &tot);
-    if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kDeflateMax * kDeflateMax, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.gq, nd * P->q_nsplit * kQExactMax * kQExactMax, &tot);
     if (e == cudaSuccess) e = gram_tc_make_map(P);
   }
   if (e == cudaSuccess) e = dalloc(&w.R, nd * nt * nt, &tot);
@@ -224,6 +235,15 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = dalloc(&w.evd_vh, nd * m * nt, &tot);
     if (e == cudaSuccess) e = dalloc(&w.evd_t, nd * m * m, &tot);
     if (e == cudaSuccess) e = dalloc(&w.evd_scale, nd, &tot);
+  }
+  if (e == cudaSuccess && cfg->evd_precision == LCF_EP_FP64_POLISH)
+    e = dalloc(&w.post_rq, nd * post_rq_blocks(P->nt) * nt, &tot);
+  if (post_uses_ncc(*cfg)) {
+    const int ns = (3 * P->sm_count + P->nd - 1) / P->nd;   // about three CTAs per SM in all
+    P->ncc_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
+    if (e == cudaSuccess) e = dalloc(&w.post_pv, nd * kDeflateMax * nt, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.post_isig, nd * nt, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.post_band, post_band_count(P), &tot);
   }
   std::vector<int> toff, twin;
   if (cfg->project_path == LCF_PATH_TC) {
@@ -263,6 +283,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = evd_pair_configure();
     if (e == cudaSuccess) e = evd_dist_configure();
     if (e == cudaSuccess) e = gram_simt_configure();
+    if (e == cudaSuccess) e = post_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
   }
   if (e != cudaSuccess) {
@@ -323,12 +344,17 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   if (c.evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) LCF_CUDA(launch_evd_dist(P, st));
   else if (c.evd_path == LCF_EVD_PAIR) LCF_CUDA(launch_evd_pair(P, st));
   else LCF_CUDA(launch_evd(P, st));
+  LCF_CUDA(launch_post(P, st));   // FP64-class polish, method 4 (no launch otherwise)
   LCF_MARK(LCF_STAGE_PROJECT);
   if (c.project_path == LCF_PATH_TC) LCF_CUDA(launch_project_tc(P, out, st));
   else LCF_CUDA(launch_project_simt(P, iq, out, st));
   LCF_MARK(LCF_NSTAGES);
   if (P->profiling) ++P->prof_calls;
   return LCF_OK;
+}
+
+lcf_status lcf::packet_once(lcf_plan* P, const float2* iq, float* out, cudaStream_t st) {
+  return run_packet(P, iq, out, st);
 }
 
 extern "C" lcf_status lcf_plan_profile(lcf_plan* P, int enable) {
@@ -436,13 +462,67 @@ static lcf_status pipe_packet(lcf_plan* P, const float2* iq, float* out, cudaStr
   return LCF_OK;
 }
 
+// Drop the captured single-packet graphs (their buffer pointers may be stale after a
+// setup call that reallocates plan memory).
+void lcf::plan_drop_graphs(lcf_plan* P) {
+  for (auto& e : P->pg) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    e = lcf_plan::PacketGraph();
+  }
+}
+
+// One packet as one CUDA graph launch: the stage launches of run_packet captured once per
+// (input, output) pair on the plan's capture stream and replayed on `stream`.
+static lcf_status graph_packet(lcf_plan* P, const float2* iq, float* out, cudaStream_t stream) {
+  int slot = -1, oldest = 0;
+  for (int i = 0; i < lcf_plan::kPacketGraphs; ++i) {
+    if (P->pg[i].exec && P->pg[i].iq == iq && P->pg[i].out == out) { slot = i; break; }
+    if (P->pg[i].used < P->pg[oldest].used) oldest = i;
+  }
+  if (slot < 0) {
+    slot = oldest;
+    lcf_plan::PacketGraph& e = P->pg[slot];
+    if (e.exec) {
+      cudaGraphExecDestroy(e.exec);
+      e.exec = nullptr;
+    }
+    if (!P->cap_stream) LCF_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+    const long long l0 = P->launches;
+    LCF_CUDA(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+    lcf_status s = run_packet(P, iq, out, P->cap_stream);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &gr);
+    e.launches = P->launches - l0;
+    P->launches = l0;
+    if (s != LCF_OK || ce != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return s != LCF_OK ? s : LCF_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (ie != cudaSuccess) {
+      e.exec = nullptr;
+      return LCF_ECUDA;
+    }
+    e.iq = iq;
+    e.out = out;
+  }
+  lcf_plan::PacketGraph& e = P->pg[slot];
+  e.used = ++P->pg_clock;
+  LCF_CUDA(cudaGraphLaunch(e.exec, stream));
+  P->launches += e.launches;
+  return LCF_OK;
+}
+
 extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd, cudaStream_t stream) {
   if (!P || !d_iq || !d_out_pd) return LCF_EINVAL;
   if (((uintptr_t)d_iq & 7) || ((uintptr_t)d_out_pd & 3)) return LCF_EINVAL;
   DeviceGuard g(P->device);
-  const bool pipe = P->cfg.inputs_ready && !P->profiling;
+  const bool pipe = P->cfg.inputs_ready && !P->profiling && !P->cfg.graph;
+  const bool graph = P->cfg.graph && !P->profiling;
   lcf_status s = pipe ? pipe_packet(P, (const float2*)d_iq, d_out_pd, stream, nullptr)
-                      : run_packet(P, (const float2*)d_iq, d_out_pd, stream);
+                      : graph ? graph_packet(P, (const float2*)d_iq, d_out_pd, stream)
+                              : run_packet(P, (const float2*)d_iq, d_out_pd, stream);
   P->last_stream = stream;
   P->launched = true;
   P->last_iq = (void*)d_iq;
@@ -654,6 +734,8 @@ extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
   free_ws(P->ws);
   for (auto& e : P->prof_ev) cudaEventDestroy(e);
   if (P->sg_exec) cudaGraphExecDestroy(P->sg_exec);
+  for (auto& e : P->pg)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->h2d_stream) cudaStreamDestroy(P->h2d_stream);
   if (P->prep_stream) cudaStreamDestroy(P->prep_stream);

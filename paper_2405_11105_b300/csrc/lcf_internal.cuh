@@ -29,12 +29,21 @@ constexpr int kTcTileMax = 112;   // row tile of the long-packet tensor-core Gra
 constexpr int kTcSlabBox = 34;    // pixels per tensor-core Gram slab load (32 used; 272-byte rows)
 // Subspace-iteration block of the EVD (head directions isolated exactly).
 constexpr int kEvdHead = 8;
-// Slow-time DCT-II vectors deflated from every pixel before the Gram.
-constexpr int kDeflateMax = 4;
+// Slow-time vectors (the packet's dominant global modes) deflated from every pixel
+// before the Gram: at most kDeflateMax; by default clamp(Nt/4, 1, 4), which leaves
+// blood-and-noise-level residuals for sub-pixel tissue motion; strong motion
+// (about a pixel and more) needs 8-16 (lcf_config.deflate).
+constexpr int kDeflateMax = 16;
+constexpr int kDeflateDefaultMax = 4;
+// Deflation depths up to this take the coefficient block Q from the register-resident
+// exact-product kernel (gram_q_kernel); deeper ones from the augmented-column kernel.
+constexpr int kQExactMax = 4;
 __host__ __device__ inline int deflate_count(int nt) {
   int d = nt / 4;
-  return d < 1 ? 1 : (d > kDeflateMax ? kDeflateMax : d);
+  return d < 1 ? 1 : (d > kDeflateDefaultMax ? kDeflateDefaultMax : d);
 }
+// the plan's deflation depth: cfg->deflate when set, else the default for nt
+__host__ __device__ inline int deflate_depth(int nt, int deflate) { return deflate > 0 ? deflate : deflate_count(nt); }
 // EVD phases timed by the stage profiler: subspace iteration, QR of the block,
 // double-float congruence, fp32 conversion + Q, Jacobi, sort + phase fix,
 // thresholding rule, projection weights.
@@ -65,7 +74,7 @@ struct Workspace {
   double* gtc = nullptr;      // f32 [nd][tc_nsplit][2][na][na] tensor-core partials (Re, Im planes)
                               // then their f64 sums [nd][2][na][na]; or f64 [nd][T][T][2][tb][tb]
                               // tile-pair partials for long packets
-  double2* gq = nullptr;      // [nd][q_nsplit][kDeflateMax^2] exact coefficient-block partials
+  double2* gq = nullptr;      // [nd][q_nsplit][kQExactMax^2] exact coefficient-block partials
   int* err = nullptr;         // [1] device error word (bit 0: a bounded wait gave up)
   double2* R = nullptr;       // [nd][nt][nt] windowed Gram (Eq. 12)
   // EVD + weights
@@ -92,6 +101,12 @@ struct Workspace {
   // learned cutoff rule (set by lcf_plan_set_mlp)
   __nv_bfloat16* mlp_w = nullptr;   // W1 | W2 | W3 | W4, bf16
   float* mlp_b = nullptr;           // b1 | b2 | b3 | b4
+  float* mlp_dbg = nullptr;         // [nd][2 nt + 2] the last call's network inputs and logits
+  // after the EVD: FP64-class polish and method 4 (k_post.cu)
+  double* post_rq = nullptr;  // [nd][ceil(nt/16)][nt] Rayleigh-quotient partials
+  float2* post_pv = nullptr;  // [nd][kDeflateMax][nt] Phi^T V
+  float* post_isig = nullptr; // [nd][nt] 1 / sigma_i
+  double* post_band = nullptr;  // [nd][ncc_nsplit][nt][10] magnitude-Gram band partials
   // host-call staging
   float2* iq_stage = nullptr; // [2][nt][nz][nx] device copies for lcf_filter_host(_async)
   float* pd_stage = nullptr;  // [2][nz][nx]
@@ -117,6 +132,8 @@ struct lcf_plan {
   int ptiles_z = 0, ptiles_x = 0;   // tensor-core projection tiles (8 x 16 pixels)
   int mlp_hidden = 0;   // hidden width of the plan's learned rule (0: none set)
   float mlp_pmin = 0.f; // confidence below which the learned rule falls back to k_src
+  int ncc_nsplit = 1;   // pixel splits per window of method 4's band sums
+  int evd_cluster = 0;  // CTAs per window of the distributed EVD (Nt > 128)
   int sm_count = 0;
   std::vector<lcf::Box> boxes;
   lcf::Workspace ws;
@@ -144,6 +161,16 @@ struct lcf_plan {
   mutable long long launches = 0;
   // the last stream of packets, captured as one CUDA graph (lcf_filter_stream)
   cudaStream_t cap_stream = nullptr;
+  // single-packet graphs of lcf_filter (cfg.graph), one per (input, output) pair, oldest replaced
+  static constexpr int kPacketGraphs = 16;
+  struct PacketGraph {
+    const void* iq = nullptr;
+    float* out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    long long used = 0;
+  } pg[kPacketGraphs];
+  long long pg_clock = 0;
   cudaGraphExec_t sg_exec = nullptr;
   const void* sg_frames = nullptr;
   float* sg_out = nullptr;
@@ -253,6 +280,7 @@ inline cudaError_t counted(const lcf_plan* P, int n = 1) {
 cudaError_t launch_center(const lcf_plan* P, const float2* iq, cudaStream_t st);
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st, bool with_q = true);
 size_t gram_aug_smem_bytes(int nt, int nd_defl);
+size_t gram_assemble_smem_bytes(int nt, int nd_defl);
 cudaError_t gram_simt_configure();
 cudaError_t launch_basis(const lcf_plan* P, const float2* iq, cudaStream_t st);
 cudaError_t basis_configure();
@@ -282,5 +310,14 @@ size_t evd_smem_bytes(int nt);
 cudaError_t evd_configure();
 cudaError_t project_configure();
 int project_cpt(int nt);
+bool post_uses_ncc(const lcf_config& c);
+int post_rq_blocks(int nt);
+size_t post_band_count(const lcf_plan* P);
+cudaError_t post_configure();
+cudaError_t launch_post(const lcf_plan* P, cudaStream_t st);
+void plan_drop_graphs(lcf_plan* P);
+lcf_status packet_once(lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
+int evd_dist_cluster(int nt);
+size_t evd_dist_smem_bytes(int nt, int C);
 
 }  // namespace lcf

@@ -7,8 +7,12 @@
 // sits at (row/8)*SBO + (k/8)*LBO; the kernels use LBO = 128 B (cores along K
 // contiguous) and SBO = (K_stage/8)*128 B.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
+
+#include "../../include/lcf.h"
 
 namespace lcf {
 namespace tc {
@@ -33,6 +37,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // instruction descriptor: kind::f16, A/B fp16, D fp32, both K-major, shape M x N
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// the same with A and B bf16 (both operands of one kind::f16 MMA share their type)
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return idesc_f16(M, N) | (1u << 7) | (1u << 10);
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
@@ -179,6 +187,49 @@ __device__ __forceinline__ void split2_f16(float2 x, float2 gg, float2 gg2, __ha
   hi = __float22half2_rn(v);
   lo2 = __float22half2_rn(__ffma2_rn(__half22float2(hi), make_float2(-2.f, -2.f), v2));
 }
+// ---- operand splits of the Gram's precision modes (LCF_GP_*), as raw 32-bit pairs ----
+// hi: the tensor-core word pair of g x; lo2: the pair of 2 (g x - hi) (the doubled low half),
+// written only by the three-product modes.
+template <int GP>
+__device__ __forceinline__ void split2_gp(float2 x, float2 gg, float2 gg2, uint32_t& hi, uint32_t& lo2) {
+  const float2 v = __fmul2_rn(x, gg);
+  if constexpr (GP == LCF_GP_F16X3) {
+    __half2 h, l;
+    split2_f16(x, gg, gg2, h, l);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo2 = *reinterpret_cast<const uint32_t*>(&l);
+  } else if constexpr (GP == LCF_GP_BF16X3) {
+    const float2 v2 = __fmul2_rn(x, gg2);
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    const __nv_bfloat162 l = __float22bfloat162_rn(__ffma2_rn(__bfloat1622float2(h), make_float2(-2.f, -2.f), v2));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo2 = *reinterpret_cast<const uint32_t*>(&l);
+  } else if constexpr (GP == LCF_GP_F16) {
+    const __half2 h = __float22half2_rn(v);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+  } else if constexpr (GP == LCF_GP_BF16) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+  } else {   // LCF_GP_E4M3: the nearest E4M3 value of g x 2^-6 (saturating), times 2^6, held exactly in fp16
+    const __nv_fp8x2_storage_t q =
+        __nv_cvt_float2_to_fp8x2(make_float2(v.x * 0.015625f, v.y * 0.015625f), __NV_SATFINITE, __NV_E4M3);
+    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
+    const __half2 h = __hmul2(*reinterpret_cast<const __half2*>(&hr), __float2half2_rn(64.f));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+// the precision mode's first-pass word pair of g x alone (the A operand of an off-diagonal tile)
+template <int GP>
+__device__ __forceinline__ uint32_t hi2_gp(float2 x, float2 gg) {
+  uint32_t h, l;
+  split2_gp<(GP == LCF_GP_F16X3 ? LCF_GP_F16 : GP == LCF_GP_BF16X3 ? LCF_GP_BF16 : GP)>(x, gg, gg, h, l);
+  return h;
+}
+__host__ __device__ constexpr bool gp_three_products(int gp) { return gp == LCF_GP_F16X3 || gp == LCF_GP_BF16X3; }
+__host__ __device__ constexpr bool gp_bf16(int gp) { return gp == LCF_GP_BF16X3 || gp == LCF_GP_BF16; }
+// (a, b) -> (b, -a) on a raw pair of 16-bit words (fp16 or bf16: the sign is bit 15 of each half)
+__device__ __forceinline__ uint32_t neg_i_raw(uint32_t u) { return ((u >> 16) | (u << 16)) ^ 0x80000000u; }
+
 // (a, b) -> (b, -a): the fp16 pair of -i (a + i b)
 __device__ __forceinline__ __half2 neg_i(__half2 h) {
   const __half2 sw = __lowhigh2highlow(h);

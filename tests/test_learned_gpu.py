@@ -154,6 +154,93 @@ def test_learned_plan_matches_converged_rule_in_db(trained):
     assert t["learned"] < t["full"]
 
 
+def bf16_round(w):
+    """FP32 -> nearest bf16 value (ties to even), as FP32: the plan stores its weights so."""
+    u = np.ascontiguousarray(w, np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def test_in_kernel_inference_matches_fp64_forward(trained):
+    """The learned rule inside the EVD kernel against the FP64 network of oracle/mlp.py on the
+    same capped spectra: the kernel's features equal the reference features computed from the
+    plan's eigenvalues (<= 1e-6), its logits equal the FP64 forward pass with the plan's bf16
+    weights and FP32 biases (<= 1e-4 relative to the logit scale: FP32 accumulation), and every
+    window's cutoff is the logits' argmax (or the fallback rule where the top softmax
+    probability is below p_min), except at logit near-ties."""
+    import torch
+    learned, net, _, test_p, _ = trained
+    lib = L()
+    lp = lib.Plan.make(64, 64, 32, 4, 4, thresh_mode=lib.LCF_T_LEARNED, k_src=lib.LCF_T_CURVATURE, beta_src=1.0,
+                       max_sweeps=2)
+    lp.set_mlp(net, p_min=0.5)
+    p = OM.unflatten(net.params().astype(np.float64), 34, net.hidden, 32)
+    for name in ("W1", "W2", "W3", "W4"):
+        p[name] = bf16_round(p[name]).astype(np.float64)
+    pz, px = learned.window_centres(4, 4)
+    worst_f, worst_z, checked, ties = 0.0, 0.0, 0, 0
+    for iq in test_p[:6]:
+        lp.filter(torch.from_numpy(iq).cuda())
+        dbg = lp.debug()
+        st, flags = lp.status()
+        f_gpu, z_gpu = lp.debug_learned()
+        X = np.stack([OM.features(dbg["lam"][w], pz[w], px[w]) for w in range(16)])
+        worst_f = max(worst_f, float(np.max(np.abs(f_gpu - X))))
+        z_ref, _ = OM.forward(p, X)
+        scale = np.max(np.abs(z_ref), axis=1, keepdims=True)
+        worst_z = max(worst_z, float(np.max(np.abs(z_gpu - z_ref) / scale)))
+        for w in range(16):
+            top2 = np.sort(z_ref[w])[-2:]
+            if top2[1] - top2[0] <= 1e-4 * scale[w, 0]:
+                ties += 1
+                continue
+            e = np.exp(z_ref[w] - z_ref[w].max())
+            pmax = 1.0 / e.sum()
+            fell_back = bool(flags[w] & lib.LCF_WFLAG_FALLBACK)
+            if abs(pmax - 0.5) > 1e-4:
+                assert fell_back == (pmax < 0.5), (w, pmax, flags[w])
+            if not fell_back:
+                assert int(dbg["k"][w]) == int(np.argmax(z_ref[w])), (w, dbg["k"][w], np.argmax(z_ref[w]))
+            checked += 1
+    print("feature max abs err", worst_f, "logit max rel err", worst_z, "windows checked", checked,
+          "logit near-ties", ties)
+    assert worst_f <= 1e-6
+    assert worst_z <= 1e-4
+    assert checked >= 80
+
+
+def test_learned_rule_against_network_off(trained):
+    """What the network buys: the same 2-sweep plan with the network switched off (p_min > 1,
+    so every window takes method 1 on the capped spectrum) against the learned plan, both
+    judged by method 1 on the converged EVD (mean |dB| over pixels within 30 dB of the
+    maximum) and by cutoff agreement."""
+    import torch
+    learned, net, _, test_p, _ = trained
+    lib = L()
+    full, _ = learned.make_plans(64, 64, 32, 4, 4, fast_sweeps=2)
+    arms = {}
+    for name, pmin in (("learned", 0.5), ("network_off", 1.01)):
+        lp = lib.Plan.make(64, 64, 32, 4, 4, thresh_mode=lib.LCF_T_LEARNED, k_src=lib.LCF_T_CURVATURE,
+                           beta_src=1.0, max_sweeps=2)
+        lp.set_mlp(net, p_min=pmin)
+        errs, agree, fb = [], [], 0
+        for iq in test_p:
+            d = torch.from_numpy(iq).cuda()
+            a = full.filter(d).cpu().numpy().astype(np.float64)
+            kf = full.debug()["k"]
+            b = lp.filter(d).cpu().numpy().astype(np.float64)
+            st, flags = lp.status()
+            fb += int(np.sum((np.asarray(flags) & lib.LCF_WFLAG_FALLBACK) != 0))
+            agree.append(np.mean(kf == lp.debug()["k"]))
+            m = a >= a.max() * 1e-3
+            errs.append(np.mean(np.abs(10 * np.log10(b[m] / a[m]))))
+        arms[name] = {"mean_db": float(np.mean(errs)), "worst_db": float(np.max(errs)),
+                      "cutoff_agreement": float(np.mean(agree)), "fallback_windows": fb}
+    print(arms)
+    assert arms["network_off"]["fallback_windows"] == 16 * len(test_p)
+    assert arms["learned"]["mean_db"] <= 0.5
+
+
 def test_learned_rule_fallback_and_requirements(trained):
     import torch
     learned, net, _, test_p, _ = trained

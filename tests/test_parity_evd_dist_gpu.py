@@ -96,69 +96,120 @@ def test_long_packet_limits():
         assert got == want, (kw, got)
 
 
-def test_stress_full_size_sampled():
-    """The precision-stress workload at its full size (256 x 192 px, Nt = 300, 10 x 10
-    windows, method 1): the whole packet through the library, then sampled outputs the
-    oracle can compute one window at a time: the Gram, eigenvalues, cutoff and alpha of
-    the nine windows that cover the image corner and of the centre window, and the power
-    Doppler of three corner pixels (covered by those nine windows only), summed from the
-    oracle's per-window EVD and weights (PD_k(p) = g_k(p)^2 / Nt sum_c wt_c^2 |s_p v_c|^2,
-    alpha_k = Nz Nx Nt / sum_c wt_c^2 lambda_c, the identities the oracle pins).  The Gram
-    and the eigenvalues in the 1e-6 lambda_1 band meet the standard tolerances; alpha and PD
-    are held to the precision-stress bound below."""
+@pytest.fixture(scope="module")
+def stress_oracle():
+    """The precision-stress workload (256 x 192 px, Nt = 300, 10 x 10 windows, method 1,
+    60 dB tissue-to-blood, 1.5 px respiratory motion plus 0.5 px jitter, -75 dB noise) and the
+    oracle's Gram, EVD and cutoff of the nine windows covering the image corner and of the
+    centre window, computed one window at a time."""
     import oracle as O
     from synth import generate_packet
     from synth.iq import STRESS_256x192x300
-    from test_parity_gpu import EIG_TOL, GRAM_TOL, configs, near_tie, run_gpu
+    from test_parity_gpu import configs
     lib = L()
     nz, nx, nt, wz, wx = 256, 192, 300, 10, 10
     iq = generate_packet(STRESS_256x192x300, seed=0)
-    cfg, oc = configs(nz, nx, nt, wz, wx, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
-    cfg.evd_path = lib.LCF_EVD_PAIR
+    _, oc = configs(nz, nx, nt, wz, wx, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0)
+    corner = [iz * wx + ix for iz in range(3) for ix in range(3)]
+    ora = {}
+    for k in corner + [wz * wx // 2 + wx // 2]:
+        R = O.gram(iq, oc, k)
+        lam, V, _ = O.eigh(R)
+        ora[k] = (R, lam, V)
+    return iq, oc, corner, ora
+
+
+def stress_errors(stress_oracle, **kw):
+    """Errors of one configuration of the library on the precision-stress packet against the
+    sampled oracle: the Gram, eigenvalues (1e-6 lambda_1 band), cutoff and alpha of the sampled
+    windows, and the power Doppler of three corner pixels (covered by the nine corner windows
+    only), summed from the oracle's per-window EVD and weights (PD_k(p) = g_k(p)^2 / Nt
+    sum_c wt_c^2 |s_p v_c|^2, alpha_k = Nz Nx Nt / sum_c wt_c^2 lambda_c: the identities the
+    oracle pins)."""
+    import oracle as O
+    from test_parity_gpu import configs, near_tie, run_gpu
+    lib = L()
+    iq, oc, corner, ora = stress_oracle
+    nz, nx, nt, wz, wx = oc.nz, oc.nx, oc.nt, oc.wz, oc.wx
+    cfg, _ = configs(nz, nx, nt, wz, wx, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0, **kw)
+    if cfg.evd_path == lib.LCF_EVD_CTA:
+        cfg.evd_path = lib.LCF_EVD_PAIR
     pd, plan, _ = run_gpu(iq, cfg)
     st, flags = plan.status()
-    assert st == lib.LCF_OK, flags
     dbg = plan.debug()
     Rg = plan.debug_gram()
     pix = [(0, 0), (1, 2), (3, 1)]
-    corner = [iz * wx + ix for iz in range(3) for ix in range(3)]
     for (z, x) in pix:   # the corner windows are exactly the ones covering the sampled pixels
         cov = [k for k in range(wz * wx) if O.window_weights(oc, k)[z, x] > 0.0]
         assert sorted(cov) == corner, (z, x, cov)
     pd_ora = np.zeros(len(pix))
-    pd_ora_ga = np.zeros(len(pix))   # with the GPU's alpha (separates the alpha and projection errors)
     s = iq.astype(np.complex128)
-    errs = {"gram": 0.0, "eig": 0.0, "alpha": 0.0}
-    for k in corner + [wz * wx // 2 + wx // 2]:
-        R = O.gram(iq, oc, k)
+    errs = {"status": int(st), "gram": 0.0, "eig": 0.0, "alpha": 0.0, "flips": 0, "ties": 0}
+    for k, (R, lam, V) in ora.items():
         errs["gram"] = max(errs["gram"], np.linalg.norm(Rg[k] - R) / np.linalg.norm(R))
-        lam, V, _ = O.eigh(R)
         m = lam >= 1e-6 * lam[0]
         errs["eig"] = max(errs["eig"], np.max(np.abs(dbg["lam"][k][m] - lam[m]) / lam[m]))
         wt, kk = O.weights(O.T_CURVATURE, lam, beta=1.0)
         kg = int(dbg["k"][k])
         if kg != kk:
-            assert near_tie(oc, lam, dbg["lam"][k], kg, kk), (k, kg, kk)
-            wt = (np.arange(nt) >= kg).astype(np.float64)   # the equally valid cutoff the GPU took
+            errs["flips"] += 1
+            if near_tie(oc, lam, dbg["lam"][k], kg, kk):
+                errs["ties"] += 1
+                wt = (np.arange(nt) >= kg).astype(np.float64)   # the equally valid cutoff the GPU took
         alpha = nz * nx * nt / np.sum(wt ** 2 * lam)
         errs["alpha"] = max(errs["alpha"], abs(dbg["alpha"][k] - alpha) / alpha)
-        print("window", k, "cutoff", kg, "kept eigenvalue sum / lambda_1", np.sum(wt ** 2 * lam) / lam[0],
-              "alpha err", abs(dbg["alpha"][k] - alpha) / alpha)
         if k in corner:
             g = O.window_weights(oc, k)
             for i, (z, x) in enumerate(pix):
                 proj = s[:, z, x] @ V   # s_p v_c over the columns c
                 pd_ora[i] += alpha * g[z, x] ** 2 / nt * np.sum(wt ** 2 * np.abs(proj) ** 2)
-                pd_ora_ga[i] += dbg["alpha"][k] * g[z, x] ** 2 / nt * np.sum(wt ** 2 * np.abs(proj) ** 2)
     pd_gpu = np.array([pd[z, x] for (z, x) in pix])
     errs["pd"] = float(np.max(np.abs(pd_gpu - pd_ora) / pd_ora))
-    errs["pd_at_gpu_alpha"] = float(np.max(np.abs(pd_gpu - pd_ora_ga) / pd_ora_ga))
-    print(errs)
-    assert np.all(np.isfinite(pd)) and pd.min() >= 0.0
+    errs["finite"] = bool(np.all(np.isfinite(pd)) and pd.min() >= 0.0)
+    return errs
+
+
+@pytest.mark.parametrize("path", ["plain", "fast"])
+def test_stress_full_size_sampled(stress_oracle, path):
+    """The precision-stress workload at its full size through the library with 12 deflated
+    slow-time vectors (the 1.5 px motion spreads the tissue over about 12 global modes, so
+    four would leave 1e-2 lambda_1 of tissue in the FP32 / tensor-core residual sums) and the
+    FP64-class eigenvalue polish: every sampled quantity meets the standard tolerances."""
+    from test_parity_gpu import ALPHA_TOL, EIG_TOL, GRAM_TOL, PD_TOL
+    lib = L()
+    kw = dict(deflate=12, evd_precision=lib.LCF_EP_FP64_POLISH)
+    if path == "fast":
+        kw.update(gram_path=lib.LCF_PATH_TC, project_path=lib.LCF_PATH_TC)
+    errs = stress_errors(stress_oracle, **kw)
+    print(path, errs)
+    assert errs["status"] == lib.LCF_OK and errs["finite"]
+    assert errs["flips"] == errs["ties"]
     assert errs["gram"] <= GRAM_TOL and errs["eig"] <= EIG_TOL
-    # At this dynamic range (60 dB tissue-to-blood, -75 dB noise) the kept eigenvalue sum is
-    # ~5e-8 of lambda_1, the FP32 unit roundoff: the FP32 eigen-decomposition resolves the
-    # kept subspace and its energy only to ~u lambda_1, so alpha and PD carry errors of order
-    # 1e-3 (measured 1.4e-3 and 2.6e-3). They are bounded here at 1e-2, ten times that floor.
-    STRESS_TOL = 1e-2
-    assert errs["alpha"] <= STRESS_TOL and errs["pd"] <= STRESS_TOL, errs
+    assert errs["alpha"] <= ALPHA_TOL and errs["pd"] <= PD_TOL, errs
+
+
+def test_stress_precision_study(stress_oracle):
+    """The precision study of the stress workload: every tensor-core product mode with the
+    FP32 and the polished eigen-decomposition (12 deflated vectors), and the default four
+    deflated vectors for contrast, each with its Gram, eigenvalue, alpha and PD errors against
+    the oracle.  The default product mode with the polish meets every tolerance; the E4M3 mode
+    (4-bit operands) cannot resolve the kept eigenvalues at this dynamic range."""
+    from test_parity_gpu import ALPHA_TOL, PD_TOL
+    lib = L()
+    rows = {}
+    for gp in ("LCF_GP_F16X3", "LCF_GP_BF16X3", "LCF_GP_F16", "LCF_GP_BF16", "LCF_GP_E4M3"):
+        for ep in ("LCF_EP_FP32", "LCF_EP_FP64_POLISH"):
+            rows[(gp, ep, 12)] = stress_errors(stress_oracle, gram_path=lib.LCF_PATH_TC, project_path=lib.LCF_PATH_TC,
+                                               gram_precision=getattr(lib, gp), evd_precision=getattr(lib, ep),
+                                               deflate=12)
+    rows[("LCF_GP_F16X3", "LCF_EP_FP32", 4)] = stress_errors(stress_oracle, gram_path=lib.LCF_PATH_TC,
+                                                            project_path=lib.LCF_PATH_TC)
+    for key, e in rows.items():
+        print(key, {k: (f"{v:.2e}" if isinstance(v, float) else v) for k, v in e.items()})
+    best = rows[("LCF_GP_F16X3", "LCF_EP_FP64_POLISH", 12)]
+    assert best["alpha"] <= ALPHA_TOL and best["pd"] <= PD_TOL
+    assert rows[("LCF_GP_E4M3", "LCF_EP_FP32", 12)]["alpha"] > ALPHA_TOL
+    # the polish never makes alpha worse, and four deflated vectors are not enough here
+    for gp in ("LCF_GP_F16X3", "LCF_GP_BF16X3", "LCF_GP_F16"):
+        assert rows[(gp, "LCF_EP_FP64_POLISH", 12)]["alpha"] <= rows[(gp, "LCF_EP_FP32", 12)]["alpha"] * 1.5
+    assert rows[("LCF_GP_F16X3", "LCF_EP_FP32", 4)]["alpha"] > ALPHA_TOL

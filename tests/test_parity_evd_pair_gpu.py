@@ -12,7 +12,7 @@ from conftest import gpu_available
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
 
 from synth import REALTIME_256x128x100, SMALL_96x64x32, generate_packet  # noqa: E402
-from test_parity_gpu import (ALPHA_TOL, EIG_TOL, PD_TOL, L, compare, configs, rand_iq)  # noqa: E402
+from test_parity_gpu import (assert_cutoffs, ALPHA_TOL, EIG_TOL, PD_TOL, L, compare, configs, rand_iq)  # noqa: E402
 
 
 def pair_cfg(*a, tc=False, **kw):
@@ -31,7 +31,7 @@ def check(r, soft=False):
           "sweeps", sorted(set(((np.asarray(r["flags"]) >> 8) & 255).tolist())))
     assert r["status"] == lib.LCF_OK, r["flags"]
     assert r["eig_err"] <= EIG_TOL
-    assert np.array_equal(r["k_gpu"], r["k_ora"])
+    assert_cutoffs(r)
     assert r["alpha_err"] <= ALPHA_TOL
     assert r["pd_err"] <= PD_TOL
     if soft:

@@ -7,7 +7,11 @@ Tolerances (stated for the FP32-class path):
   filtered IQ       rel Frobenius error <= 1e-3 (one subset, Eq. 4)
   alpha_k           rel error <= 1e-3
 Hard cutoffs k must match, except when the oracle's own deciding quantity
-has a near-tie (then both answers are correct and the case is reported).
+has a near-tie within 1e-6 relative (then both answers are correct; every
+such flip is counted and printed).
+
+configs() builds the plain FP32 path (CUDA-core Gram and projection, one-CTA
+EVD) unless a test asks for another; the library's defaults are the fast path.
 """
 import numpy as np
 import pytest
@@ -34,6 +38,7 @@ COMMON = ("nz", "nx", "nt", "wz", "wx", "all_ones_window", "support_sigmas", "th
 def configs(nz, nx, nt, wz, wx, **kw):
     lib = L()
     c = lib.lcf_config_default(nz, nx, nt, wz, wx)
+    c.gram_path, c.project_path, c.evd_path = lib.LCF_PATH_SIMT, lib.LCF_PATH_SIMT, lib.LCF_EVD_CTA
     kw.setdefault("thresh_mode", lib.LCF_T_CURVATURE)
     oc = O.OracleConfig(nz, nx, nt, wz, wx)
     oc.support_sigmas = float(c.support_sigmas)
@@ -73,15 +78,23 @@ def check_eigs(lam_g, lam_o):
     return worst
 
 
-TIE_REL = 1e-3   # two cutoffs whose deciding quantities differ by less than this are both correct
+TIE_REL = 1e-6   # two cutoffs whose deciding quantities differ by less than this are both correct
 
 
-def near_tie(ocfg, lam_ora, lam_gpu, k_gpu, k_ora):
+def near_tie(ocfg, lam_ora, lam_gpu, k_gpu, k_ora, iq=None, window=None):
     """True when the oracle's own rule, on eigenvalues that agree within tolerance, could
     equally have picked k_gpu: its deciding quantity has a near-tie between the two cutoffs,
-    and the oracle's rule applied to the GPU eigenvalues returns k_gpu."""
+    and the oracle's rule applied to the GPU eigenvalues returns k_gpu.  Method 4 decides
+    from the data, not the eigenvalues alone: there the oracle's NCC curve of the window
+    (iq, window) must have NCC(k_gpu) within TIE_REL of its minimum NCC(k_ora)."""
     mode = ocfg.thresh_mode if ocfg.thresh_mode != O.T_SIGMOID else ocfg.k_src
     beta = ocfg.beta if ocfg.thresh_mode != O.T_SIGMOID else ocfg.beta_src
+    if mode == O.T_NCC:
+        if iq is None or k_gpu < 1 or k_gpu > ocfg.nt:
+            return False
+        _, curve = O.ncc_curve(iq, ocfg, window)
+        a, b = curve[k_gpu - 1], curve[k_ora - 1]
+        return bool(np.isfinite(a) and abs(a - b) <= TIE_REL * abs(b))
     _, k_on_gpu = O.weights(mode, lam_gpu, beta=beta, k_fixed=ocfg.k_fixed, curv_norm=ocfg.curv_norm)
     if k_on_gpu != k_gpu:
         return False
@@ -102,8 +115,9 @@ def compare(iq, cfg, ocfg, want_gram=True):
     ora = O.filter(iq, ocfg, want_R=want_gram)
     dbg = plan.debug()
     st, flags = plan.status()
+    k_rule = ora.k.copy()   # the oracle rule's own cutoffs
     flips = [int(k) for k in np.nonzero(dbg["k"] != ora.k)[0]]
-    ties = [k for k in flips if near_tie(ocfg, ora.lam[k], dbg["lam"][k], int(dbg["k"][k]), int(ora.k[k]))]
+    ties = [k for k in flips if near_tie(ocfg, ora.lam[k], dbg["lam"][k], int(dbg["k"][k]), int(ora.k[k]), iq, k)]
     if flips and len(ties) == len(flips):
         # every flip is an ambiguous-but-correct cutoff: check the image against the oracle
         # evaluated at the GPU's cutoffs for those windows
@@ -111,7 +125,7 @@ def compare(iq, cfg, ocfg, want_gram=True):
         ko[ties] = dbg["k"][ties]
         ora = O.filter(iq, ocfg, want_R=want_gram, k_override=ko)
     out = {"pd_err": rel_l2(pd, ora.pd), "eig_err": check_eigs(dbg["lam"], ora.lam),
-           "k_gpu": dbg["k"], "k_ora": ora.k, "alpha_err": float(np.max(np.abs(dbg["alpha"] - ora.alpha) /
+           "k_gpu": dbg["k"], "k_ora": k_rule, "alpha_err": float(np.max(np.abs(dbg["alpha"] - ora.alpha) /
                                                                          np.maximum(ora.alpha, 1e-300))),
            "flips": flips, "ties": ties,
            "status": st, "flags": flags, "plan": plan, "ora": ora, "pd": pd, "dbg": dbg, "d_iq": d}
@@ -120,6 +134,14 @@ def compare(iq, cfg, ocfg, want_gram=True):
         out["gram_err"] = max(float(np.linalg.norm(R[k] - ora.R[k]) / np.linalg.norm(ora.R[k]))
                               for k in range(R.shape[0]))
     return out
+
+
+def assert_cutoffs(r):
+    """Hard cutoffs equal the oracle rule's own, except flips certified as near-ties (the
+    oracle's deciding quantity within TIE_REL of its competitor, and the oracle's rule on the
+    GPU's eigenvalues picking the GPU's cutoff); the raw flip count is printed."""
+    print("cutoff flips", len(r["flips"]), r["flips"], "certified near-ties", r["ties"])
+    assert r["flips"] == r["ties"], (r["flips"], r["ties"])
 
 
 # --------------------------------------------------------------- workloads
@@ -132,7 +154,7 @@ def test_small_fixed_k3():
     assert r["status"] == lib.LCF_OK, r["flags"]
     assert r["gram_err"] <= GRAM_TOL
     assert r["eig_err"] <= EIG_TOL
-    assert np.array_equal(r["k_gpu"], r["k_ora"])
+    assert_cutoffs(r)
     assert r["alpha_err"] <= ALPHA_TOL
     assert r["pd_err"] <= PD_TOL
 
@@ -188,7 +210,7 @@ def test_small_all_rules(mode, beta, extra):
     r = compare(iq, cfg, oc, want_gram=False)
     print(mode, {k: r[k] for k in ("pd_err", "eig_err", "alpha_err")})
     assert r["eig_err"] <= EIG_TOL
-    assert np.array_equal(r["k_gpu"], r["k_ora"])
+    assert_cutoffs(r)
     assert r["pd_err"] <= PD_TOL
     # weights are normalised to max 1; soft rules follow lambda^-beta, so components far below
     # 1e-6*lambda_1 (outside the eigenvalue tolerance band) carry beta times their eigenvalue error
@@ -224,7 +246,7 @@ def test_edge_shapes(shape, grid, mode):
     print(shape, {k: r[k] for k in ("pd_err", "eig_err", "gram_err", "alpha_err")})
     assert r["gram_err"] <= GRAM_TOL
     assert r["eig_err"] <= EIG_TOL
-    assert np.array_equal(r["k_gpu"], r["k_ora"])
+    assert_cutoffs(r)
     assert r["pd_err"] <= PD_TOL
 
 
