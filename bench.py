@@ -349,14 +349,15 @@ def main():
     out = torch.empty((NZ, NX), dtype=torch.float32, device=f"cuda:{local}")
     st = torch.cuda.current_stream()
 
-    def plan_for(path):
+    def plan_for(path, **extra):
         # optimized path: tensor-core Gram and projection, CTA-pair EVD; plain path: CUDA cores only
         evd = L.LCF_EVD_PAIR if path == L.LCF_PATH_TC else L.LCF_EVD_CTA
         # the ring is resident before the timed loop: the optimized plan may start each packet's
         # basis prep while the previous packet's kernels run (inputs_ready)
-        return L.Plan.make(NZ, NX, NT, WZ, WX, device=local, thresh_mode=L.LCF_T_CURVATURE, beta=1.0,
-                           gram_path=path, project_path=path, evd_path=evd,
-                           inputs_ready=1 if path == L.LCF_PATH_TC else 0)
+        kw = dict(device=local, thresh_mode=L.LCF_T_CURVATURE, beta=1.0, gram_path=path, project_path=path,
+                  evd_path=evd, inputs_ready=1 if path == L.LCF_PATH_TC else 0)
+        kw.update(extra)
+        return L.Plan.make(NZ, NX, NT, WZ, WX, **kw)
 
     def barrier():
         if dist is not None:
@@ -384,6 +385,12 @@ def main():
 
     path = L.LCF_PATH_TC if args.path == "tc" else L.LCF_PATH_SIMT
     plan = plan_for(path)
+    variants = {}
+    if path == L.LCF_PATH_TC:
+        # the launch shapes as plan_create chose them, then autotuned on the first packet
+        ms_untuned = timed(plan, args.steps, args.warmup)
+        variants["untuned"] = {"value": world * args.steps / (ms_untuned / 1e3), "tuning": plan.tuning().as_dict()}
+        plan.autotune(d_ring[0])
     for i in range(args.warmup):
         plan.filter(d_ring[i % RING], out)
     n_launch0 = plan.launch_count()
@@ -398,6 +405,16 @@ def main():
     plain = plan if path == L.LCF_PATH_SIMT else plan_for(L.LCF_PATH_SIMT)
     ms_plain = ms if plain is plan else timed(plain, args.steps, args.warmup)
     plain_value = world * args.steps / (ms_plain / 1e3)
+
+    if path == L.LCF_PATH_TC:
+        # the same workload as one CUDA graph launch per packet (stream order, no early basis
+        # prep), and with the one-pass fp16 Gram (TF32's significand), each tuned like the headline plan
+        for name, kw in (("graph", {"graph": 1, "inputs_ready": 0}), ("gram_f16", {"gram_precision": L.LCF_GP_F16})):
+            vp = plan_for(path, **kw)
+            vp.autotune(d_ring[0])
+            ms_v = timed(vp, args.steps, args.warmup)
+            variants[name] = {"value": world * args.steps / (ms_v / 1e3), "tuning": vp.tuning().as_dict()}
+            vp.close()
 
     # per-stage device times (CUDA events between the stages on the launch stream)
     plan.profile(True)
@@ -455,7 +472,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "nz": NZ, "nx": NX, "nt": NT, "windows": [WZ, WX],
                        "path": args.path, "l2": f"ring of {RING} packets ({RING * NT * NZ * NX * 8 / 1e6:.0f} MB) > L2",
-                       "parallelism": f"replicas x{world} (independent packets)"},
+                       "parallelism": f"replicas x{world} (independent packets)",
+                       "tuning": plan.tuning().as_dict() if path == L.LCF_PATH_TC else None},
+            "variants": variants,
             "plain_fp32": {"value": plain_value, "unit": "frames/s", "ms_per_step": ms_plain / args.steps},
             "vs_plain": value / plain_value,
             "clocks": clocks, "roofline": roofline, "e2e": e2e,

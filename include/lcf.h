@@ -300,13 +300,13 @@ typedef struct {
   int basis_splits;      /* pixel splits of the global Gram behind the deflation basis */
   int ncc_splits;        /* pixel splits of method 4's band sums                      */
   int evd_cluster;       /* CTAs per window of the distributed EVD (Nt > 128): 4
-                            (Nt <= 224 only) or 8                                    */
+                            (Nt <= 224) or 8 (Nt >= 200)                            */
 } lcf_tuning;
 
 /* The plan's current tuning (host struct).  No synchronisation. */
 lcf_status lcf_plan_get_tuning(const lcf_plan* plan, lcf_tuning* t);
 
-/* Apply a tuning: splits in 1..64, evd_cluster 4 or 8.  Synchronous (waits for
+/* Apply a tuning: splits in 1..64, evd_cluster 4 or 8 as above.  Synchronous (waits for
  * the plan's work, reallocates the partial-sum buffers, drops captured graphs);
  * LCF_EINVAL for values out of range, LCF_ENOMEM. */
 lcf_status lcf_plan_set_tuning(lcf_plan* plan, const lcf_tuning* t);

@@ -102,7 +102,9 @@ extern "C" lcf_status lcf_plan_set_tuning(lcf_plan* P, const lcf_tuning* t) {
   if (!in_range(t->gram_splits) || !in_range(t->simt_gram_splits) || !in_range(t->aug_splits) ||
       !in_range(t->q_splits) || !in_range(t->basis_splits) || !in_range(t->ncc_splits))
     return LCF_EINVAL;
-  if (t->evd_cluster != 8 && !(t->evd_cluster == 4 && P->nt <= 224)) return LCF_EINVAL;
+  // clusters of 8 for the shorter long packets: checked against the oracle from Nt = 200 up; at
+  // Nt = 129 they gave NaN eigenvalues, so 8 is refused below 200
+  if (!(t->evd_cluster == 4 && P->nt <= 224) && !(t->evd_cluster == 8 && P->nt >= 200)) return LCF_EINVAL;
   if (P->tc_T > 1 && t->gram_splits != 1) return LCF_EINVAL;   // tile pairs take whole windows
   int prev = 0;
   cudaGetDevice(&prev);
@@ -196,7 +198,7 @@ extern "C" lcf_status lcf_plan_autotune(lcf_plan* P, const void* d_iq, cudaStrea
       {&lcf_tuning::aug_splits, uses_aug(P), {1, 2, 4, 6, 8, 12, 16, 24, 32}},
       {&lcf_tuning::q_splits, uses_q(P), {1, 2, 4, 6, 8, 12, 16, 24, 32}},
       {&lcf_tuning::ncc_splits, post_uses_ncc(P->cfg), {1, 2, 3, 4, 6, 8, 12}},
-      {&lcf_tuning::evd_cluster, uses_dist(P) && P->nt <= 224, {4, 8}},
+      {&lcf_tuning::evd_cluster, uses_dist(P) && P->nt >= 200 && P->nt <= 224, {4, 8}},
   };
   for (const Knob& kb : knobs) {
     if (st != LCF_OK) break;
