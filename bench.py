@@ -144,10 +144,12 @@ def make_ring(seed0=0):
     return np.stack([generate_packet(REALTIME_256x128x100, seed=seed0 + i) for i in range(RING)])
 
 
-def cpu_oracle_rate(ring, n_packets, nthreads):
+def cpu_oracle_rate(ring, n_packets, nthreads, thresh="curvature"):
     """Oracle packets/s on the host (FP64, OpenMP over windows)."""
     import oracle as O
-    cfg = O.OracleConfig(NZ, NX, NT, WZ, WX, thresh_mode=O.T_CURVATURE, beta=1.0)
+    rule = {"curvature": dict(thresh_mode=O.T_CURVATURE, beta=1.0), "ncc": dict(thresh_mode=O.T_NCC),
+            "median": dict(thresh_mode=O.T_MEDIAN, beta=1.43), "fixed": dict(thresh_mode=O.T_FIXED, k_fixed=8)}[thresh]
+    cfg = O.OracleConfig(NZ, NX, NT, WZ, WX, **rule)
     t0 = time.perf_counter()
     for i in range(n_packets):
         O.filter(ring[i % len(ring)], cfg, nthreads=nthreads)
@@ -213,17 +215,28 @@ def learned_workload(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    # the same capped plan with the network switched off: every window takes method 1 on the
+    # capped spectrum (p_min above 1)
+    off = L.Plan.make(nz, nx, nt, wz, wx, thresh_mode=L.LCF_T_LEARNED, k_src=L.LCF_T_CURVATURE, beta_src=1.0,
+                      max_sweeps=meta["fast_sweeps"], **common)
+    off.set_mlp(net, p_min=1.01)
     with ClockSampler(local) as clk:
         ms_fast = timed(fast)
     ms_conv = timed(conv)
-    db, agree, fb = [], [], 0
-    for i in range(4):
-        a = conv.filter(d_ring[i]).cpu().numpy().astype(np.float64)
-        b = fast.filter(d_ring[i]).cpu().numpy().astype(np.float64)
-        m = a >= a.max() * 1e-3
-        db.append(float(np.mean(np.abs(10 * np.log10(b[m] / a[m])))))
-        agree.append(float(np.mean(conv.debug()["k"] == fast.debug()["k"])))
-        fb += int(np.sum(np.asarray(fast.status()[1]) & L.LCF_WFLAG_FALLBACK != 0))
+    ms_off = timed(off)
+
+    def judge(plan):
+        db, agree, fb = [], [], 0
+        for i in range(4):
+            a = conv.filter(d_ring[i]).cpu().numpy().astype(np.float64)
+            b = plan.filter(d_ring[i]).cpu().numpy().astype(np.float64)
+            m = a >= a.max() * 1e-3
+            db.append(float(np.mean(np.abs(10 * np.log10(b[m] / a[m])))))
+            agree.append(float(np.mean(conv.debug()["k"] == plan.debug()["k"])))
+            fb += int(np.sum(np.asarray(plan.status()[1]) & L.LCF_WFLAG_FALLBACK != 0))
+        return db, agree, fb
+    db, agree, fb = judge(fast)
+    db_off, agree_off, _ = judge(off)
     fast.profile(True)
     timed(fast)
     stages, n = fast.profile_read()
@@ -241,6 +254,10 @@ def learned_workload(args):
             "pd_db_error": {"mean_abs_db": float(np.mean(db)), "max_packet_mean_abs_db": float(np.max(db)),
                             "pixels": "PD >= 1e-3 x max of the method-1 image"},
             "cutoff_agreement": float(np.mean(agree)), "fallback_windows": fb, "windows": 4 * wz * wx,
+            "network_off": {"value": args.steps / (ms_off / 1e3), "unit": "frames/s",
+                            "mean_abs_db": float(np.mean(db_off)), "max_packet_mean_abs_db": float(np.max(db_off)),
+                            "cutoff_agreement": float(np.mean(agree_off)),
+                            "note": "same capped plan, every window method 1 on the capped spectrum"},
             "stage_ms_per_launch": {k: v / max(n, 1) for k, v in stages.items()},
             "training": meta, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -289,9 +306,8 @@ def stream_workload(args):
         b.record(st)
         b.synchronize()
         lat.append(a.elapsed_time(b))
-    plan.profile(True)
-    for i in range(4):
-        plan.filter(d[i * stride:i * stride + nt], one)
+    plan.profile(True)   # four packets of the stream, launched one by one
+    plan.filter_stream(d[:nt + 3 * stride], stride)
     stages, n = plan.profile_read()
     plan.profile(False)
     stc, flags = plan.status()
@@ -312,6 +328,42 @@ def stream_workload(args):
     return 0
 
 
+def studies_workload(args):
+    """The paper's image-quality studies re-run on a synthetic sequence whose vessel masks are
+    known (180x180 px, packets of 50 frames every 5, tissue motion that grows across the field
+    of view): maximum achievable CR / CNR per rule and subset grid over each rule's factor
+    sweep, against packet length, and the GPU time per packet; not a throughput benchmark."""
+    import torch
+    import paper_2405_11105_b300 as L
+    from paper_2405_11105_b300 import studies as S
+    from synth import Recipe, generate_frames
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+
+    def recipe(nt):
+        return Recipe(180, 180, nt, n_vessels=6, width_px=(3.0, 8.0), phi_rad=(0.1, 0.8), tbr_db=45.0,
+                      noise_db=-60.0, motion_amp_px=1.0, motion_period=40.0, motion_lateral_gain=(0.1, 2.0))
+
+    def make(nt):
+        f, t = generate_frames(recipe(nt), nt + 5 * 9, seed=21, return_truth=True)
+        return f, t["blood_mask"]
+    frames, mask = make(50)
+    base = S.score_sequence(frames, mask, 50, 5, (1, 1), L.LCF_T_NONE, 1.0, device=local)
+    rules = (L.LCF_T_CURVATURE, L.LCF_T_MEDIAN, L.LCF_T_NCC, L.LCF_T_SIGMOID, L.LCF_T_ADAPTIVE_SOFT)
+    subsets = S.subset_study(frames, mask, 50, 5, grids=((1, 1), (2, 2), (3, 3), (8, 8)), rules=rules, device=local)
+    sizes = S.packet_size_study(make, nts=(50, 70, 90), grids=((1, 1), (3, 3)), device=local)
+    best = subsets[(S.RULE_NAMES[L.LCF_T_CURVATURE], "3x3")]
+    line = {"metric": "maximum achievable CNR (dB), method 1, 3x3 subsets (synthetic 180x180 px, Nt=50, stride 5)",
+            "value": best["cnr"], "unit": "dB", "higher_is_better": True, "n_gpus": 1, "impl": "ours",
+            "data": "synthetic", "config": {"workload": "paper's quality studies on a synthetic sequence "
+                                                       "(6 vessels, 45 dB, 1 px motion growing 0.1-2x across x)"},
+            "unfiltered": base,
+            "subsets": [{"rule": k[0], "grid": k[1], **v} for k, v in subsets.items()],
+            "packet_sizes": [{"nt": k[0], "grid": k[1], **v} for k, v in sizes.items()]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,10 +372,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="tc", choices=["simt", "tc"])
     ap.add_argument("--cpu-packets", type=int, default=10)
-    ap.add_argument("--workload", default="realtime", choices=["realtime", "learned", "stream"],
+    ap.add_argument("--workload", default="realtime", choices=["realtime", "learned", "stream", "studies"],
                     help="realtime: 256x128x100 8x8 (the headline); learned: 384x256x128 16x16 with the learned "
-                         "cutoff; stream: 512x256x200 16x16, sliding packets (stride 50) as one CUDA graph")
+                         "cutoff; stream: 512x256x200 16x16, sliding packets (stride 50) as one CUDA graph; "
+                         "studies: the paper's CR/CNR studies on a synthetic sequence")
     ap.add_argument("--stream-packets", type=int, default=64)
+    # options of the headline workload's optimized plan (defaults: the library's)
+    ap.add_argument("--thresh", default="curvature", choices=["curvature", "ncc", "median", "fixed"],
+                    help="thresholding rule: method 1 (default), method 4, method 3 (beta 1.43), fixed k = 8")
+    ap.add_argument("--gram-precision", default="f16x3", choices=["f16x3", "bf16x3", "f16", "bf16", "e4m3"])
+    ap.add_argument("--evd-precision", default="fp32", choices=["fp32", "polish"])
+    ap.add_argument("--project-form", default="identity", choices=["identity", "subtract"])
+    ap.add_argument("--deflate", type=int, default=0)
+    ap.add_argument("--no-variants", action="store_true", help="skip the variant arms (untuned, graph, one-pass fp16)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -332,6 +393,8 @@ def main():
         return learned_workload(args)
     if args.workload == "stream":
         return stream_workload(args)
+    if args.workload == "studies":
+        return studies_workload(args)
 
     import numpy as np
     import torch
@@ -349,13 +412,23 @@ def main():
     out = torch.empty((NZ, NX), dtype=torch.float32, device=f"cuda:{local}")
     st = torch.cuda.current_stream()
 
+    rule = {"curvature": dict(thresh_mode=L.LCF_T_CURVATURE, beta=1.0), "ncc": dict(thresh_mode=L.LCF_T_NCC),
+            "median": dict(thresh_mode=L.LCF_T_MEDIAN, beta=1.43),
+            "fixed": dict(thresh_mode=L.LCF_T_FIXED, k_fixed=8)}[args.thresh]
+    options = dict(gram_precision=getattr(L, "LCF_GP_" + args.gram_precision.upper()),
+                   evd_precision=L.LCF_EP_FP64_POLISH if args.evd_precision == "polish" else L.LCF_EP_FP32,
+                   project_form=L.LCF_PF_SUBTRACT if args.project_form == "subtract" else L.LCF_PF_IDENTITY,
+                   deflate=args.deflate)
+
     def plan_for(path, **extra):
         # optimized path: tensor-core Gram and projection, CTA-pair EVD; plain path: CUDA cores only
         evd = L.LCF_EVD_PAIR if path == L.LCF_PATH_TC else L.LCF_EVD_CTA
         # the ring is resident before the timed loop: the optimized plan may start each packet's
         # basis prep while the previous packet's kernels run (inputs_ready)
-        kw = dict(device=local, thresh_mode=L.LCF_T_CURVATURE, beta=1.0, gram_path=path, project_path=path,
-                  evd_path=evd, inputs_ready=1 if path == L.LCF_PATH_TC else 0)
+        kw = dict(device=local, gram_path=path, project_path=path, evd_path=evd,
+                  inputs_ready=1 if path == L.LCF_PATH_TC else 0, **rule)
+        if path == L.LCF_PATH_TC:
+            kw.update(options)
         kw.update(extra)
         return L.Plan.make(NZ, NX, NT, WZ, WX, **kw)
 
@@ -386,10 +459,11 @@ def main():
     path = L.LCF_PATH_TC if args.path == "tc" else L.LCF_PATH_SIMT
     plan = plan_for(path)
     variants = {}
-    if path == L.LCF_PATH_TC:
+    if path == L.LCF_PATH_TC and not args.no_variants:
         # the launch shapes as plan_create chose them, then autotuned on the first packet
         ms_untuned = timed(plan, args.steps, args.warmup)
         variants["untuned"] = {"value": world * args.steps / (ms_untuned / 1e3), "tuning": plan.tuning().as_dict()}
+    if path == L.LCF_PATH_TC:
         plan.autotune(d_ring[0])
     for i in range(args.warmup):
         plan.filter(d_ring[i % RING], out)
@@ -406,7 +480,7 @@ def main():
     ms_plain = ms if plain is plan else timed(plain, args.steps, args.warmup)
     plain_value = world * args.steps / (ms_plain / 1e3)
 
-    if path == L.LCF_PATH_TC:
+    if path == L.LCF_PATH_TC and not args.no_variants:
         # the same workload as one CUDA graph launch per packet (stream order, no early basis
         # prep), and with the one-pass fp16 Gram (TF32's significand), each tuned like the headline plan
         for name, kw in (("graph", {"graph": 1, "inputs_ready": 0}), ("gram_f16", {"gram_precision": L.LCF_GP_F16})):
@@ -470,7 +544,10 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if path == L.LCF_PATH_SIMT else "f32 (Gram: split-f16 tensor core, f32 accumulate)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nz": NZ, "nx": NX, "nt": NT, "windows": [WZ, WX],
+            "config": {"workload": WORKLOAD if args.thresh == "curvature" else WORKLOAD.replace(
+                "adaptive curvature threshold", f"rule {args.thresh}"), "nz": NZ, "nx": NX, "nt": NT, "windows": [WZ, WX],
+                       "options": {"gram_precision": args.gram_precision, "evd_precision": args.evd_precision,
+                                   "project_form": args.project_form, "deflate": args.deflate or "default"},
                        "path": args.path, "l2": f"ring of {RING} packets ({RING * NT * NZ * NX * 8 / 1e6:.0f} MB) > L2",
                        "parallelism": f"replicas x{world} (independent packets)",
                        "tuning": plan.tuning().as_dict() if path == L.LCF_PATH_TC else None},
@@ -481,7 +558,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps, "status": L.lcf_status_string(st_code)}
     if rank == 0:
         nthreads = os.cpu_count() or 1
-        rate, dt = cpu_oracle_rate(ring, args.cpu_packets, nthreads)
+        rate, dt = cpu_oracle_rate(ring, args.cpu_packets, nthreads, args.thresh)
         line["cpu_baseline"] = {"value": rate, "unit": "frames/s", "cores": nthreads, "kind": "oracle",
                                 "sample": f"{args.cpu_packets} full packets of the workload ({dt:.1f} s)"}
         print(json.dumps(line), flush=True)

@@ -130,6 +130,18 @@ enum { LCF_GP_F16X3 = 0, LCF_GP_BF16X3 = 1, LCF_GP_F16 = 2, LCF_GP_BF16 = 3, LCF
  *                      roundoff of lambda_1 (60 dB tissue-to-blood, long packets). */
 enum { LCF_EP_FP32 = 0, LCF_EP_FP64_POLISH = 1 };
 
+/* How the power Doppler is formed from the eigen-decomposition (both equal Eq. 4
+ * for hard weights, Eq. 5 being the paper's subtractive form of it).
+ *   LCF_PF_IDENTITY  PD_k(p) = (1/Nt) sum_c wt_c^2 |(C_w V)(p, c)|^2 over the kept
+ *                    columns: one GEMM per window (default; every rule)
+ *   LCF_PF_SUBTRACT  Eq. 5, C-hat = C_w - C_w V_k V_k^H: PD_k(p) = (1/Nt)(||C_w(p,:)||^2
+ *                    - ||C_w(p,:) Q||^2), Q the k rejected eigenvectors
+ *                    re-orthonormalised in double-float, every sum double-float,
+ *                    alpha (Eq. 13) from the same sums.  Hard rules only (fixed,
+ *                    methods 1-4, learned, none); its cost grows with k instead of
+ *                    Nt - k. */
+enum { LCF_PF_IDENTITY = 0, LCF_PF_SUBTRACT = 1 };
+
 typedef struct {
   int nz, nx, nt;          /* packet size: Nz axial x Nx lateral x Nt frames      */
   int wz, wx;              /* window grid; Nd = wz*wx subsets                     */
@@ -166,6 +178,7 @@ typedef struct {
                               stages are launched one by one.  Not combined
                               with inputs_ready's early basis prep, nor used
                               while stage profiling is on                        */
+  int project_form;        /* LCF_PF_*: how PD is formed after the EVD            */
   int deflate;             /* slow-time vectors deflated from every pixel before
                               the Gram and projection products, 1..16 (< Nt);
                               0: clamp(Nt/4, 1, 4).  The deflated part is summed

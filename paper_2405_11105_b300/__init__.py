@@ -26,6 +26,7 @@ LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
 LCF_EVD_CTA, LCF_EVD_PAIR = 0, 1
 LCF_GP_F16X3, LCF_GP_BF16X3, LCF_GP_F16, LCF_GP_BF16, LCF_GP_E4M3 = range(5)
 LCF_EP_FP32, LCF_EP_FP64_POLISH = 0, 1
+LCF_PF_IDENTITY, LCF_PF_SUBTRACT = 0, 1
 STAGES = ("prep", "gram", "assemble", "evd", "project")
 EVD_PHASES = ("subspace", "qr", "congruence", "convert_q", "jacobi", "sort_phase", "rule", "weights")
 
@@ -39,7 +40,7 @@ class lcf_config(C.Structure):
                 ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int),
                 ("evd_path", C.c_int), ("inputs_ready", C.c_int),
                 ("gram_precision", C.c_int), ("evd_precision", C.c_int), ("graph", C.c_int),
-                ("deflate", C.c_int)]
+                ("project_form", C.c_int), ("deflate", C.c_int)]
 
 
 class lcf_tuning(C.Structure):

@@ -224,11 +224,12 @@ constexpr int APR = 4;   // pixels per FP32 partial sum there
 // Augmented columns Y[i][a] = sum_p g^2 conj(x_p(i)) a_p(a), i < nt + qrows, a < d
 // (rows i < nt give U, rows nt.. give Q; qrows = d, or 0 when Q comes from the
 // exact coefficient kernel).  grid: x = pixel split, y = window.
-__global__ void __launch_bounds__(256)
-gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl,
-                const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
-                int nsplit, int qrows, double2* __restrict__ aug) {
-  extern __shared__ float2 Xs[];   // [ACH][nt + d]: x_p, pixel-major
+// DM: the largest deflation depth of the instance (its accumulators are sized for it).
+template <int DM>
+__device__ __forceinline__ void gram_aug_body(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl,
+                                              const Box* __restrict__ boxes, const float* __restrict__ gz,
+                                              const float* __restrict__ gx, int nsplit, int qrows,
+                                              double2* __restrict__ aug, float2* Xs) {
   __shared__ float g2s[ACH];
   __shared__ int pix[ACH];         // linear pixel index of the step's pixels (-1: past the range)
   const int k = blockIdx.y, s = blockIdx.x;
@@ -240,9 +241,9 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
   const int npix = nz * nx;
   const float* gzk = gz + (size_t)k * nz;
   const float* gxk = gx + (size_t)k * nx;
-  // outputs per thread: nout = (nt + d) * d <= (kEvdNmax + kDeflateMax) * kDeflateMax over 256 threads
-  constexpr int OPT = ((kEvdNmax + kDeflateMax) * kDeflateMax + 255) / 256;
-  static_assert(OPT * 256 >= (kEvdNmax + kDeflateMax) * kDeflateMax, "augmented outputs per thread");
+  // outputs per thread: nout = (nt + d) * d <= (kEvdNmax + DM) * DM over 256 threads
+  constexpr int OPT = ((kEvdNmax + DM) * DM + 255) / 256;
+  static_assert(OPT * 256 >= (kEvdNmax + DM) * DM, "augmented outputs per thread");
   float2 acc[OPT];
   df hr[OPT], hi[OPT];
 #pragma unroll
@@ -313,6 +314,24 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
   }
 }
 
+template <int DM>
+__global__ void __launch_bounds__(256, DM > 4 ? 1 : 2)
+gram_aug_kernel_t(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, const Box* __restrict__ boxes,
+                  const float* __restrict__ gz, const float* __restrict__ gx, int nsplit, int qrows,
+                  double2* __restrict__ aug) {
+  extern __shared__ float2 Xs[];   // [ACH][nt + d]: x_p, pixel-major
+  gram_aug_body<DM>(xa, nz, nx, nt, nd_defl, boxes, gz, gx, nsplit, qrows, aug, Xs);
+}
+
+// the depth-4 instance under a plain name, for the allocation-free entry point (default depths)
+__global__ void __launch_bounds__(256)
+gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, const Box* __restrict__ boxes,
+                const float* __restrict__ gz, const float* __restrict__ gx, int nsplit, int qrows,
+                double2* __restrict__ aug) {
+  extern __shared__ float2 Xs[];
+  gram_aug_body<4>(xa, nz, nx, nt, nd_defl, boxes, gz, gx, nsplit, qrows, aug, Xs);
+}
+
 size_t gram_aug_smem_bytes(int nt, int nd_defl) { return (size_t)ACH * (nt + nd_defl) * sizeof(float2); }
 
 // the augmented-column kernel's staging passes 48 KB beyond Nt = 188
@@ -323,6 +342,12 @@ __global__ void gram_assemble_kernel(const double2* __restrict__ part, const dou
 cudaError_t gram_simt_configure() {
   cudaError_t e = cudaFuncSetAttribute(gram_aug_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_aug_kernel_t<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_aug_kernel_t<kDeflateMax>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gram_aug_smem_bytes(kEvdNmax, kDeflateMax));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(gram_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gram_assemble_smem_bytes(kEvdNmax, kDeflateMax));
@@ -330,9 +355,14 @@ cudaError_t gram_simt_configure() {
 
 cudaError_t launch_gram_aug(const lcf_plan* P, cudaStream_t st, bool with_q) {
   dim3 grid(P->aug_nsplit, P->nd);
-  gram_aug_kernel<<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
-      P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit,
-      with_q ? P->ndefl : 0, P->ws.gaug);
+  if (P->ndefl <= 4)
+    gram_aug_kernel_t<4><<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
+        P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit,
+        with_q ? P->ndefl : 0, P->ws.gaug);
+  else
+    gram_aug_kernel_t<kDeflateMax><<<grid, 256, gram_aug_smem_bytes(P->nt, P->ndefl), st>>>(
+        P->ws.xa, P->cfg.nz, P->cfg.nx, P->nt, P->ndefl, P->ws.box, P->ws.gz, P->ws.gx, P->aug_nsplit,
+        with_q ? P->ndefl : 0, P->ws.gaug);
   return counted(P);
 }
 

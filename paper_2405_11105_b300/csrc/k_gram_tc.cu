@@ -731,7 +731,8 @@ static void launch_gram_tc_gp(const lcf_plan* P, cudaStream_t st) {
   if (P->tc_T > 1) {
     dim3 gb(P->tc_T * P->tc_T, P->nd);
     gram_tcb_kernel<GP><<<gb, TG_THREADS, gram_tcb_smem_bytes(P->tc_tb), st>>>(
-        P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc, P->ws.err);
+        P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc,
+        P->ws.err);
   } else {
     dim3 grid(P->tc_nsplit, P->nd);
     gram_tc_kernel<GP><<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(

@@ -72,6 +72,9 @@ static lcf_status validate(const lcf_config* c) {
   if (c->gram_path != LCF_PATH_TC && c->gram_precision != LCF_GP_F16X3) return LCF_EINVAL;
   if (c->evd_precision < LCF_EP_FP32 || c->evd_precision > LCF_EP_FP64_POLISH) return LCF_EINVAL;
   if (c->graph < 0 || c->graph > 1) return LCF_EINVAL;
+  if (c->project_form < LCF_PF_IDENTITY || c->project_form > LCF_PF_SUBTRACT) return LCF_EINVAL;
+  if (c->project_form == LCF_PF_SUBTRACT && (c->thresh_mode == LCF_T_SIGMOID || c->thresh_mode == LCF_T_ADAPTIVE_SOFT))
+    return LCF_EINVAL;   // the subtractive form needs 0/1 weights
   if (c->deflate < 0 || c->deflate > kDeflateMax || (c->deflate > 0 && c->deflate >= c->nt)) return LCF_EINVAL;
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
@@ -129,7 +132,8 @@ static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
                   w.flags, w.W, w.pw, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.mlp_dbg, w.evd_B, w.evd_vh, w.evd_t,
                   w.evd_scale, w.iq_stage, w.pd_stage, w.phi_alt, w.xmax_alt, w.gglob_async, w.post_rq,
-                  w.post_pv, w.post_isig, w.post_band};
+                  w.post_pv, w.post_isig, w.post_band, w.sub_qhi, w.sub_qlo, w.sub_off, w.sub_pdk,
+                  w.sub_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -245,6 +249,22 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = dalloc(&w.post_isig, nd * nt, &tot);
     if (e == cudaSuccess) e = dalloc(&w.post_band, post_band_count(P), &tot);
   }
+  if (cfg->project_form == LCF_PF_SUBTRACT) {
+    std::vector<long long> off(nd);
+    long long tot_px = 0;
+    for (size_t k = 0; k < nd; ++k) {
+      off[k] = tot_px;
+      tot_px += (long long)(P->boxes[k].z1 - P->boxes[k].z0) * (P->boxes[k].x1 - P->boxes[k].x0);
+    }
+    const int ns = (2 * P->sm_count + P->nd - 1) / P->nd;   // about two CTAs per SM in all
+    P->sub_nsplit = ns < 1 ? 1 : (ns > 64 ? 64 : ns);
+    if (e == cudaSuccess) e = dalloc(&w.sub_qhi, nd * nt * nt, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.sub_qlo, nd * nt * nt, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.sub_off, nd, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.sub_pdk, (size_t)tot_px, &tot);
+    if (e == cudaSuccess) e = dalloc(&w.sub_part, nd * P->sub_nsplit, &tot);
+    if (e == cudaSuccess) e = cudaMemcpy(w.sub_off, off.data(), nd * sizeof(long long), cudaMemcpyHostToDevice);
+  }
   std::vector<int> toff, twin;
   if (cfg->project_path == LCF_PATH_TC) {
     project_tc_tiles(P, &P->ptiles_z, &P->ptiles_x, toff, twin);
@@ -346,7 +366,8 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   else LCF_CUDA(launch_evd(P, st));
   LCF_CUDA(launch_post(P, st));   // FP64-class polish, method 4 (no launch otherwise)
   LCF_MARK(LCF_STAGE_PROJECT);
-  if (c.project_path == LCF_PATH_TC) LCF_CUDA(launch_project_tc(P, out, st));
+  if (c.project_form == LCF_PF_SUBTRACT) LCF_CUDA(launch_project_subtract(P, iq, out, st));
+  else if (c.project_path == LCF_PATH_TC) LCF_CUDA(launch_project_tc(P, out, st));
   else LCF_CUDA(launch_project_simt(P, iq, out, st));
   LCF_MARK(LCF_NSTAGES);
   if (P->profiling) ++P->prof_calls;
@@ -604,9 +625,12 @@ extern "C" lcf_status lcf_filter_stream(lcf_plan* P, const void* d_frames, int n
   DeviceGuard g(P->device);
   const int npk = (n_frames - P->nt) / stride + 1;
   const float2* fr = (const float2*)d_frames;
+  auto stream_packet = [&](int i, cudaStream_t s_) {
+    return run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, s_);
+  };
   if (P->profiling) {   // stage events need the packets launched one by one
     for (int i = 0; i < npk; ++i) {
-      lcf_status s = run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, stream);
+      lcf_status s = stream_packet(i, stream);
       if (s != LCF_OK) return s;
     }
   } else {
@@ -623,8 +647,7 @@ extern "C" lcf_status lcf_filter_stream(lcf_plan* P, const void* d_frames, int n
       const long long l0 = P->launches;
       LCF_CUDA(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
       lcf_status s = LCF_OK;
-      for (int i = 0; i < npk && s == LCF_OK; ++i)
-        s = run_packet(P, fr + (size_t)i * stride * P->npix, d_out_pd + (size_t)i * P->npix, P->cap_stream);
+      for (int i = 0; i < npk && s == LCF_OK; ++i) s = stream_packet(i, P->cap_stream);
       cudaGraph_t gr = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &gr);
       P->sg_launches = P->launches - l0;

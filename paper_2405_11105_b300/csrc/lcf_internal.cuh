@@ -107,6 +107,12 @@ struct Workspace {
   float2* post_pv = nullptr;  // [nd][kDeflateMax][nt] Phi^T V
   float* post_isig = nullptr; // [nd][nt] 1 / sigma_i
   double* post_band = nullptr;  // [nd][ncc_nsplit][nt][10] magnitude-Gram band partials
+  // subtractive reconstruction (Eq. 5, cfg.project_form = LCF_PF_SUBTRACT; k_subtract.cu)
+  float2* sub_qhi = nullptr;  // [nd][nt][nt] orthonormalised rejected columns, high words
+  float2* sub_qlo = nullptr;  // ... low words
+  long long* sub_off = nullptr;  // [nd] offset of each window's box in sub_pdk
+  float* sub_pdk = nullptr;   // [sum of box pixels] PD_k of every window's pixels
+  double* sub_part = nullptr; // [nd][sub_nsplit] sums of PD_k
   // host-call staging
   float2* iq_stage = nullptr; // [2][nt][nz][nx] device copies for lcf_filter_host(_async)
   float* pd_stage = nullptr;  // [2][nz][nx]
@@ -134,6 +140,7 @@ struct lcf_plan {
   float mlp_pmin = 0.f; // confidence below which the learned rule falls back to k_src
   int ncc_nsplit = 1;   // pixel splits per window of method 4's band sums
   int evd_cluster = 0;  // CTAs per window of the distributed EVD (Nt > 128)
+  int sub_nsplit = 1;   // pixel splits per window of the subtractive projection
   int sm_count = 0;
   std::vector<lcf::Box> boxes;
   lcf::Workspace ws;
@@ -317,6 +324,8 @@ cudaError_t post_configure();
 cudaError_t launch_post(const lcf_plan* P, cudaStream_t st);
 void plan_drop_graphs(lcf_plan* P);
 lcf_status packet_once(lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
+cudaError_t launch_project_subtract(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
+size_t sub_prep_smem_bytes(int n);
 int evd_dist_cluster(int nt);
 size_t evd_dist_smem_bytes(int nt, int C);
 

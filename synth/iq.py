@@ -11,6 +11,8 @@ these stand in for them; sizes follow the workloads the library is timed on):
   3 px (speckle), normalised to unit mean power over the image; every frame
   is the same field shifted axially by d(t) pixels with an exact Fourier
   sub-pixel shift, then cropped (the padding keeps the shift from wrapping);
+  optionally each column x moves by d(t) g(x) with g a lateral ramp (motion
+  that differs across the field of view, as in vivo);
 * blood: straight vessels (pixels within width/2 of a line at a random angle
   and offset); per pixel a unit-variance complex AR(1) process
   b_t = rho*b_{t-1} + sqrt(1-rho^2)*n_t (rho = 0.99, scatterer decorrelation)
@@ -42,6 +44,9 @@ class Recipe:
     motion_period: float | None = None    # frames; None -> nt
     jitter_px: float = 0.0                # per-frame N(0, jitter^2) axial jitter
     rho: float = 0.99
+    # lateral heterogeneity of the motion: column x moves by d(t) * g(x), g rising linearly from
+    # motion_lateral_gain[0] at x = 0 to [1] at x = nx - 1 (None: every column moves by d(t))
+    motion_lateral_gain: tuple | None = None
 
 
 # Workloads, named by what they are.
@@ -124,8 +129,13 @@ def generate_frames(recipe: Recipe, n_frames: int, seed: int = 0, return_truth: 
     inn = np.sqrt(1.0 - rho * rho)
 
     out = np.empty((n_frames, nz, nx), np.complex64)
+    if recipe.motion_lateral_gain is not None:   # per-column gain over the padded width
+        g0, g1 = recipe.motion_lateral_gain
+        gx = g0 + (g1 - g0) * np.clip((np.arange(xp) - pad_x) / max(nx - 1, 1), 0.0, 1.0)
+    else:
+        gx = np.ones(xp)
     for f in range(n_frames):
-        shifted = np.fft.ifft(Fz * np.exp(-2j * np.pi * kz * d[f]), axis=0)
+        shifted = np.fft.ifft(Fz * np.exp(-2j * np.pi * kz * d[f] * gx[None, :]), axis=0)
         frame = shifted[pad_z:pad_z + nz, pad_x:pad_x + nx].copy()
         flat = frame.reshape(-1)
         for v in range(len(masks)):

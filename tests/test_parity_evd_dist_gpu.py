@@ -213,3 +213,15 @@ def test_stress_precision_study(stress_oracle):
     for gp in ("LCF_GP_F16X3", "LCF_GP_BF16X3", "LCF_GP_F16"):
         assert rows[(gp, "LCF_EP_FP64_POLISH", 12)]["alpha"] <= rows[(gp, "LCF_EP_FP32", 12)]["alpha"] * 1.5
     assert rows[("LCF_GP_F16X3", "LCF_EP_FP32", 4)]["alpha"] > ALPHA_TOL
+
+
+def test_stress_subtractive_form(stress_oracle):
+    """Eq. 5 with double-float sums on the precision-stress packet: with 12 deflated vectors
+    (for the cutoffs) and the FP32 eigen-decomposition, PD and alpha meet 1e-3."""
+    from test_parity_gpu import ALPHA_TOL, PD_TOL
+    lib = L()
+    errs = stress_errors(stress_oracle, deflate=12, project_form=lib.LCF_PF_SUBTRACT,
+                         gram_path=lib.LCF_PATH_TC, project_path=lib.LCF_PATH_TC)
+    print(errs)
+    assert errs["status"] == lib.LCF_OK and errs["flips"] == errs["ties"]
+    assert errs["alpha"] <= ALPHA_TOL and errs["pd"] <= PD_TOL, errs
