@@ -384,6 +384,8 @@ def main():
     ap.add_argument("--evd-precision", default="fp32", choices=["fp32", "polish"])
     ap.add_argument("--project-form", default="identity", choices=["identity", "subtract"])
     ap.add_argument("--deflate", type=int, default=0)
+    ap.add_argument("--evd", default="pair", choices=["pair", "os"],
+                    help="EVD kernel of the optimized path: two-sided CTA pair or one-sided on the Cholesky factor")
     ap.add_argument("--no-variants", action="store_true", help="skip the variant arms (untuned, graph, one-pass fp16)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -422,7 +424,7 @@ def main():
 
     def plan_for(path, **extra):
         # optimized path: tensor-core Gram and projection, CTA-pair EVD; plain path: CUDA cores only
-        evd = L.LCF_EVD_PAIR if path == L.LCF_PATH_TC else L.LCF_EVD_CTA
+        evd = (L.LCF_EVD_OS if args.evd == "os" else L.LCF_EVD_PAIR) if path == L.LCF_PATH_TC else L.LCF_EVD_CTA
         # the ring is resident before the timed loop: the optimized plan may start each packet's
         # basis prep while the previous packet's kernels run (inputs_ready)
         kw = dict(device=local, gram_path=path, project_path=path, evd_path=evd,
@@ -547,7 +549,8 @@ def main():
             "config": {"workload": WORKLOAD if args.thresh == "curvature" else WORKLOAD.replace(
                 "adaptive curvature threshold", f"rule {args.thresh}"), "nz": NZ, "nx": NX, "nt": NT, "windows": [WZ, WX],
                        "options": {"gram_precision": args.gram_precision, "evd_precision": args.evd_precision,
-                                   "project_form": args.project_form, "deflate": args.deflate or "default"},
+                                   "project_form": args.project_form, "deflate": args.deflate or "default",
+                                   "evd": args.evd},
                        "path": args.path, "l2": f"ring of {RING} packets ({RING * NT * NZ * NX * 8 / 1e6:.0f} MB) > L2",
                        "parallelism": f"replicas x{world} (independent packets)",
                        "tuning": plan.tuning().as_dict() if path == L.LCF_PATH_TC else None},

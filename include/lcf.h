@@ -98,8 +98,14 @@ enum { LCF_PATH_SIMT = 0, LCF_PATH_TC = 1 };
 /* EVD kernels.  LCF_EVD_CTA: one CTA per window holds A and V (plain path).
  * LCF_EVD_PAIR: a two-CTA cluster per window; one CTA runs the Jacobi
  * rotations on A and streams them through distributed shared memory to the
- * other, which accumulates V.  Same arithmetic and tolerances. */
-enum { LCF_EVD_CTA = 0, LCF_EVD_PAIR = 1 };
+ * other, which accumulates V.  Same arithmetic and tolerances.
+ * LCF_EVD_OS: one-sided Jacobi (Hestenes) on the pivoted FP32 Cholesky factor
+ * of the same deflated matrix, one CTA per window with the factor's columns in
+ * registers; the eigenvectors are the converged columns, so no V is
+ * accumulated (Nt <= 128; longer packets take the distributed two-sided
+ * kernel).  Same tolerances; the learned rule needs LCF_EVD_PAIR.
+ * All three: Eq. 2. */
+enum { LCF_EVD_CTA = 0, LCF_EVD_PAIR = 1, LCF_EVD_OS = 2 };
 
 /* Product precision of the tensor-core Gram (gram_path = LCF_PATH_TC; the
  * plain path's products are FP32).  Each weighted component of the deflated

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblcf.so")
  LCF_T_NONE, LCF_T_LEARNED, LCF_T_NCC) = range(9)
 LCF_WFLAG_NOCONV, LCF_WFLAG_DEGENERATE, LCF_WFLAG_FALLBACK, LCF_WFLAG_SWEEP_SHIFT = 1, 2, 4, 8
 LCF_PATH_SIMT, LCF_PATH_TC = 0, 1
-LCF_EVD_CTA, LCF_EVD_PAIR = 0, 1
+LCF_EVD_CTA, LCF_EVD_PAIR, LCF_EVD_OS = 0, 1, 2
 LCF_GP_F16X3, LCF_GP_BF16X3, LCF_GP_F16, LCF_GP_BF16, LCF_GP_E4M3 = range(5)
 LCF_EP_FP32, LCF_EP_FP64_POLISH = 0, 1
 LCF_PF_IDENTITY, LCF_PF_SUBTRACT = 0, 1

@@ -59,7 +59,7 @@ size_t evd_prep_smem_bytes(int n) {
 }
 
 __global__ void __launch_bounds__(ED_THREADS, 1)
-evd_prep_kernel(const double2* __restrict__ Rg, int n, float2* __restrict__ Bg, float2* __restrict__ Vhg,
+evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __restrict__ Bg, float2* __restrict__ Vhg,
                 float2* __restrict__ Tg, double* __restrict__ scale_g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -103,7 +103,7 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, float2* __restrict__ Bg, 
     Ys[e] = (a < n) ? make_float2(re, im) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int it = 0; it < ED_SUBSPACE_ITERS; ++it) {
+  for (int it = 0; it < iters; ++it) {
     for (int e = tid; e < n * m; e += ED_THREADS) {
       const int a = e / m, j = e % m;
       float2 acc = make_float2(0.f, 0.f);
@@ -765,11 +765,15 @@ evd_dist_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, c
   cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
+cudaError_t launch_evd_prep(const lcf_plan* P, cudaStream_t st, int iters) {
+  evd_prep_kernel<<<P->nd, ED_THREADS, evd_prep_smem_bytes(P->nt), st>>>(P->ws.R, P->nt, iters, P->ws.evd_B,
+                                                                         P->ws.evd_vh, P->ws.evd_t, P->ws.evd_scale);
+  return counted(P);
+}
+
 cudaError_t launch_evd_dist(const lcf_plan* P, cudaStream_t st) {
   const lcf_config& c = P->cfg;
-  evd_prep_kernel<<<P->nd, ED_THREADS, evd_prep_smem_bytes(P->nt), st>>>(P->ws.R, P->nt, P->ws.evd_B, P->ws.evd_vh,
-                                                                         P->ws.evd_t, P->ws.evd_scale);
-  cudaError_t e = counted(P);
+  cudaError_t e = launch_evd_prep(P, st, ED_SUBSPACE_ITERS);
   if (e != cudaSuccess) return e;
   EdArgs a;
   a.nt = P->nt; a.nz = c.nz; a.nx = c.nx;

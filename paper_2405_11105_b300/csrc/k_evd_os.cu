@@ -1,0 +1,713 @@
+// k_evd_os.cu — batched Hermitian EVD (Eq. 2) by one-sided Jacobi on a Cholesky
+// factor, one CTA per window (Nt <= 128).
+//
+// The prep kernel of the distributed EVD (k_evd_dist.cu) forms, per window,
+// B = Q^H (R / scale) Q in double-float rounded to fp32, with Q from an FP32
+// subspace iteration and its Householder QR, so the dominant (tissue) directions
+// are split off before any FP32 rotation.  This kernel then
+//   1. factors B = P L L^H P^T in FP32 with diagonal pivoting (Cholesky; a
+//      non-positive pivot ends it and leaves the rest of L zero);
+//   2. runs one-sided Jacobi (Hestenes' method) on the columns of F = P L:
+//      column pairs are rotated until every pair is orthogonal to a relative
+//      tolerance.  B = F F^H = (F J)(F J)^H for every unitary J, so at
+//      convergence each column is an eigenvector of B times the square root of
+//      its eigenvalue (the scheme Veselic and Hari give for a positive definite
+//      matrix; the rotations diagonalise L^H L, which diagonal pivoting makes
+//      closer to diagonal than B);
+//   3. eigenvalue = squared column norm (double-float sum), eigenvector =
+//      column / norm; columns that vanished (numerical rank below Nt) are
+//      replaced by a Gram-Schmidt completion;
+//   4. V = Q U through the compact WY form, sort, thresholding rule, alpha,
+//      phase fix and the projection weights W, as the other EVD kernels.
+// Only the factor's columns are rotated: the eigenvectors come out of it, so a
+// Jacobi step touches Nt x Nt numbers where the two-sided method updates A and V.
+//
+// Layout of the sweeps.  Warp w owns pair slots 4w .. 4w + 3 of the round-robin (circle)
+// ordering, i.e. eight columns, in registers: lane l holds rows l, l + 32, l + 64, l + 96 as
+// packed pairs of rows, so the 2x2 Grams and the rotations run as packed FP32 operations.  A
+// step sums the four slots' partial Grams over the warp (reduce-scatter), forms the rotations
+// (the formulas of the two-sided kernels, ep_rotation2) and applies them; the circle move (tops
+// one slot up, bottoms one slot down, top[1] takes bottom[0], bottom[h-1] takes top[h-1], top[0]
+// stays) is a renaming of registers inside the warp, unrolled over four steps, and only two
+// columns per warp and step pass through shared memory (by step parity, one barrier per step).
+#include <math.h>
+
+#include "evd_common.cuh"
+#include "lcf_internal.cuh"
+
+namespace lcf {
+
+constexpr int EO_THREADS = 512;
+constexpr float EO_TOL = 2.0e-6f;              // relative orthogonality test (cosine of two columns)
+constexpr int EO_SUBSPACE_ITERS = 3;
+
+struct EoArgs {
+  int nt, nz, nx;
+  int thresh_mode;
+  double beta, beta_src;
+  int k_fixed, k_src;
+  int pd_mode, alpha_mode, curv_norm, max_sweeps;
+  int ncp;
+  long long* clk;   // [nd][kEvdPhases + 1] phase-boundary SM clocks (profiling), or null
+};
+
+__host__ __device__ inline size_t eo_align(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct EoLayout {
+  int np, h, lda, m, nw, rp;
+  size_t a, x, perm, iperm, colj, lam, sperm, wts, s0, s1, s2, coef, keep, phs, end;
+};
+
+// a: the matrix (B, then L, then the eigenvector columns U, then V), rows in pivot order;
+// x: the step-parity exchange buffers of the sweeps, later Vh, T, X = Vh^H U and Y = T X
+__host__ __device__ inline EoLayout eo_layout(int n) {
+  EoLayout L;
+  L.np = n + (n & 1);
+  L.h = L.np / 2;
+  L.lda = L.np + 1;
+  L.m = n < kEvdHead ? n : kEvdHead;
+  L.nw = (L.h + 3) / 4;
+  L.rp = (L.np + 63) / 64;   // row pairs per lane (rows l, l + 32, ...)
+  size_t o = 0;
+  L.a = o; o = eo_align(o + (size_t)L.np * L.lda * 8);
+  {
+    const size_t xch = (size_t)2 * 2 * L.nw * L.rp * 32 * 16;
+    const size_t post = ((size_t)L.m * n + (size_t)L.m * L.m + (size_t)2 * L.m * L.np) * 8;
+    L.x = o; o = eo_align(o + (xch > post ? xch : post));
+  }
+  L.perm = o;  o = eo_align(o + (size_t)L.np * 4);
+  L.iperm = o; o = eo_align(o + (size_t)L.np * 4);
+  L.colj = o;  o = eo_align(o + (size_t)L.np * 8);
+  L.lam = o;   o = eo_align(o + (size_t)L.np * 8);   // squared norm by column position
+  L.sperm = o; o = eo_align(o + (size_t)L.np * 4);   // sorted -> column position
+  L.wts = o;   o = eo_align(o + (size_t)L.np * 8);   // lambda sorted (scaled), then weights: lam_s | wts
+  L.s0 = o;    o = eo_align(o + (size_t)L.np * 8);
+  L.s1 = o;    o = eo_align(o + (size_t)L.np * 8);
+  L.s2 = o;    o = eo_align(o + (size_t)L.np * 8);
+  L.coef = o;  o = eo_align(o + (size_t)L.np * 4);
+  L.keep = o;  o = eo_align(o + (size_t)(L.np + 1) * 4);
+  L.phs = o;   o = eo_align(o + (size_t)L.np * 8);
+  L.end = o;
+  return L;
+}
+
+size_t evd_os_smem_bytes(int nt) { return eo_layout(nt).end + (size_t)nt * 8; }   // + lam_s
+
+#define EO_STAMP(b)                                                                   \
+  do {                                                                                \
+    if (g.clk && tid == 0) g.clk[(size_t)k * (kEvdPhases + 1) + (b)] = clock64();      \
+  } while (0)
+
+// ---- one Jacobi step of a warp that owns four pair slots (eight columns) ----
+// Lane l holds rows l, l + 32, l + 64, l + 96 of every column as row pairs (XR = real parts of
+// rows (2i) * 32 + l and (2i + 1) * 32 + l, XI the imaginary parts), so the dot products and the
+// rotations run as packed FP32 pairs.  The circle move shifts tops one slot up and bottoms one
+// slot down; inside the warp that is a renaming of registers: at phase U of a four-step block
+// slot s keeps its top in T*[(s - U) & 3] and its bottom in B*[(s + U) & 3], and only the top of
+// slot 3 and the bottom of slot 0 leave the warp (through shared memory, by step parity).
+struct EoSweepCtx {
+  float4* xt;      // [parity][warp][row pair][lane]: the top leaving slot 3
+  float4* xb;      // [parity][warp][row pair][lane]: the bottom leaving slot 0
+  int nw, h, warp, lane, slast;   // slast: the slot of pair h - 1 in the last warp
+  bool wfirst, wlast;
+};
+
+// 16 partial sums v[4 s + c] (slot s, component c) summed over the warp; lane l receives the total
+// of component ((l >> 1) & 3) of slot (l >> 3)
+__device__ __forceinline__ float eo_reduce_scatter(const float (&v)[16], int lane) {
+  float w8[8], w4[4], w2[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[k] : v[8 + k], keep = hi ? v[8 + k] : v[k];
+    w8[k] = keep + __shfl_xor_sync(~0u, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool hi = lane & 8;
+    const float send = hi ? w8[k] : w8[4 + k], keep = hi ? w8[4 + k] : w8[k];
+    w4[k] = keep + __shfl_xor_sync(~0u, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool hi = lane & 4;
+    const float send = hi ? w4[k] : w4[2 + k], keep = hi ? w4[2 + k] : w4[k];
+    w2[k] = keep + __shfl_xor_sync(~0u, send, 4);
+  }
+  const bool hi = lane & 2;
+  const float w1 = (hi ? w2[1] : w2[0]) + __shfl_xor_sync(~0u, hi ? w2[0] : w2[1], 2);
+  return w1 + __shfl_xor_sync(~0u, w1, 1);
+}
+
+template <int RP, int U>
+__device__ __forceinline__ int eo_step(float2 (&TR)[4][RP], float2 (&TI)[4][RP], float2 (&BR)[4][RP],
+                                       float2 (&BI)[4][RP], const EoSweepCtx& x, int par) {
+  const int lane = x.lane;
+  // ---- the 2x2 Gram of every slot: |top|^2, |bottom|^2, conj(top) bottom
+  float v[16];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int t = (s - U) & 3, b = (s + U) & 3;
+    float2 a2 = make_float2(0.f, 0.f), b2 = a2, gr = a2, gi = a2, gj = a2;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      a2 = __ffma2_rn(TR[t][i], TR[t][i], a2);
+      a2 = __ffma2_rn(TI[t][i], TI[t][i], a2);
+      b2 = __ffma2_rn(BR[b][i], BR[b][i], b2);
+      b2 = __ffma2_rn(BI[b][i], BI[b][i], b2);
+      gr = __ffma2_rn(TR[t][i], BR[b][i], gr);
+      gr = __ffma2_rn(TI[t][i], BI[b][i], gr);
+      gi = __ffma2_rn(TR[t][i], BI[b][i], gi);
+      gj = __ffma2_rn(TI[t][i], BR[b][i], gj);
+    }
+    v[4 * s] = a2.x + a2.y;
+    v[4 * s + 1] = b2.x + b2.y;
+    v[4 * s + 2] = gr.x + gr.y;
+    v[4 * s + 3] = (gi.x + gi.y) - (gj.x + gj.y);
+  }
+  const float tot = eo_reduce_scatter(v, lane);
+  // ---- each group of 8 lanes forms the rotation of slot lane >> 3, then all four are broadcast
+  const int base = lane & 24;
+  const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 2);
+  const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 4), __shfl_sync(~0u, tot, base + 6));
+  float c, dp, dq;
+  float2 st;
+  int rot;
+  ep_rotation2(a, b, gm, EO_TOL, c, st, dp, dq, rot);   // c = 1, st = 0 without a rotation
+  if (4 * x.warp + (lane >> 3) >= x.h) rot = 0;          // slots past h - 1 hold no pair
+  const unsigned rmask = __ballot_sync(~0u, rot);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!((rmask >> (8 * s)) & 1u)) continue;   // warp-uniform
+    const float cs = __shfl_sync(~0u, c, 8 * s), sr = __shfl_sync(~0u, st.x, 8 * s), si = __shfl_sync(~0u, st.y, 8 * s);
+    const int t = (s - U) & 3, bb = (s + U) & 3;
+    // [top bottom] J: top' = c top - conj(st) bottom, bottom' = st top + c bottom
+    const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
+    const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      const float2 xr = TR[t][i], xi = TI[t][i], yr = BR[bb][i], yi = BI[bb][i];
+      TR[t][i] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
+      TI[t][i] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
+      BR[bb][i] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
+      BI[bb][i] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
+    }
+  }
+  // ---- the columns that leave the warp: slot 3's top, slot 0's bottom
+  const int t3 = (3 - U) & 3, b0 = U & 3;
+  if (x.h > 1) {
+    float4* dt = x.xt + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
+    float4* db = x.xb + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      dt[i * 32] = make_float4(TR[t3][i].x, TR[t3][i].y, TI[t3][i].x, TI[t3][i].y);
+      db[i * 32] = make_float4(BR[b0][i].x, BR[b0][i].y, BI[b0][i].x, BI[b0][i].y);
+    }
+  }
+  const int any = __syncthreads_or(rmask != 0u);
+  if (x.h == 1) {   // one pair: nothing moves, but the registers are renamed all the same
+    const int t0 = (0 - U) & 3, bn = (U + 1) & 3;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) { TR[t3][i] = TR[t0][i]; TI[t3][i] = TI[t0][i]; BR[bn][i] = BR[b0][i]; BI[bn][i] = BI[b0][i]; }
+  } else {
+    const int t0 = (0 - U) & 3;
+    // The special slots first, from old values: slot h - 1 takes its own top as bottom (into the
+    // register slot h - 1 reads its bottom from at the next step), slot 0 keeps its top (into the
+    // register slot 3's top left), slot 1 takes slot 0's bottom; with four slots in one warp the
+    // two overlap and slot 0's bottom goes through a temporary.
+    if (x.wfirst && x.wlast && x.slast == 3) {
+      float2 tr[RP], ti[RP];
+#pragma unroll
+      for (int i = 0; i < RP; ++i) { tr[i] = BR[b0][i]; ti[i] = BI[b0][i]; }
+#pragma unroll
+      for (int i = 0; i < RP; ++i) {
+        BR[b0][i] = TR[t3][i]; BI[b0][i] = TI[t3][i];
+        TR[t3][i] = TR[t0][i]; TI[t3][i] = TI[t0][i];
+        TR[t0][i] = tr[i]; TI[t0][i] = ti[i];
+      }
+    } else {
+      if (x.wlast) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (s != x.slast) continue;
+          const int tl = (s - U) & 3, bn = (s + U + 1) & 3;
+#pragma unroll
+          for (int i = 0; i < RP; ++i) { BR[bn][i] = TR[tl][i]; BI[bn][i] = TI[tl][i]; }
+        }
+      }
+      if (x.wfirst) {
+#pragma unroll
+        for (int i = 0; i < RP; ++i) {
+          TR[t3][i] = TR[t0][i]; TI[t3][i] = TI[t0][i];
+          TR[t0][i] = BR[b0][i]; TI[t0][i] = BI[b0][i];
+        }
+      }
+    }
+    // generic receives: slot 0's new top from the previous warp's slot 3, slot 3's new bottom from
+    // the next warp's slot 0 (both land in the register that just left)
+    if (x.warp > 0) {
+      const float4* s = x.xt + (size_t)(par * x.nw + x.warp - 1) * RP * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < RP; ++i) {
+        const float4 q = s[i * 32];
+        TR[t3][i] = make_float2(q.x, q.y);
+        TI[t3][i] = make_float2(q.z, q.w);
+      }
+    }
+    if (4 * x.warp + 3 < x.h - 1) {
+      const float4* s = x.xb + (size_t)(par * x.nw + x.warp + 1) * RP * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < RP; ++i) {
+        const float4 q = s[i * 32];
+        BR[b0][i] = make_float2(q.x, q.y);
+        BI[b0][i] = make_float2(q.z, q.w);
+      }
+    }
+  }
+  return any;
+}
+
+template <int RP>
+__global__ void __launch_bounds__(EO_THREADS, 1)
+evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, const float2* __restrict__ Tg,
+              const double* __restrict__ scale_g, const Box* __restrict__ boxes, EoArgs g,
+              double* __restrict__ lam_out, float2* __restrict__ V_out, float* __restrict__ wt_out,
+              int* __restrict__ kcut_out, float* __restrict__ alpha_out, int* __restrict__ flags_out,
+              float2* __restrict__ W_out, int* __restrict__ ncol_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = blockIdx.x, n = g.nt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
+  const EoLayout L = eo_layout(n);
+  const int np = L.np, h = L.h, lda = L.lda, m = L.m;
+  float2* A = reinterpret_cast<float2*>(smem + L.a);
+  int* perm = reinterpret_cast<int*>(smem + L.perm);
+  int* iperm = reinterpret_cast<int*>(smem + L.iperm);
+  float2* colj = reinterpret_cast<float2*>(smem + L.colj);
+  double* lam = reinterpret_cast<double*>(smem + L.lam);
+  int* sperm = reinterpret_cast<int*>(smem + L.sperm);
+  double* wts = reinterpret_cast<double*>(smem + L.wts);
+  double* s0 = reinterpret_cast<double*>(smem + L.s0);
+  double* s1 = reinterpret_cast<double*>(smem + L.s1);
+  double* s2 = reinterpret_cast<double*>(smem + L.s2);
+  float* coef = reinterpret_cast<float*>(smem + L.coef);
+  int* keep = reinterpret_cast<int*>(smem + L.keep);
+  float2* phs = reinterpret_cast<float2*>(smem + L.phs);
+  double* lam_s = reinterpret_cast<double*>(smem + L.end);
+  const double scale = scale_g[k];
+
+  if (!(scale > 0.0)) {   // degenerate window (zero Gram): the empty result
+    for (int e = tid; e < n * n; e += nthr) V_out[(size_t)k * n * n + e] = make_float2(e / n == e % n, 0.f);
+    for (int e = tid; e < n * g.ncp; e += nthr) W_out[(size_t)k * n * g.ncp + e] = make_float2(0.f, 0.f);
+    for (int i = tid; i < n; i += nthr) {
+      lam_out[(size_t)k * n + i] = 0.0;
+      wt_out[(size_t)k * n + i] = 0.f;
+    }
+    if (tid == 0) {
+      kcut_out[k] = 0; alpha_out[k] = 0.f; ncol_out[k] = 0;
+      flags_out[k] = LCF_WFLAG_DEGENERATE;
+    }
+    return;
+  }
+  EO_STAMP(3);
+
+  // ---------------- pivoted Cholesky of B in FP32, lower triangle in place
+  {
+    const float2* B = Bg + (size_t)k * n * n;
+    for (int i = warp; i < n; i += nthr / 32)
+      for (int c = lane; c <= i; c += 32) A[(size_t)i * lda + c] = B[(size_t)i * n + c];
+    for (int r = tid; r < np; r += nthr) perm[r] = r;
+  }
+  __shared__ int sh_piv, sh_rank;
+  __shared__ float sh_pd;
+  if (tid == 0) sh_rank = n;
+  __syncthreads();
+  float first = 0.f;
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {   // largest remaining diagonal entry, ties to the lower index
+      float best = -INFINITY;
+      int bi = 0x7fffffff;
+      for (int i = j + lane; i < n; i += 32) {
+        const float d = A[(size_t)i * lda + i].x;
+        if (d > best) { best = d; bi = i; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const float ob = __shfl_xor_sync(~0u, best, o);
+        const int oi = __shfl_xor_sync(~0u, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { sh_piv = bi; sh_pd = best; }
+    }
+    __syncthreads();
+    const int p = sh_piv;
+    const float pd = sh_pd;
+    if (j == 0) first = pd;
+    if (!(pd > first * 1e-30f) || !isfinite(pd)) {   // numerical rank j: the rest of L stays zero
+      if (tid == 0) sh_rank = j;
+      break;
+    }
+    // symmetric interchange of j and p in the lower triangle (entry (c, j) of the interchanged
+    // matrix for c > j, L's rows j and p for c < j), fused with the scaling of column j
+    const float inv = ep_rsqrt(pd);
+    for (int c = tid; c < n; c += nthr) {
+      if (c < j) {
+        if (p != j) {
+          const float2 t = A[(size_t)j * lda + c];
+          A[(size_t)j * lda + c] = A[(size_t)p * lda + c];
+          A[(size_t)p * lda + c] = t;
+        }
+      } else if (c == j) {
+        if (p != j) A[(size_t)p * lda + p] = A[(size_t)j * lda + j];
+        const float2 d = make_float2(pd * inv, 0.f);
+        A[(size_t)j * lda + j] = d;
+        colj[j] = d;
+      } else {
+        float2 v;
+        if (p == j) {
+          v = A[(size_t)c * lda + j];
+        } else if (c < p) {
+          v = cconj(A[(size_t)p * lda + c]);
+          A[(size_t)p * lda + c] = cconj(A[(size_t)c * lda + j]);
+        } else if (c == p) {
+          v = cconj(A[(size_t)p * lda + j]);
+        } else {
+          v = A[(size_t)c * lda + p];
+          A[(size_t)c * lda + p] = A[(size_t)c * lda + j];
+        }
+        v = cscale(v, inv);
+        A[(size_t)c * lda + j] = v;
+        colj[c] = v;
+      }
+    }
+    if (tid == 0 && p != j) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+    __syncthreads();
+    for (int i = j + 1 + warp; i < n; i += nthr / 32) {   // trailing update: rows by warp, columns by lane
+      const float2 li = colj[i];
+      for (int l = j + 1 + lane; l <= i; l += 32)
+        A[(size_t)i * lda + l] = csub(A[(size_t)i * lda + l], cmul(li, cconj(colj[l])));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int rk = sh_rank;
+  EO_STAMP(4);
+
+  // ---------------- one-sided Jacobi: warp w owns pair slots 4w .. 4w + 3; slot p holds columns
+  // (2p, 2p + 1) at the start
+  EoSweepCtx xc;
+  xc.xt = reinterpret_cast<float4*>(smem + L.x);
+  xc.xb = xc.xt + (size_t)2 * L.nw * RP * 32;
+  xc.nw = L.nw; xc.h = h; xc.warp = warp; xc.lane = lane;
+  xc.wfirst = warp == 0;
+  xc.wlast = warp == (h - 1) / 4;
+  xc.slast = (h - 1) - 4 * ((h - 1) / 4);
+  float2 TR[4][RP], TI[4][RP], BR[4][RP], BI[4][RP];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int p = 4 * warp + s, ct = 2 * p, cb = 2 * p + 1;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      float v[2][4];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int r = (2 * i + e) * 32 + lane;
+        const float2 t = (p < h && r < n && ct <= r && ct < rk) ? A[(size_t)r * lda + ct] : make_float2(0.f, 0.f);
+        const float2 b = (p < h && r < n && cb <= r && cb < rk) ? A[(size_t)r * lda + cb] : make_float2(0.f, 0.f);
+        v[e][0] = t.x; v[e][1] = t.y; v[e][2] = b.x; v[e][3] = b.y;
+      }
+      TR[s][i] = make_float2(v[0][0], v[1][0]);
+      TI[s][i] = make_float2(v[0][1], v[1][1]);
+      BR[s][i] = make_float2(v[0][2], v[1][2]);
+      BI[s][i] = make_float2(v[0][3], v[1][3]);
+    }
+  }
+  __syncthreads();
+  // Steps run in blocks of four (the register renaming's period); a window has converged once a
+  // whole circle (np - 1 consecutive steps, which meet every pair once) rotated nothing.
+  int converged = 0, sweeps = 0;
+  {
+    const int per = np - 1;
+    const int maxsteps = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
+    int steps = 0, quiet = 0, last = 0;
+    auto track = [&](int any) {
+      ++steps;
+      if (any) { quiet = 0; last = steps; }
+      else ++quiet;
+    };
+    while (steps < maxsteps) {
+      int r0 = eo_step<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
+      track(r0);
+      r0 = eo_step<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
+      track(r0);
+      r0 = eo_step<RP, 2>(TR, TI, BR, BI, xc, steps & 1);
+      track(r0);
+      r0 = eo_step<RP, 3>(TR, TI, BR, BI, xc, steps & 1);
+      track(r0);
+      if (quiet >= per) { converged = 1; break; }
+    }
+    sweeps = (last + per - 1) / per;
+  }
+  EO_STAMP(5);
+
+  // ---------------- columns back to shared memory (position 2p top, 2p + 1 bottom) with their
+  // squared norms (double-float sums), then normalised
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int p = 4 * warp + s;
+    df na = {0.f, 0.f}, nb = {0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      na = df_add_f(na, fmaf(TR[s][i].x, TR[s][i].x, TI[s][i].x * TI[s][i].x));
+      na = df_add_f(na, fmaf(TR[s][i].y, TR[s][i].y, TI[s][i].y * TI[s][i].y));
+      nb = df_add_f(nb, fmaf(BR[s][i].x, BR[s][i].x, BI[s][i].x * BI[s][i].x));
+      nb = df_add_f(nb, fmaf(BR[s][i].y, BR[s][i].y, BI[s][i].y * BI[s][i].y));
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      df t;
+      t.hi = __shfl_xor_sync(~0u, na.hi, o); t.lo = __shfl_xor_sync(~0u, na.lo, o); na = df_add(na, t);
+      t.hi = __shfl_xor_sync(~0u, nb.hi, o); t.lo = __shfl_xor_sync(~0u, nb.lo, o); nb = df_add(nb, t);
+    }
+    if (p < h) {
+      // squared norms below 2^-100 (the matrix is scaled to a largest diagonal in [1/2, 1)) count as
+      // vanished columns
+      double la = (double)na.hi + (double)na.lo, lb = (double)nb.hi + (double)nb.lo;
+      la = la > 7.888609052210118e-31 ? la : 0.0;
+      lb = lb > 7.888609052210118e-31 ? lb : 0.0;
+      if (lane == 0) { lam[2 * p] = la; lam[2 * p + 1] = lb; }
+      const float ia = la > 0.0 ? ep_rsqrt((float)la) : 0.f, ib = lb > 0.0 ? ep_rsqrt((float)lb) : 0.f;
+#pragma unroll
+      for (int i = 0; i < RP; ++i) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int r = (2 * i + e) * 32 + lane;
+          if (r < n) {
+            A[(size_t)r * lda + 2 * p] =
+                make_float2((e ? TR[s][i].y : TR[s][i].x) * ia, (e ? TI[s][i].y : TI[s][i].x) * ia);
+            A[(size_t)r * lda + 2 * p + 1] =
+                make_float2((e ? BR[s][i].y : BR[s][i].x) * ib, (e ? BI[s][i].y : BI[s][i].x) * ib);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // sort positions by squared norm, descending (ties to the lower position); the first n are the
+  // eigenpairs (with n odd the padding column is zero and sorts among the zeros)
+  for (int i = tid; i < np; i += nthr) {
+    const double di = lam[i];
+    int r = 0;
+    for (int j = 0; j < np; ++j) {
+      const double dj = lam[j];
+      r += (dj > di) || (dj == di && j < i);
+    }
+    sperm[r] = i;
+  }
+  for (int r = tid; r < n; r += nthr) iperm[perm[r]] = r;
+  __syncthreads();
+  // vanished columns: Gram-Schmidt completion (two passes) of unit vectors against the columns before
+  // them in sorted order (warp 0; numerical rank below Nt only)
+  if (warp == 0) {
+    int cand = 0;
+    for (int jj = 0; jj < n; ++jj) {
+      const int pos = sperm[jj];
+      if (lam[pos] > 0.0) continue;
+      for (int tries = 0; tries < n; ++tries, cand = (cand + 1) % n) {
+        for (int r = lane; r < n; r += 32) A[(size_t)r * lda + pos] = make_float2(r == cand ? 1.f : 0.f, 0.f);
+        __syncwarp();
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int q = 0; q < jj; ++q) {
+            const int qp = sperm[q];
+            float2 d = make_float2(0.f, 0.f);
+            for (int r = lane; r < n; r += 32) d = cadd(d, cmulc(A[(size_t)r * lda + qp], A[(size_t)r * lda + pos]));
+            for (int o = 16; o; o >>= 1) { d.x += __shfl_xor_sync(~0u, d.x, o); d.y += __shfl_xor_sync(~0u, d.y, o); }
+            for (int r = lane; r < n; r += 32)
+              A[(size_t)r * lda + pos] = csub(A[(size_t)r * lda + pos], cmul(d, A[(size_t)r * lda + qp]));
+            __syncwarp();
+          }
+        }
+        float nr = 0.f;
+        for (int r = lane; r < n; r += 32) nr += cabs2(A[(size_t)r * lda + pos]);
+        for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
+        if (nr > 0.5f / n) {   // some unit vector keeps at least 1/n of its square in the complement
+          const float sc = ep_rsqrt(nr);
+          for (int r = lane; r < n; r += 32) A[(size_t)r * lda + pos] = cscale(A[(size_t)r * lda + pos], sc);
+          __syncwarp();
+          cand = (cand + 1) % n;
+          break;
+        }
+      }
+      if (lane == 0) lam[pos] = 0.0;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nthr) lam_s[i] = lam[sperm[i]] * scale;
+  EO_STAMP(6);
+
+  // ---------------- rule, alpha, kept columns (warp 0, double precision)
+  __syncthreads();
+  if (warp == 0) {
+    int kk = -1;
+    const int md = g.thresh_mode;
+    if (md == LCF_T_NONE) {
+      for (int i = lane; i < n; i += 32) wts[i] = 1.0;
+      kk = 0;
+    } else if (md <= LCF_T_MEDIAN) {
+      kk = ep_rule_k(md, lam_s, n, g.beta, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+      for (int i = lane; i < n; i += 32) wts[i] = (i + 1 > kk) ? 1.0 : 0.0;
+    } else if (md == LCF_T_SIGMOID) {
+      kk = ep_rule_k(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+      for (int i = lane; i < n; i += 32) wts[i] = 1.0 / (1.0 + exp(-g.beta * ((i + 1) - kk)));
+    } else {   // LCF_T_ADAPTIVE_SOFT (method 4's rule is applied afterwards by the post kernel)
+      double mx = -INFINITY;
+      for (int i = lane; i < n; i += 32) {
+        const double u = n > 1 ? 2.5 * i / (n - 1) : 0.0;
+        wts[i] = -0.5 * u * u - g.beta * log(ep_floor(lam_s, n, i));
+        mx = fmax(mx, wts[i]);
+      }
+      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(~0u, mx, o));
+      for (int i = lane; i < n; i += 32) wts[i] = exp(wts[i] - mx);
+      kk = -1;
+    }
+    __syncwarp();
+    double S = 0.0;
+    for (int i = lane; i < n; i += 32) S += wts[i] * wts[i] * lam_s[i];
+    for (int o = 16; o; o >>= 1) S += __shfl_xor_sync(~0u, S, o);
+    double cf = 0.0;
+    if (lane == 0) {
+      const double pdsum = g.pd_mode == 0 ? S / n : S;
+      double al;
+      int fl = (converged ? 0 : LCF_WFLAG_NOCONV) | ((sweeps < 255 ? sweeps : 255) << LCF_WFLAG_SWEEP_SHIFT);
+      if (g.alpha_mode == 1) al = 1.0;
+      else {
+        const Box bx = boxes[k];
+        const double cnt = g.alpha_mode == 2 ? (double)(bx.z1 - bx.z0) * (bx.x1 - bx.x0) : (double)g.nz * g.nx;
+        if (pdsum <= 1e-300) { al = 0.0; fl |= LCF_WFLAG_DEGENERATE; }
+        else al = cnt / pdsum;
+      }
+      kcut_out[k] = kk;
+      alpha_out[k] = (float)al;
+      flags_out[k] = fl;
+      cf = sqrt(al * (g.pd_mode == 0 ? 1.0 / n : 1.0));
+    }
+    cf = __shfl_sync(~0u, cf, 0);
+    int base = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      const bool kp = i < n && wts[i] > 0.0;
+      const unsigned bal = __ballot_sync(~0u, kp);
+      if (kp) keep[1 + base + __popc(bal & ((1u << lane) - 1u))] = i;
+      if (i < n) coef[i] = (float)(wts[i] * cf);
+      base += __popc(bal);
+    }
+    if (lane == 0) { keep[0] = base; ncol_out[k] = base; }
+  }
+  // ---------------- V = Q U = U - Vh (T (Vh^H U)), rows kept in pivot order (row r is index perm[r])
+  float2* Vh = reinterpret_cast<float2*>(smem + L.x);   // [j][a], a by original index
+  float2* Tm = Vh + (size_t)m * n;                      // [i][j]
+  float2* X = Tm + (size_t)m * m;                       // [j][pos]
+  float2* Y = X + (size_t)m * np;
+  for (int e = tid; e < m * n; e += nthr) Vh[e] = Vhg[(size_t)k * m * n + e];
+  for (int e = tid; e < m * m; e += nthr) Tm[e] = Tg[(size_t)k * m * m + e];
+  __syncthreads();
+  for (int e = tid; e < m * np; e += nthr) {
+    const int j = e / np, pos = e % np;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < n; ++r) acc = cadd(acc, cmulc(Vh[(size_t)j * n + perm[r]], A[(size_t)r * lda + pos]));
+    X[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * np; e += nthr) {
+    const int i = e / np, pos = e % np;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = i; j < m; ++j) acc = cadd(acc, cmul(Tm[i * m + j], X[(size_t)j * np + pos]));
+    Y[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * np; e += nthr) {
+    const int r = e / np, pos = e % np, a = perm[r];
+    float2 v = A[(size_t)r * lda + pos];
+    for (int j = 0; j < m; ++j) v = csub(v, cmul(Vh[(size_t)j * n + a], Y[(size_t)j * np + pos]));
+    A[(size_t)r * lda + pos] = v;
+  }
+  __syncthreads();
+  // phase of each sorted eigenvector: its largest-magnitude entry made real positive (ties to the
+  // lower row by original index)
+  for (int jj = warp; jj < n; jj += (nthr / 32)) {
+    const int pos = sperm[jj];
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    for (int a = lane; a < n; a += 32) {
+      const float mg = cabs2(A[(size_t)iperm[a] * lda + pos]);
+      if (mg > best) { best = mg; bi = a; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const float ob = __shfl_xor_sync(~0u, best, o);
+      const int oi = __shfl_xor_sync(~0u, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+      const float2 v = A[(size_t)iperm[bi < n ? bi : 0] * lda + pos];   // bi >= n only if every entry is NaN
+      const float mg = sqrtf(cabs2(v));
+      phs[jj] = mg > 0.f ? make_float2(v.x / mg, -v.y / mg) : make_float2(1.f, 0.f);
+    }
+  }
+  __syncthreads();
+  EO_STAMP(7);
+  for (int i = tid; i < n; i += nthr) {
+    lam_out[(size_t)k * n + i] = lam_s[i];
+    wt_out[(size_t)k * n + i] = (float)wts[i];
+  }
+  for (int e = tid; e < n * n; e += nthr) {
+    const int a = e / n, jj = e % n;
+    V_out[(size_t)k * n * n + e] = cmul(A[(size_t)iperm[a] * lda + sperm[jj]], phs[jj]);
+  }
+  const int nc = keep[0];
+  for (int e = tid; e < n * g.ncp; e += nthr) {
+    const int a = e / g.ncp, c = e % g.ncp;
+    float2 v = make_float2(0.f, 0.f);
+    if (c < nc) {
+      const int jj = keep[1 + c];
+      v = cscale(cmul(A[(size_t)iperm[a] * lda + sperm[jj]], phs[jj]), coef[jj]);
+    }
+    W_out[(size_t)k * n * g.ncp + e] = v;
+  }
+  EO_STAMP(8);
+}
+
+template <int RP>
+static void eo_launch(const lcf_plan* P, cudaStream_t st, const EoArgs& a) {
+  evd_os_kernel<RP><<<P->nd, 32 * eo_layout(P->nt).nw, evd_os_smem_bytes(P->nt), st>>>(
+      (const float2*)P->ws.evd_B, (const float2*)P->ws.evd_vh, (const float2*)P->ws.evd_t,
+      (const double*)P->ws.evd_scale, (const Box*)P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt, P->ws.kcut,
+      P->ws.alpha, P->ws.flags, P->ws.W, P->ws.ncol);
+}
+
+template <int RP>
+static cudaError_t eo_configure_one() {
+  return cudaFuncSetAttribute(evd_os_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)evd_os_smem_bytes(RP * 64));
+}
+
+cudaError_t launch_evd_os(const lcf_plan* P, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  cudaError_t e = launch_evd_prep(P, st, EO_SUBSPACE_ITERS);
+  if (e != cudaSuccess) return e;
+  EoArgs a;
+  a.nt = P->nt; a.nz = c.nz; a.nx = c.nx;
+  a.thresh_mode = c.thresh_mode; a.beta = c.beta; a.beta_src = c.beta_src;
+  a.k_fixed = c.k_fixed; a.k_src = c.k_src; a.pd_mode = c.pd_mode; a.alpha_mode = c.alpha_mode;
+  a.curv_norm = c.curv_norm; a.max_sweeps = c.max_sweeps; a.ncp = P->ncp;
+  a.clk = P->profiling ? P->ws.evd_clk : nullptr;
+  if (eo_layout(P->nt).rp == 1) eo_launch<1>(P, st, a);
+  else eo_launch<2>(P, st, a);
+  return counted(P);
+}
+
+cudaError_t evd_os_configure() {
+  cudaError_t e = eo_configure_one<1>();
+  if (e == cudaSuccess) e = eo_configure_one<2>();
+  return e;
+}
+
+}  // namespace lcf

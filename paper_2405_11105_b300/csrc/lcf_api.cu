@@ -67,7 +67,7 @@ static lcf_status validate(const lcf_config* c) {
   if (c->curv_norm < 0 || c->curv_norm > 1) return LCF_EINVAL;
   if (c->gram_path < LCF_PATH_SIMT || c->gram_path > LCF_PATH_TC) return LCF_EINVAL;
   if (c->project_path < LCF_PATH_SIMT || c->project_path > LCF_PATH_TC) return LCF_EINVAL;
-  if (c->evd_path < LCF_EVD_CTA || c->evd_path > LCF_EVD_PAIR) return LCF_EINVAL;
+  if (c->evd_path < LCF_EVD_CTA || c->evd_path > LCF_EVD_OS) return LCF_EINVAL;
   if (c->gram_precision < LCF_GP_F16X3 || c->gram_precision > LCF_GP_E4M3) return LCF_EINVAL;
   if (c->gram_path != LCF_PATH_TC && c->gram_precision != LCF_GP_F16X3) return LCF_EINVAL;
   if (c->evd_precision < LCF_EP_FP32 || c->evd_precision > LCF_EP_FP64_POLISH) return LCF_EINVAL;
@@ -233,7 +233,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   if (e == cudaSuccess && nt > (size_t)kProjectShortNmax)
     e = dalloc(&w.pw, nd * kDeflateMax * P->ncp, &tot);
   if (e == cudaSuccess) e = dalloc(&w.ncol, nd, &tot);
-  if (cfg->evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) {
+  if ((cfg->evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) || cfg->evd_path == LCF_EVD_OS) {
     const size_t m = P->nt < kEvdHead ? P->nt : kEvdHead;
     if (e == cudaSuccess) e = dalloc(&w.evd_B, nd * nt * nt, &tot);
     if (e == cudaSuccess) e = dalloc(&w.evd_vh, nd * m * nt, &tot);
@@ -302,6 +302,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = project_tc_configure();
     if (e == cudaSuccess) e = evd_pair_configure();
     if (e == cudaSuccess) e = evd_dist_configure();
+    if (e == cudaSuccess) e = evd_os_configure();
     if (e == cudaSuccess) e = gram_simt_configure();
     if (e == cudaSuccess) e = post_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
@@ -361,8 +362,9 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   if (tc) LCF_CUDA(launch_gram_assemble_tc(P, st));
   else LCF_CUDA(launch_gram_assemble(P, st));
   LCF_MARK(LCF_STAGE_EVD);
-  if (c.evd_path == LCF_EVD_PAIR && P->nt > kEvdPairNmax) LCF_CUDA(launch_evd_dist(P, st));
+  if (c.evd_path != LCF_EVD_CTA && P->nt > kEvdPairNmax) LCF_CUDA(launch_evd_dist(P, st));
   else if (c.evd_path == LCF_EVD_PAIR) LCF_CUDA(launch_evd_pair(P, st));
+  else if (c.evd_path == LCF_EVD_OS) LCF_CUDA(launch_evd_os(P, st));
   else LCF_CUDA(launch_evd(P, st));
   LCF_CUDA(launch_post(P, st));   // FP64-class polish, method 4 (no launch otherwise)
   LCF_MARK(LCF_STAGE_PROJECT);

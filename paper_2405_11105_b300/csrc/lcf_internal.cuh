@@ -304,6 +304,12 @@ size_t mlp_plan_weight_count(int nt, int hidden);
 size_t mlp_plan_bias_count(int nt, int hidden);
 cudaError_t launch_evd_pair(const lcf_plan* P, cudaStream_t st);
 cudaError_t launch_evd_dist(const lcf_plan* P, cudaStream_t st);
+// B = Q^H (R / scale) Q (fp32, full Hermitian), the reflectors, T and the scale of every window,
+// from `iters` subspace iterations (the first stage of the distributed and one-sided EVDs)
+cudaError_t launch_evd_prep(const lcf_plan* P, cudaStream_t st, int iters);
+cudaError_t launch_evd_os(const lcf_plan* P, cudaStream_t st);
+cudaError_t evd_os_configure();
+size_t evd_os_smem_bytes(int nt);
 cudaError_t evd_dist_configure();
 cudaError_t evd_pair_configure();
 cudaError_t launch_project_simt(const lcf_plan* P, const float2* iq, float* out, cudaStream_t st);
