@@ -384,8 +384,10 @@ def main():
     ap.add_argument("--evd-precision", default="fp32", choices=["fp32", "polish"])
     ap.add_argument("--project-form", default="identity", choices=["identity", "subtract"])
     ap.add_argument("--deflate", type=int, default=0)
-    ap.add_argument("--evd", default="pair", choices=["pair", "os"],
+    ap.add_argument("--evd", default="os", choices=["pair", "os"],
                     help="EVD kernel of the optimized path: two-sided CTA pair or one-sided on the Cholesky factor")
+    ap.add_argument("--inflight", type=int, default=3,
+                    help="packets the optimized plan keeps in progress at once (lcf_filter_many)")
     ap.add_argument("--no-variants", action="store_true", help="skip the variant arms (untuned, graph, one-pass fp16)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -431,6 +433,7 @@ def main():
                   inputs_ready=1 if path == L.LCF_PATH_TC else 0, **rule)
         if path == L.LCF_PATH_TC:
             kw.update(options)
+            kw["inflight"] = args.inflight
         kw.update(extra)
         return L.Plan.make(NZ, NX, NT, WZ, WX, **kw)
 
@@ -438,16 +441,29 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def timed(plan, steps, warmup):
-        for i in range(warmup):
-            plan.filter(d_ring[i % RING], out)
+    out_many = torch.empty((RING, NZ, NX), dtype=torch.float32, device=f"cuda:{local}")
+
+    def run_packets(plan, n, single=False):
+        # n packets of the ring; a plan with packets in flight takes them RING at a time through
+        # lcf_filter_many, the others (and single=True: stage profiling) one lcf_filter each
+        if plan.cfg.inflight > 1 and not single:
+            done = 0
+            while done < n:
+                b = min(RING, n - done)
+                plan.filter_many(d_ring[:b], out_many[:b])
+                done += b
+        else:
+            for i in range(n):
+                plan.filter(d_ring[i % RING], out)
+
+    def timed(plan, steps, warmup, single=False):
+        run_packets(plan, warmup, single)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        for i in range(steps):
-            plan.filter(d_ring[i % RING], out)
+        run_packets(plan, steps, single)
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
@@ -467,8 +483,7 @@ def main():
         variants["untuned"] = {"value": world * args.steps / (ms_untuned / 1e3), "tuning": plan.tuning().as_dict()}
     if path == L.LCF_PATH_TC:
         plan.autotune(d_ring[0])
-    for i in range(args.warmup):
-        plan.filter(d_ring[i % RING], out)
+    run_packets(plan, args.warmup)
     n_launch0 = plan.launch_count()
     with ClockSampler(local) as clk:
         ms = timed(plan, args.steps, args.warmup)
@@ -493,8 +508,8 @@ def main():
             vp.close()
 
     # per-stage device times (CUDA events between the stages on the launch stream)
-    plan.profile(True)
-    ms_prof = timed(plan, args.steps, 0)
+    plan.profile(True)   # one packet at a time on the plan's own workspace: stage times without overlap
+    ms_prof = timed(plan, args.steps, 0, single=True)
     stages, ncalls = plan.profile_read()
     plan.profile(False)
     per_launch = {k: v / max(ncalls, 1) for k, v in stages.items()}
@@ -552,7 +567,8 @@ def main():
                                    "project_form": args.project_form, "deflate": args.deflate or "default",
                                    "evd": args.evd},
                        "path": args.path, "l2": f"ring of {RING} packets ({RING * NT * NZ * NX * 8 / 1e6:.0f} MB) > L2",
-                       "parallelism": f"replicas x{world} (independent packets)",
+                       "parallelism": f"replicas x{world} (independent packets), "
+                                      f"{args.inflight if path == L.LCF_PATH_TC else 1} packets in flight per GPU",
                        "tuning": plan.tuning().as_dict() if path == L.LCF_PATH_TC else None},
             "variants": variants,
             "plain_fp32": {"value": plain_value, "unit": "frames/s", "ms_per_step": ms_plain / args.steps},

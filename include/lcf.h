@@ -192,6 +192,14 @@ typedef struct {
                               residual meets the FP32 / tensor-core products:
                               strong tissue motion (a pixel or more) needs 8-16
                               to bring the residual down to blood and noise     */
+  int inflight;            /* packets lcf_filter_many and lcf_filter_host_async
+                              keep in progress at once, 1..4 (0: 1).  Each
+                              packet beyond the first has its own workspace and
+                              plan-owned stream, so the EVD of one packet (which
+                              holds one SM per window) runs beside the other
+                              stages and EVDs of the next: more images per
+                              second, the same time per image.  No counterpart
+                              in the paper, which filters one packet at a time */
 } lcf_config;
 
 /* Fill *cfg with defaults for an nz x nx x nt packet and a wz x wx grid:
@@ -231,10 +239,13 @@ lcf_status lcf_filter_host(lcf_plan* plan, const void* h_iq, float* h_out_pd, cu
  * may be interleaved (the next pipelined prep waits for them).  h_iq must stay unchanged and h_out_pd must not
  * be read until lcf_plan_sync returns (pinned host memory required for the
  * overlap).  Calls of one plan must use the same `stream`.  The first call
- * creates the copy stream and its events. */
+ * creates the copy stream and its events.  With cfg.inflight > 1 consecutive
+ * calls rotate over the plan's lanes: each lane pipelines its own packets on
+ * its own plan-owned stream (after the work queued on `stream` before the
+ * call), so up to inflight packets compute at once. */
 lcf_status lcf_filter_host_async(lcf_plan* plan, const void* h_iq, float* h_out_pd, cudaStream_t stream);
 
-/* Wait for every copy and kernel of the plan's pipelined host calls. */
+/* Wait for every copy and kernel of the plan's pipelined host calls (every lane). */
 lcf_status lcf_plan_sync(lcf_plan* plan);
 
 /* Sliding-packet processing (packets of nt frames every `stride` frames, as
@@ -292,6 +303,17 @@ enum {
  * (no synchronisation).  Enabling resets the accumulated times.  Up to 4096
  * calls are kept between reads; older ones are dropped. */
 lcf_status lcf_plan_profile(lcf_plan* plan, int enable);
+
+/* Several independent packets (no counterpart in the paper: serving-side
+ * batching).  Filters npk packets, d_iq = [npk][Nt][Nz][Nx] complex64 on the
+ * device, into d_out_pd = [npk][Nz][Nx] float32 (Eq. 4, 13 per packet), with up
+ * to cfg.inflight packets in progress at once: packet p runs on the plan's lane
+ * p mod inflight, each lane with its own workspace and plan-owned stream.  All of
+ * it starts after the work queued on `stream` before the call, and work queued
+ * on `stream` after the call waits for every image.  Images equal lcf_filter's.
+ * lcf_plan_status and the debug calls then describe the last packet of lane 0.
+ * LCF_EINVAL for null pointers, npk < 0 or misaligned buffers. */
+lcf_status lcf_filter_many(lcf_plan* plan, const void* d_iq, int npk, float* d_out_pd, cudaStream_t stream);
 
 /* Synchronise and return the device time of each stage summed over the
  * calls recorded since profiling was enabled: ms[LCF_NSTAGES] (host),

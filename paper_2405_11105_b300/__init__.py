@@ -40,7 +40,7 @@ class lcf_config(C.Structure):
                 ("gram_path", C.c_int), ("project_path", C.c_int), ("max_sweeps", C.c_int),
                 ("evd_path", C.c_int), ("inputs_ready", C.c_int),
                 ("gram_precision", C.c_int), ("evd_precision", C.c_int), ("graph", C.c_int),
-                ("project_form", C.c_int), ("deflate", C.c_int)]
+                ("project_form", C.c_int), ("deflate", C.c_int), ("inflight", C.c_int)]
 
 
 class lcf_tuning(C.Structure):
@@ -67,6 +67,7 @@ def _load():
         "lcf_config_default": ([C.POINTER(lcf_config), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
         "lcf_plan_create": ([C.POINTER(lcf_config), C.c_int, C.POINTER(vp)], C.c_int),
         "lcf_filter": ([vp, vp, vp, vp], C.c_int),
+        "lcf_filter_many": ([vp, vp, C.c_int, vp, vp], C.c_int),
         "lcf_filter_host": ([vp, vp, vp, vp], C.c_int),
         "lcf_filter_host_async": ([vp, vp, vp, vp], C.c_int),
         "lcf_plan_sync": ([vp], C.c_int),
@@ -266,6 +267,22 @@ class Plan:
             out = torch.empty((c.nz, c.nx), dtype=torch.float32, device=iq.device)
         st = (stream or torch.cuda.current_stream(iq.device)).cuda_stream
         _check(lcf_filter(self.handle, iq.data_ptr(), out.data_ptr(), st), "lcf_filter")
+        return out
+
+    def filter_many(self, iq, out=None, stream=None):
+        """iq: complex64 CUDA tensor [npk, nt, nz, nx] -> float32 PD images [npk, nz, nx]; up to
+        cfg.inflight packets in progress at once (lcf_filter_many)."""
+        import torch
+        c = self.cfg
+        if iq.dtype != torch.complex64 or not iq.is_cuda or not iq.is_contiguous():
+            raise ValueError("iq must be a contiguous complex64 CUDA tensor")
+        if iq.dim() != 4 or tuple(iq.shape[1:]) != (c.nt, c.nz, c.nx):
+            raise ValueError(f"iq shape {tuple(iq.shape)} != (npk, {c.nt}, {c.nz}, {c.nx})")
+        npk = iq.shape[0]
+        if out is None:
+            out = torch.empty((npk, c.nz, c.nx), dtype=torch.float32, device=iq.device)
+        st = (stream or torch.cuda.current_stream(iq.device)).cuda_stream
+        _check(_lib.lcf_filter_many(self.handle, iq.data_ptr(), int(npk), out.data_ptr(), st), "lcf_filter_many")
         return out
 
     def filter_host(self, iq_host, out_host=None, stream=None):

@@ -53,9 +53,10 @@ struct EdArgs {
 
 // ----------------------------------------------------------------------------
 // evd_prep_kernel: shared memory Ys, Zs (m x ldy, column-major), Yd, Zd (n x m df64)
+// + for Nt <= kEvdPairNmax, fp32(R / scale) (n x n) for the subspace iteration
 size_t evd_prep_smem_bytes(int n) {
   const int m = n < kEvdHead ? n : kEvdHead, ldy = n + 1;
-  return 2 * (size_t)m * ldy * 8 + 2 * (size_t)n * m * 16 + 1024;
+  return 2 * (size_t)m * ldy * 8 + 2 * (size_t)n * m * 16 + 1024 + (n <= kEvdPairNmax ? (size_t)n * n * 8 : 0);
 }
 
 __global__ void __launch_bounds__(ED_THREADS, 1)
@@ -69,6 +70,8 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
   float2* Zs = Ys + (size_t)m * ldy;
   zdf* Yd = reinterpret_cast<zdf*>(Zs + (size_t)m * ldy);
   zdf* Zd = Yd + (size_t)n * m;
+  float2* Rf = reinterpret_cast<float2*>(smem + 2 * (size_t)m * ldy * 8 + 2 * (size_t)n * m * 16 + 1024);
+  const bool rf = n <= kEvdPairNmax;   // fp32(R / scale) staged once in shared memory
   __shared__ double sh_scale;
   __shared__ float betas[kEvdHead];
   __shared__ float2 us[kEvdHead];
@@ -93,6 +96,12 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
   const double scale = ldexp(1.0, ex);
   const float s_lo = ldexpf(1.f, -ex);
   if (tid == 0) scale_g[k] = scale;
+  if (rf) {
+    for (int e = tid; e < n * n; e += ED_THREADS) {
+      const double2 r = R[e];
+      Rf[e] = make_float2(df_from_double_scaled(r.x, ex).hi, df_from_double_scaled(r.y, ex).hi);
+    }
+  }
 
   // ---- subspace iteration on fp32(R / scale), R from global memory
   for (int e = tid; e < m * ldy; e += ED_THREADS) {
@@ -109,9 +118,16 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
       float2 acc = make_float2(0.f, 0.f);
       const double2* rr = R + (size_t)a * n;
       const float2* yy = Ys + (size_t)j * ldy;
+      const float2* rs = Rf + (size_t)a * n;
       for (int b = 0; b < n; ++b) {
-        const double2 rd = rr[b];
-        const float2 r = make_float2((float)rd.x * s_lo, (float)rd.y * s_lo), y = yy[b];
+        float2 r;
+        if (rf) {
+          r = rs[b];
+        } else {
+          const double2 rd = rr[b];
+          r = make_float2((float)rd.x * s_lo, (float)rd.y * s_lo);
+        }
+        const float2 y = yy[b];
         acc.x = fmaf(r.x, y.x, fmaf(-r.y, y.y, acc.x));
         acc.y = fmaf(r.x, y.y, fmaf(r.y, y.x, acc.y));
       }
@@ -215,8 +231,12 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
     for (int b = sub; a < n && b < n; b += 4) {
       const double2 r = R[(size_t)a * n + b];
       zdf rz;
-      rz.re = df_from_double(r.x); rz.im = df_from_double(r.y);
-      rz.re.hi *= s_lo; rz.re.lo *= s_lo; rz.im.hi *= s_lo; rz.im.lo *= s_lo;
+      if (rf) {   // integer-pipe split for the short packets; the long ones keep the FP64 conversion
+        rz.re = df_from_double_scaled(r.x, ex); rz.im = df_from_double_scaled(r.y, ex);
+      } else {
+        rz.re = df_from_double(r.x); rz.im = df_from_double(r.y);
+        rz.re.hi *= s_lo; rz.re.lo *= s_lo; rz.im.hi *= s_lo; rz.im.lo *= s_lo;
+      }
 #pragma unroll
       for (int j = 0; j < kEvdHead; ++j)
         if (j < m) acc[j] = zdf_add(acc[j], zdf_mul_c(rz, Zs[(size_t)j * ldy + b]));
@@ -279,8 +299,12 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
     if (a > b) continue;
     const double2 r = R[(size_t)a * n + b];
     zdf x;
-    x.re = df_from_double(r.x); x.im = df_from_double(r.y);
-    x.re.hi *= s_lo; x.re.lo *= s_lo; x.im.hi *= s_lo; x.im.lo *= s_lo;
+    if (rf) {
+      x.re = df_from_double_scaled(r.x, ex); x.im = df_from_double_scaled(r.y, ex);
+    } else {
+      x.re = df_from_double(r.x); x.im = df_from_double(r.y);
+      x.re.hi *= s_lo; x.re.lo *= s_lo; x.im.hi *= s_lo; x.im.lo *= s_lo;
+    }
     zdf c = {{0.f, 0.f}, {0.f, 0.f}};
     for (int j = 0; j < m; ++j) {
       zdf zb = Zd[b * m + j];
@@ -802,8 +826,9 @@ cudaError_t launch_evd_dist(const lcf_plan* P, cudaStream_t st) {
 }
 
 cudaError_t evd_dist_configure() {
+  const size_t pa = evd_prep_smem_bytes(kEvdPairNmax), pb = evd_prep_smem_bytes(kEvdNmax);
   cudaError_t e = cudaFuncSetAttribute(evd_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)evd_prep_smem_bytes(kEvdNmax));
+                                       (int)(pa > pb ? pa : pb));
   size_t mx = 0;
   for (int nt = kEvdPairNmax + 1; nt <= kEvdNmax; ++nt)   // both cluster sizes where they fit
     for (int C = evd_dist_cluster(nt); C <= 8; C += 4) mx = evd_dist_smem_bytes(nt, C) > mx ? evd_dist_smem_bytes(nt, C) : mx;

@@ -5,8 +5,8 @@
 // B = Q^H (R / scale) Q in double-float rounded to fp32, with Q from an FP32
 // subspace iteration and its Householder QR, so the dominant (tissue) directions
 // are split off before any FP32 rotation.  This kernel then
-//   1. factors B = P L L^H P^T in FP32 with diagonal pivoting (Cholesky; a
-//      non-positive pivot ends it and leaves the rest of L zero);
+//   1. factors B = P L L^H P^T in FP32 with diagonal pivoting (Cholesky in panels of
+//      eight columns; a non-positive pivot ends it and leaves the rest of L zero);
 //   2. runs one-sided Jacobi (Hestenes' method) on the columns of F = P L:
 //      column pairs are rotated until every pair is orthogonal to a relative
 //      tolerance.  B = F F^H = (F J)(F J)^H for every unitary J, so at
@@ -40,6 +40,7 @@ namespace lcf {
 constexpr int EO_THREADS = 512;
 constexpr float EO_TOL = 2.0e-6f;              // relative orthogonality test (cosine of two columns)
 constexpr int EO_SUBSPACE_ITERS = 3;
+constexpr int EO_PANEL = 8;                    // Cholesky panel width
 
 struct EoArgs {
   int nt, nz, nx;
@@ -310,80 +311,85 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   EO_STAMP(3);
 
-  // ---------------- pivoted Cholesky of B in FP32, lower triangle in place
+  // ---------------- pivoted Cholesky of B in FP32, lower triangle in place, in panels of
+  // EO_PANEL columns: warp 0 factors a panel left-looking (pivot on the running diagonal dg,
+  // symmetric interchange, column = (entry - the panel's earlier columns) / sqrt(pivot)), then
+  // every warp applies the panel to the trailing lower triangle
+  float* dg = reinterpret_cast<float*>(colj);   // running diagonal of the Schur complement
   {
     const float2* B = Bg + (size_t)k * n * n;
     for (int i = warp; i < n; i += nthr / 32)
       for (int c = lane; c <= i; c += 32) A[(size_t)i * lda + c] = B[(size_t)i * n + c];
     for (int r = tid; r < np; r += nthr) perm[r] = r;
+    for (int i = tid; i < n; i += nthr) dg[i] = B[(size_t)i * n + i].x;
   }
-  __shared__ int sh_piv, sh_rank;
-  __shared__ float sh_pd;
-  if (tid == 0) sh_rank = n;
+  __shared__ int sh_rank, sh_stop;
+  if (tid == 0) { sh_rank = n; sh_stop = 0; }
   __syncthreads();
-  float first = 0.f;
-  for (int j = 0; j < n; ++j) {
-    if (warp == 0) {   // largest remaining diagonal entry, ties to the lower index
-      float best = -INFINITY;
-      int bi = 0x7fffffff;
-      for (int i = j + lane; i < n; i += 32) {
-        const float d = A[(size_t)i * lda + i].x;
-        if (d > best) { best = d; bi = i; }
+  float first = 0.f;   // warp 0: the first pivot
+  for (int j0 = 0; j0 < n; j0 += EO_PANEL) {
+    const int j1 = j0 + EO_PANEL < n ? j0 + EO_PANEL : n;
+    if (warp == 0) {
+      for (int j = j0; j < j1; ++j) {
+        float best = -INFINITY;   // largest remaining diagonal entry, ties to the lower index
+        int bi = 0x7fffffff;
+        for (int i = j + lane; i < n; i += 32) {
+          const float d = dg[i];
+          if (d > best) { best = d; bi = i; }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const float ob = __shfl_xor_sync(~0u, best, o);
+          const int oi = __shfl_xor_sync(~0u, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (j == 0) first = best;
+        if (!(best > first * 1e-30f) || !isfinite(best)) {   // numerical rank j: the rest of L stays zero
+          if (lane == 0) { sh_rank = j; sh_stop = 1; }
+          break;
+        }
+        const int p = bi;
+        if (p != j) {   // symmetric interchange of j and p; pending panel updates move with the rows
+          for (int c = lane; c < n; c += 32) {
+            float2 t;
+            if (c < j) {
+              t = A[(size_t)j * lda + c]; A[(size_t)j * lda + c] = A[(size_t)p * lda + c]; A[(size_t)p * lda + c] = t;
+            } else if (c == j) {
+              t = A[(size_t)j * lda + j]; A[(size_t)j * lda + j] = A[(size_t)p * lda + p]; A[(size_t)p * lda + p] = t;
+              A[(size_t)p * lda + j] = cconj(A[(size_t)p * lda + j]);
+            } else if (c < p) {
+              t = A[(size_t)c * lda + j];
+              A[(size_t)c * lda + j] = cconj(A[(size_t)p * lda + c]);
+              A[(size_t)p * lda + c] = cconj(t);
+            } else if (c > p) {
+              t = A[(size_t)c * lda + j]; A[(size_t)c * lda + j] = A[(size_t)c * lda + p]; A[(size_t)c * lda + p] = t;
+            }
+          }
+          if (lane == 0) {
+            const float td = dg[j]; dg[j] = dg[p]; dg[p] = td;
+            const int tp = perm[j]; perm[j] = perm[p]; perm[p] = tp;
+          }
+          __syncwarp();
+        }
+        const float inv = ep_rsqrt(best);
+        for (int i = j + 1 + lane; i < n; i += 32) {
+          float2 v = A[(size_t)i * lda + j];
+          for (int l = j0; l < j; ++l) v = csub(v, cmul(A[(size_t)i * lda + l], cconj(A[(size_t)j * lda + l])));
+          v = cscale(v, inv);
+          A[(size_t)i * lda + j] = v;
+          dg[i] -= cabs2(v);
+        }
+        if (lane == 0) A[(size_t)j * lda + j] = make_float2(best * inv, 0.f);
+        __syncwarp();
       }
-      for (int o = 16; o; o >>= 1) {
-        const float ob = __shfl_xor_sync(~0u, best, o);
-        const int oi = __shfl_xor_sync(~0u, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) { sh_piv = bi; sh_pd = best; }
     }
     __syncthreads();
-    const int p = sh_piv;
-    const float pd = sh_pd;
-    if (j == 0) first = pd;
-    if (!(pd > first * 1e-30f) || !isfinite(pd)) {   // numerical rank j: the rest of L stays zero
-      if (tid == 0) sh_rank = j;
-      break;
-    }
-    // symmetric interchange of j and p in the lower triangle (entry (c, j) of the interchanged
-    // matrix for c > j, L's rows j and p for c < j), fused with the scaling of column j
-    const float inv = ep_rsqrt(pd);
-    for (int c = tid; c < n; c += nthr) {
-      if (c < j) {
-        if (p != j) {
-          const float2 t = A[(size_t)j * lda + c];
-          A[(size_t)j * lda + c] = A[(size_t)p * lda + c];
-          A[(size_t)p * lda + c] = t;
-        }
-      } else if (c == j) {
-        if (p != j) A[(size_t)p * lda + p] = A[(size_t)j * lda + j];
-        const float2 d = make_float2(pd * inv, 0.f);
-        A[(size_t)j * lda + j] = d;
-        colj[j] = d;
-      } else {
-        float2 v;
-        if (p == j) {
-          v = A[(size_t)c * lda + j];
-        } else if (c < p) {
-          v = cconj(A[(size_t)p * lda + c]);
-          A[(size_t)p * lda + c] = cconj(A[(size_t)c * lda + j]);
-        } else if (c == p) {
-          v = cconj(A[(size_t)p * lda + j]);
-        } else {
-          v = A[(size_t)c * lda + p];
-          A[(size_t)c * lda + p] = A[(size_t)c * lda + j];
-        }
-        v = cscale(v, inv);
-        A[(size_t)c * lda + j] = v;
-        colj[c] = v;
+    if (sh_stop) break;
+    for (int i = j1 + warp; i < n; i += nthr / 32) {   // trailing update: rows by warp, columns by lane
+      for (int l = j1 + lane; l <= i; l += 32) {
+        float2 acc = A[(size_t)i * lda + l];
+        for (int c = j0; c < j1; ++c) acc = csub(acc, cmul(A[(size_t)i * lda + c], cconj(A[(size_t)l * lda + c])));
+        A[(size_t)i * lda + l] = acc;
       }
-    }
-    if (tid == 0 && p != j) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
-    __syncthreads();
-    for (int i = j + 1 + warp; i < n; i += nthr / 32) {   // trailing update: rows by warp, columns by lane
-      const float2 li = colj[i];
-      for (int l = j + 1 + lane; l <= i; l += 32)
-        A[(size_t)i * lda + l] = csub(A[(size_t)i * lda + l], cmul(li, cconj(colj[l])));
     }
     __syncthreads();
   }

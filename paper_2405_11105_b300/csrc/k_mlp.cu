@@ -406,6 +406,10 @@ extern "C" lcf_status lcf_plan_set_mlp(lcf_plan* P, const lcf_mlp* N, float p_mi
   if (cudaStreamSynchronize(0) != cudaSuccess) return LCF_ECUDA;
   P->mlp_hidden = N->hidden;
   P->mlp_pmin = p_min;
+  for (size_t l = 1; l < P->lanes.size(); ++l) {   // the in-flight lanes use the same network
+    const lcf_status s = lcf_plan_set_mlp(P->lanes[l], N, p_min);
+    if (s != LCF_OK) return s;
+  }
   return LCF_OK;
 }
 

@@ -76,6 +76,7 @@ static lcf_status validate(const lcf_config* c) {
   if (c->project_form == LCF_PF_SUBTRACT && (c->thresh_mode == LCF_T_SIGMOID || c->thresh_mode == LCF_T_ADAPTIVE_SOFT))
     return LCF_EINVAL;   // the subtractive form needs 0/1 weights
   if (c->deflate < 0 || c->deflate > kDeflateMax || (c->deflate > 0 && c->deflate >= c->nt)) return LCF_EINVAL;
+  if (c->inflight < 0 || c->inflight > 4) return LCF_EINVAL;
   if ((long long)c->nz * c->nx * (c->nt + kDeflateMax) > (1LL << 31)) return LCF_EUNSUPPORTED;
   if (c->nt > kEvdNmax) return LCF_EUNSUPPORTED;
   if (c->evd_path == LCF_EVD_CTA && c->nt > kEvdCtaNmax) return LCF_EUNSUPPORTED;
@@ -140,6 +141,18 @@ static void free_ws(Workspace& w) {
 }
 
 static bool g_configured[64] = {false};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_plan** out) {
   if (!out) return LCF_EINVAL;
@@ -315,20 +328,32 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
   }
   cudaSetDevice(prev);
   *out = P;
+  if (cfg->inflight > 1) {   // lanes 1 .. inflight-1: sub-plans with their own workspaces
+    lcf_status ls = LCF_OK;
+    lcf_config c1 = *cfg;
+    c1.inflight = 1;
+    P->lanes.assign(cfg->inflight, nullptr);
+    for (int l = 1; l < cfg->inflight && ls == LCF_OK; ++l) ls = lcf_plan_create(&c1, device, &P->lanes[l]);
+    if (ls == LCF_OK) {
+      DeviceGuard dg(device);
+      P->lane_st.assign(cfg->inflight, nullptr);
+      P->lane_ev.assign(cfg->inflight, nullptr);
+      cudaError_t le = cudaEventCreateWithFlags(&P->ev_many, cudaEventDisableTiming);
+      for (int l = 0; l < cfg->inflight && le == cudaSuccess; ++l) {
+        le = cudaStreamCreateWithFlags(&P->lane_st[l], cudaStreamNonBlocking);
+        if (le == cudaSuccess) le = cudaEventCreateWithFlags(&P->lane_ev[l], cudaEventDisableTiming);
+      }
+      if (le != cudaSuccess) ls = LCF_ECUDA;
+    }
+    if (ls != LCF_OK) {
+      lcf_plan_destroy(P);
+      *out = nullptr;
+      return ls;
+    }
+  }
   return LCF_OK;
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int d) {
-    cudaGetDevice(&prev);
-    if (prev != d) cudaSetDevice(d);
-    else prev = -1;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 // Event for stage boundary b (0..LCF_NSTAGES) of the current call, or null.
 static cudaEvent_t prof_event(lcf_plan* P, int b) {
@@ -553,6 +578,37 @@ extern "C" lcf_status lcf_filter(lcf_plan* P, const void* d_iq, float* d_out_pd,
   return s;
 }
 
+extern "C" lcf_status lcf_filter_many(lcf_plan* P, const void* d_iq, int npk, float* d_out_pd, cudaStream_t stream) {
+  if (!P || npk < 0 || (npk > 0 && (!d_iq || !d_out_pd))) return LCF_EINVAL;
+  if (((uintptr_t)d_iq & 7) || ((uintptr_t)d_out_pd & 3)) return LCF_EINVAL;
+  const size_t in_elems = (size_t)P->nt * P->npix, out_elems = (size_t)P->npix;
+  const float2* iq = (const float2*)d_iq;
+  const int K = (int)P->lanes.size() > 1 ? (int)P->lanes.size() : 1;
+  if (K == 1 || npk <= 1) {
+    for (int p = 0; p < npk; ++p) {
+      const lcf_status s = lcf_filter(P, iq + p * in_elems, d_out_pd + p * out_elems, stream);
+      if (s != LCF_OK) return s;
+    }
+    return LCF_OK;
+  }
+  DeviceGuard g(P->device);
+  const int nl = npk < K ? npk : K;
+  LCF_CUDA(cudaEventRecord(P->ev_many, stream));
+  for (int l = 0; l < nl; ++l) LCF_CUDA(cudaStreamWaitEvent(P->lane_st[l], P->ev_many, 0));
+  for (int p = 0; p < npk; ++p) {
+    const int l = p % K;
+    const lcf_status s = lcf_filter(l ? P->lanes[l] : P, iq + p * in_elems, d_out_pd + p * out_elems, P->lane_st[l]);
+    if (s != LCF_OK) return s;
+  }
+  for (int l = 0; l < nl; ++l) {
+    LCF_CUDA(cudaEventRecord(P->lane_ev[l], P->lane_st[l]));
+    LCF_CUDA(cudaStreamWaitEvent(stream, P->lane_ev[l], 0));
+  }
+  P->last_stream = stream;
+  P->launched = true;
+  return LCF_OK;
+}
+
 extern "C" lcf_status lcf_filter_host(lcf_plan* P, const void* h_iq, float* h_out_pd, cudaStream_t stream) {
   if (!P || !h_iq || !h_out_pd) return LCF_EINVAL;
   DeviceGuard g(P->device);
@@ -571,8 +627,21 @@ extern "C" lcf_status lcf_filter_host(lcf_plan* P, const void* h_iq, float* h_ou
   return LCF_OK;
 }
 
+static lcf_status host_async_one(lcf_plan* P, const void* h_iq, float* h_out_pd, cudaStream_t stream);
+
 extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float* h_out_pd, cudaStream_t stream) {
   if (!P || !h_iq || !h_out_pd) return LCF_EINVAL;
+  if (P->lanes.size() > 1) {   // consecutive calls rotate over the lanes
+    DeviceGuard g(P->device);
+    const int l = (int)(P->lane_seq++ % (long long)P->lanes.size());
+    LCF_CUDA(cudaEventRecord(P->ev_many, stream));
+    LCF_CUDA(cudaStreamWaitEvent(P->lane_st[l], P->ev_many, 0));
+    return host_async_one(l ? P->lanes[l] : P, h_iq, h_out_pd, P->lane_st[l]);
+  }
+  return host_async_one(P, h_iq, h_out_pd, stream);
+}
+
+static lcf_status host_async_one(lcf_plan* P, const void* h_iq, float* h_out_pd, cudaStream_t stream) {
   DeviceGuard g(P->device);
   if (!P->h2d_stream) {
     LCF_CUDA(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
@@ -609,7 +678,12 @@ extern "C" lcf_status lcf_filter_host_async(lcf_plan* P, const void* h_iq, float
 
 extern "C" lcf_status lcf_plan_sync(lcf_plan* P) {
   if (!P) return LCF_EINVAL;
+  for (size_t l = 1; l < P->lanes.size(); ++l) {
+    const lcf_status s = lcf_plan_sync(P->lanes[l]);
+    if (s != LCF_OK) return s;
+  }
   DeviceGuard g(P->device);
+  for (cudaStream_t ls : P->lane_st) LCF_CUDA(cudaStreamSynchronize(ls));
   if (P->h2d_stream) LCF_CUDA(cudaStreamSynchronize(P->h2d_stream));
   if (P->prep_stream) LCF_CUDA(cudaStreamSynchronize(P->prep_stream));
   // the last pipelined packet of each staging buffer, whichever stream it ran on; earlier
@@ -745,14 +819,28 @@ extern "C" lcf_status lcf_plan_windows(lcf_plan* P, int* nd, int k, int* box) {
 extern "C" lcf_status lcf_plan_launch_count(const lcf_plan* P, long long* n) {
   if (!P || !n) return LCF_EINVAL;
   *n = P->launches;
+  for (size_t l = 1; l < P->lanes.size(); ++l) {
+    long long m = 0;
+    lcf_plan_launch_count(P->lanes[l], &m);
+    *n += m;
+  }
   return LCF_OK;
 }
 
-extern "C" size_t lcf_plan_workspace_bytes(const lcf_plan* P) { return P ? P->ws_bytes : 0; }
+extern "C" size_t lcf_plan_workspace_bytes(const lcf_plan* P) {
+  if (!P) return 0;
+  size_t b = P->ws_bytes;
+  for (size_t l = 1; l < P->lanes.size(); ++l) b += lcf_plan_workspace_bytes(P->lanes[l]);
+  return b;
+}
 
 extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
   if (!P) return LCF_EINVAL;
+  for (size_t l = 1; l < P->lanes.size(); ++l)
+    if (P->lanes[l]) lcf_plan_destroy(P->lanes[l]);
   DeviceGuard g(P->device);
+  for (cudaStream_t ls : P->lane_st)
+    if (ls) cudaStreamSynchronize(ls);
   if (P->h2d_stream) cudaStreamSynchronize(P->h2d_stream);   // pipelined host calls still in flight
   if (P->prep_stream) cudaStreamSynchronize(P->prep_stream);
   if (P->launched) cudaStreamSynchronize(P->last_stream);
@@ -771,6 +859,12 @@ extern "C" lcf_status lcf_plan_destroy(lcf_plan* P) {
     if (P->ev_pdone[b]) cudaEventDestroy(P->ev_pdone[b]);
   }
   if (P->ev_seq) cudaEventDestroy(P->ev_seq);
+  // the lane streams last: last_stream may be one of them
+  for (cudaStream_t ls : P->lane_st)
+    if (ls) cudaStreamDestroy(ls);
+  for (cudaEvent_t le : P->lane_ev)
+    if (le) cudaEventDestroy(le);
+  if (P->ev_many) cudaEventDestroy(P->ev_many);
   delete P;
   return LCF_OK;
 }

@@ -183,6 +183,13 @@ struct lcf_plan {
   float* sg_out = nullptr;
   int sg_n = 0, sg_stride = 0;
   long long sg_launches = 0;
+  // packets in flight (cfg.inflight > 1): lane 0 is this plan, lanes 1.. are sub-plans with
+  // their own workspaces; every lane has a plan-owned stream
+  std::vector<lcf_plan*> lanes;
+  std::vector<cudaStream_t> lane_st;
+  std::vector<cudaEvent_t> lane_ev;
+  cudaEvent_t ev_many = nullptr;
+  long long lane_seq = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;
   long prof_calls = 0;
@@ -229,6 +236,33 @@ __device__ __forceinline__ df two_prod_df(float a, float b) {
 __device__ __forceinline__ df df_from_double(double d) {
   float h = (float)d;
   return {h, (float)(d - (double)h)};
+}
+// d * 2^-ex as a double-float, on the integer pipes (the double -> float conversion instruction
+// runs on the FP64 units, which are few on this part): hi = the top 24 significand bits, lo = the
+// next 29 bits rounded down to 24, renormalised; |error| < 2^-47 |d|.  Zero, subnormal doubles
+// and results below the float range give zero; overflow and inf / NaN give inf / NaN in hi.
+__device__ __forceinline__ df df_from_double_scaled(double d, int ex) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  const int e = (int)((u >> 52) & 0x7ffu);
+  const unsigned long long mant = u & 0xfffffffffffffull;
+  if (e == 0) return {__uint_as_float(sign), 0.f};
+  if (e == 0x7ff) return {__uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u)), 0.f};
+  const int E = e - 1023 - ex;   // unbiased exponent of the scaled value
+  if (E + 127 >= 255) return {__uint_as_float(sign | 0x7f800000u), 0.f};
+  if (E + 127 <= 0) return {__uint_as_float(sign), 0.f};
+  const float hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | (unsigned)(mant >> 29));
+  const unsigned mr = (unsigned)(mant & 0x1fffffffull);   // remainder: mr * 2^(E - 52)
+  float lo = 0.f;
+  if (mr) {
+    const int hb = 31 - __clz(mr);                      // leading bit of the remainder
+    const int fe = hb + E - 52 + 127;
+    if (fe > 0) {
+      const unsigned m24 = hb >= 23 ? (mr >> (hb - 23)) : (mr << (23 - hb));
+      lo = __uint_as_float(sign | ((unsigned)fe << 23) | (m24 & 0x7fffffu));
+    }
+  }
+  return quick_two_sum(hi, lo);
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }

@@ -97,7 +97,7 @@ extern "C" lcf_status lcf_plan_get_tuning(const lcf_plan* P, lcf_tuning* t) {
   return LCF_OK;
 }
 
-extern "C" lcf_status lcf_plan_set_tuning(lcf_plan* P, const lcf_tuning* t) {
+static lcf_status set_tuning_one(lcf_plan* P, const lcf_tuning* t) {
   if (!P || !t) return LCF_EINVAL;
   if (!in_range(t->gram_splits) || !in_range(t->simt_gram_splits) || !in_range(t->aug_splits) ||
       !in_range(t->q_splits) || !in_range(t->basis_splits) || !in_range(t->ncc_splits))
@@ -144,6 +144,13 @@ extern "C" lcf_status lcf_plan_set_tuning(lcf_plan* P, const lcf_tuning* t) {
   return st;
 }
 
+// the plan and its in-flight lanes take the same launch shapes
+extern "C" lcf_status lcf_plan_set_tuning(lcf_plan* P, const lcf_tuning* t) {
+  lcf_status st = set_tuning_one(P, t);
+  for (size_t l = 1; st == LCF_OK && P && l < P->lanes.size(); ++l) st = set_tuning_one(P->lanes[l], t);
+  return st;
+}
+
 extern "C" lcf_status lcf_plan_autotune(lcf_plan* P, const void* d_iq, cudaStream_t stream, const char* cache_path,
                                         int* from_cache) {
   if (!P || !d_iq || ((uintptr_t)d_iq & 7)) return LCF_EINVAL;
@@ -170,7 +177,7 @@ extern "C" lcf_status lcf_plan_autotune(lcf_plan* P, const void* d_iq, cudaStrea
       }
       fclose(f);
       if (hit) {
-        lcf_status s = lcf_plan_set_tuning(P, &got);
+        lcf_status s = lcf_plan_set_tuning(P, &got);   // a cached result: the lanes too
         if (s == LCF_OK && from_cache) *from_cache = 1;
         return s;
       }
@@ -208,7 +215,7 @@ extern "C" lcf_status lcf_plan_autotune(lcf_plan* P, const void* d_iq, cudaStrea
     for (int v : kb.cand) {
       lcf_tuning t = cur;
       t.*kb.field = v;
-      if (lcf_plan_set_tuning(P, &t) != LCF_OK) continue;
+      if (set_tuning_one(P, &t) != LCF_OK) continue;   // candidates on the plan alone
       float ms = 0.f;
       st = time_packet(P, (const float2*)d_iq, out, stream, e0, e1, &ms);
       if (st != LCF_OK) break;
@@ -219,7 +226,7 @@ extern "C" lcf_status lcf_plan_autotune(lcf_plan* P, const void* d_iq, cudaStrea
     }
     cur.*kb.field = best_v;
   }
-  if (st == LCF_OK) st = lcf_plan_set_tuning(P, &cur);
+  if (st == LCF_OK) st = lcf_plan_set_tuning(P, &cur);   // the result on every lane
   P->profiling = prof;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
