@@ -282,7 +282,8 @@ def stream_workload(args):
     del frames
     out = torch.empty((npk, nz, nx), dtype=torch.float32, device=f"cuda:{local}")
     plan = L.Plan.make(nz, nx, nt, wz, wx, device=local, thresh_mode=L.LCF_T_ADAPTIVE_SOFT, beta=1.0,
-                       gram_path=L.LCF_PATH_TC, project_path=L.LCF_PATH_TC, evd_path=L.LCF_EVD_PAIR)
+                       gram_path=L.LCF_PATH_TC, project_path=L.LCF_PATH_TC,
+                       evd_path=L.LCF_EVD_OS if args.evd == "os" else L.LCF_EVD_PAIR)
     st = torch.cuda.current_stream()
     plan.filter_stream(d, stride, out)          # captures the stream graph
     torch.cuda.synchronize()
@@ -318,7 +319,7 @@ def stream_workload(args):
             "config": {"workload": f"{npk} packets of 512x256 px x Nt=200 sliding by {stride} frames over one "
                                    f"frame ring ({n_frames} frames, {d.numel() * 8 / 1e9:.2f} GB), 16x16 windows, "
                                    "method 6 soft weights; each stream one CUDA graph launch",
-                       "l2": "frame ring >> L2"},
+                       "l2": "frame ring >> L2", "evd": args.evd},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "note": "one packet launched alone, CUDA events"},
             "stage_ms_per_launch": {k: v / max(n, 1) for k, v in stages.items()},
@@ -386,6 +387,8 @@ def main():
     ap.add_argument("--deflate", type=int, default=0)
     ap.add_argument("--evd", default="os", choices=["pair", "os"],
                     help="EVD kernel of the optimized path: two-sided CTA pair or one-sided on the Cholesky factor")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (a profiler run can reuse the tuning of a plain run)")
     ap.add_argument("--inflight", type=int, default=3,
                     help="packets the optimized plan keeps in progress at once (lcf_filter_many)")
     ap.add_argument("--no-variants", action="store_true", help="skip the variant arms (untuned, graph, one-pass fp16)")
@@ -482,7 +485,7 @@ def main():
         ms_untuned = timed(plan, args.steps, args.warmup)
         variants["untuned"] = {"value": world * args.steps / (ms_untuned / 1e3), "tuning": plan.tuning().as_dict()}
     if path == L.LCF_PATH_TC:
-        plan.autotune(d_ring[0])
+        plan.autotune(d_ring[0], cache_path=args.tune_cache)
     run_packets(plan, args.warmup)
     n_launch0 = plan.launch_count()
     with ClockSampler(local) as clk:
@@ -502,7 +505,7 @@ def main():
         # prep), and with the one-pass fp16 Gram (TF32's significand), each tuned like the headline plan
         for name, kw in (("graph", {"graph": 1, "inputs_ready": 0}), ("gram_f16", {"gram_precision": L.LCF_GP_F16})):
             vp = plan_for(path, **kw)
-            vp.autotune(d_ring[0])
+            vp.autotune(d_ring[0], cache_path=args.tune_cache)
             ms_v = timed(vp, args.steps, args.warmup)
             variants[name] = {"value": world * args.steps / (ms_v / 1e3), "tuning": vp.tuning().as_dict()}
             vp.close()

@@ -1,0 +1,773 @@
+// k_evd_osc.cu — batched Hermitian EVD (Eq. 2) by one-sided Jacobi on a Cholesky
+// factor for packets longer than one SM holds (128 < Nt <= 224), on a cluster of
+// four CTAs per window.
+//
+// Same numerical plan as the one-CTA kernel (k_evd_os.cu): B = Q^H (R / scale) Q
+// from the distributed EVD's prep kernel (FP32 subspace iteration, Householder QR,
+// double-float congruence), its pivoted FP32 Cholesky factor L, one-sided Jacobi
+// (Hestenes) on the columns of F = P L until every pair of columns is orthogonal to
+// the relative tolerance, eigenvalue = squared column norm, eigenvector = column /
+// norm, V = Q U, sort, rules, alpha, phase fix, W.
+//
+//  evd_chol_kernel   one CTA per window: the packed lower triangle of B in shared
+//                    memory, factored in panels of eight columns (warp 0 factors a
+//                    panel left-looking with the pivot on the running diagonal,
+//                    every warp applies it to the trailing triangle); L (pivot row
+//                    order), the permutation and the numerical rank to global memory.
+//  evd_osc_kernel    the sweeps and everything after, on a cluster of four CTAs.  CTA
+//                    c holds rows [c R, (c + 1) R) (R = ceil(Nt / 4)) of every column in
+//                    registers; warp w owns pair slots 8w .. 8w + 7 of the circle
+//                    ordering (16 columns), lane l rows l and l + 32 of the CTA's share
+//                    as one packed pair.  A step sums each slot's partial 2x2 Gram over
+//                    the warp (reduce-scatter: lane l ends with value l), sends that
+//                    partial to the other three CTAs (st.async into their shared memory,
+//                    completing the bytes of their step-parity mbarrier), adds the four
+//                    partials in rank order (so every CTA forms the same rotations),
+//                    rotates, and moves columns: inside a warp by renaming registers
+//                    (period eight), between warps through shared memory.  Every wait
+//                    is bounded (2 s).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "evd_common.cuh"
+#include "lcf_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lcf {
+
+constexpr int EC_THREADS = 1024;               // Cholesky kernel
+constexpr int EC_PANEL = 8;
+constexpr int EQ_C = 4;                        // CTAs per window of the sweeps
+constexpr int EQ_S = 8;                        // pair slots per warp
+constexpr float EQ_TOL = 2.0e-6f;              // relative orthogonality test
+constexpr int EQ_SUBSPACE_ITERS = 6;
+
+// ---------------------------------------------------------------------------------------------
+// evd_chol_kernel: packed lower triangle (i, c <= i) at i (i + 1) / 2 + c
+__host__ __device__ inline size_t ec_tri(int n) { return (size_t)n * (n + 1) / 2; }
+size_t evd_chol_smem_bytes(int n) { return ec_tri(n) * 8 + (size_t)n * 4 + 64; }
+
+__global__ void __launch_bounds__(EC_THREADS, 1)
+evd_chol_kernel(float2* __restrict__ Bg, const double* __restrict__ scale_g, int n, int* __restrict__ perm_g,
+                int* __restrict__ rank_g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = EC_THREADS / 32;
+  float2* A = reinterpret_cast<float2*>(smem);                 // packed lower triangle
+  float* dg = reinterpret_cast<float*>(smem + ec_tri(n) * 8);  // running diagonal
+  int* perm = perm_g + (size_t)k * n;
+  __shared__ int sh_rank, sh_stop;
+  float2* B = Bg + (size_t)k * n * n;
+  if (!(scale_g[k] > 0.0)) {   // degenerate window: the sweep kernel writes the empty result
+    if (tid == 0) rank_g[k] = 0;
+    return;
+  }
+  for (int i = warp; i < n; i += nwarp)
+    for (int c = lane; c <= i; c += 32) A[ec_tri(i) + c] = B[(size_t)i * n + c];
+  for (int i = tid; i < n; i += EC_THREADS) { dg[i] = B[(size_t)i * n + i].x; perm[i] = i; }
+  if (tid == 0) { sh_rank = n; sh_stop = 0; }
+  __syncthreads();
+  float first = 0.f;
+  for (int j0 = 0; j0 < n; j0 += EC_PANEL) {
+    const int j1 = j0 + EC_PANEL < n ? j0 + EC_PANEL : n;
+    if (warp == 0) {
+      for (int j = j0; j < j1; ++j) {
+        float best = -INFINITY;
+        int bi = 0x7fffffff;
+        for (int i = j + lane; i < n; i += 32) {
+          const float d = dg[i];
+          if (d > best) { best = d; bi = i; }
+        }
+        for (int o = 16; o; o >>= 1) {
+          const float ob = __shfl_xor_sync(~0u, best, o);
+          const int oi = __shfl_xor_sync(~0u, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (j == 0) first = best;
+        if (!(best > first * 1e-30f) || !isfinite(best)) {
+          if (lane == 0) { sh_rank = j; sh_stop = 1; }
+          break;
+        }
+        const int p = bi;
+        if (p != j) {   // symmetric interchange of j and p (pending panel updates move with the rows)
+          for (int c = lane; c < n; c += 32) {
+            float2 t;
+            if (c < j) {
+              t = A[ec_tri(j) + c]; A[ec_tri(j) + c] = A[ec_tri(p) + c]; A[ec_tri(p) + c] = t;
+            } else if (c == j) {
+              t = A[ec_tri(j) + j]; A[ec_tri(j) + j] = A[ec_tri(p) + p]; A[ec_tri(p) + p] = t;
+              A[ec_tri(p) + j] = cconj(A[ec_tri(p) + j]);
+            } else if (c < p) {
+              t = A[ec_tri(c) + j];
+              A[ec_tri(c) + j] = cconj(A[ec_tri(p) + c]);
+              A[ec_tri(p) + c] = cconj(t);
+            } else if (c > p) {
+              t = A[ec_tri(c) + j]; A[ec_tri(c) + j] = A[ec_tri(c) + p]; A[ec_tri(c) + p] = t;
+            }
+          }
+          if (lane == 0) {
+            const float td = dg[j]; dg[j] = dg[p]; dg[p] = td;
+            const int tp = perm[j]; perm[j] = perm[p]; perm[p] = tp;
+          }
+          __syncwarp();
+        }
+        const float inv = ep_rsqrt(best);
+        for (int i = j + 1 + lane; i < n; i += 32) {
+          float2 v = A[ec_tri(i) + j];
+          for (int l = j0; l < j; ++l) v = csub(v, cmul(A[ec_tri(i) + l], cconj(A[ec_tri(j) + l])));
+          v = cscale(v, inv);
+          A[ec_tri(i) + j] = v;
+          dg[i] -= cabs2(v);
+        }
+        if (lane == 0) A[ec_tri(j) + j] = make_float2(best * inv, 0.f);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (sh_stop) break;
+    for (int i = j1 + warp; i < n; i += nwarp) {
+      for (int l = j1 + lane; l <= i; l += 32) {
+        float2 acc = A[ec_tri(i) + l];
+        for (int c = j0; c < j1; ++c) acc = csub(acc, cmul(A[ec_tri(i) + c], cconj(A[ec_tri(l) + c])));
+        A[ec_tri(i) + l] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int rk = sh_rank;
+  // L (rows in pivot order) over B: zero above the diagonal and from column rk on
+  for (int e = tid; e < n * n; e += EC_THREADS) {
+    const int i = e / n, c = e % n;
+    B[e] = (c <= i && c < rk) ? A[ec_tri(i) + c] : make_float2(0.f, 0.f);
+  }
+  if (tid == 0) rank_g[k] = rk;
+}
+
+
+
+struct EqArgs {
+  int nt, nz, nx;
+  int thresh_mode;
+  double beta, beta_src;
+  int k_fixed, k_src;
+  int pd_mode, alpha_mode, curv_norm, max_sweeps;
+  int ncp;
+  int* err;
+};
+
+__host__ __device__ inline size_t eq_align(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct EqLayout {
+  int np, h, nw, R, lda, m;
+  size_t u, x, lamp, lam, sperm, perm, lams, wts, s0, s1, s2, coef, keep, phs, cmax, vh, tm, y, bar, end;
+};
+// u: this CTA's rows of the columns (then of U, then of V); x: the sweeps' exchange buffers, later
+// the partial products Vh^H U of every CTA
+__host__ __device__ inline EqLayout eq_layout(int n) {
+  EqLayout L;
+  // the pair slots are padded to whole warps (zero columns, which never rotate), so the last slot
+  // of the ordering is always slot 7 of the last warp
+  L.nw = ((n + 1) / 2 + EQ_S - 1) / EQ_S;
+  L.h = EQ_S * L.nw;
+  L.np = 2 * L.h;
+  L.R = (n + EQ_C - 1) / EQ_C;
+  L.lda = L.np + 1;
+  L.m = n < kEvdHead ? n : kEvdHead;
+  size_t o = 0;
+  L.u = o;     o = eq_align(o + (size_t)L.R * L.lda * 8);
+  {
+    const size_t sweep = (size_t)2 * 2 * L.nw * 32 * 16 + (size_t)2 * EQ_C * L.nw * 32 * 4;
+    const size_t post = (size_t)EQ_C * L.m * L.np * 8;
+    L.x = o;   o = eq_align(o + (sweep > post ? sweep : post));
+  }
+  L.lamp = o;  o = eq_align(o + (size_t)EQ_C * L.np * 8);
+  L.lam = o;   o = eq_align(o + (size_t)L.np * 8);
+  L.sperm = o; o = eq_align(o + (size_t)L.np * 4);
+  L.perm = o;  o = eq_align(o + (size_t)L.np * 4);
+  L.lams = o;  o = eq_align(o + (size_t)L.np * 8);
+  L.wts = o;   o = eq_align(o + (size_t)L.np * 8);
+  L.s0 = o;    o = eq_align(o + (size_t)L.np * 8);
+  L.s1 = o;    o = eq_align(o + (size_t)L.np * 8);
+  L.s2 = o;    o = eq_align(o + (size_t)L.np * 8);
+  L.coef = o;  o = eq_align(o + (size_t)L.np * 4);
+  L.keep = o;  o = eq_align(o + (size_t)(L.np + 1) * 4);
+  L.phs = o;   o = eq_align(o + (size_t)L.np * 8);
+  L.cmax = o;  o = eq_align(o + (size_t)EQ_C * L.np * 16);
+  L.vh = o;    o = eq_align(o + (size_t)L.m * n * 8);
+  L.tm = o;    o = eq_align(o + (size_t)L.m * L.m * 8);
+  L.y = o;     o = eq_align(o + (size_t)L.m * L.np * 8);
+  L.bar = o;   o = eq_align(o + 2 * 8);
+  L.end = o;
+  return L;
+}
+size_t evd_osc_smem_bytes(int nt) { return eq_layout(nt).end; }
+
+// ---------------------------------------------------------------------------------------------
+// evd_osc_kernel: the sweeps on a cluster of EQ_C CTAs
+struct EqCtx {
+  float4* xt;            // [parity][warp][lane]: the top leaving slot 7
+  float4* xb;            // [parity][warp][lane]: the bottom leaving slot 0
+  float* recv;           // [parity][source rank][warp][lane]: the other CTAs' partial sums
+  uint32_t peer_recv[EQ_C], peer_bar[EQ_C];   // cluster addresses of each CTA's recv and mbarriers
+  uint64_t* bar;         // this CTA's mbarriers, one per step parity
+  unsigned bytes;        // partial-sum bytes a step brings in: (EQ_C - 1) * nw * 32 * 4
+  int nw, h, warp, lane, tid, rank;
+  bool wfirst, wlast;
+};
+
+__device__ __forceinline__ void eq_st_async_f32(uint32_t addr, float v, uint32_t bar_cluster_addr) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(addr), "r"(__float_as_uint(v)), "r"(bar_cluster_addr) : "memory");
+}
+
+// The reduce-scatter of 32 partial sums (value 4 s + c: slot s, component c) after its first level
+// (w16[q] = value q + value q + 16 on lanes without bit 4, value q + 16 + value q on the others):
+// lane l receives the warp's sum of value l
+__device__ __forceinline__ float eq_reduce_scatter_rest(const float (&w16)[16], int lane) {
+  float w8[8], w4[4], w2[2];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const bool hi = lane & 8;
+    w8[q] = (hi ? w16[8 + q] : w16[q]) + __shfl_xor_sync(~0u, hi ? w16[q] : w16[8 + q], 8);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool hi = lane & 4;
+    w4[q] = (hi ? w8[4 + q] : w8[q]) + __shfl_xor_sync(~0u, hi ? w8[q] : w8[4 + q], 4);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const bool hi = lane & 2;
+    w2[q] = (hi ? w4[2 + q] : w4[q]) + __shfl_xor_sync(~0u, hi ? w4[q] : w4[2 + q], 2);
+  }
+  const bool hi = lane & 1;
+  return (hi ? w2[1] : w2[0]) + __shfl_xor_sync(~0u, hi ? w2[0] : w2[1], 1);
+}
+
+// |top|^2, |bottom|^2, Re and Im of conj(top) bottom over the lane's two rows
+__device__ __forceinline__ void eq_gram(float2 tr, float2 ti, float2 br, float2 bi, float (&u)[4]) {
+  float2 a2 = __fmul2_rn(tr, tr);
+  a2 = __ffma2_rn(ti, ti, a2);
+  float2 b2 = __fmul2_rn(br, br);
+  b2 = __ffma2_rn(bi, bi, b2);
+  float2 gr = __fmul2_rn(tr, br);
+  gr = __ffma2_rn(ti, bi, gr);
+  const float2 gi = __fmul2_rn(tr, bi), gj = __fmul2_rn(ti, br);
+  u[0] = a2.x + a2.y;
+  u[1] = b2.x + b2.y;
+  u[2] = gr.x + gr.y;
+  u[3] = (gi.x + gi.y) - (gj.x + gj.y);
+}
+
+// One step at phase U of an eight-step block (slot s keeps its top in T*[(s - U) & 7], its bottom
+// in B*[(s + U) & 7]); r is the step's index (its parity picks the buffers and the mbarrier).
+// Returns whether any slot of the CTA rotated; *ok turns false when a wait gives up.
+template <int U>
+__device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 (&BR)[8], float2 (&BI)[8],
+                                       const EqCtx& x, int r, bool* ok) {
+  const int lane = x.lane, par = r & 1;
+  // slots s and s + 4 together, folded at once into the first level of the reduce-scatter
+  float w16[16];
+  const bool hi16 = lane & 16;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    float u[4], u2[4];
+    eq_gram(TR[(s - U) & 7], TI[(s - U) & 7], BR[(s + U) & 7], BI[(s + U) & 7], u);
+    eq_gram(TR[(s + 4 - U) & 7], TI[(s + 4 - U) & 7], BR[(s + 4 + U) & 7], BI[(s + 4 + U) & 7], u2);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      w16[4 * s + c] = (hi16 ? u2[c] : u[c]) + __shfl_xor_sync(~0u, hi16 ? u[c] : u2[c], 16);
+  }
+  const float part = eq_reduce_scatter_rest(w16, lane);   // this CTA's rows
+  // ---- the partial to the other CTAs, then the sum of all four in rank order
+  if (x.tid == 0) ep_arrive_expect_tx(&x.bar[par], x.bytes);
+  const uint32_t off = (uint32_t)((((par * EQ_C + x.rank) * x.nw + x.warp) * 32 + lane) * 4);
+#pragma unroll
+  for (int q = 0; q < EQ_C; ++q)
+    if (q != x.rank) eq_st_async_f32(x.peer_recv[q] + off, part, x.peer_bar[q] + (uint32_t)(par * 8));
+  if (*ok) *ok = ep_wait(&x.bar[par], (r >> 1) & 1);
+  float tot = 0.f;
+#pragma unroll
+  for (int q = 0; q < EQ_C; ++q)
+    tot += q == x.rank ? part : x.recv[(((par * EQ_C + q) * x.nw + x.warp) * 32) + lane];
+  // ---- each group of four lanes forms the rotation of slot lane >> 2
+  const int base = lane & 28;
+  const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 1);
+  const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 2), __shfl_sync(~0u, tot, base + 3));
+  float c, dp, dq;
+  float2 st;
+  int rot;
+  ep_rotation2(a, b, gm, EQ_TOL, c, st, dp, dq, rot);
+  const unsigned rmask = __ballot_sync(~0u, rot);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    if (!((rmask >> (4 * s)) & 1u)) continue;   // warp-uniform
+    const float cs = __shfl_sync(~0u, c, 4 * s), sr = __shfl_sync(~0u, st.x, 4 * s), si = __shfl_sync(~0u, st.y, 4 * s);
+    const int t = (s - U) & 7, bb = (s + U) & 7;
+    const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
+    const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
+    const float2 xr = TR[t], xi = TI[t], yr = BR[bb], yi = BI[bb];
+    TR[t] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
+    TI[t] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
+    BR[bb] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
+    BI[bb] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
+  }
+  // ---- the circle move: slot 7's top and slot 0's bottom leave the warp
+  const int t7 = (7 - U) & 7, t0 = (0 - U) & 7, b0 = U & 7;
+  {
+    x.xt[(par * x.nw + x.warp) * 32 + lane] = make_float4(TR[t7].x, TR[t7].y, TI[t7].x, TI[t7].y);
+    x.xb[(par * x.nw + x.warp) * 32 + lane] = make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y);
+  }
+  const int any = __syncthreads_or(rmask != 0u);
+  // slot h - 1 (slot 7 of the last warp) takes its own top as bottom, into the register slot 0's
+  // bottom left; slot 0 keeps its top, slot 1 takes slot 0's bottom (through a temporary when one
+  // warp holds both ends)
+  if (x.wfirst && x.wlast) {
+    const float2 tr = BR[b0], ti = BI[b0];
+    BR[b0] = TR[t7]; BI[b0] = TI[t7];
+    TR[t7] = TR[t0]; TI[t7] = TI[t0];
+    TR[t0] = tr; TI[t0] = ti;
+  } else if (x.wlast) {
+    BR[b0] = TR[t7]; BI[b0] = TI[t7];
+  } else if (x.wfirst) {
+    TR[t7] = TR[t0]; TI[t7] = TI[t0];
+    TR[t0] = BR[b0]; TI[t0] = BI[b0];
+  }
+  if (x.warp > 0) {
+    const float4 q = x.xt[(par * x.nw + x.warp - 1) * 32 + lane];
+    TR[t7] = make_float2(q.x, q.y); TI[t7] = make_float2(q.z, q.w);
+  }
+  if (8 * x.warp + 7 < x.h - 1) {
+    const float4 q = x.xb[(par * x.nw + x.warp + 1) * 32 + lane];
+    BR[b0] = make_float2(q.x, q.y); BI[b0] = make_float2(q.z, q.w);
+  }
+  return any;
+}
+
+
+__global__ void __launch_bounds__(32 * ((kEvdOscNmax / 2 + EQ_S - 1) / EQ_S), 1)
+evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
+               const float2* __restrict__ Vhg, const float2* __restrict__ Tg, const double* __restrict__ scale_g,
+               const Box* __restrict__ boxes, EqArgs g, double* __restrict__ lam_out, float2* __restrict__ V_out,
+               float* __restrict__ wt_out, int* __restrict__ kcut_out, float* __restrict__ alpha_out,
+               int* __restrict__ flags_out, float2* __restrict__ W_out, int* __restrict__ ncol_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), k = blockIdx.x / EQ_C, n = g.nt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
+  const EqLayout L = eq_layout(n);
+  const int np = L.np, h = L.h, lda = L.lda, m = L.m;
+  const int r0 = rank * L.R, r1 = r0 + L.R < n ? r0 + L.R : n, nr = r1 > r0 ? r1 - r0 : 0;   // own rows (pivot order)
+  float2* U = reinterpret_cast<float2*>(smem + L.u);   // [row - r0][pos]
+  double* lamp = reinterpret_cast<double*>(smem + L.lamp);
+  double* lam = reinterpret_cast<double*>(smem + L.lam);
+  int* sperm = reinterpret_cast<int*>(smem + L.sperm);
+  int* perm = reinterpret_cast<int*>(smem + L.perm);
+  double* lam_s = reinterpret_cast<double*>(smem + L.lams);
+  double* wts = reinterpret_cast<double*>(smem + L.wts);
+  double* s0 = reinterpret_cast<double*>(smem + L.s0);
+  double* s1 = reinterpret_cast<double*>(smem + L.s1);
+  double* s2 = reinterpret_cast<double*>(smem + L.s2);
+  float* coef = reinterpret_cast<float*>(smem + L.coef);
+  int* keep = reinterpret_cast<int*>(smem + L.keep);
+  float2* phs = reinterpret_cast<float2*>(smem + L.phs);
+  float4* cmax = reinterpret_cast<float4*>(smem + L.cmax);
+  float2* Vh = reinterpret_cast<float2*>(smem + L.vh);
+  float2* Tm = reinterpret_cast<float2*>(smem + L.tm);
+  float2* Y = reinterpret_cast<float2*>(smem + L.y);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  const double scale = scale_g[k];
+
+  if (!(scale > 0.0)) {   // degenerate window (zero Gram): every CTA writes its share of the empty result
+    const int v0 = (int)((long)n * rank / EQ_C), v1 = (int)((long)n * (rank + 1) / EQ_C);
+    for (int e = tid; e < (v1 - v0) * n; e += nthr) {
+      const int a = v0 + e / n, c = e % n;
+      V_out[(size_t)k * n * n + (size_t)a * n + c] = make_float2(a == c, 0.f);
+    }
+    for (int e = tid; e < (v1 - v0) * g.ncp; e += nthr) W_out[(size_t)k * n * g.ncp + (size_t)v0 * g.ncp + e] = make_float2(0.f, 0.f);
+    if (rank == 0) {
+      for (int i = tid; i < n; i += nthr) { lam_out[(size_t)k * n + i] = 0.0; wt_out[(size_t)k * n + i] = 0.f; }
+      if (tid == 0) { kcut_out[k] = 0; alpha_out[k] = 0.f; ncol_out[k] = 0; flags_out[k] = LCF_WFLAG_DEGENERATE; }
+    }
+    return;   // every CTA of the cluster leaves before any cluster-level exchange
+  }
+  for (int i = tid; i < n; i += nthr) perm[i] = perm_g[(size_t)k * n + i];
+  if (tid == 0) {
+    ep_bar_init(&bar[0], 1);
+    ep_bar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster.sync();   // barriers of every CTA initialised
+
+  EqCtx xc;
+  xc.xt = reinterpret_cast<float4*>(smem + L.x);
+  xc.xb = xc.xt + (size_t)2 * L.nw * 32;
+  xc.recv = reinterpret_cast<float*>(xc.xb + (size_t)2 * L.nw * 32);
+  for (int q = 0; q < EQ_C; ++q) {
+    xc.peer_recv[q] = ep_mapa(ep_smem(xc.recv), (uint32_t)q);
+    xc.peer_bar[q] = ep_mapa(ep_smem(bar), (uint32_t)q);
+  }
+  xc.bar = bar;
+  xc.bytes = (unsigned)((EQ_C - 1) * L.nw * 32 * 4);
+  xc.nw = L.nw; xc.h = h; xc.warp = warp; xc.lane = lane; xc.tid = tid; xc.rank = rank;
+  xc.wfirst = warp == 0;
+  xc.wlast = warp == L.nw - 1;
+
+  // ---- registers: slot p = 8 warp + s holds columns (2p, 2p + 1); lane l rows r0 + l and r0 + 32 + l
+  float2 TR[8], TI[8], BR[8], BI[8];
+  {
+    const float2* Lw = Lg + (size_t)k * n * n;
+    const int ra = r0 + lane, rb = r0 + 32 + lane;
+    const bool va = lane < nr, vb = 32 + lane < nr;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int p = EQ_S * warp + s, ct = 2 * p, cb = 2 * p + 1;
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 ta = (p < h && va && ct < n) ? Lw[(size_t)ra * n + ct] : z;
+      const float2 tb = (p < h && vb && ct < n) ? Lw[(size_t)rb * n + ct] : z;
+      const float2 ba = (p < h && va && cb < n) ? Lw[(size_t)ra * n + cb] : z;
+      const float2 bb = (p < h && vb && cb < n) ? Lw[(size_t)rb * n + cb] : z;
+      TR[s] = make_float2(ta.x, tb.x); TI[s] = make_float2(ta.y, tb.y);
+      BR[s] = make_float2(ba.x, bb.x); BI[s] = make_float2(ba.y, bb.y);
+    }
+  }
+  // ---- sweeps, in blocks of eight steps; converged once a whole circle (np - 1 steps) rotated
+  // nothing.  Every CTA forms the same rotations, so every CTA reaches the same decision.
+  __shared__ int sh_fail;
+  if (tid == 0) sh_fail = 0;
+  __syncthreads();
+  bool ok = true;
+  int converged = 0, sweeps = 0;
+  {
+    const int per = np - 1;
+    const int maxsteps = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
+    int steps = 0, quiet = 0, last = 0;
+    auto track = [&](int any) {
+      ++steps;
+      if (any) { quiet = 0; last = steps; }
+      else ++quiet;
+    };
+    while (steps < maxsteps) {
+      int a = eq_step<0>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<1>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<2>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<3>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<4>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<5>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<6>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      a = eq_step<7>(TR, TI, BR, BI, xc, steps, &ok); track(a);
+      if (__syncthreads_or(!ok)) { sh_fail = 1; break; }   // a wait gave up: stop exchanging
+      if (quiet >= per) { converged = 1; break; }
+    }
+    sweeps = (last + per - 1) / per;
+  }
+  __syncthreads();
+  ok = !sh_fail;
+
+  // ---- squared column norms: this CTA's rows (double-float), summed over the cluster in rank order
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int p = EQ_S * warp + s;
+    df na = {0.f, 0.f}, nb = {0.f, 0.f};
+    na = df_add_f(na, fmaf(TR[s].x, TR[s].x, TI[s].x * TI[s].x));
+    na = df_add_f(na, fmaf(TR[s].y, TR[s].y, TI[s].y * TI[s].y));
+    nb = df_add_f(nb, fmaf(BR[s].x, BR[s].x, BI[s].x * BI[s].x));
+    nb = df_add_f(nb, fmaf(BR[s].y, BR[s].y, BI[s].y * BI[s].y));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      df t;
+      t.hi = __shfl_xor_sync(~0u, na.hi, o); t.lo = __shfl_xor_sync(~0u, na.lo, o); na = df_add(na, t);
+      t.hi = __shfl_xor_sync(~0u, nb.hi, o); t.lo = __shfl_xor_sync(~0u, nb.lo, o); nb = df_add(nb, t);
+    }
+    if (p < h && lane < EQ_C) {   // lane q writes into CTA q
+      double* dst = cluster.map_shared_rank(lamp, (unsigned)lane);
+      dst[rank * np + 2 * p] = (double)na.hi + (double)na.lo;
+      dst[rank * np + 2 * p + 1] = (double)nb.hi + (double)nb.lo;
+    }
+    // this CTA's rows, unnormalised for now
+    if (p < h) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int rr = e * 32 + lane;
+        if (rr < nr) {
+          U[(size_t)rr * lda + 2 * p] = make_float2(e ? TR[s].y : TR[s].x, e ? TI[s].y : TI[s].x);
+          U[(size_t)rr * lda + 2 * p + 1] = make_float2(e ? BR[s].y : BR[s].x, e ? BI[s].y : BI[s].x);
+        }
+      }
+    }
+  }
+  cluster.sync();   // every CTA's partial norms are here
+  for (int i = tid; i < np; i += nthr) {
+    double t = 0.0;
+    for (int q = 0; q < EQ_C; ++q) t += lamp[q * np + i];
+    lam[i] = t > 7.888609052210118e-31 ? t : 0.0;   // below 2^-100 (largest diagonal in [1/2, 1)): vanished
+  }
+  __syncthreads();
+  for (int i = tid; i < np; i += nthr) {   // positions by squared norm, descending, ties to the lower one
+    const double di = lam[i];
+    int r = 0;
+    for (int j = 0; j < np; ++j) {
+      const double dj = lam[j];
+      r += (dj > di) || (dj == di && j < i);
+    }
+    sperm[r] = i;
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * np; e += nthr) {   // normalise
+    const int rr = e / np, pos = e % np;
+    const float sc = lam[pos] > 0.0 ? ep_rsqrt((float)lam[pos]) : 0.f;
+    U[(size_t)rr * lda + pos] = cscale(U[(size_t)rr * lda + pos], sc);
+  }
+  __syncthreads();
+  // ---- vanished columns (numerical rank below Nt): Gram-Schmidt completion on CTA 0 over the whole
+  // columns, through the scratch buffer [pos][row] in global memory (every CTA decides the same)
+  int nzero = 0;
+  for (int jj = 0; jj < n; ++jj) nzero += lam[sperm[jj]] == 0.0;
+  if (nzero > 0) {
+    float2* S = V_out + (size_t)k * n * n;   // [sorted index][row]: V_out is written last
+    for (int e = tid; e < nr * n; e += nthr) {
+      const int rr = e / n, jj = e % n;
+      S[(size_t)jj * n + r0 + rr] = U[(size_t)rr * lda + sperm[jj]];
+    }
+    cluster.sync();
+    if (rank == 0 && warp == 0) {
+      int cand = 0;
+      for (int jj = 0; jj < n; ++jj) {
+        if (lam[sperm[jj]] > 0.0) continue;
+        float2* col = S + (size_t)jj * n;
+        for (int tries = 0; tries < n; ++tries, cand = (cand + 1) % n) {
+          for (int r = lane; r < n; r += 32) col[r] = make_float2(r == cand ? 1.f : 0.f, 0.f);
+          __syncwarp();
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int q = 0; q < jj; ++q) {
+              const float2* cq = S + (size_t)q * n;
+              float2 d = make_float2(0.f, 0.f);
+              for (int r = lane; r < n; r += 32) d = cadd(d, cmulc(cq[r], col[r]));
+              for (int o = 16; o; o >>= 1) { d.x += __shfl_xor_sync(~0u, d.x, o); d.y += __shfl_xor_sync(~0u, d.y, o); }
+              for (int r = lane; r < n; r += 32) col[r] = csub(col[r], cmul(d, cq[r]));
+              __syncwarp();
+            }
+          }
+          float nrm = 0.f;
+          for (int r = lane; r < n; r += 32) nrm += cabs2(col[r]);
+          for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(~0u, nrm, o);
+          if (nrm > 0.5f / n) {   // some unit vector keeps at least 1/n of its square in the complement
+            const float sc = ep_rsqrt(nrm);
+            for (int r = lane; r < n; r += 32) col[r] = cscale(col[r], sc);
+            __syncwarp();
+            cand = (cand + 1) % n;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    cluster.sync();
+    for (int e = tid; e < nr * n; e += nthr) {
+      const int rr = e / n, jj = e % n;
+      U[(size_t)rr * lda + sperm[jj]] = S[(size_t)jj * n + r0 + rr];
+    }
+    __syncthreads();
+  }
+  // ---- V = Q U = U - Vh (T (Vh^H U)): Vh^H U summed over the cluster (rank order)
+  float2* Xp = reinterpret_cast<float2*>(smem + L.x);   // [source rank][j][pos] (the sweeps are over)
+  for (int e = tid; e < m * n; e += nthr) Vh[e] = Vhg[(size_t)k * m * n + e];
+  for (int e = tid; e < m * m; e += nthr) Tm[e] = Tg[(size_t)k * m * m + e];
+  __syncthreads();
+  for (int e = tid; e < m * np; e += nthr) {
+    const int j = e / np, pos = e % np;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int rr = 0; rr < nr; ++rr) acc = cadd(acc, cmulc(Vh[(size_t)j * n + perm[r0 + rr]], U[(size_t)rr * lda + pos]));
+    for (int q = 0; q < EQ_C; ++q) cluster.map_shared_rank(Xp, (unsigned)q)[((size_t)rank * m + j) * np + pos] = acc;
+  }
+  cluster.sync();
+  for (int e = tid; e < m * np; e += nthr) {   // Y = T X, T upper triangular
+    const int i = e / np, pos = e % np;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = i; j < m; ++j) {
+      float2 xs = make_float2(0.f, 0.f);
+      for (int q = 0; q < EQ_C; ++q) xs = cadd(xs, Xp[((size_t)q * m + j) * np + pos]);
+      acc = cadd(acc, cmul(Tm[i * m + j], xs));
+    }
+    Y[e] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * np; e += nthr) {
+    const int rr = e / np, pos = e % np, a = perm[r0 + rr];
+    float2 v = U[(size_t)rr * lda + pos];
+    for (int j = 0; j < m; ++j) v = csub(v, cmul(Vh[(size_t)j * n + a], Y[(size_t)j * np + pos]));
+    U[(size_t)rr * lda + pos] = v;
+  }
+  // ---- sort, rule, alpha, kept columns (every CTA the same; CTA 0 writes the per-window results)
+  for (int i = tid; i < n; i += nthr) lam_s[i] = lam[sperm[i]] * scale;
+  __syncthreads();
+  if (warp == 0) {
+    int kk = -1;
+    const int md = g.thresh_mode;
+    if (md == LCF_T_NONE) {
+      for (int i = lane; i < n; i += 32) wts[i] = 1.0;
+      kk = 0;
+    } else if (md <= LCF_T_MEDIAN) {
+      kk = ep_rule_k(md, lam_s, n, g.beta, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+      for (int i = lane; i < n; i += 32) wts[i] = (i + 1 > kk) ? 1.0 : 0.0;
+    } else if (md == LCF_T_SIGMOID) {
+      kk = ep_rule_k(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
+      for (int i = lane; i < n; i += 32) wts[i] = 1.0 / (1.0 + exp(-g.beta * ((i + 1) - kk)));
+    } else {   // LCF_T_ADAPTIVE_SOFT (method 4's rule is applied afterwards by the post kernel)
+      double mx = -INFINITY;
+      for (int i = lane; i < n; i += 32) {
+        const double u = n > 1 ? 2.5 * i / (n - 1) : 0.0;
+        wts[i] = -0.5 * u * u - g.beta * log(ep_floor(lam_s, n, i));
+        mx = fmax(mx, wts[i]);
+      }
+      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(~0u, mx, o));
+      for (int i = lane; i < n; i += 32) wts[i] = exp(wts[i] - mx);
+      kk = -1;
+    }
+    __syncwarp();
+    double S = 0.0;
+    for (int i = lane; i < n; i += 32) S += wts[i] * wts[i] * lam_s[i];
+    for (int o = 16; o; o >>= 1) S += __shfl_xor_sync(~0u, S, o);
+    double cf = 0.0;
+    if (lane == 0) {
+      const double pdsum = g.pd_mode == 0 ? S / n : S;
+      double al;
+      int fl = (converged ? 0 : LCF_WFLAG_NOCONV) | ((sweeps < 255 ? sweeps : 255) << LCF_WFLAG_SWEEP_SHIFT);
+      if (g.alpha_mode == 1) al = 1.0;
+      else {
+        const Box bx = boxes[k];
+        const double cnt = g.alpha_mode == 2 ? (double)(bx.z1 - bx.z0) * (bx.x1 - bx.x0) : (double)g.nz * g.nx;
+        if (pdsum <= 1e-300) { al = 0.0; fl |= LCF_WFLAG_DEGENERATE; }
+        else al = cnt / pdsum;
+      }
+      if (rank == 0) {
+        kcut_out[k] = kk;
+        alpha_out[k] = (float)al;
+        flags_out[k] = fl;
+      }
+      cf = sqrt(al * (g.pd_mode == 0 ? 1.0 / n : 1.0));
+    }
+    cf = __shfl_sync(~0u, cf, 0);
+    int base = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      const bool kp = i < n && wts[i] > 0.0;
+      const unsigned bal = __ballot_sync(~0u, kp);
+      if (kp) keep[1 + base + __popc(bal & ((1u << lane) - 1u))] = i;
+      if (i < n) coef[i] = (float)(wts[i] * cf);
+      base += __popc(bal);
+    }
+    if (lane == 0) {
+      keep[0] = base;
+      if (rank == 0) ncol_out[k] = base;
+    }
+  }
+  __syncthreads();
+  if (rank == 0) {
+    for (int i = tid; i < n; i += nthr) {
+      lam_out[(size_t)k * n + i] = lam_s[i];
+      wt_out[(size_t)k * n + i] = (float)wts[i];
+    }
+  }
+  // ---- phase of each sorted eigenvector: its largest-magnitude entry (over the cluster's rows, ties
+  // to the lower row by original index) made real positive
+  for (int jj = warp; jj < n; jj += nthr / 32) {
+    const int pos = sperm[jj];
+    float best = -1.f;
+    int ba = 0x7fffffff;
+    float2 bv = make_float2(0.f, 0.f);
+    for (int rr = lane; rr < nr; rr += 32) {
+      const float2 v = U[(size_t)rr * lda + pos];
+      const float mg = cabs2(v);
+      const int a = perm[r0 + rr];
+      if (mg > best || (mg == best && a < ba)) { best = mg; ba = a; bv = v; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      const float ob = __shfl_xor_sync(~0u, best, o);
+      const int oa = __shfl_xor_sync(~0u, ba, o);
+      const float ox = __shfl_xor_sync(~0u, bv.x, o), oy = __shfl_xor_sync(~0u, bv.y, o);
+      if (ob > best || (ob == best && oa < ba)) { best = ob; ba = oa; bv = make_float2(ox, oy); }
+    }
+    if (lane < EQ_C)
+      cluster.map_shared_rank(cmax, (unsigned)lane)[(size_t)rank * np + jj] = make_float4(best, __int_as_float(ba), bv.x, bv.y);
+  }
+  cluster.sync();
+  for (int jj = tid; jj < n; jj += nthr) {
+    float best = -1.f;
+    int ba = 0x7fffffff;
+    float2 bv = make_float2(1.f, 0.f);
+    for (int q = 0; q < EQ_C; ++q) {
+      const float4 c4 = cmax[(size_t)q * np + jj];
+      const int a = __float_as_int(c4.y);
+      if (c4.x > best || (c4.x == best && a < ba)) { best = c4.x; ba = a; bv = make_float2(c4.z, c4.w); }
+    }
+    const float mg = sqrtf(cabs2(bv));
+    phs[jj] = mg > 0.f ? make_float2(bv.x / mg, -bv.y / mg) : make_float2(1.f, 0.f);
+  }
+  __syncthreads();
+  // ---- V and W rows of this CTA (row a = perm[r] by original index)
+  for (int e = tid; e < nr * n; e += nthr) {
+    const int rr = e / n, jj = e % n, a = perm[r0 + rr];
+    V_out[(size_t)k * n * n + (size_t)a * n + jj] = cmul(U[(size_t)rr * lda + sperm[jj]], phs[jj]);
+  }
+  const int nc = keep[0];
+  for (int e = tid; e < nr * g.ncp; e += nthr) {
+    const int rr = e / g.ncp, c = e % g.ncp, a = perm[r0 + rr];
+    float2 v = make_float2(0.f, 0.f);
+    if (c < nc) {
+      const int jj = keep[1 + c];
+      v = cscale(cmul(U[(size_t)rr * lda + sperm[jj]], phs[jj]), coef[jj]);
+    }
+    W_out[(size_t)k * n * g.ncp + (size_t)a * g.ncp + c] = v;
+  }
+  if (!ok && tid == 0) atomicOr(g.err, 1);
+  cluster.sync();   // no CTA leaves while another may still write into its shared memory
+}
+
+
+cudaError_t launch_evd_osc(const lcf_plan* P, cudaStream_t st) {
+  const lcf_config& c = P->cfg;
+  const int n = P->nt;
+  cudaError_t e = launch_evd_prep(P, st, EQ_SUBSPACE_ITERS);
+  if (e != cudaSuccess) return e;
+  evd_chol_kernel<<<P->nd, EC_THREADS, evd_chol_smem_bytes(n), st>>>(P->ws.evd_B, P->ws.evd_scale, n, P->ws.evd_perm,
+                                                                       P->ws.evd_rank);
+  if ((e = counted(P)) != cudaSuccess) return e;
+  EqArgs a;
+  a.nt = n; a.nz = c.nz; a.nx = c.nx;
+  a.thresh_mode = c.thresh_mode; a.beta = c.beta; a.beta_src = c.beta_src;
+  a.k_fixed = c.k_fixed; a.k_src = c.k_src; a.pd_mode = c.pd_mode; a.alpha_mode = c.alpha_mode;
+  a.curv_norm = c.curv_norm; a.max_sweeps = c.max_sweeps; a.ncp = P->ncp;
+  a.err = P->ws.err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(EQ_C * P->nd);
+  cfg.blockDim = dim3(32 * eq_layout(n).nw);
+  cfg.dynamicSmemBytes = evd_osc_smem_bytes(n);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = EQ_C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, evd_osc_kernel, (const float2*)P->ws.evd_B, (const int*)P->ws.evd_perm,
+                         (const float2*)P->ws.evd_vh, (const float2*)P->ws.evd_t, (const double*)P->ws.evd_scale,
+                         (const Box*)P->ws.box, a, P->ws.lam, P->ws.V, P->ws.wt, P->ws.kcut, P->ws.alpha, P->ws.flags,
+                         P->ws.W, P->ws.ncol);
+  if (e != cudaSuccess) return e;
+  return counted(P);
+}
+
+cudaError_t evd_osc_configure() {
+  cudaError_t e = cudaFuncSetAttribute(evd_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)evd_chol_smem_bytes(kEvdOscNmax));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(evd_osc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)evd_osc_smem_bytes(kEvdOscNmax));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(evd_osc_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+  return e;
+}
+
+}  // namespace lcf

@@ -132,7 +132,7 @@ static cudaError_t dalloc(T** p, size_t count, size_t* total) {
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.gz, w.gx, w.box, w.phi, w.gglob, w.xa, w.gpart, w.gaug, w.xmax, w.gtc, w.gq, w.err, w.R, w.lam, w.V, w.wt, w.kcut, w.alpha,
                   w.flags, w.W, w.pw, w.ncol, w.tile_off, w.tile_win, w.bimg, w.bscale, w.evd_clk, w.mlp_w, w.mlp_b, w.mlp_dbg, w.evd_B, w.evd_vh, w.evd_t,
-                  w.evd_scale, w.iq_stage, w.pd_stage, w.phi_alt, w.xmax_alt, w.gglob_async, w.post_rq,
+                  w.evd_scale, w.evd_perm, w.evd_rank, w.iq_stage, w.pd_stage, w.phi_alt, w.xmax_alt, w.gglob_async, w.post_rq,
                   w.post_pv, w.post_isig, w.post_band, w.sub_qhi, w.sub_qlo, w.sub_off, w.sub_pdk,
                   w.sub_part};
   for (void* p : ptrs)
@@ -252,6 +252,10 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = dalloc(&w.evd_vh, nd * m * nt, &tot);
     if (e == cudaSuccess) e = dalloc(&w.evd_t, nd * m * m, &tot);
     if (e == cudaSuccess) e = dalloc(&w.evd_scale, nd, &tot);
+    if (e == cudaSuccess && cfg->evd_path == LCF_EVD_OS && P->nt > kEvdPairNmax && P->nt <= kEvdOscNmax) {
+      e = dalloc(&w.evd_perm, nd * nt, &tot);
+      if (e == cudaSuccess) e = dalloc(&w.evd_rank, nd, &tot);
+    }
   }
   if (e == cudaSuccess && cfg->evd_precision == LCF_EP_FP64_POLISH)
     e = dalloc(&w.post_rq, nd * post_rq_blocks(P->nt) * nt, &tot);
@@ -316,6 +320,7 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     if (e == cudaSuccess) e = evd_pair_configure();
     if (e == cudaSuccess) e = evd_dist_configure();
     if (e == cudaSuccess) e = evd_os_configure();
+    if (e == cudaSuccess) e = evd_osc_configure();
     if (e == cudaSuccess) e = gram_simt_configure();
     if (e == cudaSuccess) e = post_configure();
     if (e == cudaSuccess && device < 64) g_configured[device] = true;
@@ -387,7 +392,8 @@ static lcf_status run_packet(lcf_plan* P, const float2* iq, float* out, cudaStre
   if (tc) LCF_CUDA(launch_gram_assemble_tc(P, st));
   else LCF_CUDA(launch_gram_assemble(P, st));
   LCF_MARK(LCF_STAGE_EVD);
-  if (c.evd_path != LCF_EVD_CTA && P->nt > kEvdPairNmax) LCF_CUDA(launch_evd_dist(P, st));
+  if (c.evd_path == LCF_EVD_OS && P->nt > kEvdPairNmax && P->nt <= kEvdOscNmax) LCF_CUDA(launch_evd_osc(P, st));
+  else if (c.evd_path != LCF_EVD_CTA && P->nt > kEvdPairNmax) LCF_CUDA(launch_evd_dist(P, st));
   else if (c.evd_path == LCF_EVD_PAIR) LCF_CUDA(launch_evd_pair(P, st));
   else if (c.evd_path == LCF_EVD_OS) LCF_CUDA(launch_evd_os(P, st));
   else LCF_CUDA(launch_evd(P, st));

@@ -98,6 +98,8 @@ struct Workspace {
   float2* evd_vh = nullptr;   // [nd][m][nt] Householder vectors of Q
   float2* evd_t = nullptr;    // [nd][m][m] compact WY factor T
   double* evd_scale = nullptr;// [nd] power-of-two scale (0: degenerate window)
+  int* evd_perm = nullptr;     // [nd][nt] pivot order of the Cholesky factor (one-sided EVD, Nt > 128)
+  int* evd_rank = nullptr;     // [nd] its numerical rank
   // learned cutoff rule (set by lcf_plan_set_mlp)
   __nv_bfloat16* mlp_w = nullptr;   // W1 | W2 | W3 | W4, bf16
   float* mlp_b = nullptr;           // b1 | b2 | b3 | b4
@@ -342,6 +344,10 @@ cudaError_t launch_evd_dist(const lcf_plan* P, cudaStream_t st);
 // from `iters` subspace iterations (the first stage of the distributed and one-sided EVDs)
 cudaError_t launch_evd_prep(const lcf_plan* P, cudaStream_t st, int iters);
 cudaError_t launch_evd_os(const lcf_plan* P, cudaStream_t st);
+// one-sided EVD for 128 < Nt <= kEvdOscNmax: Cholesky kernel, then a cluster of four CTAs per window
+constexpr int kEvdOscNmax = 224;
+cudaError_t launch_evd_osc(const lcf_plan* P, cudaStream_t st);
+cudaError_t evd_osc_configure();
 cudaError_t evd_os_configure();
 size_t evd_os_smem_bytes(int nt);
 cudaError_t evd_dist_configure();

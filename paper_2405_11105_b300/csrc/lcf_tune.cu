@@ -22,7 +22,9 @@ namespace {
 bool uses_tc_one_tile(const lcf_plan* P) { return P->cfg.gram_path == LCF_PATH_TC && P->tc_T == 1; }
 bool uses_aug(const lcf_plan* P) { return P->cfg.gram_path == LCF_PATH_SIMT || P->tc_na == P->nt; }
 bool uses_q(const lcf_plan* P) { return P->cfg.gram_path == LCF_PATH_TC && P->ndefl <= kQExactMax; }
-bool uses_dist(const lcf_plan* P) { return P->cfg.evd_path != LCF_EVD_CTA && P->nt > kEvdPairNmax; }
+bool uses_dist(const lcf_plan* P) {
+  return P->cfg.evd_path != LCF_EVD_CTA && P->nt > kEvdPairNmax && !(P->cfg.evd_path == LCF_EVD_OS && P->nt <= kEvdOscNmax);
+}
 
 // the split-dependent buffers, in the sizes their current splits need (elements)
 struct SplitSizes {

@@ -172,3 +172,57 @@ def test_os_learned_rule_is_refused():
     with pytest.raises(lib.LcfError) as e:
         lib.Plan(c).close()
     assert e.value.status == lib.LCF_EUNSUPPORTED
+
+
+# ---- packets longer than 128 frames: Cholesky kernel + four-CTA cluster sweeps (Nt <= 224)
+@pytest.mark.parametrize("shape,grid,mode,tc", [
+    ((129, 33, 29), (2, 2), "LCF_T_MEDIAN", False),      # shortest: 9 warps, 65 slots padded to 72
+    ((200, 40, 36), (2, 2), "LCF_T_CURVATURE", True),    # the streaming workload's packet length
+    ((200, 40, 36), (2, 2), "LCF_T_ADAPTIVE_SOFT", True),
+    ((201, 30, 26), (1, 2), "LCF_T_FIXED", False),       # odd length: a zero padding column
+    ((224, 24, 20), (1, 2), "LCF_T_SLOPE", True),        # longest on this path: 14 warps, no padding
+    ((150, 22, 18), (1, 1), "LCF_T_NCC", True),          # method 4 after the cluster EVD
+])
+def test_os_long_packets(shape, grid, mode, tc):
+    lib = L()
+    nt, nz, nx = shape
+    cfg, oc = os_cfg(nz, nx, nt, grid[0], grid[1], tc=tc, thresh_mode=getattr(lib, mode), k_fixed=3, beta=1.0)
+    check(compare(rand_iq(7, nt, nz, nx), cfg, oc, want_gram=False), soft=mode == "LCF_T_ADAPTIVE_SOFT")
+
+
+def test_os_long_rank_deficient():
+    """144 pixels, 160 frames: the Cholesky kernel stops at the numerical rank and CTA 0 completes
+    the vanished columns over the whole cluster's rows."""
+    lib = L()
+    cfg, oc = os_cfg(12, 12, 160, 1, 1, thresh_mode=lib.LCF_T_FIXED, k_fixed=2, all_ones_window=1)
+    check(compare(rand_iq(10, 160, 12, 12), cfg, oc, want_gram=False))
+
+
+def test_os_long_zero_packet_is_degenerate():
+    import torch
+    lib = L()
+    plan = lib.Plan.make(24, 20, 200, 2, 2, evd_path=lib.LCF_EVD_OS)
+    pd = plan.filter(torch.zeros((200, 24, 20), dtype=torch.complex64, device="cuda"))
+    st, flags = plan.status()
+    assert st == lib.LCF_EDEGENERATE
+    assert np.all(np.asarray(flags) & lib.LCF_WFLAG_DEGENERATE)
+    assert float(pd.abs().max()) == 0.0
+
+
+def test_os_long_matches_distributed_evd():
+    """The streaming length: eigenvalues and images of the one-sided cluster kernel and the
+    two-sided distributed kernel agree far inside the oracle tolerance."""
+    import torch
+    lib = L()
+    iq = torch.from_numpy(rand_iq(11, 200, 64, 48)).cuda()
+    res = {}
+    for ev in (lib.LCF_EVD_PAIR, lib.LCF_EVD_OS):
+        plan = lib.Plan.make(64, 48, 200, 4, 4, thresh_mode=lib.LCF_T_CURVATURE, beta=1.0, evd_path=ev)
+        pd = plan.filter(iq).cpu().numpy().astype(np.float64)
+        res[ev] = (pd, plan.debug()["lam"])
+    (pa, la), (pb, lb) = res[lib.LCF_EVD_PAIR], res[lib.LCF_EVD_OS]
+    band = la >= 1e-6 * la[:, :1]
+    rel = np.max(np.abs(la - lb)[band] / la[band])
+    print("eigenvalue rel diff", rel, "pd rel", np.linalg.norm(pa - pb) / np.linalg.norm(pa))
+    assert rel <= 2e-5
+    assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 2e-4
