@@ -32,20 +32,30 @@ SUM_P = 778752          # pixels summed over the 64 window supports
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the kernel on this workload, valid only while the kernel's sources hash as they did then
+# the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    "evd": {"bytes": 10.55e6, "profile": "profiles/evd_pair_kernel_256x128x100_8x8.md",
-            "sources": {"paper_2405_11105_b300/csrc/k_evd_pair.cu":
-                        "1009f85991485b46621e713d25b5986447e5b8d30cb1cd7cbbef818ea32fe087",
-                        "paper_2405_11105_b300/csrc/evd_common.cuh":
-                        "5f49c4e22ff1c65643b5fa3ad4b49488b54f5289a099077851b31487f275d22d"}},
+    # the one-sided EVD stage: evd_prep_kernel 10.35 MB + evd_os_kernel 3.88 MB
+    ("evd", "os"): {"bytes": 14.23e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+                    "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
+                                "61c763771922996b71be9c0c6ca02345299696e58b9964b73995d66b42f02d17",
+                                "paper_2405_11105_b300/csrc/k_evd_dist.cu":
+                                "0fd81ff905cede863522eebc24bd789f71a5f9777ed11f868ce1b85c099946e6",
+                                "paper_2405_11105_b300/csrc/evd_common.cuh":
+                                "5f49c4e22ff1c65643b5fa3ad4b49488b54f5289a099077851b31487f275d22d",
+                                "paper_2405_11105_b300/csrc/lcf_internal.cuh":
+                                "1e0aa59856ef34cb4cfdb48503a50b03a87dd782a8fce27ded9e732ed9cdd007"}},
+    ("evd", "pair"): {"bytes": 10.55e6, "profile": "profiles/evd_pair_kernel_256x128x100_8x8.md",
+                      "sources": {"paper_2405_11105_b300/csrc/k_evd_pair.cu":
+                                  "1009f85991485b46621e713d25b5986447e5b8d30cb1cd7cbbef818ea32fe087",
+                                  "paper_2405_11105_b300/csrc/evd_common.cuh":
+                                  "5f49c4e22ff1c65643b5fa3ad4b49488b54f5289a099077851b31487f275d22d"}},
 }
 
 
-def captured_traffic(stage):
-    """Bytes per launch from the capture, or None once a source of the kernel has changed."""
+def captured_traffic(stage, evd="os"):
+    """Bytes per launch from the capture, or None once a source of the stage's kernels has changed."""
     import hashlib
-    rec = CAPTURED_TRAFFIC.get(stage)
+    rec = CAPTURED_TRAFFIC.get((stage, evd))
     if not rec:
         return None
     for rel, digest in rec["sources"].items():
@@ -531,10 +541,15 @@ def main():
     achieved = (work.get(dom) or 0.0) / (per_launch[dom] * 1e-3) / 1e12 if work.get(dom) else None
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved and peak else None,
-                "traffic": captured_traffic(dom) if path == L.LCF_PATH_TC else None,
+                "traffic": captured_traffic(dom, args.evd) if path == L.LCF_PATH_TC else None,
+                # SMs the dominant stage holds per packet: the one-sided EVD one per window, the CTA
+                # pair two; the packets in flight share the rest of the 148
+                "sms_held": (WZ * WX * (1 if args.evd == "os" else 2)) if dom == "evd" and path == L.LCF_PATH_TC else None,
                 "traffic_unit": "bytes per launch (ncu capture)",
                 "peak_source": peak_src,
                 "stage_ms_per_launch": per_launch}
+    if roofline["sms_held"] and roofline["frac"]:   # the same rate against the peak of the SMs it holds
+        roofline["frac_of_held_sms"] = roofline["frac"] * 148 / roofline["sms_held"]
 
     # end to end through the public API with host buffers (pinned)
     # (pipelined host calls: each packet's input copy overlaps the previous packet's kernels;
