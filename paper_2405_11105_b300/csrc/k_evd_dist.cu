@@ -113,25 +113,41 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
   }
   __syncthreads();
   for (int it = 0; it < iters; ++it) {
-    for (int e = tid; e < n * m; e += ED_THREADS) {
-      const int a = e / m, j = e % m;
-      float2 acc = make_float2(0.f, 0.f);
-      const double2* rr = R + (size_t)a * n;
-      const float2* yy = Ys + (size_t)j * ldy;
-      const float2* rs = Rf + (size_t)a * n;
-      for (int b = 0; b < n; ++b) {
-        float2 r;
-        if (rf) {
-          r = rs[b];
-        } else {
-          const double2 rd = rr[b];
-          r = make_float2((float)rd.x * s_lo, (float)rd.y * s_lo);
+    if (rf) {   // Z = R Y from the staged fp32 copy, one thread per (row, column)
+      for (int e = tid; e < n * m; e += ED_THREADS) {
+        const int a = e / m, j = e % m;
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* yy = Ys + (size_t)j * ldy;
+        const float2* rs = Rf + (size_t)a * n;
+        for (int b = 0; b < n; ++b) {
+          const float2 r = rs[b], y = yy[b];
+          acc.x = fmaf(r.x, y.x, fmaf(-r.y, y.y, acc.x));
+          acc.y = fmaf(r.x, y.y, fmaf(r.y, y.x, acc.y));
         }
-        const float2 y = yy[b];
-        acc.x = fmaf(r.x, y.x, fmaf(-r.y, y.y, acc.x));
-        acc.y = fmaf(r.x, y.y, fmaf(r.y, y.x, acc.y));
+        Zs[(size_t)j * ldy + a] = acc;
       }
-      Zs[(size_t)j * ldy + a] = acc;
+    } else {    // from global memory, one thread per row: each double converted once for all columns
+      for (int a = tid; a < n; a += ED_THREADS) {
+        float2 acc[kEvdHead];
+#pragma unroll
+        for (int j = 0; j < kEvdHead; ++j) acc[j] = make_float2(0.f, 0.f);
+        const double2* rr = R + (size_t)a * n;
+        for (int b = 0; b < n; ++b) {
+          const double2 rd = rr[b];
+          const float2 r = make_float2((float)rd.x * s_lo, (float)rd.y * s_lo);
+#pragma unroll
+          for (int j = 0; j < kEvdHead; ++j) {
+            if (j < m) {
+              const float2 y = Ys[(size_t)j * ldy + b];
+              acc[j].x = fmaf(r.x, y.x, fmaf(-r.y, y.y, acc[j].x));
+              acc[j].y = fmaf(r.x, y.y, fmaf(r.y, y.x, acc[j].y));
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kEvdHead; ++j)
+          if (j < m) Zs[(size_t)j * ldy + a] = acc[j];
+      }
     }
     __syncthreads();
     for (int j = 0; j < m; ++j) {   // CGS2 of Z's columns into Y

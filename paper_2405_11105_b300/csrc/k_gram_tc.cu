@@ -391,8 +391,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
 }
 
 // ---------------------------------------------------------------------------
-// Long packets (Nt > 128 residual rows): the Nt x Nt residual block in row tiles of tb
-// rows (T tiles), one CTA per (window, tile pair (a, b)) over the whole window support.
+// Long packets (Nt > 128 residual rows): the na x na block (na = Nt + d augmented rows when the
+// exact kernel takes the coefficient block, so the tiles give U too; else the Nt residual rows)
+// in row tiles of tb rows (T tiles), one CTA per (window, tile pair (a, b)) over the whole
+// window support.
 // The CTA forms D'(a, b) = A_hi(a) (B_hi(b) + 2 B_lo(b))^T with the operands of the short
 // kernel (B(b) = [w ; -i w] of tile b's rows), A from tile a's rows (aliasing B_hi when
 // a == b); both orders of every off-diagonal pair are formed, so the assembly takes the
@@ -410,7 +412,7 @@ size_t gram_tcb_smem_bytes(int tb) {
 
 template <int GP>
 __global__ void __launch_bounds__(TG_THREADS, 1)
-gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int tb, int T, const Box* __restrict__ boxes,
+gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt /* rows tiled */, int tb, int T, const Box* __restrict__ boxes,
                 const float* __restrict__ gz, const float* __restrict__ gx, const unsigned* __restrict__ xmax_bits,
                 double* __restrict__ part, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
@@ -731,8 +733,8 @@ static void launch_gram_tc_gp(const lcf_plan* P, cudaStream_t st) {
   if (P->tc_T > 1) {
     dim3 gb(P->tc_T * P->tc_T, P->nd);
     gram_tcb_kernel<GP><<<gb, TG_THREADS, gram_tcb_smem_bytes(P->tc_tb), st>>>(
-        P->ws.xa, c.nz, c.nx, P->nt, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc,
-        P->ws.err);
+        P->ws.xa, c.nz, c.nx, na, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc,
+        P->ws.err);   // na rows: the augmented rows when the tiles give U too, else the residual rows
   } else {
     dim3 grid(P->tc_nsplit, P->nd);
     gram_tc_kernel<GP><<<grid, TW_THREADS, gram_tc_smem_bytes(na), st>>>(

@@ -196,11 +196,14 @@ extern "C" lcf_status lcf_plan_create(const lcf_config* cfg, int device, lcf_pla
     P->tc_nsplit = (int)(ts < 1 ? 1 : (ts > 64 ? 64 : ts));
   }
   // one tensor-core tile holds the augmented rows when they fit and the exact-product kernel
-  // takes the coefficient block; otherwise the residual rows alone, U and Q from CUDA cores
+  // takes the coefficient block; otherwise the residual rows alone, U and Q from CUDA cores.
+  // Long packets (Nt > 128) tile the augmented rows when the exact kernel takes Q (d <= 4), so
+  // the tile pairs give U too, and the residual rows alone otherwise.
   P->tc_na = (P->n1 <= kTcGramNaMax && P->ndefl <= kQExactMax) ? P->n1 : P->nt;
+  if (P->nt > kTcGramNaMax && P->ndefl <= kQExactMax) P->tc_na = P->n1;
   if (P->tc_na > kTcGramNaMax) {   // long packets: tile pairs of at most kTcTileMax rows, no pixel splits
-    P->tc_T = (P->nt + kTcTileMax - 1) / kTcTileMax;
-    P->tc_tb = ((P->nt + P->tc_T - 1) / P->tc_T + 7) / 8 * 8;
+    P->tc_T = (P->tc_na + kTcTileMax - 1) / kTcTileMax;
+    P->tc_tb = ((P->tc_na + P->tc_T - 1) / P->tc_T + 7) / 8 * 8;
     P->tc_nsplit = 1;
   } else {
     P->tc_T = 1;
