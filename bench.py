@@ -399,7 +399,7 @@ def main():
                     help="EVD kernel of the optimized path: two-sided CTA pair or one-sided on the Cholesky factor")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (a profiler run can reuse the tuning of a plain run)")
-    ap.add_argument("--inflight", type=int, default=3,
+    ap.add_argument("--inflight", type=int, default=4,
                     help="packets the optimized plan keeps in progress at once (lcf_filter_many)")
     ap.add_argument("--no-variants", action="store_true", help="skip the variant arms (untuned, graph, one-pass fp16)")
     args = ap.parse_args()
