@@ -100,10 +100,13 @@ enum { LCF_PATH_SIMT = 0, LCF_PATH_TC = 1 };
  * rotations on A and streams them through distributed shared memory to the
  * other, which accumulates V.  Same arithmetic and tolerances.
  * LCF_EVD_OS: one-sided Jacobi (Hestenes) on the pivoted FP32 Cholesky factor
- * of the same deflated matrix, one CTA per window with the factor's columns in
- * registers; the eigenvectors are the converged columns, so no V is
- * accumulated (Nt <= 128; longer packets take the distributed two-sided
- * kernel).  Same tolerances; the learned rule needs LCF_EVD_PAIR.
+ * of the same deflated matrix, the factor's columns in registers: one CTA per
+ * window up to Nt = 128, a four-CTA cluster per window (rows split across the
+ * CTAs) up to Nt = 224; the eigenvectors are the converged columns, so no V is
+ * accumulated.  Longer packets take the distributed two-sided kernel.  Same
+ * tolerances; one SM per window at Nt <= 128 (the CTA pair holds two), which
+ * leaves room for other packets in flight (cfg.inflight).  The learned rule
+ * needs LCF_EVD_PAIR.
  * All three: Eq. 2. */
 enum { LCF_EVD_CTA = 0, LCF_EVD_PAIR = 1, LCF_EVD_OS = 2 };
 

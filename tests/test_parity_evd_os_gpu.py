@@ -226,3 +226,36 @@ def test_os_long_matches_distributed_evd():
     print("eigenvalue rel diff", rel, "pd rel", np.linalg.norm(pa - pb) / np.linalg.norm(pa))
     assert rel <= 2e-5
     assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 2e-4
+
+
+@pytest.mark.parametrize("nt,nz,nx,grid", [(32, 48, 40, (3, 3)), (200, 40, 36, (2, 2))])
+def test_os_stream_graph_matches_packets(nt, nz, nx, grid):
+    """lcf_filter_stream (all packets one CUDA graph, the cluster kernel launched with its cluster
+    attribute inside the capture) gives every packet's lcf_filter image bit for bit."""
+    import torch
+    lib = L()
+    stride = 8
+    frames = torch.from_numpy(rand_iq(12, nt + 3 * stride, nz, nx)).cuda()
+    plan = lib.Plan.make(nz, nx, nt, grid[0], grid[1], evd_path=lib.LCF_EVD_OS, thresh_mode=lib.LCF_T_CURVATURE,
+                         beta=1.0)
+    outs = plan.filter_stream(frames, stride)
+    outs2 = plan.filter_stream(frames, stride, outs.clone())   # the captured graph again
+    torch.cuda.synchronize()
+    assert outs.shape[0] == 4 and torch.equal(outs, outs2)
+    for i in range(4):
+        one = plan.filter(frames[i * stride:i * stride + nt].contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(one, outs[i]), i
+
+
+def test_os_long_packets_in_flight():
+    """Lanes with the cluster EVD: images equal lcf_filter's bit for bit."""
+    import torch
+    lib = L()
+    iq = torch.from_numpy(np.stack([rand_iq(20 + i, 200, 40, 36) for i in range(5)])).cuda()
+    single = lib.Plan.make(40, 36, 200, 2, 2, evd_path=lib.LCF_EVD_OS)
+    ref = torch.stack([single.filter(iq[p]) for p in range(5)])
+    many = lib.Plan.make(40, 36, 200, 2, 2, evd_path=lib.LCF_EVD_OS, inflight=3)
+    out = many.filter_many(iq)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
