@@ -249,4 +249,42 @@ __device__ __forceinline__ void ep_rotation2(float app, float aqq, float2 b, flo
   }
 }
 
+// The rotation of ep_rotation2 for the one-sided kernels (the updated diagonal is not needed:
+// column norms are summed again) together with the "calm" test of the stopping rule: a pair is
+// calm when it does not rotate, or when its cosine |b| / sqrt(app aqq) is at most clim and its
+// sine |st| at most slim.  One rotation of the pair (p, q) with sine s moves the cosine of p or q
+// with a third column by at most about s times that column's cosine with the other one, and a
+// circle touches each pair 2 (n - 2) times, so after a whole calm circle every cosine is at most
+// about 2 n clim slim.  With clim = sqrt(n) tol and slim = 1 / (2 n^(3/2)) that is tol, the
+// rotation threshold itself, and the circle that would only confirm convergence is skipped (the
+// sweep-level test of one-sided Jacobi SVD codes, which stop once n max|cos| max|sin| is below
+// the tolerance).
+__device__ __forceinline__ void ep_rotation_os(float app, float aqq, float2 b, float tol, float clim2, float slim2,
+                                               float& c, float2& st, int& rot, bool& calm) {
+  const float b2 = b.x * b.x + b.y * b.y;
+  c = 1.f;
+  st = make_float2(0.f, 0.f);
+  rot = 0;
+  calm = true;
+  const float pq = fabsf(app * aqq);
+  if (b2 > 0.f && b2 > (tol * tol) * pq) {
+    const float d = aqq - app;
+    const float x = fmaf(d, d, 4.f * b2);
+    if (!(x >= 7.888609052e-31f)) {   // 2^-100
+      float dp, dq;
+      ep_rotation(app, aqq, b, tol, c, st, dp, dq, rot);
+      calm = b2 <= clim2 * pq && st.x * st.x + st.y * st.y <= slim2;
+      return;
+    }
+    const float ir = ep_rsqrt(x);
+    const float y = fmaf(0.5f * fabsf(d), ir, 0.5f);
+    const float ic = ep_rsqrt(y);
+    c = y * ic;
+    const float f = (d < 0.f ? -ir : ir) * ic;
+    st = make_float2(f * b.x, f * b.y);
+    rot = 1;
+    calm = b2 <= clim2 * pq && (f * f) * b2 <= slim2;   // |st|^2 = f^2 |b|^2
+  }
+}
+
 }  // namespace lcf

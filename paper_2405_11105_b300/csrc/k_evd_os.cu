@@ -5,9 +5,10 @@
 // B = Q^H (R / scale) Q in double-float rounded to fp32, with Q from an FP32
 // subspace iteration and its Householder QR, so the dominant (tissue) directions
 // are split off before any FP32 rotation.  This kernel then
-//   1. factors B = P L L^H P^T in FP32 with diagonal pivoting (Cholesky in panels of
-//      eight columns; a non-positive pivot ends it and leaves the rest of L zero);
-//   2. runs one-sided Jacobi (Hestenes' method) on the columns of F = P L:
+//   1. factors B = F F^H in FP32 by Cholesky with diagonal pivoting, F = P L with its rows
+//      left in the original order (right-looking, every warp; a non-positive pivot ends it and
+//      leaves the rest of F zero);
+//   2. runs one-sided Jacobi (Hestenes' method) on the columns of F:
 //      column pairs are rotated until every pair is orthogonal to a relative
 //      tolerance.  B = F F^H = (F J)(F J)^H for every unitary J, so at
 //      convergence each column is an eigenvector of B times the square root of
@@ -40,7 +41,7 @@ namespace lcf {
 constexpr int EO_THREADS = 512;
 constexpr float EO_TOL = 2.0e-6f;              // relative orthogonality test (cosine of two columns)
 constexpr int EO_SUBSPACE_ITERS = 3;
-constexpr int EO_PANEL = 8;                    // Cholesky panel width
+constexpr int EO_CB = 4;                       // Cholesky columns per trailing update
 
 struct EoArgs {
   int nt, nz, nx;
@@ -56,11 +57,12 @@ __host__ __device__ inline size_t eo_align(size_t x) { return (x + 15) & ~(size_
 
 struct EoLayout {
   int np, h, lda, m, nw, rp;
-  size_t a, x, perm, iperm, colj, lam, sperm, wts, s0, s1, s2, coef, keep, phs, end;
+  size_t a, x, colj, lam, sperm, wts, s0, s1, s2, coef, keep, phs, end;
 };
 
-// a: the matrix (B, then L, then the eigenvector columns U, then V), rows in pivot order;
-// x: the step-parity exchange buffers of the sweeps, later Vh, T, X = Vh^H U and Y = T X
+// a: the matrix (B, then the Cholesky factor, then the eigenvector columns U, then V), rows by index;
+// x: the Cholesky block's columns, the step-parity exchange buffers of the sweeps, later Vh, T,
+// X = Vh^H U and Y = T X
 __host__ __device__ inline EoLayout eo_layout(int n) {
   EoLayout L;
   L.np = n + (n & 1);
@@ -74,10 +76,11 @@ __host__ __device__ inline EoLayout eo_layout(int n) {
   {
     const size_t xch = (size_t)2 * 2 * L.nw * L.rp * 32 * 16;
     const size_t post = ((size_t)L.m * n + (size_t)L.m * L.m + (size_t)2 * L.m * L.np) * 8;
-    L.x = o; o = eo_align(o + (xch > post ? xch : post));
+    const size_t chol = (size_t)EO_CB * L.np * 8;   // the Cholesky block's columns
+    size_t need = xch > post ? xch : post;
+    need = need > chol ? need : chol;
+    L.x = o; o = eo_align(o + need);
   }
-  L.perm = o;  o = eo_align(o + (size_t)L.np * 4);
-  L.iperm = o; o = eo_align(o + (size_t)L.np * 4);
   L.colj = o;  o = eo_align(o + (size_t)L.np * 8);
   L.lam = o;   o = eo_align(o + (size_t)L.np * 8);   // squared norm by column position
   L.sperm = o; o = eo_align(o + (size_t)L.np * 4);   // sorted -> column position
@@ -99,6 +102,14 @@ size_t evd_os_smem_bytes(int nt) { return eo_layout(nt).end + (size_t)nt * 8; } 
     if (g.clk && tid == 0) g.clk[(size_t)k * (kEvdPhases + 1) + (b)] = clock64();      \
   } while (0)
 
+// Row r of column c of the Cholesky factor G (pivot pc = index eliminated at step c), read from
+// the in-place storage of the right-looking factorisation
+__device__ __forceinline__ float2 eo_factor(const float2* A, int lda, const int* pos, int pc, int c, int r) {
+  if (r == pc) return A[(size_t)pc * lda + pc];
+  if (pos[r] < c) return make_float2(0.f, 0.f);
+  return r > pc ? A[(size_t)r * lda + pc] : cconj(A[(size_t)pc * lda + r]);
+}
+
 // ---- one Jacobi step of a warp that owns four pair slots (eight columns) ----
 // Lane l holds rows l, l + 32, l + 64, l + 96 of every column as row pairs (XR = real parts of
 // rows (2i) * 32 + l and (2i + 1) * 32 + l, XI the imaginary parts), so the dot products and the
@@ -111,6 +122,7 @@ struct EoSweepCtx {
   float4* xb;      // [parity][warp][row pair][lane]: the bottom leaving slot 0
   int nw, h, warp, lane, slast;   // slast: the slot of pair h - 1 in the last warp
   bool wfirst, wlast;
+  float clim2, slim2;             // squared cosine and sine bounds of a calm step (ep_rotation_os)
 };
 
 // 16 partial sums v[4 s + c] (slot s, component c) summed over the warp; lane l receives the total
@@ -171,12 +183,14 @@ __device__ __forceinline__ int eo_step(float2 (&TR)[4][RP], float2 (&TI)[4][RP],
   const int base = lane & 24;
   const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 2);
   const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 4), __shfl_sync(~0u, tot, base + 6));
-  float c, dp, dq;
+  float c;
   float2 st;
   int rot;
-  ep_rotation2(a, b, gm, EO_TOL, c, st, dp, dq, rot);   // c = 1, st = 0 without a rotation
-  if (4 * x.warp + (lane >> 3) >= x.h) rot = 0;          // slots past h - 1 hold no pair
+  bool calm;
+  ep_rotation_os(a, b, gm, EO_TOL, x.clim2, x.slim2, c, st, rot, calm);   // c = 1, st = 0 without a rotation
+  if (4 * x.warp + (lane >> 3) >= x.h) { rot = 0; calm = true; }         // slots past h - 1 hold no pair
   const unsigned rmask = __ballot_sync(~0u, rot);
+  const unsigned wmask = __ballot_sync(~0u, !calm);
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     if (!((rmask >> (8 * s)) & 1u)) continue;   // warp-uniform
@@ -205,7 +219,7 @@ __device__ __forceinline__ int eo_step(float2 (&TR)[4][RP], float2 (&TI)[4][RP],
       db[i * 32] = make_float4(BR[b0][i].x, BR[b0][i].y, BI[b0][i].x, BI[b0][i].y);
     }
   }
-  const int any = __syncthreads_or(rmask != 0u);
+  const int any = __syncthreads_or(wmask != 0u);
   if (x.h == 1) {   // one pair: nothing moves, but the registers are renamed all the same
     const int t0 = (0 - U) & 3, bn = (U + 1) & 3;
 #pragma unroll
@@ -281,8 +295,6 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   const EoLayout L = eo_layout(n);
   const int np = L.np, h = L.h, lda = L.lda, m = L.m;
   float2* A = reinterpret_cast<float2*>(smem + L.a);
-  int* perm = reinterpret_cast<int*>(smem + L.perm);
-  int* iperm = reinterpret_cast<int*>(smem + L.iperm);
   float2* colj = reinterpret_cast<float2*>(smem + L.colj);
   double* lam = reinterpret_cast<double*>(smem + L.lam);
   int* sperm = reinterpret_cast<int*>(smem + L.sperm);
@@ -311,90 +323,105 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   EO_STAMP(3);
 
-  // ---------------- pivoted Cholesky of B in FP32, lower triangle in place, in panels of
-  // EO_PANEL columns: warp 0 factors a panel left-looking (pivot on the running diagonal dg,
-  // symmetric interchange, column = (entry - the panel's earlier columns) / sqrt(pivot)), then
-  // every warp applies the panel to the trailing lower triangle
-  float* dg = reinterpret_cast<float*>(colj);   // running diagonal of the Schur complement
+  // ---------------- pivoted Cholesky of B in FP32 by every warp, without interchanges: step j
+  // takes as pivot p_j the remaining index with the largest diagonal of the Schur complement S and
+  // writes column j of the factor, g_r = S(r, p_j) / sqrt(S(p_j, p_j)) for the remaining r, over
+  // S's column p_j (lower triangle storage: S(r, c) at A[max][min], conjugated above the diagonal)
+  // and sqrt(S(p_j, p_j)) at A[p_j][p_j].  The factor G (column j = step j, rows in the original
+  // order) has G G^H = B: row r of column j is zero once r was eliminated before step j.  Columns
+  // go in blocks of EO_CB: inside a block a column subtracts the block's earlier columns from the
+  // stored S(r, p_j) (one row per thread) and the running diagonal is updated at once, so the next
+  // pivot is known after one barrier; the remaining lower triangle then takes the block's rank-EO_CB
+  // update in one pass over all its pairs.  A non-positive pivot ends it (numerical rank rk);
+  // columns rk .. n - 1 stay zero.  The remaining indices (in increasing order) and their running
+  // diagonal are kept by list position, double-buffered by step parity, so every warp searches the
+  // pivot itself (n <= 128: at most four list positions per lane).
+  float* dgb = reinterpret_cast<float*>(colj);       // running diagonal by list position, [parity][np]
+  float2* gv = reinterpret_cast<float2*>(smem + L.x);   // the block's columns by index, [EO_CB][np]
+  int* remb = reinterpret_cast<int*>(lam);           // remaining indices, [parity][np]
+  int* pos = reinterpret_cast<int*>(s1);             // step that eliminated each index (n: none)
+  int* ord = reinterpret_cast<int*>(s2);             // index eliminated at each step
+  const int nwarp = nthr / 32;
   {
     const float2* B = Bg + (size_t)k * n * n;
-    for (int i = warp; i < n; i += nthr / 32)
+    for (int i = warp; i < n; i += nwarp)
       for (int c = lane; c <= i; c += 32) A[(size_t)i * lda + c] = B[(size_t)i * n + c];
-    for (int r = tid; r < np; r += nthr) perm[r] = r;
-    for (int i = tid; i < n; i += nthr) dg[i] = B[(size_t)i * n + i].x;
+    for (int r = tid; r < np; r += nthr) { remb[r] = r; pos[r] = n; }
+    for (int i = tid; i < n; i += nthr) dgb[i] = B[(size_t)i * n + i].x;
   }
-  __shared__ int sh_rank, sh_stop;
-  if (tid == 0) { sh_rank = n; sh_stop = 0; }
   __syncthreads();
-  float first = 0.f;   // warp 0: the first pivot
-  for (int j0 = 0; j0 < n; j0 += EO_PANEL) {
-    const int j1 = j0 + EO_PANEL < n ? j0 + EO_PANEL : n;
-    if (warp == 0) {
-      for (int j = j0; j < j1; ++j) {
-        float best = -INFINITY;   // largest remaining diagonal entry, ties to the lower index
-        int bi = 0x7fffffff;
-        for (int i = j + lane; i < n; i += 32) {
-          const float d = dg[i];
-          if (d > best) { best = d; bi = i; }
-        }
+  int rk = n;
+  {
+    float first = 0.f;
+    bool stop = false;
+    for (int j0 = 0; j0 < n && !stop; j0 += EO_CB) {
+      const int j1 = j0 + EO_CB < n ? j0 + EO_CB : n;
+      int j = j0;
+      for (; j < j1; ++j) {
+        const int cnt = n - j, par = j & 1, t = j - j0;
+        const int* rin = remb + par * np;
+        int* rout = remb + (par ^ 1) * np;
+        const float* din = dgb + par * np;
+        float* dout = dgb + (par ^ 1) * np;
+        float dd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dd[q] = lane + 32 * q < cnt ? din[lane + 32 * q] : -INFINITY;
+        float best = -INFINITY;   // the largest remaining diagonal entry, ties to the lower index
+        int ba = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (dd[q] > best) { best = dd[q]; ba = lane + 32 * q; }
+#pragma unroll
         for (int o = 16; o; o >>= 1) {
           const float ob = __shfl_xor_sync(~0u, best, o);
-          const int oi = __shfl_xor_sync(~0u, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          const int oa = __shfl_xor_sync(~0u, ba, o);
+          if (ob > best || (ob == best && oa < ba)) { best = ob; ba = oa; }
         }
         if (j == 0) first = best;
-        if (!(best > first * 1e-30f) || !isfinite(best)) {   // numerical rank j: the rest of L stays zero
-          if (lane == 0) { sh_rank = j; sh_stop = 1; }
-          break;
-        }
-        const int p = bi;
-        if (p != j) {   // symmetric interchange of j and p; pending panel updates move with the rows
-          for (int c = lane; c < n; c += 32) {
-            float2 t;
-            if (c < j) {
-              t = A[(size_t)j * lda + c]; A[(size_t)j * lda + c] = A[(size_t)p * lda + c]; A[(size_t)p * lda + c] = t;
-            } else if (c == j) {
-              t = A[(size_t)j * lda + j]; A[(size_t)j * lda + j] = A[(size_t)p * lda + p]; A[(size_t)p * lda + p] = t;
-              A[(size_t)p * lda + j] = cconj(A[(size_t)p * lda + j]);
-            } else if (c < p) {
-              t = A[(size_t)c * lda + j];
-              A[(size_t)c * lda + j] = cconj(A[(size_t)p * lda + c]);
-              A[(size_t)p * lda + c] = cconj(t);
-            } else if (c > p) {
-              t = A[(size_t)c * lda + j]; A[(size_t)c * lda + j] = A[(size_t)c * lda + p]; A[(size_t)c * lda + p] = t;
-            }
-          }
-          if (lane == 0) {
-            const float td = dg[j]; dg[j] = dg[p]; dg[p] = td;
-            const int tp = perm[j]; perm[j] = perm[p]; perm[p] = tp;
-          }
-          __syncwarp();
-        }
+        if (!(best > first * 1e-30f) || !isfinite(best)) { rk = j; stop = true; break; }   // in every warp
+        const int pa = ba, p = rin[pa];
         const float inv = ep_rsqrt(best);
-        for (int i = j + 1 + lane; i < n; i += 32) {
-          float2 v = A[(size_t)i * lda + j];
-          for (int l = j0; l < j; ++l) v = csub(v, cmul(A[(size_t)i * lda + l], cconj(A[(size_t)j * lda + l])));
-          v = cscale(v, inv);
-          A[(size_t)i * lda + j] = v;
-          dg[i] -= cabs2(v);
+        for (int a = tid; a < cnt; a += nthr) {
+          const int r = rin[a];
+          if (a == pa) {
+            A[(size_t)p * lda + p] = make_float2(best * inv, 0.f);
+            ord[j] = p;
+            pos[p] = j;
+          } else {
+            float2* e = r > p ? &A[(size_t)r * lda + p] : &A[(size_t)p * lda + r];
+            float2 v = r > p ? *e : cconj(*e);
+            for (int u = 0; u < t; ++u) v = csub(v, cmul(gv[u * np + r], cconj(gv[u * np + p])));
+            const float2 g = cscale(v, inv);
+            *e = r > p ? g : cconj(g);
+            gv[t * np + r] = g;
+            const int ao = a - (a > pa);
+            dout[ao] = din[a] - cabs2(g);
+            rout[ao] = r;
+          }
         }
-        if (lane == 0) A[(size_t)j * lda + j] = make_float2(best * inv, 0.f);
-        __syncwarp();
+        __syncthreads();
       }
-    }
-    __syncthreads();
-    if (sh_stop) break;
-    for (int i = j1 + warp; i < n; i += nthr / 32) {   // trailing update: rows by warp, columns by lane
-      for (int l = j1 + lane; l <= i; l += 32) {
-        float2 acc = A[(size_t)i * lda + l];
-        for (int c = j0; c < j1; ++c) acc = csub(acc, cmul(A[(size_t)i * lda + c], cconj(A[(size_t)l * lda + c])));
-        A[(size_t)i * lda + l] = acc;
+      if (stop) break;
+      // the block's update of the remaining lower triangle: pair e = a (a - 1) / 2 + b of list
+      // positions b < a; S(r, c) -= sum_u g_u[r] conj(g_u[c]) for the pair's indices r, c
+      const int cnt = n - j, nb = j - j0;
+      const int* rl = remb + (j & 1) * np;
+      const int npair = cnt * (cnt - 1) / 2;
+      for (int e = tid; e < npair; e += nthr) {
+        int a = (int)(0.5f * (1.f + sqrtf(8.f * (float)e + 1.f)));
+        if (a * (a - 1) / 2 > e) --a;
+        else if ((a + 1) * a / 2 <= e) ++a;
+        const int b = e - a * (a - 1) / 2;
+        const int r = rl[a], c = rl[b];
+        const int hi = r > c ? r : c, lo = r > c ? c : r;
+        float2 acc = A[(size_t)hi * lda + lo];
+        for (int u = 0; u < nb; ++u) acc = csub(acc, cmul(gv[u * np + hi], cconj(gv[u * np + lo])));
+        A[(size_t)hi * lda + lo] = acc;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   __syncthreads();
-  const int rk = sh_rank;
   EO_STAMP(4);
 
   // ---------------- one-sided Jacobi: warp w owns pair slots 4w .. 4w + 3; slot p holds columns
@@ -403,6 +430,8 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   xc.xt = reinterpret_cast<float4*>(smem + L.x);
   xc.xb = xc.xt + (size_t)2 * L.nw * RP * 32;
   xc.nw = L.nw; xc.h = h; xc.warp = warp; xc.lane = lane;
+  xc.clim2 = (float)np * EO_TOL * EO_TOL;
+  xc.slim2 = 0.25f / ((float)np * np * np);
   xc.wfirst = warp == 0;
   xc.wlast = warp == (h - 1) / 4;
   xc.slast = (h - 1) - 4 * ((h - 1) / 4);
@@ -416,8 +445,8 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int r = (2 * i + e) * 32 + lane;
-        const float2 t = (p < h && r < n && ct <= r && ct < rk) ? A[(size_t)r * lda + ct] : make_float2(0.f, 0.f);
-        const float2 b = (p < h && r < n && cb <= r && cb < rk) ? A[(size_t)r * lda + cb] : make_float2(0.f, 0.f);
+        const float2 t = (p < h && r < n && ct < rk) ? eo_factor(A, lda, pos, ord[ct], ct, r) : make_float2(0.f, 0.f);
+        const float2 b = (p < h && r < n && cb < rk) ? eo_factor(A, lda, pos, ord[cb], cb, r) : make_float2(0.f, 0.f);
         v[e][0] = t.x; v[e][1] = t.y; v[e][2] = b.x; v[e][3] = b.y;
       }
       TR[s][i] = make_float2(v[0][0], v[1][0]);
@@ -428,7 +457,8 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   __syncthreads();
   // Steps run in blocks of four (the register renaming's period); a window has converged once a
-  // whole circle (np - 1 consecutive steps, which meet every pair once) rotated nothing.
+  // whole circle (np - 1 consecutive steps, which meet every pair once) was calm: no rotation
+  // above the cosine and sine bounds of ep_rotation_os.
   int converged = 0, sweeps = 0;
   {
     const int per = np - 1;
@@ -508,7 +538,6 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
     }
     sperm[r] = i;
   }
-  for (int r = tid; r < n; r += nthr) iperm[perm[r]] = r;
   __syncthreads();
   // vanished columns: Gram-Schmidt completion (two passes) of unit vectors against the columns before
   // them in sorted order (warp 0; numerical rank below Nt only)
@@ -608,7 +637,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
     }
     if (lane == 0) { keep[0] = base; ncol_out[k] = base; }
   }
-  // ---------------- V = Q U = U - Vh (T (Vh^H U)), rows kept in pivot order (row r is index perm[r])
+  // ---------------- V = Q U = U - Vh (T (Vh^H U))
   float2* Vh = reinterpret_cast<float2*>(smem + L.x);   // [j][a], a by original index
   float2* Tm = Vh + (size_t)m * n;                      // [i][j]
   float2* X = Tm + (size_t)m * m;                       // [j][pos]
@@ -619,7 +648,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   for (int e = tid; e < m * np; e += nthr) {
     const int j = e / np, pos = e % np;
     float2 acc = make_float2(0.f, 0.f);
-    for (int r = 0; r < n; ++r) acc = cadd(acc, cmulc(Vh[(size_t)j * n + perm[r]], A[(size_t)r * lda + pos]));
+    for (int r = 0; r < n; ++r) acc = cadd(acc, cmulc(Vh[(size_t)j * n + r], A[(size_t)r * lda + pos]));
     X[e] = acc;
   }
   __syncthreads();
@@ -631,9 +660,9 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   __syncthreads();
   for (int e = tid; e < n * np; e += nthr) {
-    const int r = e / np, pos = e % np, a = perm[r];
+    const int r = e / np, pos = e % np;
     float2 v = A[(size_t)r * lda + pos];
-    for (int j = 0; j < m; ++j) v = csub(v, cmul(Vh[(size_t)j * n + a], Y[(size_t)j * np + pos]));
+    for (int j = 0; j < m; ++j) v = csub(v, cmul(Vh[(size_t)j * n + r], Y[(size_t)j * np + pos]));
     A[(size_t)r * lda + pos] = v;
   }
   __syncthreads();
@@ -644,7 +673,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
     float best = -1.f;
     int bi = 0x7fffffff;
     for (int a = lane; a < n; a += 32) {
-      const float mg = cabs2(A[(size_t)iperm[a] * lda + pos]);
+      const float mg = cabs2(A[(size_t)a * lda + pos]);
       if (mg > best) { best = mg; bi = a; }
     }
     for (int o = 16; o; o >>= 1) {
@@ -653,7 +682,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     if (lane == 0) {
-      const float2 v = A[(size_t)iperm[bi < n ? bi : 0] * lda + pos];   // bi >= n only if every entry is NaN
+      const float2 v = A[(size_t)(bi < n ? bi : 0) * lda + pos];   // bi >= n only if every entry is NaN
       const float mg = sqrtf(cabs2(v));
       phs[jj] = mg > 0.f ? make_float2(v.x / mg, -v.y / mg) : make_float2(1.f, 0.f);
     }
@@ -666,7 +695,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   for (int e = tid; e < n * n; e += nthr) {
     const int a = e / n, jj = e % n;
-    V_out[(size_t)k * n * n + e] = cmul(A[(size_t)iperm[a] * lda + sperm[jj]], phs[jj]);
+    V_out[(size_t)k * n * n + e] = cmul(A[(size_t)a * lda + sperm[jj]], phs[jj]);
   }
   const int nc = keep[0];
   for (int e = tid; e < n * g.ncp; e += nthr) {
@@ -674,7 +703,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
     float2 v = make_float2(0.f, 0.f);
     if (c < nc) {
       const int jj = keep[1 + c];
-      v = cscale(cmul(A[(size_t)iperm[a] * lda + sperm[jj]], phs[jj]), coef[jj]);
+      v = cscale(cmul(A[(size_t)a * lda + sperm[jj]], phs[jj]), coef[jj]);
     }
     W_out[(size_t)k * n * g.ncp + e] = v;
   }

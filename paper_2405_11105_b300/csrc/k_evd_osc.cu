@@ -214,6 +214,7 @@ struct EqCtx {
   unsigned bytes;        // partial-sum bytes a step brings in: (EQ_C - 1) * nw * 32 * 4
   int nw, h, warp, lane, tid, rank;
   bool wfirst, wlast;
+  float clim2, slim2;    // squared cosine and sine bounds of a calm step (ep_rotation_os)
 };
 
 __device__ __forceinline__ void eq_st_async_f32(uint32_t addr, float v, uint32_t bar_cluster_addr) {
@@ -295,11 +296,13 @@ __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 
   const int base = lane & 28;
   const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 1);
   const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 2), __shfl_sync(~0u, tot, base + 3));
-  float c, dp, dq;
+  float c;
   float2 st;
   int rot;
-  ep_rotation2(a, b, gm, EQ_TOL, c, st, dp, dq, rot);
+  bool calm;
+  ep_rotation_os(a, b, gm, EQ_TOL, x.clim2, x.slim2, c, st, rot, calm);
   const unsigned rmask = __ballot_sync(~0u, rot);
+  const unsigned wmask = __ballot_sync(~0u, !calm);
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     if (!((rmask >> (4 * s)) & 1u)) continue;   // warp-uniform
@@ -319,7 +322,7 @@ __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 
     x.xt[(par * x.nw + x.warp) * 32 + lane] = make_float4(TR[t7].x, TR[t7].y, TI[t7].x, TI[t7].y);
     x.xb[(par * x.nw + x.warp) * 32 + lane] = make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y);
   }
-  const int any = __syncthreads_or(rmask != 0u);
+  const int any = __syncthreads_or(wmask != 0u);
   // slot h - 1 (slot 7 of the last warp) takes its own top as bottom, into the register slot 0's
   // bottom left; slot 0 keeps its top, slot 1 takes slot 0's bottom (through a temporary when one
   // warp holds both ends)
@@ -411,6 +414,8 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
   xc.bar = bar;
   xc.bytes = (unsigned)((EQ_C - 1) * L.nw * 32 * 4);
   xc.nw = L.nw; xc.h = h; xc.warp = warp; xc.lane = lane; xc.tid = tid; xc.rank = rank;
+  xc.clim2 = (float)np * EQ_TOL * EQ_TOL;
+  xc.slim2 = 0.25f / ((float)np * np * np);
   xc.wfirst = warp == 0;
   xc.wlast = warp == L.nw - 1;
 
@@ -432,8 +437,9 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
       BR[s] = make_float2(ba.x, bb.x); BI[s] = make_float2(ba.y, bb.y);
     }
   }
-  // ---- sweeps, in blocks of eight steps; converged once a whole circle (np - 1 steps) rotated
-  // nothing.  Every CTA forms the same rotations, so every CTA reaches the same decision.
+  // ---- sweeps, in blocks of eight steps; converged once a whole circle (np - 1 steps) was calm
+  // (no rotation above the bounds of ep_rotation_os).  Every CTA forms the same rotations, so every CTA
+  // reaches the same decision.
   __shared__ int sh_fail;
   if (tid == 0) sh_fail = 0;
   __syncthreads();
