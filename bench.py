@@ -34,14 +34,14 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    # the one-sided EVD stage: evd_prep_kernel 10.35 MB + evd_os_kernel 3.91 MB
-    ("evd", "os"): {"bytes": 14.26e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+    # the one-sided EVD stage: evd_prep_kernel 10.35 MB + evd_os_kernel 3.90 MB
+    ("evd", "os"): {"bytes": 14.25e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "61c763771922996b71be9c0c6ca02345299696e58b9964b73995d66b42f02d17",
+                                "07889532daac361367d3b1d070383b42c7ed3284cf5051a30a5f81250a560f63",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "012f98a6ccfab4ab00945437406f1d375bc5f7e32e342f35d7a751466c9ea849",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":
-                                "5f49c4e22ff1c65643b5fa3ad4b49488b54f5289a099077851b31487f275d22d",
+                                "e94da384b6101ccb3ec412d8d3462094bdb5b419f12848449819fe823d146e62",
                                 "paper_2405_11105_b300/csrc/lcf_internal.cuh":
                                 "1e0aa59856ef34cb4cfdb48503a50b03a87dd782a8fce27ded9e732ed9cdd007"}},
     ("evd", "pair"): {"bytes": 10.55e6, "profile": "profiles/evd_pair_kernel_256x128x100_8x8.md",
