@@ -89,6 +89,9 @@ def test_os_small_all_rules(mode, beta, extra):
     ((17, 30, 22), (2, 2), "LCF_T_SLOPE"),       # slot h-1 = 8: the first slot of the third warp
     ((128, 40, 36), (2, 2), "LCF_T_CURVATURE"),   # largest Nt: 64 slots, 16 rows per lane
     ((127, 33, 29), (2, 3), "LCF_T_MEDIAN"),
+    ((64, 28, 26), (2, 2), "LCF_T_CURVATURE"),   # 64 rows: the last one-row-pair layout
+    ((65, 28, 26), (2, 2), "LCF_T_SLOPE"),       # 65: two row pairs, a zero padding column
+    ((3, 10, 9), (1, 2), "LCF_T_FIXED"),         # two slots, one of them half padding
 ])
 def test_os_edge_shapes(shape, grid, mode):
     lib = L()
