@@ -68,6 +68,27 @@ def captured_traffic(stage, evd="os"):
     return rec["bytes"]
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The slowest rank's time, on every rank (replicas: the job takes as long as its slowest GPU).
+    `dist` is torch.distributed once a process group is up, else None (one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: every rank processed units_per_rank units in (at most) `seconds`."""
+    return world * units_per_rank / seconds
+
+
+def ring_seed(rank):
+    """Seed of a rank's packet ring: each replica filters its own packets."""
+    return 1000 * rank
+
+
 def env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -424,7 +445,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    ring = make_ring(seed0=1000 * rank)
+    ring = make_ring(seed0=ring_seed(rank))
     d_ring = torch.from_numpy(ring).to(f"cuda:{local}")
     out = torch.empty((NZ, NX), dtype=torch.float32, device=f"cuda:{local}")
     st = torch.cuda.current_stream()
@@ -480,12 +501,7 @@ def main():
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dist, f"cuda:{local}")
 
     path = L.LCF_PATH_TC if args.path == "tc" else L.LCF_PATH_SIMT
     plan = plan_for(path)
@@ -493,7 +509,7 @@ def main():
     if path == L.LCF_PATH_TC and not args.no_variants:
         # the launch shapes as plan_create chose them, then autotuned on the first packet
         ms_untuned = timed(plan, args.steps, args.warmup)
-        variants["untuned"] = {"value": world * args.steps / (ms_untuned / 1e3), "tuning": plan.tuning().as_dict()}
+        variants["untuned"] = {"value": job_rate(world, args.steps, ms_untuned / 1e3), "tuning": plan.tuning().as_dict()}
     if path == L.LCF_PATH_TC:
         plan.autotune(d_ring[0], cache_path=args.tune_cache)
     run_packets(plan, args.warmup)
@@ -503,12 +519,12 @@ def main():
     # kernels of this library launched per timed step (the warm-up inside timed() is excluded)
     launches_per_step = (plan.launch_count() - n_launch0) // (args.steps + args.warmup)
     clocks = clk.summary()
-    value = world * args.steps / (ms / 1e3)
+    value = job_rate(world, args.steps, ms / 1e3)
 
     # plain FP32 path (the metric's denominator) on the same ring
     plain = plan if path == L.LCF_PATH_SIMT else plan_for(L.LCF_PATH_SIMT)
     ms_plain = ms if plain is plan else timed(plain, args.steps, args.warmup)
-    plain_value = world * args.steps / (ms_plain / 1e3)
+    plain_value = job_rate(world, args.steps, ms_plain / 1e3)
 
     if path == L.LCF_PATH_TC and not args.no_variants:
         # the same workload as one CUDA graph launch per packet (stream order, no early basis
@@ -517,7 +533,7 @@ def main():
             vp = plan_for(path, **kw)
             vp.autotune(d_ring[0], cache_path=args.tune_cache)
             ms_v = timed(vp, args.steps, args.warmup)
-            variants[name] = {"value": world * args.steps / (ms_v / 1e3), "tuning": vp.tuning().as_dict()}
+            variants[name] = {"value": job_rate(world, args.steps, ms_v / 1e3), "tuning": vp.tuning().as_dict()}
             vp.close()
 
     # per-stage device times (CUDA events between the stages on the launch stream)
@@ -565,12 +581,8 @@ def main():
         plan.filter_host_async(host_ring[i % RING], host_out[i % RING])
     plan.sync()
     t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * args.steps / e2e_s, "unit": "frames/s",
+    e2e_s = max_over_ranks(t1 - t0, dist, f"cuda:{local}")
+    e2e = {"value": job_rate(world, args.steps, e2e_s), "unit": "frames/s",
            "h2d_bytes_per_step": int(NT * NZ * NX * 8), "d2h_bytes_per_step": int(NZ * NX * 4)}
 
     st_code, flags = plan.status()
