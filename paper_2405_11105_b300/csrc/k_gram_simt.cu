@@ -230,8 +230,8 @@ __device__ __forceinline__ void gram_aug_body(const float2* __restrict__ xa, int
                                               const Box* __restrict__ boxes, const float* __restrict__ gz,
                                               const float* __restrict__ gx, int nsplit, int qrows,
                                               double2* __restrict__ aug, float2* Xs) {
-  __shared__ float g2s[ACH];
-  __shared__ int pix[ACH];         // linear pixel index of the step's pixels (-1: past the range)
+  __shared__ float g2s[2][ACH];    // the steps' window weights squared, by step parity
+  __shared__ int pix[2][ACH];      // linear pixel index of the steps' pixels (-1: past the range)
   const int k = blockIdx.y, s = blockIdx.x;
   const int na = nt + nd_defl, nout = (nt + qrows) * nd_defl;
   const Box b = boxes[k];
@@ -249,8 +249,10 @@ __device__ __forceinline__ void gram_aug_body(const float2* __restrict__ xa, int
 #pragma unroll
   for (int u = 0; u < OPT; ++u) { acc[u] = make_float2(0.f, 0.f); hr[u] = {0.f, 0.f}; hi[u] = {0.f, 0.f}; }
 
-  for (long l = l0; l < l1; l += ACH) {
-    if (threadIdx.x < ACH) {   // the step's pixels and weights, once per pixel
+  // Steps of ACH pixels, double-buffered: the copies of step t + 1 (cp.async, zero-filled past the
+  // range) are in flight while step t is summed.
+  auto pixels = [&](long l, int buf) {   // the step's pixels and weights, once per pixel
+    if (threadIdx.x < ACH) {
       const int ll = (int)l + threadIdx.x;   // box pixel counts are below 2^31 (plan validation)
       int p = -1;
       float g2 = 0.f;
@@ -261,15 +263,39 @@ __device__ __forceinline__ void gram_aug_body(const float2* __restrict__ xa, int
         const float g = gzk[z] * gxk[x];
         g2 = g * g;
       }
-      pix[threadIdx.x] = p;
-      g2s[threadIdx.x] = g2;
+      pix[buf][threadIdx.x] = p;
+      g2s[buf][threadIdx.x] = g2;
     }
-    __syncthreads();
+  };
+  auto stage = [&](int buf) {
+    float2* dst = Xs + (size_t)buf * ACH * na;
     for (int e = threadIdx.x; e < ACH * na; e += blockDim.x) {
-      const int pp = e % ACH, i = e / ACH, p = pix[pp];
-      Xs[pp * na + i] = p >= 0 ? xa[(size_t)i * npix + p] : make_float2(0.f, 0.f);
+      const int pp = e % ACH, i = e / ACH, p = pix[buf][pp];
+      const float2* src = p >= 0 ? xa + (size_t)i * npix + p : xa;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst + pp * na + i)),
+                   "l"(src), "r"(p >= 0 ? 8 : 0)
+                   : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (l0 < l1) {
+    pixels(l0, 0);
     __syncthreads();
+    stage(0);
+  }
+  int buf = 0;
+  for (long l = l0; l < l1; l += ACH, buf ^= 1) {
+    if (l + ACH < l1) pixels(l + ACH, buf ^ 1);
+    __syncthreads();   // the next step's pixels are known; every thread is past step t - 1 (its buffer)
+    if (l + ACH < l1) {
+      stage(buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();   // step t's rows are in
+    const float2* Xb = Xs + (size_t)buf * ACH * na;
+    const float* g2b = g2s[buf];
 #pragma unroll
     for (int u = 0; u < OPT; ++u) {
       int o = threadIdx.x + u * blockDim.x;
@@ -280,8 +306,8 @@ __device__ __forceinline__ void gram_aug_body(const float2* __restrict__ xa, int
         // (g^2 * conj(x_i) * x_b in double-float) so that its rounding, which
         // reaches every eigenvalue through Phi, stays at the double-float level
         for (int pp = 0; pp < ACH; ++pp) {
-          float g2 = g2s[pp];
-          float2 xi = Xs[pp * na + i], xb = Xs[pp * na + nt + a];
+          float g2 = g2b[pp];
+          float2 xi = Xb[pp * na + i], xb = Xb[pp * na + nt + a];
           df wr = two_prod_df(g2, xi.x), wi = two_prod_df(-g2, xi.y);      // g^2 conj(x_i)
           df rr = df_mul_f(wr, xb.x), ii = df_mul_f(wi, xb.y);
           df ri = df_mul_f(wr, xb.y), ir = df_mul_f(wi, xb.x);
@@ -293,8 +319,8 @@ __device__ __forceinline__ void gram_aug_body(const float2* __restrict__ xa, int
       for (int p0 = 0; p0 < ACH; p0 += APR) {
 #pragma unroll
         for (int pp = p0; pp < p0 + APR; ++pp) {
-          float g2 = g2s[pp];
-          float2 xi = Xs[pp * na + i], xb = Xs[pp * na + nt + a];
+          float g2 = g2b[pp];
+          float2 xi = Xb[pp * na + i], xb = Xb[pp * na + nt + a];
           float ar = g2 * xi.x, ai = -g2 * xi.y;          // g^2 conj(x_i)
           acc[u].x = fmaf(ar, xb.x, fmaf(-ai, xb.y, acc[u].x));
           acc[u].y = fmaf(ar, xb.y, fmaf(ai, xb.x, acc[u].y));
@@ -319,7 +345,7 @@ __global__ void __launch_bounds__(256, DM > 4 ? 1 : 2)
 gram_aug_kernel_t(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, const Box* __restrict__ boxes,
                   const float* __restrict__ gz, const float* __restrict__ gx, int nsplit, int qrows,
                   double2* __restrict__ aug) {
-  extern __shared__ float2 Xs[];   // [ACH][nt + d]: x_p, pixel-major
+  extern __shared__ float2 Xs[];   // [2][ACH][nt + d]: x_p, pixel-major, by step parity
   gram_aug_body<DM>(xa, nz, nx, nt, nd_defl, boxes, gz, gx, nsplit, qrows, aug, Xs);
 }
 
@@ -332,7 +358,7 @@ gram_aug_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_de
   gram_aug_body<4>(xa, nz, nx, nt, nd_defl, boxes, gz, gx, nsplit, qrows, aug, Xs);
 }
 
-size_t gram_aug_smem_bytes(int nt, int nd_defl) { return (size_t)ACH * (nt + nd_defl) * sizeof(float2); }
+size_t gram_aug_smem_bytes(int nt, int nd_defl) { return (size_t)2 * ACH * (nt + nd_defl) * sizeof(float2); }   // two steps
 
 // the augmented-column kernel's staging passes 48 KB beyond Nt = 188
 size_t gram_assemble_smem_bytes(int nt, int nd_defl);
