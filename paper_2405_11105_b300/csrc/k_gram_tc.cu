@@ -726,11 +726,278 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   }
 }
 
+// ---------------------------------------------------------------------------
+// Long packets, pipelined: the one-tile kernel's warp roles over a tile pair (a, b).  One CTA per
+// (window, tile pair) over the whole window support; the loader warp brings tile b's rows of each
+// slab (and tile a's, off the diagonal) with tensor-map loads of kTcSlabBox x tb; the sixteen
+// producer warps take their rows of the slab into registers, hand the slot back, then split tile
+// b's rows into B_hi / B_lo ([w ; -i w], as the one-tile kernel) and tile a's into A (hi words
+// only; on the diagonal A aliases B_hi); one warp issues D' = A (B_hi + 2 B_lo)^T in chains of
+// TG_CPA slabs, promoted by the producers into FP32 sums in tensor memory.  The block partial goes
+// out as doubles in the layout of gram_tcb_kernel (both orders of every off-diagonal pair, whose
+// Hermitian part the assembly takes).
+__host__ __device__ inline size_t tcp_slot_bytes(int tb, bool same) {
+  return ((size_t)(same ? 1 : 2) * tb * TW_ROWB + 1023) / 1024 * 1024;
+}
+static size_t tcp_smem_bytes(int tb, int nstg, int nraw) {
+  return 1024 + (size_t)nstg * tcb_stage_bytes(tb, false) + (size_t)nraw * tcp_slot_bytes(tb, false);
+}
+// stages and slab slots of a launch, sized for an off-diagonal pair: three and two when they fit,
+// else fewer (two and one at tb = 104: the producers release a slot before they split it)
+static void tcp_shape(int tb, int* nstg, int* nraw) {
+  const int cand[4][2] = {{3, 2}, {3, 1}, {2, 2}, {2, 1}};
+  for (const auto& c : cand)
+    if (tcp_smem_bytes(tb, c[0], c[1]) <= 232448 - 2048) { *nstg = c[0]; *nraw = c[1]; return; }
+  *nstg = 0;
+  *nraw = 0;
+}
+
+template <int GP>
+__global__ void __launch_bounds__(TW_THREADS, 1)
+gram_tcp_kernel(const __grid_constant__ CUtensorMap tmx, int nz, int nx, int nt /* rows tiled */, int tb, int T,
+                const Box* __restrict__ boxes, const float* __restrict__ gz, const float* __restrict__ gx,
+                const unsigned* __restrict__ xmax_bits, int nstg, int nraw, double* __restrict__ part,
+                int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t full_bar[TG_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TG_STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t accfree_bar;
+  __shared__ __align__(8) uint64_t rfull_bar[2];
+  __shared__ __align__(8) uint64_t rempty_bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ float wts[2][TG_PX];
+
+  const int k = blockIdx.y, ta = blockIdx.x / T, tbk = blockIdx.x % T;
+  const bool same = ta == tbk;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ra0 = ta * tb, rna = min(tb, nt - ra0), rb0 = tbk * tb, rnb = min(tb, nt - rb0);
+  const int nbh = tc_nbh(rnb), N = 2 * nbh, rh = same ? tc_rows_hi(nbh) : N;
+  const size_t a_bytes = same ? 0 : (size_t)128 * TG_K * 2, hi_bytes = (size_t)rh * TG_K * 2;
+  const size_t st_bytes = a_bytes + hi_bytes + (size_t)N * TG_K * 2;
+  const size_t slot_bytes = tcp_slot_bytes(tb, same);
+  const Box b = boxes[k];
+  const int nch = (b.x1 - b.x0 + ((nx & 1) ? 1 : (b.x0 & 1)) + TG_PX - 1) / TG_PX;
+  const int nst = (b.z1 - b.z0) * nch;
+  const int nchain = (nst + TG_CPA - 1) / TG_CPA;
+  unsigned char* raw = smem + nstg * st_bytes;
+
+  for (size_t e = tid; e < (nstg * st_bytes + nraw * slot_bytes) / 16; e += TW_THREADS)
+    reinterpret_cast<uint4*>(smem)[e] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (tid == 0) {
+    for (int i = 0; i < nstg; ++i) {
+      tc::mbar_init(&full_bar[i], TW_PROD);
+      tc::mbar_init(&empty_bar[i], 1);
+    }
+    tc::mbar_init(&acc_bar, 1);
+    tc::mbar_init(&accfree_bar, TW_PROD);
+    for (int i = 0; i < nraw; ++i) {
+      tc::mbar_init(&rfull_bar[i], 1);
+      tc::mbar_init(&rempty_bar[i], TW_PROD);
+    }
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == TW_PROD) {
+    // ---- MMA warp (as the one-tile kernel; A is tile a's buffer off the diagonal)
+    const uint32_t idesc = tc::gp_bf16(GP) ? tc::idesc_bf16(128, N) : tc::idesc_f16(128, N);
+    const uint32_t sb = tc::smem_u32(smem);
+    const uint64_t da0 = tc::smem_desc(sb, 128, TG_SBO), dh0 = tc::smem_desc(sb + (uint32_t)a_bytes, 128, TG_SBO);
+    const uint64_t dl0 = tc::smem_desc(sb + (uint32_t)(a_bytes + hi_bytes), 128, TG_SBO);
+    bool ok = true;
+    for (int i = 0; i < nst; ++i) {
+      const int si = i % nstg, c = i / TG_CPA;
+      if (ok) ok = tc::mbar_wait(&full_bar[si], (i / nstg) & 1);
+      if (i % TG_CPA == 0 && c > 0 && ok) ok = tc::mbar_wait(&accfree_bar, (c - 1) & 1);
+      ok = __all_sync(~0u, ok);
+      tc::fence_after();
+      const uint64_t so = (uint64_t)((si * st_bytes) >> 4);
+      if (tc::elect_one()) {
+#pragma unroll
+        for (int ks = 0; ks < TG_K / 16; ++ks) {
+          const uint64_t ad = da0 + so + (uint64_t)(16 * ks), hd = dh0 + so + (uint64_t)(16 * ks);
+          const uint64_t ld = dl0 + so + (uint64_t)(16 * ks);
+          tc::mma_f16(tbase, ad, hd, idesc, (i % TG_CPA == 0 && ks == 0) ? 0u : 1u);
+          if constexpr (tc::gp_three_products(GP)) tc::mma_f16(tbase, ad, ld, idesc, 1u);
+        }
+        tc::mma_commit(&empty_bar[si]);
+        if (i % TG_CPA == TG_CPA - 1 || i == nst - 1) tc::mma_commit(&acc_bar);
+      }
+      __syncwarp();
+    }
+    if (!ok && lane == 0) atomicOr(err, 1);
+  } else if (warp == TW_PROD + 1) {
+    // ---- loader warp: slab i into slot i mod nraw: tile b's rows, then tile a's
+    bool ok = true;
+    const float* gzk = gz + (size_t)k * nz;
+    const float* gxk = gx + (size_t)k * nx;
+    const uint32_t bytes = (uint32_t)((same ? 1 : 2) * tb * TW_ROWB);
+    TcSlab q;
+    q.start(0, nch);
+    for (int i = 0; i < nst; ++i, q.next(nch)) {
+      const int sl = i % nraw;
+      if (i >= nraw && ok) ok = tc::mbar_wait(&rempty_bar[sl], ((i / nraw) - 1) & 1);
+      ok = __all_sync(~0u, ok);
+      const int x = q.xs(b, nx) + lane;
+      wts[sl][lane] = (x >= b.x0 && x < b.x1) ? gzk[q.z(b)] * gxk[x] : 0.f;
+      __syncwarp();
+      if (lane == 0) {
+        unsigned char* dst = raw + (size_t)sl * slot_bytes;
+        tc::mbar_arrive_expect_tx(&rfull_bar[sl], bytes);
+        tc::tma_load_2d(dst, &tmx, (int)q.p0(b, nx), rb0, &rfull_bar[sl]);
+        if (!same) tc::tma_load_2d(dst + (size_t)tb * TW_ROWB, &tmx, (int)q.p0(b, nx), ra0, &rfull_bar[sl]);
+      }
+    }
+    if (!ok && lane == 0) atomicOr(err, 1);
+  } else {
+    // ---- producer warps: pixel slots (ps, ps + 1), rows rl + 16 j of both tiles (as the one-tile
+    // kernel's producers)
+    const int pg = warp & 7, jh = warp >> 3, lgrp = warp & 3, cq = warp >> 2;
+    const int ps = 4 * pg + 2 * (lane & 1), rl = lane >> 1;
+    const float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
+    const int roff = rl * TW_ROWB + ps * 8;
+    const uint32_t soff = (uint32_t)((rl >> 3) * TG_SBO + (2 * ps >> 3) * 128 + (rl & 7) * 16 + (2 * ps & 7) * 2);
+    const uint32_t sneg = (uint32_t)(nbh >> 3) * TG_SBO;
+    const uint32_t tl = tbase + ((uint32_t)(lgrp * 32) << 16);
+    const int nb16 = (N + 15) / 16;
+    bool ok = true;
+    auto promote = [&](int c) {
+      if (ok) ok = tc::mbar_wait(&acc_bar, c & 1);
+      tc::fence_after();
+#pragma unroll
+      for (int bq = 0; bq < 4; ++bq) {
+        const int blk = cq + 4 * bq;
+        if (blk < nb16) {
+          uint32_t a[16], t[16];
+          tc::tmem_ld16_async(tl + (uint32_t)(16 * blk), a);
+          if (c > 0) tc::tmem_ld16_async(tl + TW_SUMS + (uint32_t)(16 * blk), t);
+          tc::tmem_wait_ld();
+          if (c > 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = __float_as_uint(__uint_as_float(a[j]) + __uint_as_float(t[j]));
+          }
+          tc::tmem_st16(tl + TW_SUMS + (uint32_t)(16 * blk), a);
+        }
+      }
+      tc::tmem_wait_st();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&accfree_bar);
+    };
+    int next_c = 0;
+    for (int i = 0; i < nst; ++i) {
+      const int si = i % nstg, sl = i % nraw;
+      if (ok) ok = tc::mbar_wait(&rfull_bar[sl], (i / nraw) & 1);
+      const float g0 = wts[sl][ps], g1 = wts[sl][ps + 1];
+      // this thread's rows of both tiles into registers, then the slot goes back to the loader
+      float4 vb[kTcGramNaMax / 32], va[kTcGramNaMax / 32];
+      {
+        const unsigned char* src = raw + (size_t)sl * slot_bytes + roff;
+#pragma unroll
+        for (int jj = 0; jj < kTcGramNaMax / 32; ++jj) {
+          const int j = 2 * jj + jh, r = rl + 16 * j;
+          vb[jj] = r < rnb ? *reinterpret_cast<const float4*>(src + j * 16 * TW_ROWB) : make_float4(0.f, 0.f, 0.f, 0.f);
+          va[jj] = (!same && r < rna) ? *reinterpret_cast<const float4*>(src + (size_t)tb * TW_ROWB + j * 16 * TW_ROWB)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&rempty_bar[sl]);
+      if (i >= nstg && ok) ok = tc::mbar_wait(&empty_bar[si], ((i / nstg) - 1) & 1);
+      {
+        unsigned char* Ahi = smem + si * st_bytes + soff;
+        unsigned char* Bhi = Ahi + a_bytes;
+        unsigned char* Blo = Bhi + hi_bytes;
+        const float2 gg0 = make_float2(g0 * sc, g0 * sc), gg1 = make_float2(g1 * sc, g1 * sc);
+        const float2 gd0 = make_float2(2.f * gg0.x, 2.f * gg0.x), gd1 = make_float2(2.f * gg1.x, 2.f * gg1.x);
+#pragma unroll
+        for (int jj = 0; jj < kTcGramNaMax / 32; ++jj) {
+          const int j = 2 * jj + jh, r = rl + 16 * j;
+          if (r < rnb) {
+            const float4 v = vb[jj];
+            uint32_t h0, h1, l0 = 0u, l1 = 0u;
+            tc::split2_gp<GP>(make_float2(v.x, v.y), gg0, gd0, h0, l0);
+            tc::split2_gp<GP>(make_float2(v.z, v.w), gg1, gd1, h1, l1);
+            *reinterpret_cast<uint2*>(Bhi + j * 2 * TG_SBO) = make_uint2(h0, h1);
+            *reinterpret_cast<uint2*>(Bhi + sneg + j * 2 * TG_SBO) = make_uint2(tc::neg_i_raw(h0), tc::neg_i_raw(h1));
+            if constexpr (tc::gp_three_products(GP)) {
+              *reinterpret_cast<uint2*>(Blo + j * 2 * TG_SBO) = make_uint2(l0, l1);
+              *reinterpret_cast<uint2*>(Blo + sneg + j * 2 * TG_SBO) = make_uint2(tc::neg_i_raw(l0), tc::neg_i_raw(l1));
+            }
+          }
+          if (!same && r < rna) {
+            const float4 v = va[jj];
+            *reinterpret_cast<uint2*>(Ahi + j * 2 * TG_SBO) =
+                make_uint2(tc::hi2_gp<GP>(make_float2(v.x, v.y), gg0), tc::hi2_gp<GP>(make_float2(v.z, v.w), gg1));
+          }
+        }
+      }
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&full_bar[si]);
+      if (i % TG_CPA == 1 && i / TG_CPA >= 1) promote(next_c++);
+    }
+    while (next_c < nchain) promote(next_c++);
+    if (!ok && lane == 0) atomicOr(err, 1);
+
+    // block partial (doubles): plane 0 = Re D', plane 1 = Im D' (rows < rna, columns < rnb), through
+    // shared memory for coalesced writes
+    float* tr = reinterpret_cast<float*>(smem);   // [2][rna][ldt]
+    const int ldt = rnb + 1 - (rnb & 1);
+    tc_bar_producers();
+    const int row = lgrp * 32 + lane;
+#pragma unroll
+    for (int bq = 0; bq < 4; ++bq) {
+      const int blk = cq + 4 * bq;
+      if (blk < nb16) {
+        uint32_t a[16];
+        if (nchain > 0) {
+          tc::tmem_ld16_async(tl + TW_SUMS + (uint32_t)(16 * blk), a);
+          tc::tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) a[j] = 0u;
+        }
+        if (row < rna) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = 16 * blk + j, pl = col >= nbh ? 1 : 0, cj = col - pl * nbh;
+            if (col < N && cj < rnb) tr[((size_t)pl * rna + row) * ldt + cj] = __uint_as_float(a[j]);
+          }
+        }
+      }
+    }
+    tc::fence_before();
+    tc_bar_producers();
+    double* out = part + (((size_t)k * T + ta) * T + tbk) * 2 * (size_t)tb * tb;
+    for (int e = tid; e < 2 * rna * rnb; e += 32 * TW_PROD) {
+      const int pl = e / (rna * rnb), rem = e - pl * rna * rnb, r = rem / rnb, j = rem - r * rnb;
+      out[(size_t)pl * tb * tb + (size_t)r * tb + j] = (double)tr[((size_t)pl * rna + r) * ldt + j];
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
 template <int GP>
 static void launch_gram_tc_gp(const lcf_plan* P, cudaStream_t st) {
   const lcf_config& c = P->cfg;
   const int na = P->tc_na;
-  if (P->tc_T > 1) {
+  int nstg = 0, nraw = 0;
+  if (P->tc_T > 1) tcp_shape(P->tc_tb, &nstg, &nraw);
+  if (P->tc_T > 1 && P->tm_xa_ok && nstg > 0) {
+    dim3 gb(P->tc_T * P->tc_T, P->nd);
+    gram_tcp_kernel<GP><<<gb, TW_THREADS, tcp_smem_bytes(P->tc_tb, nstg, nraw), st>>>(
+        P->tm_xa, c.nz, c.nx, na, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, nstg, nraw,
+        P->ws.gtc, P->ws.err);
+  } else if (P->tc_T > 1) {
     dim3 gb(P->tc_T * P->tc_T, P->nd);
     gram_tcb_kernel<GP><<<gb, TG_THREADS, gram_tcb_smem_bytes(P->tc_tb), st>>>(
         P->ws.xa, c.nz, c.nx, na, P->tc_tb, P->tc_T, P->ws.box, P->ws.gz, P->ws.gx, P->ws.xmax, P->ws.gtc,
@@ -826,7 +1093,7 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
 // made (no driver entry point), with the same results.
 cudaError_t gram_tc_make_map(lcf_plan* P) {
   P->tm_xa_ok = false;
-  if (P->tc_T != 1 || (P->npix & 1)) return cudaSuccess;
+  if (P->npix & 1) return cudaSuccess;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -841,7 +1108,8 @@ cudaError_t gram_tc_make_map(lcf_plan* P) {
   }
   const cuuint64_t dims[2] = {(cuuint64_t)P->npix, (cuuint64_t)P->n1};
   const cuuint64_t strides[1] = {(cuuint64_t)P->npix * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)kTcSlabBox, (cuuint32_t)P->tc_na};
+  // one tile's rows a box (tile pairs), else all the rows of the one-tile kernel
+  const cuuint32_t box[2] = {(cuuint32_t)kTcSlabBox, (cuuint32_t)(P->tc_T > 1 ? P->tc_tb : P->tc_na)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(&P->tm_xa, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, P->ws.xa, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -852,7 +1120,15 @@ cudaError_t gram_tc_make_map(lcf_plan* P) {
 
 template <int GP>
 static cudaError_t gram_tc_configure_gp(size_t mx) {
-  const cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+  if (e != cudaSuccess) return e;
+  size_t mp = 0;   // the largest tile-pair launch over every tile height
+  for (int tb = 8; tb <= kTcTileMax; tb += 8) {
+    int nstg = 0, nraw = 0;
+    tcp_shape(tb, &nstg, &nraw);
+    if (nstg > 0 && tcp_smem_bytes(tb, nstg, nraw) > mp) mp = tcp_smem_bytes(tb, nstg, nraw);
+  }
+  e = cudaFuncSetAttribute(gram_tcp_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(gram_tcb_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)gram_tcb_smem_bytes(kTcTileMax));
