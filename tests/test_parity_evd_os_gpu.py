@@ -185,6 +185,7 @@ def test_os_learned_rule_is_refused():
     ((201, 30, 26), (1, 2), "LCF_T_FIXED", False),       # odd length: a zero padding column
     ((224, 24, 20), (1, 2), "LCF_T_SLOPE", True),        # longest on this path: 14 warps, no padding
     ((150, 22, 18), (1, 1), "LCF_T_NCC", True),          # method 4 after the cluster EVD
+    ((200, 33, 29), (2, 2), "LCF_T_CURVATURE", True),    # odd pixel count: tile pairs without the tensor map
 ])
 def test_os_long_packets(shape, grid, mode, tc):
     lib = L()
