@@ -398,8 +398,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmx, int use_map, const float
 // The CTA forms D'(a, b) = A_hi(a) (B_hi(b) + 2 B_lo(b))^T with the operands of the short
 // kernel (B(b) = [w ; -i w] of tile b's rows), A from tile a's rows (aliasing B_hi when
 // a == b); both orders of every off-diagonal pair are formed, so the assembly takes the
-// Hermitian part 1/2 (D'(a, b) + D'(b, a)^H) as before.  The split reads the packet
-// directly (no fp32 staging: the two tiles' rows would not fit beside the stages).
+// Hermitian part 1/2 (D'(a, b) + D'(b, a)^H) as before.  This lock-step kernel reads the packet
+// directly (no fp32 staging) and is the path for odd pixel counts, where no tensor map can be made;
+// otherwise gram_tcp_kernel below runs the same products as a pipeline.
 constexpr int TB_STAGES = 3;
 __host__ __device__ inline size_t tcb_stage_bytes(int tb, bool same) {
   const int nbh = tc_nbh(tb), rh = same ? tc_rows_hi(nbh) : 2 * nbh;
