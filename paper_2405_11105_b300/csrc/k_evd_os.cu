@@ -282,6 +282,119 @@ __device__ __forceinline__ int eo_step(float2 (&TR)[4][RP], float2 (&TI)[4][RP],
   return any;
 }
 
+// ---- the step of a last warp that holds two pair slots (four columns) ----
+// When the last warp has at most two pairs it runs this step: the same dots, rotation and apply
+// for slots 0 and 1 only (register sets 0 and 1, renamed with period two), eight partial sums
+// reduce-scattered so that lane l receives component ((l >> 2) & 3) of slot (l >> 4).  It holds
+// pair h - 1 (slot slast, its own top becomes its bottom) and trades slot 0's top and bottom with
+// the previous warp as a four-slot warp trades its slots 3 and 0; the top leaving its slot 1 is
+// written for no reader.
+__device__ __forceinline__ float eo_reduce_scatter8(const float (&v)[8], int lane) {
+  float w4[4], w2[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[k] : v[4 + k], keep = hi ? v[4 + k] : v[k];
+    w4[k] = keep + __shfl_xor_sync(~0u, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool hi = lane & 8;
+    const float send = hi ? w4[k] : w4[2 + k], keep = hi ? w4[2 + k] : w4[k];
+    w2[k] = keep + __shfl_xor_sync(~0u, send, 8);
+  }
+  const bool hi = lane & 4;
+  float w1 = (hi ? w2[1] : w2[0]) + __shfl_xor_sync(~0u, hi ? w2[0] : w2[1], 4);
+  w1 += __shfl_xor_sync(~0u, w1, 2);
+  return w1 + __shfl_xor_sync(~0u, w1, 1);
+}
+
+template <int RP, int U>
+__device__ __forceinline__ int eo_step2(float2 (&TR)[4][RP], float2 (&TI)[4][RP], float2 (&BR)[4][RP],
+                                        float2 (&BI)[4][RP], const EoSweepCtx& x, int par) {
+  const int lane = x.lane;
+  float v[8];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int t = (s - U) & 1, b = (s + U) & 1;
+    float2 a2 = make_float2(0.f, 0.f), b2 = a2, gr = a2, gi = a2, gj = a2;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      a2 = __ffma2_rn(TR[t][i], TR[t][i], a2);
+      a2 = __ffma2_rn(TI[t][i], TI[t][i], a2);
+      b2 = __ffma2_rn(BR[b][i], BR[b][i], b2);
+      b2 = __ffma2_rn(BI[b][i], BI[b][i], b2);
+      gr = __ffma2_rn(TR[t][i], BR[b][i], gr);
+      gr = __ffma2_rn(TI[t][i], BI[b][i], gr);
+      gi = __ffma2_rn(TR[t][i], BI[b][i], gi);
+      gj = __ffma2_rn(TI[t][i], BR[b][i], gj);
+    }
+    v[4 * s] = a2.x + a2.y;
+    v[4 * s + 1] = b2.x + b2.y;
+    v[4 * s + 2] = gr.x + gr.y;
+    v[4 * s + 3] = (gi.x + gi.y) - (gj.x + gj.y);
+  }
+  const float tot = eo_reduce_scatter8(v, lane);
+  const int base = lane & 16;
+  const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 4);
+  const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 8), __shfl_sync(~0u, tot, base + 12));
+  float c;
+  float2 st;
+  int rot;
+  bool calm;
+  ep_rotation_os(a, b, gm, EO_TOL, x.clim2, x.slim2, c, st, rot, calm);
+  if (4 * x.warp + (lane >> 4) >= x.h) { rot = 0; calm = true; }
+  const unsigned rmask = __ballot_sync(~0u, rot);
+  const unsigned wmask = __ballot_sync(~0u, !calm);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (!((rmask >> (16 * s)) & 1u)) continue;   // warp-uniform
+    const float cs = __shfl_sync(~0u, c, 16 * s), sr = __shfl_sync(~0u, st.x, 16 * s), si = __shfl_sync(~0u, st.y, 16 * s);
+    const int t = (s - U) & 1, bb = (s + U) & 1;
+    const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
+    const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      const float2 xr = TR[t][i], xi = TI[t][i], yr = BR[bb][i], yi = BI[bb][i];
+      TR[t][i] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
+      TI[t][i] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
+      BR[bb][i] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
+      BI[bb][i] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
+    }
+  }
+  // slot 1's top (no reader) and slot 0's bottom leave the warp
+  const int t1 = (1 - U) & 1, b0 = U & 1;
+  {
+    float4* dt = x.xt + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
+    float4* db = x.xb + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      dt[i * 32] = make_float4(TR[t1][i].x, TR[t1][i].y, TI[t1][i].x, TI[t1][i].y);
+      db[i * 32] = make_float4(BR[b0][i].x, BR[b0][i].y, BI[b0][i].x, BI[b0][i].y);
+    }
+  }
+  const int any = __syncthreads_or(wmask != 0u);
+  // slot slast (pair h - 1) takes its own top as bottom, into the register its bottom is read from
+  // at the next step; slot 0's new top comes from the previous warp's slot 3
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    if (s != x.slast) continue;
+    const int tl = (s - U) & 1, bn = (s + U + 1) & 1;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) { BR[bn][i] = TR[tl][i]; BI[bn][i] = TI[tl][i]; }
+  }
+  {
+    const float4* src = x.xt + (size_t)(par * x.nw + x.warp - 1) * RP * 32 + lane;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      const float4 q4 = src[i * 32];
+      TR[t1][i] = make_float2(q4.x, q4.y);
+      TI[t1][i] = make_float2(q4.z, q4.w);
+    }
+  }
+  return any;
+}
+
 template <int RP>
 __global__ void __launch_bounds__(EO_THREADS, 1)
 evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, const float2* __restrict__ Tg,
@@ -469,15 +582,29 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
       if (any) { quiet = 0; last = steps; }
       else ++quiet;
     };
+    // the last warp runs the two-slot step when it holds at most two pairs (and is not the only warp)
+    const bool two = L.nw > 1 && warp == L.nw - 1 && h - 4 * (L.nw - 1) <= 2;
     while (steps < maxsteps) {
-      int r0 = eo_step<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
-      track(r0);
-      r0 = eo_step<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
-      track(r0);
-      r0 = eo_step<RP, 2>(TR, TI, BR, BI, xc, steps & 1);
-      track(r0);
-      r0 = eo_step<RP, 3>(TR, TI, BR, BI, xc, steps & 1);
-      track(r0);
+      int r0;
+      if (two) {
+        r0 = eo_step2<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+        r0 = eo_step2<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+        r0 = eo_step2<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+        r0 = eo_step2<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+      } else {
+        r0 = eo_step<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+        r0 = eo_step<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+        r0 = eo_step<RP, 2>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+        r0 = eo_step<RP, 3>(TR, TI, BR, BI, xc, steps & 1);
+        track(r0);
+      }
       if (quiet >= per) { converged = 1; break; }
     }
     sweeps = (last + per - 1) / per;
