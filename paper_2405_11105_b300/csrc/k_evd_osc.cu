@@ -17,9 +17,10 @@
 //  evd_osc_kernel    the sweeps and everything after, on a cluster of four CTAs.  CTA
 //                    c holds rows [c R, (c + 1) R) (R = ceil(Nt / 4)) of every column in
 //                    registers; warp w owns pair slots 8w .. 8w + 7 of the circle
-//                    ordering (16 columns), lane l rows l and l + 32 of the CTA's share
-//                    as one packed pair.  A step sums each slot's partial 2x2 Gram over
-//                    the warp (reduce-scatter: lane l ends with value l), sends that
+//                    ordering (16 columns; a last warp with at most four pairs holds
+//                    four slots and runs a four-slot step), lane l rows l and l + 32 of
+//                    the CTA's share as one packed pair.  A step sums each slot's
+//                    partial 2x2 Gram over the warp (reduce-scatter), sends that
 //                    partial to the other three CTAs (st.async into their shared memory,
 //                    completing the bytes of their step-parity mbarrier), adds the four
 //                    partials in rank order (so every CTA forms the same rotations),
@@ -40,6 +41,7 @@ constexpr int EC_THREADS = 1024;               // Cholesky kernel
 constexpr int EC_PANEL = 8;
 constexpr int EQ_C = 4;                        // CTAs per window of the sweeps
 constexpr int EQ_S = 8;                        // pair slots per warp
+static_assert((EQ_C & (EQ_C - 1)) == 0, "cluster ranks wrap by masking");
 constexpr float EQ_TOL = 2.0e-6f;              // relative orthogonality test
 constexpr int EQ_SUBSPACE_ITERS = 6;
 
@@ -164,12 +166,18 @@ struct EqLayout {
 };
 // u: this CTA's rows of the columns (then of U, then of V); x: the sweeps' exchange buffers, later
 // the partial products Vh^H U of every CTA
+// whether the last of several warps holds at most four of the ceil(Nt / 2) pairs
+__host__ __device__ inline bool eq_four(int n) {
+  const int h = (n + 1) / 2, nw = (h + EQ_S - 1) / EQ_S;
+  return nw > 1 && h - EQ_S * (nw - 1) <= 4;
+}
 __host__ __device__ inline EqLayout eq_layout(int n) {
   EqLayout L;
-  // the pair slots are padded to whole warps (zero columns, which never rotate), so the last slot
-  // of the ordering is always slot 7 of the last warp
+  // the pair slots are padded (zero columns, which never rotate) so that pair h - 1 is the last
+  // slot of the last warp: slot 7, or slot 3 when that warp holds at most four pairs and runs the
+  // four-slot step
   L.nw = ((n + 1) / 2 + EQ_S - 1) / EQ_S;
-  L.h = EQ_S * L.nw;
+  L.h = EQ_S * L.nw - (eq_four(n) ? 4 : 0);
   L.np = 2 * L.h;
   L.R = (n + EQ_C - 1) / EQ_C;
   L.lda = L.np + 1;
@@ -206,20 +214,63 @@ size_t evd_osc_smem_bytes(int nt) { return eq_layout(nt).end; }
 // ---------------------------------------------------------------------------------------------
 // evd_osc_kernel: the sweeps on a cluster of EQ_C CTAs
 struct EqCtx {
-  float4* xt;            // [parity][warp][lane]: the top leaving slot 7
-  float4* xb;            // [parity][warp][lane]: the bottom leaving slot 0
-  float* recv;           // [parity][source rank][warp][lane]: the other CTAs' partial sums
-  uint32_t peer_recv[EQ_C], peer_bar[EQ_C];   // cluster addresses of each CTA's recv and mbarriers
-  uint64_t* bar;         // this CTA's mbarriers, one per step parity
-  unsigned bytes;        // partial-sum bytes a step brings in: (EQ_C - 1) * nw * 32 * 4
-  int nw, h, warp, lane, tid, rank;
+  // As few registers as the sweep loop can live with (it keeps every column in registers and
+  // runs at the 128-register bound): 32-bit shared addresses, the rest derived.
+  uint32_t xt_s;         // float4 [parity][warp][lane]: the top leaving slot 7; after it
+                         // float4 [parity][warp][lane]: the bottom leaving slot 0 (xb), then
+                         // float [parity][source rank][warp][lane]: the other CTAs' partial sums (recv)
+  uint32_t bdelta;       // this CTA's mbarriers (one per step parity) less its recv
+  int nw, warp, lane, rank;
   bool wfirst, wlast;
   float clim2, slim2;    // squared cosine and sine bounds of a calm step (ep_rotation_os)
+  __device__ __forceinline__ uint32_t xb() const { return xt_s + (uint32_t)(nw * 2 * 32 * 16); }
+  __device__ __forceinline__ uint32_t recv() const { return xt_s + (uint32_t)(nw * 4 * 32 * 16); }
+  __device__ __forceinline__ uint32_t bar() const { return recv() + bdelta; }
+  // the partial-sum bytes a step brings in
+  __device__ __forceinline__ uint32_t bytes() const { return (uint32_t)((EQ_C - 1) * nw * 32 * 4); }
 };
 
+// plain (compiler-scheduled) shared-memory accesses by 32-bit shared address
+__device__ __forceinline__ void eq_sts4(uint32_t a, float4 v) {
+  *reinterpret_cast<float4*>(__cvta_shared_to_generic(a)) = v;
+}
+__device__ __forceinline__ float4 eq_lds4(uint32_t a) {
+  return *reinterpret_cast<const float4*>(__cvta_shared_to_generic(a));
+}
+__device__ __forceinline__ float eq_lds(uint32_t a) {
+  return *reinterpret_cast<const float*>(__cvta_shared_to_generic(a));
+}
+__device__ __forceinline__ void eq_arrive_expect_tx(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+// wait on this CTA's mbarrier at address b with acquire at cluster scope, for at most EP_WAIT_NS
+// of wall time; false if the limit ran out
+__device__ __forceinline__ bool eq_try(uint32_t b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred q;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 q, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(done)
+      : "r"(b), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool eq_wait(uint32_t b, uint32_t parity) {
+  if (eq_try(b, parity)) return true;
+  const uint64_t t0 = ep_now();
+  for (;;) {
+    if (eq_try(b, parity)) return true;
+    if (ep_now() - t0 > EP_WAIT_NS) return false;
+  }
+}
 __device__ __forceinline__ void eq_st_async_f32(uint32_t addr, float v, uint32_t bar_cluster_addr) {
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
                ::"r"(addr), "r"(__float_as_uint(v)), "r"(bar_cluster_addr) : "memory");
+}
+
+// this CTA's partial sum at byte offset off of CTA q's recv, completing bytes of q's mbarrier par
+__device__ __forceinline__ void eq_send(const EqCtx& x, uint32_t off, int par, int q, float part) {
+  eq_st_async_f32(ep_mapa(x.recv() + off, (uint32_t)q), part, ep_mapa(x.bar() + (uint32_t)(par * 8), (uint32_t)q));
 }
 
 // The reduce-scatter of 32 partial sums (value 4 s + c: slot s, component c) after its first level
@@ -262,12 +313,14 @@ __device__ __forceinline__ void eq_gram(float2 tr, float2 ti, float2 br, float2 
 }
 
 // One step at phase U of an eight-step block (slot s keeps its top in T*[(s - U) & 7], its bottom
-// in B*[(s + U) & 7]); r is the step's index (its parity picks the buffers and the mbarrier).
+// in B*[(s + U) & 7]).  Blocks start at multiples of eight steps, so the step's parity (which picks
+// the buffers and the mbarrier) is U & 1 and the mbarrier's phase (U >> 1) & 1.
 // Returns whether any slot of the CTA rotated; *ok turns false when a wait gives up.
 template <int U>
 __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 (&BR)[8], float2 (&BI)[8],
-                                       const EqCtx& x, int r, bool* ok) {
-  const int lane = x.lane, par = r & 1;
+                                       const EqCtx& x, bool* ok) {
+  const int lane = x.lane;
+  constexpr int par = U & 1;
   // slots s and s + 4 together, folded at once into the first level of the reduce-scatter
   float w16[16];
   const bool hi16 = lane & 16;
@@ -282,16 +335,16 @@ __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 
   }
   const float part = eq_reduce_scatter_rest(w16, lane);   // this CTA's rows
   // ---- the partial to the other CTAs, then the sum of all four in rank order
-  if (x.tid == 0) ep_arrive_expect_tx(&x.bar[par], x.bytes);
+  if ((x.warp | lane) == 0) eq_arrive_expect_tx(x.bar() + (uint32_t)(par * 8), x.bytes());
   const uint32_t off = (uint32_t)((((par * EQ_C + x.rank) * x.nw + x.warp) * 32 + lane) * 4);
 #pragma unroll
-  for (int q = 0; q < EQ_C; ++q)
-    if (q != x.rank) eq_st_async_f32(x.peer_recv[q] + off, part, x.peer_bar[q] + (uint32_t)(par * 8));
-  if (*ok) *ok = ep_wait(&x.bar[par], (r >> 1) & 1);
+  for (int j = 0; j < EQ_C - 1; ++j)
+    eq_send(x, off, par, (x.rank + 1 + j) & (EQ_C - 1), part);
+  if (*ok) *ok = eq_wait(x.bar() + (uint32_t)(par * 8), (U >> 1) & 1);
   float tot = 0.f;
 #pragma unroll
   for (int q = 0; q < EQ_C; ++q)
-    tot += q == x.rank ? part : x.recv[(((par * EQ_C + q) * x.nw + x.warp) * 32) + lane];
+    tot += q == x.rank ? part : eq_lds(x.recv() + (uint32_t)((((par * EQ_C + q) * x.nw + x.warp) * 32 + lane) * 4));
   // ---- each group of four lanes forms the rotation of slot lane >> 2
   const int base = lane & 28;
   const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 1);
@@ -319,8 +372,9 @@ __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 
   // ---- the circle move: slot 7's top and slot 0's bottom leave the warp
   const int t7 = (7 - U) & 7, t0 = (0 - U) & 7, b0 = U & 7;
   {
-    x.xt[(par * x.nw + x.warp) * 32 + lane] = make_float4(TR[t7].x, TR[t7].y, TI[t7].x, TI[t7].y);
-    x.xb[(par * x.nw + x.warp) * 32 + lane] = make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y);
+    const uint32_t o = (uint32_t)(((par * x.nw + x.warp) * 32 + lane) * 16);
+    eq_sts4(x.xt_s + o, make_float4(TR[t7].x, TR[t7].y, TI[t7].x, TI[t7].y));
+    eq_sts4(x.xb() + o, make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y));
   }
   const int any = __syncthreads_or(wmask != 0u);
   // slot h - 1 (slot 7 of the last warp) takes its own top as bottom, into the register slot 0's
@@ -338,12 +392,104 @@ __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 
     TR[t0] = BR[b0]; TI[t0] = BI[b0];
   }
   if (x.warp > 0) {
-    const float4 q = x.xt[(par * x.nw + x.warp - 1) * 32 + lane];
+    const float4 q = eq_lds4(x.xt_s + (uint32_t)(((par * x.nw + x.warp - 1) * 32 + lane) * 16));
     TR[t7] = make_float2(q.x, q.y); TI[t7] = make_float2(q.z, q.w);
   }
-  if (8 * x.warp + 7 < x.h - 1) {
-    const float4 q = x.xb[(par * x.nw + x.warp + 1) * 32 + lane];
+  if (!x.wlast) {   // slot 7 is not pair h - 1
+    const float4 q = eq_lds4(x.xb() + (uint32_t)(((par * x.nw + x.warp + 1) * 32 + lane) * 16));
     BR[b0] = make_float2(q.x, q.y); BI[b0] = make_float2(q.z, q.w);
+  }
+  return any;
+}
+
+// ---- the step of a last warp that holds at most four pair slots (eight columns) ----
+// The same dots, rotation and apply for slots 0..3 only (register sets 0..3, renamed with period
+// four), sixteen partial sums reduce-scattered so that lane l holds component (l >> 1) & 3 of slot
+// l >> 3, and the same exchange of that partial with the other CTAs (whose last warps run this step
+// too; a pass of four steps starts at a multiple of four, so parity and phase follow from U as
+// there).  Its slot 3 holds pair h - 1 (the layout pads the pairs to that) and its slot 0 trades top
+// and bottom with the previous warp; no warp reads the top leaving slot 3.
+__device__ __forceinline__ float eq_reduce_scatter16(const float (&v)[16], int lane) {
+  float w8[8], w4[4], w2[2];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const bool hi = lane & 16;
+    w8[q] = (hi ? v[8 + q] : v[q]) + __shfl_xor_sync(~0u, hi ? v[q] : v[8 + q], 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool hi = lane & 8;
+    w4[q] = (hi ? w8[4 + q] : w8[q]) + __shfl_xor_sync(~0u, hi ? w8[q] : w8[4 + q], 8);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const bool hi = lane & 4;
+    w2[q] = (hi ? w4[2 + q] : w4[q]) + __shfl_xor_sync(~0u, hi ? w4[q] : w4[2 + q], 4);
+  }
+  const bool hi = lane & 2;
+  const float w1 = (hi ? w2[1] : w2[0]) + __shfl_xor_sync(~0u, hi ? w2[0] : w2[1], 2);
+  return w1 + __shfl_xor_sync(~0u, w1, 1);
+}
+
+template <int U>
+__device__ __forceinline__ int eq_step4(float2 (&TR)[8], float2 (&TI)[8], float2 (&BR)[8], float2 (&BI)[8],
+                                        const EqCtx& x, bool* ok) {
+  const int lane = x.lane;
+  constexpr int par = U & 1;
+  float v[16];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    float u[4];
+    eq_gram(TR[(s - U) & 3], TI[(s - U) & 3], BR[(s + U) & 3], BI[(s + U) & 3], u);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[4 * s + c] = u[c];
+  }
+  const float part = eq_reduce_scatter16(v, lane);
+  if ((x.warp | lane) == 0) eq_arrive_expect_tx(x.bar() + (uint32_t)(par * 8), x.bytes());
+  const uint32_t off = (uint32_t)((((par * EQ_C + x.rank) * x.nw + x.warp) * 32 + lane) * 4);
+#pragma unroll
+  for (int j = 0; j < EQ_C - 1; ++j)
+    eq_send(x, off, par, (x.rank + 1 + j) & (EQ_C - 1), part);
+  if (*ok) *ok = eq_wait(x.bar() + (uint32_t)(par * 8), (U >> 1) & 1);
+  float tot = 0.f;
+#pragma unroll
+  for (int q = 0; q < EQ_C; ++q)
+    tot += q == x.rank ? part : eq_lds(x.recv() + (uint32_t)((((par * EQ_C + q) * x.nw + x.warp) * 32 + lane) * 4));
+  // ---- each group of eight lanes forms the rotation of slot lane >> 3
+  const int base = lane & 24;
+  const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 2);
+  const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 4), __shfl_sync(~0u, tot, base + 6));
+  float c;
+  float2 st;
+  int rot;
+  bool calm;
+  ep_rotation_os(a, b, gm, EQ_TOL, x.clim2, x.slim2, c, st, rot, calm);
+  const unsigned rmask = __ballot_sync(~0u, rot);
+  const unsigned wmask = __ballot_sync(~0u, !calm);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!((rmask >> (8 * s)) & 1u)) continue;   // warp-uniform
+    const float cs = __shfl_sync(~0u, c, 8 * s), sr = __shfl_sync(~0u, st.x, 8 * s), si = __shfl_sync(~0u, st.y, 8 * s);
+    const int t = (s - U) & 3, bb = (s + U) & 3;
+    const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
+    const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
+    const float2 xr = TR[t], xi = TI[t], yr = BR[bb], yi = BI[bb];
+    TR[t] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
+    TI[t] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
+    BR[bb] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
+    BI[bb] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
+  }
+  // ---- slot 0's bottom leaves for the previous warp
+  const int t3 = (3 - U) & 3, b0 = U & 3;
+  eq_sts4(x.xb() + (uint32_t)(((par * x.nw + x.warp) * 32 + lane) * 16),
+          make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y));
+  const int any = __syncthreads_or(wmask != 0u);
+  // slot 3 takes its own top as bottom, into the register slot 0's bottom left; slot 0's new top
+  // comes from the previous warp's slot 7, into the register slot 3's top left
+  BR[b0] = TR[t3]; BI[b0] = TI[t3];
+  {
+    const float4 q = eq_lds4(x.xt_s + (uint32_t)(((par * x.nw + x.warp - 1) * 32 + lane) * 16));
+    TR[t3] = make_float2(q.x, q.y); TI[t3] = make_float2(q.z, q.w);
   }
   return any;
 }
@@ -404,16 +550,9 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
   cluster.sync();   // barriers of every CTA initialised
 
   EqCtx xc;
-  xc.xt = reinterpret_cast<float4*>(smem + L.x);
-  xc.xb = xc.xt + (size_t)2 * L.nw * 32;
-  xc.recv = reinterpret_cast<float*>(xc.xb + (size_t)2 * L.nw * 32);
-  for (int q = 0; q < EQ_C; ++q) {
-    xc.peer_recv[q] = ep_mapa(ep_smem(xc.recv), (uint32_t)q);
-    xc.peer_bar[q] = ep_mapa(ep_smem(bar), (uint32_t)q);
-  }
-  xc.bar = bar;
-  xc.bytes = (unsigned)((EQ_C - 1) * L.nw * 32 * 4);
-  xc.nw = L.nw; xc.h = h; xc.warp = warp; xc.lane = lane; xc.tid = tid; xc.rank = rank;
+  xc.xt_s = ep_smem(smem + L.x);
+  xc.nw = L.nw; xc.warp = warp; xc.lane = lane; xc.rank = rank;
+  xc.bdelta = ep_smem(bar) - xc.recv();
   xc.clim2 = (float)np * EQ_TOL * EQ_TOL;
   xc.slim2 = 0.25f / ((float)np * np * np);
   xc.wfirst = warp == 0;
@@ -454,17 +593,33 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
       if (any) { quiet = 0; last = steps; }
       else ++quiet;
     };
-    while (steps < maxsteps) {
-      int a = eq_step<0>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<1>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<2>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<3>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<4>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<5>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<6>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      a = eq_step<7>(TR, TI, BR, BI, xc, steps, &ok); track(a);
-      if (__syncthreads_or(!ok)) { sh_fail = 1; break; }   // a wait gave up: stop exchanging
-      if (quiet >= per) { converged = 1; break; }
+    // the two loops apart, so that each keeps its own registers; the four-slot loop holds one
+    // period (four steps) of code and meets the block's barrier every second pass, i.e. at the
+    // same steps as the eight-slot loop
+    if (eq_four(n) && warp == L.nw - 1) {
+      for (int half = 0;; half ^= 1) {
+        int a = eq_step4<0>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step4<1>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step4<2>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step4<3>(TR, TI, BR, BI, xc, &ok); track(a);
+        if (!half) continue;
+        if (__syncthreads_or(!ok)) { sh_fail = 1; break; }   // a wait gave up: stop exchanging
+        if (quiet >= per) { converged = 1; break; }
+        if (steps >= maxsteps) break;
+      }
+    } else {
+      while (steps < maxsteps) {
+        int a = eq_step<0>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<1>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<2>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<3>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<4>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<5>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<6>(TR, TI, BR, BI, xc, &ok); track(a);
+        a = eq_step<7>(TR, TI, BR, BI, xc, &ok); track(a);
+        if (__syncthreads_or(!ok)) { sh_fail = 1; break; }   // a wait gave up: stop exchanging
+        if (quiet >= per) { converged = 1; break; }
+      }
     }
     sweeps = (last + per - 1) / per;
   }
