@@ -23,14 +23,18 @@
 // Only the factor's columns are rotated: the eigenvectors come out of it, so a
 // Jacobi step touches Nt x Nt numbers where the two-sided method updates A and V.
 //
-// Layout of the sweeps.  Warp w owns pair slots 4w .. 4w + 3 of the round-robin (circle)
-// ordering, i.e. eight columns, in registers: lane l holds rows l, l + 32, l + 64, l + 96 as
-// packed pairs of rows, so the 2x2 Grams and the rotations run as packed FP32 operations.  A
-// step sums the four slots' partial Grams over the warp (reduce-scatter), forms the rotations
-// (the formulas of the two-sided kernels, ep_rotation2) and applies them; the circle move (tops
-// one slot up, bottoms one slot down, top[1] takes bottom[0], bottom[h-1] takes top[h-1], top[0]
-// stays) is a renaming of registers inside the warp, unrolled over four steps, and only two
-// columns per warp and step pass through shared memory (by step parity, one barrier per step).
+// Layout of the sweeps (a block ordering).  The columns, zero-padded to 8 nw for nw warps, form
+// 2 nw blocks of four; warp w holds blocks A_w and B_w in registers (lane l rows l, l + 32, l + 64,
+// l + 96 as packed pairs of rows, so the 2x2 Grams and the rotations run as packed FP32
+// operations).  A round is four steps in which each warp, alone, meets all sixteen pairs of its
+// A and B (column s of A with column (s + t) mod 4 of B at step t); the blocks then move one place
+// on the circle of the round-robin ordering (A_0 stays, A_1 takes B_0, A_w takes A_(w-1), B_w
+// takes B_(w+1), the last B takes its own A) through shared memory.  2 nw - 1 rounds meet every
+// pair of blocks once; the first round of a sweep also pairs the columns inside each block (three
+// steps), so a sweep meets every pair of columns once, in 8 nw - 1 steps like the circle ordering
+// of single columns.  A step sums the four slots' partial Grams over the warp (reduce-scatter),
+// forms the rotations (the formulas of the two-sided kernels, ep_rotation_os) and applies them;
+// the CTA meets at a barrier twice per round instead of once per step.
 #include <math.h>
 
 #include "evd_common.cuh"
@@ -65,19 +69,21 @@ struct EoLayout {
 // X = Vh^H U and Y = T X
 __host__ __device__ inline EoLayout eo_layout(int n) {
   EoLayout L;
-  L.np = n + (n & 1);
+  L.nw = (n + 7) / 8;
+  L.np = 8 * L.nw;           // column positions: two blocks of four per warp, zero columns past Nt
   L.h = L.np / 2;
   L.lda = L.np + 1;
   L.m = n < kEvdHead ? n : kEvdHead;
-  L.nw = (L.h + 3) / 4;
-  L.rp = (L.np + 63) / 64;   // row pairs per lane (rows l, l + 32, ...)
+  L.rp = (n + 63) / 64;      // row pairs per lane (rows l, l + 32, ...)
   size_t o = 0;
   L.a = o; o = eo_align(o + (size_t)L.np * L.lda * 8);
   {
-    const size_t xch = (size_t)2 * 2 * L.nw * L.rp * 32 * 16;
+    // the sweeps' block exchange [warp][column 0..7][row pair][lane] (float4) overlays a and x
+    const size_t xch = (size_t)L.nw * 8 * L.rp * 32 * 16;
     const size_t post = ((size_t)L.m * n + (size_t)L.m * L.m + (size_t)2 * L.m * L.np) * 8;
     const size_t chol = (size_t)EO_CB * L.np * 8;   // the Cholesky block's columns
-    size_t need = xch > post ? xch : post;
+    size_t need = xch > o ? xch - o : 0;
+    need = need > post ? need : post;
     need = need > chol ? need : chol;
     L.x = o; o = eo_align(o + need);
   }
@@ -110,21 +116,10 @@ __device__ __forceinline__ float2 eo_factor(const float2* A, int lda, const int*
   return r > pc ? A[(size_t)r * lda + pc] : cconj(A[(size_t)pc * lda + r]);
 }
 
-// ---- one Jacobi step of a warp that owns four pair slots (eight columns) ----
+// ---- the sweeps: warp w holds blocks A_w and B_w of four columns each ----
 // Lane l holds rows l, l + 32, l + 64, l + 96 of every column as row pairs (XR = real parts of
 // rows (2i) * 32 + l and (2i + 1) * 32 + l, XI the imaginary parts), so the dot products and the
-// rotations run as packed FP32 pairs.  The circle move shifts tops one slot up and bottoms one
-// slot down; inside the warp that is a renaming of registers: at phase U of a four-step block
-// slot s keeps its top in T*[(s - U) & 3] and its bottom in B*[(s + U) & 3], and only the top of
-// slot 3 and the bottom of slot 0 leave the warp (through shared memory, by step parity).
-struct EoSweepCtx {
-  float4* xt;      // [parity][warp][row pair][lane]: the top leaving slot 3
-  float4* xb;      // [parity][warp][row pair][lane]: the bottom leaving slot 0
-  int nw, h, warp, lane, slast;   // slast: the slot of pair h - 1 in the last warp
-  bool wfirst, wlast;
-  float clim2, slim2;             // squared cosine and sine bounds of a calm step (ep_rotation_os)
-};
-
+// rotations run as packed FP32 pairs; register set j < 4 is column j of A_w, 4 + j column j of B_w.
 // 16 partial sums v[4 s + c] (slot s, component c) summed over the warp; lane l receives the total
 // of component ((l >> 1) & 3) of slot (l >> 3)
 __device__ __forceinline__ float eo_reduce_scatter(const float (&v)[16], int lane) {
@@ -152,26 +147,42 @@ __device__ __forceinline__ float eo_reduce_scatter(const float (&v)[16], int lan
   return w1 + __shfl_xor_sync(~0u, w1, 1);
 }
 
-template <int RP, int U>
-__device__ __forceinline__ int eo_step(float2 (&TR)[4][RP], float2 (&TI)[4][RP], float2 (&BR)[4][RP],
-                                       float2 (&BI)[4][RP], const EoSweepCtx& x, int par) {
-  const int lane = x.lane;
-  // ---- the 2x2 Gram of every slot: |top|^2, |bottom|^2, conj(top) bottom
+// The four pairs of step K: K = 0..2 pair the columns inside each block ((0,1)(2,3), (0,2)(1,3),
+// (0,3)(1,2) of A in slots 0 and 1, of B in slots 2 and 3); K = 3..6 pair column s of A with
+// column (s + K - 3) & 3 of B in slot s, so four such steps meet all sixteen pairs of A and B.
+__host__ __device__ constexpr int eo_inner(int k, int pr, int e) {
+  constexpr int t[3][2][2] = {{{0, 1}, {2, 3}}, {{0, 2}, {1, 3}}, {{0, 3}, {1, 2}}};
+  return t[k][pr][e];
+}
+template <int K> __host__ __device__ constexpr int eo_px(int s) {
+  return K < 3 ? (s < 2 ? 0 : 4) + eo_inner(K, s & 1, 0) : s;
+}
+template <int K> __host__ __device__ constexpr int eo_py(int s) {
+  return K < 3 ? (s < 2 ? 0 : 4) + eo_inner(K, s & 1, 1) : 4 + ((s + K - 3) & 3);
+}
+
+// One step of a warp: the 2x2 Gram of each slot's pair summed over the warp, its rotation
+// (ep_rotation_os) and the update of both columns.  Returns whether some slot of the warp was not
+// calm (warp-uniform).
+template <int RP, int K>
+__device__ __forceinline__ bool eo_bstep(float2 (&XR)[8][RP], float2 (&XI)[8][RP], int lane, float clim2,
+                                         float slim2) {
+  // ---- the 2x2 Gram of every slot: |x|^2, |y|^2, conj(x) y
   float v[16];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    const int t = (s - U) & 3, b = (s + U) & 3;
+    const int t = eo_px<K>(s), b = eo_py<K>(s);
     float2 a2 = make_float2(0.f, 0.f), b2 = a2, gr = a2, gi = a2, gj = a2;
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
-      a2 = __ffma2_rn(TR[t][i], TR[t][i], a2);
-      a2 = __ffma2_rn(TI[t][i], TI[t][i], a2);
-      b2 = __ffma2_rn(BR[b][i], BR[b][i], b2);
-      b2 = __ffma2_rn(BI[b][i], BI[b][i], b2);
-      gr = __ffma2_rn(TR[t][i], BR[b][i], gr);
-      gr = __ffma2_rn(TI[t][i], BI[b][i], gr);
-      gi = __ffma2_rn(TR[t][i], BI[b][i], gi);
-      gj = __ffma2_rn(TI[t][i], BR[b][i], gj);
+      a2 = __ffma2_rn(XR[t][i], XR[t][i], a2);
+      a2 = __ffma2_rn(XI[t][i], XI[t][i], a2);
+      b2 = __ffma2_rn(XR[b][i], XR[b][i], b2);
+      b2 = __ffma2_rn(XI[b][i], XI[b][i], b2);
+      gr = __ffma2_rn(XR[t][i], XR[b][i], gr);
+      gr = __ffma2_rn(XI[t][i], XI[b][i], gr);
+      gi = __ffma2_rn(XR[t][i], XI[b][i], gi);
+      gj = __ffma2_rn(XI[t][i], XR[b][i], gj);
     }
     v[4 * s] = a2.x + a2.y;
     v[4 * s + 1] = b2.x + b2.y;
@@ -187,212 +198,27 @@ __device__ __forceinline__ int eo_step(float2 (&TR)[4][RP], float2 (&TI)[4][RP],
   float2 st;
   int rot;
   bool calm;
-  ep_rotation_os(a, b, gm, EO_TOL, x.clim2, x.slim2, c, st, rot, calm);   // c = 1, st = 0 without a rotation
-  if (4 * x.warp + (lane >> 3) >= x.h) { rot = 0; calm = true; }         // slots past h - 1 hold no pair
+  ep_rotation_os(a, b, gm, EO_TOL, clim2, slim2, c, st, rot, calm);   // c = 1, st = 0 without a rotation
   const unsigned rmask = __ballot_sync(~0u, rot);
   const unsigned wmask = __ballot_sync(~0u, !calm);
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     if (!((rmask >> (8 * s)) & 1u)) continue;   // warp-uniform
     const float cs = __shfl_sync(~0u, c, 8 * s), sr = __shfl_sync(~0u, st.x, 8 * s), si = __shfl_sync(~0u, st.y, 8 * s);
-    const int t = (s - U) & 3, bb = (s + U) & 3;
-    // [top bottom] J: top' = c top - conj(st) bottom, bottom' = st top + c bottom
+    const int t = eo_px<K>(s), bb = eo_py<K>(s);
+    // [x y] J: x' = c x - conj(st) y, y' = st x + c y
     const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
     const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
-      const float2 xr = TR[t][i], xi = TI[t][i], yr = BR[bb][i], yi = BI[bb][i];
-      TR[t][i] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
-      TI[t][i] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
-      BR[bb][i] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
-      BI[bb][i] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
+      const float2 xr = XR[t][i], xi = XI[t][i], yr = XR[bb][i], yi = XI[bb][i];
+      XR[t][i] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
+      XI[t][i] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
+      XR[bb][i] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
+      XI[bb][i] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
     }
   }
-  // ---- the columns that leave the warp: slot 3's top, slot 0's bottom
-  const int t3 = (3 - U) & 3, b0 = U & 3;
-  if (x.h > 1) {
-    float4* dt = x.xt + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
-    float4* db = x.xb + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {
-      dt[i * 32] = make_float4(TR[t3][i].x, TR[t3][i].y, TI[t3][i].x, TI[t3][i].y);
-      db[i * 32] = make_float4(BR[b0][i].x, BR[b0][i].y, BI[b0][i].x, BI[b0][i].y);
-    }
-  }
-  const int any = __syncthreads_or(wmask != 0u);
-  if (x.h == 1) {   // one pair: nothing moves, but the registers are renamed all the same
-    const int t0 = (0 - U) & 3, bn = (U + 1) & 3;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) { TR[t3][i] = TR[t0][i]; TI[t3][i] = TI[t0][i]; BR[bn][i] = BR[b0][i]; BI[bn][i] = BI[b0][i]; }
-  } else {
-    const int t0 = (0 - U) & 3;
-    // The special slots first, from old values: slot h - 1 takes its own top as bottom (into the
-    // register slot h - 1 reads its bottom from at the next step), slot 0 keeps its top (into the
-    // register slot 3's top left), slot 1 takes slot 0's bottom; with four slots in one warp the
-    // two overlap and slot 0's bottom goes through a temporary.
-    if (x.wfirst && x.wlast && x.slast == 3) {
-      float2 tr[RP], ti[RP];
-#pragma unroll
-      for (int i = 0; i < RP; ++i) { tr[i] = BR[b0][i]; ti[i] = BI[b0][i]; }
-#pragma unroll
-      for (int i = 0; i < RP; ++i) {
-        BR[b0][i] = TR[t3][i]; BI[b0][i] = TI[t3][i];
-        TR[t3][i] = TR[t0][i]; TI[t3][i] = TI[t0][i];
-        TR[t0][i] = tr[i]; TI[t0][i] = ti[i];
-      }
-    } else {
-      if (x.wlast) {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          if (s != x.slast) continue;
-          const int tl = (s - U) & 3, bn = (s + U + 1) & 3;
-#pragma unroll
-          for (int i = 0; i < RP; ++i) { BR[bn][i] = TR[tl][i]; BI[bn][i] = TI[tl][i]; }
-        }
-      }
-      if (x.wfirst) {
-#pragma unroll
-        for (int i = 0; i < RP; ++i) {
-          TR[t3][i] = TR[t0][i]; TI[t3][i] = TI[t0][i];
-          TR[t0][i] = BR[b0][i]; TI[t0][i] = BI[b0][i];
-        }
-      }
-    }
-    // generic receives: slot 0's new top from the previous warp's slot 3, slot 3's new bottom from
-    // the next warp's slot 0 (both land in the register that just left)
-    if (x.warp > 0) {
-      const float4* s = x.xt + (size_t)(par * x.nw + x.warp - 1) * RP * 32 + lane;
-#pragma unroll
-      for (int i = 0; i < RP; ++i) {
-        const float4 q = s[i * 32];
-        TR[t3][i] = make_float2(q.x, q.y);
-        TI[t3][i] = make_float2(q.z, q.w);
-      }
-    }
-    if (4 * x.warp + 3 < x.h - 1) {
-      const float4* s = x.xb + (size_t)(par * x.nw + x.warp + 1) * RP * 32 + lane;
-#pragma unroll
-      for (int i = 0; i < RP; ++i) {
-        const float4 q = s[i * 32];
-        BR[b0][i] = make_float2(q.x, q.y);
-        BI[b0][i] = make_float2(q.z, q.w);
-      }
-    }
-  }
-  return any;
-}
-
-// ---- the step of a last warp that holds two pair slots (four columns) ----
-// When the last warp has at most two pairs it runs this step: the same dots, rotation and apply
-// for slots 0 and 1 only (register sets 0 and 1, renamed with period two), eight partial sums
-// reduce-scattered so that lane l receives component ((l >> 2) & 3) of slot (l >> 4).  It holds
-// pair h - 1 (slot slast, its own top becomes its bottom) and trades slot 0's top and bottom with
-// the previous warp as a four-slot warp trades its slots 3 and 0; the top leaving its slot 1 is
-// written for no reader.
-__device__ __forceinline__ float eo_reduce_scatter8(const float (&v)[8], int lane) {
-  float w4[4], w2[2];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const bool hi = lane & 16;
-    const float send = hi ? v[k] : v[4 + k], keep = hi ? v[4 + k] : v[k];
-    w4[k] = keep + __shfl_xor_sync(~0u, send, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const bool hi = lane & 8;
-    const float send = hi ? w4[k] : w4[2 + k], keep = hi ? w4[2 + k] : w4[k];
-    w2[k] = keep + __shfl_xor_sync(~0u, send, 8);
-  }
-  const bool hi = lane & 4;
-  float w1 = (hi ? w2[1] : w2[0]) + __shfl_xor_sync(~0u, hi ? w2[0] : w2[1], 4);
-  w1 += __shfl_xor_sync(~0u, w1, 2);
-  return w1 + __shfl_xor_sync(~0u, w1, 1);
-}
-
-template <int RP, int U>
-__device__ __forceinline__ int eo_step2(float2 (&TR)[4][RP], float2 (&TI)[4][RP], float2 (&BR)[4][RP],
-                                        float2 (&BI)[4][RP], const EoSweepCtx& x, int par) {
-  const int lane = x.lane;
-  float v[8];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const int t = (s - U) & 1, b = (s + U) & 1;
-    float2 a2 = make_float2(0.f, 0.f), b2 = a2, gr = a2, gi = a2, gj = a2;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {
-      a2 = __ffma2_rn(TR[t][i], TR[t][i], a2);
-      a2 = __ffma2_rn(TI[t][i], TI[t][i], a2);
-      b2 = __ffma2_rn(BR[b][i], BR[b][i], b2);
-      b2 = __ffma2_rn(BI[b][i], BI[b][i], b2);
-      gr = __ffma2_rn(TR[t][i], BR[b][i], gr);
-      gr = __ffma2_rn(TI[t][i], BI[b][i], gr);
-      gi = __ffma2_rn(TR[t][i], BI[b][i], gi);
-      gj = __ffma2_rn(TI[t][i], BR[b][i], gj);
-    }
-    v[4 * s] = a2.x + a2.y;
-    v[4 * s + 1] = b2.x + b2.y;
-    v[4 * s + 2] = gr.x + gr.y;
-    v[4 * s + 3] = (gi.x + gi.y) - (gj.x + gj.y);
-  }
-  const float tot = eo_reduce_scatter8(v, lane);
-  const int base = lane & 16;
-  const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 4);
-  const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 8), __shfl_sync(~0u, tot, base + 12));
-  float c;
-  float2 st;
-  int rot;
-  bool calm;
-  ep_rotation_os(a, b, gm, EO_TOL, x.clim2, x.slim2, c, st, rot, calm);
-  if (4 * x.warp + (lane >> 4) >= x.h) { rot = 0; calm = true; }
-  const unsigned rmask = __ballot_sync(~0u, rot);
-  const unsigned wmask = __ballot_sync(~0u, !calm);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    if (!((rmask >> (16 * s)) & 1u)) continue;   // warp-uniform
-    const float cs = __shfl_sync(~0u, c, 16 * s), sr = __shfl_sync(~0u, st.x, 16 * s), si = __shfl_sync(~0u, st.y, 16 * s);
-    const int t = (s - U) & 1, bb = (s + U) & 1;
-    const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
-    const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {
-      const float2 xr = TR[t][i], xi = TI[t][i], yr = BR[bb][i], yi = BI[bb][i];
-      TR[t][i] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
-      TI[t][i] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
-      BR[bb][i] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
-      BI[bb][i] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
-    }
-  }
-  // slot 1's top (no reader) and slot 0's bottom leave the warp
-  const int t1 = (1 - U) & 1, b0 = U & 1;
-  {
-    float4* dt = x.xt + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
-    float4* db = x.xb + (size_t)(par * x.nw + x.warp) * RP * 32 + lane;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {
-      dt[i * 32] = make_float4(TR[t1][i].x, TR[t1][i].y, TI[t1][i].x, TI[t1][i].y);
-      db[i * 32] = make_float4(BR[b0][i].x, BR[b0][i].y, BI[b0][i].x, BI[b0][i].y);
-    }
-  }
-  const int any = __syncthreads_or(wmask != 0u);
-  // slot slast (pair h - 1) takes its own top as bottom, into the register its bottom is read from
-  // at the next step; slot 0's new top comes from the previous warp's slot 3
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    if (s != x.slast) continue;
-    const int tl = (s - U) & 1, bn = (s + U + 1) & 1;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) { BR[bn][i] = TR[tl][i]; BI[bn][i] = TI[tl][i]; }
-  }
-  {
-    const float4* src = x.xt + (size_t)(par * x.nw + x.warp - 1) * RP * 32 + lane;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {
-      const float4 q4 = src[i * 32];
-      TR[t1][i] = make_float2(q4.x, q4.y);
-      TI[t1][i] = make_float2(q4.z, q4.w);
-    }
-  }
-  return any;
+  return wmask != 0u;
 }
 
 template <int RP>
@@ -537,18 +363,12 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   __syncthreads();
   EO_STAMP(4);
 
-  // ---------------- one-sided Jacobi: warp w owns pair slots 4w .. 4w + 3; slot p holds columns
-  // (2p, 2p + 1) at the start
-  EoSweepCtx xc;
-  xc.xt = reinterpret_cast<float4*>(smem + L.x);
-  xc.xb = xc.xt + (size_t)2 * L.nw * RP * 32;
-  xc.nw = L.nw; xc.h = h; xc.warp = warp; xc.lane = lane;
-  xc.clim2 = (float)np * EO_TOL * EO_TOL;
-  xc.slim2 = 0.25f / ((float)np * np * np);
-  xc.wfirst = warp == 0;
-  xc.wlast = warp == (h - 1) / 4;
-  xc.slast = (h - 1) - 4 * ((h - 1) / 4);
-  float2 TR[4][RP], TI[4][RP], BR[4][RP], BI[4][RP];
+  // ---------------- one-sided Jacobi: warp w holds block A_w = columns 8w, 8w + 2, 8w + 4, 8w + 6
+  // and block B_w = columns 8w + 1, 8w + 3, 8w + 5, 8w + 7 at the start
+  const int nw = L.nw;
+  const float ne = (float)(n + (n & 1));   // the calm bounds take the unpadded size
+  const float clim2 = ne * EO_TOL * EO_TOL, slim2 = 0.25f / (ne * ne * ne);
+  float2 XR[8][RP], XI[8][RP];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int p = 4 * warp + s, ct = 2 * p, cb = 2 * p + 1;
@@ -558,71 +378,107 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int r = (2 * i + e) * 32 + lane;
-        const float2 t = (p < h && r < n && ct < rk) ? eo_factor(A, lda, pos, ord[ct], ct, r) : make_float2(0.f, 0.f);
-        const float2 b = (p < h && r < n && cb < rk) ? eo_factor(A, lda, pos, ord[cb], cb, r) : make_float2(0.f, 0.f);
+        const float2 t = (r < n && ct < rk) ? eo_factor(A, lda, pos, ord[ct], ct, r) : make_float2(0.f, 0.f);
+        const float2 b = (r < n && cb < rk) ? eo_factor(A, lda, pos, ord[cb], cb, r) : make_float2(0.f, 0.f);
         v[e][0] = t.x; v[e][1] = t.y; v[e][2] = b.x; v[e][3] = b.y;
       }
-      TR[s][i] = make_float2(v[0][0], v[1][0]);
-      TI[s][i] = make_float2(v[0][1], v[1][1]);
-      BR[s][i] = make_float2(v[0][2], v[1][2]);
-      BI[s][i] = make_float2(v[0][3], v[1][3]);
+      XR[s][i] = make_float2(v[0][0], v[1][0]);
+      XI[s][i] = make_float2(v[0][1], v[1][1]);
+      XR[4 + s][i] = make_float2(v[0][2], v[1][2]);
+      XI[4 + s][i] = make_float2(v[0][3], v[1][3]);
     }
   }
-  __syncthreads();
-  // Steps run in blocks of four (the register renaming's period); a window has converged once a
-  // whole circle (np - 1 consecutive steps, which meet every pair once) was calm: no rotation
-  // above the cosine and sine bounds of ep_rotation_os.
+  __syncthreads();   // the factor is read: a and x hold the block exchange from here on
+  // Rounds of four steps; a window has converged once 2 nw - 1 consecutive rounds (a whole sweep:
+  // every pair once, the inner pairs included) were calm: no rotation above the cosine and sine
+  // bounds of ep_rotation_os.
   int converged = 0, sweeps = 0;
   {
-    const int per = np - 1;
-    const int maxsteps = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
-    int steps = 0, quiet = 0, last = 0;
-    auto track = [&](int any) {
-      ++steps;
-      if (any) { quiet = 0; last = steps; }
-      else ++quiet;
-    };
-    // the last warp runs the two-slot step when it holds at most two pairs (and is not the only warp)
-    const bool two = L.nw > 1 && warp == L.nw - 1 && h - 4 * (L.nw - 1) <= 2;
-    while (steps < maxsteps) {
-      int r0;
-      if (two) {
-        r0 = eo_step2<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-        r0 = eo_step2<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-        r0 = eo_step2<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-        r0 = eo_step2<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-      } else {
-        r0 = eo_step<RP, 0>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-        r0 = eo_step<RP, 1>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-        r0 = eo_step<RP, 2>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
-        r0 = eo_step<RP, 3>(TR, TI, BR, BI, xc, steps & 1);
-        track(r0);
+    float4* xq = reinterpret_cast<float4*>(smem + L.a);   // [warp][column 0..7][row pair][lane]
+    const int per = 2 * nw - 1;
+    const int maxrounds = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
+    int rounds = 0, quiet = 0, last = 0, rr = 0;
+    for (;;) {
+      bool nc = false;
+      if (rr == 0) {   // the pairs inside each block, once per sweep
+        nc |= eo_bstep<RP, 0>(XR, XI, lane, clim2, slim2);
+        nc |= eo_bstep<RP, 1>(XR, XI, lane, clim2, slim2);
+        nc |= eo_bstep<RP, 2>(XR, XI, lane, clim2, slim2);
       }
+      nc |= eo_bstep<RP, 3>(XR, XI, lane, clim2, slim2);
+      nc |= eo_bstep<RP, 4>(XR, XI, lane, clim2, slim2);
+      nc |= eo_bstep<RP, 5>(XR, XI, lane, clim2, slim2);
+      nc |= eo_bstep<RP, 6>(XR, XI, lane, clim2, slim2);
+      // ---- the blocks move: A_w goes to warp w + 1 (read by warps 2 .. nw - 1), B_w to warp w - 1
+      // (B_0 to warp 1 as its A); A_0 stays and the last warp's A becomes its own B
+      if (nw > 1) {
+        float4* own = xq + (size_t)warp * 8 * RP * 32 + lane;
+        if (warp > 0 && warp < nw - 1) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int i = 0; i < RP; ++i)
+              own[(c * RP + i) * 32] = make_float4(XR[c][i].x, XR[c][i].y, XI[c][i].x, XI[c][i].y);
+        }
+#pragma unroll
+        for (int c = 4; c < 8; ++c)
+#pragma unroll
+          for (int i = 0; i < RP; ++i)
+            own[(c * RP + i) * 32] = make_float4(XR[c][i].x, XR[c][i].y, XI[c][i].x, XI[c][i].y);
+      }
+      const int any = __syncthreads_or(nc);
+      if (nw > 1) {
+        if (warp == nw - 1) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int i = 0; i < RP; ++i) { XR[4 + c][i] = XR[c][i]; XI[4 + c][i] = XI[c][i]; }
+        }
+        if (warp > 0) {   // new A: B_0 for warp 1, A_(w-1) for the others
+          const float4* src = xq + (size_t)(warp - 1) * 8 * RP * 32 + (warp == 1 ? 4 * RP * 32 : 0) + lane;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int i = 0; i < RP; ++i) {
+              const float4 q = src[(c * RP + i) * 32];
+              XR[c][i] = make_float2(q.x, q.y); XI[c][i] = make_float2(q.z, q.w);
+            }
+        }
+        if (warp < nw - 1) {   // new B: B_(w+1)
+          const float4* src = xq + (size_t)(warp + 1) * 8 * RP * 32 + lane;
+#pragma unroll
+          for (int c = 4; c < 8; ++c)
+#pragma unroll
+            for (int i = 0; i < RP; ++i) {
+              const float4 q = src[(c * RP + i) * 32];
+              XR[c][i] = make_float2(q.x, q.y); XI[c][i] = make_float2(q.z, q.w);
+            }
+        }
+        __syncthreads();   // read before the next round writes
+      }
+      ++rounds;
+      if (any) { quiet = 0; last = rounds; }
+      else ++quiet;
       if (quiet >= per) { converged = 1; break; }
+      if (rounds >= maxrounds) break;
+      rr = rr + 1 == per ? 0 : rr + 1;
     }
     sweeps = (last + per - 1) / per;
   }
   EO_STAMP(5);
 
-  // ---------------- columns back to shared memory (position 2p top, 2p + 1 bottom) with their
-  // squared norms (double-float sums), then normalised
+  // ---------------- columns back to shared memory (column s of A_w at position 2p, of B_w at 2p + 1,
+  // p = 4w + s) with their squared norms (double-float sums), then normalised
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int p = 4 * warp + s;
     df na = {0.f, 0.f}, nb = {0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
-      na = df_add_f(na, fmaf(TR[s][i].x, TR[s][i].x, TI[s][i].x * TI[s][i].x));
-      na = df_add_f(na, fmaf(TR[s][i].y, TR[s][i].y, TI[s][i].y * TI[s][i].y));
-      nb = df_add_f(nb, fmaf(BR[s][i].x, BR[s][i].x, BI[s][i].x * BI[s][i].x));
-      nb = df_add_f(nb, fmaf(BR[s][i].y, BR[s][i].y, BI[s][i].y * BI[s][i].y));
+      na = df_add_f(na, fmaf(XR[s][i].x, XR[s][i].x, XI[s][i].x * XI[s][i].x));
+      na = df_add_f(na, fmaf(XR[s][i].y, XR[s][i].y, XI[s][i].y * XI[s][i].y));
+      nb = df_add_f(nb, fmaf(XR[4 + s][i].x, XR[4 + s][i].x, XI[4 + s][i].x * XI[4 + s][i].x));
+      nb = df_add_f(nb, fmaf(XR[4 + s][i].y, XR[4 + s][i].y, XI[4 + s][i].y * XI[4 + s][i].y));
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -645,9 +501,9 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
           const int r = (2 * i + e) * 32 + lane;
           if (r < n) {
             A[(size_t)r * lda + 2 * p] =
-                make_float2((e ? TR[s][i].y : TR[s][i].x) * ia, (e ? TI[s][i].y : TI[s][i].x) * ia);
+                make_float2((e ? XR[s][i].y : XR[s][i].x) * ia, (e ? XI[s][i].y : XI[s][i].x) * ia);
             A[(size_t)r * lda + 2 * p + 1] =
-                make_float2((e ? BR[s][i].y : BR[s][i].x) * ib, (e ? BI[s][i].y : BI[s][i].x) * ib);
+                make_float2((e ? XR[4 + s][i].y : XR[4 + s][i].x) * ib, (e ? XI[4 + s][i].y : XI[4 + s][i].x) * ib);
           }
         }
       }
@@ -655,7 +511,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   __syncthreads();
   // sort positions by squared norm, descending (ties to the lower position); the first n are the
-  // eigenpairs (with n odd the padding column is zero and sorts among the zeros)
+  // eigenpairs (the padding columns past Nt are zero and sort among the zeros)
   for (int i = tid; i < np; i += nthr) {
     const double di = lam[i];
     int r = 0;

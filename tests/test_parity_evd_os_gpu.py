@@ -80,18 +80,20 @@ def test_os_small_all_rules(mode, beta, extra):
 
 
 @pytest.mark.parametrize("shape,grid,mode", [
-    ((33, 40, 70), (2, 3), "LCF_T_FIXED"),       # odd Nt: a zero padding column
+    ((33, 40, 70), (2, 3), "LCF_T_FIXED"),       # odd Nt: five warps, seven zero columns
     ((16, 17, 23), (1, 1), "LCF_T_MEDIAN"),
     ((112, 24, 20), (2, 2), "LCF_T_CURVATURE"),
-    ((2, 8, 8), (1, 1), "LCF_T_FIXED"),          # one pair slot, one step per sweep
-    ((4, 8, 8), (1, 1), "LCF_T_FIXED"),          # two slots
+    ((2, 8, 8), (1, 1), "LCF_T_FIXED"),          # one warp, six zero columns, no block exchange
+    ((4, 8, 8), (1, 1), "LCF_T_FIXED"),          # one warp, two columns per block
     ((5, 12, 9), (2, 2), "LCF_T_CURVATURE"),     # head block = whole matrix (m = Nt)
-    ((17, 30, 22), (2, 2), "LCF_T_SLOPE"),       # slot h-1 = 8: the first slot of the third warp
-    ((128, 40, 36), (2, 2), "LCF_T_CURVATURE"),   # largest Nt: 64 slots, 16 rows per lane
+    ((17, 30, 22), (2, 2), "LCF_T_SLOPE"),       # three warps, the last holding one column
+    ((128, 40, 36), (2, 2), "LCF_T_CURVATURE"),   # largest Nt: 16 warps, 32 blocks, no padding
     ((127, 33, 29), (2, 3), "LCF_T_MEDIAN"),
+    ((9, 14, 12), (1, 1), "LCF_T_CURVATURE"),    # two warps: the smallest block exchange
+    ((24, 16, 14), (1, 1), "LCF_T_MEDIAN"),      # three warps, no padding
     ((64, 28, 26), (2, 2), "LCF_T_CURVATURE"),   # 64 rows: the last one-row-pair layout
-    ((65, 28, 26), (2, 2), "LCF_T_SLOPE"),       # 65: two row pairs, a zero padding column
-    ((3, 10, 9), (1, 2), "LCF_T_FIXED"),         # two slots, one of them half padding
+    ((65, 28, 26), (2, 2), "LCF_T_SLOPE"),       # 65: two row pairs, nine warps, seven zero columns
+    ((3, 10, 9), (1, 2), "LCF_T_FIXED"),         # one warp, five zero columns
 ])
 def test_os_edge_shapes(shape, grid, mode):
     lib = L()
@@ -162,7 +164,7 @@ def test_os_matches_pair_evd():
     band = la >= 1e-6 * la[:, :1]
     rel = np.max(np.abs(la - lb)[band] / la[band])
     print("eigenvalue rel diff", rel, "pd rel", np.linalg.norm(pa - pb) / np.linalg.norm(pa))
-    assert rel <= 2e-5
+    assert rel <= 4e-5   # each path's own error against the oracle: <= 2.5e-5 (one-sided), 4.2e-6 (two-sided)
     assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 2e-4
 
 
@@ -231,7 +233,7 @@ def test_os_long_matches_distributed_evd():
     band = la >= 1e-6 * la[:, :1]
     rel = np.max(np.abs(la - lb)[band] / la[band])
     print("eigenvalue rel diff", rel, "pd rel", np.linalg.norm(pa - pb) / np.linalg.norm(pa))
-    assert rel <= 2e-5
+    assert rel <= 4e-5   # each path's own error against the oracle: <= 2.5e-5 (one-sided), 4.2e-6 (two-sided)
     assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 2e-4
 
 
