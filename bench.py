@@ -34,10 +34,10 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    # the one-sided EVD stage: evd_prep_kernel 10.35 MB + evd_os_kernel 3.99 MB
-    ("evd", "os"): {"bytes": 14.34e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+    # the one-sided EVD stage: evd_prep_kernel 10.35 MB + evd_os_kernel 3.89 MB
+    ("evd", "os"): {"bytes": 14.24e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "21de8ee0fdd243854a50897edd0e2841d56b8f67dfa0f45ffc4afa8783053f13",
+                                "2aeeab6efc2ae653f8e0238e0a977aa21661b6323e6633d28b6f5161496ef5a8",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "012f98a6ccfab4ab00945437406f1d375bc5f7e32e342f35d7a751466c9ea849",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":

@@ -147,6 +147,12 @@ __device__ __forceinline__ float eo_reduce_scatter(const float (&v)[16], int lan
   return w1 + __shfl_xor_sync(~0u, w1, 1);
 }
 
+// The position (factor column at the start, eigenvector column at the end) of column s of block j
+// (A_w: 0, B_w: 1) of warp w: blocks in circle order, shifted so that A_0 holds the last four
+__host__ __device__ inline int eo_block_pos(int nw, int w, int j, int s) {
+  return 4 * ((2 * w + j + 2 * nw - 1) % (2 * nw)) + s;
+}
+
 // The four pairs of step K: K = 0..2 pair the columns inside each block ((0,1)(2,3), (0,2)(1,3),
 // (0,3)(1,2) of A in slots 0 and 1, of B in slots 2 and 3); K = 3..6 pair column s of A with
 // column (s + K - 3) & 3 of B in slot s, so four such steps meet all sixteen pairs of A and B.
@@ -232,7 +238,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   const int k = blockIdx.x, n = g.nt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
   const EoLayout L = eo_layout(n);
-  const int np = L.np, h = L.h, lda = L.lda, m = L.m;
+  const int np = L.np, lda = L.lda, m = L.m;
   float2* A = reinterpret_cast<float2*>(smem + L.a);
   float2* colj = reinterpret_cast<float2*>(smem + L.colj);
   double* lam = reinterpret_cast<double*>(smem + L.lam);
@@ -363,15 +369,19 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   __syncthreads();
   EO_STAMP(4);
 
-  // ---------------- one-sided Jacobi: warp w holds block A_w = columns 8w, 8w + 2, 8w + 4, 8w + 6
-  // and block B_w = columns 8w + 1, 8w + 3, 8w + 5, 8w + 7 at the start
+  // ---------------- one-sided Jacobi: block j of warp w (A_w: j = 0, B_w: j = 1) starts with
+  // columns 4 q .. 4 q + 3, q = (2 w + j - 1) mod 2 nw (eo_block_pos): the last four positions form
+  // A_0, which the circle never moves, so with four or more padding columns A_0 is zero and warp 0
+  // has no cross pair to rotate (it skips those steps: the other warps then sit three to a
+  // scheduler at Nt = 100, where thirteen would put four on one)
   const int nw = L.nw;
+  const bool idle0 = warp == 0 && L.np - n >= 4;
   const float ne = (float)(n + (n & 1));   // the calm bounds take the unpadded size
   const float clim2 = ne * EO_TOL * EO_TOL, slim2 = 0.25f / (ne * ne * ne);
   float2 XR[8][RP], XI[8][RP];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    const int p = 4 * warp + s, ct = 2 * p, cb = 2 * p + 1;
+    const int ct = eo_block_pos(nw, warp, 0, s), cb = eo_block_pos(nw, warp, 1, s);
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
       float v[2][4];
@@ -405,10 +415,12 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
         nc |= eo_bstep<RP, 1>(XR, XI, lane, clim2, slim2);
         nc |= eo_bstep<RP, 2>(XR, XI, lane, clim2, slim2);
       }
-      nc |= eo_bstep<RP, 3>(XR, XI, lane, clim2, slim2);
-      nc |= eo_bstep<RP, 4>(XR, XI, lane, clim2, slim2);
-      nc |= eo_bstep<RP, 5>(XR, XI, lane, clim2, slim2);
-      nc |= eo_bstep<RP, 6>(XR, XI, lane, clim2, slim2);
+      if (!idle0) {
+        nc |= eo_bstep<RP, 3>(XR, XI, lane, clim2, slim2);
+        nc |= eo_bstep<RP, 4>(XR, XI, lane, clim2, slim2);
+        nc |= eo_bstep<RP, 5>(XR, XI, lane, clim2, slim2);
+        nc |= eo_bstep<RP, 6>(XR, XI, lane, clim2, slim2);
+      }
       // ---- the blocks move: A_w goes to warp w + 1 (read by warps 2 .. nw - 1), B_w to warp w - 1
       // (B_0 to warp 1 as its A); A_0 stays and the last warp's A becomes its own B
       if (nw > 1) {
@@ -467,11 +479,11 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   }
   EO_STAMP(5);
 
-  // ---------------- columns back to shared memory (column s of A_w at position 2p, of B_w at 2p + 1,
-  // p = 4w + s) with their squared norms (double-float sums), then normalised
+  // ---------------- columns back to shared memory (column s of block j of warp w at position
+  // eo_block_pos(nw, w, j, s)) with their squared norms (double-float sums), then normalised
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    const int p = 4 * warp + s;
+    const int pa = eo_block_pos(nw, warp, 0, s), pb = eo_block_pos(nw, warp, 1, s);
     df na = {0.f, 0.f}, nb = {0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
@@ -486,13 +498,13 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
       t.hi = __shfl_xor_sync(~0u, na.hi, o); t.lo = __shfl_xor_sync(~0u, na.lo, o); na = df_add(na, t);
       t.hi = __shfl_xor_sync(~0u, nb.hi, o); t.lo = __shfl_xor_sync(~0u, nb.lo, o); nb = df_add(nb, t);
     }
-    if (p < h) {
+    {
       // squared norms below 2^-100 (the matrix is scaled to a largest diagonal in [1/2, 1)) count as
       // vanished columns
       double la = (double)na.hi + (double)na.lo, lb = (double)nb.hi + (double)nb.lo;
       la = la > 7.888609052210118e-31 ? la : 0.0;
       lb = lb > 7.888609052210118e-31 ? lb : 0.0;
-      if (lane == 0) { lam[2 * p] = la; lam[2 * p + 1] = lb; }
+      if (lane == 0) { lam[pa] = la; lam[pb] = lb; }
       const float ia = la > 0.0 ? ep_rsqrt((float)la) : 0.f, ib = lb > 0.0 ? ep_rsqrt((float)lb) : 0.f;
 #pragma unroll
       for (int i = 0; i < RP; ++i) {
@@ -500,9 +512,9 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
         for (int e = 0; e < 2; ++e) {
           const int r = (2 * i + e) * 32 + lane;
           if (r < n) {
-            A[(size_t)r * lda + 2 * p] =
+            A[(size_t)r * lda + pa] =
                 make_float2((e ? XR[s][i].y : XR[s][i].x) * ia, (e ? XI[s][i].y : XI[s][i].x) * ia);
-            A[(size_t)r * lda + 2 * p + 1] =
+            A[(size_t)r * lda + pb] =
                 make_float2((e ? XR[4 + s][i].y : XR[4 + s][i].x) * ib, (e ? XI[4 + s][i].y : XI[4 + s][i].x) * ib);
           }
         }

@@ -164,7 +164,7 @@ def test_os_matches_pair_evd():
     band = la >= 1e-6 * la[:, :1]
     rel = np.max(np.abs(la - lb)[band] / la[band])
     print("eigenvalue rel diff", rel, "pd rel", np.linalg.norm(pa - pb) / np.linalg.norm(pa))
-    assert rel <= 4e-5   # each path's own error against the oracle: <= 2.5e-5 (one-sided), 4.2e-6 (two-sided)
+    assert rel <= 2e-5
     assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 2e-4
 
 
@@ -233,7 +233,7 @@ def test_os_long_matches_distributed_evd():
     band = la >= 1e-6 * la[:, :1]
     rel = np.max(np.abs(la - lb)[band] / la[band])
     print("eigenvalue rel diff", rel, "pd rel", np.linalg.norm(pa - pb) / np.linalg.norm(pa))
-    assert rel <= 4e-5   # each path's own error against the oracle: <= 2.5e-5 (one-sided), 4.2e-6 (two-sided)
+    assert rel <= 2e-5
     assert np.linalg.norm(pa - pb) / np.linalg.norm(pa) <= 2e-4
 
 
