@@ -16,17 +16,17 @@
 //                    order), the permutation and the numerical rank to global memory.
 //  evd_osc_kernel    the sweeps and everything after, on a cluster of four CTAs.  CTA
 //                    c holds rows [c R, (c + 1) R) (R = ceil(Nt / 4)) of every column in
-//                    registers; warp w owns pair slots 8w .. 8w + 7 of the circle
-//                    ordering (16 columns; a last warp with at most four pairs holds
-//                    four slots and runs a four-slot step), lane l rows l and l + 32 of
-//                    the CTA's share as one packed pair.  A step sums each slot's
-//                    partial 2x2 Gram over the warp (reduce-scatter), sends that
-//                    partial to the other three CTAs (st.async into their shared memory,
-//                    completing the bytes of their step-parity mbarrier), adds the four
-//                    partials in rank order (so every CTA forms the same rotations),
-//                    rotates, and moves columns: inside a warp by renaming registers
-//                    (period eight), between warps through shared memory.  Every wait
-//                    is bounded (2 s).
+//                    registers, lane l rows l and l + 32 of the CTA's share as one
+//                    packed pair; the columns (zero-padded to 16 per warp) form blocks of
+//                    eight, two per warp, in a block ordering: a round is eight steps in
+//                    which each warp meets all pairs of its two blocks, then the blocks
+//                    move one place on the circle through shared memory.  A step sums
+//                    each slot's partial 2x2 Gram over the warp (reduce-scatter), sends
+//                    that partial to the same warp of the other three CTAs (st.async into
+//                    their shared memory, completing the bytes of that warp's
+//                    step-parity mbarrier), adds the four partials in rank order (so
+//                    every CTA forms the same rotations) and rotates.  Every wait is
+//                    bounded (2 s).
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -40,7 +40,6 @@ namespace lcf {
 constexpr int EC_THREADS = 1024;               // Cholesky kernel
 constexpr int EC_PANEL = 8;
 constexpr int EQ_C = 4;                        // CTAs per window of the sweeps
-constexpr int EQ_S = 8;                        // pair slots per warp
 static_assert((EQ_C & (EQ_C - 1)) == 0, "cluster ranks wrap by masking");
 constexpr float EQ_TOL = 2.0e-6f;              // relative orthogonality test
 constexpr int EQ_SUBSPACE_ITERS = 6;
@@ -159,6 +158,7 @@ struct EqArgs {
 };
 
 __host__ __device__ inline size_t eq_align(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t eq_xq_bytes(int nw) { return (size_t)nw * 16 * 32 * 16; }
 
 struct EqLayout {
   int np, h, nw, R, lda, m;
@@ -166,28 +166,25 @@ struct EqLayout {
 };
 // u: this CTA's rows of the columns (then of U, then of V); x: the sweeps' exchange buffers, later
 // the partial products Vh^H U of every CTA
-// whether the last of several warps holds at most four of the ceil(Nt / 2) pairs
-__host__ __device__ inline bool eq_four(int n) {
-  const int h = (n + 1) / 2, nw = (h + EQ_S - 1) / EQ_S;
-  return nw > 1 && h - EQ_S * (nw - 1) <= 4;
-}
 __host__ __device__ inline EqLayout eq_layout(int n) {
   EqLayout L;
-  // the pair slots are padded (zero columns, which never rotate) so that pair h - 1 is the last
-  // slot of the last warp: slot 7, or slot 3 when that warp holds at most four pairs and runs the
-  // four-slot step
-  L.nw = ((n + 1) / 2 + EQ_S - 1) / EQ_S;
-  L.h = EQ_S * L.nw - (eq_four(n) ? 4 : 0);
-  L.np = 2 * L.h;
+  // two blocks of eight columns per warp; zero columns past Nt
+  L.nw = (n + 15) / 16;
+  L.np = 16 * L.nw;
+  L.h = L.np / 2;
   L.R = (n + EQ_C - 1) / EQ_C;
   L.lda = L.np + 1;
   L.m = n < kEvdHead ? n : kEvdHead;
   size_t o = 0;
   L.u = o;     o = eq_align(o + (size_t)L.R * L.lda * 8);
   {
-    const size_t sweep = (size_t)2 * 2 * L.nw * 32 * 16 + (size_t)2 * EQ_C * L.nw * 32 * 4;
+    // the sweeps' buffers overlay u and x from u's start: the block exchange [warp][column 0..15]
+    // [lane] (float4), then the partial sums [parity][source rank][warp][lane] (float)
+    const size_t sweep = eq_xq_bytes(L.nw) + (size_t)2 * EQ_C * L.nw * 32 * 4;
     const size_t post = (size_t)EQ_C * L.m * L.np * 8;
-    L.x = o;   o = eq_align(o + (sweep > post ? sweep : post));
+    size_t need = sweep > o ? sweep - o : 0;
+    need = need > post ? need : post;
+    L.x = o;   o = eq_align(o + need);
   }
   L.lamp = o;  o = eq_align(o + (size_t)EQ_C * L.np * 8);
   L.lam = o;   o = eq_align(o + (size_t)L.np * 8);
@@ -205,7 +202,7 @@ __host__ __device__ inline EqLayout eq_layout(int n) {
   L.vh = o;    o = eq_align(o + (size_t)L.m * n * 8);
   L.tm = o;    o = eq_align(o + (size_t)L.m * L.m * 8);
   L.y = o;     o = eq_align(o + (size_t)L.m * L.np * 8);
-  L.bar = o;   o = eq_align(o + 2 * 8);
+  L.bar = o;   o = eq_align(o + (size_t)2 * L.nw * 8);   // one mbarrier per step parity and warp
   L.end = o;
   return L;
 }
@@ -215,20 +212,15 @@ size_t evd_osc_smem_bytes(int nt) { return eq_layout(nt).end; }
 // evd_osc_kernel: the sweeps on a cluster of EQ_C CTAs
 struct EqCtx {
   // As few registers as the sweep loop can live with (it keeps every column in registers and
-  // runs at the 128-register bound): 32-bit shared addresses, the rest derived.
-  uint32_t xt_s;         // float4 [parity][warp][lane]: the top leaving slot 7; after it
-                         // float4 [parity][warp][lane]: the bottom leaving slot 0 (xb), then
-                         // float [parity][source rank][warp][lane]: the other CTAs' partial sums (recv)
-  uint32_t bdelta;       // this CTA's mbarriers (one per step parity) less its recv
+  // runs near the 128-register bound): 32-bit shared addresses, the rest derived.
+  uint32_t recv_s;       // float [parity][source rank][warp][lane]: the other CTAs' partial sums
+  uint32_t bar_s;        // this CTA's mbarriers [parity][warp]
   int nw, warp, lane, rank;
-  bool wfirst, wlast;
   float clim2, slim2;    // squared cosine and sine bounds of a calm step (ep_rotation_os)
-  __device__ __forceinline__ uint32_t xb() const { return xt_s + (uint32_t)(nw * 2 * 32 * 16); }
-  __device__ __forceinline__ uint32_t recv() const { return xt_s + (uint32_t)(nw * 4 * 32 * 16); }
-  __device__ __forceinline__ uint32_t bar() const { return recv() + bdelta; }
-  // the partial-sum bytes a step brings in
-  __device__ __forceinline__ uint32_t bytes() const { return (uint32_t)((EQ_C - 1) * nw * 32 * 4); }
+  __device__ __forceinline__ uint32_t bar(int par) const { return bar_s + (uint32_t)((par * nw + warp) * 8); }
 };
+// the partial-sum bytes a warp's step brings in: one float per lane from each other CTA
+constexpr uint32_t EQ_STEP_BYTES = (EQ_C - 1) * 32 * 4;
 
 // plain (compiler-scheduled) shared-memory accesses by 32-bit shared address
 __device__ __forceinline__ void eq_sts4(uint32_t a, float4 v) {
@@ -268,9 +260,10 @@ __device__ __forceinline__ void eq_st_async_f32(uint32_t addr, float v, uint32_t
                ::"r"(addr), "r"(__float_as_uint(v)), "r"(bar_cluster_addr) : "memory");
 }
 
-// this CTA's partial sum at byte offset off of CTA q's recv, completing bytes of q's mbarrier par
+// this warp's partial sum at byte offset off of CTA q's recv, completing bytes of the mbarrier of
+// the same warp and parity in CTA q
 __device__ __forceinline__ void eq_send(const EqCtx& x, uint32_t off, int par, int q, float part) {
-  eq_st_async_f32(ep_mapa(x.recv() + off, (uint32_t)q), part, ep_mapa(x.bar() + (uint32_t)(par * 8), (uint32_t)q));
+  eq_st_async_f32(ep_mapa(x.recv_s + off, (uint32_t)q), part, ep_mapa(x.bar(par), (uint32_t)q));
 }
 
 // The reduce-scatter of 32 partial sums (value 4 s + c: slot s, component c) after its first level
@@ -312,39 +305,53 @@ __device__ __forceinline__ void eq_gram(float2 tr, float2 ti, float2 br, float2 
   u[3] = (gi.x + gi.y) - (gj.x + gj.y);
 }
 
-// One step at phase U of an eight-step block (slot s keeps its top in T*[(s - U) & 7], its bottom
-// in B*[(s + U) & 7]).  Blocks start at multiples of eight steps, so the step's parity (which picks
-// the buffers and the mbarrier) is U & 1 and the mbarrier's phase (U >> 1) & 1.
-// Returns whether any slot of the CTA rotated; *ok turns false when a wait gives up.
-template <int U>
-__device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 (&BR)[8], float2 (&BI)[8],
-                                       const EqCtx& x, bool* ok) {
-  const int lane = x.lane;
-  constexpr int par = U & 1;
+// The pairs of step K (register set j < 8: column j of block A_w, 8 + j: column j of B_w).
+// K = 0..6 pair the columns inside each block by the round-robin of eight (round K: (7, K) and
+// (K + i, K - i) mod 7 for i = 1..3), A's four pairs in slots 0..3 and B's in slots 4..7; K = 7..14
+// pair column s of A with column (s + K - 7) mod 8 of B in slot s, so eight such steps meet all 64
+// pairs of A and B.
+__host__ __device__ constexpr int eq_rr(int k, int q, int e) {
+  return q == 0 ? (e == 0 ? 7 : k) : (e == 0 ? (k + q) % 7 : (k + 7 - q) % 7);
+}
+template <int K> __host__ __device__ constexpr int eq_px(int s) {
+  return K < 7 ? (s < 4 ? 0 : 8) + eq_rr(K, s & 3, 0) : s;
+}
+template <int K> __host__ __device__ constexpr int eq_py(int s) {
+  return K < 7 ? (s < 4 ? 0 : 8) + eq_rr(K, s & 3, 1) : 8 + ((s + K - 7) & 7);
+}
+
+// One step of a warp (the r-th it runs; r's parity picks the buffers and the mbarrier).  The
+// eight slots' partial 2x2 Grams over this CTA's rows are reduce-scattered over the warp (lane l
+// ends with value l: slot l >> 2, component l & 3), sent to the same warp of the other CTAs and
+// summed with theirs in rank order (so every CTA forms the same rotations), and each group of four
+// lanes forms its slot's rotation; then both columns of every rotating slot are updated.  Returns
+// whether some slot was not calm (warp-uniform); *ok turns false when a wait gives up.
+template <int K>
+__device__ __forceinline__ bool eq_bstep(float2 (&XR)[16], float2 (&XI)[16], const EqCtx& x, int r, bool* ok) {
+  const int lane = x.lane, par = r & 1;
   // slots s and s + 4 together, folded at once into the first level of the reduce-scatter
   float w16[16];
   const bool hi16 = lane & 16;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     float u[4], u2[4];
-    eq_gram(TR[(s - U) & 7], TI[(s - U) & 7], BR[(s + U) & 7], BI[(s + U) & 7], u);
-    eq_gram(TR[(s + 4 - U) & 7], TI[(s + 4 - U) & 7], BR[(s + 4 + U) & 7], BI[(s + 4 + U) & 7], u2);
+    eq_gram(XR[eq_px<K>(s)], XI[eq_px<K>(s)], XR[eq_py<K>(s)], XI[eq_py<K>(s)], u);
+    eq_gram(XR[eq_px<K>(s + 4)], XI[eq_px<K>(s + 4)], XR[eq_py<K>(s + 4)], XI[eq_py<K>(s + 4)], u2);
 #pragma unroll
     for (int c = 0; c < 4; ++c)
       w16[4 * s + c] = (hi16 ? u2[c] : u[c]) + __shfl_xor_sync(~0u, hi16 ? u[c] : u2[c], 16);
   }
   const float part = eq_reduce_scatter_rest(w16, lane);   // this CTA's rows
   // ---- the partial to the other CTAs, then the sum of all four in rank order
-  if ((x.warp | lane) == 0) eq_arrive_expect_tx(x.bar() + (uint32_t)(par * 8), x.bytes());
+  if (lane == 0) eq_arrive_expect_tx(x.bar(par), EQ_STEP_BYTES);
   const uint32_t off = (uint32_t)((((par * EQ_C + x.rank) * x.nw + x.warp) * 32 + lane) * 4);
 #pragma unroll
-  for (int j = 0; j < EQ_C - 1; ++j)
-    eq_send(x, off, par, (x.rank + 1 + j) & (EQ_C - 1), part);
-  if (*ok) *ok = eq_wait(x.bar() + (uint32_t)(par * 8), (U >> 1) & 1);
+  for (int j = 0; j < EQ_C - 1; ++j) eq_send(x, off, par, (x.rank + 1 + j) & (EQ_C - 1), part);
+  if (*ok) *ok = eq_wait(x.bar(par), (r >> 1) & 1);
   float tot = 0.f;
 #pragma unroll
   for (int q = 0; q < EQ_C; ++q)
-    tot += q == x.rank ? part : eq_lds(x.recv() + (uint32_t)((((par * EQ_C + q) * x.nw + x.warp) * 32 + lane) * 4));
+    tot += q == x.rank ? part : eq_lds(x.recv_s + (uint32_t)((((par * EQ_C + q) * x.nw + x.warp) * 32 + lane) * 4));
   // ---- each group of four lanes forms the rotation of slot lane >> 2
   const int base = lane & 28;
   const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 1);
@@ -360,142 +367,26 @@ __device__ __forceinline__ int eq_step(float2 (&TR)[8], float2 (&TI)[8], float2 
   for (int s = 0; s < 8; ++s) {
     if (!((rmask >> (4 * s)) & 1u)) continue;   // warp-uniform
     const float cs = __shfl_sync(~0u, c, 4 * s), sr = __shfl_sync(~0u, st.x, 4 * s), si = __shfl_sync(~0u, st.y, 4 * s);
-    const int t = (s - U) & 7, bb = (s + U) & 7;
+    const int t = eq_px<K>(s), bb = eq_py<K>(s);
     const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
     const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
-    const float2 xr = TR[t], xi = TI[t], yr = BR[bb], yi = BI[bb];
-    TR[t] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
-    TI[t] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
-    BR[bb] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
-    BI[bb] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
+    const float2 xr = XR[t], xi = XI[t], yr = XR[bb], yi = XI[bb];
+    XR[t] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
+    XI[t] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
+    XR[bb] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
+    XI[bb] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
   }
-  // ---- the circle move: slot 7's top and slot 0's bottom leave the warp
-  const int t7 = (7 - U) & 7, t0 = (0 - U) & 7, b0 = U & 7;
-  {
-    const uint32_t o = (uint32_t)(((par * x.nw + x.warp) * 32 + lane) * 16);
-    eq_sts4(x.xt_s + o, make_float4(TR[t7].x, TR[t7].y, TI[t7].x, TI[t7].y));
-    eq_sts4(x.xb() + o, make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y));
-  }
-  const int any = __syncthreads_or(wmask != 0u);
-  // slot h - 1 (slot 7 of the last warp) takes its own top as bottom, into the register slot 0's
-  // bottom left; slot 0 keeps its top, slot 1 takes slot 0's bottom (through a temporary when one
-  // warp holds both ends)
-  if (x.wfirst && x.wlast) {
-    const float2 tr = BR[b0], ti = BI[b0];
-    BR[b0] = TR[t7]; BI[b0] = TI[t7];
-    TR[t7] = TR[t0]; TI[t7] = TI[t0];
-    TR[t0] = tr; TI[t0] = ti;
-  } else if (x.wlast) {
-    BR[b0] = TR[t7]; BI[b0] = TI[t7];
-  } else if (x.wfirst) {
-    TR[t7] = TR[t0]; TI[t7] = TI[t0];
-    TR[t0] = BR[b0]; TI[t0] = BI[b0];
-  }
-  if (x.warp > 0) {
-    const float4 q = eq_lds4(x.xt_s + (uint32_t)(((par * x.nw + x.warp - 1) * 32 + lane) * 16));
-    TR[t7] = make_float2(q.x, q.y); TI[t7] = make_float2(q.z, q.w);
-  }
-  if (!x.wlast) {   // slot 7 is not pair h - 1
-    const float4 q = eq_lds4(x.xb() + (uint32_t)(((par * x.nw + x.warp + 1) * 32 + lane) * 16));
-    BR[b0] = make_float2(q.x, q.y); BI[b0] = make_float2(q.z, q.w);
-  }
-  return any;
+  return wmask != 0u;
 }
 
-// ---- the step of a last warp that holds at most four pair slots (eight columns) ----
-// The same dots, rotation and apply for slots 0..3 only (register sets 0..3, renamed with period
-// four), sixteen partial sums reduce-scattered so that lane l holds component (l >> 1) & 3 of slot
-// l >> 3, and the same exchange of that partial with the other CTAs (whose last warps run this step
-// too; a pass of four steps starts at a multiple of four, so parity and phase follow from U as
-// there).  Its slot 3 holds pair h - 1 (the layout pads the pairs to that) and its slot 0 trades top
-// and bottom with the previous warp; no warp reads the top leaving slot 3.
-__device__ __forceinline__ float eq_reduce_scatter16(const float (&v)[16], int lane) {
-  float w8[8], w4[4], w2[2];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const bool hi = lane & 16;
-    w8[q] = (hi ? v[8 + q] : v[q]) + __shfl_xor_sync(~0u, hi ? v[q] : v[8 + q], 16);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const bool hi = lane & 8;
-    w4[q] = (hi ? w8[4 + q] : w8[q]) + __shfl_xor_sync(~0u, hi ? w8[q] : w8[4 + q], 8);
-  }
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const bool hi = lane & 4;
-    w2[q] = (hi ? w4[2 + q] : w4[q]) + __shfl_xor_sync(~0u, hi ? w4[q] : w4[2 + q], 4);
-  }
-  const bool hi = lane & 2;
-  const float w1 = (hi ? w2[1] : w2[0]) + __shfl_xor_sync(~0u, hi ? w2[0] : w2[1], 2);
-  return w1 + __shfl_xor_sync(~0u, w1, 1);
-}
-
-template <int U>
-__device__ __forceinline__ int eq_step4(float2 (&TR)[8], float2 (&TI)[8], float2 (&BR)[8], float2 (&BI)[8],
-                                        const EqCtx& x, bool* ok) {
-  const int lane = x.lane;
-  constexpr int par = U & 1;
-  float v[16];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    float u[4];
-    eq_gram(TR[(s - U) & 3], TI[(s - U) & 3], BR[(s + U) & 3], BI[(s + U) & 3], u);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) v[4 * s + c] = u[c];
-  }
-  const float part = eq_reduce_scatter16(v, lane);
-  if ((x.warp | lane) == 0) eq_arrive_expect_tx(x.bar() + (uint32_t)(par * 8), x.bytes());
-  const uint32_t off = (uint32_t)((((par * EQ_C + x.rank) * x.nw + x.warp) * 32 + lane) * 4);
-#pragma unroll
-  for (int j = 0; j < EQ_C - 1; ++j)
-    eq_send(x, off, par, (x.rank + 1 + j) & (EQ_C - 1), part);
-  if (*ok) *ok = eq_wait(x.bar() + (uint32_t)(par * 8), (U >> 1) & 1);
-  float tot = 0.f;
-#pragma unroll
-  for (int q = 0; q < EQ_C; ++q)
-    tot += q == x.rank ? part : eq_lds(x.recv() + (uint32_t)((((par * EQ_C + q) * x.nw + x.warp) * 32 + lane) * 4));
-  // ---- each group of eight lanes forms the rotation of slot lane >> 3
-  const int base = lane & 24;
-  const float a = __shfl_sync(~0u, tot, base), b = __shfl_sync(~0u, tot, base + 2);
-  const float2 gm = make_float2(__shfl_sync(~0u, tot, base + 4), __shfl_sync(~0u, tot, base + 6));
-  float c;
-  float2 st;
-  int rot;
-  bool calm;
-  ep_rotation_os(a, b, gm, EQ_TOL, x.clim2, x.slim2, c, st, rot, calm);
-  const unsigned rmask = __ballot_sync(~0u, rot);
-  const unsigned wmask = __ballot_sync(~0u, !calm);
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (!((rmask >> (8 * s)) & 1u)) continue;   // warp-uniform
-    const float cs = __shfl_sync(~0u, c, 8 * s), sr = __shfl_sync(~0u, st.x, 8 * s), si = __shfl_sync(~0u, st.y, 8 * s);
-    const int t = (s - U) & 3, bb = (s + U) & 3;
-    const float2 C2 = make_float2(cs, cs), SR = make_float2(sr, sr), SI = make_float2(si, si);
-    const float2 NSR = make_float2(-sr, -sr), NSI = make_float2(-si, -si);
-    const float2 xr = TR[t], xi = TI[t], yr = BR[bb], yi = BI[bb];
-    TR[t] = __ffma2_rn(NSI, yi, __ffma2_rn(NSR, yr, __fmul2_rn(C2, xr)));
-    TI[t] = __ffma2_rn(SI, yr, __ffma2_rn(NSR, yi, __fmul2_rn(C2, xi)));
-    BR[bb] = __ffma2_rn(C2, yr, __ffma2_rn(NSI, xi, __fmul2_rn(SR, xr)));
-    BI[bb] = __ffma2_rn(C2, yi, __ffma2_rn(SI, xr, __fmul2_rn(SR, xi)));
-  }
-  // ---- slot 0's bottom leaves for the previous warp
-  const int t3 = (3 - U) & 3, b0 = U & 3;
-  eq_sts4(x.xb() + (uint32_t)(((par * x.nw + x.warp) * 32 + lane) * 16),
-          make_float4(BR[b0].x, BR[b0].y, BI[b0].x, BI[b0].y));
-  const int any = __syncthreads_or(wmask != 0u);
-  // slot 3 takes its own top as bottom, into the register slot 0's bottom left; slot 0's new top
-  // comes from the previous warp's slot 7, into the register slot 3's top left
-  BR[b0] = TR[t3]; BI[b0] = TI[t3];
-  {
-    const float4 q = eq_lds4(x.xt_s + (uint32_t)(((par * x.nw + x.warp - 1) * 32 + lane) * 16));
-    TR[t3] = make_float2(q.x, q.y); TI[t3] = make_float2(q.z, q.w);
-  }
-  return any;
+// The position (column of L at the start, of U at the end) of column s of block j (A_w: 0, B_w: 1)
+// of warp w: blocks in circle order, shifted so that A_0 holds the last eight
+__host__ __device__ inline int eq_block_pos(int nw, int w, int j, int s) {
+  return 8 * ((2 * w + j + 2 * nw - 1) % (2 * nw)) + s;
 }
 
 
-__global__ void __launch_bounds__(32 * ((kEvdOscNmax / 2 + EQ_S - 1) / EQ_S), 1)
+__global__ void __launch_bounds__(32 * ((kEvdOscNmax + 15) / 16), 1)
 evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
                const float2* __restrict__ Vhg, const float2* __restrict__ Tg, const double* __restrict__ scale_g,
                const Box* __restrict__ boxes, EqArgs g, double* __restrict__ lam_out, float2* __restrict__ V_out,
@@ -506,7 +397,7 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
   const int rank = (int)cluster.block_rank(), k = blockIdx.x / EQ_C, n = g.nt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = blockDim.x;
   const EqLayout L = eq_layout(n);
-  const int np = L.np, h = L.h, lda = L.lda, m = L.m;
+  const int np = L.np, lda = L.lda, m = L.m;
   const int r0 = rank * L.R, r1 = r0 + L.R < n ? r0 + L.R : n, nr = r1 > r0 ? r1 - r0 : 0;   // own rows (pivot order)
   float2* U = reinterpret_cast<float2*>(smem + L.u);   // [row - r0][pos]
   double* lamp = reinterpret_cast<double*>(smem + L.lamp);
@@ -542,84 +433,122 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
     return;   // every CTA of the cluster leaves before any cluster-level exchange
   }
   for (int i = tid; i < n; i += nthr) perm[i] = perm_g[(size_t)k * n + i];
-  if (tid == 0) {
-    ep_bar_init(&bar[0], 1);
-    ep_bar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  if (tid < 2 * L.nw) ep_bar_init(&bar[tid], 1);   // [parity][warp]
+  if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   cluster.sync();   // barriers of every CTA initialised
 
+  // ---- blocks: block j of warp w (A_w: j = 0, B_w: j = 1) starts with columns eq_block_pos(nw, w,
+  // j, 0..7) of L, this CTA's rows (lane l rows r0 + l and r0 + 32 + l as a packed pair).  The last
+  // eight positions form A_0, which the circle never moves: with eight or more zero columns past Nt
+  // warp 0 has no cross pair to rotate and skips those steps (at Nt = 200 the other twelve warps
+  // then sit three to a scheduler).
+  const int nw = L.nw;
+  const bool idle0 = warp == 0 && np - n >= 8;
   EqCtx xc;
-  xc.xt_s = ep_smem(smem + L.x);
-  xc.nw = L.nw; xc.warp = warp; xc.lane = lane; xc.rank = rank;
-  xc.bdelta = ep_smem(bar) - xc.recv();
-  xc.clim2 = (float)np * EQ_TOL * EQ_TOL;
-  xc.slim2 = 0.25f / ((float)np * np * np);
-  xc.wfirst = warp == 0;
-  xc.wlast = warp == L.nw - 1;
-
-  // ---- registers: slot p = 8 warp + s holds columns (2p, 2p + 1); lane l rows r0 + l and r0 + 32 + l
-  float2 TR[8], TI[8], BR[8], BI[8];
+  xc.recv_s = ep_smem(smem + L.u) + (uint32_t)eq_xq_bytes(nw);
+  xc.bar_s = ep_smem(bar);
+  xc.nw = nw; xc.warp = warp; xc.lane = lane; xc.rank = rank;
+  {
+    const float ne = (float)(n + (n & 1));   // the calm bounds take the unpadded size
+    xc.clim2 = ne * EQ_TOL * EQ_TOL;
+    xc.slim2 = 0.25f / (ne * ne * ne);
+  }
+  float2 XR[16], XI[16];
   {
     const float2* Lw = Lg + (size_t)k * n * n;
     const int ra = r0 + lane, rb = r0 + 32 + lane;
     const bool va = lane < nr, vb = 32 + lane < nr;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const int p = EQ_S * warp + s, ct = 2 * p, cb = 2 * p + 1;
+    for (int j = 0; j < 16; ++j) {
+      const int c = eq_block_pos(nw, warp, j >> 3, j & 7);
       const float2 z = make_float2(0.f, 0.f);
-      const float2 ta = (p < h && va && ct < n) ? Lw[(size_t)ra * n + ct] : z;
-      const float2 tb = (p < h && vb && ct < n) ? Lw[(size_t)rb * n + ct] : z;
-      const float2 ba = (p < h && va && cb < n) ? Lw[(size_t)ra * n + cb] : z;
-      const float2 bb = (p < h && vb && cb < n) ? Lw[(size_t)rb * n + cb] : z;
-      TR[s] = make_float2(ta.x, tb.x); TI[s] = make_float2(ta.y, tb.y);
-      BR[s] = make_float2(ba.x, bb.x); BI[s] = make_float2(ba.y, bb.y);
+      const float2 ta = (va && c < n) ? Lw[(size_t)ra * n + c] : z;
+      const float2 tb = (vb && c < n) ? Lw[(size_t)rb * n + c] : z;
+      XR[j] = make_float2(ta.x, tb.x); XI[j] = make_float2(ta.y, tb.y);
     }
   }
-  // ---- sweeps, in blocks of eight steps; converged once a whole circle (np - 1 steps) was calm
-  // (no rotation above the bounds of ep_rotation_os).  Every CTA forms the same rotations, so every CTA
-  // reaches the same decision.
+  // ---- sweeps in rounds: eight steps in which each warp meets all pairs of its A and B, then the
+  // blocks move one place on the circle (A_0 stays, A_1 takes B_0, A_w takes A_(w-1), B_w takes
+  // B_(w+1), the last B takes its own A) through shared memory; the first round of a sweep adds the
+  // seven steps of the pairs inside each block.  A warp waits only for the same warp of the other
+  // CTAs at each step (its own mbarrier) and for the whole CTA at the round's exchange.  Converged
+  // once a whole sweep of rounds (2 nw - 1, which meet every pair once) was calm; every CTA forms the
+  // same rotations, so every CTA reaches the same decision.
   __shared__ int sh_fail;
   if (tid == 0) sh_fail = 0;
   __syncthreads();
   bool ok = true;
   int converged = 0, sweeps = 0;
   {
-    const int per = np - 1;
-    const int maxsteps = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
-    int steps = 0, quiet = 0, last = 0;
-    auto track = [&](int any) {
-      ++steps;
-      if (any) { quiet = 0; last = steps; }
+    const uint32_t xq = ep_smem(smem + L.u);   // float4 [warp][column 0..15][lane], overlays u
+    const int per = 2 * nw - 1;
+    const int maxrounds = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
+    int rounds = 0, quiet = 0, last = 0, rr = 0, r = 0;
+    for (;;) {
+      bool nc = false;
+      if (rr == 0) {   // the pairs inside each block, once per sweep
+        nc |= eq_bstep<0>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<1>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<2>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<3>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<4>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<5>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<6>(XR, XI, xc, r++, &ok);
+      }
+      if (!idle0) {
+        nc |= eq_bstep<7>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<8>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<9>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<10>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<11>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<12>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<13>(XR, XI, xc, r++, &ok);
+        nc |= eq_bstep<14>(XR, XI, xc, r++, &ok);
+      }
+      // ---- the blocks move: A_w to warp w + 1 (read by warps 2 .. nw - 1), B_w to warp w - 1 (B_0
+      // to warp 1 as its A)
+      if (nw > 1) {
+        const uint32_t own = xq + (uint32_t)((warp * 16 * 32 + lane) * 16);
+        if (warp > 0 && warp < nw - 1) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            eq_sts4(own + (uint32_t)(j * 32 * 16), make_float4(XR[j].x, XR[j].y, XI[j].x, XI[j].y));
+        }
+#pragma unroll
+        for (int j = 8; j < 16; ++j)
+          eq_sts4(own + (uint32_t)(j * 32 * 16), make_float4(XR[j].x, XR[j].y, XI[j].x, XI[j].y));
+      }
+      const int any = __syncthreads_or(nc);
+      if (nw > 1) {
+        if (warp == nw - 1) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) { XR[8 + j] = XR[j]; XI[8 + j] = XI[j]; }
+        }
+        if (warp > 0) {   // new A: B_0 for warp 1, A_(w-1) for the others
+          const uint32_t src = xq + (uint32_t)((((warp - 1) * 16 + (warp == 1 ? 8 : 0)) * 32 + lane) * 16);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 q = eq_lds4(src + (uint32_t)(j * 32 * 16));
+            XR[j] = make_float2(q.x, q.y); XI[j] = make_float2(q.z, q.w);
+          }
+        }
+        if (warp < nw - 1) {   // new B: B_(w+1)
+          const uint32_t src = xq + (uint32_t)((((warp + 1) * 16 + 8) * 32 + lane) * 16);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 q = eq_lds4(src + (uint32_t)(j * 32 * 16));
+            XR[8 + j] = make_float2(q.x, q.y); XI[8 + j] = make_float2(q.z, q.w);
+          }
+        }
+      }
+      // read before the next round writes; and stop exchanging once a wait gave up
+      if (__syncthreads_or(!ok)) { sh_fail = 1; break; }
+      ++rounds;
+      if (any) { quiet = 0; last = rounds; }
       else ++quiet;
-    };
-    // the two loops apart, so that each keeps its own registers; the four-slot loop holds one
-    // period (four steps) of code and meets the block's barrier every second pass, i.e. at the
-    // same steps as the eight-slot loop
-    if (eq_four(n) && warp == L.nw - 1) {
-      for (int half = 0;; half ^= 1) {
-        int a = eq_step4<0>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step4<1>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step4<2>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step4<3>(TR, TI, BR, BI, xc, &ok); track(a);
-        if (!half) continue;
-        if (__syncthreads_or(!ok)) { sh_fail = 1; break; }   // a wait gave up: stop exchanging
-        if (quiet >= per) { converged = 1; break; }
-        if (steps >= maxsteps) break;
-      }
-    } else {
-      while (steps < maxsteps) {
-        int a = eq_step<0>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<1>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<2>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<3>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<4>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<5>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<6>(TR, TI, BR, BI, xc, &ok); track(a);
-        a = eq_step<7>(TR, TI, BR, BI, xc, &ok); track(a);
-        if (__syncthreads_or(!ok)) { sh_fail = 1; break; }   // a wait gave up: stop exchanging
-        if (quiet >= per) { converged = 1; break; }
-      }
+      if (quiet >= per) { converged = 1; break; }
+      if (rounds >= maxrounds) break;
+      rr = rr + 1 == per ? 0 : rr + 1;
     }
     sweeps = (last + per - 1) / per;
   }
@@ -629,32 +558,31 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
   // ---- squared column norms: this CTA's rows (double-float), summed over the cluster in rank order
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
-    const int p = EQ_S * warp + s;
+    const int pa = eq_block_pos(nw, warp, 0, s), pb = eq_block_pos(nw, warp, 1, s);
+    const float2 tr = XR[s], ti = XI[s], br = XR[8 + s], bi = XI[8 + s];
     df na = {0.f, 0.f}, nb = {0.f, 0.f};
-    na = df_add_f(na, fmaf(TR[s].x, TR[s].x, TI[s].x * TI[s].x));
-    na = df_add_f(na, fmaf(TR[s].y, TR[s].y, TI[s].y * TI[s].y));
-    nb = df_add_f(nb, fmaf(BR[s].x, BR[s].x, BI[s].x * BI[s].x));
-    nb = df_add_f(nb, fmaf(BR[s].y, BR[s].y, BI[s].y * BI[s].y));
+    na = df_add_f(na, fmaf(tr.x, tr.x, ti.x * ti.x));
+    na = df_add_f(na, fmaf(tr.y, tr.y, ti.y * ti.y));
+    nb = df_add_f(nb, fmaf(br.x, br.x, bi.x * bi.x));
+    nb = df_add_f(nb, fmaf(br.y, br.y, bi.y * bi.y));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       df t;
       t.hi = __shfl_xor_sync(~0u, na.hi, o); t.lo = __shfl_xor_sync(~0u, na.lo, o); na = df_add(na, t);
       t.hi = __shfl_xor_sync(~0u, nb.hi, o); t.lo = __shfl_xor_sync(~0u, nb.lo, o); nb = df_add(nb, t);
     }
-    if (p < h && lane < EQ_C) {   // lane q writes into CTA q
+    if (lane < EQ_C) {   // lane q writes into CTA q
       double* dst = cluster.map_shared_rank(lamp, (unsigned)lane);
-      dst[rank * np + 2 * p] = (double)na.hi + (double)na.lo;
-      dst[rank * np + 2 * p + 1] = (double)nb.hi + (double)nb.lo;
+      dst[rank * np + pa] = (double)na.hi + (double)na.lo;
+      dst[rank * np + pb] = (double)nb.hi + (double)nb.lo;
     }
     // this CTA's rows, unnormalised for now
-    if (p < h) {
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int rr = e * 32 + lane;
-        if (rr < nr) {
-          U[(size_t)rr * lda + 2 * p] = make_float2(e ? TR[s].y : TR[s].x, e ? TI[s].y : TI[s].x);
-          U[(size_t)rr * lda + 2 * p + 1] = make_float2(e ? BR[s].y : BR[s].x, e ? BI[s].y : BI[s].x);
-        }
+    for (int e = 0; e < 2; ++e) {
+      const int rr = e * 32 + lane;
+      if (rr < nr) {
+        U[(size_t)rr * lda + pa] = make_float2(e ? tr.y : tr.x, e ? ti.y : ti.x);
+        U[(size_t)rr * lda + pb] = make_float2(e ? br.y : br.x, e ? bi.y : bi.x);
       }
     }
   }

@@ -181,13 +181,13 @@ def test_os_learned_rule_is_refused():
 
 # ---- packets longer than 128 frames: Cholesky kernel + four-CTA cluster sweeps (Nt <= 224)
 @pytest.mark.parametrize("shape,grid,mode,tc", [
-    ((129, 33, 29), (2, 2), "LCF_T_MEDIAN", False),      # shortest: 9 warps, 65 slots padded to 68 (four-slot last warp)
-    ((136, 20, 18), (1, 1), "LCF_T_FIXED", False),       # 68 slots: a four-slot last warp, no padding
-    ((182, 21, 17), (1, 1), "LCF_T_CURVATURE", True),    # 91 slots padded to 92 (four-slot last warp)
-    ((170, 20, 18), (1, 1), "LCF_T_MEDIAN", False),      # 85 slots padded to 88 (eight-slot last warp)
-    ((200, 40, 36), (2, 2), "LCF_T_CURVATURE", True),    # the streaming workload's packet length: 100 slots
+    ((129, 33, 29), (2, 2), "LCF_T_MEDIAN", False),      # shortest: 9 warps, 144 columns, warp 0 idle in cross steps
+    ((136, 20, 18), (1, 1), "LCF_T_FIXED", False),       # 144 columns, 8 padding: warp 0 idle
+    ((182, 21, 17), (1, 1), "LCF_T_CURVATURE", True),    # 192 columns, 10 padding
+    ((170, 20, 18), (1, 1), "LCF_T_MEDIAN", False),      # 176 columns, 6 padding: every warp works
+    ((200, 40, 36), (2, 2), "LCF_T_CURVATURE", True),    # the streaming workload's packet length: 208 columns
     ((200, 40, 36), (2, 2), "LCF_T_ADAPTIVE_SOFT", True),
-    ((201, 30, 26), (1, 2), "LCF_T_FIXED", False),       # odd length: 101 slots padded to 104
+    ((201, 30, 26), (1, 2), "LCF_T_FIXED", False),       # odd length: 208 columns, 7 padding
     ((224, 24, 20), (1, 2), "LCF_T_SLOPE", True),        # longest on this path: 14 warps, no padding
     ((150, 22, 18), (1, 1), "LCF_T_NCC", True),          # method 4 after the cluster EVD
     ((200, 33, 29), (2, 2), "LCF_T_CURVATURE", True),    # odd pixel count: tile pairs without the tensor map
