@@ -34,12 +34,12 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    # the one-sided EVD stage: evd_prep_kernel 10.35 MB + evd_os_kernel 3.89 MB
-    ("evd", "os"): {"bytes": 14.24e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.88 MB
+    ("evd", "os"): {"bytes": 14.30e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
                                 "2aeeab6efc2ae653f8e0238e0a977aa21661b6323e6633d28b6f5161496ef5a8",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
-                                "012f98a6ccfab4ab00945437406f1d375bc5f7e32e342f35d7a751466c9ea849",
+                                "8c289eda9c7e7231dae1028e56bbd723621b784f046164a1530f2268e80bf034",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":
                                 "e94da384b6101ccb3ec412d8d3462094bdb5b419f12848449819fe823d146e62",
                                 "paper_2405_11105_b300/csrc/lcf_internal.cuh":

@@ -74,7 +74,6 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
   const bool rf = n <= kEvdPairNmax;   // fp32(R / scale) staged once in shared memory
   __shared__ double sh_scale;
   __shared__ float betas[kEvdHead];
-  __shared__ float2 us[kEvdHead];
   __shared__ float2 Tm[kEvdHead * kEvdHead];
   __shared__ zdf Mm[kEvdHead * kEvdHead], MT[kEvdHead * kEvdHead], W2[kEvdHead * kEvdHead];
   __shared__ float2 cs[kEvdHead];
@@ -150,6 +149,62 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
       }
     }
     __syncthreads();
+    if (rf) {   // Nt <= 128: CGS2 of Z's columns into Y by warp 0 in registers (lane: rows lane + 32 i)
+      if (warp == 0) {
+        float2 z[kEvdHead][4];
+#pragma unroll
+        for (int j = 0; j < kEvdHead; ++j)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int a = lane + 32 * i;
+            z[j][i] = (j < m && a < n) ? Zs[(size_t)j * ldy + a] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+        for (int j = 0; j < kEvdHead; ++j) {
+          if (j >= m) break;
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass) {
+            float2 c[kEvdHead];
+#pragma unroll
+            for (int l = 0; l < j; ++l) {
+              float2 d = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) d = cadd(d, cmulc(z[l][i], z[j][i]));
+              for (int o = 16; o; o >>= 1) { d.x += __shfl_xor_sync(~0u, d.x, o); d.y += __shfl_xor_sync(~0u, d.y, o); }
+              c[l] = d;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              float2 v = z[j][i];
+#pragma unroll
+              for (int l = 0; l < j; ++l) v = csub(v, cmul(c[l], z[l][i]));
+              z[j][i] = v;
+            }
+          }
+          float nr = 0.f;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) nr += cabs2(z[j][i]);
+          for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
+          if (nr > 0.f) {   // a vanished column keeps the previous iterate
+            const float sc = rsqrtf(nr);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              z[j][i] = cscale(z[j][i], sc);
+              const int a = lane + 32 * i;
+              if (a < n) Ys[(size_t)j * ldy + a] = z[j][i];
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int a = lane + 32 * i;
+              z[j][i] = a < n ? Ys[(size_t)j * ldy + a] : make_float2(0.f, 0.f);
+            }
+          }
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     for (int j = 0; j < m; ++j) {   // CGS2 of Z's columns into Y
       float2* zj = Zs + (size_t)j * ldy;
       for (int pass = 0; pass < 2 && j > 0; ++pass) {
@@ -183,10 +238,12 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
       __syncthreads();
     }
   }
-  // ---- Householder QR of Y (warp 0), reflectors -> Zs; compact WY T
-  if (warp == 0) {
-    for (int j = 0; j < m; ++j) {
-      float2* yj = Ys + (size_t)j * ldy;
+  // ---- Householder QR of Y, reflectors -> Zs; compact WY T.  Column j's reflector by warp 0, its
+  // application to the later columns by one warp each; T's inner products by all warps.
+  for (int j = 0; j < m; ++j) {
+    float2* yj = Ys + (size_t)j * ldy;
+    float2* vj = Zs + (size_t)j * ldy;
+    if (warp == 0) {
       float nr = 0.f;
       for (int a = j + lane; a < n; a += 32) nr += cabs2(yj[a]);
       for (int o = 16; o; o >>= 1) nr += __shfl_xor_sync(~0u, nr, o);
@@ -195,35 +252,39 @@ evd_prep_kernel(const double2* __restrict__ Rg, int n, int iters, float2* __rest
       const float ax0 = sqrtf(cabs2(x0));
       const float2 e = ax0 > 0.f ? cscale(x0, 1.f / ax0) : make_float2(1.f, 0.f);
       const float beta = alpha > 0.f ? 1.f / (alpha * (alpha + ax0)) : 0.f;
-      float2* vj = Zs + (size_t)j * ldy;
       for (int a = lane; a < ldy; a += 32) {
         float2 v = (a < j || a >= n) ? make_float2(0.f, 0.f) : yj[a];
         if (a == j) v = cadd(x0, cscale(e, alpha));
         vj[a] = v;
       }
       if (lane == 0) betas[j] = beta;
-      __syncwarp();
-      for (int c = j + 1; c < m; ++c) {
-        float2* yc = Ys + (size_t)c * ldy;
-        float2 t = make_float2(0.f, 0.f);
-        for (int a = j + lane; a < n; a += 32) t = cadd(t, cmulc(vj[a], yc[a]));
-        for (int o = 16; o; o >>= 1) { t.x += __shfl_xor_sync(~0u, t.x, o); t.y += __shfl_xor_sync(~0u, t.y, o); }
-        t = cscale(t, beta);
-        for (int a = j + lane; a < n; a += 32) yc[a] = csub(yc[a], cmul(vj[a], t));
-        __syncwarp();
-      }
     }
+    __syncthreads();
+    const int c = j + warp;   // warp w > 0 updates column j + w
+    if (warp > 0 && c < m) {
+      float2* yc = Ys + (size_t)c * ldy;
+      float2 t = make_float2(0.f, 0.f);
+      for (int a = j + lane; a < n; a += 32) t = cadd(t, cmulc(vj[a], yc[a]));
+      for (int o = 16; o; o >>= 1) { t.x += __shfl_xor_sync(~0u, t.x, o); t.y += __shfl_xor_sync(~0u, t.y, o); }
+      t = cscale(t, betas[j]);
+      for (int a = j + lane; a < n; a += 32) yc[a] = csub(yc[a], cmul(vj[a], t));
+    }
+    __syncthreads();
+  }
+  for (int q = warp; q < m * m; q += ED_THREADS / 32) {   // Mm[i m + j].re.hi = v_i^H v_j, i < j
+    const int i = q / m, j = q % m;
+    if (i >= j) continue;
+    float2 c = make_float2(0.f, 0.f);
+    for (int a = lane; a < n; a += 32) c = cadd(c, cmulc(Zs[(size_t)i * ldy + a], Zs[(size_t)j * ldy + a]));
+    for (int o = 16; o; o >>= 1) { c.x += __shfl_xor_sync(~0u, c.x, o); c.y += __shfl_xor_sync(~0u, c.y, o); }
+    if (lane == 0) Mm[q].re.hi = c.x, Mm[q].im.hi = c.y;
+  }
+  __syncthreads();
+  if (warp == 0) {
     for (int j = 0; j < m; ++j) {
-      for (int i = 0; i < j; ++i) {
-        float2 c = make_float2(0.f, 0.f);
-        for (int a = lane; a < n; a += 32) c = cadd(c, cmulc(Zs[(size_t)i * ldy + a], Zs[(size_t)j * ldy + a]));
-        for (int o = 16; o; o >>= 1) { c.x += __shfl_xor_sync(~0u, c.x, o); c.y += __shfl_xor_sync(~0u, c.y, o); }
-        if (lane == 0) us[i] = c;
-      }
-      __syncwarp();
       if (lane < j) {
         float2 acc = make_float2(0.f, 0.f);
-        for (int l = lane; l < j; ++l) acc = cadd(acc, cmul(Tm[lane * m + l], us[l]));
+        for (int l = lane; l < j; ++l) acc = cadd(acc, cmul(Tm[lane * m + l], make_float2(Mm[l * m + j].re.hi, Mm[l * m + j].im.hi)));
         Tm[lane * m + j] = cscale(acc, -betas[j]);
       }
       if (lane == 0) {
