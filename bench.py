@@ -37,7 +37,7 @@ CAPTURED_TRAFFIC = {
     # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.88 MB
     ("evd", "os"): {"bytes": 14.30e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "2aeeab6efc2ae653f8e0238e0a977aa21661b6323e6633d28b6f5161496ef5a8",
+                                "01e338df1ff1fae35a2e11c0da3c3ec6f7dabbe1f00cf017f8ebf5791131d01d",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "8c289eda9c7e7231dae1028e56bbd723621b784f046164a1530f2268e80bf034",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":

@@ -46,6 +46,7 @@ constexpr int EO_THREADS = 512;
 constexpr float EO_TOL = 2.0e-6f;              // relative orthogonality test (cosine of two columns)
 constexpr int EO_SUBSPACE_ITERS = 3;
 constexpr int EO_CB = 4;                       // Cholesky columns per trailing update
+constexpr size_t EO_SMEM_MAX = 227 * 1024;     // dynamic shared memory a CTA may opt in to
 
 struct EoArgs {
   int nt, nz, nx;
@@ -60,15 +61,16 @@ struct EoArgs {
 __host__ __device__ inline size_t eo_align(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct EoLayout {
-  int np, h, lda, m, nw, rp;
+  int np, h, lda, m, nw, rp, nbuf;   // nbuf: block-exchange buffers (2: by round parity)
   size_t a, x, colj, lam, sperm, wts, s0, s1, s2, coef, keep, phs, end;
 };
 
 // a: the matrix (B, then the Cholesky factor, then the eigenvector columns U, then V), rows by index;
 // x: the Cholesky block's columns, the step-parity exchange buffers of the sweeps, later Vh, T,
 // X = Vh^H U and Y = T X
-__host__ __device__ inline EoLayout eo_layout(int n) {
+__host__ __device__ inline EoLayout eo_layout_b(int n, int nbuf) {
   EoLayout L;
+  L.nbuf = nbuf;
   L.nw = (n + 7) / 8;
   L.np = 8 * L.nw;           // column positions: two blocks of four per warp, zero columns past Nt
   L.h = L.np / 2;
@@ -78,8 +80,8 @@ __host__ __device__ inline EoLayout eo_layout(int n) {
   size_t o = 0;
   L.a = o; o = eo_align(o + (size_t)L.np * L.lda * 8);
   {
-    // the sweeps' block exchange [warp][column 0..7][row pair][lane] (float4) overlays a and x
-    const size_t xch = (size_t)L.nw * 8 * L.rp * 32 * 16;
+    // the sweeps' block exchange [buffer][warp][column 0..7][row pair][lane] (float4) overlays a and x
+    const size_t xch = (size_t)nbuf * L.nw * 8 * L.rp * 32 * 16;
     const size_t post = ((size_t)L.m * n + (size_t)L.m * L.m + (size_t)2 * L.m * L.np) * 8;
     const size_t chol = (size_t)EO_CB * L.np * 8;   // the Cholesky block's columns
     size_t need = xch > o ? xch - o : 0;
@@ -99,6 +101,11 @@ __host__ __device__ inline EoLayout eo_layout(int n) {
   L.phs = o;   o = eo_align(o + (size_t)L.np * 8);
   L.end = o;
   return L;
+}
+// two exchange buffers (one barrier a round) where they fit in shared memory, else one (two barriers)
+__host__ __device__ inline EoLayout eo_layout(int n) {
+  const EoLayout L = eo_layout_b(n, 2);
+  return L.end + (size_t)n * 8 + 4096 <= EO_SMEM_MAX ? L : eo_layout_b(n, 1);
 }
 
 size_t evd_os_smem_bytes(int nt) { return eo_layout(nt).end + (size_t)nt * 8; }   // + lam_s
@@ -404,7 +411,8 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   // bounds of ep_rotation_os.
   int converged = 0, sweeps = 0;
   {
-    float4* xq = reinterpret_cast<float4*>(smem + L.a);   // [warp][column 0..7][row pair][lane]
+    float4* xq0 = reinterpret_cast<float4*>(smem + L.a);   // [buffer][warp][column 0..7][row pair][lane]
+    const size_t xbuf = (size_t)nw * 8 * RP * 32;           // float4 per buffer
     const int per = 2 * nw - 1;
     const int maxrounds = (g.max_sweeps > 0 ? g.max_sweeps : 40) * per;
     int rounds = 0, quiet = 0, last = 0, rr = 0;
@@ -423,6 +431,7 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
       }
       // ---- the blocks move: A_w goes to warp w + 1 (read by warps 2 .. nw - 1), B_w to warp w - 1
       // (B_0 to warp 1 as its A); A_0 stays and the last warp's A becomes its own B
+      float4* xq = xq0 + (L.nbuf == 2 ? (size_t)(rounds & 1) * xbuf : 0);
       if (nw > 1) {
         float4* own = xq + (size_t)warp * 8 * RP * 32 + lane;
         if (warp > 0 && warp < nw - 1) {
@@ -466,7 +475,9 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
               XR[c][i] = make_float2(q.x, q.y); XI[c][i] = make_float2(q.z, q.w);
             }
         }
-        __syncthreads();   // read before the next round writes
+        // read before the next round writes: with two buffers the next round writes the other one,
+        // and the round after it only after the next round's barrier, which follows these reads
+        if (L.nbuf == 1) __syncthreads();
       }
       ++rounds;
       if (any) { quiet = 0; last = rounds; }
@@ -715,8 +726,11 @@ static void eo_launch(const lcf_plan* P, cudaStream_t st, const EoArgs& a) {
 
 template <int RP>
 static cudaError_t eo_configure_one() {
-  return cudaFuncSetAttribute(evd_os_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)evd_os_smem_bytes(RP * 64));
+  // the largest request of the packet lengths this instance serves (two exchange buffers make a
+  // shorter packet's request the larger one)
+  size_t mx = 0;
+  for (int n = (RP - 1) * 64 + 1; n <= RP * 64; ++n) mx = evd_os_smem_bytes(n) > mx ? evd_os_smem_bytes(n) : mx;
+  return cudaFuncSetAttribute(evd_os_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 
 cudaError_t launch_evd_os(const lcf_plan* P, cudaStream_t st) {
