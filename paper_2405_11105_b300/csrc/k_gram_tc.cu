@@ -625,7 +625,16 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
 // R from the tensor-core partials: R' = Herm(sum D') / s^2 for the residual block and U
 // (U from the CUDA-core augmented-column partials instead when the tensor-core rows
 // nb are the residual rows alone, nb = nt), Q from the exact kernel;
-// R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T (FP64)
+// R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T, i.e. R'_cc + W Phi^T + (W Phi^T)^H with
+// W = U + 1/2 conj(Phi) Q.  W is formed in FP64 (nt d entries); the Nt (Nt + 1) / 2 entries of R
+// are summed in double-float on the FP32 pipes (the partials split into two floats on the integer
+// pipes, the power-of-two scale folded into the exponent), FP64 being ~1/62 of FP32 on this part;
+// an entry whose double-float sum leaves the float range is redone in FP64.
+// Shared memory: W [nt][kDeflateMax] (double2), Q [kDeflateMax]^2 (double2), W again as double-float
+// [nt][kDeflateMax], Phi [d][kEvdNmax] (float2).
+static size_t gram_assemble_tc_smem_bytes(int nt, int nd_defl) {
+  return ((size_t)(nt + kDeflateMax) * kDeflateMax + (size_t)nt * kDeflateMax) * 16 + (size_t)nd_defl * kEvdNmax * 8;
+}
 __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const double2* __restrict__ qpart,
                                         const double2* __restrict__ aug, int aug_nsplit, int aug_qrows,
                                         const float2* __restrict__ phi, const unsigned* __restrict__ xmax_bits,
@@ -635,18 +644,24 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   // packets whose augmented rows fit one tile)
   const int k = blockIdx.y;
   const double* pk = part + (size_t)k * wstride;
-  extern __shared__ double2 asm_dyn[];   // U [nt][kDeflateMax], Q [kDeflateMax]^2, ph [d][kEvdNmax]
+  extern __shared__ double2 asm_dyn[];
   double2 (*U)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn);
   double2 (*Q)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn + (size_t)nt * kDeflateMax);
-  double2 (*ph)[kEvdNmax] =
-      reinterpret_cast<double2 (*)[kEvdNmax]>(asm_dyn + (size_t)(nt + kDeflateMax) * kDeflateMax);
+  zdf (*Wz)[kDeflateMax] = reinterpret_cast<zdf (*)[kDeflateMax]>(asm_dyn + (size_t)(nt + kDeflateMax) * kDeflateMax);
+  float2 (*phf)[kEvdNmax] =
+      reinterpret_cast<float2 (*)[kEvdNmax]>(asm_dyn + (size_t)(2 * nt + kDeflateMax) * kDeflateMax);
   __shared__ double inv_s2;
+  __shared__ int hx_s;
   if (threadIdx.x == 0) {
     float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
     inv_s2 = 1.0 / ((double)sc * (double)sc);
+    int e;
+    frexpf(sc, &e);          // sc = 2^(e - 1)
+    hx_s = 2 * (e - 1) + 1;   // 1/2 of 1/sc^2 = 2^-hx
   }
   __syncthreads();
   const double is2 = inv_s2;
+  const int hx = hx_s;
   // Hermitian part of the summed D' at (a, b)
   // (split 0 of each window holds the sum over splits, see gram_tc_reduce_kernel)
   const size_t t2 = (size_t)tb * tb;
@@ -674,8 +689,7 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
       }
       U[i][a] = make_double2(sx, sy);
     }
-    float2 f = phi[a * nt + i];
-    ph[a][i] = make_double2((double)f.x, (double)f.y);
+    phf[a][i] = phi[a * nt + i];
   }
   for (int e = threadIdx.x; e < nd_defl * nd_defl; e += blockDim.x) {
     int a = e / nd_defl, c = e % nd_defl;
@@ -700,14 +714,28 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   __syncthreads();
   constexpr int WPT = (kEvdNmax * kDeflateMax + 255) / 256;   // W entries per thread (blockDim 256)
   double2 wv[WPT];
-  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 496 < 512)
-    int e = threadIdx.x + u * blockDim.x;
-    if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
+  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q
+    const int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) {
+      const int i = e / nd_defl, a = e % nd_defl;
+      double2 w = U[i][a];
+      for (int c = 0; c < nd_defl; ++c) {
+        const float2 f = phf[c][i];
+        const double2 q = Q[c][a];
+        w.x += 0.5 * ((double)f.x * q.x + (double)f.y * q.y);
+        w.y += 0.5 * ((double)f.x * q.y - (double)f.y * q.x);
+      }
+      wv[u] = w;
+    }
   }
   __syncthreads();
   for (int u = 0; u < WPT; ++u) {
-    int e = threadIdx.x + u * blockDim.x;
-    if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
+    const int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) {
+      const int i = e / nd_defl, a = e % nd_defl;
+      U[i][a] = wv[u];
+      Wz[i][a] = {df_from_double(wv[u].x), df_from_double(wv[u].y)};
+    }
   }
   __syncthreads();
   // upper triangle (row-wise enumeration), each entry written with its mirror
@@ -719,8 +747,30 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     while (i > 0 && i * nt - (i * (i - 1)) / 2 > e) --i;
     while (i + 1 < nt && (i + 1) * nt - ((i + 1) * i) / 2 <= e) ++i;
     const int j = i + (e - (i * nt - (i * (i - 1)) / 2));
-    double2 r = herm(i, j);
-    add_w_terms(r, i, j, nd_defl, U, ph);
+    // R'_cc (Hermitian part of D' / s^2) and W Phi^T + (W Phi^T)^H in double-float
+    df xr = df_add(df_from_double_scaled(dre(i, j, 0), hx), df_from_double_scaled(dre(j, i, 0), hx));
+    df xi = df_add(df_from_double_scaled(dre(i, j, 1), hx), df_neg(df_from_double_scaled(dre(j, i, 1), hx)));
+    for (int a = 0; a < nd_defl; ++a) {
+      const zdf wi = Wz[i][a], wj = Wz[j][a];
+      const float2 fi = phf[a][i], fj = phf[a][j];
+      // W_ia Phi_ja + conj(W_ja Phi_ia)
+      xr = df_add(xr, df_add(df_mul_f(wi.re, fj.x), df_neg(df_mul_f(wi.im, fj.y))));
+      xr = df_add(xr, df_add(df_mul_f(wj.re, fi.x), df_neg(df_mul_f(wj.im, fi.y))));
+      xi = df_add(xi, df_add(df_mul_f(wi.re, fj.y), df_mul_f(wi.im, fj.x)));
+      xi = df_add(xi, df_neg(df_add(df_mul_f(wj.re, fi.y), df_mul_f(wj.im, fi.x))));
+    }
+    double2 r;
+    if (isfinite(xr.hi) && isfinite(xr.lo) && isfinite(xi.hi) && isfinite(xi.lo)) {
+      r = make_double2(df_to_double(xr), df_to_double(xi));
+    } else {   // beyond the float range: FP64
+      r = herm(i, j);
+      for (int a = 0; a < nd_defl; ++a) {
+        const double2 wi = U[i][a], wj = U[j][a];
+        const double2 fj = make_double2(phf[a][j].x, phf[a][j].y), fi = make_double2(phf[a][i].x, phf[a][i].y);
+        r.x += (wi.x * fj.x - wi.y * fj.y) + (wj.x * fi.x - wj.y * fi.y);
+        r.y += (wi.x * fj.y + wi.y * fj.x) - (wj.x * fi.y + wj.y * fi.x);
+      }
+    }
     if (i == j) r.y = 0.0;
     R[(size_t)k * nt * nt + (size_t)i * nt + j] = r;
     if (i != j) R[(size_t)k * nt * nt + (size_t)j * nt + i] = make_double2(r.x, -r.y);
@@ -1078,7 +1128,7 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   // four blocks per window: each recomputes the window's W-form columns (FP64), so fewer blocks
   // cost less FP64 work in total, and four still fill the GPU at Nd = 64
   dim3 grid((nup + 255) / 256 < 4 ? (nup + 255) / 256 : 4, P->nd);
-  gram_assemble_tc_kernel<<<grid, 256, gram_assemble_smem_bytes(P->nt, P->ndefl), st>>>(
+  gram_assemble_tc_kernel<<<grid, 256, gram_assemble_tc_smem_bytes(P->nt, P->ndefl), st>>>(
       P->tc_T > 1 ? P->ws.gtc : sums, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ndefl > kQExactMax ? P->ndefl : 0,
       P->ws.phi, P->ws.xmax,
                                                  P->tc_T > 1 ? (size_t)P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
@@ -1139,7 +1189,7 @@ cudaError_t gram_tc_configure() {
   size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
   for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
   cudaError_t e = cudaFuncSetAttribute(gram_assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)gram_assemble_smem_bytes(kEvdNmax, kDeflateMax));
+                                       (int)gram_assemble_tc_smem_bytes(kEvdNmax, kDeflateMax));
   if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_F16X3>(mx);
   if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_BF16X3>(mx);
   if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_F16>(mx);
