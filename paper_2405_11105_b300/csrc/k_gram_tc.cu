@@ -568,7 +568,8 @@ gram_tcb_kernel(const float2* __restrict__ xa, int nz, int nx, int nt /* rows ti
 }
 
 // Coefficient block Q[a][b] = sum_p g^2 conj(a_pa) a_pb with exact products
-// (double-float), one partial per (window, split).
+// (double-float), one partial per (window, split).  Q is Hermitian: the upper triangle is summed
+// and the lower written as its conjugate.
 __global__ void __launch_bounds__(256)
 gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl, const Box* __restrict__ boxes,
               const float* __restrict__ gz, const float* __restrict__ gx, int nsplit, double2* __restrict__ q) {
@@ -592,7 +593,7 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
 #pragma unroll
     for (int i = 0; i < kQExactMax; ++i)
 #pragma unroll
-      for (int j = 0; j < kQExactMax; ++j) {
+      for (int j = i; j < kQExactMax; ++j) {
         if (i >= nd_defl || j >= nd_defl) continue;
         df wr = two_prod_df(g2, a[i].x), wi = two_prod_df(-g2, a[i].y);   // g^2 conj(a_i)
         df rr = df_mul_f(wr, a[j].x), ii = df_mul_f(wi, a[j].y);
@@ -605,6 +606,7 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
   __shared__ df red_r[8][kQExactMax * kQExactMax], red_i[8][kQExactMax * kQExactMax];
 #pragma unroll
   for (int e = 0; e < kQExactMax * kQExactMax; ++e) {
+    if (e / kQExactMax > e % kQExactMax) continue;   // the upper triangle only
     df vr = qr[e], vi = qi[e];
     for (int o = 16; o; o >>= 1) {
       df tr = {__shfl_xor_sync(~0u, vr.hi, o), __shfl_xor_sync(~0u, vr.lo, o)};
@@ -616,25 +618,18 @@ gram_q_kernel(const float2* __restrict__ xa, int nz, int nx, int nt, int nd_defl
   }
   __syncthreads();
   if (tid < kQExactMax * kQExactMax) {
+    const int i = tid / kQExactMax, j = tid % kQExactMax, e = i <= j ? tid : j * kQExactMax + i;
     df vr = {0.f, 0.f}, vi = {0.f, 0.f};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { vr = df_add(vr, red_r[w][tid]); vi = df_add(vi, red_i[w][tid]); }
-    q[((size_t)k * nsplit + s) * kQExactMax * kQExactMax + tid] = make_double2(df_to_double(vr), df_to_double(vi));
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { vr = df_add(vr, red_r[w][e]); vi = df_add(vi, red_i[w][e]); }
+    const double im = df_to_double(vi);
+    q[((size_t)k * nsplit + s) * kQExactMax * kQExactMax + tid] = make_double2(df_to_double(vr), i <= j ? im : -im);
   }
 }
 
 // R from the tensor-core partials: R' = Herm(sum D') / s^2 for the residual block and U
 // (U from the CUDA-core augmented-column partials instead when the tensor-core rows
 // nb are the residual rows alone, nb = nt), Q from the exact kernel;
-// R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T, i.e. R'_cc + W Phi^T + (W Phi^T)^H with
-// W = U + 1/2 conj(Phi) Q.  W is formed in FP64 (nt d entries); the Nt (Nt + 1) / 2 entries of R
-// are summed in double-float on the FP32 pipes (the partials split into two floats on the integer
-// pipes, the power-of-two scale folded into the exponent), FP64 being ~1/62 of FP32 on this part;
-// an entry whose double-float sum leaves the float range is redone in FP64.
-// Shared memory: W [nt][kDeflateMax] (double2), Q [kDeflateMax]^2 (double2), W again as double-float
-// [nt][kDeflateMax], Phi [d][kEvdNmax] (float2).
-static size_t gram_assemble_tc_smem_bytes(int nt, int nd_defl) {
-  return ((size_t)(nt + kDeflateMax) * kDeflateMax + (size_t)nt * kDeflateMax) * 16 + (size_t)nd_defl * kEvdNmax * 8;
-}
+// R = R'_cc + U Phi^T + Phi U^H + Phi Q Phi^T (FP64)
 __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const double2* __restrict__ qpart,
                                         const double2* __restrict__ aug, int aug_nsplit, int aug_qrows,
                                         const float2* __restrict__ phi, const unsigned* __restrict__ xmax_bits,
@@ -644,24 +639,18 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   // packets whose augmented rows fit one tile)
   const int k = blockIdx.y;
   const double* pk = part + (size_t)k * wstride;
-  extern __shared__ double2 asm_dyn[];
+  extern __shared__ double2 asm_dyn[];   // U [nt][kDeflateMax], Q [kDeflateMax]^2, ph [d][kEvdNmax]
   double2 (*U)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn);
   double2 (*Q)[kDeflateMax] = reinterpret_cast<double2 (*)[kDeflateMax]>(asm_dyn + (size_t)nt * kDeflateMax);
-  zdf (*Wz)[kDeflateMax] = reinterpret_cast<zdf (*)[kDeflateMax]>(asm_dyn + (size_t)(nt + kDeflateMax) * kDeflateMax);
-  float2 (*phf)[kEvdNmax] =
-      reinterpret_cast<float2 (*)[kEvdNmax]>(asm_dyn + (size_t)(2 * nt + kDeflateMax) * kDeflateMax);
+  double2 (*ph)[kEvdNmax] =
+      reinterpret_cast<double2 (*)[kEvdNmax]>(asm_dyn + (size_t)(nt + kDeflateMax) * kDeflateMax);
   __shared__ double inv_s2;
-  __shared__ int hx_s;
   if (threadIdx.x == 0) {
     float sc = tc::pow2_scale(__uint_as_float(*xmax_bits));
     inv_s2 = 1.0 / ((double)sc * (double)sc);
-    int e;
-    frexpf(sc, &e);          // sc = 2^(e - 1)
-    hx_s = 2 * (e - 1) + 1;   // 1/2 of 1/sc^2 = 2^-hx
   }
   __syncthreads();
   const double is2 = inv_s2;
-  const int hx = hx_s;
   // Hermitian part of the summed D' at (a, b)
   // (split 0 of each window holds the sum over splits, see gram_tc_reduce_kernel)
   const size_t t2 = (size_t)tb * tb;
@@ -689,7 +678,8 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
       }
       U[i][a] = make_double2(sx, sy);
     }
-    phf[a][i] = phi[a * nt + i];
+    float2 f = phi[a * nt + i];
+    ph[a][i] = make_double2((double)f.x, (double)f.y);
   }
   for (int e = threadIdx.x; e < nd_defl * nd_defl; e += blockDim.x) {
     int a = e / nd_defl, c = e % nd_defl;
@@ -714,28 +704,14 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
   __syncthreads();
   constexpr int WPT = (kEvdNmax * kDeflateMax + 255) / 256;   // W entries per thread (blockDim 256)
   double2 wv[WPT];
-  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q
-    const int e = threadIdx.x + u * blockDim.x;
-    if (e < nt * nd_defl) {
-      const int i = e / nd_defl, a = e % nd_defl;
-      double2 w = U[i][a];
-      for (int c = 0; c < nd_defl; ++c) {
-        const float2 f = phf[c][i];
-        const double2 q = Q[c][a];
-        w.x += 0.5 * ((double)f.x * q.x + (double)f.y * q.y);
-        w.y += 0.5 * ((double)f.x * q.y - (double)f.y * q.x);
-      }
-      wv[u] = w;
-    }
+  for (int u = 0; u < WPT; ++u) {              // W = U + 1/2 conj(Phi) Q (nt*d <= 496 < 512)
+    int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) wv[u] = deflated_w(e / nd_defl, e % nd_defl, nd_defl, U, Q, ph);
   }
   __syncthreads();
   for (int u = 0; u < WPT; ++u) {
-    const int e = threadIdx.x + u * blockDim.x;
-    if (e < nt * nd_defl) {
-      const int i = e / nd_defl, a = e % nd_defl;
-      U[i][a] = wv[u];
-      Wz[i][a] = {df_from_double(wv[u].x), df_from_double(wv[u].y)};
-    }
+    int e = threadIdx.x + u * blockDim.x;
+    if (e < nt * nd_defl) U[e / nd_defl][e % nd_defl] = wv[u];
   }
   __syncthreads();
   // upper triangle (row-wise enumeration), each entry written with its mirror
@@ -747,30 +723,8 @@ __global__ void gram_assemble_tc_kernel(const double* __restrict__ part, const d
     while (i > 0 && i * nt - (i * (i - 1)) / 2 > e) --i;
     while (i + 1 < nt && (i + 1) * nt - ((i + 1) * i) / 2 <= e) ++i;
     const int j = i + (e - (i * nt - (i * (i - 1)) / 2));
-    // R'_cc (Hermitian part of D' / s^2) and W Phi^T + (W Phi^T)^H in double-float
-    df xr = df_add(df_from_double_scaled(dre(i, j, 0), hx), df_from_double_scaled(dre(j, i, 0), hx));
-    df xi = df_add(df_from_double_scaled(dre(i, j, 1), hx), df_neg(df_from_double_scaled(dre(j, i, 1), hx)));
-    for (int a = 0; a < nd_defl; ++a) {
-      const zdf wi = Wz[i][a], wj = Wz[j][a];
-      const float2 fi = phf[a][i], fj = phf[a][j];
-      // W_ia Phi_ja + conj(W_ja Phi_ia)
-      xr = df_add(xr, df_add(df_mul_f(wi.re, fj.x), df_neg(df_mul_f(wi.im, fj.y))));
-      xr = df_add(xr, df_add(df_mul_f(wj.re, fi.x), df_neg(df_mul_f(wj.im, fi.y))));
-      xi = df_add(xi, df_add(df_mul_f(wi.re, fj.y), df_mul_f(wi.im, fj.x)));
-      xi = df_add(xi, df_neg(df_add(df_mul_f(wj.re, fi.y), df_mul_f(wj.im, fi.x))));
-    }
-    double2 r;
-    if (isfinite(xr.hi) && isfinite(xr.lo) && isfinite(xi.hi) && isfinite(xi.lo)) {
-      r = make_double2(df_to_double(xr), df_to_double(xi));
-    } else {   // beyond the float range: FP64
-      r = herm(i, j);
-      for (int a = 0; a < nd_defl; ++a) {
-        const double2 wi = U[i][a], wj = U[j][a];
-        const double2 fj = make_double2(phf[a][j].x, phf[a][j].y), fi = make_double2(phf[a][i].x, phf[a][i].y);
-        r.x += (wi.x * fj.x - wi.y * fj.y) + (wj.x * fi.x - wj.y * fi.y);
-        r.y += (wi.x * fj.y + wi.y * fj.x) - (wj.x * fi.y + wj.y * fi.x);
-      }
-    }
+    double2 r = herm(i, j);
+    add_w_terms(r, i, j, nd_defl, U, ph);
     if (i == j) r.y = 0.0;
     R[(size_t)k * nt * nt + (size_t)i * nt + j] = r;
     if (i != j) R[(size_t)k * nt * nt + (size_t)j * nt + i] = make_double2(r.x, -r.y);
@@ -1128,7 +1082,7 @@ cudaError_t launch_gram_assemble_tc(const lcf_plan* P, cudaStream_t st) {
   // four blocks per window: each recomputes the window's W-form columns (FP64), so fewer blocks
   // cost less FP64 work in total, and four still fill the GPU at Nd = 64
   dim3 grid((nup + 255) / 256 < 4 ? (nup + 255) / 256 : 4, P->nd);
-  gram_assemble_tc_kernel<<<grid, 256, gram_assemble_tc_smem_bytes(P->nt, P->ndefl), st>>>(
+  gram_assemble_tc_kernel<<<grid, 256, gram_assemble_smem_bytes(P->nt, P->ndefl), st>>>(
       P->tc_T > 1 ? P->ws.gtc : sums, P->ws.gq, P->ws.gaug, P->aug_nsplit, P->ndefl > kQExactMax ? P->ndefl : 0,
       P->ws.phi, P->ws.xmax,
                                                  P->tc_T > 1 ? (size_t)P->tc_T * P->tc_T * 2 * P->tc_tb * P->tc_tb
@@ -1189,7 +1143,7 @@ cudaError_t gram_tc_configure() {
   size_t mx = 0;   // the largest launch over every augmented row length (three or two stages)
   for (int na = 3; na <= kTcGramNaMax; ++na) mx = gram_tc_smem_bytes(na) > mx ? gram_tc_smem_bytes(na) : mx;
   cudaError_t e = cudaFuncSetAttribute(gram_assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)gram_assemble_tc_smem_bytes(kEvdNmax, kDeflateMax));
+                                       (int)gram_assemble_smem_bytes(kEvdNmax, kDeflateMax));
   if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_F16X3>(mx);
   if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_BF16X3>(mx);
   if (e == cudaSuccess) e = gram_tc_configure_gp<LCF_GP_F16>(mx);
