@@ -34,10 +34,10 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.88 MB
-    ("evd", "os"): {"bytes": 14.30e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.87 MB
+    ("evd", "os"): {"bytes": 14.29e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "01e338df1ff1fae35a2e11c0da3c3ec6f7dabbe1f00cf017f8ebf5791131d01d",
+                                "612b012f8bc79af98cc42cc7e42383657820836cc05ffc99f2d83bbee45cda4c",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "8c289eda9c7e7231dae1028e56bbd723621b784f046164a1530f2268e80bf034",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":
