@@ -34,14 +34,14 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.87 MB
-    ("evd", "os"): {"bytes": 14.29e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.89 MB
+    ("evd", "os"): {"bytes": 14.31e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "612b012f8bc79af98cc42cc7e42383657820836cc05ffc99f2d83bbee45cda4c",
+                                "732621d3116a929561881f0ccd68b4147924be053e204fe7805ccc6bf19e1c83",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "8c289eda9c7e7231dae1028e56bbd723621b784f046164a1530f2268e80bf034",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":
-                                "e94da384b6101ccb3ec412d8d3462094bdb5b419f12848449819fe823d146e62",
+                                "0f0ae737dea39388208244c9264a3fb8da86ac8d54d0816e2b38660ff92a5563",
                                 "paper_2405_11105_b300/csrc/lcf_internal.cuh":
                                 "1e0aa59856ef34cb4cfdb48503a50b03a87dd782a8fce27ded9e732ed9cdd007"}},
     ("evd", "pair"): {"bytes": 10.55e6, "profile": "profiles/evd_pair_kernel_256x128x100_8x8.md",

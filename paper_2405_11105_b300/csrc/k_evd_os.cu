@@ -234,82 +234,6 @@ __device__ __forceinline__ bool eo_bstep(float2 (&XR)[8][RP], float2 (&XI)[8][RP
   return wmask != 0u;
 }
 
-// k of a hard rule (FIXED, CURVATURE, SLOPE, MEDIAN) over the whole CTA: the per-element FP64
-// arithmetic of ep_rule_k (log10, the normalisation, the two gradients, the curvature) one element
-// per thread, so the FP64 units of all four schedulers share it (warp 0 alone took ~40 us at
-// Nt = 100); the maximum (ties to the smallest index) and the counts do not depend on the order.
-// Every thread calls it and gets k.  Uses y, d1, d2 (n doubles each) and red (one int).
-__device__ int eo_rule_k_cta(int mode, const double* lam, int n, double beta, int k_fixed, int literal, double* y,
-                             double* d1, double* d2, int* red, int tid, int nthr) {
-  if (mode == LCF_T_FIXED) return k_fixed < 0 ? 0 : (k_fixed > n ? n : k_fixed);
-  if (mode == LCF_T_MEDIAN) {
-    const double med = (n & 1) ? lam[n / 2] : 0.5 * (lam[n / 2 - 1] + lam[n / 2]);
-    const double T = beta * med;
-    if (tid == 0) *red = 0;
-    __syncthreads();
-    int cnt = 0;
-    for (int i = tid; i < n; i += nthr) cnt += lam[i] > T;
-    if (cnt) atomicAdd(red, cnt);
-    __syncthreads();
-    const int r = *red;
-    __syncthreads();
-    return r;
-  }
-  if (mode != LCF_T_CURVATURE && mode != LCF_T_SLOPE) return 0;
-  if (mode == LCF_T_CURVATURE ? n < 3 : n < 2) return 0;
-  const double bt = mode == LCF_T_CURVATURE ? beta : 1.0;
-  for (int i = tid; i < n; i += nthr) y[i] = log10(ep_floor(lam, n, i));
-  __syncthreads();
-  const double y1 = y[0], yn = y[n - 1], span = y1 - yn;
-  __syncthreads();
-  for (int i = tid; i < n; i += nthr) {
-    if (literal) y[i] = (y1 != 0.0) ? bt * y[i] / y1 * n : 0.0;
-    else y[i] = (span > 0) ? bt * n * (y[i] - yn) / span : 0.0;
-  }
-  __syncthreads();
-  for (int i = tid; i < n; i += nthr)
-    d1[i] = i == 0 ? y[1] - y[0] : (i == n - 1 ? y[n - 1] - y[n - 2] : 0.5 * (y[i + 1] - y[i - 1]));
-  __syncthreads();
-  if (mode == LCF_T_SLOPE) {
-    if (tid == 0) *red = n - 1;
-    __syncthreads();
-    for (int i = tid; i < n; i += nthr)
-      if (-d1[i] <= beta) atomicMin(red, i);
-    __syncthreads();
-    const int r = *red;
-    __syncthreads();
-    return r;
-  }
-  for (int i = tid; i < n; i += nthr)
-    d2[i] = i == 0 ? d1[1] - d1[0] : (i == n - 1 ? d1[n - 1] - d1[n - 2] : 0.5 * (d1[i + 1] - d1[i - 1]));
-  __syncthreads();
-  for (int i = tid; i < n; i += nthr) {   // the curvature, into y
-    if (i >= 1 && i < n - 1) {
-      const double q = 1.0 + d1[i] * d1[i];
-      y[i] = fabs(d2[i]) / (q * sqrt(q));
-    }
-  }
-  __syncthreads();
-  if (tid < 32) {
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = 1 + tid; i < n - 1; i += 32) {
-      const double kap = y[i];
-      if (kap > best) { best = kap; bi = i; }
-    }
-    for (int o = 16; o; o >>= 1) {   // max, ties to the smallest index (first maximum)
-      const double ob = __shfl_xor_sync(~0u, best, o);
-      const int oi = __shfl_xor_sync(~0u, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (tid == 0) *red = bi == 0x7fffffff ? 2 : bi + 1;
-  }
-  __syncthreads();
-  const int r = *red;
-  __syncthreads();
-  return r;
-}
-
 template <int RP>
 __global__ void __launch_bounds__(EO_THREADS, 1)
 evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, const float2* __restrict__ Tg,
@@ -666,37 +590,8 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   __syncthreads();
   __shared__ int sh_red;
   __shared__ double sh_mx;
-  int kk = -1;
-  {
-    const int md = g.thresh_mode;
-    if (md == LCF_T_NONE) {
-      for (int i = tid; i < n; i += nthr) wts[i] = 1.0;
-      kk = 0;
-    } else if (md <= LCF_T_MEDIAN) {
-      kk = eo_rule_k_cta(md, lam_s, n, g.beta, g.k_fixed, g.curv_norm, s0, s1, s2, &sh_red, tid, nthr);
-      for (int i = tid; i < n; i += nthr) wts[i] = (i + 1 > kk) ? 1.0 : 0.0;
-    } else if (md == LCF_T_SIGMOID) {
-      kk = eo_rule_k_cta(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, &sh_red, tid, nthr);
-      for (int i = tid; i < n; i += nthr) wts[i] = 1.0 / (1.0 + exp(-g.beta * ((i + 1) - kk)));
-    } else {   // LCF_T_ADAPTIVE_SOFT (method 4's rule is applied afterwards by the post kernel)
-      for (int i = tid; i < n; i += nthr) {
-        const double u = n > 1 ? 2.5 * i / (n - 1) : 0.0;
-        wts[i] = -0.5 * u * u - g.beta * log(ep_floor(lam_s, n, i));
-      }
-      __syncthreads();
-      if (warp == 0) {
-        double mx = -INFINITY;
-        for (int i = lane; i < n; i += 32) mx = fmax(mx, wts[i]);
-        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(~0u, mx, o));
-        if (lane == 0) sh_mx = mx;
-      }
-      __syncthreads();
-      const double mx = sh_mx;
-      for (int i = tid; i < n; i += nthr) wts[i] = exp(wts[i] - mx);
-      kk = -1;
-    }
-  }
-  __syncthreads();
+  const int kk = ep_rule_weights_cta(g.thresh_mode, lam_s, n, g.beta, g.beta_src, g.k_fixed, g.k_src, g.curv_norm, wts,
+                                     s0, s1, s2, &sh_red, &sh_mx, tid, nthr);
   if (warp == 0) {
     double S = 0.0;
     for (int i = lane; i < n; i += 32) S += wts[i] * wts[i] * lam_s[i];

@@ -691,30 +691,11 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
   // ---- sort, rule, alpha, kept columns (every CTA the same; CTA 0 writes the per-window results)
   for (int i = tid; i < n; i += nthr) lam_s[i] = lam[sperm[i]] * scale;
   __syncthreads();
+  __shared__ int sh_red;
+  __shared__ double sh_mx;
+  const int kk = ep_rule_weights_cta(g.thresh_mode, lam_s, n, g.beta, g.beta_src, g.k_fixed, g.k_src, g.curv_norm, wts,
+                                     s0, s1, s2, &sh_red, &sh_mx, tid, nthr);
   if (warp == 0) {
-    int kk = -1;
-    const int md = g.thresh_mode;
-    if (md == LCF_T_NONE) {
-      for (int i = lane; i < n; i += 32) wts[i] = 1.0;
-      kk = 0;
-    } else if (md <= LCF_T_MEDIAN) {
-      kk = ep_rule_k(md, lam_s, n, g.beta, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
-      for (int i = lane; i < n; i += 32) wts[i] = (i + 1 > kk) ? 1.0 : 0.0;
-    } else if (md == LCF_T_SIGMOID) {
-      kk = ep_rule_k(g.k_src, lam_s, n, g.beta_src, g.k_fixed, g.curv_norm, s0, s1, s2, lane);
-      for (int i = lane; i < n; i += 32) wts[i] = 1.0 / (1.0 + exp(-g.beta * ((i + 1) - kk)));
-    } else {   // LCF_T_ADAPTIVE_SOFT (method 4's rule is applied afterwards by the post kernel)
-      double mx = -INFINITY;
-      for (int i = lane; i < n; i += 32) {
-        const double u = n > 1 ? 2.5 * i / (n - 1) : 0.0;
-        wts[i] = -0.5 * u * u - g.beta * log(ep_floor(lam_s, n, i));
-        mx = fmax(mx, wts[i]);
-      }
-      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(~0u, mx, o));
-      for (int i = lane; i < n; i += 32) wts[i] = exp(wts[i] - mx);
-      kk = -1;
-    }
-    __syncwarp();
     double S = 0.0;
     for (int i = lane; i < n; i += 32) S += wts[i] * wts[i] * lam_s[i];
     for (int o = 16; o; o >>= 1) S += __shfl_xor_sync(~0u, S, o);
