@@ -45,7 +45,7 @@ namespace lcf {
 constexpr int EO_THREADS = 512;
 constexpr float EO_TOL = 2.0e-6f;              // relative orthogonality test (cosine of two columns)
 constexpr int EO_SUBSPACE_ITERS = 3;
-constexpr int EO_CB = 4;                       // Cholesky columns per trailing update
+constexpr int EO_CB = 8;                       // Cholesky columns per trailing update
 constexpr size_t EO_SMEM_MAX = 227 * 1024;     // dynamic shared memory a CTA may opt in to
 
 struct EoArgs {
