@@ -34,10 +34,10 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the stage's kernels on this workload, valid only while their sources hash as they did then
 CAPTURED_TRAFFIC = {
-    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.87 MB
-    ("evd", "os"): {"bytes": 14.29e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
+    # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.96 MB
+    ("evd", "os"): {"bytes": 14.38e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "5900b28a2dd32dd24d4c80be2aa3e27eab62b7e447c2af810c7eff409f9d7fad",
+                                "80a8b3499bd6545cbe8e9a3874140499a04f7eb340ae0700320ce6518f52b1c4",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "8c289eda9c7e7231dae1028e56bbd723621b784f046164a1530f2268e80bf034",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":

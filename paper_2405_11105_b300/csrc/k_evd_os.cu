@@ -535,19 +535,23 @@ evd_os_kernel(const float2* __restrict__ Bg, const float2* __restrict__ Vhg, con
   __syncthreads();
   // sort positions by squared norm, descending (ties to the lower position); the first n are the
   // eigenpairs (the padding columns past Nt are zero and sort among the zeros)
+  // (the squared norms are >= 0, so their bit patterns order as integers: the comparisons run on
+  // the integer pipes, not on the few FP64 units)
+  const long long* lbits = reinterpret_cast<const long long*>(lam);
   for (int i = tid; i < np; i += nthr) {
-    const double di = lam[i];
+    const long long di = lbits[i];
     int r = 0;
     for (int j = 0; j < np; ++j) {
-      const double dj = lam[j];
+      const long long dj = lbits[j];
       r += (dj > di) || (dj == di && j < i);
     }
     sperm[r] = i;
   }
   __syncthreads();
   // vanished columns: Gram-Schmidt completion (two passes) of unit vectors against the columns before
-  // them in sorted order (warp 0; numerical rank below Nt only)
-  if (warp == 0) {
+  // them in sorted order (warp 0; numerical rank below Nt only: the zeros sort last, so none when the
+  // n-th norm is positive)
+  if (warp == 0 && !(lbits[sperm[n - 1]] > 0)) {
     int cand = 0;
     for (int jj = 0; jj < n; ++jj) {
       const int pos = sperm[jj];

@@ -593,27 +593,28 @@ evd_osc_kernel(const float2* __restrict__ Lg, const int* __restrict__ perm_g,
     lam[i] = t > 7.888609052210118e-31 ? t : 0.0;   // below 2^-100 (largest diagonal in [1/2, 1)): vanished
   }
   __syncthreads();
+  // (the squared norms are >= 0, so their bit patterns order as integers: the comparisons run on
+  // the integer pipes, not on the few FP64 units; coef holds each position's scale until the rule)
+  const long long* lbits = reinterpret_cast<const long long*>(lam);
   for (int i = tid; i < np; i += nthr) {   // positions by squared norm, descending, ties to the lower one
-    const double di = lam[i];
+    const long long di = lbits[i];
     int r = 0;
     for (int j = 0; j < np; ++j) {
-      const double dj = lam[j];
+      const long long dj = lbits[j];
       r += (dj > di) || (dj == di && j < i);
     }
     sperm[r] = i;
+    coef[i] = di > 0 ? ep_rsqrt((float)lam[i]) : 0.f;
   }
   __syncthreads();
   for (int e = tid; e < nr * np; e += nthr) {   // normalise
     const int rr = e / np, pos = e % np;
-    const float sc = lam[pos] > 0.0 ? ep_rsqrt((float)lam[pos]) : 0.f;
-    U[(size_t)rr * lda + pos] = cscale(U[(size_t)rr * lda + pos], sc);
+    U[(size_t)rr * lda + pos] = cscale(U[(size_t)rr * lda + pos], coef[pos]);
   }
   __syncthreads();
   // ---- vanished columns (numerical rank below Nt): Gram-Schmidt completion on CTA 0 over the whole
   // columns, through the scratch buffer [pos][row] in global memory (every CTA decides the same)
-  int nzero = 0;
-  for (int jj = 0; jj < n; ++jj) nzero += lam[sperm[jj]] == 0.0;
-  if (nzero > 0) {
+  if (!(lbits[sperm[n - 1]] > 0)) {   // the zeros sort last: some among the first n
     float2* S = V_out + (size_t)k * n * n;   // [sorted index][row]: V_out is written last
     for (int e = tid; e < nr * n; e += nthr) {
       const int rr = e / n, jj = e % n;
