@@ -10,10 +10,10 @@
 // norm, V = Q U, sort, rules, alpha, phase fix, W.
 //
 //  evd_chol_kernel   one CTA per window: the packed lower triangle of B in shared
-//                    memory, factored in panels of eight columns (warp 0 factors a
-//                    panel left-looking with the pivot on the running diagonal,
-//                    every warp applies it to the trailing triangle); L (pivot row
-//                    order), the permutation and the numerical rank to global memory.
+//                    memory, factored right-looking with diagonal pivoting and no
+//                    interchanges (every thread on each column, the trailing triangle
+//                    updated per block of eight columns); L (pivot row order), the
+//                    permutation and the numerical rank to global memory.
 //  evd_osc_kernel    the sweeps and everything after, on a cluster of four CTAs.  CTA
 //                    c holds rows [c R, (c + 1) R) (R = ceil(Nt / 4)) of every column in
 //                    registers, lane l rows l and l + 32 of the CTA's share as one
@@ -38,109 +38,136 @@ namespace cg = cooperative_groups;
 namespace lcf {
 
 constexpr int EC_THREADS = 1024;               // Cholesky kernel
-constexpr int EC_PANEL = 8;
 constexpr int EQ_C = 4;                        // CTAs per window of the sweeps
 static_assert((EQ_C & (EQ_C - 1)) == 0, "cluster ranks wrap by masking");
 constexpr float EQ_TOL = 2.0e-6f;              // relative orthogonality test
 constexpr int EQ_SUBSPACE_ITERS = 6;
 
 // ---------------------------------------------------------------------------------------------
-// evd_chol_kernel: packed lower triangle (i, c <= i) at i (i + 1) / 2 + c
+// evd_chol_kernel: packed lower triangle (i, c <= i) at i (i + 1) / 2 + c.  Right-looking
+// Cholesky with diagonal pivoting and no interchanges (the one-CTA kernel's scheme): step j takes
+// as pivot the remaining index p with the largest diagonal of the Schur complement (every warp
+// finds it from the list of remaining indices and their diagonal, double-buffered by step
+// parity), writes column j of the factor over p's column of the complement (conjugated where the
+// pair lies above the diagonal) and the square root of the pivot on p's diagonal; columns go in
+// blocks of EC_CB, each column subtracting the block's earlier columns from its stored entries,
+// the remaining triangle taking the block's rank-EC_CB update in one pass over its pairs.  Out: L
+// with rows in pivot order (the indices eliminated at steps 0, 1, ..., then the remaining ones)
+// and that permutation.
 __host__ __device__ inline size_t ec_tri(int n) { return (size_t)n * (n + 1) / 2; }
-size_t evd_chol_smem_bytes(int n) { return ec_tri(n) * 8 + (size_t)n * 4 + 64; }
+constexpr int EC_CB = 8;
+size_t evd_chol_smem_bytes(int n) {
+  return ec_tri(n) * 8 + (size_t)EC_CB * n * 8 + (size_t)2 * n * 4 * 2 + (size_t)2 * n * 4 + 64;
+}
 
 __global__ void __launch_bounds__(EC_THREADS, 1)
 evd_chol_kernel(float2* __restrict__ Bg, const double* __restrict__ scale_g, int n, int* __restrict__ perm_g,
                 int* __restrict__ rank_g) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = EC_THREADS / 32;
-  float2* A = reinterpret_cast<float2*>(smem);                 // packed lower triangle
-  float* dg = reinterpret_cast<float*>(smem + ec_tri(n) * 8);  // running diagonal
+  const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nthr = EC_THREADS;
+  float2* A = reinterpret_cast<float2*>(smem);                            // packed lower triangle
+  float2* gv = A + ec_tri(n);                                             // the block's columns, [EC_CB][n]
+  float* dgb = reinterpret_cast<float*>(gv + (size_t)EC_CB * n);          // diagonal by list position, [2][n]
+  int* remb = reinterpret_cast<int*>(dgb + 2 * n);                        // remaining indices, [2][n]
+  int* pos = remb + 2 * n;                                                // step that eliminated each index
+  int* ord = pos + n;                                                     // index eliminated at each step
   int* perm = perm_g + (size_t)k * n;
-  __shared__ int sh_rank, sh_stop;
   float2* B = Bg + (size_t)k * n * n;
   if (!(scale_g[k] > 0.0)) {   // degenerate window: the sweep kernel writes the empty result
     if (tid == 0) rank_g[k] = 0;
     return;
   }
-  for (int i = warp; i < n; i += nwarp)
+  for (int i = warp; i < n; i += nthr / 32)
     for (int c = lane; c <= i; c += 32) A[ec_tri(i) + c] = B[(size_t)i * n + c];
-  for (int i = tid; i < n; i += EC_THREADS) { dg[i] = B[(size_t)i * n + i].x; perm[i] = i; }
-  if (tid == 0) { sh_rank = n; sh_stop = 0; }
+  for (int i = tid; i < n; i += nthr) { dgb[i] = B[(size_t)i * n + i].x; remb[i] = i; pos[i] = n; }
   __syncthreads();
-  float first = 0.f;
-  for (int j0 = 0; j0 < n; j0 += EC_PANEL) {
-    const int j1 = j0 + EC_PANEL < n ? j0 + EC_PANEL : n;
-    if (warp == 0) {
-      for (int j = j0; j < j1; ++j) {
-        float best = -INFINITY;
-        int bi = 0x7fffffff;
-        for (int i = j + lane; i < n; i += 32) {
-          const float d = dg[i];
-          if (d > best) { best = d; bi = i; }
+  auto S = [&](int r, int c) -> float2* { return r > c ? &A[ec_tri(r) + c] : &A[ec_tri(c) + r]; };
+  int rk = n;
+  {
+    float first = 0.f;
+    bool stop = false;
+    for (int j0 = 0; j0 < n && !stop; j0 += EC_CB) {
+      const int j1 = j0 + EC_CB < n ? j0 + EC_CB : n;
+      int j = j0;
+      for (; j < j1; ++j) {
+        const int cnt = n - j, par = j & 1, t = j - j0;
+        const int* rin = remb + par * n;
+        int* rout = remb + (par ^ 1) * n;
+        const float* din = dgb + par * n;
+        float* dout = dgb + (par ^ 1) * n;
+        constexpr int NQ = (kEvdOscNmax + 31) / 32;
+        float best = -INFINITY;   // the largest remaining diagonal entry, ties to the lower list position
+        int ba = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int a = lane + 32 * q;
+          const float d = a < cnt ? din[a] : -INFINITY;
+          if (d > best) { best = d; ba = a; }
         }
+#pragma unroll
         for (int o = 16; o; o >>= 1) {
           const float ob = __shfl_xor_sync(~0u, best, o);
-          const int oi = __shfl_xor_sync(~0u, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          const int oa = __shfl_xor_sync(~0u, ba, o);
+          if (ob > best || (ob == best && oa < ba)) { best = ob; ba = oa; }
         }
         if (j == 0) first = best;
-        if (!(best > first * 1e-30f) || !isfinite(best)) {
-          if (lane == 0) { sh_rank = j; sh_stop = 1; }
-          break;
-        }
-        const int p = bi;
-        if (p != j) {   // symmetric interchange of j and p (pending panel updates move with the rows)
-          for (int c = lane; c < n; c += 32) {
-            float2 t;
-            if (c < j) {
-              t = A[ec_tri(j) + c]; A[ec_tri(j) + c] = A[ec_tri(p) + c]; A[ec_tri(p) + c] = t;
-            } else if (c == j) {
-              t = A[ec_tri(j) + j]; A[ec_tri(j) + j] = A[ec_tri(p) + p]; A[ec_tri(p) + p] = t;
-              A[ec_tri(p) + j] = cconj(A[ec_tri(p) + j]);
-            } else if (c < p) {
-              t = A[ec_tri(c) + j];
-              A[ec_tri(c) + j] = cconj(A[ec_tri(p) + c]);
-              A[ec_tri(p) + c] = cconj(t);
-            } else if (c > p) {
-              t = A[ec_tri(c) + j]; A[ec_tri(c) + j] = A[ec_tri(c) + p]; A[ec_tri(c) + p] = t;
-            }
-          }
-          if (lane == 0) {
-            const float td = dg[j]; dg[j] = dg[p]; dg[p] = td;
-            const int tp = perm[j]; perm[j] = perm[p]; perm[p] = tp;
-          }
-          __syncwarp();
-        }
+        if (!(best > first * 1e-30f) || !isfinite(best)) { rk = j; stop = true; break; }   // in every warp
+        const int pa = ba, p = rin[pa];
         const float inv = ep_rsqrt(best);
-        for (int i = j + 1 + lane; i < n; i += 32) {
-          float2 v = A[ec_tri(i) + j];
-          for (int l = j0; l < j; ++l) v = csub(v, cmul(A[ec_tri(i) + l], cconj(A[ec_tri(j) + l])));
-          v = cscale(v, inv);
-          A[ec_tri(i) + j] = v;
-          dg[i] -= cabs2(v);
+        for (int a = tid; a < cnt; a += nthr) {
+          const int r = rin[a];
+          if (a == pa) {
+            A[ec_tri(p) + p] = make_float2(best * inv, 0.f);
+            ord[j] = p;
+            pos[p] = j;
+          } else {
+            float2* e = S(r, p);
+            float2 v = r > p ? *e : cconj(*e);
+            for (int u = 0; u < t; ++u) v = csub(v, cmul(gv[u * n + r], cconj(gv[u * n + p])));
+            const float2 g = cscale(v, inv);
+            *e = r > p ? g : cconj(g);
+            gv[t * n + r] = g;
+            const int ao = a - (a > pa);
+            dout[ao] = din[a] - cabs2(g);
+            rout[ao] = r;
+          }
         }
-        if (lane == 0) A[ec_tri(j) + j] = make_float2(best * inv, 0.f);
-        __syncwarp();
+        __syncthreads();
       }
-    }
-    __syncthreads();
-    if (sh_stop) break;
-    for (int i = j1 + warp; i < n; i += nwarp) {
-      for (int l = j1 + lane; l <= i; l += 32) {
-        float2 acc = A[ec_tri(i) + l];
-        for (int c = j0; c < j1; ++c) acc = csub(acc, cmul(A[ec_tri(i) + c], cconj(A[ec_tri(l) + c])));
-        A[ec_tri(i) + l] = acc;
+      if (stop) break;
+      // the block's update of the remaining lower triangle: pair e = a (a - 1) / 2 + b of list
+      // positions b < a; S(r, c) -= sum_u g_u[r] conj(g_u[c]) for the pair's indices r, c
+      const int cnt = n - j, nb = j - j0;
+      const int* rl = remb + (j & 1) * n;
+      const int npair = cnt * (cnt - 1) / 2;
+      for (int e = tid; e < npair; e += nthr) {
+        int a = (int)(0.5f * (1.f + sqrtf(8.f * (float)e + 1.f)));
+        if (a * (a - 1) / 2 > e) --a;
+        else if ((a + 1) * a / 2 <= e) ++a;
+        const int b = e - a * (a - 1) / 2;
+        const int r = rl[a], c = rl[b];
+        const int hi = r > c ? r : c, lo = r > c ? c : r;
+        float2 acc = A[ec_tri(hi) + lo];
+        for (int u = 0; u < nb; ++u) acc = csub(acc, cmul(gv[u * n + hi], cconj(gv[u * n + lo])));
+        A[ec_tri(hi) + lo] = acc;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
+  // the permutation: the eliminated indices in step order, then the remaining ones (a stop at step
+  // rk leaves them in list parity rk & 1)
+  for (int i = tid; i < n; i += nthr) perm[i] = i < rk ? ord[i] : remb[(rk & 1) * n + (i - rk)];
   __syncthreads();
-  const int rk = sh_rank;
-  // L (rows in pivot order) over B: zero above the diagonal and from column rk on
-  for (int e = tid; e < n * n; e += EC_THREADS) {
+  // L (rows in pivot order) over B: zero above the diagonal and from column rk on; row i of L is
+  // row perm[i] of the factor, whose column c (pivot pc) is S(perm[i], pc) below the pivot's step
+  for (int e = tid; e < n * n; e += nthr) {
     const int i = e / n, c = e % n;
-    B[e] = (c <= i && c < rk) ? A[ec_tri(i) + c] : make_float2(0.f, 0.f);
+    float2 v = make_float2(0.f, 0.f);
+    if (c <= i && c < rk) {
+      const int r = perm[i], pc = ord[c];
+      v = r == pc ? A[ec_tri(r) + r] : (r > pc ? A[ec_tri(r) + pc] : cconj(A[ec_tri(pc) + r]));
+    }
+    B[e] = v;
   }
   if (tid == 0) rank_g[k] = rk;
 }
