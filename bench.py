@@ -37,7 +37,7 @@ CAPTURED_TRAFFIC = {
     # the one-sided EVD stage: evd_prep_kernel 10.42 MB + evd_os_kernel 3.96 MB
     ("evd", "os"): {"bytes": 14.38e6, "profile": "profiles/evd_os_kernel_256x128x100_8x8.md",
                     "sources": {"paper_2405_11105_b300/csrc/k_evd_os.cu":
-                                "80a8b3499bd6545cbe8e9a3874140499a04f7eb340ae0700320ce6518f52b1c4",
+                                "8d62c741b5101e16eb4d05782250bfe92fdd39a8416b05f0a10e69fda5e06f33",
                                 "paper_2405_11105_b300/csrc/k_evd_dist.cu":
                                 "8c289eda9c7e7231dae1028e56bbd723621b784f046164a1530f2268e80bf034",
                                 "paper_2405_11105_b300/csrc/evd_common.cuh":

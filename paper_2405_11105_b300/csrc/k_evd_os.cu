@@ -34,7 +34,8 @@
 // steps), so a sweep meets every pair of columns once, in 8 nw - 1 steps like the circle ordering
 // of single columns.  A step sums the four slots' partial Grams over the warp (reduce-scatter),
 // forms the rotations (the formulas of the two-sided kernels, ep_rotation_os) and applies them;
-// the CTA meets at a barrier twice per round instead of once per step.
+// the CTA meets at a barrier once per round (twice where only one exchange buffer fits) instead
+// of once per step.
 #include <math.h>
 
 #include "evd_common.cuh"
